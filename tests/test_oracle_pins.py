@@ -1,0 +1,407 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+None of these re-types an oracle formula: each compares the oracle with an
+independent route to the same result -- closed-form stencils and eigenvalues
+of the d-linear finite element operator, the Galerkin identity of nested
+element spaces, the textbook additive correction scheme (Algorithm 1) built
+from Kronecker products, dense direct solves, and the analytic Poisson
+solution of Section 7.1.
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+TH = math.pi / 6
+
+
+def dense_level(d, level, k2, theta, w):
+    """Dense matrix of the oracle's level operator on interior unknowns,
+    obtained by applying it to unit vectors."""
+    lev = O.Level(d, level, k2, theta, w)
+    n = 3 ** level
+    inner = list(itertools.product(range(1, n), repeat=d))
+    A = np.zeros((len(inner), len(inner)), dtype=np.complex128)
+    for j, idx in enumerate(inner):
+        e = np.zeros((n + 1,) * d, dtype=np.complex128)
+        e[idx] = 1
+        col = lev.apply(e)
+        A[:, j] = [col[i] for i in inner]
+    return A, inner, lev
+
+
+# ---------------------------------------------------------------- 1D blocks
+def tri_1d(hs):
+    """Assembled 1D stiffness and mass on n cells of widths hs, interior rows
+    and columns: the textbook tridiagonal matrices of linear elements."""
+    n = len(hs)
+    K = np.zeros((n - 1, n - 1), dtype=np.complex128)
+    M = np.zeros((n - 1, n - 1), dtype=np.complex128)
+    for i in range(1, n):  # vertex i between cells i-1 and i
+        r = i - 1
+        K[r, r] = 1 / hs[i - 1] + 1 / hs[i]
+        M[r, r] = (hs[i - 1] + hs[i]) / 3
+        if r > 0:
+            K[r, r - 1] = -1 / hs[i - 1]
+            M[r, r - 1] = hs[i - 1] / 6
+        if r < n - 2:
+            K[r, r + 1] = -1 / hs[i]
+            M[r, r + 1] = hs[i] / 6
+    return K, M
+
+
+def kron_all(mats):
+    out = mats[0]
+    for m in mats[1:]:
+        out = np.kron(out, m)
+    return out
+
+
+def kron_operator(d, level, theta, w, k2):
+    """H = sum_j (x)_k (K if k == j else M) - k2 (x)_k M for a constant shift:
+    the separable form of the tensor-product element operator."""
+    hs = O.axis_spacing(level, theta, w)  # same widths on every axis
+    K, M = tri_1d(hs)
+    H = -k2 * kron_all([M] * d)
+    for j in range(d):
+        H = H + kron_all([K if k == j else M for k in range(d)])
+    return H
+
+
+def interp_1d(nc):
+    """Interior-to-interior tripartite linear interpolation in 1D."""
+    P = np.zeros((3 * nc - 1, nc - 1))
+    for c in range(1, nc):
+        for o in range(-2, 3):
+            f = 3 * c + o
+            if 1 <= f <= 3 * nc - 1:
+                P[f - 1, c - 1] = 1 - abs(o) / 3
+    return P
+
+
+# ---------------------------------------------------------------- element matrices
+def test_element_matrix_2d_closed_form():
+    h = 1 / 9
+    kc, mc = O.element_matrices((h, h))
+    # bilinear square element, local order (y, x): (0,0),(0,1),(1,0),(1,1)
+    K = np.array([[4, -1, -1, -2], [-1, 4, -2, -1], [-1, -2, 4, -1], [-2, -1, -1, 4]]) / 6
+    M = np.array([[4, 2, 2, 1], [2, 4, 1, 2], [2, 1, 4, 2], [1, 2, 2, 4]]) * h * h / 36
+    np.testing.assert_allclose(kc, K, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(mc, M, rtol=0, atol=1e-18)
+
+
+def _stencil(d, level, with_phi, k2=0.0, theta=0.0, w=0.0):
+    n = 3 ** level
+    lev = O.Level(d, level, np.full((n + 1,) * d, k2), theta, w)
+    e = np.zeros((n + 1,) * d, dtype=np.complex128)
+    c = (n // 2,) * d
+    e[c] = 1
+    col = lev.apply(e, with_phi=with_phi)
+    sl = tuple(slice(i - 1, i + 2) for i in c)
+    return col[sl]
+
+
+def test_assembled_stencils_2d():
+    h = 1 / 27
+    K = _stencil(2, 3, True)
+    np.testing.assert_allclose(K, np.array([[-1, -1, -1], [-1, 8, -1], [-1, -1, -1]]) / 3,
+                               rtol=0, atol=1e-14)
+    M = _stencil(2, 3, False)
+    np.testing.assert_allclose(M, np.array([[1, 4, 1], [4, 16, 4], [1, 4, 1]]) * h * h / 36,
+                               rtol=1e-14, atol=0)
+
+
+def test_assembled_stencils_3d():
+    h = 1 / 9
+    K = _stencil(3, 2, True)
+    cls = np.zeros((3, 3, 3))
+    for idx in itertools.product(range(3), repeat=3):
+        nz = sum(1 for i in idx if i != 1)
+        cls[idx] = {0: 8 * h / 3, 1: 0.0, 2: -h / 6, 3: -h / 12}[nz]
+    np.testing.assert_allclose(K, cls, rtol=0, atol=1e-15)
+    M = _stencil(3, 2, False)
+    w = np.array([1.0, 4.0, 1.0])
+    ref = np.einsum("i,j,k->ijk", w, w, w) * h ** 3 / 216
+    np.testing.assert_allclose(M, ref, rtol=1e-14, atol=0)
+
+
+def test_diagonal_closed_form_and_dense():
+    # uniform real interior: D = 8/3 - k^2 * 16 h^2/36
+    h, k2 = 1 / 27, (4 * math.pi) ** 2
+    n = 27
+    lev = O.Level(2, 3, np.full((n + 1,) * 2, k2), 0.0, 0.0)
+    np.testing.assert_allclose(lev.diag[5, 7], 8 / 3 - k2 * 16 * h * h / 36, rtol=1e-14)
+    # with a layer and a varying shift: the diagonal of the dense operator
+    rng = np.random.default_rng(0)
+    k2f = rng.uniform(10, 50, size=(10, 10))
+    A, inner, lev = dense_level(2, 2, k2f, TH, 0.2)
+    np.testing.assert_allclose([lev.diag[i] for i in inner], np.diag(A), rtol=1e-14)
+
+
+# ---------------------------------------------------------------- operator
+@pytest.mark.parametrize("d,level", [(2, 3), (3, 2)])
+def test_sine_mode_eigenvalues_uniform_complex_scaling(d, level):
+    """Full complex scaled grid (w = 0.5): H s = lambda s for the Dirichlet
+    sine modes with lambda = sum_j kappa_j prod_{k!=j} mu_k - k^2 prod mu."""
+    n = 3 ** level
+    k2 = (4 * math.pi) ** 2
+    lev = O.Level(d, level, np.full((n + 1,) * d, k2), TH, 0.5)
+    hc = (1 / n) * complex(math.cos(TH), math.sin(TH))
+    x = np.arange(n + 1) / n
+    for modes in [(1,) * d, (2, 3, 1)[:d], (n - 1,) + (4,) * (d - 1)]:
+        s = np.ones((1,) * d)
+        for ax, m in enumerate(modes):
+            shape = [1] * d
+            shape[ax] = n + 1
+            s = s * np.sin(m * math.pi * x).reshape(shape)
+        s = s.astype(np.complex128)
+        kap = [(2 / hc) * (1 - math.cos(m * math.pi / n)) for m in modes]
+        mu = [(hc / 3) * (2 + math.cos(m * math.pi / n)) for m in modes]
+        lam = -k2 * np.prod(mu)
+        for j in range(d):
+            lam += kap[j] * np.prod([mu[k] for k in range(d) if k != j])
+        Hs = lev.apply(s)
+        inner = (slice(1, -1),) * d
+        np.testing.assert_allclose(Hs[inner], lam * s[inner], rtol=1e-12,
+                                   atol=1e-13 * abs(lam))
+
+
+@pytest.mark.parametrize("d,level,w", [(2, 2, 0.2), (2, 3, 4 / 27), (3, 2, 0.1)])
+def test_operator_equals_kronecker_of_1d_elements(d, level, w):
+    """Coordinate-wise scaling with constant shift gives the separable operator
+    sum_j (x)(K or M) - k^2 (x)M of 1D assembled matrices with per-cell widths."""
+    n = 3 ** level
+    k2 = 30.0
+    A, _, _ = dense_level(d, level, np.full((n + 1,) * d, k2), TH, w)
+    H = kron_operator(d, level, TH, w, k2)
+    np.testing.assert_allclose(A, H, rtol=0, atol=1e-13 * np.abs(H).max())
+
+
+def test_complex_symmetric_with_layer_and_varying_shift():
+    rng = np.random.default_rng(1)
+    k2 = rng.uniform(-20, 80, size=(10, 10))
+    A, _, _ = dense_level(2, 2, k2, TH, 0.15)
+    np.testing.assert_allclose(A, A.T, rtol=0, atol=1e-14 * np.abs(A).max())
+    assert np.abs(A - A.conj().T).max() > 1e-3  # not Hermitian: complex h
+
+
+def test_layer_membership_and_mass_rhs():
+    """f = 1: b_v = sum over adjacent cells of prod_j h_j / 2^d, so a vertex
+    whose cells are rotated along x only gets h e^{i th} * h (coordinate-wise
+    scaling); the centre-of-cell rule puts exactly 4 cells per side in the
+    layer of width 4/27 at depth 3."""
+    n = 27
+    rot = O.rotated_cells(3, 4 / 27)
+    assert rot.sum() == 8 and rot[:4].all() and rot[-4:].all() and not rot[4:-4].any()
+    assert O.rotated_cells(2, 4 / 27).sum() == 2 and O.rotated_cells(1, 4 / 27).sum() == 0
+    assert O.rotated_cells(3, 0.5).all()
+    h = 1 / n
+    e = complex(math.cos(TH), math.sin(TH))
+    H = O.Hierarchy(2, 3, np.zeros((n + 1, n + 1)), TH, 4 / 27)
+    H.set_rhs_nodal(np.ones((n + 1, n + 1)))
+    b = H.b
+    np.testing.assert_allclose(b[13, 13], h * h, rtol=1e-14)          # interior
+    np.testing.assert_allclose(b[13, 2], h * e * h, rtol=1e-14)       # x-layer only (axis 1 = x)
+    np.testing.assert_allclose(b[2, 13], h * h * e, rtol=1e-14)       # y-layer only
+    np.testing.assert_allclose(b[2, 2], h * h * e * e, rtol=1e-14)    # corner
+    # vertex 4 lies between a rotated cell (3) and a plain one (4)
+    np.testing.assert_allclose(b[13, 4], h * (h * e + h) / 2, rtol=1e-14)
+
+
+# ---------------------------------------------------------------- transfers
+@pytest.mark.parametrize("d,level", [(2, 2), (3, 2)])
+def test_restriction_is_prolongation_transpose(d, level):
+    nf, nc = 3 ** level, 3 ** (level - 1)
+    Nc, Nf = (nc + 1) ** d, (nf + 1) ** d
+    P = np.zeros((Nf, Nc))
+    R = np.zeros((Nc, Nf))
+    for j in range(Nc):
+        e = np.zeros(Nc)
+        e[j] = 1
+        P[:, j] = O.prolong(e.reshape((nc + 1,) * d)).real.ravel()
+    for j in range(Nf):
+        e = np.zeros(Nf)
+        e[j] = 1
+        R[:, j] = O.restrict(e.reshape((nf + 1,) * d)).real.ravel()
+    np.testing.assert_array_equal(R, P.T)
+    # partition of unity and the 3^d column sum of interior coarse vertices
+    np.testing.assert_allclose(P.sum(axis=1), 1.0, rtol=0, atol=1e-15)
+    inner_c = [i for i, idx in enumerate(itertools.product(range(nc + 1), repeat=d))
+               if all(0 < k < nc for k in idx)]
+    np.testing.assert_allclose(R.sum(axis=1)[inner_c], 3.0 ** d, rtol=1e-15)
+    # independent construction from 1D weights
+    P1 = np.zeros((nf + 1, nc + 1))
+    for c in range(nc + 1):
+        for o in range(-2, 3):
+            if 0 <= 3 * c + o <= nf:
+                P1[3 * c + o, c] = 1 - abs(o) / 3
+    np.testing.assert_allclose(P, kron_all([P1] * d), rtol=0, atol=2.5e-16)
+
+
+def test_prolongation_reproduces_dlinear_functions():
+    nc = 9
+    xc = np.arange(nc + 1) / nc
+    xf = np.arange(3 * nc + 1) / (3 * nc)
+    f = lambda y, x: 2.0 - 3 * x + 0.5 * y + 7 * x * y
+    Yc, Xc = np.meshgrid(xc, xc, indexing="ij")
+    Yf, Xf = np.meshgrid(xf, xf, indexing="ij")
+    np.testing.assert_allclose(O.prolong(f(Yc, Xc)).real, f(Yf, Xf), rtol=0, atol=1e-13)
+    np.testing.assert_array_equal(O.inject(O.prolong(f(Yc, Xc))), f(Yc, Xc).astype(complex))
+
+
+@pytest.mark.parametrize("d,level,k2", [(2, 2, 30.0), (2, 3, (4 * math.pi) ** 2), (3, 2, -40.0)])
+def test_galerkin_identity_uniform_scaling(d, level, k2):
+    """H_{l-1} = R H_l P for invariant scaling and shift (Section 3)."""
+    nf, nc = 3 ** level, 3 ** (level - 1)
+    Hf, _, _ = dense_level(d, level, np.full((nf + 1,) * d, k2), TH, 0.5)
+    Hc, _, _ = dense_level(d, level - 1, np.full((nc + 1,) * d, k2), TH, 0.5)
+    P = kron_all([interp_1d(nc)] * d)
+    G = P.T @ Hf @ P
+    np.testing.assert_allclose(G, Hc, rtol=0, atol=1e-13 * np.abs(Hc).max())
+
+
+def test_galerkin_defect_at_unaligned_layer_edge():
+    """With a layer edge that coarse cells straddle, rediscretisation deviates
+    from R H P (Section 6, remark after Lemma 2) -- but only near the edge."""
+    k2 = 30.0
+    Hf, _, _ = dense_level(2, 3, np.full((28, 28), k2), TH, 4 / 27)
+    Hc, inner, _ = dense_level(2, 2, np.full((10, 10), k2), TH, 4 / 27)
+    P = kron_all([interp_1d(9)] * 2)
+    E = np.abs(P.T @ Hf @ P - Hc).max(axis=1)
+    assert E.max() > 1e-3
+    far = [r for r, (y, x) in enumerate(inner) if 3 <= y <= 6 and 3 <= x <= 6]
+    assert E[far].max() < 1e-12
+
+
+# ---------------------------------------------------------------- cycle
+def _problem(d, depth, k2, theta, w, seed=0):
+    n = 3 ** depth
+    rng = np.random.default_rng(seed)
+    H = O.Hierarchy(d, depth, np.full((n + 1,) * d, k2), theta, w)
+    f = rng.standard_normal((n + 1,) * d) + 1j * rng.standard_normal((n + 1,) * d)
+    H.set_rhs_nodal(f)
+    u0 = rng.standard_normal((n + 1,) * d) + 1j * rng.standard_normal((n + 1,) * d)
+    H.set_solution(u0)
+    return H
+
+
+def test_single_level_cycle_is_damped_jacobi():
+    H = _problem(2, 1, 20.0, TH, 0.2)
+    A, inner, lev = dense_level(2, 1, np.full((4, 4), 20.0), TH, 0.2)
+    u = np.array([H.u[i] for i in inner])
+    b = np.array([H.b[i] for i in inner])
+    w = 0.7 - 0.1j
+    ref = u + w * (b - A @ u) / np.diag(A)
+    H.cycle(np.array([w]))
+    np.testing.assert_allclose([H.u[i] for i in inner], ref, rtol=1e-14)
+
+
+@pytest.mark.parametrize("d,depth", [(2, 3), (3, 2)])
+@pytest.mark.parametrize("variant,transfer", [(O.ADD, O.DLINEAR), (O.HB, O.DLINEAR),
+                                              (O.ADD, O.HIERARCHICAL)])
+def test_fas_cycle_equals_additive_correction_scheme(d, depth, variant, transfer):
+    """Lemma 2 and Theorem 2: with invariant scaling and shift the FAS cycle
+    is the textbook additive correction scheme (Algorithm 1 unrolled)
+    u + sum_l P^{L-l} T_l omega_l D_l^{-1} R^{L-l} (b - H u),
+    here assembled from Kronecker products of 1D matrices."""
+    k2 = 25.0
+    Hh = _problem(d, depth, k2, TH, 0.5)
+    omega = np.array([0.55 + 0.05j, 0.6, 0.65 - 0.02j][:depth])
+    Hs = {lev: kron_operator(d, lev, TH, 0.5, k2) for lev in range(1, depth + 1)}
+    Ps = {lev: kron_all([interp_1d(3 ** (lev - 1))] * d) for lev in range(2, depth + 1)}
+    n = 3 ** depth
+    inner = list(itertools.product(range(1, n), repeat=d))
+    u = np.array([Hh.u[i] for i in inner])
+    b = np.array([Hh.b[i] for i in inner])
+    r = b - Hs[depth] @ u
+    corr = np.zeros_like(u)
+    for lev in range(depth, 0, -1):
+        rl = r
+        for m in range(depth, lev, -1):
+            rl = Ps[m].T @ rl
+        du = omega[lev - 1] * rl / np.diag(Hs[lev])
+        nl = 3 ** lev
+        idx = list(itertools.product(range(1, nl), repeat=d))
+        cp = np.array([all(i % 3 == 0 for i in t) for t in idx])
+        if variant == O.HB:
+            du = np.where(cp, 0, du)
+        if transfer == O.HIERARCHICAL and lev > 1:
+            du = du - Ps[lev] @ du[cp]       # P I du
+        for m in range(lev + 1, depth + 1):
+            du = Ps[m] @ du
+        corr += du
+    Hh.cycle(omega, variant, transfer)
+    got = np.array([Hh.u[i] for i in inner])
+    np.testing.assert_allclose(got, u + corr, rtol=0, atol=1e-12 * np.abs(u + corr).max())
+
+
+def test_cycle_fixed_point_is_dense_solution_galerkin():
+    """A convergent Galerkin setup (Poisson-like, phi < 0, theta = 0) converges
+    to the dense direct solution of the 9x9-cell problem."""
+    H = _problem(2, 2, -30.0, 0.0, 0.0, seed=3)
+    H.set_solution(np.zeros((10, 10)))
+    A, inner, _ = dense_level(2, 2, np.full((10, 10), -30.0), 0.0, 0.0)
+    x = np.linalg.solve(A, np.array([H.b[i] for i in inner]))
+    om = O.omega_scheme(O.UCG, 0.6, 2)
+    for _ in range(200):
+        H.cycle(om, O.ADD, O.HIERARCHICAL)
+    np.testing.assert_allclose([H.u[i] for i in inner], x, rtol=0, atol=1e-10 * np.abs(x).max())
+
+
+def test_poisson_analytic_discrete_solution():
+    """Section 7.1: rhs d pi^2 prod sin(pi x_i), phi = 0, theta = 0.  The mode
+    (1,..,1) diagonalises K and M, so the discrete solution is
+    pi^2 (mu/kappa) prod sin(pi x_i); the cycle converges to it and it is an
+    O(h^2) approximation of prod sin(pi x_i)."""
+    for d, depth in [(2, 3), (3, 2)]:
+        n = 3 ** depth
+        h = 1 / n
+        x = np.arange(n + 1) / n
+        s = np.ones((1,) * d)
+        for ax in range(d):
+            shape = [1] * d
+            shape[ax] = n + 1
+            s = s * np.sin(math.pi * x).reshape(shape)
+        H = O.Hierarchy(d, depth, np.zeros((n + 1,) * d), 0.0, 0.0)
+        H.set_rhs_nodal(d * math.pi ** 2 * s)
+        kap = (2 / h) * (1 - math.cos(math.pi * h))
+        mu = (h / 3) * (2 + math.cos(math.pi * h))
+        exact = math.pi ** 2 * (mu / kap) * s
+        np.testing.assert_allclose(H.residual(exact.astype(complex)), 0, atol=1e-12)
+        om = O.omega_scheme(O.UCG, 0.8 if d == 2 else 0.6, depth)
+        for _ in range(300):
+            H.cycle(om, O.ADD, O.HIERARCHICAL)
+        np.testing.assert_allclose(H.u.real, exact, rtol=0, atol=1e-9)
+        assert np.abs(H.u.imag).max() < 1e-12
+        err = np.abs(exact - s).max()
+        assert err < 2.0 * (math.pi * h) ** 2 / 12 * d + 1e-12
+
+
+def test_bpx_and_hb_cpoint_structure():
+    """BPX: (id - P I) vanishes at c-points, so corr_l there equals P corr_{l-1}
+    (Section 4.2); hb: the masked update leaves corr_l = P corr_{l-1} at
+    c-points as well, while f-point updates pass unchanged."""
+    for variant, transfer in [(O.ADD, O.HIERARCHICAL), (O.HB, O.DLINEAR)]:
+        H = _problem(2, 3, 10.0, TH, 0.2)
+        tr = {}
+        H.cycle(np.array([0.6, 0.6, 0.6]), variant, transfer, trace=tr)
+        for lev in (2, 3):
+            cp = O.cpoint_mask(2, lev)
+            pc = O.prolong(tr["corr"][lev - 1])
+            np.testing.assert_allclose(tr["corr"][lev][cp], pc[cp], rtol=0, atol=1e-14)
+            fp = ~cp
+            fp[0, :] = fp[-1, :] = fp[:, 0] = fp[:, -1] = False
+            assert np.abs(tr["corr"][lev][fp] - pc[fp]).max() > 1e-8
+
+
+def test_omega_schemes():
+    np.testing.assert_allclose(O.omega_scheme(O.JACOBI, 0.6, 3), [0, 0, 0.6])
+    np.testing.assert_allclose(O.omega_scheme(O.UCG, 0.6, 3), [0.6, 0.6, 0.6])
+    np.testing.assert_allclose(O.omega_scheme(O.LGRID, 0.6, 4, l_grid=1), [0, 0, 0.6, 0.6])
+    np.testing.assert_allclose(O.omega_scheme(O.EXP, 0.5, 3), [0.125, 0.25, 0.5])
+    np.testing.assert_allclose(O.omega_scheme(O.TRANSITION, 0.5, 3, iter_n=2),
+                               [0.5 ** 1.5, 0.5, 0.5 ** 0.5])
+    np.testing.assert_allclose(O.omega_scheme(O.TRANSITION, 0.5, 3, iter_n=1), [1, 1, 1])
