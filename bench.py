@@ -1,0 +1,368 @@
+#!/usr/bin/env python
+"""Benchmark of the additive multilevel Helmholtz cycle on GB300.
+
+Default workload: the 2D complex128 variant-sweep configuration -- depth 6
+(729 x 729 fine cells, 529,984 interior unknowns), k = 20 pi, exterior
+scaling layer of 10% per side with theta = pi/6, f = three Gaussians of width
+0.02 (seed 1).  A step is one BPX additive FAS cycle (omega = 0.6 on every
+level) through the C ABI: fused fine sweep, coarse sweeps, prolongation, and
+the fused fine residual norm.  The metric is fine-grid interior DoF-updates/s
+(interior vertices x cycles / s).  L2 is flushed (256 MB write) before every
+timed step; steps are timed with CUDA events on the solver's stream.
+
+``--impl reference`` times the FP64 CPU oracle (test infrastructure) on the
+host cores on a bounded sample of the same workload.  Under torchrun with
+N > 1 every rank runs an independent replica of the solve (a single solve
+does not shard); value is the sum over ranks divided by the slowest rank's
+time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1508_03954_gb300 import workloads as W  # noqa: E402
+
+METRIC = "additive-cycle DoF-updates/s"
+UNIT = "DoF-updates/s"
+# FP64 peak of GB300 from unit counts and clock: 152 SMs x 2 FP64 FMA/clk/SM
+# x 2 flops x 2.07 GHz (the nominal 1.25 TFLOP/s of the data sheet).
+FP64_PEAK_FLOPS = 152 * 2 * 2 * 2.07e9
+FP32_PEAK_FLOPS = 152 * 128 * 2 * 2.07e9
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# ---------------------------------------------------------------- algorithmic counts
+def complex_row_fraction(d, depth, w):
+    """Fraction of interior fine vertices whose stencil row has complex
+    entries (some adjacent cell lies in the scaling layer)."""
+    n = 3 ** depth
+    i = np.arange(n)
+    if w >= 0.5:
+        return 1.0
+    rot = np.minimum(2 * i + 1, 2 * n - 2 * i - 1) < 2.0 * w * n
+    v = np.arange(1, n)
+    cplx_axis = rot[v - 1] | rot[v]
+    real_frac_axis = 1.0 - cplx_axis.mean()
+    return 1.0 - real_frac_axis ** d
+
+
+def fine_sweep_counts(d, depth, w, bpx, omega_real, word=16):
+    """(flops, bytes) the method needs for one finest-level sweep.
+
+    Per interior fine vertex (real x complex MAC = 4 flops, complex x complex
+    MAC = 8 flops): residual and hierarchical residual rows of 3^d entries
+    (complex where a neighbouring cell is scaled, real otherwise) plus the
+    subtraction from b; d-linear interpolation of the pending coarse
+    correction and of I u ((5/3)^d MACs on average each); restriction
+    (5^d / 3^d MACs per fine vertex); Jacobi (complex or real scaling); BPX
+    surplus of du ((5/3)^d MACs); the update and |r|^2.
+    Bytes: U read, b read, U' written on the fine level (3 words per
+    vertex), pending correction read and b, u written on the next coarser
+    level (3 words per coarse vertex)."""
+    n = 3 ** depth
+    ns = 3 ** d
+    fc = complex_row_fraction(d, depth, w)
+    row = fc * (ns * 8 + 2) + (1 - fc) * (ns * 4 + 2)
+    interp = (5.0 / 3.0) ** d * 4
+    jac = fc * 6 + (1 - fc) * (2 if omega_real else 6)
+    per = 2 * row + interp + (interp + 2) + interp + jac + (interp + 2 if bpx else 0) + 2 + 4
+    flops = per * (n - 1) ** d
+    nbytes = 3 * word * (n + 1) ** d + 3 * word * (n // 3 + 1) ** d
+    return flops, nbytes
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) >= 9:
+                rows.append(p)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- traffic record
+def recorded_traffic(kernel_key, source_files):
+    """DRAM bytes per launch of the timed kernel from the committed ncu summary,
+    if it was taken with the current source (sha256 over the CUDA sources)."""
+    h = hashlib.sha256()
+    for f in source_files:
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    sha = h.hexdigest()[:16]
+    path = os.path.join(ROOT, "profiles", f"{kernel_key}.md")
+    if not os.path.exists(path):
+        return None, sha
+    txt = open(path).read()
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    s = re.search(r"source_sha256_16:\s*([0-9a-f]+)", txt)
+    if m and s and s.group(1) == sha:
+        return float(m.group(1)), sha
+    return None, sha
+
+
+# ---------------------------------------------------------------- oracle timing
+def oracle_cycles(cfg, ncycles, omega, budget_s=None):
+    import oracle as O
+    o = O.Hierarchy(cfg["d"], cfg["depth"], cfg["k2"], cfg["theta"], cfg["layer_width"])
+    o.set_rhs_nodal(cfg["f"])
+    done, t0 = 0, time.perf_counter()
+    while done < ncycles:
+        o.cycle(omega, O.ADD, O.HIERARCHICAL)
+        done += 1
+        if budget_s is not None and time.perf_counter() - t0 > budget_s:
+            break
+    return done, time.perf_counter() - t0
+
+
+def cpu_baseline_line(cfg, budget_s=15.0):
+    depth = cfg["depth"]
+    omega = np.full(depth, 0.6)
+    done, dt = oracle_cycles(cfg, 1000, omega, budget_s)
+    units = (3 ** depth - 1) ** cfg["d"] * done
+    return {"value": units / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{done} BPX cycles of the depth-{depth} 2D workload "
+                      f"({dt:.1f} s, numpy FP64, one thread)"}
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    # size one step so that warmup + steps fit in about two minutes
+    est = {6: 1.6, 5: 0.2, 4: 0.025, 3: 0.004}
+    depth = 6
+    for dd in (6, 5, 4, 3):
+        depth = dd
+        if (args.steps + args.warmup) * est[dd] <= 120:
+            break
+    cfg = W.config2(depth=depth)
+    omega = np.full(depth, 0.6)
+    import oracle as O
+    o = O.Hierarchy(cfg["d"], depth, cfg["k2"], cfg["theta"], cfg["layer_width"])
+    o.set_rhs_nodal(cfg["f"])
+    for _ in range(args.warmup):
+        o.cycle(omega, O.ADD, O.HIERARCHICAL)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.cycle(omega, O.ADD, O.HIERARCHICAL)
+    dt = time.perf_counter() - t0
+    units = (3 ** depth - 1) ** 2 * args.steps
+    val = units / dt
+    sample = (f"one FP64 oracle BPX cycle per step on the depth-{depth} instance of the "
+              f"workload ({(3 ** depth - 1) ** 2} interior unknowns)")
+    line = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c128 (f64)", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": "2D complex128 variant sweep (BPX cycle), k=20pi, 10% ECS layer, "
+                                   f"theta=pi/6, sampled at depth {depth}"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=200)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local_rank)
+
+    from paper_1508_03954_gb300 import build as B
+    from paper_1508_03954_gb300 import mg
+    B.build()
+    mg.load()
+
+    cfg = W.config2()
+    d, depth = cfg["d"], cfg["depth"]
+    s = mg.Solver(d, depth, cfg["k2"], cfg["theta"], cfg["layer_width"])
+    stream = torch.cuda.current_stream()
+    s.set_stream(stream.cuda_stream)
+    f_dev = torch.from_numpy(cfg["f"]).cuda()
+    s.set_rhs(f_dev)
+    omega = np.full(depth, 0.6)
+    variant, transfer = mg.MG_BPX, mg.MG_HIERARCHICAL
+    interior = (3 ** depth - 1) ** d
+
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+    for _ in range(args.warmup):
+        s.cycle(variant, omega, transfer)
+    torch.cuda.synchronize()
+    s.set_timing(True)
+    s.get_stats()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(local_rank)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for k in range(args.steps):
+        flush.fill_(float(k & 7))
+        starts[k].record(stream)
+        s.cycle(variant, omega, transfer)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clk = clocks.stop()
+    launches, nsweeps, sweep_ms = s.get_stats()
+    s.set_timing(False)
+    total_ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
+    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    value = interior * args.steps * world / (total_ms / 1e3)
+
+    # end to end through the public API with pinned host buffers
+    u_h = torch.zeros(s.shape, dtype=torch.complex128).pin_memory()
+    f_h = torch.from_numpy(cfg["f"]).pin_memory()
+    out_h = torch.empty(s.shape, dtype=torch.complex128).pin_memory()
+    s.get_solution(u_h)
+    e2e_ms = 0.0
+    ne = max(1, args.e2e_steps)
+    for k in range(ne + 3):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        s.set_solution(u_h)
+        s.set_rhs(f_h)
+        s.cycle(variant, omega, transfer)
+        s.get_solution(out_h)
+        b.record(stream)
+        b.synchronize()
+        if k >= 3:
+            e2e_ms += a.elapsed_time(b)
+        u_h.copy_(out_h)
+    te = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = interior * ne * world / (float(te.item()) / 1e3)
+
+    peaks, src = measured_peaks()
+    flops, nbytes = fine_sweep_counts(d, depth, cfg["layer_width"], bpx=True, omega_real=True)
+    sweep_s = (sweep_ms / max(nsweeps, 1)) / 1e3
+    achieved = flops / sweep_s
+    csrc = os.path.join(ROOT, "paper_1508_03954_gb300", "csrc")
+    traffic, sha = recorded_traffic("fine_sweep_c128_2d_depth6",
+                                    [os.path.join(csrc, f) for f in sorted(os.listdir(csrc))])
+    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": FP64_PEAK_FLOPS / 1e12,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_FLOPS, "traffic": traffic,
+                "kernel": "sweep_kernel<double,2,8,256> (finest level)",
+                "peak_source": "FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
+                "hbm": {"achieved_gbs": nbytes / sweep_s / 1e9, "peak_gbs": peaks.get("hbm_gbs"),
+                        "frac": nbytes / sweep_s / 1e9 / peaks.get("hbm_gbs", 6800.0),
+                        "peak_source": src},
+                "sweep_ms": sweep_ms / max(nsweeps, 1),
+                "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": nbytes,
+                "source_sha256_16": sha}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c128 (f64)", "data": "synthetic",
+            "config": {"workload": "2D complex128 variant sweep: depth 6 (729^2 cells, 529,984 "
+                                   "interior unknowns), k=20pi, 10% ECS layer theta=pi/6, 3 Gaussians "
+                                   "(seed 1); step = one BPX additive FAS cycle, omega=0.6",
+                       "l2": "flushed before every timed step (256 MB write)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": roofline,
+            "e2e": {"value": e2e_value, "unit": UNIT,
+                    "h2d_bytes_per_step": 2 * 16 * s.nv, "d2h_bytes_per_step": 16 * s.nv,
+                    "what": "mg_set_solution + mg_set_rhs from pinned host, mg_cycle, "
+                            "mg_get_solution to pinned host"},
+            "gpu_launches": launches, "clocks": clk}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_line(cfg)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    s.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,169 @@
+/*
+ * mg.h -- C ABI of the GB300 additive multilevel Helmholtz solver.
+ *
+ * The library solves the p-dimensional Helmholtz model
+ *     [-Laplace - phi] psi = chi   on (0,1)^d, zero Dirichlet boundary,
+ * (Section 2, Eq. pHelmholtz, phi = k^2) with d-linear finite elements on the
+ * regular levels l = 1..L of a tripartitioned spacetree (Section 3) and
+ * complex grid spacing h e^{i theta} inside an exterior scaling layer
+ * (Section 2 "complex scaled grid", Section 7.3-7.4).  One call of mg_cycle
+ * is one additive FAS cycle (Algorithm 2 / Appendix A Algorithm 4):
+ * residual and hierarchical residual on every level, restriction to every
+ * coarser level, damped Jacobi on all levels at once, then correction and
+ * prolongation back to the fine grid.
+ *
+ * Conventions shared by every call
+ *  - d is 2 or 3; level l has n = 3^l cells per axis and (n+1)^d vertices
+ *    including the Dirichlet ring.  Vertex arrays are row-major with x
+ *    fastest: index = x + (n+1)*(y + (n+1)*z).  Complex values are
+ *    interleaved (re, im) FP64 pairs (mg_c128).  Boundary entries are zero.
+ *  - Pointers marked "host or device" are read on the host when the
+ *    accompanying on_device flag is 0 and as device pointers of the current
+ *    CUDA device otherwise.  The caller keeps ownership of every array it
+ *    passes; the library copies what it needs before returning.
+ *  - Every call returns an MG_* status and never aborts; no C++ exception
+ *    crosses the ABI.  Arguments are validated before any device work.
+ *    mg_last_error returns a human-readable message of the last failure of
+ *    a context.  Device work is enqueued on the context's stream;
+ *    asynchronous device errors surface as MG_ERR_CUDA at the next
+ *    synchronising call (mg_residual_norm, mg_solve, mg_get_solution with a
+ *    host destination).
+ *  - A context owns every device buffer it allocates and frees them in
+ *    mg_destroy.  Contexts are not thread-safe; distinct contexts are
+ *    independent.
+ */
+#ifndef MG_H
+#define MG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mg_ctx mg_ctx;
+typedef struct { double re, im; } mg_c128;
+
+enum {
+  MG_OK = 0,
+  MG_ERR_INVALID = 1,    /* bad argument; nothing was enqueued               */
+  MG_ERR_CUDA = 2,       /* a CUDA runtime call failed                       */
+  MG_ERR_OOM = 3,        /* device allocation failed                         */
+  MG_DIVERGED = 4,       /* relative residual > 1e6, NaN or Inf (Table 2 bottom) */
+  MG_NOT_CONVERGED = 5,  /* max_cycles reached above tol                     */
+  MG_ERR_TIMEOUT = 6     /* a bounded device-side wait gave up               */
+};
+
+/* Relaxation variant (Section 4.2): MG_HB masks the Jacobi update at
+ * c-points, Eq. hb-omega.  Transfer: MG_DLINEAR adds the update as is
+ * (T = id); MG_HIERARCHICAL adds only its hierarchical surplus
+ * T = (id - P I), the BPX prolongation of Appendix A.  MG_BPX is
+ * MG_ADD with MG_HIERARCHICAL. */
+enum { MG_ADD = 0, MG_HB = 1, MG_BPX = 2 };
+enum { MG_DLINEAR = 0, MG_HIERARCHICAL = 1 };
+/* Arithmetic of the cycles: complex128 throughout, or complex64 cycles with
+ * FP32 accumulation inside an FP64 defect-correction loop (fine residual,
+ * solution update and norms in FP64). */
+enum { MG_C128 = 0, MG_C64_REFINE = 1 };
+/* Relaxation schemes of the Section 4.1 table (succ = L - l on a regular grid). */
+enum { MG_OMEGA_JACOBI = 0, MG_OMEGA_UCG = 1, MG_OMEGA_LGRID = 2, MG_OMEGA_EXP = 3,
+       MG_OMEGA_TRANSITION = 4 };
+
+/* Creates a solver for the hierarchy of depth L = depth (levels 1..L).
+ *  k2_field   host, (3^L+1)^d FP64 values of phi = k^2 at the fine vertices
+ *             (Section 3: phi is a per-vertex weight).  Coarse levels sample
+ *             it at their own vertices (injection); a cell uses the mean of
+ *             its 2^d vertex values.  A constant field takes a faster path.
+ *  theta      rotation angle of the complex spacing, 0 <= theta < pi/2.
+ *  layer_width  0 <= w <= 0.5: along each axis, a cell whose centre lies
+ *             closer than w to a face has spacing h e^{i theta}
+ *             (coordinate-wise exterior scaling); w = 0.5 rotates every cell
+ *             (the complex scaled grid of Section 7.3).
+ * The solution starts at zero and the rhs at zero.
+ * Errors: MG_ERR_INVALID (d not in {2,3}, depth < 1 or too deep for the
+ * device, theta or w out of range, NULL pointers), MG_ERR_OOM, MG_ERR_CUDA. */
+int mg_create(int d, int depth, const double* k2_field, double theta,
+              double layer_width, mg_ctx** out);
+
+/* Releases every device buffer of the context (NULL is ignored). */
+void mg_destroy(mg_ctx* ctx);
+
+/* Enqueues all later work on this cudaStream_t (0 = legacy default stream). */
+int mg_set_stream(mg_ctx* ctx, void* cuda_stream);
+
+/* Nodal right-hand side f (host or device, fine-vertex layout).  The library
+ * forms b_L = M_L f with the consistent, complex-scaled mass matrix
+ * (Section 3: chi holds the weight of the discretised right-hand side).
+ * Resets the reference residual used by relative norms. */
+int mg_set_rhs(mg_ctx* ctx, const mg_c128* f_nodal, int on_device);
+
+/* Sets the fine solution u (host or device); boundary entries are ignored.
+ * Clears any pending correction and the reference residual. */
+int mg_set_solution(mg_ctx* ctx, const mg_c128* u, int on_device);
+
+/* Writes the current fine solution, with every correction of the cycles
+ * run so far applied, to out (host or device, fine-vertex layout).
+ * Synchronises the stream when out is a host pointer. */
+int mg_get_solution(mg_ctx* ctx, mg_c128* out, int on_device);
+
+/* One additive FAS cycle (Algorithm 2; Appendix A Algorithm 4) on levels
+ * 1..L.  omega_per_level: host, L complex relaxation factors, index l-1
+ * (Section 4.1: one factor per level).  variant MG_ADD/MG_HB/MG_BPX and
+ * transfer MG_DLINEAR/MG_HIERARCHICAL as above.  Asynchronous. */
+int mg_cycle(mg_ctx* ctx, int variant, const mg_c128* omega_per_level, int transfer);
+
+/* Euclidean norm of the fine residual b - H u over the fine vertices and
+ * its ratio to the residual of the starting solution (Section 7 norms; on a
+ * regular grid the h-weighted norm gives the same ratio).  Synchronising. */
+int mg_residual_norm(mg_ctx* ctx, double* abs_l2, double* rel_l2);
+
+/* Runs cycles until the relative residual is <= tol (MG_OK), max_cycles
+ * were run (MG_NOT_CONVERGED) or the iteration diverged (MG_DIVERGED).
+ * With precision MG_C128 every cycle is the plain complex128 cycle; with
+ * MG_C64_REFINE see mg_set_precision.  cycles_done counts fine-grid cycles
+ * (inner cycles for the refinement form); rel_res is the final relative
+ * FP64 residual.  Either output pointer may be NULL. */
+int mg_solve(mg_ctx* ctx, int variant, const mg_c128* omega, int transfer, double tol,
+             int max_cycles, int* cycles_done, double* rel_res);
+
+/* Selects the arithmetic of mg_solve.  MG_C64_REFINE: each outer step forms
+ * r = b - H u in FP64, runs inner_cycles complex64 cycles on H e = r from
+ * e = 0, and adds e to u in FP64. */
+int mg_set_precision(mg_ctx* ctx, int precision, int inner_cycles);
+
+/* Grid unfolding (Section 4 remark on FMG; Section 7.1): stages s = 1..L-1
+ * solve on levels 1..s with b_s = M_s f_s and run cycles_per_stage cycles,
+ * each stage starting from the d-linear interpolation of the previous one;
+ * the fine solution is then set to the interpolation of stage L-1.  Level
+ * l of stage s uses omega[l-1 + L-s].  Needs mg_set_rhs first. */
+int mg_fmg(mg_ctx* ctx, int variant, const mg_c128* omega, int transfer, int cycles_per_stage);
+
+/* Host helper: fills out[0..depth-1] with the relaxation factors of one
+ * Section 4.1 scheme, succ = depth - l: Jacobi only, undamped coarse grid,
+ * undamped L-grid (l_grid), exponential omega_s^(succ+1) or transition
+ * omega_s^((1-1/iter_n)(succ+1)). */
+int mg_omega_scheme(int scheme, mg_c128 omega_s, int depth, int iter_n, int l_grid,
+                    mg_c128* out);
+
+/* Copies one per-level device array to out (host or device) for inspection:
+ * which = 0 solution (fine: with pending corrections applied; coarse: the
+ * injected copy the last cycle used), 1 right-hand side b_l.  Synchronises
+ * when out is a host pointer. */
+int mg_get_level(mg_ctx* ctx, int level, int which, mg_c128* out, int on_device);
+
+/* Instrumentation.  mg_set_timing(ctx, 1) makes every later cycle record a
+ * CUDA event pair around its finest-level sweep kernel on the context's
+ * stream.  mg_get_stats synchronises the stream and returns, since the last
+ * mg_get_stats call: the number of kernels the context launched, the number
+ * of timed fine sweeps and their summed device time in milliseconds; it
+ * then resets all three.  Any output pointer may be NULL. */
+int mg_set_timing(mg_ctx* ctx, int enable);
+int mg_get_stats(mg_ctx* ctx, long long* kernel_launches, int* fine_sweeps,
+                 double* fine_sweep_ms);
+
+/* Message of the last failure on this context ("" if none); ctx may be NULL
+ * for failures of mg_create. */
+const char* mg_last_error(const mg_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MG_H */

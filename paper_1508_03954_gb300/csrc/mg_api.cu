@@ -1,0 +1,798 @@
+// mg_api.cu -- C ABI of the GB300 additive multilevel Helmholtz solver
+// (declarations and argument contracts in include/mg.h).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "mg.h"
+#include "mg_kernels.cuh"
+
+using mg::cplx;
+using cd = std::complex<double>;
+
+namespace {
+
+constexpr int kMaxDepth2 = 9;  // (3^9+1)^2 vertices: 387 M
+constexpr int kMaxDepth3 = 6;  // (3^6+1)^3 vertices: 389 M
+constexpr int kThreads = 256;
+constexpr int kTC2 = 8;        // coarse cells per tile edge, 2D
+constexpr int kTC3 = 2;        // coarse cells per tile edge, 3D
+
+long long ipow(long long b, int e) {
+  long long r = 1;
+  while (e-- > 0) r *= b;
+  return r;
+}
+
+// Per-level operator data and arrays of one precision.
+template <typename R>
+struct Hier {
+  struct Lev {
+    int n = 0;
+    size_t nv = 0;
+    cplx<R>* u[2] = {nullptr, nullptr};
+    cplx<R>* b = nullptr;
+    cplx<R>* t = nullptr;
+    cplx<R>* corr = nullptr;  // level 1 aliases t
+    uint8_t* typ = nullptr;
+    cplx<R>* coefH = nullptr;
+    cplx<R>* coefM = nullptr;
+    R* phic = nullptr;
+    cplx<R>* hcell = nullptr;
+    std::vector<cd> diag;     // D per vertex type (constant shift)
+  };
+  int d = 0, L = 0;
+  bool varphi = false;
+  bool ready = false;
+  std::vector<Lev> lev;
+  int cur = 0;               // active fine U buffer
+  double* partial = nullptr;
+  unsigned* ticket = nullptr;
+  double* norm2 = nullptr;   // [0] cycle norm, [1] standalone norm
+  std::vector<void*> allocs;
+};
+
+}  // namespace
+
+struct mg_ctx {
+  int d = 0, L = 0;
+  double theta = 0, w = 0;
+  cudaStream_t stream = 0;
+  Hier<double> h64;
+  Hier<float> h32;
+  int precision = MG_C128;
+  int inner_cycles = 4;
+  double r0 = -1.0;                    // reference residual norm
+  std::vector<double> k2;              // fine k^2 (host copy)
+  cplx<double>* f_dev = nullptr;       // nodal f (fine)
+  cplx<double>* scratch = nullptr;     // fine-size FP64 scratch
+  double* host_norm = nullptr;         // pinned
+  std::string err;
+  // instrumentation
+  long long launches = 0;
+  bool timing = false;
+  std::vector<cudaEvent_t> ev;         // pairs around fine sweeps
+  size_t ev_used = 0;
+};
+
+namespace {
+
+thread_local std::string g_create_err;
+
+int fail(mg_ctx* c, int code, const std::string& m) {
+  if (c) c->err = m; else g_create_err = m;
+  return code;
+}
+
+#define MG_CUDA(ctx, call)                                                              \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess) {                                                            \
+      return fail((ctx), e_ == cudaErrorMemoryAllocation ? MG_ERR_OOM : MG_ERR_CUDA,   \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                 \
+    }                                                                                   \
+  } while (0)
+
+// ------------------------------------------------------------------ geometry
+// Along one axis a cell of level l lies in the scaling layer when its centre
+// (i + 1/2)/n is closer than w to a face: min(2i+1, 2n-2i-1) < 2 w n
+// (integer form); w >= 0.5 scales every cell (complex scaled grid).
+std::vector<uint8_t> layer_flags(int n, double w) {
+  std::vector<uint8_t> rot(n);
+  for (int i = 0; i < n; ++i) {
+    long long a = 2LL * i + 1, b = 2LL * n - 2LL * i - 1;
+    rot[i] = (w >= 0.5) || ((double)std::min(a, b) < 2.0 * w * (double)n);
+  }
+  return rot;
+}
+
+// Stencil rows of the d-linear element operator for every vertex type.  A
+// vertex of type t has left/right cell widths hl, hr along each axis; its
+// assembled 1D stiffness row is (-1/hl, 1/hl + 1/hr, -1/hr) and its 1D mass
+// row (hl/6, (hl+hr)/3, hr/6).  The d-dimensional rows are the tensor
+// products K = sum_j (x)_a (K if a == j else M), M = (x)_a M (Section 3).
+void type_tables(int d, int n, double theta, std::vector<cd>& K, std::vector<cd>& M) {
+  const double h = 1.0 / n;
+  const cd hrot = h * cd(std::cos(theta), std::sin(theta));
+  cd KX[4][3], MX[4][3];
+  for (int t = 0; t < 4; ++t) {
+    cd hl = (t & 1) ? hrot : cd(h), hr = (t & 2) ? hrot : cd(h);
+    KX[t][0] = -1.0 / hl;
+    KX[t][1] = 1.0 / hl + 1.0 / hr;
+    KX[t][2] = -1.0 / hr;
+    MX[t][0] = hl / 6.0;
+    MX[t][1] = (hl + hr) / 3.0;
+    MX[t][2] = hr / 6.0;
+  }
+  const int NT = (int)ipow(4, d), NS = (int)ipow(3, d);
+  K.assign((size_t)NT * NS, cd(0));
+  M.assign((size_t)NT * NS, cd(0));
+  for (int t = 0; t < NT; ++t) {
+    int ta[3] = {t % 4, (t / 4) % 4, t / 16};
+    for (int k = 0; k < NS; ++k) {
+      int ka[3] = {k % 3, (k / 3) % 3, k / 9};
+      cd m(1);
+      for (int a = 0; a < d; ++a) m *= MX[ta[a]][ka[a]];
+      cd kk(0);
+      for (int j = 0; j < d; ++j) {
+        cd p(1);
+        for (int a = 0; a < d; ++a) p *= (a == j ? KX[ta[a]][ka[a]] : MX[ta[a]][ka[a]]);
+        kk += p;
+      }
+      K[(size_t)t * NS + k] = kk;
+      M[(size_t)t * NS + k] = m;
+    }
+  }
+}
+
+template <typename R>
+std::vector<cplx<R>> to_dev_type(const std::vector<cd>& v) {
+  std::vector<cplx<R>> o(v.size());
+  for (size_t i = 0; i < v.size(); ++i) o[i] = cplx<R>{(R)v[i].real(), (R)v[i].imag()};
+  return o;
+}
+
+template <typename R>
+int dalloc(mg_ctx* c, Hier<R>& H, void** p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return fail(c, MG_ERR_OOM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+  }
+  H.allocs.push_back(*p);
+  e = cudaMemset(*p, 0, bytes);
+  if (e != cudaSuccess) return fail(c, MG_ERR_CUDA, cudaGetErrorString(e));
+  return MG_OK;
+}
+
+template <typename R>
+void free_hier(Hier<R>& H) {
+  for (void* p : H.allocs) cudaFree(p);
+  H.allocs.clear();
+  H.lev.clear();
+  H.ready = false;
+}
+
+// Builds the arrays and tables of one precision.
+template <typename R>
+int build_hier(mg_ctx* c, Hier<R>& H) {
+  const int d = c->d, L = c->L;
+  H.d = d;
+  H.L = L;
+  H.lev.assign(L + 1, typename Hier<R>::Lev());
+  const int nL = (int)ipow(3, L);
+  // constant or varying shift
+  bool constant = true;
+  for (size_t i = 1; i < c->k2.size(); ++i)
+    if (c->k2[i] != c->k2[0]) { constant = false; break; }
+  H.varphi = !constant;
+  const double phi0 = c->k2[0];
+  size_t max_blocks = 1;
+  int rc;
+  for (int l = 1; l <= L; ++l) {
+    auto& V = H.lev[l];
+    V.n = (int)ipow(3, l);
+    V.nv = (size_t)ipow(V.n + 1, d);
+    const size_t bytes = V.nv * sizeof(cplx<R>);
+    for (int k = 0; k < 2; ++k)
+      if ((rc = dalloc(c, H, (void**)&V.u[k], bytes)) != MG_OK) return rc;
+    if ((rc = dalloc(c, H, (void**)&V.b, bytes)) != MG_OK) return rc;
+    if ((rc = dalloc(c, H, (void**)&V.t, bytes)) != MG_OK) return rc;
+    if (l == 1) {
+      V.corr = V.t;
+    } else if ((rc = dalloc(c, H, (void**)&V.corr, bytes)) != MG_OK) {
+      return rc;
+    }
+    // vertex types
+    std::vector<uint8_t> rot = layer_flags(V.n, c->w), typ(V.n + 1);
+    for (int i = 0; i <= V.n; ++i) {
+      int left = rot[std::max(i - 1, 0)], right = rot[std::min(i, V.n - 1)];
+      typ[i] = (uint8_t)(left + 2 * right);
+    }
+    if ((rc = dalloc(c, H, (void**)&V.typ, typ.size())) != MG_OK) return rc;
+    MG_CUDA(c, cudaMemcpy(V.typ, typ.data(), typ.size(), cudaMemcpyHostToDevice));
+    std::vector<cd> K, M;
+    type_tables(d, V.n, c->theta, K, M);
+    std::vector<cd> Hh(K.size());
+    for (size_t i = 0; i < K.size(); ++i) Hh[i] = H.varphi ? K[i] : K[i] - phi0 * M[i];
+    const int NT = (int)ipow(4, d), NS = (int)ipow(3, d);
+    V.diag.resize(NT);
+    for (int t = 0; t < NT; ++t) V.diag[t] = Hh[(size_t)t * NS + NS / 2];
+    auto hH = to_dev_type<R>(Hh), hM = to_dev_type<R>(M);
+    if ((rc = dalloc(c, H, (void**)&V.coefH, hH.size() * sizeof(cplx<R>))) != MG_OK) return rc;
+    if ((rc = dalloc(c, H, (void**)&V.coefM, hM.size() * sizeof(cplx<R>))) != MG_OK) return rc;
+    MG_CUDA(c, cudaMemcpy(V.coefH, hH.data(), hH.size() * sizeof(cplx<R>), cudaMemcpyHostToDevice));
+    MG_CUDA(c, cudaMemcpy(V.coefM, hM.data(), hM.size() * sizeof(cplx<R>), cudaMemcpyHostToDevice));
+    if (H.varphi) {
+      // cell shift: mean of the 2^d vertex values of k^2 sampled on level l
+      const long long stride = ipow(3, L - l);
+      const long long NL = nL + 1;
+      const size_t ncell = (size_t)ipow(V.n, d);
+      std::vector<R> phic(ncell);
+      for (size_t ci = 0; ci < ncell; ++ci) {
+        long long q[3] = {0, 0, 0}, r = (long long)ci;
+        for (int a = 0; a < d; ++a) { q[a] = r % V.n; r /= V.n; }
+        double s = 0;
+        for (int e = 0; e < (1 << d); ++e) {
+          long long gi = 0, st = 1;
+          for (int a = 0; a < d; ++a) {
+            gi += (q[a] + ((e >> a) & 1)) * stride * st;
+            st *= NL;
+          }
+          s += c->k2[(size_t)gi];
+        }
+        phic[ci] = (R)(s / (double)(1 << d));
+      }
+      if ((rc = dalloc(c, H, (void**)&V.phic, ncell * sizeof(R))) != MG_OK) return rc;
+      MG_CUDA(c, cudaMemcpy(V.phic, phic.data(), ncell * sizeof(R), cudaMemcpyHostToDevice));
+      const double h = 1.0 / V.n;
+      const cd hrot = h * cd(std::cos(c->theta), std::sin(c->theta));
+      std::vector<cd> hc(V.n);
+      for (int i = 0; i < V.n; ++i) hc[i] = rot[i] ? hrot : cd(h);
+      auto hcd = to_dev_type<R>(hc);
+      if ((rc = dalloc(c, H, (void**)&V.hcell, hcd.size() * sizeof(cplx<R>))) != MG_OK) return rc;
+      MG_CUDA(c, cudaMemcpy(V.hcell, hcd.data(), hcd.size() * sizeof(cplx<R>), cudaMemcpyHostToDevice));
+    }
+    const int TC = d == 2 ? kTC2 : kTC3;
+    size_t nb = (size_t)ipow((V.n / 3 + 1 + TC - 1) / TC, d);
+    max_blocks = std::max(max_blocks, nb);
+  }
+  max_blocks = std::max<size_t>(max_blocks, 152 * 16);
+  if ((rc = dalloc(c, H, (void**)&H.partial, max_blocks * sizeof(double))) != MG_OK) return rc;
+  if ((rc = dalloc(c, H, (void**)&H.ticket, 4 * sizeof(unsigned))) != MG_OK) return rc;
+  if ((rc = dalloc(c, H, (void**)&H.norm2, 4 * sizeof(double))) != MG_OK) return rc;
+  H.cur = 0;
+  H.ready = true;
+  return MG_OK;
+}
+
+// ------------------------------------------------------------------ launches
+template <typename R, int D>
+cudaError_t launch_sweep(cudaStream_t s, mg::SweepArgs<R>& A) {
+  constexpr int TC = D == 2 ? kTC2 : kTC3;
+  const int nc = A.n / 3;
+  const int tiles = (nc + 1 + TC - 1) / TC;
+  int nblk = 1;
+  for (int a = 0; a < 3; ++a) A.tiles[a] = a < D ? tiles : 1;
+  for (int a = 0; a < D; ++a) nblk *= tiles;
+  const size_t smem = mg::sweep_smem_bytes<R, D, TC>(A.varphi);
+  auto kern = mg::sweep_kernel<R, D, TC, kThreads>;
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)mg::sweep_smem_bytes<R, D, TC>(1));
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  kern<<<nblk, kThreads, smem, s>>>(A);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t sweep(mg_ctx* c, Hier<R>& H, int l, bool fine, int s_active, int hb, int hier,
+                  const cplx<double>* omega) {
+  auto& V = H.lev[l];
+  ++c->launches;
+  mg::SweepArgs<R> A;
+  std::memset(&A, 0, sizeof(A));
+  A.n = V.n;
+  A.fine = fine ? 1 : 0;
+  A.has_coarse = l > 1 ? 1 : 0;
+  A.hb = hb;
+  A.hier = hier;
+  A.varphi = H.varphi ? 1 : 0;
+  A.u = fine ? V.u[H.cur] : V.u[0];
+  A.c = (fine && l > 1) ? H.lev[l - 1].corr : nullptr;
+  A.b = V.b;
+  A.out = fine ? V.u[1 - H.cur] : V.t;
+  if (l > 1) {
+    A.b_coarse = H.lev[l - 1].b;
+    A.u_coarse = H.lev[l - 1].u[0];
+  }
+  A.typ = V.typ;
+  A.coef = V.coefH;
+  A.phic = V.phic;
+  A.hcell = V.hcell;
+  // the factor of level l in stage s_active is the one of level l + (L - s)
+  const cd om(omega[l - 1 + (H.L - s_active)].x, omega[l - 1 + (H.L - s_active)].y);
+  A.omega = cplx<R>{(R)om.real(), (R)om.imag()};
+  if (!H.varphi) {
+    for (size_t t = 0; t < V.diag.size(); ++t) {
+      cd q = om / V.diag[t];
+      A.omd[t] = cplx<R>{(R)q.real(), (R)q.imag()};
+    }
+  }
+  A.partial = H.partial;
+  A.ticket = H.ticket;
+  A.norm2 = H.norm2;
+  return c->d == 2 ? launch_sweep<R, 2>(c->stream, A) : launch_sweep<R, 3>(c->stream, A);
+}
+
+int grid_for(size_t nv) {
+  size_t b = (nv + kThreads - 1) / kThreads;
+  return (int)std::min<size_t>(std::max<size_t>(b, 1), 152 * 16);
+}
+
+template <typename R>
+cudaError_t prolong(mg_ctx* c, Hier<R>& H, int l) {
+  auto& V = H.lev[l];
+  ++c->launches;
+  if (c->d == 2)
+    mg::prolong_add_kernel<R, 2><<<grid_for(V.nv), kThreads, 0, c->stream>>>(
+        V.n, V.t, H.lev[l - 1].corr, V.corr);
+  else
+    mg::prolong_add_kernel<R, 3><<<grid_for(V.nv), kThreads, 0, c->stream>>>(
+        V.n, V.t, H.lev[l - 1].corr, V.corr);
+  return cudaGetLastError();
+}
+
+// One cycle on levels 1..s (s = active finest level).
+template <typename R>
+int run_cycle(mg_ctx* c, Hier<R>& H, int s, int hb, int hier, const cplx<double>* omega) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (c->timing) {
+    if (c->ev_used + 2 > c->ev.size()) {
+      for (int k = 0; k < 64; ++k) {
+        cudaEvent_t ev;
+        if (cudaEventCreate(&ev) != cudaSuccess) return fail(c, MG_ERR_CUDA, "cudaEventCreate failed");
+        c->ev.push_back(ev);
+      }
+    }
+    e0 = c->ev[c->ev_used];
+    e1 = c->ev[c->ev_used + 1];
+    c->ev_used += 2;
+    cudaEventRecord(e0, c->stream);
+  }
+  cudaError_t e = sweep(c, H, s, true, s, hb, hier, omega);
+  if (c->timing && e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+  for (int l = s - 1; l >= 1 && e == cudaSuccess; --l) e = sweep(c, H, l, false, s, hb, hier, omega);
+  for (int l = 2; l <= s - 1 && e == cudaSuccess; ++l) e = prolong(c, H, l);
+  if (e != cudaSuccess) return fail(c, MG_ERR_CUDA, std::string("cycle launch: ") + cudaGetErrorString(e));
+  H.cur = 1 - H.cur;
+  return MG_OK;
+}
+
+// materialised fine solution of level s into out (same precision)
+template <typename R>
+cudaError_t materialize(mg_ctx* c, Hier<R>& H, int s, cplx<R>* out) {
+  auto& V = H.lev[s];
+  ++c->launches;
+  const cplx<R>* cc = s > 1 ? H.lev[s - 1].corr : nullptr;
+  if (c->d == 2)
+    mg::materialize_kernel<R, 2><<<grid_for(V.nv), kThreads, 0, c->stream>>>(V.n, V.u[H.cur], cc, out);
+  else
+    mg::materialize_kernel<R, 3><<<grid_for(V.nv), kThreads, 0, c->stream>>>(V.n, V.u[H.cur], cc, out);
+  return cudaGetLastError();
+}
+
+// y = b - H_l x or y = A x with a chosen table, optional norm into norm2[slot]
+template <typename R, typename RO>
+cudaError_t stencil(mg_ctx* c, Hier<R>& H, int l, int xs, const cplx<R>* x, const cplx<R>* b,
+                    const cplx<R>* coef, bool with_phi, cplx<RO>* y, int slot) {
+  auto& V = H.lev[l];
+  ++c->launches;
+  const int g = grid_for(V.nv);
+  double* nrm = slot >= 0 ? H.norm2 + slot : nullptr;
+  if (c->d == 2)
+    mg::stencil_kernel<R, RO, 2><<<g, kThreads, 0, c->stream>>>(
+        V.n, xs, x, b, V.typ, coef, with_phi ? V.phic : nullptr, V.hcell, y, H.partial,
+        H.ticket + 1, nrm);
+  else
+    mg::stencil_kernel<R, RO, 3><<<g, kThreads, 0, c->stream>>>(
+        V.n, xs, x, b, V.typ, coef, with_phi ? V.phic : nullptr, V.hcell, y, H.partial,
+        H.ticket + 1, nrm);
+  return cudaGetLastError();
+}
+
+int zero_pending(mg_ctx* c, Hier<double>& H, int s) {
+  for (int l = 1; l < s; ++l) {
+    MG_CUDA(c, cudaMemsetAsync(H.lev[l].corr, 0, H.lev[l].nv * sizeof(cplx<double>), c->stream));
+    MG_CUDA(c, cudaMemsetAsync(H.lev[l].t, 0, H.lev[l].nv * sizeof(cplx<double>), c->stream));
+  }
+  return MG_OK;
+}
+
+int check_ctx(mg_ctx* c) { return c == nullptr ? MG_ERR_INVALID : MG_OK; }
+
+int decode_variant(mg_ctx* c, int variant, int transfer, int* hb, int* hier) {
+  if (variant < MG_ADD || variant > MG_BPX) return fail(c, MG_ERR_INVALID, "variant must be MG_ADD, MG_HB or MG_BPX");
+  if (transfer != MG_DLINEAR && transfer != MG_HIERARCHICAL)
+    return fail(c, MG_ERR_INVALID, "transfer must be MG_DLINEAR or MG_HIERARCHICAL");
+  *hb = variant == MG_HB;
+  *hier = (transfer == MG_HIERARCHICAL) || (variant == MG_BPX);
+  return MG_OK;
+}
+
+// ||b_s - H_s u_s|| of the materialised fine solution of level s (FP64),
+// synchronising.
+int fine_residual(mg_ctx* c, int s, double* out) {
+  auto& H = c->h64;
+  cudaError_t e = materialize(c, H, s, c->scratch);
+  if (e == cudaSuccess)
+    e = stencil<double, double>(c, H, s, 1, c->scratch, H.lev[s].b, H.lev[s].coefH, true,
+                                (cplx<double>*)nullptr, 1);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->host_norm, H.norm2 + 1, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return fail(c, MG_ERR_CUDA, std::string("residual: ") + cudaGetErrorString(e));
+  *out = std::sqrt(*c->host_norm);
+  return MG_OK;
+}
+
+int ensure_r0(mg_ctx* c) {
+  if (c->r0 >= 0) return MG_OK;
+  double r;
+  int rc = fine_residual(c, c->L, &r);
+  if (rc != MG_OK) return rc;
+  c->r0 = r;
+  return MG_OK;
+}
+
+// rhs of level s from the stored nodal f: b_s = M_s (f sampled on level s)
+int set_level_rhs(mg_ctx* c, int s) {
+  auto& H = c->h64;
+  cudaError_t e = stencil<double, double>(c, H, s, (int)ipow(3, c->L - s), c->f_dev, nullptr,
+                                          H.lev[s].coefM, false, H.lev[s].b, -1);
+  if (e != cudaSuccess) return fail(c, MG_ERR_CUDA, cudaGetErrorString(e));
+  return MG_OK;
+}
+
+}  // namespace
+
+// =========================================================================
+extern "C" {
+
+int mg_create(int d, int depth, const double* k2_field, double theta, double layer_width,
+              mg_ctx** out) {
+  g_create_err.clear();
+  if (out == nullptr) return fail(nullptr, MG_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (d != 2 && d != 3) return fail(nullptr, MG_ERR_INVALID, "d must be 2 or 3");
+  if (depth < 1 || depth > (d == 2 ? kMaxDepth2 : kMaxDepth3))
+    return fail(nullptr, MG_ERR_INVALID, "depth out of range");
+  if (k2_field == nullptr) return fail(nullptr, MG_ERR_INVALID, "k2_field is NULL");
+  if (!(theta >= 0.0 && theta < M_PI / 2)) return fail(nullptr, MG_ERR_INVALID, "theta must be in [0, pi/2)");
+  if (!(layer_width >= 0.0 && layer_width <= 0.5))
+    return fail(nullptr, MG_ERR_INVALID, "layer_width must be in [0, 0.5]");
+  const size_t nvf = (size_t)ipow(ipow(3, depth) + 1, d);
+  for (size_t i = 0; i < nvf; ++i)
+    if (!std::isfinite(k2_field[i])) return fail(nullptr, MG_ERR_INVALID, "k2_field holds a non-finite value");
+  // memory estimate: 5 fine-size c128 arrays per level plus scratch and f
+  {
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return fail(nullptr, MG_ERR_CUDA, "cudaMemGetInfo failed");
+    const double need = (double)nvf * 16.0 * 5.0 * 1.2 + (double)nvf * 32.0;
+    if (need > (double)fr) return fail(nullptr, MG_ERR_OOM, "grid too large for free device memory");
+  }
+  mg_ctx* c = new (std::nothrow) mg_ctx();
+  if (c == nullptr) return fail(nullptr, MG_ERR_OOM, "host allocation failed");
+  c->d = d;
+  c->L = depth;
+  c->theta = theta;
+  c->w = layer_width;
+  c->k2.assign(k2_field, k2_field + nvf);
+  int rc = build_hier<double>(c, c->h64);
+  if (rc == MG_OK) {
+    cudaError_t e = cudaMalloc(&c->f_dev, nvf * sizeof(cplx<double>));
+    if (e == cudaSuccess) e = cudaMemset(c->f_dev, 0, nvf * sizeof(cplx<double>));
+    if (e == cudaSuccess) e = cudaMalloc(&c->scratch, nvf * sizeof(cplx<double>));
+    if (e == cudaSuccess) e = cudaMallocHost(&c->host_norm, 4 * sizeof(double));
+    if (e != cudaSuccess) rc = fail(c, MG_ERR_OOM, cudaGetErrorString(e));
+  }
+  if (rc != MG_OK) {
+    g_create_err = c->err;
+    mg_destroy(c);
+    return rc;
+  }
+  *out = c;
+  return MG_OK;
+}
+
+void mg_destroy(mg_ctx* c) {
+  if (c == nullptr) return;
+  for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+  free_hier(c->h64);
+  free_hier(c->h32);
+  if (c->f_dev) cudaFree(c->f_dev);
+  if (c->scratch) cudaFree(c->scratch);
+  if (c->host_norm) cudaFreeHost(c->host_norm);
+  delete c;
+}
+
+int mg_set_stream(mg_ctx* c, void* s) {
+  if (check_ctx(c)) return MG_ERR_INVALID;
+  c->stream = (cudaStream_t)s;
+  return MG_OK;
+}
+
+int mg_set_rhs(mg_ctx* c, const mg_c128* f, int on_device) {
+  if (check_ctx(c)) return MG_ERR_INVALID;
+  if (f == nullptr) return fail(c, MG_ERR_INVALID, "f is NULL");
+  const size_t nv = c->h64.lev[c->L].nv;
+  MG_CUDA(c, cudaMemcpyAsync(c->f_dev, f, nv * sizeof(mg_c128),
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+  int rc = set_level_rhs(c, c->L);
+  if (rc != MG_OK) return rc;
+  c->r0 = -1.0;
+  return MG_OK;
+}
+
+int mg_set_solution(mg_ctx* c, const mg_c128* u, int on_device) {
+  if (check_ctx(c)) return MG_ERR_INVALID;
+  if (u == nullptr) return fail(c, MG_ERR_INVALID, "u is NULL");
+  auto& H = c->h64;
+  auto& V = H.lev[c->L];
+  // copy, then zero the boundary through the materialise kernel (c = none)
+  MG_CUDA(c, cudaMemcpyAsync(c->scratch, u, V.nv * sizeof(mg_c128),
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+  if (c->d == 2)
+    mg::materialize_kernel<double, 2><<<grid_for(V.nv), kThreads, 0, c->stream>>>(V.n, c->scratch, nullptr, V.u[H.cur]);
+  else
+    mg::materialize_kernel<double, 3><<<grid_for(V.nv), kThreads, 0, c->stream>>>(V.n, c->scratch, nullptr, V.u[H.cur]);
+  MG_CUDA(c, cudaGetLastError());
+  int rc = zero_pending(c, H, c->L);
+  if (rc != MG_OK) return rc;
+  c->r0 = -1.0;
+  return MG_OK;
+}
+
+int mg_get_solution(mg_ctx* c, mg_c128* out, int on_device) {
+  if (check_ctx(c)) return MG_ERR_INVALID;
+  if (out == nullptr) return fail(c, MG_ERR_INVALID, "out is NULL");
+  auto& H = c->h64;
+  const size_t nv = H.lev[c->L].nv;
+  if (on_device) {
+    MG_CUDA(c, materialize(c, H, c->L, (cplx<double>*)out));
+    return MG_OK;
+  }
+  MG_CUDA(c, materialize(c, H, c->L, c->scratch));
+  MG_CUDA(c, cudaMemcpyAsync(out, c->scratch, nv * sizeof(mg_c128), cudaMemcpyDeviceToHost, c->stream));
+  MG_CUDA(c, cudaStreamSynchronize(c->stream));
+  return MG_OK;
+}
+
+int mg_get_level(mg_ctx* c, int level, int which, mg_c128* out, int on_device) {
+  if (check_ctx(c)) return MG_ERR_INVALID;
+  if (out == nullptr || level < 1 || level > c->L || (which != 0 && which != 1))
+    return fail(c, MG_ERR_INVALID, "bad level/which/out");
+  if (level == c->L && which == 0) return mg_get_solution(c, out, on_device);
+  auto& V = c->h64.lev[level];
+  const void* src = which == 0 ? (const void*)V.u[0] : (const void*)V.b;
+  MG_CUDA(c, cudaMemcpyAsync(out, src, V.nv * sizeof(mg_c128),
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+  if (!on_device) MG_CUDA(c, cudaStreamSynchronize(c->stream));
+  return MG_OK;
+}
+
+int mg_cycle(mg_ctx* c, int variant, const mg_c128* omega, int transfer) {
+  if (check_ctx(c)) return MG_ERR_INVALID;
+  if (omega == nullptr) return fail(c, MG_ERR_INVALID, "omega is NULL");
+  int hb, hier;
+  if (decode_variant(c, variant, transfer, &hb, &hier)) return MG_ERR_INVALID;
+  return run_cycle(c, c->h64, c->L, hb, hier, reinterpret_cast<const cplx<double>*>(omega));
+}
+
+int mg_residual_norm(mg_ctx* c, double* abs_l2, double* rel_l2) {
+  if (check_ctx(c)) return MG_ERR_INVALID;
+  int rc = ensure_r0(c);
+  if (rc != MG_OK) return rc;
+  double r;
+  if ((rc = fine_residual(c, c->L, &r)) != MG_OK) return rc;
+  if (abs_l2) *abs_l2 = r;
+  if (rel_l2) *rel_l2 = c->r0 > 0 ? r / c->r0 : 0.0;
+  return MG_OK;
+}
+
+int mg_set_precision(mg_ctx* c, int precision, int inner_cycles) {
+  if (check_ctx(c)) return MG_ERR_INVALID;
+  if (precision != MG_C128 && precision != MG_C64_REFINE) return fail(c, MG_ERR_INVALID, "bad precision");
+  if (inner_cycles < 1 || inner_cycles > 1000) return fail(c, MG_ERR_INVALID, "inner_cycles out of range");
+  c->precision = precision;
+  c->inner_cycles = inner_cycles;
+  if (precision == MG_C64_REFINE && !c->h32.ready) {
+    int rc = build_hier<float>(c, c->h32);
+    if (rc != MG_OK) { free_hier(c->h32); return rc; }
+  }
+  return MG_OK;
+}
+
+int mg_solve(mg_ctx* c, int variant, const mg_c128* omega, int transfer, double tol, int max_cycles,
+             int* cycles_done, double* rel_res) {
+  if (check_ctx(c)) return MG_ERR_INVALID;
+  if (omega == nullptr) return fail(c, MG_ERR_INVALID, "omega is NULL");
+  if (!(tol > 0) || max_cycles < 0) return fail(c, MG_ERR_INVALID, "tol must be > 0 and max_cycles >= 0");
+  int hb, hier;
+  if (decode_variant(c, variant, transfer, &hb, &hier)) return MG_ERR_INVALID;
+  const cplx<double>* om = reinterpret_cast<const cplx<double>*>(omega);
+  int rc = ensure_r0(c);
+  if (rc != MG_OK) return rc;
+  const int L = c->L;
+  int done = 0;
+  double rel = 0;
+  {
+    double r;
+    if ((rc = fine_residual(c, L, &r)) != MG_OK) return rc;
+    rel = c->r0 > 0 ? r / c->r0 : 0.0;
+  }
+  auto finish = [&](int status) {
+    if (cycles_done) *cycles_done = done;
+    if (rel_res) *rel_res = rel;
+    return status;
+  };
+  auto diverged = [&](double x) { return !std::isfinite(x) || x > 1e6; };
+  if (c->precision == MG_C128) {
+    // fused norm of the iterate entering each cycle, read every few cycles
+    const int check = std::max(1, std::min(8, max_cycles / 8));
+    while (true) {
+      if (diverged(rel)) return finish(MG_DIVERGED);
+      if (rel <= tol) return finish(MG_OK);
+      if (done >= max_cycles) return finish(MG_NOT_CONVERGED);
+      const int m = std::min(check, max_cycles - done);
+      for (int k = 0; k < m; ++k) {
+        if ((rc = run_cycle(c, c->h64, L, hb, hier, om)) != MG_OK) return rc;
+        ++done;
+      }
+      MG_CUDA(c, cudaMemcpyAsync(c->host_norm, c->h64.norm2, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+      MG_CUDA(c, cudaStreamSynchronize(c->stream));
+      const double prev = std::sqrt(*c->host_norm) / (c->r0 > 0 ? c->r0 : 1.0);
+      if (diverged(prev) || prev <= tol || done >= max_cycles) {
+        double r;
+        if ((rc = fine_residual(c, L, &r)) != MG_OK) return rc;
+        rel = c->r0 > 0 ? r / c->r0 : 0.0;
+      } else {
+        rel = prev;  // residual of the iterate that entered the last cycle
+      }
+    }
+  }
+  // complex64 cycles inside FP64 defect correction
+  auto& H = c->h64;
+  auto& E = c->h32;
+  auto& VF = H.lev[L];
+  auto& EF = E.lev[L];
+  cplx<double>* u = VF.u[H.cur];
+  // u must be materialised: fold any pending correction into U
+  MG_CUDA(c, materialize(c, H, L, c->scratch));
+  MG_CUDA(c, cudaMemcpyAsync(u, c->scratch, VF.nv * sizeof(cplx<double>), cudaMemcpyDeviceToDevice, c->stream));
+  if ((rc = zero_pending(c, H, L)) != MG_OK) return rc;
+  while (true) {
+    if (diverged(rel)) return finish(MG_DIVERGED);
+    if (rel <= tol) return finish(MG_OK);
+    if (done >= max_cycles) return finish(MG_NOT_CONVERGED);
+    // r = b - H u in FP64, stored as complex64 rhs of the inner problem
+    MG_CUDA(c, (stencil<double, float>(c, H, L, 1, u, VF.b, VF.coefH, true, EF.b, -1)));
+    MG_CUDA(c, cudaMemsetAsync(EF.u[E.cur], 0, EF.nv * sizeof(cplx<float>), c->stream));
+    for (int l = 1; l < L; ++l) {
+      MG_CUDA(c, cudaMemsetAsync(E.lev[l].corr, 0, E.lev[l].nv * sizeof(cplx<float>), c->stream));
+      MG_CUDA(c, cudaMemsetAsync(E.lev[l].t, 0, E.lev[l].nv * sizeof(cplx<float>), c->stream));
+    }
+    const int m = std::min(c->inner_cycles, std::max(1, max_cycles - done));
+    for (int k = 0; k < m; ++k) {
+      if ((rc = run_cycle(c, E, L, hb, hier, om)) != MG_OK) return rc;
+      ++done;
+    }
+    // u += E + P corr (FP64 update)
+    const cplx<float>* cc = L > 1 ? E.lev[L - 1].corr : nullptr;
+    ++c->launches;
+    if (c->d == 2)
+      mg::update_kernel<float, 2><<<grid_for(VF.nv), kThreads, 0, c->stream>>>(VF.n, u, EF.u[E.cur], cc);
+    else
+      mg::update_kernel<float, 3><<<grid_for(VF.nv), kThreads, 0, c->stream>>>(VF.n, u, EF.u[E.cur], cc);
+    MG_CUDA(c, cudaGetLastError());
+    double r;
+    MG_CUDA(c, (stencil<double, double>(c, H, L, 1, u, VF.b, VF.coefH, true, (cplx<double>*)nullptr, 1)));
+    MG_CUDA(c, cudaMemcpyAsync(c->host_norm, H.norm2 + 1, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    MG_CUDA(c, cudaStreamSynchronize(c->stream));
+    r = std::sqrt(*c->host_norm);
+    rel = c->r0 > 0 ? r / c->r0 : 0.0;
+  }
+}
+
+int mg_fmg(mg_ctx* c, int variant, const mg_c128* omega, int transfer, int cycles_per_stage) {
+  if (check_ctx(c)) return MG_ERR_INVALID;
+  if (omega == nullptr || cycles_per_stage < 0) return fail(c, MG_ERR_INVALID, "bad omega/cycles_per_stage");
+  int hb, hier;
+  if (decode_variant(c, variant, transfer, &hb, &hier)) return MG_ERR_INVALID;
+  const cplx<double>* om = reinterpret_cast<const cplx<double>*>(omega);
+  auto& H = c->h64;
+  const int L = c->L;
+  int rc;
+  for (int s = 1; s <= L; ++s) {
+    auto& V = H.lev[s];
+    if (s < L && (rc = set_level_rhs(c, s)) != MG_OK) return rc;
+    if (s == 1) {
+      MG_CUDA(c, cudaMemsetAsync(V.u[H.cur], 0, V.nv * sizeof(cplx<double>), c->stream));
+    } else {
+      // u_s = P u_{s-1}: materialised previous stage, interpolated
+      MG_CUDA(c, materialize(c, H, s - 1, c->scratch));
+      const cplx<double>* nul = nullptr;
+      if (c->d == 2)
+        mg::materialize_kernel<double, 2><<<grid_for(V.nv), kThreads, 0, c->stream>>>(
+            V.n, nul, c->scratch, V.u[H.cur]);
+      else
+        mg::materialize_kernel<double, 3><<<grid_for(V.nv), kThreads, 0, c->stream>>>(
+            V.n, nul, c->scratch, V.u[H.cur]);
+      MG_CUDA(c, cudaGetLastError());
+    }
+    if ((rc = zero_pending(c, H, s)) != MG_OK) return rc;
+    if (s == L) break;
+    for (int k = 0; k < cycles_per_stage; ++k)
+      if ((rc = run_cycle(c, H, s, hb, hier, om)) != MG_OK) return rc;
+  }
+  // coarse right-hand sides of later cycles are restricted from b_L again
+  c->r0 = -1.0;
+  return MG_OK;
+}
+
+int mg_omega_scheme(int scheme, mg_c128 omega_s, int depth, int iter_n, int l_grid, mg_c128* out) {
+  if (out == nullptr || depth < 1) return MG_ERR_INVALID;
+  if (scheme == MG_OMEGA_TRANSITION && iter_n < 1) return MG_ERR_INVALID;
+  const cd w(omega_s.re, omega_s.im);
+  for (int l = 1; l <= depth; ++l) {
+    const int succ = depth - l;
+    cd v;
+    switch (scheme) {
+      case MG_OMEGA_JACOBI: v = succ == 0 ? w : cd(0); break;
+      case MG_OMEGA_UCG: v = w; break;
+      case MG_OMEGA_LGRID: v = succ <= l_grid ? w : cd(0); break;
+      case MG_OMEGA_EXP: v = std::pow(w, (double)(succ + 1)); break;
+      case MG_OMEGA_TRANSITION: v = std::pow(w, (1.0 - 1.0 / iter_n) * (succ + 1)); break;
+      default: return MG_ERR_INVALID;
+    }
+    out[l - 1].re = v.real();
+    out[l - 1].im = v.imag();
+  }
+  return MG_OK;
+}
+
+int mg_set_timing(mg_ctx* c, int enable) {
+  if (check_ctx(c)) return MG_ERR_INVALID;
+  c->timing = enable != 0;
+  return MG_OK;
+}
+
+int mg_get_stats(mg_ctx* c, long long* launches, int* fine_sweeps, double* fine_ms) {
+  if (check_ctx(c)) return MG_ERR_INVALID;
+  MG_CUDA(c, cudaStreamSynchronize(c->stream));
+  double ms = 0;
+  for (size_t i = 0; i + 1 < c->ev_used; i += 2) {
+    float t = 0;
+    MG_CUDA(c, cudaEventElapsedTime(&t, c->ev[i], c->ev[i + 1]));
+    ms += t;
+  }
+  if (launches) *launches = c->launches;
+  if (fine_sweeps) *fine_sweeps = (int)(c->ev_used / 2);
+  if (fine_ms) *fine_ms = ms;
+  c->launches = 0;
+  c->ev_used = 0;
+  return MG_OK;
+}
+
+const char* mg_last_error(const mg_ctx* c) { return c ? c->err.c_str() : g_create_err.c_str(); }
+
+}  // extern "C"

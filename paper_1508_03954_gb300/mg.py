@@ -1,0 +1,269 @@
+"""Thin ctypes binding of the C ABI in include/mg.h.
+
+Argument marshalling only: every step of the solver runs in the CUDA library
+``_lib/libmg.so``.  The library must be built (``build.build()``); when it is
+missing every entry point raises ``RuntimeError`` -- there is no CPU
+fallback.  Arrays are numpy arrays (host) or torch CUDA tensors (device),
+complex128, C-contiguous, fine-vertex layout with x fastest.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+MG_OK, MG_ERR_INVALID, MG_ERR_CUDA, MG_ERR_OOM, MG_DIVERGED, MG_NOT_CONVERGED, MG_ERR_TIMEOUT = range(7)
+MG_ADD, MG_HB, MG_BPX = 0, 1, 2
+MG_DLINEAR, MG_HIERARCHICAL = 0, 1
+MG_C128, MG_C64_REFINE = 0, 1
+MG_OMEGA_JACOBI, MG_OMEGA_UCG, MG_OMEGA_LGRID, MG_OMEGA_EXP, MG_OMEGA_TRANSITION = range(5)
+
+STATUS_NAMES = {0: "MG_OK", 1: "MG_ERR_INVALID", 2: "MG_ERR_CUDA", 3: "MG_ERR_OOM",
+                4: "MG_DIVERGED", 5: "MG_NOT_CONVERGED", 6: "MG_ERR_TIMEOUT"}
+
+# every symbol include/mg.h declares
+EXPORTS = ["mg_create", "mg_destroy", "mg_set_stream", "mg_set_rhs", "mg_set_solution",
+           "mg_get_solution", "mg_cycle", "mg_residual_norm", "mg_solve", "mg_set_precision",
+           "mg_fmg", "mg_omega_scheme", "mg_get_level", "mg_set_timing", "mg_get_stats",
+           "mg_last_error"]
+
+
+class MgC128(ctypes.Structure):
+    _fields_ = [("re", ctypes.c_double), ("im", ctypes.c_double)]
+
+
+class MgError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Loads the CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or lib_path()
+    if not os.path.exists(p):
+        raise RuntimeError(f"CUDA library {p} is not built; run "
+                           "paper_1508_03954_gb300.build.build() (no CPU fallback exists)")
+    L = ctypes.CDLL(p)
+    vp, ip, dp = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    pc = ctypes.POINTER(MgC128)
+    sig = {
+        "mg_create": (ip, [ip, ip, ctypes.POINTER(dp), dp, dp, ctypes.POINTER(vp)]),
+        "mg_destroy": (None, [vp]),
+        "mg_set_stream": (ip, [vp, vp]),
+        "mg_set_rhs": (ip, [vp, vp, ip]),
+        "mg_set_solution": (ip, [vp, vp, ip]),
+        "mg_get_solution": (ip, [vp, vp, ip]),
+        "mg_cycle": (ip, [vp, ip, pc, ip]),
+        "mg_residual_norm": (ip, [vp, ctypes.POINTER(dp), ctypes.POINTER(dp)]),
+        "mg_solve": (ip, [vp, ip, pc, ip, dp, ip, ctypes.POINTER(ip), ctypes.POINTER(dp)]),
+        "mg_set_precision": (ip, [vp, ip, ip]),
+        "mg_fmg": (ip, [vp, ip, pc, ip, ip]),
+        "mg_omega_scheme": (ip, [ip, MgC128, ip, ip, ip, pc]),
+        "mg_get_level": (ip, [vp, ip, ip, vp, ip]),
+        "mg_set_timing": (ip, [vp, ip]),
+        "mg_get_stats": (ip, [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ip),
+                              ctypes.POINTER(dp)]),
+        "mg_last_error": (ctypes.c_char_p, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _omega_array(omega, depth):
+    om = np.ascontiguousarray(np.asarray(omega, dtype=np.complex128).reshape(-1))
+    if om.shape[0] != depth:
+        raise ValueError(f"omega needs {depth} entries (one per level)")
+    arr = (MgC128 * depth)()
+    for i, w in enumerate(om):
+        arr[i].re, arr[i].im = float(w.real), float(w.imag)
+    return arr
+
+
+def _ptr(x, nvals):
+    """(pointer, on_device, keepalive) of a complex128 array of nvals values."""
+    if hasattr(x, "data_ptr") and hasattr(x, "is_cuda"):
+        import torch
+        if x.dtype != torch.complex128 or not x.is_contiguous() or x.numel() != nvals:
+            raise ValueError("device arrays must be contiguous complex128 tensors of the fine size")
+        return ctypes.c_void_p(x.data_ptr()), (1 if x.is_cuda else 0), x
+    a = np.ascontiguousarray(np.asarray(x, dtype=np.complex128))
+    if a.size != nvals:
+        raise ValueError(f"expected {nvals} values, got {a.size}")
+    return a.ctypes.data_as(ctypes.c_void_p), 0, a
+
+
+def omega_scheme(scheme, omega_s, depth, iter_n=1, l_grid=0):
+    L = load()
+    out = (MgC128 * depth)()
+    w = MgC128(float(np.real(omega_s)), float(np.imag(omega_s)))
+    rc = L.mg_omega_scheme(scheme, w, depth, iter_n, l_grid, out)
+    if rc != MG_OK:
+        raise MgError(rc, "mg_omega_scheme")
+    return np.array([complex(o.re, o.im) for o in out])
+
+
+class Solver:
+    """One solver context (mg_create .. mg_destroy)."""
+
+    def __init__(self, d, depth, k2_field, theta, layer_width):
+        L = load()
+        self.d, self.depth = d, depth
+        self.n = 3 ** depth
+        self.shape = (self.n + 1,) * d
+        self.nv = (self.n + 1) ** d
+        k2 = np.ascontiguousarray(np.asarray(k2_field, dtype=np.float64))
+        if k2.size != self.nv:
+            raise ValueError(f"k2_field needs {self.nv} values")
+        h = ctypes.c_void_p()
+        rc = L.mg_create(d, depth, k2.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                         float(theta), float(layer_width), ctypes.byref(h))
+        if rc != MG_OK:
+            raise MgError(rc, L.mg_last_error(None).decode())
+        self._h = h
+        self._L = L
+
+    # -- helpers
+    def _check(self, rc, what):
+        if rc not in (MG_OK,):
+            raise MgError(rc, f"{what}: {self._L.mg_last_error(self._h).decode()}")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.mg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- API
+    def set_stream(self, stream_handle):
+        self._check(self._L.mg_set_stream(self._h, ctypes.c_void_p(stream_handle)), "mg_set_stream")
+
+    def set_rhs(self, f):
+        p, dev, _keep = _ptr(f, self.nv)
+        self._check(self._L.mg_set_rhs(self._h, p, dev), "mg_set_rhs")
+
+    def set_solution(self, u):
+        p, dev, _keep = _ptr(u, self.nv)
+        self._check(self._L.mg_set_solution(self._h, p, dev), "mg_set_solution")
+
+    def get_solution(self, out=None):
+        if out is None:
+            out = np.empty(self.shape, dtype=np.complex128)
+        p, dev, _keep = _ptr(out, self.nv)
+        self._check(self._L.mg_get_solution(self._h, p, dev), "mg_get_solution")
+        return out
+
+    def get_level(self, level, which):
+        n = 3 ** level
+        out = np.empty(((n + 1),) * self.d, dtype=np.complex128)
+        rc = self._L.mg_get_level(self._h, level, which, out.ctypes.data_as(ctypes.c_void_p), 0)
+        self._check(rc, "mg_get_level")
+        return out
+
+    def cycle(self, variant, omega, transfer):
+        self._check(self._L.mg_cycle(self._h, variant, _omega_array(omega, self.depth), transfer),
+                    "mg_cycle")
+
+    def residual_norm(self):
+        a, r = ctypes.c_double(), ctypes.c_double()
+        self._check(self._L.mg_residual_norm(self._h, ctypes.byref(a), ctypes.byref(r)),
+                    "mg_residual_norm")
+        return a.value, r.value
+
+    def solve(self, variant, omega, transfer, tol, max_cycles):
+        """Returns (status, cycles_done, rel_res); MG_DIVERGED and
+        MG_NOT_CONVERGED are returned, not raised."""
+        n, rel = ctypes.c_int(), ctypes.c_double()
+        rc = self._L.mg_solve(self._h, variant, _omega_array(omega, self.depth), transfer,
+                              float(tol), int(max_cycles), ctypes.byref(n), ctypes.byref(rel))
+        if rc not in (MG_OK, MG_DIVERGED, MG_NOT_CONVERGED):
+            self._check(rc, "mg_solve")
+        return rc, n.value, rel.value
+
+    def set_precision(self, precision, inner_cycles):
+        self._check(self._L.mg_set_precision(self._h, precision, inner_cycles), "mg_set_precision")
+
+    def set_timing(self, enable):
+        self._check(self._L.mg_set_timing(self._h, 1 if enable else 0), "mg_set_timing")
+
+    def get_stats(self):
+        """(kernel launches, timed fine sweeps, their device ms) since the last call."""
+        n, k, ms = ctypes.c_longlong(), ctypes.c_int(), ctypes.c_double()
+        self._check(self._L.mg_get_stats(self._h, ctypes.byref(n), ctypes.byref(k), ctypes.byref(ms)),
+                    "mg_get_stats")
+        return n.value, k.value, ms.value
+
+    def fmg(self, variant, omega, transfer, cycles_per_stage):
+        self._check(self._L.mg_fmg(self._h, variant, _omega_array(omega, self.depth), transfer,
+                                   cycles_per_stage), "mg_fmg")
+
+
+# module-level names matching the C ABI
+def mg_create(d, depth, k2_field, theta, layer_width):
+    return Solver(d, depth, k2_field, theta, layer_width)
+
+
+def mg_destroy(s):
+    s.close()
+
+
+def mg_set_stream(s, stream):
+    s.set_stream(stream)
+
+
+def mg_set_rhs(s, f):
+    s.set_rhs(f)
+
+
+def mg_set_solution(s, u):
+    s.set_solution(u)
+
+
+def mg_get_solution(s, out=None):
+    return s.get_solution(out)
+
+
+def mg_cycle(s, variant, omega, transfer):
+    s.cycle(variant, omega, transfer)
+
+
+def mg_residual_norm(s):
+    return s.residual_norm()
+
+
+def mg_solve(s, variant, omega, transfer, tol, max_cycles):
+    return s.solve(variant, omega, transfer, tol, max_cycles)
+
+
+def mg_set_precision(s, precision, inner_cycles):
+    s.set_precision(precision, inner_cycles)
+
+
+def mg_fmg(s, variant, omega, transfer, cycles_per_stage):
+    s.fmg(variant, omega, transfer, cycles_per_stage)
+
+
+def mg_omega_scheme(scheme, omega_s, depth, iter_n=1, l_grid=0):
+    return omega_scheme(scheme, omega_s, depth, iter_n, l_grid)
