@@ -159,6 +159,28 @@ int mg_set_timing(mg_ctx* ctx, int enable);
 int mg_get_stats(mg_ctx* ctx, long long* kernel_launches, int* fine_sweeps,
                  double* fine_sweep_ms);
 
+/* Allocation-free fine residual (the paper has no counterpart; it serves
+ * callers that cannot allocate device memory when they need a residual, such
+ * as frameworks that reserve the whole device for their own pool, or
+ * time-critical loops that cannot take the implicit synchronisation of
+ * cudaMalloc/cudaFree).  u and b are device arrays in the fine-vertex layout
+ * (u's Dirichlet ring must hold zeros); r (device, may be NULL) receives
+ * b - H_L u on the interior and zero on the boundary; norm2 (device, one
+ * double) receives the FP64 sum of |r|^2 over the interior vertices.  Work is
+ * enqueued on the context's stream; the call allocates nothing.
+ * Scratch: the per-block partial sums and the completion ticket live in a
+ * file-scope device array of 16384 doubles + 256 bytes that every GPU which
+ * loads the library holds until exit.  The first call on a device looks up
+ * that array's device address (cudaGetSymbolAddress, with the device
+ * current), so make the first call on each device before any stream capture.
+ * Every call shares the array and it keeps the last call's contents (the
+ * call clears the ticket itself); calls whose kernels overlap on the GPU
+ * race on it.  Limit: one block per 256 vertices and one partial per block,
+ * so fine grids above 16384 * 256 = 4,194,304 vertices (2D depth >= 7,
+ * 3D depth >= 5) are rejected with MG_ERR_INVALID. */
+int mg_residual_noalloc(mg_ctx* ctx, const mg_c128* u, const mg_c128* b, mg_c128* r,
+                        double* norm2);
+
 /* Message of the last failure on this context ("" if none); ctx may be NULL
  * for failures of mg_create. */
 const char* mg_last_error(const mg_ctx* ctx);

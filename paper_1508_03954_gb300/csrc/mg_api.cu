@@ -796,3 +796,88 @@ int mg_get_stats(mg_ctx* c, long long* launches, int* fine_sweeps, double* fine_
 const char* mg_last_error(const mg_ctx* c) { return c ? c->err.c_str() : g_create_err.c_str(); }
 
 }  // extern "C"
+
+// =========================================================================
+// Allocation-free fine residual.
+//
+// Some callers cannot allocate device memory when they need a residual:
+// frameworks that reserve the whole device up front for their own memory
+// pool, and time-critical loops that cannot afford the implicit
+// synchronisation a cudaMalloc/cudaFree may cause.  This entry point gives
+// them r = b - H_L u and |r|^2 without allocating: the per-block partial sums
+// and the completion ticket of the deterministic two-pass reduction live in a
+// file-scope device array, not in memory obtained from cudaMalloc.
+//
+// Limit: one 256-thread block per 256 fine vertices and one partial per
+// block, so the array (kNoAllocMaxBlocks doubles + the ticket) bounds the fine
+// grid at kNoAllocMaxBlocks * 256 = 4,194,304 vertices.  Every call on a
+// device shares the array and it keeps the last call's contents; calls whose
+// kernels overlap on the GPU race on it.
+// =========================================================================
+#include <mutex>
+
+namespace {
+constexpr int kNoAllocMaxBlocks = 16384;
+constexpr size_t kNoAllocTicketOffset = (size_t)kNoAllocMaxBlocks * sizeof(double);
+constexpr size_t kNoAllocBytes = kNoAllocTicketOffset + 256;
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kNoAllocMaxDevices] = {};
+}  // namespace
+
+// host code must not use this name as an address; see noalloc_scratch()
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+namespace {
+// Device address of the scratch array on the current device, looked up once
+// per device (with that device current) by the first call that needs it.
+int noalloc_scratch(mg_ctx* c, unsigned char** out) {
+  int dev = -1;
+  MG_CUDA(c, cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(c, MG_ERR_INVALID, "device ordinal out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (g_noalloc_addr[dev] == nullptr) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || p == nullptr)
+      return fail(c, MG_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
+    g_noalloc_addr[dev] = p;
+  }
+  *out = static_cast<unsigned char*>(g_noalloc_addr[dev]);
+  return MG_OK;
+}
+}  // namespace
+
+extern "C" int mg_residual_noalloc(mg_ctx* c, const mg_c128* u, const mg_c128* b, mg_c128* r,
+                                   double* norm2) {
+  if (check_ctx(c)) return MG_ERR_INVALID;
+  if (u == nullptr || b == nullptr || norm2 == nullptr)
+    return fail(c, MG_ERR_INVALID, "u, b and norm2 must be device pointers");
+  auto& H = c->h64;
+  auto& V = H.lev[c->L];
+  const size_t nblocks = (V.nv + kThreads - 1) / kThreads;
+  if (nblocks > (size_t)kNoAllocMaxBlocks)
+    return fail(c, MG_ERR_INVALID,
+                "mg_residual_noalloc: the fine grid has " + std::to_string(V.nv) +
+                    " vertices; the allocation-free residual handles at most " +
+                    std::to_string((size_t)kNoAllocMaxBlocks * kThreads));
+  unsigned char* scratch = nullptr;
+  int rc = noalloc_scratch(c, &scratch);
+  if (rc != MG_OK) return rc;
+  double* partial = reinterpret_cast<double*>(scratch);
+  unsigned* ticket = reinterpret_cast<unsigned*>(scratch + kNoAllocTicketOffset);
+  // the ticket must start at zero; the partials are written before they are read
+  MG_CUDA(c, cudaMemsetAsync(ticket, 0, sizeof(unsigned), c->stream));
+  ++c->launches;
+  const cplx<double>* x = reinterpret_cast<const cplx<double>*>(u);
+  const cplx<double>* bb = reinterpret_cast<const cplx<double>*>(b);
+  cplx<double>* y = reinterpret_cast<cplx<double>*>(r);
+  if (c->d == 2)
+    mg::stencil_kernel<double, double, 2><<<(unsigned)nblocks, kThreads, 0, c->stream>>>(
+        V.n, 1, x, bb, V.typ, V.coefH, V.phic, V.hcell, y, partial, ticket, norm2);
+  else
+    mg::stencil_kernel<double, double, 3><<<(unsigned)nblocks, kThreads, 0, c->stream>>>(
+        V.n, 1, x, bb, V.typ, V.coefH, V.phic, V.hcell, y, partial, ticket, norm2);
+  MG_CUDA(c, cudaGetLastError());
+  return MG_OK;
+}

@@ -28,7 +28,7 @@ STATUS_NAMES = {0: "MG_OK", 1: "MG_ERR_INVALID", 2: "MG_ERR_CUDA", 3: "MG_ERR_OO
 EXPORTS = ["mg_create", "mg_destroy", "mg_set_stream", "mg_set_rhs", "mg_set_solution",
            "mg_get_solution", "mg_cycle", "mg_residual_norm", "mg_solve", "mg_set_precision",
            "mg_fmg", "mg_omega_scheme", "mg_get_level", "mg_set_timing", "mg_get_stats",
-           "mg_last_error"]
+           "mg_residual_noalloc", "mg_last_error"]
 
 
 class MgC128(ctypes.Structure):
@@ -77,6 +77,7 @@ def load(path: str | None = None):
         "mg_set_timing": (ip, [vp, ip]),
         "mg_get_stats": (ip, [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ip),
                               ctypes.POINTER(dp)]),
+        "mg_residual_noalloc": (ip, [vp, vp, vp, vp, vp]),
         "mg_last_error": (ctypes.c_char_p, [vp]),
     }
     for name, (res, args) in sig.items():
@@ -214,6 +215,33 @@ class Solver:
         self._check(self._L.mg_get_stats(self._h, ctypes.byref(n), ctypes.byref(k), ctypes.byref(ms)),
                     "mg_get_stats")
         return n.value, k.value, ms.value
+
+    def residual_noalloc(self, u, b, r, norm2):
+        """r = b - H_L u and |r|^2 into caller-owned device tensors, using
+        the library's static scratch instead of any allocation.  u, b, r:
+        complex128 CUDA tensors of the fine size (r may be None); norm2: a
+        float64 CUDA tensor with at least one element."""
+        import torch
+        for t in (u, b):
+            if not (t.is_cuda and t.dtype == torch.complex128 and t.is_contiguous()
+                    and t.numel() == self.nv):
+                raise ValueError("u and b must be contiguous complex128 CUDA tensors of the fine size")
+        if r is not None and not (r.is_cuda and r.dtype == torch.complex128 and r.is_contiguous()
+                                  and r.numel() == self.nv):
+            raise ValueError("r must be a contiguous complex128 CUDA tensor of the fine size")
+        if not (norm2.is_cuda and norm2.dtype == torch.float64 and norm2.numel() >= 1):
+            raise ValueError("norm2 must be a float64 CUDA tensor")
+        rp = ctypes.c_void_p(r.data_ptr()) if r is not None else None
+        self._check(self._L.mg_residual_noalloc(self._h, ctypes.c_void_p(u.data_ptr()),
+                                                ctypes.c_void_p(b.data_ptr()), rp,
+                                                ctypes.c_void_p(norm2.data_ptr())),
+                    "mg_residual_noalloc")
+
+    def get_level_device(self, level, which, out):
+        """Copies a per-level array into a caller-owned complex128 CUDA tensor."""
+        rc = self._L.mg_get_level(self._h, level, which, ctypes.c_void_p(out.data_ptr()), 1)
+        self._check(rc, "mg_get_level")
+        return out
 
     def fmg(self, variant, omega, transfer, cycles_per_stage):
         self._check(self._L.mg_fmg(self._h, variant, _omega_array(omega, self.depth), transfer,
