@@ -68,26 +68,33 @@ def complex_row_fraction(d, depth, w):
     return 1.0 - real_frac_axis ** d
 
 
-def fine_sweep_counts(d, depth, w, bpx, omega_real, word=16):
+def fine_sweep_counts(d, depth, w, bpx, omega_real, word=16, galerkin=True):
     """(flops, bytes) the method needs for one finest-level sweep.
 
-    Per interior fine vertex (real x complex MAC = 4 flops, complex x complex
-    MAC = 8 flops): residual and hierarchical residual rows of 3^d entries
-    (complex where a neighbouring cell is scaled, real otherwise) plus the
-    subtraction from b; d-linear interpolation of the pending coarse
-    correction and of I u ((5/3)^d MACs on average each); restriction
-    (5^d / 3^d MACs per fine vertex); Jacobi (complex or real scaling); BPX
-    surplus of du ((5/3)^d MACs); the update and |r|^2.
-    Bytes: U read, b read, U' written on the fine level (3 words per
-    vertex), pending correction read and b, u written on the next coarser
-    level (3 words per coarse vertex)."""
+    Per interior fine vertex (an FMA is 2 flops; real x complex MAC = 4 flops,
+    complex x complex MAC = 8 flops): the residual row of 3^d entries (complex
+    where a neighbouring cell is scaled, real otherwise, b folded into the
+    accumulation); d-linear interpolation of the pending coarse correction
+    ((5/3)^d MACs on average); restriction ((5/3)^d MACs per fine vertex);
+    the coarse right-hand side either as G u_{l-1} (one 3^d Galerkin row per
+    coarse vertex, galerkin=True) or as the hierarchical residual b - H uhat
+    with the surplus uhat = u - P I u (galerkin=False); Jacobi (complex or
+    real scaling); BPX surplus of du ((5/3)^d MACs + subtraction); the update
+    and |r|^2.
+    Bytes: U read, b read, U' written on the fine level (3 words per vertex),
+    pending correction read and b, u written on the next coarser level (3
+    words per coarse vertex)."""
     n = 3 ** depth
     ns = 3 ** d
     fc = complex_row_fraction(d, depth, w)
-    row = fc * (ns * 8 + 2) + (1 - fc) * (ns * 4 + 2)
+    row = fc * ns * 8 + (1 - fc) * ns * 4
     interp = (5.0 / 3.0) ** d * 4
     jac = fc * 6 + (1 - fc) * (2 if omega_real else 6)
-    per = 2 * row + interp + (interp + 2) + interp + jac + (interp + 2 if bpx else 0) + 2 + 4
+    if galerkin:
+        coarse_rhs = fc * 8 + (1 - fc) * 4          # one G entry per fine vertex on average
+    else:
+        coarse_rhs = row + 2 + interp + 2           # second row on uhat, surplus
+    per = row + interp + interp + coarse_rhs + jac + (interp + 2 if bpx else 0) + 2 + 4
     flops = per * (n - 1) ** d
     nbytes = 3 * word * (n + 1) ** d + 3 * word * (n // 3 + 1) ** d
     return flops, nbytes
@@ -270,7 +277,6 @@ def main():
     for _ in range(args.warmup):
         s.cycle(variant, omega, transfer)
     torch.cuda.synchronize()
-    s.set_timing(True)
     s.get_stats()
 
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -289,14 +295,27 @@ def main():
     if dist is not None:
         dist.barrier()
     clk = clocks.stop()
-    launches, nsweeps, sweep_ms = s.get_stats()
-    s.set_timing(False)
+    launches, _, _ = s.get_stats()
     total_ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
     t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
     if dist is not None:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     total_ms = float(t.item())
     value = interior * args.steps * world / (total_ms / 1e3)
+
+    # the dominant kernel alone: the same cycles with an event pair around the
+    # finest-level sweep (a separate pass, so the timed steps above run the
+    # whole cycle as one graph)
+    s.set_timing(True)
+    for _ in range(3):
+        s.cycle(variant, omega, transfer)
+    torch.cuda.synchronize()
+    s.get_stats()
+    for k in range(min(args.steps, 500)):
+        flush.fill_(float(k & 7))
+        s.cycle(variant, omega, transfer)
+    _, nsweeps, sweep_ms = s.get_stats()
+    s.set_timing(False)
 
     # end to end through the public API with pinned host buffers
     u_h = torch.zeros(s.shape, dtype=torch.complex128).pin_memory()
@@ -328,11 +347,11 @@ def main():
     sweep_s = (sweep_ms / max(nsweeps, 1)) / 1e3
     achieved = flops / sweep_s
     csrc = os.path.join(ROOT, "paper_1508_03954_gb300", "csrc")
-    traffic, sha = recorded_traffic("fine_sweep_c128_2d_depth6",
+    traffic, sha = recorded_traffic("fine_sweep2_c128_2d_depth6",
                                     [os.path.join(csrc, f) for f in sorted(os.listdir(csrc))])
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": FP64_PEAK_FLOPS / 1e12,
                 "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_FLOPS, "traffic": traffic,
-                "kernel": "sweep_kernel<double,2,8,256> (finest level)",
+                "kernel": "sweep2_kernel<12,256> (finest level, FP64)",
                 "peak_source": "FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
                 "hbm": {"achieved_gbs": nbytes / sweep_s / 1e9, "peak_gbs": peaks.get("hbm_gbs"),
                         "frac": nbytes / sweep_s / 1e9 / peaks.get("hbm_gbs", 6800.0),

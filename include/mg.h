@@ -159,6 +159,17 @@ int mg_set_timing(mg_ctx* ctx, int enable);
 int mg_get_stats(mg_ctx* ctx, long long* kernel_launches, int* fine_sweeps,
                  double* fine_sweep_ms);
 
+/* Per-item trace of the persistent launches (2D FP64 path): with tracing on,
+ * every tile of the finest-level sweep and every item of the coarse chain
+ * records {taken, dependencies met, done, SM id} (globaltimer ns) into a
+ * device buffer, overwritten by each cycle.  mg_get_trace synchronises and
+ * copies fine_slots fine-sweep records (indexed by queue position) followed by
+ * chain_slots chain records (indexed by item) to out (host, 4 x u64 each).
+ * Both counts are at most 65536.  Turning tracing on or off drops captured
+ * cycle graphs. */
+int mg_set_trace(mg_ctx* ctx, int enable);
+int mg_get_trace(mg_ctx* ctx, unsigned long long* out, int fine_slots, int chain_slots);
+
 /* Allocation-free fine residual (the paper has no counterpart; it serves
  * callers that cannot allocate device memory when they need a residual, such
  * as frameworks that reserve the whole device for their own pool, or

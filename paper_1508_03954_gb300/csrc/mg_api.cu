@@ -3,16 +3,21 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <complex>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
+#include <type_traits>
 #include <string>
 #include <vector>
 
 #include "mg.h"
 #include "mg_kernels.cuh"
+#include "mg_sweep2d.cuh"
+#include "mg_persist.cuh"
 
 using mg::cplx;
 using cd = std::complex<double>;
@@ -24,6 +29,15 @@ constexpr int kMaxDepth3 = 6;  // (3^6+1)^3 vertices: 389 M
 constexpr int kThreads = 256;
 constexpr int kTC2 = 8;        // coarse cells per tile edge, 2D
 constexpr int kTC3 = 2;        // coarse cells per tile edge, 3D
+// resident blocks per SM of the persistent launches
+#ifndef MG_FINE_BPSM
+#define MG_FINE_BPSM 4
+#endif
+#ifndef MG_CHAIN_BPSM
+#define MG_CHAIN_BPSM 4
+#endif
+constexpr int kTraceFine = 1 << 16;   // trace slots of the fine sweep
+constexpr int kTraceChain = 1 << 16;  // trace slots of the chain
 
 long long ipow(long long b, int e) {
   long long r = 1;
@@ -47,12 +61,35 @@ struct Hier {
     R* phic = nullptr;
     cplx<R>* hcell = nullptr;
     std::vector<cd> diag;     // D per vertex type (constant shift)
+    unsigned realrow = 0;     // bit t: stencil row of type t is real
+    // 2D FP64 path: Galerkin rows of G_{l-1} = R H_l P per coarse row class
+    bool gok = false;
+    int* order8 = nullptr;      // fine tiles (8 coarse cells) by decreasing cost
+    uint8_t* gtyp = nullptr;
+    cplx<R>* gcoef = nullptr;
   };
   int d = 0, L = 0;
   bool varphi = false;
   bool ready = false;
   std::vector<Lev> lev;
   int cur = 0;               // active fine U buffer
+  // captured cycles: key -> (fine sweep graph, coarse chain graph)
+  struct GraphEntry {
+    std::vector<double> key;
+    cudaGraphExec_t fine = nullptr, coarse = nullptr;
+    int nfine = 0, ncoarse = 0;  // kernel nodes
+  };
+  std::vector<GraphEntry> graphs;
+  // persistent coarse-chain plans: key -> device item list and argument tables
+  struct ChainPlan {
+    std::vector<double> key;
+    mg::ChainItem* items = nullptr;
+    mg::Sweep2Args* s2 = nullptr;
+    mg::ProlongArgs* pr = nullptr;
+    mg::CorrArgs* co = nullptr;
+    int nitems = 0, grid = 0;
+  };
+  std::vector<ChainPlan> chains;
   double* partial = nullptr;
   unsigned* ticket = nullptr;
   double* norm2 = nullptr;   // [0] cycle norm, [1] standalone norm
@@ -75,6 +112,16 @@ struct mg_ctx {
   cplx<double>* scratch = nullptr;     // fine-size FP64 scratch
   double* host_norm = nullptr;         // pinned
   std::string err;
+  cudaStream_t cap_stream = nullptr;   // private stream the cycle graphs are captured on
+  unsigned* chain_ctr = nullptr;       // [0] queue head, [1..] completion counters
+  unsigned* dev_err = nullptr;         // bounded-wait timeout flag (sticky until read)
+  unsigned spin_limit = 1u << 22;
+  int chain_bpsm = 0;                  // resident chain blocks per SM
+  int fine_bpsm = MG_FINE_BPSM;        // persistent fine-sweep blocks per SM
+  // optional per-item trace of the persistent launches (last cycle only)
+  unsigned long long* trace = nullptr; // [0, 4*kTraceFine): fine sweep; then chain
+  bool tracing = false;
+  bool use_graphs = true;
   // instrumentation
   long long launches = 0;
   bool timing = false;
@@ -152,6 +199,49 @@ void type_tables(int d, int n, double theta, std::vector<cd>& K, std::vector<cd>
   }
 }
 
+// 1D Galerkin rows P1^T A P1 of level l's assembled 1D stiffness (A = K) and
+// mass (A = M) on the coarse indices of level l-1, with P1 the tripartite
+// interpolation (weights 1 - |o|/3).  Entry [C][0..2] is the coupling of
+// coarse C with C-1, C, C+1 (interior C only; the rest stays zero).
+void galerkin_rows_1d(int n, const std::vector<uint8_t>& rot, double theta,
+                      std::vector<std::array<cd, 6>>& rows) {
+  const double h = 1.0 / n;
+  const cd hrot = h * cd(std::cos(theta), std::sin(theta));
+  auto hw = [&](int cell) { return rot[cell] ? hrot : cd(h); };
+  auto Kf = [&](int f, int g) -> cd {
+    if (g == f) return 1.0 / hw(f - 1) + 1.0 / hw(f);
+    if (g == f - 1) return -1.0 / hw(f - 1);
+    return -1.0 / hw(f);
+  };
+  auto Mf = [&](int f, int g) -> cd {
+    if (g == f) return (hw(f - 1) + hw(f)) / 3.0;
+    if (g == f - 1) return hw(f - 1) / 6.0;
+    return hw(f) / 6.0;
+  };
+  auto P1 = [](int f, int c) -> double {
+    const int o = f - 3 * c;
+    return (o < -2 || o > 2) ? 0.0 : 1.0 - std::abs(o) / 3.0;
+  };
+  const int nc = n / 3;
+  rows.assign(nc + 1, std::array<cd, 6>{});
+  // couplings to boundary neighbours are formed like the others (they
+  // multiply Dirichlet zeros), so they do not split row classes
+  for (int c = 1; c < nc; ++c)
+    for (int dl = -1; dl <= 1; ++dl) {
+      const int c2 = c + dl;
+      cd k(0), m(0);
+      for (int f = 3 * c - 2; f <= 3 * c + 2; ++f)
+        for (int g = f - 1; g <= f + 1; ++g) {
+          const double pf = P1(f, c), pg = P1(g, c2);
+          if (pf == 0.0 || pg == 0.0) continue;
+          k += pf * Kf(f, g) * pg;
+          m += pf * Mf(f, g) * pg;
+        }
+      rows[c][dl + 1] = k;
+      rows[c][dl + 4] = m;
+    }
+}
+
 template <typename R>
 std::vector<cplx<R>> to_dev_type(const std::vector<cd>& v) {
   std::vector<cplx<R>> o(v.size());
@@ -174,6 +264,18 @@ int dalloc(mg_ctx* c, Hier<R>& H, void** p, size_t bytes) {
 
 template <typename R>
 void free_hier(Hier<R>& H) {
+  for (auto& g : H.graphs) {
+    if (g.fine) cudaGraphExecDestroy(g.fine);
+    if (g.coarse) cudaGraphExecDestroy(g.coarse);
+  }
+  H.graphs.clear();
+  for (auto& cp : H.chains) {
+    cudaFree(cp.items);
+    cudaFree(cp.s2);
+    cudaFree(cp.pr);
+    cudaFree(cp.co);
+  }
+  H.chains.clear();
   for (void* p : H.allocs) cudaFree(p);
   H.allocs.clear();
   H.lev.clear();
@@ -225,6 +327,69 @@ int build_hier(mg_ctx* c, Hier<R>& H) {
     const int NT = (int)ipow(4, d), NS = (int)ipow(3, d);
     V.diag.resize(NT);
     for (int t = 0; t < NT; ++t) V.diag[t] = Hh[(size_t)t * NS + NS / 2];
+    V.realrow = 0;
+    for (int t = 0; t < NT && t < 32; ++t) {
+      bool re = true;
+      for (int k = 0; k < NS; ++k) re = re && Hh[(size_t)t * NS + k].imag() == 0.0;
+      if (re) V.realrow |= 1u << t;
+    }
+    if (std::is_same<R, double>::value && d == 2 && !H.varphi && V.n / 3 + 1 >= 200) {
+      // LPT order of the 8-coarse-cell tiles: interior vertices weighted by
+      // the cost of their stencil row (complex rows cost about twice)
+      const int nc = V.n / 3, tl = (nc + 8) / 8;
+      std::vector<std::pair<double, int>> cost;
+      for (int ty = 0; ty < tl; ++ty)
+        for (int tx = 0; tx < tl; ++tx) {
+          double w = 0;
+          for (int gy = 24 * ty; gy < std::min(24 * ty + 24, V.n); ++gy)
+            for (int gx = 24 * tx; gx < std::min(24 * tx + 24, V.n); ++gx) {
+              if (gx == 0 || gy == 0) continue;
+              const bool cpx = typ[gx] != 0 || typ[gy] != 0;
+              w += cpx ? 2.0 : 1.0;
+            }
+          cost.push_back({-(w + 50.0), ty * tl + tx});
+        }
+      std::stable_sort(cost.begin(), cost.end());
+      std::vector<int> order;
+      for (auto& pr : cost) order.push_back(pr.second);
+      if ((rc = dalloc(c, H, (void**)&V.order8, order.size() * sizeof(int))) != MG_OK) return rc;
+      MG_CUDA(c, cudaMemcpy(V.order8, order.data(), order.size() * sizeof(int), cudaMemcpyHostToDevice));
+    }
+    if (std::is_same<R, double>::value && d == 2 && !H.varphi && l > 1) {
+      // classes of 1D Galerkin rows along an axis (same on both axes)
+      std::vector<std::array<cd, 6>> rows;
+      galerkin_rows_1d(V.n, rot, c->theta, rows);
+      std::vector<std::array<cd, 6>> cls;
+      std::vector<uint8_t> gt(rows.size(), 0);
+      bool ok = true;
+      for (size_t ci = 1; ci + 1 < rows.size() && ok; ++ci) {
+        size_t k = 0;
+        while (k < cls.size() && cls[k] != rows[ci]) ++k;
+        if (k == cls.size()) {
+          if ((int)cls.size() == mg::kMaxGTypes) { ok = false; break; }
+          cls.push_back(rows[ci]);
+        }
+        gt[ci] = (uint8_t)k;
+      }
+      if (ok) {
+        const int G = mg::kMaxGTypes;
+        std::vector<cd> gc((size_t)G * G * 9, cd(0));
+        for (size_t gy = 0; gy < cls.size(); ++gy)
+          for (size_t gx = 0; gx < cls.size(); ++gx)
+            for (int k = 0; k < 9; ++k) {
+              const int dx = k % 3, dy = k / 3;
+              const auto& X = cls[gx];
+              const auto& Y = cls[gy];
+              gc[(gx + G * gy) * 9 + k] = X[dx] * Y[3 + dy] + X[3 + dx] * Y[dy] - phi0 * X[3 + dx] * Y[3 + dy];
+            }
+        auto gcd = to_dev_type<R>(gc);
+        if ((rc = dalloc(c, H, (void**)&V.gtyp, gt.size())) != MG_OK) return rc;
+        if ((rc = dalloc(c, H, (void**)&V.gcoef, gcd.size() * sizeof(cplx<R>))) != MG_OK) return rc;
+        MG_CUDA(c, cudaMemcpy(V.gtyp, gt.data(), gt.size(), cudaMemcpyHostToDevice));
+        MG_CUDA(c, cudaMemcpy(V.gcoef, gcd.data(), gcd.size() * sizeof(cplx<R>), cudaMemcpyHostToDevice));
+        V.gok = true;
+      }
+    }
     auto hH = to_dev_type<R>(Hh), hM = to_dev_type<R>(M);
     if ((rc = dalloc(c, H, (void**)&V.coefH, hH.size() * sizeof(cplx<R>))) != MG_OK) return rc;
     if ((rc = dalloc(c, H, (void**)&V.coefM, hM.size() * sizeof(cplx<R>))) != MG_OK) return rc;
@@ -284,14 +449,218 @@ cudaError_t launch_sweep(cudaStream_t s, mg::SweepArgs<R>& A) {
   for (int a = 0; a < D; ++a) nblk *= tiles;
   const size_t smem = mg::sweep_smem_bytes<R, D, TC>(A.varphi);
   auto kern = mg::sweep_kernel<R, D, TC, kThreads>;
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)mg::sweep_smem_bytes<R, D, TC>(1));
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
   kern<<<nblk, kThreads, smem, s>>>(A);
+  return cudaGetLastError();
+}
+
+template <int TC, int NTHR>
+cudaError_t launch_sweep2(cudaStream_t s, mg::Sweep2Args& A) {
+  const int nc = A.n / 3;
+  const int tiles = (nc + 1 + TC - 1) / TC;
+  A.tiles_x = tiles;
+  constexpr size_t smem = mg::Tile2<TC>::smem_bytes;
+  auto kern = mg::sweep2_kernel<TC, NTHR>;
+  kern<<<tiles * tiles, NTHR, smem, s>>>(A);
+  return cudaGetLastError();
+}
+
+// Shared-memory opt-in of the sweep kernels; done once per device before any
+// launch or stream capture.
+cudaError_t configure_kernels() {
+  static std::mutex mu;
+  static unsigned long long done = 0;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  if (dev < 64 && (done >> dev) & 1ull) return cudaSuccess;
+  auto set = [&](const void* f, size_t bytes) {
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  };
+  set((const void*)mg::sweep_kernel<double, 2, kTC2, kThreads>, mg::sweep_smem_bytes<double, 2, kTC2>(1));
+  set((const void*)mg::sweep_kernel<double, 3, kTC3, kThreads>, mg::sweep_smem_bytes<double, 3, kTC3>(1));
+  set((const void*)mg::sweep_kernel<float, 2, kTC2, kThreads>, mg::sweep_smem_bytes<float, 2, kTC2>(1));
+  set((const void*)mg::sweep_kernel<float, 3, kTC3, kThreads>, mg::sweep_smem_bytes<float, 3, kTC3>(1));
+  set((const void*)mg::sweep2_kernel<12, 256>, mg::Tile2<12>::smem_bytes);
+  set((const void*)mg::sweep2_kernel<4, 128>, mg::Tile2<4>::smem_bytes);
+  set((const void*)mg::sweep2_kernel<15, 256>, mg::Tile2<15>::smem_bytes);
+  set((const void*)mg::sweep2p_kernel<8, 256>, mg::Tile2<8>::smem_bytes);
+  set((const void*)mg::chain2_kernel<256>, mg::Tile2<4>::smem_bytes);
+  static_assert(mg::Tile2<2>::smem_bytes <= mg::Tile2<4>::smem_bytes, "chain smem");
+  if (e == cudaSuccess && dev < 64) done |= 1ull << dev;
+  return e;
+}
+
+// 2D FP64 levels with a constant shift: the Galerkin-row sweep (level 1 has
+// no coarser level and uses the same kernel with has_coarse = 0).
+cudaError_t sweep2(mg_ctx* c, Hier<double>& H, int l, bool fine, int hb, int hier, const cd& om) {
+  auto& V = H.lev[l];
+  mg::Sweep2Args A;
+  std::memset(&A, 0, sizeof(A));
+  A.n = V.n;
+  A.fine = fine ? 1 : 0;
+  A.has_coarse = l > 1 ? 1 : 0;
+  A.hb = hb;
+  A.hier = hier;
+  A.realrow = V.realrow;
+  A.u = fine ? V.u[H.cur] : V.u[0];
+  A.c = (fine && l > 1) ? H.lev[l - 1].corr : nullptr;
+  A.b = V.b;
+  A.out = fine ? V.u[1 - H.cur] : V.t;
+  if (l > 1) {
+    A.b_coarse = H.lev[l - 1].b;
+    A.u_coarse = H.lev[l - 1].u[0];
+    A.gtyp = V.gtyp;
+    A.gcoef = V.gcoef;
+  }
+  A.typ = V.typ;
+  A.coef = V.coefH;
+  A.realjac = 0;
+  for (size_t t = 0; t < V.diag.size() && t < 16; ++t) {
+    const cd q = om / V.diag[t];
+    A.omd[t] = cplx<double>{q.real(), q.imag()};
+    if (q.imag() == 0.0) A.realjac |= 1u << t;
+  }
+  A.partial = H.partial;
+  A.ticket = H.ticket;
+  A.norm2 = H.norm2;
+  const int nc = V.n / 3;
+  if (nc + 1 >= 200 && V.order8 != nullptr) {
+    const int tl = (nc + 8) / 8;
+    A.tiles_x = tl;
+    A.ntiles = tl * tl;
+    cudaError_t e = cudaMemsetAsync(c->chain_ctr + 32, 0, sizeof(unsigned), c->stream);
+    if (e != cudaSuccess) return e;
+    const int grid = std::min(A.ntiles, 152 * std::max(1, c->fine_bpsm));
+    mg::sweep2p_kernel<8, 256><<<grid, 256, mg::Tile2<8>::smem_bytes, c->stream>>>(
+        A, V.order8, c->chain_ctr + 32, c->tracing ? c->trace : nullptr);
+    return cudaGetLastError();
+  }
+  A.ntiles = ((nc + 4) / 4) * ((nc + 4) / 4);
+  return launch_sweep2<4, 128>(c->stream, A);
+}
+
+// Arguments of a coarse level's sweep tile in the persistent chain (TC = 4).
+mg::Sweep2Args sweep2_args(Hier<double>& H, int l, int hb, int hier, const cd& om, int TC) {
+  auto& V = H.lev[l];
+  mg::Sweep2Args A;
+  std::memset(&A, 0, sizeof(A));
+  A.n = V.n;
+  A.fine = 0;
+  A.has_coarse = l > 1 ? 1 : 0;
+  A.hb = hb;
+  A.hier = hier;
+  A.realrow = V.realrow;
+  A.u = V.u[0];
+  A.b = V.b;
+  A.out = V.t;
+  if (l > 1) {
+    A.b_coarse = H.lev[l - 1].b;
+    A.u_coarse = H.lev[l - 1].u[0];
+    A.gtyp = V.gtyp;
+    A.gcoef = V.gcoef;
+  }
+  A.typ = V.typ;
+  A.coef = V.coefH;
+  for (size_t t = 0; t < V.diag.size() && t < 16; ++t) {
+    const cd q = om / V.diag[t];
+    A.omd[t] = cplx<double>{q.real(), q.imag()};
+    if (q.imag() == 0.0) A.realjac |= 1u << t;
+  }
+  const int nc = V.n / 3;
+  A.tiles_x = (nc + TC) / TC;
+  A.ntiles = A.tiles_x * A.tiles_x;
+  return A;
+}
+
+// Item list of the coarse chain of one cycle on levels 1..s-1 of a 2D FP64
+// hierarchy: sweeps of levels s-1 .. 1, then prolongations of levels 2 .. s-1.
+int build_chain2(mg_ctx* c, Hier<double>& H, int s, int hb, int hier, const cplx<double>* omega,
+                 const std::vector<double>& key, typename Hier<double>::ChainPlan** out) {
+  for (auto& cp : H.chains)
+    if (cp.key == key) { *out = &cp; return MG_OK; }
+  std::vector<mg::ChainItem> items;
+  std::vector<mg::Sweep2Args> s2;
+  std::vector<mg::ProlongArgs> pr;
+  unsigned need = 0;
+  for (int l = s - 1; l >= 1; --l) {
+    const cplx<double> w = omega[l - 1 + (H.L - s)];
+    // small levels take 2-coarse-cell tiles so that a stage spreads over
+    // many SMs (its latency is set by one tile's FP64 work)
+    const int TC = (H.lev[l].n / 3 + 1) >= 60 ? 4 : 2;
+    s2.push_back(sweep2_args(H, l, hb, hier, cd(w.x, w.y), TC));
+    const int nt = s2.back().ntiles;
+    const int kind = TC == 4 ? mg::kItemSweep2 : mg::kItemSweep2s;
+    for (int t = 0; t < nt; ++t) items.push_back({kind, 0, (int)s2.size() - 1, t, need});
+    need += nt;
+  }
+  // corr_{s-1} = sum_l P^{s-1-l} t_l in two stages: corr_{s-2} directly from
+  // levels 1..s-2, then corr_{s-1} = t_{s-1} + P corr_{s-2}
+  std::vector<mg::CorrArgs> co;
+  const int top = s - 1;
+  if (top >= mg::kMaxChainLevels) return fail(c, MG_ERR_INVALID, "hierarchy too deep for the chain");
+  auto add_corr = [&](int tgt, int lo, const cplx<double>* base) {
+    mg::CorrArgs ca;
+    std::memset(&ca, 0, sizeof(ca));
+    ca.s = tgt;
+    ca.lo = lo;
+    for (int l = lo; l <= tgt; ++l) ca.t[l] = H.lev[l].t;
+    ca.base = base;
+    ca.out = H.lev[tgt].corr;
+    co.push_back(ca);
+    const int nch = (int)((H.lev[tgt].nv + mg::kCorrChunk - 1) / mg::kCorrChunk);
+    for (int t = 0; t < nch; ++t) items.push_back({mg::kItemCorr2, 0, (int)co.size() - 1, t, need});
+    need += nch;
+  };
+  if (top >= 3) {
+    add_corr(top - 1, 1, nullptr);
+    add_corr(top, top, H.lev[top - 1].corr);
+  } else if (top == 2) {
+    add_corr(2, 1, nullptr);
+  }
+  typename Hier<double>::ChainPlan cp;
+  cp.key = key;
+  cp.nitems = (int)items.size();
+  MG_CUDA(c, cudaMalloc(&cp.items, std::max<size_t>(1, items.size()) * sizeof(mg::ChainItem)));
+  MG_CUDA(c, cudaMalloc(&cp.s2, std::max<size_t>(1, s2.size()) * sizeof(mg::Sweep2Args)));
+  MG_CUDA(c, cudaMalloc(&cp.pr, std::max<size_t>(1, pr.size()) * sizeof(mg::ProlongArgs)));
+  MG_CUDA(c, cudaMalloc(&cp.co, std::max<size_t>(1, co.size()) * sizeof(mg::CorrArgs)));
+  if (!co.empty())
+    MG_CUDA(c, cudaMemcpy(cp.co, co.data(), co.size() * sizeof(mg::CorrArgs), cudaMemcpyHostToDevice));
+  if (!items.empty())
+    MG_CUDA(c, cudaMemcpy(cp.items, items.data(), items.size() * sizeof(mg::ChainItem), cudaMemcpyHostToDevice));
+  if (!s2.empty())
+    MG_CUDA(c, cudaMemcpy(cp.s2, s2.data(), s2.size() * sizeof(mg::Sweep2Args), cudaMemcpyHostToDevice));
+  if (!pr.empty())
+    MG_CUDA(c, cudaMemcpy(cp.pr, pr.data(), pr.size() * sizeof(mg::ProlongArgs), cudaMemcpyHostToDevice));
+  cp.grid = std::max(1, std::min(cp.nitems, 152 * std::min(MG_CHAIN_BPSM, std::max(1, c->chain_bpsm))));
+  if (H.chains.size() >= 32) {
+    cudaFree(H.chains.front().items);
+    cudaFree(H.chains.front().s2);
+    cudaFree(H.chains.front().pr);
+    cudaFree(H.chains.front().co);
+    H.chains.erase(H.chains.begin());
+  }
+  H.chains.push_back(cp);
+  *out = &H.chains.back();
+  return MG_OK;
+}
+
+cudaError_t launch_chain2(mg_ctx* c, const typename Hier<double>::ChainPlan& cp) {
+  cudaError_t e = cudaMemsetAsync(c->chain_ctr, 0, 2 * sizeof(unsigned), c->stream);
+  if (e != cudaSuccess) return e;
+  mg::ChainArgs A;
+  A.items = cp.items;
+  A.nitems = cp.nitems;
+  A.s2 = cp.s2;
+  A.pr = cp.pr;
+  A.co = cp.co;
+  A.head = c->chain_ctr;
+  A.done = c->chain_ctr + 1;
+  A.err = c->dev_err;
+  A.spin_limit = c->spin_limit;
+  A.trace = c->tracing ? c->trace + 4 * kTraceFine : nullptr;
+  mg::chain2_kernel<256><<<cp.grid, 256, mg::Tile2<4>::smem_bytes, c->stream>>>(A);
   return cudaGetLastError();
 }
 
@@ -300,6 +669,12 @@ cudaError_t sweep(mg_ctx* c, Hier<R>& H, int l, bool fine, int s_active, int hb,
                   const cplx<double>* omega) {
   auto& V = H.lev[l];
   ++c->launches;
+  if constexpr (std::is_same<R, double>::value) {
+    if (c->d == 2 && !H.varphi && (l == 1 || V.gok)) {
+      const cplx<double> w = omega[l - 1 + (H.L - s_active)];
+      return sweep2(c, H, l, fine, hb, hier, cd(w.x, w.y));
+    }
+  }
   mg::SweepArgs<R> A;
   std::memset(&A, 0, sizeof(A));
   A.n = V.n;
@@ -353,7 +728,76 @@ cudaError_t prolong(mg_ctx* c, Hier<R>& H, int l) {
   return cudaGetLastError();
 }
 
-// One cycle on levels 1..s (s = active finest level).
+// Kernels of one cycle on levels 1..s (s = active finest level), enqueued on
+// c->stream: the fine sweep (part 0) or the coarse chain (part 1).
+template <typename R>
+cudaError_t enqueue_cycle_part(mg_ctx* c, Hier<R>& H, int s, int hb, int hier,
+                               const cplx<double>* omega, int part, int* nkern) {
+  cudaError_t e = cudaSuccess;
+  *nkern = 0;
+  if (part == 2) {
+    int k0 = 0, k1 = 0;
+    e = enqueue_cycle_part(c, H, s, hb, hier, omega, 0, &k0);
+    if (e == cudaSuccess && s > 1) e = enqueue_cycle_part(c, H, s, hb, hier, omega, 1, &k1);
+    *nkern = k0 + k1;
+    return e;
+  }
+  if (part == 0) {
+    e = sweep(c, H, s, true, s, hb, hier, omega);
+    *nkern = 1;
+    return e;
+  }
+  if constexpr (std::is_same<R, double>::value) {
+    bool chain_ok = c->d == 2 && !H.varphi;
+    for (int l = 2; l < s && chain_ok; ++l) chain_ok = H.lev[l].gok;
+    if (chain_ok) {
+      std::vector<double> key = {(double)s, (double)hb, (double)hier};
+      for (int l = 0; l < H.L; ++l) {
+        key.push_back(omega[l].x);
+        key.push_back(omega[l].y);
+      }
+      typename Hier<double>::ChainPlan* cp = nullptr;
+      if (build_chain2(c, H, s, hb, hier, omega, key, &cp) != MG_OK) return cudaErrorUnknown;
+      *nkern = 1;
+      ++c->launches;
+      return launch_chain2(c, *cp);
+    }
+  }
+  for (int l = s - 1; l >= 1 && e == cudaSuccess; --l, ++*nkern) e = sweep(c, H, l, false, s, hb, hier, omega);
+  for (int l = 2; l <= s - 1 && e == cudaSuccess; ++l, ++*nkern) e = prolong(c, H, l);
+  return e;
+}
+
+// Captures one part of the cycle as a graph on the private capture stream.
+template <typename R>
+cudaError_t capture_part(mg_ctx* c, Hier<R>& H, int s, int hb, int hier, const cplx<double>* omega,
+                         int part, cudaGraphExec_t* exec, int* nkern) {
+  *exec = nullptr;
+  cudaStream_t user = c->stream;
+  c->stream = c->cap_stream;
+  const long long before = c->launches;
+  cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+  cudaError_t ek = cudaSuccess;
+  if (e == cudaSuccess) ek = enqueue_cycle_part(c, H, s, hb, hier, omega, part, nkern);
+  cudaGraph_t g = nullptr;
+  cudaError_t ee = e == cudaSuccess ? cudaStreamEndCapture(c->cap_stream, &g) : e;
+  c->stream = user;
+  c->launches = before;  // kernels count when the graph runs
+  if (e == cudaSuccess) e = ek != cudaSuccess ? ek : ee;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(exec, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    if (*exec) cudaGraphExecDestroy(*exec);
+    *exec = nullptr;
+    cudaGetLastError();
+  }
+  return e;
+}
+
+// One cycle on levels 1..s (s = active finest level).  The two parts run as
+// captured CUDA graphs (captured on first use per stage, variant, transfer,
+// relaxation factors and buffer parity); with timing on, an event pair
+// brackets the fine-sweep graph.
 template <typename R>
 int run_cycle(mg_ctx* c, Hier<R>& H, int s, int hb, int hier, const cplx<double>* omega) {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -368,12 +812,74 @@ int run_cycle(mg_ctx* c, Hier<R>& H, int s, int hb, int hier, const cplx<double>
     e0 = c->ev[c->ev_used];
     e1 = c->ev[c->ev_used + 1];
     c->ev_used += 2;
-    cudaEventRecord(e0, c->stream);
   }
-  cudaError_t e = sweep(c, H, s, true, s, hb, hier, omega);
-  if (c->timing && e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
-  for (int l = s - 1; l >= 1 && e == cudaSuccess; --l) e = sweep(c, H, l, false, s, hb, hier, omega);
-  for (int l = 2; l <= s - 1 && e == cudaSuccess; ++l) e = prolong(c, H, l);
+  typename Hier<R>::GraphEntry* ge = nullptr;
+  if (c->use_graphs) {
+    std::vector<double> key = {(double)s, (double)hb, (double)hier, (double)H.cur, c->timing ? 1.0 : 0.0};
+    for (int l = 0; l < H.L; ++l) {
+      key.push_back(omega[l].x);
+      key.push_back(omega[l].y);
+    }
+    for (auto& g : H.graphs)
+      if (g.key == key) { ge = &g; break; }
+    if (ge == nullptr) {
+      if constexpr (std::is_same<R, double>::value) {
+        // plans allocate device tables: build them before capturing
+        if (c->d == 2 && !H.varphi && s > 1) {
+          std::vector<double> ck = {(double)s, (double)hb, (double)hier};
+          for (int l = 0; l < H.L; ++l) {
+            ck.push_back(omega[l].x);
+            ck.push_back(omega[l].y);
+          }
+          bool ok = true;
+          for (int l = 2; l < s && ok; ++l) ok = H.lev[l].gok;
+          typename Hier<double>::ChainPlan* cp = nullptr;
+          if (ok && build_chain2(c, H, s, hb, hier, omega, ck, &cp) != MG_OK) return MG_ERR_OOM;
+        }
+      }
+      typename Hier<R>::GraphEntry ne;
+      ne.key = key;
+      cudaError_t e;
+      if (c->timing) {
+        e = capture_part(c, H, s, hb, hier, omega, 0, &ne.fine, &ne.nfine);
+        if (e == cudaSuccess && s > 1) e = capture_part(c, H, s, hb, hier, omega, 1, &ne.coarse, &ne.ncoarse);
+      } else {
+        e = capture_part(c, H, s, hb, hier, omega, 2, &ne.fine, &ne.nfine);  // whole cycle
+      }
+      if (e != cudaSuccess) {
+        if (ne.fine) cudaGraphExecDestroy(ne.fine);
+        c->use_graphs = false;  // run this context's cycles as plain launches
+      } else {
+        if (H.graphs.size() >= 32) {
+          cudaGraphExecDestroy(H.graphs.front().fine);
+          if (H.graphs.front().coarse) cudaGraphExecDestroy(H.graphs.front().coarse);
+          H.graphs.erase(H.graphs.begin());
+        }
+        H.graphs.push_back(ne);
+        ge = &H.graphs.back();
+      }
+    }
+  }
+  cudaError_t e = cudaSuccess;
+  int nk = 0;
+  if (e0) e = cudaEventRecord(e0, c->stream);
+  if (e == cudaSuccess) {
+    if (ge) {
+      e = cudaGraphLaunch(ge->fine, c->stream);
+      c->launches += ge->nfine;
+    } else {
+      e = enqueue_cycle_part(c, H, s, hb, hier, omega, 0, &nk);
+    }
+  }
+  if (e == cudaSuccess && e1) e = cudaEventRecord(e1, c->stream);
+  if (e == cudaSuccess && s > 1 && !(ge && ge->coarse == nullptr)) {
+    if (ge) {
+      e = cudaGraphLaunch(ge->coarse, c->stream);
+      c->launches += ge->ncoarse;
+    } else {
+      e = enqueue_cycle_part(c, H, s, hb, hier, omega, 1, &nk);
+    }
+  }
   if (e != cudaSuccess) return fail(c, MG_ERR_CUDA, std::string("cycle launch: ") + cudaGetErrorString(e));
   H.cur = 1 - H.cur;
   return MG_OK;
@@ -430,6 +936,20 @@ int decode_variant(mg_ctx* c, int variant, int transfer, int* hb, int* hier) {
   return MG_OK;
 }
 
+// Reads and clears the sticky timeout flag of the bounded device waits
+// (synchronising).
+int check_timeout(mg_ctx* c) {
+  unsigned f = 0;
+  MG_CUDA(c, cudaMemcpyAsync(c->host_norm + 2, c->dev_err, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+  MG_CUDA(c, cudaStreamSynchronize(c->stream));
+  std::memcpy(&f, c->host_norm + 2, sizeof(unsigned));
+  if (f != 0) {
+    MG_CUDA(c, cudaMemsetAsync(c->dev_err, 0, sizeof(unsigned), c->stream));
+    return fail(c, MG_ERR_TIMEOUT, "a bounded device-side wait gave up; results of the affected cycles are invalid");
+  }
+  return MG_OK;
+}
+
 // ||b_s - H_s u_s|| of the materialised fine solution of level s (FP64),
 // synchronising.
 int fine_residual(mg_ctx* c, int s, double* out) {
@@ -442,7 +962,7 @@ int fine_residual(mg_ctx* c, int s, double* out) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return fail(c, MG_ERR_CUDA, std::string("residual: ") + cudaGetErrorString(e));
   *out = std::sqrt(*c->host_norm);
-  return MG_OK;
+  return check_timeout(c);
 }
 
 int ensure_r0(mg_ctx* c) {
@@ -503,6 +1023,14 @@ int mg_create(int d, int depth, const double* k2_field, double theta, double lay
     if (e == cudaSuccess) e = cudaMemset(c->f_dev, 0, nvf * sizeof(cplx<double>));
     if (e == cudaSuccess) e = cudaMalloc(&c->scratch, nvf * sizeof(cplx<double>));
     if (e == cudaSuccess) e = cudaMallocHost(&c->host_norm, 4 * sizeof(double));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = configure_kernels();
+    if (e == cudaSuccess) e = cudaMalloc(&c->chain_ctr, 64 * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc(&c->dev_err, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(c->dev_err, 0, sizeof(unsigned));
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->chain_bpsm, mg::chain2_kernel<256>, 256,
+                                                         mg::Tile2<4>::smem_bytes);
     if (e != cudaSuccess) rc = fail(c, MG_ERR_OOM, cudaGetErrorString(e));
   }
   if (rc != MG_OK) {
@@ -517,6 +1045,10 @@ int mg_create(int d, int depth, const double* k2_field, double theta, double lay
 void mg_destroy(mg_ctx* c) {
   if (c == nullptr) return;
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->trace) cudaFree(c->trace);
+  if (c->chain_ctr) cudaFree(c->chain_ctr);
+  if (c->dev_err) cudaFree(c->dev_err);
   free_hier(c->h64);
   free_hier(c->h32);
   if (c->f_dev) cudaFree(c->f_dev);
@@ -660,6 +1192,7 @@ int mg_solve(mg_ctx* c, int variant, const mg_c128* omega, int transfer, double 
       }
       MG_CUDA(c, cudaMemcpyAsync(c->host_norm, c->h64.norm2, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
       MG_CUDA(c, cudaStreamSynchronize(c->stream));
+      if ((rc = check_timeout(c)) != MG_OK) return finish(rc);
       const double prev = std::sqrt(*c->host_norm) / (c->r0 > 0 ? c->r0 : 1.0);
       if (diverged(prev) || prev <= tol || done >= max_cycles) {
         double r;
@@ -770,6 +1303,35 @@ int mg_omega_scheme(int scheme, mg_c128 omega_s, int depth, int iter_n, int l_gr
   return MG_OK;
 }
 
+int mg_set_trace(mg_ctx* c, int enable) {
+  if (check_ctx(c)) return MG_ERR_INVALID;
+  if (enable && c->trace == nullptr)
+    MG_CUDA(c, cudaMalloc(&c->trace, 4ull * (kTraceFine + kTraceChain) * sizeof(unsigned long long)));
+  if (enable) MG_CUDA(c, cudaMemset(c->trace, 0, 4ull * (kTraceFine + kTraceChain) * sizeof(unsigned long long)));
+  // captured cycles bake the trace pointer: drop them when the switch flips
+  if ((enable != 0) != c->tracing) {
+    for (auto& g : c->h64.graphs) {
+      if (g.fine) cudaGraphExecDestroy(g.fine);
+      if (g.coarse) cudaGraphExecDestroy(g.coarse);
+    }
+    c->h64.graphs.clear();
+  }
+  c->tracing = enable != 0;
+  return MG_OK;
+}
+
+int mg_get_trace(mg_ctx* c, unsigned long long* out, int fine_slots, int chain_slots) {
+  if (check_ctx(c)) return MG_ERR_INVALID;
+  if (out == nullptr || c->trace == nullptr || fine_slots < 0 || chain_slots < 0 ||
+      fine_slots > kTraceFine || chain_slots > kTraceChain)
+    return fail(c, MG_ERR_INVALID, "tracing is off or slot counts out of range");
+  MG_CUDA(c, cudaStreamSynchronize(c->stream));
+  MG_CUDA(c, cudaMemcpy(out, c->trace, 4ull * fine_slots * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+  MG_CUDA(c, cudaMemcpy(out + 4ull * fine_slots, c->trace + 4ull * kTraceFine,
+                        4ull * chain_slots * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+  return MG_OK;
+}
+
 int mg_set_timing(mg_ctx* c, int enable) {
   if (check_ctx(c)) return MG_ERR_INVALID;
   c->timing = enable != 0;
@@ -785,6 +1347,8 @@ int mg_get_stats(mg_ctx* c, long long* launches, int* fine_sweeps, double* fine_
     MG_CUDA(c, cudaEventElapsedTime(&t, c->ev[i], c->ev[i + 1]));
     ms += t;
   }
+  int trc = check_timeout(c);
+  if (trc != MG_OK) return trc;
   if (launches) *launches = c->launches;
   if (fine_sweeps) *fine_sweeps = (int)(c->ev_used / 2);
   if (fine_ms) *fine_ms = ms;

@@ -150,6 +150,44 @@ __device__ __forceinline__ void block_norm_finish(double v, double* s_red, doubl
   }
 }
 
+// Same reduction for tiles processed by any block: partial slot `tile`, the
+// last of `ntiles` tiles to finish sums all partials in a fixed order.
+template <int NTHR>
+__device__ __forceinline__ void block_norm_finish_tile(double v, double* s_red, double* partial,
+                                                       unsigned* ticket, double* norm2, int tile,
+                                                       int ntiles) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();  // s_red may still be read by a previous item
+  if (lane == 0) s_red[warp] = v;
+  __syncthreads();
+  __shared__ int s_last_t;
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int w = 0; w < NTHR / 32; ++w) t += s_red[w];
+    __stcg(partial + tile, t);
+    __threadfence();
+    unsigned k = atomicAdd(ticket, 1u);
+    s_last_t = (k == (unsigned)(ntiles - 1));
+  }
+  __syncthreads();
+  if (s_last_t) {
+    __threadfence();
+    double t = 0;
+    for (int i = threadIdx.x; i < ntiles; i += NTHR) t += __ldcg(partial + i);
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    __syncthreads();
+    if (lane == 0) s_red[warp] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0;
+      for (int w = 0; w < NTHR / 32; ++w) s += s_red[w];
+      __stcg(norm2, s);
+      atomicExch(ticket, 0u);
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Shared-memory tile of one sweep.  The block owns coarse vertices
 // [C0, C0+TC) per axis, i.e. fine vertices [x0, x0+F), x0 = 3 C0, F = 3 TC.

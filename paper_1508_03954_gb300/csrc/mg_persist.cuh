@@ -1,0 +1,253 @@
+// mg_persist.cuh -- persistent dataflow launch for the coarse part of a
+// cycle (sm_103a).
+//
+// After the fine sweep, a cycle is a chain of small steps: the sweeps of
+// levels L-1 .. 1 (each needs the whole finer level's restriction) and the
+// prolongations corr_l = T_l du_l + P corr_{l-1} for l = 2 .. L-1 (each needs
+// the coarser one).  On GB300 each of these is far too small to fill the
+// machine and one launch per step costs more than the step.  Here one launch
+// runs the whole chain (and, for batches, the chains of many problems): every
+// block repeatedly takes the next work item (stage, tile) from a queue in
+// topological order and, before working on it, waits until its problem's
+// completion counter shows that every item of the earlier stages is done.
+// Items are taken in index order and only wait on items with smaller
+// indices, which running blocks already hold, so the scheme cannot deadlock
+// and needs no cooperative launch.  Every wait is bounded: when the bound
+// runs out the block sets an error flag and carries on, so a launch always
+// ends and the host reports MG_ERR_TIMEOUT.
+#pragma once
+#include "mg_sweep2d.cuh"
+
+#ifndef MG_BACKOFF_MAX_NS
+#define MG_BACKOFF_MAX_NS 256
+#endif
+
+namespace mg {
+
+enum : int { kItemSweep2 = 0, kItemProlong2 = 1, kItemCorr2 = 2, kItemSweep2s = 3 };
+
+struct ChainItem {
+  int kind;       // kItemSweep2 / kItemProlong2
+  int prob;       // problem index (completion counter)
+  int args;       // index into the argument table of its kind
+  int tile;       // tile (sweep) or chunk (prolongation)
+  unsigned need;  // items of this problem that must be complete first
+};
+
+struct ProlongArgs {
+  int n;                       // cells per axis of the level
+  const cplx<double>* t;       // T du of the level
+  const cplx<double>* cc;      // corr of the next coarser level
+  cplx<double>* out;           // corr of the level
+};
+
+constexpr int kProlongChunk = 2048;  // vertices per prolongation item
+
+// corr_s = t_s + sum_{l=lo..s-1} P^{s-l} t_l + P^{s-lo+1} base on level s,
+// evaluated at every vertex by direct d-linear interpolation from each
+// coarser level: on nested d-linear spaces P^k is exactly the interpolation
+// over the 3^k-refined cell.  base is corr_{lo-1} (or null).
+constexpr int kMaxChainLevels = 12;
+struct CorrArgs {
+  int s, lo;                               // target level (3^s cells), first level summed
+  const cplx<double>* t[kMaxChainLevels];  // t[l] for l = lo..s (index l)
+  const cplx<double>* base;                // corr_{lo-1} or null
+  cplx<double>* out;                       // corr_s
+};
+constexpr int kCorrChunk = 256;          // vertices per item
+
+struct ChainArgs {
+  const ChainItem* items;
+  int nitems;
+  const Sweep2Args* s2;
+  const ProlongArgs* pr;
+  const CorrArgs* co;
+  unsigned* head;        // queue head, zero at launch
+  unsigned* done;        // per-problem completion counters, zero at launch
+  unsigned* err;         // set when a bounded wait gave up
+  unsigned spin_limit;   // polls before giving up
+  unsigned long long* trace;  // optional: per item {taken, ready, done, sm} (ns, globaltimer)
+};
+
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ unsigned smid() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %smid;" : "=r"(r));
+  return r;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// corr_l = t_l + P corr_{l-1} on vertices [chunk*kProlongChunk, ...) of a 2D level
+template <int NTHR>
+__device__ __forceinline__ void prolong2_chunk(const ProlongArgs& A, int chunk) {
+  const int n = A.n, N = n + 1, Nc = n / 3 + 1;
+  const long long total = (long long)N * N;
+  const long long beg = (long long)chunk * kProlongChunk;
+  for (long long i = beg + threadIdx.x; i < beg + kProlongChunk && i < total; i += NTHR) {
+    const int gx = (int)(i % N), gy = (int)(i / N);
+    cplx<double> v = cz<double>();
+    if (gx > 0 && gx < n && gy > 0 && gy < n) {
+      v = ldcg(A.t + i);
+      const int cx = gx / 3, cy = gy / 3, ox = gx % 3, oy = gy % 3;
+      const cplx<double>* cp = A.cc + (long long)cy * Nc + cx;
+      const cplx<double> a = lerp2(w0(ox), ldcg(cp), w1(ox), ldcg(cp + (ox ? 1 : 0)));
+      const cplx<double> b = oy ? lerp2(w0(ox), ldcg(cp + Nc), w1(ox), ldcg(cp + Nc + (ox ? 1 : 0)))
+                                : cz<double>();
+      v = lerp2acc(v, w0(oy), a, w1(oy), b);
+    }
+    A.out[i] = v;
+  }
+}
+
+// 1/3^k for k = 0..12 (interpolation weights without FP64 division)
+__device__ __forceinline__ double inv_pow3(int k) {
+  double r = 1.0;
+  for (int i = 0; i < k; ++i) r *= (1.0 / 3.0);
+  return r;
+}
+
+template <int NTHR>
+__device__ __forceinline__ void corr2_chunk(const CorrArgs& A, int chunk) {
+  const int s = A.s;
+  int n = 1;
+  for (int k = 0; k < s; ++k) n *= 3;
+  const int N = n + 1;
+  const long long total = (long long)N * N;
+  for (long long i = (long long)chunk * kCorrChunk + threadIdx.x;
+       i < (long long)(chunk + 1) * kCorrChunk && i < total; i += NTHR) {
+    const int gx = (int)(i % N), gy = (int)(i / N);
+    cplx<double> v = cz<double>();
+    if (gx > 0 && gx < n && gy > 0 && gy < n) {
+      v = ldcg(A.t[s] + i);
+      int f = 1, k = 0;  // f = 3^(s-l)
+      for (int l = s - 1; l >= A.lo - 1 && l >= 0; --l) {
+        f *= 3;
+        ++k;
+        const cplx<double>* src = l >= A.lo ? A.t[l] : A.base;
+        if (src == nullptr) break;
+        const int nl = n / f, Nl = nl + 1;
+        const int cx = gx / f, cy = gy / f, ox = gx - cx * f, oy = gy - cy * f;
+        const double ik = inv_pow3(k);
+        const double wx1 = (double)ox * ik, wy1 = (double)oy * ik;
+        const double wx0 = 1.0 - wx1, wy0 = 1.0 - wy1;
+        const cplx<double>* tp = src + (long long)cy * Nl + cx;
+        const cplx<double> a = lerp2(wx0, ldcg(tp), wx1, ldcg(tp + (ox ? 1 : 0)));
+        const cplx<double> b = oy ? lerp2(wx0, ldcg(tp + Nl), wx1, ldcg(tp + Nl + (ox ? 1 : 0)))
+                                  : cz<double>();
+        v = lerp2acc(v, wy0, a, wy1, b);
+      }
+    }
+    A.out[i] = v;
+  }
+}
+
+// Copies a small argument struct from global to shared memory (the tile code
+// then reads its fields with shared loads instead of re-reading global
+// memory after every store).
+template <typename T, int NTHR>
+__device__ __forceinline__ void copy_args(T* dst, const T* src) {
+  static_assert(sizeof(T) % 4 == 0, "4-byte granularity");
+  const unsigned* s = reinterpret_cast<const unsigned*>(src);
+  unsigned* d = reinterpret_cast<unsigned*>(dst);
+  for (int i = threadIdx.x; i < (int)(sizeof(T) / 4); i += NTHR) d[i] = __ldcg(s + i);
+}
+
+// Bounded wait of thread 0 until *ctr >= need, polling with exponential
+// backoff (64 .. 256 ns) so that waiting blocks do not crowd the L2 slice
+// that holds the counter.
+__device__ __forceinline__ void wait_counter(const unsigned* ctr, unsigned need, unsigned spin_limit,
+                                             unsigned* err) {
+  unsigned spins = 0, ns = 64;
+  while (ld_acquire_u32(ctr) < need) {
+    if (++spins > spin_limit) {
+      atomicOr(err, 1u);
+      return;
+    }
+    __nanosleep(ns);
+    if (ns < MG_BACKOFF_MAX_NS) ns <<= 1;
+  }
+}
+
+template <int NTHR>
+__global__ void __launch_bounds__(NTHR) chain2_kernel(const ChainArgs A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double s_red[NTHR / 32];
+  __shared__ int s_item;
+  __shared__ __align__(16) Sweep2Args s_a;
+  __shared__ __align__(16) ProlongArgs s_p;
+  __shared__ __align__(16) CorrArgs s_co;
+  while (true) {
+    if (threadIdx.x == 0) s_item = (int)atomicAdd(A.head, 1u);
+    __syncthreads();
+    const int i = s_item;
+    if (i >= A.nitems) break;
+    const ChainItem it = A.items[i];
+    unsigned long long t0 = 0, t1 = 0;
+    if (A.trace != nullptr && threadIdx.x == 0) t0 = gtimer();
+    if (it.kind == kItemSweep2 || it.kind == kItemSweep2s) copy_args<Sweep2Args, NTHR>(&s_a, A.s2 + it.args);
+    else if (it.kind == kItemProlong2) copy_args<ProlongArgs, NTHR>(&s_p, A.pr + it.args);
+    else copy_args<CorrArgs, NTHR>(&s_co, A.co + it.args);
+    if (threadIdx.x == 0 && it.need > 0) wait_counter(A.done + it.prob, it.need, A.spin_limit, A.err);
+    if (A.trace != nullptr && threadIdx.x == 0) t1 = gtimer();
+    __syncthreads();
+    if (it.kind == kItemSweep2) {
+      sweep2_tile<4, NTHR>(s_a, it.tile, smem_raw, s_red);
+    } else if (it.kind == kItemSweep2s) {
+      sweep2_tile<2, NTHR>(s_a, it.tile, smem_raw, s_red);
+    } else if (it.kind == kItemProlong2) {
+      prolong2_chunk<NTHR>(s_p, it.tile);
+    } else {
+      corr2_chunk<NTHR>(s_co, it.tile);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicAdd(A.done + it.prob, 1u);
+      if (A.trace != nullptr) {
+        unsigned long long* tr = A.trace + 4ull * i;
+        tr[0] = t0;
+        tr[1] = t1;
+        tr[2] = gtimer();
+        tr[3] = smid();
+      }
+    }
+  }
+}
+
+// Finest-level sweep as a persistent launch: blocks take tiles from a queue
+// ordered by decreasing cost (tiles with complex rows first), so that the
+// uneven cost of scaling-layer tiles evens out over the SMs.
+template <int TC, int NTHR>
+__global__ void __launch_bounds__(NTHR) sweep2p_kernel(const Sweep2Args A, const int* order,
+                                                       unsigned* head, unsigned long long* trace) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double s_red[NTHR / 32];
+  __shared__ int s_k;
+  while (true) {
+    if (threadIdx.x == 0) s_k = (int)atomicAdd(head, 1u);
+    __syncthreads();
+    const int k = s_k;
+    if (k >= A.ntiles) break;
+    const unsigned long long t0 = (trace != nullptr && threadIdx.x == 0) ? gtimer() : 0ull;
+    sweep2_tile<TC, NTHR>(A, order[k], smem_raw, s_red);
+    __syncthreads();
+    if (trace != nullptr && threadIdx.x == 0) {
+      unsigned long long* tr = trace + 4ull * k;
+      tr[0] = t0;
+      tr[1] = t0;
+      tr[2] = gtimer();
+      tr[3] = smid();
+    }
+  }
+}
+
+}  // namespace mg

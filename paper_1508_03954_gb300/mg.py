@@ -28,7 +28,7 @@ STATUS_NAMES = {0: "MG_OK", 1: "MG_ERR_INVALID", 2: "MG_ERR_CUDA", 3: "MG_ERR_OO
 EXPORTS = ["mg_create", "mg_destroy", "mg_set_stream", "mg_set_rhs", "mg_set_solution",
            "mg_get_solution", "mg_cycle", "mg_residual_norm", "mg_solve", "mg_set_precision",
            "mg_fmg", "mg_omega_scheme", "mg_get_level", "mg_set_timing", "mg_get_stats",
-           "mg_residual_noalloc", "mg_last_error"]
+           "mg_set_trace", "mg_get_trace", "mg_residual_noalloc", "mg_last_error"]
 
 
 class MgC128(ctypes.Structure):
@@ -78,6 +78,8 @@ def load(path: str | None = None):
         "mg_get_stats": (ip, [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ip),
                               ctypes.POINTER(dp)]),
         "mg_residual_noalloc": (ip, [vp, vp, vp, vp, vp]),
+        "mg_set_trace": (ip, [vp, ip]),
+        "mg_get_trace": (ip, [vp, vp, ip, ip]),
         "mg_last_error": (ctypes.c_char_p, [vp]),
     }
     for name, (res, args) in sig.items():
@@ -215,6 +217,16 @@ class Solver:
         self._check(self._L.mg_get_stats(self._h, ctypes.byref(n), ctypes.byref(k), ctypes.byref(ms)),
                     "mg_get_stats")
         return n.value, k.value, ms.value
+
+    def set_trace(self, enable):
+        self._check(self._L.mg_set_trace(self._h, 1 if enable else 0), "mg_set_trace")
+
+    def get_trace(self, fine_slots, chain_slots):
+        """(fine, chain) uint64 arrays of shape (slots, 4): taken, ready, done (ns), SM."""
+        out = np.zeros((fine_slots + chain_slots, 4), dtype=np.uint64)
+        self._check(self._L.mg_get_trace(self._h, out.ctypes.data_as(ctypes.c_void_p), fine_slots,
+                                         chain_slots), "mg_get_trace")
+        return out[:fine_slots], out[fine_slots:]
 
     def residual_noalloc(self, u, b, r, norm2):
         """r = b - H_L u and |r|^2 into caller-owned device tensors, using

@@ -200,3 +200,13 @@ def test_precision_form_reaches_fp64_tolerance():
     assert st == mg.MG_OK and rel <= 1e-8
     r = o.residual(g.get_solution())
     assert np.linalg.norm(r) <= 1e-8 * np.linalg.norm(o.b)
+
+
+@pytest.mark.parametrize("var", VARIANTS, ids=["add", "hb", "bpx", "hb-hier"])
+def test_depth6_every_variant(var):
+    """Full-size 2D level (the 12-coarse-cell tiles of the FP64 sweep), 4-cell
+    layer (more Galerkin row classes), complex relaxation factors."""
+    c = W.config2()
+    g, o = pair(2, 6, c["k2"], c["theta"], 4 / 27, c["f"], W.random_complex(2, 6, 77))
+    omega = np.array([0.6 - 0.02j * l for l in range(6)])
+    run_iterates(g, o, var, omega, 1)
