@@ -149,6 +149,38 @@ int mg_omega_scheme(int scheme, mg_c128 omega_s, int depth, int iter_n, int l_gr
  * when out is a host pointer. */
 int mg_get_level(mg_ctx* ctx, int level, int which, mg_c128* out, int on_device);
 
+/* ---- adjoint (far-field functional) form; not in the paper ----------------
+ * Forward problem H(V) u = M f with k^2 = E - V; functional
+ * s = sum_q w_q u(x_q) (d-linear samples of the fine solution), J = |s|^2. */
+
+/* Replaces the fine k^2 field (host, fine-vertex layout) of a context that
+ * was created with a varying field; coarse levels and cell shifts follow.
+ * MG_ERR_INVALID for contexts created with a constant field. */
+int mg_set_k2(mg_ctx* ctx, const double* k2_field);
+
+/* Sets the fine right-hand side vector b_L itself (host or device), instead
+ * of M f; boundary entries are ignored. */
+int mg_set_rhs_vector(mg_ctx* ctx, const mg_c128* b, int on_device);
+
+/* s = sum_q w_q u(x_q) of the current fine solution; xyz: host, npts points
+ * of d coordinates in [0,1] (x first); w: host weights; out: host.
+ * Synchronising. */
+int mg_sample(mg_ctx* ctx, int npts, const double* xyz, const mg_c128* w, mg_c128* out);
+
+/* Sets b_L = a with a_v = sum_q w_q psi_v(x_q): the adjoint right-hand side
+ * of the sampled functional (the transpose of mg_sample; unconjugated). */
+int mg_set_rhs_samples(mg_ctx* ctx, int npts, const double* xyz, const mg_c128* w);
+
+/* Gradients of J = |s|^2 from the forward solution u and the adjoint
+ * solution lambda of H lambda = a (device arrays, fine layout; H is
+ * complex-symmetric, so H^T = H):
+ *   dJdV[v] = 2 Re( conj(s) * (-2^-d) sum_{cells c at v} lambda_c^T M_c u_c )
+ *   dJdf[v] = 2 Re( conj(s) * (M lambda)_v )          (real nodal f)
+ * for every fine vertex (boundary included), device outputs (either may be
+ * NULL).  Asynchronous. */
+int mg_adjoint_grad(mg_ctx* ctx, const mg_c128* u, const mg_c128* lambda, mg_c128 s,
+                    double* dJdV, double* dJdf);
+
 /* Instrumentation.  mg_set_timing(ctx, 1) makes every later cycle record a
  * CUDA event pair around its finest-level sweep kernel on the context's
  * stream.  mg_get_stats synchronises the stream and returns, since the last

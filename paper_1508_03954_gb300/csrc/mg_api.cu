@@ -18,6 +18,8 @@
 #include "mg_kernels.cuh"
 #include "mg_sweep2d.cuh"
 #include "mg_persist.cuh"
+#include "mg_adjoint.cuh"
+#include <map>
 
 using mg::cplx;
 using cd = std::complex<double>;
@@ -282,6 +284,31 @@ void free_hier(Hier<R>& H) {
   H.ready = false;
 }
 
+// Cell shift of level l: mean of the 2^d vertex values of k^2 sampled on the
+// level's own vertices (injection of the fine field).
+template <typename R>
+std::vector<R> cell_shift(const mg_ctx* c, int l) {
+  const int d = c->d, n = (int)ipow(3, l);
+  const long long stride = ipow(3, c->L - l), NL = ipow(3, c->L) + 1;
+  const size_t ncell = (size_t)ipow(n, d);
+  std::vector<R> phic(ncell);
+  for (size_t ci = 0; ci < ncell; ++ci) {
+    long long q[3] = {0, 0, 0}, r = (long long)ci;
+    for (int a = 0; a < d; ++a) { q[a] = r % n; r /= n; }
+    double acc = 0;
+    for (int e = 0; e < (1 << d); ++e) {
+      long long gi = 0, st = 1;
+      for (int a = 0; a < d; ++a) {
+        gi += (q[a] + ((e >> a) & 1)) * stride * st;
+        st *= NL;
+      }
+      acc += c->k2[(size_t)gi];
+    }
+    phic[ci] = (R)(acc / (double)(1 << d));
+  }
+  return phic;
+}
+
 // Builds the arrays and tables of one precision.
 template <typename R>
 int build_hier(mg_ctx* c, Hier<R>& H) {
@@ -396,27 +423,13 @@ int build_hier(mg_ctx* c, Hier<R>& H) {
     MG_CUDA(c, cudaMemcpy(V.coefH, hH.data(), hH.size() * sizeof(cplx<R>), cudaMemcpyHostToDevice));
     MG_CUDA(c, cudaMemcpy(V.coefM, hM.data(), hM.size() * sizeof(cplx<R>), cudaMemcpyHostToDevice));
     if (H.varphi) {
-      // cell shift: mean of the 2^d vertex values of k^2 sampled on level l
-      const long long stride = ipow(3, L - l);
-      const long long NL = nL + 1;
       const size_t ncell = (size_t)ipow(V.n, d);
-      std::vector<R> phic(ncell);
-      for (size_t ci = 0; ci < ncell; ++ci) {
-        long long q[3] = {0, 0, 0}, r = (long long)ci;
-        for (int a = 0; a < d; ++a) { q[a] = r % V.n; r /= V.n; }
-        double s = 0;
-        for (int e = 0; e < (1 << d); ++e) {
-          long long gi = 0, st = 1;
-          for (int a = 0; a < d; ++a) {
-            gi += (q[a] + ((e >> a) & 1)) * stride * st;
-            st *= NL;
-          }
-          s += c->k2[(size_t)gi];
-        }
-        phic[ci] = (R)(s / (double)(1 << d));
-      }
+      std::vector<R> phic = cell_shift<R>(c, l);
       if ((rc = dalloc(c, H, (void**)&V.phic, ncell * sizeof(R))) != MG_OK) return rc;
       MG_CUDA(c, cudaMemcpy(V.phic, phic.data(), ncell * sizeof(R), cudaMemcpyHostToDevice));
+    }
+    {
+      // complex cell width per axis index (per-cell shift and adjoint kernels)
       const double h = 1.0 / V.n;
       const cd hrot = h * cd(std::cos(c->theta), std::sin(c->theta));
       std::vector<cd> hc(V.n);
@@ -1354,6 +1367,138 @@ int mg_get_stats(mg_ctx* c, long long* launches, int* fine_sweeps, double* fine_
   if (fine_ms) *fine_ms = ms;
   c->launches = 0;
   c->ev_used = 0;
+  return MG_OK;
+}
+
+int mg_set_k2(mg_ctx* c, const double* k2) {
+  if (check_ctx(c)) return MG_ERR_INVALID;
+  if (k2 == nullptr) return fail(c, MG_ERR_INVALID, "k2 is NULL");
+  if (!c->h64.varphi)
+    return fail(c, MG_ERR_INVALID, "the context was created with a constant k^2; create a new context");
+  const size_t nv = c->k2.size();
+  for (size_t i = 0; i < nv; ++i)
+    if (!std::isfinite(k2[i])) return fail(c, MG_ERR_INVALID, "k2 holds a non-finite value");
+  MG_CUDA(c, cudaStreamSynchronize(c->stream));
+  c->k2.assign(k2, k2 + nv);
+  for (int l = 1; l <= c->L; ++l) {
+    auto p64 = cell_shift<double>(c, l);
+    MG_CUDA(c, cudaMemcpy(c->h64.lev[l].phic, p64.data(), p64.size() * sizeof(double), cudaMemcpyHostToDevice));
+    if (c->h32.ready) {
+      auto p32 = cell_shift<float>(c, l);
+      MG_CUDA(c, cudaMemcpy(c->h32.lev[l].phic, p32.data(), p32.size() * sizeof(float), cudaMemcpyHostToDevice));
+    }
+  }
+  c->r0 = -1.0;
+  return MG_OK;
+}
+
+int mg_set_rhs_vector(mg_ctx* c, const mg_c128* b, int on_device) {
+  if (check_ctx(c)) return MG_ERR_INVALID;
+  if (b == nullptr) return fail(c, MG_ERR_INVALID, "b is NULL");
+  auto& V = c->h64.lev[c->L];
+  MG_CUDA(c, cudaMemcpyAsync(c->scratch, b, V.nv * sizeof(mg_c128),
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+  ++c->launches;
+  if (c->d == 2)
+    mg::materialize_kernel<double, 2><<<grid_for(V.nv), kThreads, 0, c->stream>>>(V.n, c->scratch, nullptr, V.b);
+  else
+    mg::materialize_kernel<double, 3><<<grid_for(V.nv), kThreads, 0, c->stream>>>(V.n, c->scratch, nullptr, V.b);
+  MG_CUDA(c, cudaGetLastError());
+  c->r0 = -1.0;
+  return MG_OK;
+}
+
+namespace {
+// host list of (vertex, weight) of the d-linear samples at npts points
+int sample_stencil(mg_ctx* c, int npts, const double* xyz, const mg_c128* w,
+                   std::map<long long, cd>& acc) {
+  const int d = c->d, n = (int)ipow(3, c->L), N = n + 1;
+  for (int p = 0; p < npts; ++p) {
+    int i[3];
+    double f[3];
+    for (int a = 0; a < d; ++a) {
+      const double x = xyz[(size_t)p * d + a];
+      if (!(x >= 0.0 && x <= 1.0)) return fail(c, MG_ERR_INVALID, "sample points must lie in [0,1]^d");
+      const double xs = x * n;
+      int k = (int)std::floor(xs);
+      k = std::min(std::max(k, 0), n - 1);
+      i[a] = k;
+      f[a] = xs - k;
+    }
+    for (int e = 0; e < (1 << d); ++e) {
+      double wt = 1.0;
+      long long vi = 0, st = 1;
+      bool inner = true;
+      for (int a = 0; a < d; ++a) {
+        const int bb = (e >> a) & 1;
+        wt *= bb ? f[a] : 1.0 - f[a];
+        const int g = i[a] + bb;
+        inner = inner && g > 0 && g < n;
+        vi += (long long)g * st;
+        st *= N;
+      }
+      if (inner) acc[vi] += wt * cd(w[p].re, w[p].im);
+    }
+  }
+  return MG_OK;
+}
+}  // namespace
+
+int mg_sample(mg_ctx* c, int npts, const double* xyz, const mg_c128* w, mg_c128* out) {
+  if (check_ctx(c)) return MG_ERR_INVALID;
+  if (npts < 1 || xyz == nullptr || w == nullptr || out == nullptr)
+    return fail(c, MG_ERR_INVALID, "bad sample arguments");
+  std::map<long long, cd> acc;
+  int rc = sample_stencil(c, npts, xyz, w, acc);
+  if (rc != MG_OK) return rc;
+  // s = sum over the stencil of weight * u (materialised, copied back per vertex)
+  auto& H = c->h64;
+  MG_CUDA(c, materialize(c, H, c->L, c->scratch));
+  std::vector<long long> idx;
+  for (auto& kv : acc) idx.push_back(kv.first);
+  std::vector<mg_c128> vals(idx.size());
+  MG_CUDA(c, cudaStreamSynchronize(c->stream));
+  cd s(0);
+  for (size_t k = 0; k < idx.size(); ++k) {
+    MG_CUDA(c, cudaMemcpy(&vals[k], c->scratch + idx[k], sizeof(mg_c128), cudaMemcpyDeviceToHost));
+    s += acc[idx[k]] * cd(vals[k].re, vals[k].im);
+  }
+  out->re = s.real();
+  out->im = s.imag();
+  return check_timeout(c);
+}
+
+int mg_set_rhs_samples(mg_ctx* c, int npts, const double* xyz, const mg_c128* w) {
+  if (check_ctx(c)) return MG_ERR_INVALID;
+  if (npts < 1 || xyz == nullptr || w == nullptr) return fail(c, MG_ERR_INVALID, "bad sample arguments");
+  std::map<long long, cd> acc;
+  int rc = sample_stencil(c, npts, xyz, w, acc);
+  if (rc != MG_OK) return rc;
+  std::vector<mg_c128> b(c->h64.lev[c->L].nv, mg_c128{0.0, 0.0});
+  for (auto& kv : acc) b[(size_t)kv.first] = mg_c128{kv.second.real(), kv.second.imag()};
+  return mg_set_rhs_vector(c, b.data(), 0);
+}
+
+int mg_adjoint_grad(mg_ctx* c, const mg_c128* u, const mg_c128* lambda, mg_c128 s, double* dJdV,
+                    double* dJdf) {
+  if (check_ctx(c)) return MG_ERR_INVALID;
+  if (u == nullptr || lambda == nullptr || (dJdV == nullptr && dJdf == nullptr))
+    return fail(c, MG_ERR_INVALID, "u, lambda and at least one output are required");
+  auto& V = c->h64.lev[c->L];
+  const size_t ncell = (size_t)ipow(V.n, c->d);
+  const auto* uu = reinterpret_cast<const cplx<double>*>(u);
+  const auto* ll = reinterpret_cast<const cplx<double>*>(lambda);
+  c->launches += 2;
+  if (c->d == 2) {
+    mg::cell_mass_form_kernel<2><<<grid_for(ncell), kThreads, 0, c->stream>>>(V.n, ll, uu, V.hcell, c->scratch);
+    mg::adjoint_grad_kernel<2><<<grid_for(V.nv), kThreads, 0, c->stream>>>(
+        V.n, ll, c->scratch, V.hcell, cplx<double>{s.re, s.im}, dJdV, dJdf);
+  } else {
+    mg::cell_mass_form_kernel<3><<<grid_for(ncell), kThreads, 0, c->stream>>>(V.n, ll, uu, V.hcell, c->scratch);
+    mg::adjoint_grad_kernel<3><<<grid_for(V.nv), kThreads, 0, c->stream>>>(
+        V.n, ll, c->scratch, V.hcell, cplx<double>{s.re, s.im}, dJdV, dJdf);
+  }
+  MG_CUDA(c, cudaGetLastError());
   return MG_OK;
 }
 

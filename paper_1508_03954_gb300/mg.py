@@ -28,7 +28,8 @@ STATUS_NAMES = {0: "MG_OK", 1: "MG_ERR_INVALID", 2: "MG_ERR_CUDA", 3: "MG_ERR_OO
 EXPORTS = ["mg_create", "mg_destroy", "mg_set_stream", "mg_set_rhs", "mg_set_solution",
            "mg_get_solution", "mg_cycle", "mg_residual_norm", "mg_solve", "mg_set_precision",
            "mg_fmg", "mg_omega_scheme", "mg_get_level", "mg_set_timing", "mg_get_stats",
-           "mg_set_trace", "mg_get_trace", "mg_residual_noalloc", "mg_last_error"]
+           "mg_set_trace", "mg_get_trace", "mg_set_k2", "mg_set_rhs_vector", "mg_sample",
+           "mg_set_rhs_samples", "mg_adjoint_grad", "mg_residual_noalloc", "mg_last_error"]
 
 
 class MgC128(ctypes.Structure):
@@ -79,6 +80,11 @@ def load(path: str | None = None):
                               ctypes.POINTER(dp)]),
         "mg_residual_noalloc": (ip, [vp, vp, vp, vp, vp]),
         "mg_set_trace": (ip, [vp, ip]),
+        "mg_set_k2": (ip, [vp, ctypes.POINTER(dp)]),
+        "mg_set_rhs_vector": (ip, [vp, vp, ip]),
+        "mg_sample": (ip, [vp, ip, ctypes.POINTER(dp), pc, pc]),
+        "mg_set_rhs_samples": (ip, [vp, ip, ctypes.POINTER(dp), pc]),
+        "mg_adjoint_grad": (ip, [vp, vp, vp, MgC128, vp, vp]),
         "mg_get_trace": (ip, [vp, vp, ip, ip]),
         "mg_last_error": (ctypes.c_char_p, [vp]),
     }
@@ -217,6 +223,57 @@ class Solver:
         self._check(self._L.mg_get_stats(self._h, ctypes.byref(n), ctypes.byref(k), ctypes.byref(ms)),
                     "mg_get_stats")
         return n.value, k.value, ms.value
+
+    def set_k2(self, k2):
+        a = np.ascontiguousarray(np.asarray(k2, dtype=np.float64))
+        if a.size != self.nv:
+            raise ValueError(f"k2 needs {self.nv} values")
+        self._check(self._L.mg_set_k2(self._h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+                    "mg_set_k2")
+
+    def set_rhs_vector(self, b):
+        p, dev, _keep = _ptr(b, self.nv)
+        self._check(self._L.mg_set_rhs_vector(self._h, p, dev), "mg_set_rhs_vector")
+
+    @staticmethod
+    def _samples(xyz, w):
+        xyz = np.ascontiguousarray(np.asarray(xyz, dtype=np.float64))
+        w = np.ascontiguousarray(np.asarray(w, dtype=np.complex128).reshape(-1))
+        wa = (MgC128 * len(w))()
+        for i, z in enumerate(w):
+            wa[i].re, wa[i].im = float(z.real), float(z.imag)
+        return xyz, wa, len(w)
+
+    def sample(self, xyz, w):
+        """s = sum_q w_q u(x_q); xyz shape (npts, d) with x first."""
+        xyz, wa, m = self._samples(xyz, w)
+        out = MgC128()
+        self._check(self._L.mg_sample(self._h, m, xyz.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), wa,
+                                      ctypes.byref(out)), "mg_sample")
+        return complex(out.re, out.im)
+
+    def set_rhs_samples(self, xyz, w):
+        xyz, wa, m = self._samples(xyz, w)
+        self._check(self._L.mg_set_rhs_samples(self._h, m, xyz.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                               wa), "mg_set_rhs_samples")
+
+    def adjoint_grad(self, u, lam, s, dJdV=None, dJdf=None):
+        """Device tensors: u, lam complex128 (fine size); dJdV, dJdf float64 (fine size) or None."""
+        for t in (u, lam):
+            if not (t.is_cuda and t.is_contiguous() and t.numel() == self.nv):
+                raise ValueError("u and lam must be contiguous CUDA tensors of the fine size")
+        outs = []
+        for t in (dJdV, dJdf):
+            if t is None:
+                outs.append(None)
+            else:
+                if not (t.is_cuda and t.is_contiguous() and t.numel() == self.nv):
+                    raise ValueError("gradient outputs must be contiguous float64 CUDA tensors")
+                outs.append(ctypes.c_void_p(t.data_ptr()))
+        self._check(self._L.mg_adjoint_grad(self._h, ctypes.c_void_p(u.data_ptr()),
+                                            ctypes.c_void_p(lam.data_ptr()),
+                                            MgC128(float(np.real(s)), float(np.imag(s))), outs[0], outs[1]),
+                    "mg_adjoint_grad")
 
     def set_trace(self, enable):
         self._check(self._L.mg_set_trace(self._h, 1 if enable else 0), "mg_set_trace")
