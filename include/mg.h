@@ -181,6 +181,49 @@ int mg_set_rhs_samples(mg_ctx* ctx, int npts, const double* xyz, const mg_c128* 
 int mg_adjoint_grad(mg_ctx* ctx, const mg_c128* u, const mg_c128* lambda, mg_c128 s,
                     double* dJdV, double* dJdf);
 
+/* ---- batched form; not in the paper (its multichannel idea, Section 7.5) --
+ * n independent 2D problems of any depths, each with a constant k^2, solved
+ * together: every outer defect-correction step of every problem (FP64
+ * residual, inner_cycles complex64 cycles, FP64 update) runs in ONE
+ * persistent launch whose work items (problem, stage, tile) are taken from a
+ * queue in dependency order, replayed as a CUDA graph. */
+typedef struct mg_batch mg_batch;
+
+/* Creates n contexts (arrays d, depth, theta, layer_width of n entries; k2:
+ * n host pointers to fine k^2 fields that must each be constant).  The batch
+ * owns the contexts.  MG_ERR_INVALID for 3D or varying-k^2 problems. */
+int mg_batch_create(int n, const int* d, const int* depth, const double* const* k2,
+                    const double* theta, const double* layer_width, mg_batch** out);
+void mg_batch_destroy(mg_batch* batch);
+
+/* Context of problem p (owned by the batch): set its rhs, solution, read
+ * its solution or run single-problem calls on it with the mg_* API. */
+int mg_batch_get_ctx(mg_batch* batch, int p, mg_ctx** out);
+
+/* Enqueues the batch's work (and its contexts' work) on this stream. */
+int mg_batch_set_stream(mg_batch* batch, void* cuda_stream);
+
+/* Solves every problem to relative FP64 residual tol (relative to its
+ * residual at the start of the call), at most max_outer outer steps of
+ * inner_cycles complex64 cycles each.  omega: n host pointers, problem p's
+ * has depth_p entries.  Per problem: status (MG_OK / MG_NOT_CONVERGED /
+ * MG_DIVERGED), inner cycles run and final relative residual (any output
+ * may be NULL).  Returns MG_OK unless the call itself failed. */
+int mg_batch_solve(mg_batch* batch, int variant, const mg_c128* const* omega, int transfer,
+                   double tol, int max_outer, int inner_cycles, int* status, int* cycles,
+                   double* rel_res);
+
+/* Autotuner: times one outer step of the batch for every candidate fine tile
+ * (4 or 8 coarse cells per edge) and persistent residency (2, 4 or 8 blocks
+ * per SM), keeps the fastest for later solves and restores the solutions.
+ * Outputs (may be NULL): chosen tile, residency, its time per outer step. */
+int mg_batch_autotune(mg_batch* batch, int variant, const mg_c128* const* omega, int transfer,
+                      int inner_cycles, int* tile_out, int* blocks_per_sm_out, double* ms_out);
+
+/* Persistent launches issued by the batch so far. */
+long long mg_batch_launches(const mg_batch* batch);
+const char* mg_batch_last_error(const mg_batch* batch);
+
 /* Instrumentation.  mg_set_timing(ctx, 1) makes every later cycle record a
  * CUDA event pair around its finest-level sweep kernel on the context's
  * stream.  mg_get_stats synchronises the stream and returns, since the last

@@ -460,6 +460,7 @@ cudaError_t launch_sweep(cudaStream_t s, mg::SweepArgs<R>& A) {
   int nblk = 1;
   for (int a = 0; a < 3; ++a) A.tiles[a] = a < D ? tiles : 1;
   for (int a = 0; a < D; ++a) nblk *= tiles;
+  A.ntiles = nblk;
   const size_t smem = mg::sweep_smem_bytes<R, D, TC>(A.varphi);
   auto kern = mg::sweep_kernel<R, D, TC, kThreads>;
   kern<<<nblk, kThreads, smem, s>>>(A);
@@ -1590,3 +1591,519 @@ extern "C" int mg_residual_noalloc(mg_ctx* c, const mg_c128* u, const mg_c128* b
   MG_CUDA(c, cudaGetLastError());
   return MG_OK;
 }
+
+// =========================================================================
+// Batched form: many independent 2D problems, one persistent launch per
+// outer defect-correction iteration (mg_batch.cuh).
+// =========================================================================
+#include "mg_batch.cuh"
+
+struct mg_batch {
+  std::vector<mg_ctx*> ctx;
+  cudaStream_t stream = 0;
+  // plan (item list and argument tables) of the last solve configuration
+  std::vector<double> key;
+  mg::ChainItem* items = nullptr;
+  mg::SweepArgs<float>* sw = nullptr;
+  mg::ResArgs* res = nullptr;
+  mg::UpdArgs* upd = nullptr;
+  mg::CorrArgsF* co = nullptr;
+  int nitems = 0;
+  int* active_dev = nullptr;
+  int* active_host = nullptr;       // pinned
+  unsigned* ctr = nullptr;          // [0] head, [1 + p] problem counters
+  unsigned* err = nullptr;
+  double* norm_dev = nullptr;
+  double* norm_host = nullptr;      // pinned
+  int tc = 8, bpsm = 4;             // fine tile and residency (autotuned)
+  cudaGraphExec_t graph = nullptr;
+  std::vector<double> graph_key;
+  long long launches = 0;
+  std::string errmsg;
+};
+
+namespace {
+int bfail(mg_batch* b, int code, const std::string& m) {
+  if (b) b->errmsg = m;
+  return code;
+}
+#define MG_BCUDA(b, call)                                                               \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess) return bfail((b), MG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+template <int TC>
+size_t batch_smem() {
+  size_t a = mg::sweep_smem_bytes<float, 2, TC>(0), b2 = mg::sweep_smem_bytes<float, 2, 2>(0);
+  return a > b2 ? a : b2;
+}
+
+void free_plan(mg_batch* b) {
+  cudaFree(b->items);
+  cudaFree(b->sw);
+  cudaFree(b->res);
+  cudaFree(b->upd);
+  cudaFree(b->co);
+  b->items = nullptr;
+  b->sw = nullptr;
+  b->res = nullptr;
+  b->upd = nullptr;
+  b->co = nullptr;
+  b->nitems = 0;
+  b->key.clear();
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  b->graph = nullptr;
+  b->graph_key.clear();
+}
+
+// complex64 sweep arguments of level l of problem c (inner hierarchy)
+mg::SweepArgs<float> fsweep_args(mg_ctx* c, int l, bool fine, int k, int hb, int hier, const cd& om, int tc) {
+  auto& E = c->h32;
+  auto& V = E.lev[l];
+  mg::SweepArgs<float> A;
+  std::memset(&A, 0, sizeof(A));
+  A.n = V.n;
+  A.fine = fine ? 1 : 0;
+  A.first = (fine && k == 0) ? 1 : 0;
+  A.has_coarse = l > 1 ? 1 : 0;
+  A.hb = hb;
+  A.hier = hier;
+  A.u = fine ? V.u[k % 2] : V.u[0];
+  A.c = (fine && l > 1) ? E.lev[l - 1].corr : nullptr;
+  A.b = V.b;
+  A.out = fine ? V.u[(k + 1) % 2] : V.t;
+  if (l > 1) {
+    A.b_coarse = E.lev[l - 1].b;
+    A.u_coarse = E.lev[l - 1].u[0];
+  }
+  A.typ = V.typ;
+  A.coef = V.coefH;
+  A.hcell = V.hcell;
+  A.omega = cplx<float>{(float)om.real(), (float)om.imag()};
+  for (size_t t = 0; t < V.diag.size() && t < (size_t)mg::kMaxTypes; ++t) {
+    const cd q = om / V.diag[t];
+    A.omd[t] = cplx<float>{(float)q.real(), (float)q.imag()};
+  }
+  const int nc = V.n / 3, tl = (nc + 1 + tc - 1) / tc;
+  A.tiles[0] = tl;
+  A.tiles[1] = tl;
+  A.tiles[2] = 1;
+  A.ntiles = tl * tl;
+  return A;
+}
+
+int build_batch_plan(mg_batch* b, int hb, int hier, const cplx<double>* const* omega, int m,
+                     const std::vector<double>& key) {
+  if (b->key == key && b->items) return MG_OK;
+  free_plan(b);
+  const int np = (int)b->ctx.size();
+  std::vector<mg::SweepArgs<float>> sw;
+  std::vector<mg::ResArgs> res;
+  std::vector<mg::UpdArgs> upd;
+  std::vector<mg::CorrArgsF> co;
+  // per problem: list of stages, each a list of items (need filled later)
+  std::vector<std::vector<std::vector<mg::ChainItem>>> stages(np);
+  for (int p = 0; p < np; ++p) {
+    mg_ctx* c = b->ctx[p];
+    const int L = c->L;
+    auto& H = c->h64;
+    auto& E = c->h32;
+    auto& S = stages[p];
+    auto V = [&](int l) -> int { return E.lev[l].n / 3 + 1; };
+    // residual stage
+    {
+      mg::ResArgs r;
+      std::memset(&r, 0, sizeof(r));
+      r.n = H.lev[L].n;
+      r.nchunks = (int)((H.lev[L].nv + mg::kBatchChunk - 1) / mg::kBatchChunk);
+      r.u = H.lev[L].u[H.cur];
+      r.b = H.lev[L].b;
+      r.out = E.lev[L].b;
+      r.typ = H.lev[L].typ;
+      r.coef = H.lev[L].coefH;
+      r.partial = H.partial;
+      r.ticket = H.ticket + 2;
+      r.norm2 = b->norm_dev + p;
+      res.push_back(r);
+      std::vector<mg::ChainItem> st;
+      for (int t = 0; t < r.nchunks; ++t) st.push_back({mg::kBRes, p, (int)res.size() - 1, t, 0});
+      S.push_back(st);
+    }
+    for (int k = 0; k < m; ++k) {
+      for (int l = L; l >= 1; --l) {
+        const cplx<double> w = omega[p][l - 1];
+        const bool fine = l == L;
+        const int tc = (fine || V(l) >= 40) ? b->tc : 2;
+        const int kind = tc == 2 ? mg::kBSweepS : mg::kBSweep;
+        sw.push_back(fsweep_args(c, l, fine, k, hb, hier, cd(w.x, w.y), tc));
+        std::vector<mg::ChainItem> st;
+        for (int t = 0; t < sw.back().ntiles; ++t) st.push_back({kind, p, (int)sw.size() - 1, t, 0});
+        S.push_back(st);
+      }
+      const int top = L - 1;
+      auto add_corr = [&](int tgt, int lo, const cplx<float>* base) {
+        mg::CorrArgsF ca;
+        std::memset(&ca, 0, sizeof(ca));
+        ca.s = tgt;
+        ca.lo = lo;
+        for (int l = lo; l <= tgt; ++l) ca.t[l] = E.lev[l].t;
+        ca.base = base;
+        ca.out = E.lev[tgt].corr;
+        co.push_back(ca);
+        std::vector<mg::ChainItem> st;
+        const int nch = (int)((E.lev[tgt].nv + mg::kBatchChunk - 1) / mg::kBatchChunk);
+        for (int t = 0; t < nch; ++t) st.push_back({mg::kBCorr, p, (int)co.size() - 1, t, 0});
+        S.push_back(st);
+      };
+      if (top >= 3) {
+        add_corr(top - 1, 1, nullptr);
+        add_corr(top, top, E.lev[top - 1].corr);
+      } else if (top == 2) {
+        add_corr(2, 1, nullptr);
+      }
+    }
+    {
+      mg::UpdArgs u;
+      u.n = H.lev[L].n;
+      u.u = H.lev[L].u[H.cur];
+      u.e = E.lev[L].u[m % 2];
+      u.c = L > 1 ? E.lev[L - 1].corr : nullptr;
+      upd.push_back(u);
+      std::vector<mg::ChainItem> st;
+      const int nch = (int)((H.lev[L].nv + mg::kBatchChunk - 1) / mg::kBatchChunk);
+      for (int t = 0; t < nch; ++t) st.push_back({mg::kBUpd, p, (int)upd.size() - 1, t, 0});
+      S.push_back(st);
+    }
+    unsigned need = 0;
+    for (auto& st : S) {
+      for (auto& it : st) it.need = need;
+      need += (unsigned)st.size();
+    }
+  }
+  // stage-major order across problems
+  std::vector<mg::ChainItem> items;
+  size_t maxst = 0;
+  for (auto& S : stages) maxst = std::max(maxst, S.size());
+  for (size_t j = 0; j < maxst; ++j)
+    for (int p = 0; p < np; ++p)
+      if (j < stages[p].size()) items.insert(items.end(), stages[p][j].begin(), stages[p][j].end());
+  b->nitems = (int)items.size();
+  auto up = [&](void** dst, const void* src, size_t bytes) -> cudaError_t {
+    cudaError_t e = cudaMalloc(dst, std::max<size_t>(bytes, 16));
+    if (e == cudaSuccess && bytes) e = cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
+    return e;
+  };
+  MG_BCUDA(b, up((void**)&b->items, items.data(), items.size() * sizeof(mg::ChainItem)));
+  MG_BCUDA(b, up((void**)&b->sw, sw.data(), sw.size() * sizeof(mg::SweepArgs<float>)));
+  MG_BCUDA(b, up((void**)&b->res, res.data(), res.size() * sizeof(mg::ResArgs)));
+  MG_BCUDA(b, up((void**)&b->upd, upd.data(), upd.size() * sizeof(mg::UpdArgs)));
+  MG_BCUDA(b, up((void**)&b->co, co.data(), co.size() * sizeof(mg::CorrArgsF)));
+  b->key = key;
+  return MG_OK;
+}
+
+// enqueue one outer iteration (counters, flags, kernel, norms) on b->stream
+cudaError_t enqueue_batch(mg_batch* b) {
+  const int np = (int)b->ctx.size();
+  cudaError_t e = cudaMemcpyAsync(b->active_dev, b->active_host, np * sizeof(int), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->ctr, 0, (np + 1) * sizeof(unsigned), b->stream);
+  mg::BatchArgs A;
+  A.items = b->items;
+  A.nitems = b->nitems;
+  A.sw = b->sw;
+  A.res = b->res;
+  A.upd = b->upd;
+  A.co = b->co;
+  A.active = b->active_dev;
+  A.head = b->ctr;
+  A.done = b->ctr + 1;
+  A.err = b->err;
+  A.spin_limit = 1u << 22;
+  const int grid = 152 * b->bpsm;
+  if (e == cudaSuccess) {
+    if (b->tc == 8)
+      mg::batch2_kernel<8, 256><<<grid, 256, batch_smem<8>(), b->stream>>>(A);
+    else
+      mg::batch2_kernel<4, 256><<<grid, 256, batch_smem<4>(), b->stream>>>(A);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->norm_host, b->norm_dev, np * sizeof(double), cudaMemcpyDeviceToHost, b->stream);
+  return e;
+}
+
+// one outer iteration as a captured graph (captured once per plan and tuning)
+int run_batch(mg_batch* b) {
+  std::vector<double> gk = b->key;
+  gk.push_back(b->tc);
+  gk.push_back(b->bpsm);
+  if (b->graph == nullptr || b->graph_key != gk) {
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    cudaStream_t cs;
+    MG_BCUDA(b, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaStream_t user = b->stream;
+    b->stream = cs;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    cudaError_t ek = e == cudaSuccess ? enqueue_batch(b) : e;
+    cudaError_t ee = e == cudaSuccess ? cudaStreamEndCapture(cs, &g) : e;
+    b->stream = user;
+    if (e == cudaSuccess) e = ek != cudaSuccess ? ek : ee;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+      b->graph = nullptr;
+      return bfail(b, MG_ERR_CUDA, std::string("batch graph: ") + cudaGetErrorString(e));
+    }
+    b->graph_key = gk;
+  }
+  MG_BCUDA(b, cudaGraphLaunch(b->graph, b->stream));
+  ++b->launches;
+  return MG_OK;
+}
+
+int batch_prepare(mg_batch* b, int variant, const mg_c128* const* omega, int transfer, int inner, int* hbp,
+                  int* hierp) {
+  if (omega == nullptr) return bfail(b, MG_ERR_INVALID, "omega is NULL");
+  if (inner < 1 || inner > 64) return bfail(b, MG_ERR_INVALID, "inner_cycles must be in 1..64");
+  int hb, hier;
+  if (variant < MG_ADD || variant > MG_BPX || (transfer != MG_DLINEAR && transfer != MG_HIERARCHICAL))
+    return bfail(b, MG_ERR_INVALID, "bad variant/transfer");
+  hb = variant == MG_HB;
+  hier = (transfer == MG_HIERARCHICAL) || (variant == MG_BPX);
+  std::vector<double> key = {(double)hb, (double)hier, (double)inner, (double)b->tc};
+  for (size_t p = 0; p < b->ctx.size(); ++p) {
+    if (omega[p] == nullptr) return bfail(b, MG_ERR_INVALID, "omega[p] is NULL");
+    for (int l = 0; l < b->ctx[p]->L; ++l) {
+      key.push_back(omega[p][l].re);
+      key.push_back(omega[p][l].im);
+    }
+  }
+  std::vector<const cplx<double>*> om(b->ctx.size());
+  for (size_t p = 0; p < b->ctx.size(); ++p) om[p] = reinterpret_cast<const cplx<double>*>(omega[p]);
+  int rc = build_batch_plan(b, hb, hier, om.data(), inner, key);
+  *hbp = hb;
+  *hierp = hier;
+  return rc;
+}
+
+// fold pending corrections of the FP64 fine solutions (the batch updates u in place)
+int batch_materialize(mg_batch* b) {
+  for (mg_ctx* c : b->ctx) {
+    auto& H = c->h64;
+    cudaStream_t keep = c->stream;
+    c->stream = b->stream;
+    cudaError_t e = materialize(c, H, c->L, c->scratch);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(H.lev[c->L].u[H.cur], c->scratch, H.lev[c->L].nv * sizeof(cplx<double>),
+                          cudaMemcpyDeviceToDevice, b->stream);
+    c->stream = keep;
+    if (e != cudaSuccess) return bfail(b, MG_ERR_CUDA, cudaGetErrorString(e));
+    if (zero_pending(c, H, c->L) != MG_OK) return bfail(b, MG_ERR_CUDA, c->err);
+  }
+  return MG_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int mg_batch_create(int n, const int* d, const int* depth, const double* const* k2, const double* theta,
+                    const double* layer_width, mg_batch** out) {
+  if (out == nullptr || n < 1 || d == nullptr || depth == nullptr || k2 == nullptr || theta == nullptr ||
+      layer_width == nullptr)
+    return MG_ERR_INVALID;
+  *out = nullptr;
+  for (int p = 0; p < n; ++p)
+    if (d[p] != 2) return fail(nullptr, MG_ERR_INVALID, "batched problems must be 2D");
+  mg_batch* b = new (std::nothrow) mg_batch();
+  if (b == nullptr) return MG_ERR_OOM;
+  auto cleanup = [&](int rc) {
+    mg_batch_destroy(b);
+    return rc;
+  };
+  for (int p = 0; p < n; ++p) {
+    mg_ctx* c = nullptr;
+    int rc = mg_create(d[p], depth[p], k2[p], theta[p], layer_width[p], &c);
+    if (rc != MG_OK) return cleanup(rc);
+    b->ctx.push_back(c);
+    if (c->h64.varphi) return cleanup(fail(nullptr, MG_ERR_INVALID, "batched problems need a constant k^2"));
+    rc = mg_set_precision(c, MG_C64_REFINE, 4);
+    if (rc != MG_OK) return cleanup(rc);
+  }
+  cudaError_t e = cudaMalloc(&b->active_dev, n * sizeof(int));
+  if (e == cudaSuccess) e = cudaMallocHost(&b->active_host, n * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&b->ctr, (n + 1) * sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMalloc(&b->err, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemset(b->err, 0, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMalloc(&b->norm_dev, n * sizeof(double));
+  if (e == cudaSuccess) e = cudaMallocHost(&b->norm_host, n * sizeof(double));
+  auto setsm = [&](const void* f, size_t bytes) {
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  };
+  setsm((const void*)mg::batch2_kernel<8, 256>, batch_smem<8>());
+  setsm((const void*)mg::batch2_kernel<4, 256>, batch_smem<4>());
+  if (e != cudaSuccess) return cleanup(fail(nullptr, MG_ERR_CUDA, cudaGetErrorString(e)));
+  for (int p = 0; p < n; ++p) b->active_host[p] = 1;
+  *out = b;
+  return MG_OK;
+}
+
+void mg_batch_destroy(mg_batch* b) {
+  if (b == nullptr) return;
+  free_plan(b);
+  for (mg_ctx* c : b->ctx) mg_destroy(c);
+  cudaFree(b->active_dev);
+  if (b->active_host) cudaFreeHost(b->active_host);
+  cudaFree(b->ctr);
+  cudaFree(b->err);
+  cudaFree(b->norm_dev);
+  if (b->norm_host) cudaFreeHost(b->norm_host);
+  delete b;
+}
+
+int mg_batch_get_ctx(mg_batch* b, int p, mg_ctx** out) {
+  if (b == nullptr || out == nullptr || p < 0 || p >= (int)b->ctx.size()) return MG_ERR_INVALID;
+  *out = b->ctx[p];
+  return MG_OK;
+}
+
+int mg_batch_set_stream(mg_batch* b, void* stream) {
+  if (b == nullptr) return MG_ERR_INVALID;
+  b->stream = (cudaStream_t)stream;
+  for (mg_ctx* c : b->ctx) c->stream = b->stream;
+  return MG_OK;
+}
+
+int mg_batch_solve(mg_batch* b, int variant, const mg_c128* const* omega, int transfer, double tol,
+                   int max_outer, int inner_cycles, int* status, int* cycles, double* rel_res) {
+  if (b == nullptr) return MG_ERR_INVALID;
+  if (!(tol > 0) || max_outer < 0) return bfail(b, MG_ERR_INVALID, "tol must be > 0 and max_outer >= 0");
+  int hb, hier;
+  int rc = batch_prepare(b, variant, omega, transfer, inner_cycles, &hb, &hier);
+  if (rc != MG_OK) return rc;
+  if ((rc = batch_materialize(b)) != MG_OK) return rc;
+  const int np = (int)b->ctx.size();
+  std::vector<double> r0(np, -1.0), rel(np, 1.0);
+  std::vector<int> st(np, MG_NOT_CONVERGED), outer(np, 0);
+  for (int p = 0; p < np; ++p) b->active_host[p] = 1;
+  int live = np;
+  for (int it = 0; it <= max_outer && live > 0; ++it) {
+    if ((rc = run_batch(b)) != MG_OK) return rc;
+    MG_BCUDA(b, cudaStreamSynchronize(b->stream));
+    for (int p = 0; p < np; ++p) {
+      if (!b->active_host[p]) continue;
+      const double r = std::sqrt(b->norm_host[p]);
+      if (r0[p] < 0) r0[p] = r;
+      rel[p] = r0[p] > 0 ? r / r0[p] : 0.0;
+      if (!std::isfinite(rel[p]) || rel[p] > 1e6) {
+        st[p] = MG_DIVERGED;
+      } else if (rel[p] <= tol) {
+        st[p] = MG_OK;
+      } else if (it == max_outer) {
+        st[p] = MG_NOT_CONVERGED;
+      } else {
+        ++outer[p];
+        continue;  // stays active: this launch already ran its next outer step
+      }
+      b->active_host[p] = 0;
+      --live;
+    }
+  }
+  unsigned f = 0;
+  MG_BCUDA(b, cudaMemcpy(&f, b->err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  if (f) {
+    cudaMemset(b->err, 0, sizeof(unsigned));
+    return bfail(b, MG_ERR_TIMEOUT, "a bounded device-side wait gave up");
+  }
+  // final FP64 residual of every solution relative to its starting residual
+  for (int p = 0; p < np; ++p) {
+    mg_ctx* c = b->ctx[p];
+    double r;
+    if ((rc = fine_residual(c, c->L, &r)) != MG_OK) return bfail(b, rc, c->err);
+    const double relp = r0[p] > 0 ? r / r0[p] : 0.0;
+    if (st[p] == MG_OK && relp > tol) st[p] = MG_NOT_CONVERGED;
+    if (status) status[p] = st[p];
+    if (cycles) cycles[p] = outer[p] * inner_cycles;
+    if (rel_res) rel_res[p] = relp;
+    c->r0 = r0[p];
+  }
+  return MG_OK;
+}
+
+int mg_batch_autotune(mg_batch* b, int variant, const mg_c128* const* omega, int transfer, int inner_cycles,
+                      int* tc_out, int* bpsm_out, double* best_ms) {
+  if (b == nullptr) return MG_ERR_INVALID;
+  int rc = batch_materialize(b);
+  if (rc != MG_OK) return rc;
+  const int np = (int)b->ctx.size();
+  // the trial launches update the solutions: save and restore them
+  std::vector<cplx<double>*> saved(np, nullptr);
+  for (int p = 0; p < np; ++p) {
+    auto& V = b->ctx[p]->h64.lev[b->ctx[p]->L];
+    MG_BCUDA(b, cudaMalloc(&saved[p], V.nv * sizeof(cplx<double>)));
+    MG_BCUDA(b, cudaMemcpyAsync(saved[p], V.u[b->ctx[p]->h64.cur], V.nv * sizeof(cplx<double>),
+                                cudaMemcpyDeviceToDevice, b->stream));
+  }
+  for (int p = 0; p < np; ++p) b->active_host[p] = 1;
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  double best = 1e30;
+  int btc = b->tc, bb = b->bpsm;
+  cudaEvent_t e0, e1;
+  MG_BCUDA(b, cudaEventCreate(&e0));
+  MG_BCUDA(b, cudaEventCreate(&e1));
+  for (int tc : {4, 8}) {
+    int occ = 0;
+    if (tc == 8)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mg::batch2_kernel<8, 256>, 256, batch_smem<8>());
+    else
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mg::batch2_kernel<4, 256>, 256, batch_smem<4>());
+    for (int bp : {2, 4, 8}) {
+      if (bp > occ) continue;
+      b->tc = tc;
+      b->bpsm = bp;
+      int hb, hier;
+      if ((rc = batch_prepare(b, variant, omega, transfer, inner_cycles, &hb, &hier)) != MG_OK) break;
+      if ((rc = run_batch(b)) != MG_OK) break;  // warm-up
+      MG_BCUDA(b, cudaEventRecord(e0, b->stream));
+      for (int r = 0; r < 3 && rc == MG_OK; ++r) rc = run_batch(b);
+      MG_BCUDA(b, cudaEventRecord(e1, b->stream));
+      MG_BCUDA(b, cudaEventSynchronize(e1));
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rc == MG_OK && ms / 3 < best) {
+        best = ms / 3;
+        btc = tc;
+        bb = bp;
+      }
+    }
+    if (rc != MG_OK) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  for (int p = 0; p < np; ++p) {
+    auto& V = b->ctx[p]->h64.lev[b->ctx[p]->L];
+    cudaMemcpyAsync(V.u[b->ctx[p]->h64.cur], saved[p], V.nv * sizeof(cplx<double>), cudaMemcpyDeviceToDevice,
+                    b->stream);
+  }
+  cudaStreamSynchronize(b->stream);
+  for (auto* s : saved) cudaFree(s);
+  if (rc != MG_OK) return rc;
+  b->tc = btc;
+  b->bpsm = bb;
+  if (tc_out) *tc_out = btc;
+  if (bpsm_out) *bpsm_out = bb;
+  if (best_ms) *best_ms = best;
+  (void)sms;
+  return MG_OK;
+}
+
+long long mg_batch_launches(const mg_batch* b) { return b ? b->launches : -1; }
+
+const char* mg_batch_last_error(const mg_batch* b) { return b ? b->errmsg.c_str() : ""; }
+
+}  // extern "C"

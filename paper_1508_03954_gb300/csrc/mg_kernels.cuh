@@ -94,6 +94,8 @@ struct SweepArgs {
   int hb;           // variant hierarchical basis (mask c-points)
   int hier;         // transfer (id - P I)
   int varphi;       // per-cell shift (table holds K only)
+  int first;        // fine: U is zero and nothing is pending (first inner cycle)
+  int ntiles;       // tiles of the level (last-tile norm reduction)
   int tiles[3];     // tiles per axis
   const cplx<R>* u;       // fine: pending U; coarse: materialised u_l
   const cplx<R>* c;       // fine: pending corr on level l-1 (nullptr = none)
@@ -289,10 +291,25 @@ __device__ __forceinline__ cplx<R> diag_phi(const int* bc, const R* s_phi, const
   return acc;
 }
 
+// Loads of arrays that other blocks of the same launch may have written
+// (persistent launches) bypass L1.
+template <typename T> __device__ __forceinline__ T ldcg_(const T* p) { return __ldcg(p); }
+template <> __device__ __forceinline__ cplx<double> ldcg_(const cplx<double>* p) {
+  const double2 v = __ldcg(reinterpret_cast<const double2*>(p));
+  return cplx<double>{v.x, v.y};
+}
+template <> __device__ __forceinline__ cplx<float> ldcg_(const cplx<float>* p) {
+  const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+  return cplx<float>{v.x, v.y};
+}
+
+// One tile of the sweep (see TileGeom); `tile` indexes the tiles of the
+// level with x fastest.
 template <typename R, int D, int TC, int NTHR>
-__global__ void __launch_bounds__(NTHR) sweep_kernel(const SweepArgs<R> A) {
+__device__ __forceinline__ void sweep_tile(const SweepArgs<R>& A, int tile_index,
+                                           unsigned char* smem_raw, double* s_red) {
   using G = TileGeom<D, TC>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __syncthreads();  // a previous tile of this block may still read shared memory
   cplx<R>* s_u = reinterpret_cast<cplx<R>*>(smem_raw);
   cplx<R>* s_h = s_u + G::NU;       // uhat
   cplx<R>* s_du = s_h + G::NU;
@@ -301,12 +318,11 @@ __global__ void __launch_bounds__(NTHR) sweep_kernel(const SweepArgs<R> A) {
   cplx<R>* s_coef = s_c + G::NC;
   R* s_phi = reinterpret_cast<R*>(s_coef + G::NT * G::NS);
   cplx<R>* s_hc = reinterpret_cast<cplx<R>*>(s_phi + IPow<G::NCELL, D>::v);
-  __shared__ double s_red[NTHR / 32];
 
   const int n = A.n, N = n + 1, nc = n / 3;
   int tile[3] = {0, 0, 0};
   {
-    int t = blockIdx.x;
+    int t = tile_index;
     tile[0] = t % A.tiles[0];
     t /= A.tiles[0];
     if (D > 1) { tile[1] = t % A.tiles[1]; t /= A.tiles[1]; }
@@ -319,7 +335,7 @@ __global__ void __launch_bounds__(NTHR) sweep_kernel(const SweepArgs<R> A) {
   // stencil rows
   for (int i = threadIdx.x; i < G::NT * G::NS; i += NTHR) s_coef[i] = A.coef[i];
   // pending coarse correction
-  const bool use_c = A.fine && A.c != nullptr;
+  const bool use_c = A.fine && !A.first && A.c != nullptr;
   if (use_c) {
     for (int t = threadIdx.x; t < G::NC; t += NTHR) {
       int q[3];
@@ -333,7 +349,7 @@ __global__ void __launch_bounds__(NTHR) sweep_kernel(const SweepArgs<R> A) {
         gi += (long long)cc * st;
         st *= (nc + 1);
       }
-      s_c[t] = in ? A.c[gi] : cz<R>();
+      s_c[t] = in ? ldcg_(A.c + gi) : cz<R>();
     }
   }
   if (A.varphi) {
@@ -374,8 +390,8 @@ __global__ void __launch_bounds__(NTHR) sweep_kernel(const SweepArgs<R> A) {
       st *= N;
     }
     cplx<R> v = cz<R>();
-    if (inner) {
-      v = A.u[gi];
+    if (inner && !(A.fine && A.first)) {
+      v = ldcg_(A.u + gi);
       if (use_c) {
         // P c: corners of the coarse cell containing g
 #pragma unroll
@@ -474,7 +490,7 @@ __global__ void __launch_bounds__(NTHR) sweep_kernel(const SweepArgs<R> A) {
         hu = hu - mass_phi<R, D, TC>(s_u, pb, bc, s_phi, s_hc);
         dg = dg - diag_phi<R, D, TC>(bc, s_phi, s_hc);
       }
-      cplx<R> r = A.b[gi] - hu;
+      cplx<R> r = ldcg_(A.b + gi) - hu;
       du = A.varphi ? cdiv(A.omega * r, dg) : A.omd[ty] * r;
       if (A.fine && owned) nrm += (double)r.x * (double)r.x + (double)r.y * (double)r.y;
     }
@@ -507,7 +523,7 @@ __global__ void __launch_bounds__(NTHR) sweep_kernel(const SweepArgs<R> A) {
 #pragma unroll
         for (int k = 0; k < G::NS; ++k) hu = cfma(cf[k], s_h[pb + soff[k]], hu);
         if (A.varphi) hu = hu - mass_phi<R, D, TC>(s_h, pb, bc, s_phi, s_hc);
-        rh = A.b[gi] - hu;
+        rh = ldcg_(A.b + gi) - hu;
       }
       s_rh[t] = rh;
     }
@@ -616,9 +632,16 @@ __global__ void __launch_bounds__(NTHR) sweep_kernel(const SweepArgs<R> A) {
     }
   }
 
-  if (A.fine) {
-    block_norm_finish<NTHR>(nrm, s_red, A.partial, A.ticket, A.norm2, gridDim.x);
+  if (A.fine && A.norm2 != nullptr) {
+    block_norm_finish_tile<NTHR>(nrm, s_red, A.partial, A.ticket, A.norm2, tile_index, A.ntiles);
   }
+}
+
+template <typename R, int D, int TC, int NTHR>
+__global__ void __launch_bounds__(NTHR) sweep_kernel(const SweepArgs<R> A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double s_red[NTHR / 32];
+  sweep_tile<R, D, TC, NTHR>(A, blockIdx.x, smem_raw, s_red);
 }
 
 // ---------------------------------------------------------------------------

@@ -29,7 +29,9 @@ EXPORTS = ["mg_create", "mg_destroy", "mg_set_stream", "mg_set_rhs", "mg_set_sol
            "mg_get_solution", "mg_cycle", "mg_residual_norm", "mg_solve", "mg_set_precision",
            "mg_fmg", "mg_omega_scheme", "mg_get_level", "mg_set_timing", "mg_get_stats",
            "mg_set_trace", "mg_get_trace", "mg_set_k2", "mg_set_rhs_vector", "mg_sample",
-           "mg_set_rhs_samples", "mg_adjoint_grad", "mg_residual_noalloc", "mg_last_error"]
+           "mg_set_rhs_samples", "mg_adjoint_grad", "mg_residual_noalloc", "mg_batch_create",
+           "mg_batch_destroy", "mg_batch_get_ctx", "mg_batch_set_stream", "mg_batch_solve",
+           "mg_batch_autotune", "mg_batch_launches", "mg_batch_last_error", "mg_last_error"]
 
 
 class MgC128(ctypes.Structure):
@@ -86,6 +88,17 @@ def load(path: str | None = None):
         "mg_set_rhs_samples": (ip, [vp, ip, ctypes.POINTER(dp), pc]),
         "mg_adjoint_grad": (ip, [vp, vp, vp, MgC128, vp, vp]),
         "mg_get_trace": (ip, [vp, vp, ip, ip]),
+        "mg_batch_create": (ip, [ip, ctypes.POINTER(ip), ctypes.POINTER(ip), ctypes.POINTER(ctypes.POINTER(dp)),
+                                 ctypes.POINTER(dp), ctypes.POINTER(dp), ctypes.POINTER(vp)]),
+        "mg_batch_destroy": (None, [vp]),
+        "mg_batch_get_ctx": (ip, [vp, ip, ctypes.POINTER(vp)]),
+        "mg_batch_set_stream": (ip, [vp, vp]),
+        "mg_batch_solve": (ip, [vp, ip, ctypes.POINTER(pc), ip, dp, ip, ip, ctypes.POINTER(ip),
+                                ctypes.POINTER(ip), ctypes.POINTER(dp)]),
+        "mg_batch_autotune": (ip, [vp, ip, ctypes.POINTER(pc), ip, ip, ctypes.POINTER(ip), ctypes.POINTER(ip),
+                                   ctypes.POINTER(dp)]),
+        "mg_batch_launches": (ctypes.c_longlong, [vp]),
+        "mg_batch_last_error": (ctypes.c_char_p, [vp]),
         "mg_last_error": (ctypes.c_char_p, [vp]),
     }
     for name, (res, args) in sig.items():
@@ -132,6 +145,20 @@ def omega_scheme(scheme, omega_s, depth, iter_n=1, l_grid=0):
 class Solver:
     """One solver context (mg_create .. mg_destroy)."""
 
+    @classmethod
+    def wrap(cls, handle, d, depth, owner):
+        """A view of a context owned by someone else (a batch)."""
+        self = cls.__new__(cls)
+        self.d, self.depth = d, depth
+        self.n = 3 ** depth
+        self.shape = (self.n + 1,) * d
+        self.nv = (self.n + 1) ** d
+        self._h = None  # never destroyed through this view
+        self._view = handle
+        self._owner = owner
+        self._L = load()
+        return self
+
     def __init__(self, d, depth, k2_field, theta, layer_width):
         L = load()
         self.d, self.depth = d, depth
@@ -147,17 +174,19 @@ class Solver:
         if rc != MG_OK:
             raise MgError(rc, L.mg_last_error(None).decode())
         self._h = h
+        self._view = h
         self._L = L
 
     # -- helpers
     def _check(self, rc, what):
         if rc not in (MG_OK,):
-            raise MgError(rc, f"{what}: {self._L.mg_last_error(self._h).decode()}")
+            raise MgError(rc, f"{what}: {self._L.mg_last_error(self._view).decode()}")
 
     def close(self):
         if getattr(self, "_h", None):
             self._L.mg_destroy(self._h)
             self._h = None
+            self._view = None
 
     def __del__(self):
         try:
@@ -167,37 +196,37 @@ class Solver:
 
     # -- API
     def set_stream(self, stream_handle):
-        self._check(self._L.mg_set_stream(self._h, ctypes.c_void_p(stream_handle)), "mg_set_stream")
+        self._check(self._L.mg_set_stream(self._view, ctypes.c_void_p(stream_handle)), "mg_set_stream")
 
     def set_rhs(self, f):
         p, dev, _keep = _ptr(f, self.nv)
-        self._check(self._L.mg_set_rhs(self._h, p, dev), "mg_set_rhs")
+        self._check(self._L.mg_set_rhs(self._view, p, dev), "mg_set_rhs")
 
     def set_solution(self, u):
         p, dev, _keep = _ptr(u, self.nv)
-        self._check(self._L.mg_set_solution(self._h, p, dev), "mg_set_solution")
+        self._check(self._L.mg_set_solution(self._view, p, dev), "mg_set_solution")
 
     def get_solution(self, out=None):
         if out is None:
             out = np.empty(self.shape, dtype=np.complex128)
         p, dev, _keep = _ptr(out, self.nv)
-        self._check(self._L.mg_get_solution(self._h, p, dev), "mg_get_solution")
+        self._check(self._L.mg_get_solution(self._view, p, dev), "mg_get_solution")
         return out
 
     def get_level(self, level, which):
         n = 3 ** level
         out = np.empty(((n + 1),) * self.d, dtype=np.complex128)
-        rc = self._L.mg_get_level(self._h, level, which, out.ctypes.data_as(ctypes.c_void_p), 0)
+        rc = self._L.mg_get_level(self._view, level, which, out.ctypes.data_as(ctypes.c_void_p), 0)
         self._check(rc, "mg_get_level")
         return out
 
     def cycle(self, variant, omega, transfer):
-        self._check(self._L.mg_cycle(self._h, variant, _omega_array(omega, self.depth), transfer),
+        self._check(self._L.mg_cycle(self._view, variant, _omega_array(omega, self.depth), transfer),
                     "mg_cycle")
 
     def residual_norm(self):
         a, r = ctypes.c_double(), ctypes.c_double()
-        self._check(self._L.mg_residual_norm(self._h, ctypes.byref(a), ctypes.byref(r)),
+        self._check(self._L.mg_residual_norm(self._view, ctypes.byref(a), ctypes.byref(r)),
                     "mg_residual_norm")
         return a.value, r.value
 
@@ -205,22 +234,22 @@ class Solver:
         """Returns (status, cycles_done, rel_res); MG_DIVERGED and
         MG_NOT_CONVERGED are returned, not raised."""
         n, rel = ctypes.c_int(), ctypes.c_double()
-        rc = self._L.mg_solve(self._h, variant, _omega_array(omega, self.depth), transfer,
+        rc = self._L.mg_solve(self._view, variant, _omega_array(omega, self.depth), transfer,
                               float(tol), int(max_cycles), ctypes.byref(n), ctypes.byref(rel))
         if rc not in (MG_OK, MG_DIVERGED, MG_NOT_CONVERGED):
             self._check(rc, "mg_solve")
         return rc, n.value, rel.value
 
     def set_precision(self, precision, inner_cycles):
-        self._check(self._L.mg_set_precision(self._h, precision, inner_cycles), "mg_set_precision")
+        self._check(self._L.mg_set_precision(self._view, precision, inner_cycles), "mg_set_precision")
 
     def set_timing(self, enable):
-        self._check(self._L.mg_set_timing(self._h, 1 if enable else 0), "mg_set_timing")
+        self._check(self._L.mg_set_timing(self._view, 1 if enable else 0), "mg_set_timing")
 
     def get_stats(self):
         """(kernel launches, timed fine sweeps, their device ms) since the last call."""
         n, k, ms = ctypes.c_longlong(), ctypes.c_int(), ctypes.c_double()
-        self._check(self._L.mg_get_stats(self._h, ctypes.byref(n), ctypes.byref(k), ctypes.byref(ms)),
+        self._check(self._L.mg_get_stats(self._view, ctypes.byref(n), ctypes.byref(k), ctypes.byref(ms)),
                     "mg_get_stats")
         return n.value, k.value, ms.value
 
@@ -228,12 +257,12 @@ class Solver:
         a = np.ascontiguousarray(np.asarray(k2, dtype=np.float64))
         if a.size != self.nv:
             raise ValueError(f"k2 needs {self.nv} values")
-        self._check(self._L.mg_set_k2(self._h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+        self._check(self._L.mg_set_k2(self._view, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
                     "mg_set_k2")
 
     def set_rhs_vector(self, b):
         p, dev, _keep = _ptr(b, self.nv)
-        self._check(self._L.mg_set_rhs_vector(self._h, p, dev), "mg_set_rhs_vector")
+        self._check(self._L.mg_set_rhs_vector(self._view, p, dev), "mg_set_rhs_vector")
 
     @staticmethod
     def _samples(xyz, w):
@@ -248,13 +277,13 @@ class Solver:
         """s = sum_q w_q u(x_q); xyz shape (npts, d) with x first."""
         xyz, wa, m = self._samples(xyz, w)
         out = MgC128()
-        self._check(self._L.mg_sample(self._h, m, xyz.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), wa,
+        self._check(self._L.mg_sample(self._view, m, xyz.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), wa,
                                       ctypes.byref(out)), "mg_sample")
         return complex(out.re, out.im)
 
     def set_rhs_samples(self, xyz, w):
         xyz, wa, m = self._samples(xyz, w)
-        self._check(self._L.mg_set_rhs_samples(self._h, m, xyz.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+        self._check(self._L.mg_set_rhs_samples(self._view, m, xyz.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                                wa), "mg_set_rhs_samples")
 
     def adjoint_grad(self, u, lam, s, dJdV=None, dJdf=None):
@@ -270,18 +299,18 @@ class Solver:
                 if not (t.is_cuda and t.is_contiguous() and t.numel() == self.nv):
                     raise ValueError("gradient outputs must be contiguous float64 CUDA tensors")
                 outs.append(ctypes.c_void_p(t.data_ptr()))
-        self._check(self._L.mg_adjoint_grad(self._h, ctypes.c_void_p(u.data_ptr()),
+        self._check(self._L.mg_adjoint_grad(self._view, ctypes.c_void_p(u.data_ptr()),
                                             ctypes.c_void_p(lam.data_ptr()),
                                             MgC128(float(np.real(s)), float(np.imag(s))), outs[0], outs[1]),
                     "mg_adjoint_grad")
 
     def set_trace(self, enable):
-        self._check(self._L.mg_set_trace(self._h, 1 if enable else 0), "mg_set_trace")
+        self._check(self._L.mg_set_trace(self._view, 1 if enable else 0), "mg_set_trace")
 
     def get_trace(self, fine_slots, chain_slots):
         """(fine, chain) uint64 arrays of shape (slots, 4): taken, ready, done (ns), SM."""
         out = np.zeros((fine_slots + chain_slots, 4), dtype=np.uint64)
-        self._check(self._L.mg_get_trace(self._h, out.ctypes.data_as(ctypes.c_void_p), fine_slots,
+        self._check(self._L.mg_get_trace(self._view, out.ctypes.data_as(ctypes.c_void_p), fine_slots,
                                          chain_slots), "mg_get_trace")
         return out[:fine_slots], out[fine_slots:]
 
@@ -301,19 +330,19 @@ class Solver:
         if not (norm2.is_cuda and norm2.dtype == torch.float64 and norm2.numel() >= 1):
             raise ValueError("norm2 must be a float64 CUDA tensor")
         rp = ctypes.c_void_p(r.data_ptr()) if r is not None else None
-        self._check(self._L.mg_residual_noalloc(self._h, ctypes.c_void_p(u.data_ptr()),
+        self._check(self._L.mg_residual_noalloc(self._view, ctypes.c_void_p(u.data_ptr()),
                                                 ctypes.c_void_p(b.data_ptr()), rp,
                                                 ctypes.c_void_p(norm2.data_ptr())),
                     "mg_residual_noalloc")
 
     def get_level_device(self, level, which, out):
         """Copies a per-level array into a caller-owned complex128 CUDA tensor."""
-        rc = self._L.mg_get_level(self._h, level, which, ctypes.c_void_p(out.data_ptr()), 1)
+        rc = self._L.mg_get_level(self._view, level, which, ctypes.c_void_p(out.data_ptr()), 1)
         self._check(rc, "mg_get_level")
         return out
 
     def fmg(self, variant, omega, transfer, cycles_per_stage):
-        self._check(self._L.mg_fmg(self._h, variant, _omega_array(omega, self.depth), transfer,
+        self._check(self._L.mg_fmg(self._view, variant, _omega_array(omega, self.depth), transfer,
                                    cycles_per_stage), "mg_fmg")
 
 
@@ -364,3 +393,73 @@ def mg_fmg(s, variant, omega, transfer, cycles_per_stage):
 
 def mg_omega_scheme(scheme, omega_s, depth, iter_n=1, l_grid=0):
     return omega_scheme(scheme, omega_s, depth, iter_n, l_grid)
+
+
+class Batch:
+    """Many 2D problems solved together (mg_batch_*)."""
+
+    def __init__(self, specs):
+        """specs: list of dicts with d, depth, k2 (constant field), theta, layer_width."""
+        L = load()
+        n = len(specs)
+        self._keep = [np.ascontiguousarray(np.asarray(sp["k2"], dtype=np.float64)) for sp in specs]
+        d = (ctypes.c_int * n)(*[sp["d"] for sp in specs])
+        dep = (ctypes.c_int * n)(*[sp["depth"] for sp in specs])
+        th = (ctypes.c_double * n)(*[sp["theta"] for sp in specs])
+        lw = (ctypes.c_double * n)(*[sp["layer_width"] for sp in specs])
+        kp = (ctypes.POINTER(ctypes.c_double) * n)(*[k.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+                                                      for k in self._keep])
+        h = ctypes.c_void_p()
+        rc = L.mg_batch_create(n, d, dep, kp, th, lw, ctypes.byref(h))
+        if rc != MG_OK:
+            raise MgError(rc, L.mg_last_error(None).decode())
+        self._h, self._L, self.n = h, L, n
+        self.depths = [sp["depth"] for sp in specs]
+        self.solvers = []
+        for p in range(n):
+            ch = ctypes.c_void_p()
+            L.mg_batch_get_ctx(h, p, ctypes.byref(ch))
+            self.solvers.append(Solver.wrap(ch, specs[p]["d"], specs[p]["depth"], self))
+
+    def _om(self, omegas):
+        arrs = [_omega_array(omegas[p], self.depths[p]) for p in range(self.n)]
+        self._om_keep = arrs
+        return (ctypes.POINTER(MgC128) * self.n)(*[ctypes.cast(a, ctypes.POINTER(MgC128)) for a in arrs])
+
+    def _check(self, rc, what):
+        if rc != MG_OK:
+            raise MgError(rc, f"{what}: {self._L.mg_batch_last_error(self._h).decode()}")
+
+    def set_stream(self, stream_handle):
+        self._check(self._L.mg_batch_set_stream(self._h, ctypes.c_void_p(stream_handle)), "mg_batch_set_stream")
+
+    def solve(self, variant, omegas, transfer, tol, max_outer, inner_cycles):
+        """Returns (status[n], inner cycles[n], rel_res[n])."""
+        st = (ctypes.c_int * self.n)()
+        cy = (ctypes.c_int * self.n)()
+        rl = (ctypes.c_double * self.n)()
+        rc = self._L.mg_batch_solve(self._h, variant, self._om(omegas), transfer, float(tol), int(max_outer),
+                                    int(inner_cycles), st, cy, rl)
+        self._check(rc, "mg_batch_solve")
+        return list(st), list(cy), list(rl)
+
+    def autotune(self, variant, omegas, transfer, inner_cycles):
+        tc, bp, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        rc = self._L.mg_batch_autotune(self._h, variant, self._om(omegas), transfer, int(inner_cycles),
+                                       ctypes.byref(tc), ctypes.byref(bp), ctypes.byref(ms))
+        self._check(rc, "mg_batch_autotune")
+        return tc.value, bp.value, ms.value
+
+    def launches(self):
+        return self._L.mg_batch_launches(self._h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.mg_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

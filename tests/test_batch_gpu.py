@@ -1,0 +1,119 @@
+"""Batched form: many 2D problems of uneven depth in one persistent launch
+per outer defect-correction step.  Every batched solution is checked with
+the FP64 oracle's own residual; the configured indefinite problems that
+diverge must be reported per problem without disturbing the others."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1508_03954_gb300 import build as B
+from paper_1508_03954_gb300 import mg
+from paper_1508_03954_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    B.build()
+    mg.load()
+
+
+def _omegas(depths):
+    return [O.omega_scheme(O.EXP, 0.6, L) for L in depths]
+
+
+def _oracle_rel(prob, u, u0=None):
+    o = O.Hierarchy(2, prob["depth"], prob["k2"], prob["theta"], prob["layer_width"])
+    o.set_rhs_nodal(prob["f"])
+    r = np.linalg.norm(o.residual(u))
+    r0 = np.linalg.norm(o.residual(np.zeros_like(u) if u0 is None else u0))
+    return r / r0
+
+
+def test_small_batch_matches_oracle_residual_and_individual_solves():
+    specs = W.config4_specs(8)
+    probs = [W.definite(W.config4_problem(dict(sp, depth=[2, 3, 4, 3][i % 4]))) for i, sp in enumerate(specs)]
+    bt = mg.Batch(probs)
+    for p, pr in enumerate(probs):
+        bt.solvers[p].set_rhs(pr["f"])
+    st, cyc, rel = bt.solve(mg.MG_ADD, _omegas([p["depth"] for p in probs]), mg.MG_DLINEAR, 1e-10, 200, 4)
+    assert all(s == mg.MG_OK for s in st), st
+    for p, pr in enumerate(probs):
+        u = bt.solvers[p].get_solution()
+        orel = _oracle_rel(pr, u)
+        assert orel <= 1.01e-10 and abs(orel - rel[p]) <= 1e-3 * orel + 1e-15, (p, orel, rel[p])
+    # the single-problem refinement form reaches the same solution
+    for p in (0, 3):
+        pr = probs[p]
+        s = mg.Solver(2, pr["depth"], pr["k2"], pr["theta"], pr["layer_width"])
+        s.set_rhs(pr["f"])
+        s.set_precision(mg.MG_C64_REFINE, 4)
+        st1, _, rel1 = s.solve(mg.MG_ADD, O.omega_scheme(O.EXP, 0.6, pr["depth"]), mg.MG_DLINEAR, 1e-10, 2000)
+        assert st1 == mg.MG_OK
+        ub, us = bt.solvers[p].get_solution(), s.get_solution()
+        assert np.linalg.norm(ub - us) <= 1e-8 * np.linalg.norm(us)
+    bt.close()
+
+
+def test_divergent_problems_are_reported_per_problem():
+    specs = W.config4_specs(6)
+    probs = []
+    for i, sp in enumerate(specs):
+        pr = W.config4_problem(dict(sp, depth=3, k=40.0 if i % 2 else sp["k"]))
+        probs.append(pr if i % 2 else W.definite(pr))  # odd: indefinite k = 40
+    bt = mg.Batch(probs)
+    for p, pr in enumerate(probs):
+        bt.solvers[p].set_rhs(pr["f"])
+    st, _, rel = bt.solve(mg.MG_ADD, _omegas([3] * 6), mg.MG_DLINEAR, 1e-10, 300, 4)
+    for p in range(6):
+        if p % 2 == 0:
+            assert st[p] == mg.MG_OK and _oracle_rel(probs[p], bt.solvers[p].get_solution()) <= 1.01e-10
+        else:
+            assert st[p] in (mg.MG_DIVERGED, mg.MG_NOT_CONVERGED)
+    bt.close()
+
+
+def test_autotune_keeps_solutions_and_picks_a_candidate():
+    specs = W.config4_specs(4)
+    probs = [W.definite(W.config4_problem(dict(sp, depth=4))) for sp in specs]
+    bt = mg.Batch(probs)
+    rng = np.random.default_rng(1)
+    u0 = []
+    for p, pr in enumerate(probs):
+        bt.solvers[p].set_rhs(pr["f"])
+        u = W.random_complex(2, 4, 100 + p)
+        O.zero_boundary(u)
+        bt.solvers[p].set_solution(u)
+        u0.append(u)
+    om = _omegas([4] * 4)
+    tc, bp, ms = bt.autotune(mg.MG_ADD, om, mg.MG_DLINEAR, 4)
+    assert tc in (4, 8) and bp in (2, 4, 8) and ms > 0
+    for p in range(4):
+        np.testing.assert_array_equal(bt.solvers[p].get_solution(), u0[p])
+    st, _, _ = bt.solve(mg.MG_ADD, om, mg.MG_DLINEAR, 1e-9, 200, 4)
+    assert all(s == mg.MG_OK for s in st)
+    for p in range(4):
+        assert _oracle_rel(probs[p], bt.solvers[p].get_solution(), u0[p]) <= 1.01e-9
+    bt.close()
+
+
+def test_config4_full_batch_definite_companions():
+    """256 problems of depth 4-6 (about 51 M fine unknowns); sampled oracle
+    checks on the depth-4 problems."""
+    specs = W.config4_specs(256)
+    probs = [W.definite(W.config4_problem(sp)) for sp in specs]
+    bt = mg.Batch(probs)
+    for p, pr in enumerate(probs):
+        bt.solvers[p].set_rhs(pr["f"])
+    om = _omegas([p["depth"] for p in probs])
+    bt.autotune(mg.MG_ADD, om, mg.MG_DLINEAR, 4)
+    st, cyc, rel = bt.solve(mg.MG_ADD, om, mg.MG_DLINEAR, 1e-8, 300, 4)
+    assert all(s == mg.MG_OK for s in st), [i for i, s in enumerate(st) if s != mg.MG_OK]
+    assert max(rel) <= 1e-8
+    d4 = [p for p, pr in enumerate(probs) if pr["depth"] == 4][:4]
+    for p in d4:
+        assert _oracle_rel(probs[p], bt.solvers[p].get_solution()) <= 1.01e-8
+    bt.close()
