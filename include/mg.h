@@ -115,6 +115,11 @@ int mg_cycle(mg_ctx* ctx, int variant, const mg_c128* omega_per_level, int trans
  * regular grid the h-weighted norm gives the same ratio).  Synchronising. */
 int mg_residual_norm(mg_ctx* ctx, double* abs_l2, double* rel_l2);
 
+/* Residual norm of the iterate that entered the last complex128 cycle, as
+ * fused into that cycle's finest-level sweep (no extra pass); rel_l2 is -1
+ * when no reference residual exists yet.  Synchronising. */
+int mg_last_cycle_norm(mg_ctx* ctx, double* abs_l2, double* rel_l2);
+
 /* Runs cycles until the relative residual is <= tol (MG_OK), max_cycles
  * were run (MG_NOT_CONVERGED) or the iteration diverged (MG_DIVERGED).
  * With precision MG_C128 every cycle is the plain complex128 cycle; with

@@ -17,6 +17,7 @@
 #include "mg.h"
 #include "mg_kernels.cuh"
 #include "mg_sweep2d.cuh"
+#include "mg_sweep3d.cuh"
 #include "mg_persist.cuh"
 #include "mg_adjoint.cuh"
 #include <map>
@@ -63,7 +64,9 @@ struct Hier {
     R* phic = nullptr;
     cplx<R>* hcell = nullptr;
     std::vector<cd> diag;     // D per vertex type (constant shift)
-    unsigned realrow = 0;     // bit t: stencil row of type t is real
+    unsigned realrow = 0;     // bit t: stencil row of type t is real (2D types)
+    unsigned long long realrow3 = 0;  // same for the 64 3D types
+    bool g3ok = false;        // 3D Galerkin-row tables available
     // 2D FP64 path: Galerkin rows of G_{l-1} = R H_l P per coarse row class
     bool gok = false;
     int* order8 = nullptr;      // fine tiles (8 coarse cells) by decreasing cost
@@ -86,9 +89,9 @@ struct Hier {
   struct ChainPlan {
     std::vector<double> key;
     mg::ChainItem* items = nullptr;
-    mg::Sweep2Args* s2 = nullptr;
-    mg::ProlongArgs* pr = nullptr;
-    mg::CorrArgs* co = nullptr;
+    mg::Sweep2Args<R>* s2 = nullptr;
+    mg::ProlongArgs<R>* pr = nullptr;
+    mg::CorrArgs<R>* co = nullptr;
     int nitems = 0, grid = 0;
   };
   std::vector<ChainPlan> chains;
@@ -355,12 +358,52 @@ int build_hier(mg_ctx* c, Hier<R>& H) {
     V.diag.resize(NT);
     for (int t = 0; t < NT; ++t) V.diag[t] = Hh[(size_t)t * NS + NS / 2];
     V.realrow = 0;
-    for (int t = 0; t < NT && t < 32; ++t) {
+    V.realrow3 = 0;
+    for (int t = 0; t < NT; ++t) {
       bool re = true;
       for (int k = 0; k < NS; ++k) re = re && Hh[(size_t)t * NS + k].imag() == 0.0;
-      if (re) V.realrow |= 1u << t;
+      if (re && t < 32) V.realrow |= 1u << t;
+      if (re) V.realrow3 |= 1ull << t;
     }
-    if (std::is_same<R, double>::value && d == 2 && !H.varphi && V.n / 3 + 1 >= 200) {
+    if (d == 3 && !H.varphi && l > 1) {
+      std::vector<std::array<cd, 6>> rows;
+      galerkin_rows_1d(V.n, rot, c->theta, rows);
+      std::vector<std::array<cd, 6>> cls;
+      std::vector<uint8_t> gt(rows.size(), 0);
+      bool ok = true;
+      for (size_t ci = 1; ci + 1 < rows.size() && ok; ++ci) {
+        size_t k = 0;
+        while (k < cls.size() && cls[k] != rows[ci]) ++k;
+        if (k == cls.size()) {
+          if ((int)cls.size() == mg::kMaxG3) { ok = false; break; }
+          cls.push_back(rows[ci]);
+        }
+        gt[ci] = (uint8_t)k;
+      }
+      if (ok) {
+        const int G = mg::kMaxG3;
+        std::vector<cd> gc((size_t)G * G * G * 27, cd(0));
+        for (size_t gz = 0; gz < cls.size(); ++gz)
+          for (size_t gy = 0; gy < cls.size(); ++gy)
+            for (size_t gx = 0; gx < cls.size(); ++gx)
+              for (int k = 0; k < 27; ++k) {
+                const int dx = k % 3, dy = (k / 3) % 3, dz = k / 9;
+                const auto& X = cls[gx];
+                const auto& Y = cls[gy];
+                const auto& Zr = cls[gz];
+                gc[(gx + G * (gy + G * gz)) * 27 + k] =
+                    X[dx] * Y[3 + dy] * Zr[3 + dz] + X[3 + dx] * Y[dy] * Zr[3 + dz] +
+                    X[3 + dx] * Y[3 + dy] * Zr[dz] - phi0 * X[3 + dx] * Y[3 + dy] * Zr[3 + dz];
+              }
+        auto gcd = to_dev_type<R>(gc);
+        if ((rc = dalloc(c, H, (void**)&V.gtyp, gt.size())) != MG_OK) return rc;
+        if ((rc = dalloc(c, H, (void**)&V.gcoef, gcd.size() * sizeof(cplx<R>))) != MG_OK) return rc;
+        MG_CUDA(c, cudaMemcpy(V.gtyp, gt.data(), gt.size(), cudaMemcpyHostToDevice));
+        MG_CUDA(c, cudaMemcpy(V.gcoef, gcd.data(), gcd.size() * sizeof(cplx<R>), cudaMemcpyHostToDevice));
+        V.g3ok = true;
+      }
+    }
+    if (d == 2 && !H.varphi && V.n / 3 + 1 >= 200) {
       // LPT order of the 8-coarse-cell tiles: interior vertices weighted by
       // the cost of their stencil row (complex rows cost about twice)
       const int nc = V.n / 3, tl = (nc + 8) / 8;
@@ -382,7 +425,7 @@ int build_hier(mg_ctx* c, Hier<R>& H) {
       if ((rc = dalloc(c, H, (void**)&V.order8, order.size() * sizeof(int))) != MG_OK) return rc;
       MG_CUDA(c, cudaMemcpy(V.order8, order.data(), order.size() * sizeof(int), cudaMemcpyHostToDevice));
     }
-    if (std::is_same<R, double>::value && d == 2 && !H.varphi && l > 1) {
+    if (d == 2 && !H.varphi && l > 1) {
       // classes of 1D Galerkin rows along an axis (same on both axes)
       std::vector<std::array<cd, 6>> rows;
       galerkin_rows_1d(V.n, rot, c->theta, rows);
@@ -467,13 +510,13 @@ cudaError_t launch_sweep(cudaStream_t s, mg::SweepArgs<R>& A) {
   return cudaGetLastError();
 }
 
-template <int TC, int NTHR>
-cudaError_t launch_sweep2(cudaStream_t s, mg::Sweep2Args& A) {
+template <int TC, int NTHR, typename R>
+cudaError_t launch_sweep2(cudaStream_t s, mg::Sweep2Args<R>& A) {
   const int nc = A.n / 3;
   const int tiles = (nc + 1 + TC - 1) / TC;
   A.tiles_x = tiles;
-  constexpr size_t smem = mg::Tile2<TC>::smem_bytes;
-  auto kern = mg::sweep2_kernel<TC, NTHR>;
+  constexpr size_t smem = mg::Tile2<TC, R>::smem_bytes;
+  auto kern = mg::sweep2_kernel<TC, NTHR, R>;
   kern<<<tiles * tiles, NTHR, smem, s>>>(A);
   return cudaGetLastError();
 }
@@ -499,17 +542,25 @@ cudaError_t configure_kernels() {
   set((const void*)mg::sweep2_kernel<4, 128>, mg::Tile2<4>::smem_bytes);
   set((const void*)mg::sweep2_kernel<15, 256>, mg::Tile2<15>::smem_bytes);
   set((const void*)mg::sweep2p_kernel<8, 256>, mg::Tile2<8>::smem_bytes);
+  set((const void*)mg::sweep2p_kernel<8, 256, float>, mg::Tile2<8, float>::smem_bytes);
+  set((const void*)mg::sweep2_kernel<4, 128, float>, mg::Tile2<4, float>::smem_bytes);
+  set((const void*)mg::chain2_kernel<256, float>, mg::Tile2<4, float>::smem_bytes);
+  set((const void*)mg::sweep3_kernel<double, 6, 512>, mg::Tile3<double, 6>::smem_bytes);
+  set((const void*)mg::sweep3_kernel<double, 4, 256>, mg::Tile3<double, 4>::smem_bytes);
+  set((const void*)mg::sweep3_kernel<float, 7, 512>, mg::Tile3<float, 7>::smem_bytes);
+  set((const void*)mg::sweep3_kernel<float, 4, 256>, mg::Tile3<float, 4>::smem_bytes);
   set((const void*)mg::chain2_kernel<256>, mg::Tile2<4>::smem_bytes);
   static_assert(mg::Tile2<2>::smem_bytes <= mg::Tile2<4>::smem_bytes, "chain smem");
   if (e == cudaSuccess && dev < 64) done |= 1ull << dev;
   return e;
 }
 
-// 2D FP64 levels with a constant shift: the Galerkin-row sweep (level 1 has
+// 2D levels with a constant shift: the Galerkin-row sweep (level 1 has
 // no coarser level and uses the same kernel with has_coarse = 0).
-cudaError_t sweep2(mg_ctx* c, Hier<double>& H, int l, bool fine, int hb, int hier, const cd& om) {
+template <typename R>
+cudaError_t sweep2(mg_ctx* c, Hier<R>& H, int l, bool fine, int hb, int hier, const cd& om) {
   auto& V = H.lev[l];
-  mg::Sweep2Args A;
+  mg::Sweep2Args<R> A;
   std::memset(&A, 0, sizeof(A));
   A.n = V.n;
   A.fine = fine ? 1 : 0;
@@ -532,7 +583,7 @@ cudaError_t sweep2(mg_ctx* c, Hier<double>& H, int l, bool fine, int hb, int hie
   A.realjac = 0;
   for (size_t t = 0; t < V.diag.size() && t < 16; ++t) {
     const cd q = om / V.diag[t];
-    A.omd[t] = cplx<double>{q.real(), q.imag()};
+    A.omd[t] = cplx<R>{(R)q.real(), (R)q.imag()};
     if (q.imag() == 0.0) A.realjac |= 1u << t;
   }
   A.partial = H.partial;
@@ -546,18 +597,19 @@ cudaError_t sweep2(mg_ctx* c, Hier<double>& H, int l, bool fine, int hb, int hie
     cudaError_t e = cudaMemsetAsync(c->chain_ctr + 32, 0, sizeof(unsigned), c->stream);
     if (e != cudaSuccess) return e;
     const int grid = std::min(A.ntiles, 152 * std::max(1, c->fine_bpsm));
-    mg::sweep2p_kernel<8, 256><<<grid, 256, mg::Tile2<8>::smem_bytes, c->stream>>>(
+    mg::sweep2p_kernel<8, 256, R><<<grid, 256, mg::Tile2<8, R>::smem_bytes, c->stream>>>(
         A, V.order8, c->chain_ctr + 32, c->tracing ? c->trace : nullptr);
     return cudaGetLastError();
   }
   A.ntiles = ((nc + 4) / 4) * ((nc + 4) / 4);
-  return launch_sweep2<4, 128>(c->stream, A);
+  return launch_sweep2<4, 128, R>(c->stream, A);
 }
 
 // Arguments of a coarse level's sweep tile in the persistent chain (TC = 4).
-mg::Sweep2Args sweep2_args(Hier<double>& H, int l, int hb, int hier, const cd& om, int TC) {
+template <typename R>
+mg::Sweep2Args<R> sweep2_args(Hier<R>& H, int l, int hb, int hier, const cd& om, int TC) {
   auto& V = H.lev[l];
-  mg::Sweep2Args A;
+  mg::Sweep2Args<R> A;
   std::memset(&A, 0, sizeof(A));
   A.n = V.n;
   A.fine = 0;
@@ -578,7 +630,7 @@ mg::Sweep2Args sweep2_args(Hier<double>& H, int l, int hb, int hier, const cd& o
   A.coef = V.coefH;
   for (size_t t = 0; t < V.diag.size() && t < 16; ++t) {
     const cd q = om / V.diag[t];
-    A.omd[t] = cplx<double>{q.real(), q.imag()};
+    A.omd[t] = cplx<R>{(R)q.real(), (R)q.imag()};
     if (q.imag() == 0.0) A.realjac |= 1u << t;
   }
   const int nc = V.n / 3;
@@ -589,13 +641,14 @@ mg::Sweep2Args sweep2_args(Hier<double>& H, int l, int hb, int hier, const cd& o
 
 // Item list of the coarse chain of one cycle on levels 1..s-1 of a 2D FP64
 // hierarchy: sweeps of levels s-1 .. 1, then prolongations of levels 2 .. s-1.
-int build_chain2(mg_ctx* c, Hier<double>& H, int s, int hb, int hier, const cplx<double>* omega,
-                 const std::vector<double>& key, typename Hier<double>::ChainPlan** out) {
+template <typename R>
+int build_chain2(mg_ctx* c, Hier<R>& H, int s, int hb, int hier, const cplx<double>* omega,
+                 const std::vector<double>& key, typename Hier<R>::ChainPlan** out) {
   for (auto& cp : H.chains)
     if (cp.key == key) { *out = &cp; return MG_OK; }
   std::vector<mg::ChainItem> items;
-  std::vector<mg::Sweep2Args> s2;
-  std::vector<mg::ProlongArgs> pr;
+  std::vector<mg::Sweep2Args<R>> s2;
+  std::vector<mg::ProlongArgs<R>> pr;
   unsigned need = 0;
   for (int l = s - 1; l >= 1; --l) {
     const cplx<double> w = omega[l - 1 + (H.L - s)];
@@ -610,11 +663,11 @@ int build_chain2(mg_ctx* c, Hier<double>& H, int s, int hb, int hier, const cplx
   }
   // corr_{s-1} = sum_l P^{s-1-l} t_l in two stages: corr_{s-2} directly from
   // levels 1..s-2, then corr_{s-1} = t_{s-1} + P corr_{s-2}
-  std::vector<mg::CorrArgs> co;
+  std::vector<mg::CorrArgs<R>> co;
   const int top = s - 1;
   if (top >= mg::kMaxChainLevels) return fail(c, MG_ERR_INVALID, "hierarchy too deep for the chain");
-  auto add_corr = [&](int tgt, int lo, const cplx<double>* base) {
-    mg::CorrArgs ca;
+  auto add_corr = [&](int tgt, int lo, const cplx<R>* base) {
+    mg::CorrArgs<R> ca;
     std::memset(&ca, 0, sizeof(ca));
     ca.s = tgt;
     ca.lo = lo;
@@ -632,21 +685,21 @@ int build_chain2(mg_ctx* c, Hier<double>& H, int s, int hb, int hier, const cplx
   } else if (top == 2) {
     add_corr(2, 1, nullptr);
   }
-  typename Hier<double>::ChainPlan cp;
+  typename Hier<R>::ChainPlan cp;
   cp.key = key;
   cp.nitems = (int)items.size();
   MG_CUDA(c, cudaMalloc(&cp.items, std::max<size_t>(1, items.size()) * sizeof(mg::ChainItem)));
-  MG_CUDA(c, cudaMalloc(&cp.s2, std::max<size_t>(1, s2.size()) * sizeof(mg::Sweep2Args)));
-  MG_CUDA(c, cudaMalloc(&cp.pr, std::max<size_t>(1, pr.size()) * sizeof(mg::ProlongArgs)));
-  MG_CUDA(c, cudaMalloc(&cp.co, std::max<size_t>(1, co.size()) * sizeof(mg::CorrArgs)));
+  MG_CUDA(c, cudaMalloc(&cp.s2, std::max<size_t>(1, s2.size()) * sizeof(mg::Sweep2Args<R>)));
+  MG_CUDA(c, cudaMalloc(&cp.pr, std::max<size_t>(1, pr.size()) * sizeof(mg::ProlongArgs<R>)));
+  MG_CUDA(c, cudaMalloc(&cp.co, std::max<size_t>(1, co.size()) * sizeof(mg::CorrArgs<R>)));
   if (!co.empty())
-    MG_CUDA(c, cudaMemcpy(cp.co, co.data(), co.size() * sizeof(mg::CorrArgs), cudaMemcpyHostToDevice));
+    MG_CUDA(c, cudaMemcpy(cp.co, co.data(), co.size() * sizeof(mg::CorrArgs<R>), cudaMemcpyHostToDevice));
   if (!items.empty())
     MG_CUDA(c, cudaMemcpy(cp.items, items.data(), items.size() * sizeof(mg::ChainItem), cudaMemcpyHostToDevice));
   if (!s2.empty())
-    MG_CUDA(c, cudaMemcpy(cp.s2, s2.data(), s2.size() * sizeof(mg::Sweep2Args), cudaMemcpyHostToDevice));
+    MG_CUDA(c, cudaMemcpy(cp.s2, s2.data(), s2.size() * sizeof(mg::Sweep2Args<R>), cudaMemcpyHostToDevice));
   if (!pr.empty())
-    MG_CUDA(c, cudaMemcpy(cp.pr, pr.data(), pr.size() * sizeof(mg::ProlongArgs), cudaMemcpyHostToDevice));
+    MG_CUDA(c, cudaMemcpy(cp.pr, pr.data(), pr.size() * sizeof(mg::ProlongArgs<R>), cudaMemcpyHostToDevice));
   cp.grid = std::max(1, std::min(cp.nitems, 152 * std::min(MG_CHAIN_BPSM, std::max(1, c->chain_bpsm))));
   if (H.chains.size() >= 32) {
     cudaFree(H.chains.front().items);
@@ -660,10 +713,11 @@ int build_chain2(mg_ctx* c, Hier<double>& H, int s, int hb, int hier, const cplx
   return MG_OK;
 }
 
-cudaError_t launch_chain2(mg_ctx* c, const typename Hier<double>::ChainPlan& cp) {
+template <typename R>
+cudaError_t launch_chain2(mg_ctx* c, const typename Hier<R>::ChainPlan& cp) {
   cudaError_t e = cudaMemsetAsync(c->chain_ctr, 0, 2 * sizeof(unsigned), c->stream);
   if (e != cudaSuccess) return e;
-  mg::ChainArgs A;
+  mg::ChainArgs<R> A;
   A.items = cp.items;
   A.nitems = cp.nitems;
   A.s2 = cp.s2;
@@ -674,8 +728,67 @@ cudaError_t launch_chain2(mg_ctx* c, const typename Hier<double>::ChainPlan& cp)
   A.err = c->dev_err;
   A.spin_limit = c->spin_limit;
   A.trace = c->tracing ? c->trace + 4 * kTraceFine : nullptr;
-  mg::chain2_kernel<256><<<cp.grid, 256, mg::Tile2<4>::smem_bytes, c->stream>>>(A);
+  mg::chain2_kernel<256, R><<<cp.grid, 256, mg::Tile2<4, R>::smem_bytes, c->stream>>>(A);
   return cudaGetLastError();
+}
+
+// 3D levels with a constant shift: the z-marching Galerkin-row sweep.
+template <typename R, int TC, int NTHR>
+cudaError_t launch_sweep3(cudaStream_t s, mg::Sweep3Args<R>& A) {
+  const int nc = A.n / 3;
+  const int tl = (nc + 1 + TC - 1) / TC;
+  A.tiles_x = tl;
+  A.ntiles_xy = tl * tl;
+  // enough z-chunks for about four resident blocks per SM
+  const int nz = std::max(1, std::min(nc + 1, (2 * 152 + A.ntiles_xy - 1) / A.ntiles_xy));
+  A.zchunk = (nc + 1 + nz - 1) / nz;
+  A.nzchunks = (nc + 1 + A.zchunk - 1) / A.zchunk;
+  A.ntiles = A.ntiles_xy * A.nzchunks;
+  mg::sweep3_kernel<R, TC, NTHR><<<A.ntiles, NTHR, mg::Tile3<R, TC>::smem_bytes, s>>>(A);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t sweep3(mg_ctx* c, Hier<R>& H, int l, bool fine, int hb, int hier, const cd& om) {
+  auto& V = H.lev[l];
+  mg::Sweep3Args<R> A;
+  std::memset(&A, 0, sizeof(A));
+  A.n = V.n;
+  A.fine = fine ? 1 : 0;
+  A.first = 0;
+  A.has_coarse = l > 1 ? 1 : 0;
+  A.hb = hb;
+  A.hier = hier;
+  A.realrow = V.realrow3;
+  A.u = fine ? V.u[H.cur] : V.u[0];
+  A.c = (fine && l > 1) ? H.lev[l - 1].corr : nullptr;
+  A.b = V.b;
+  A.out = fine ? V.u[1 - H.cur] : V.t;
+  if (l > 1) {
+    A.b_coarse = H.lev[l - 1].b;
+    A.u_coarse = H.lev[l - 1].u[0];
+    A.gtyp = V.gtyp;
+    A.gcoef = V.gcoef;
+  }
+  A.typ = V.typ;
+  A.coef = V.coefH;
+  A.realjac = 0;
+  for (size_t t = 0; t < V.diag.size() && t < 64; ++t) {
+    const cd q = om / V.diag[t];
+    A.omd[t] = cplx<R>{(R)q.real(), (R)q.imag()};
+    if (q.imag() == 0.0) A.realjac |= 1ull << t;
+  }
+  A.partial = H.partial;
+  A.ticket = H.ticket;
+  A.norm2 = fine ? H.norm2 : nullptr;
+  const int nc = V.n / 3;
+  if constexpr (std::is_same<R, double>::value) {
+    if (nc + 1 >= 25) return launch_sweep3<double, 6, 512>(c->stream, A);
+    return launch_sweep3<double, 4, 256>(c->stream, A);
+  } else {
+    if (nc + 1 >= 25) return launch_sweep3<float, 7, 512>(c->stream, A);
+    return launch_sweep3<float, 4, 256>(c->stream, A);
+  }
 }
 
 template <typename R>
@@ -683,11 +796,13 @@ cudaError_t sweep(mg_ctx* c, Hier<R>& H, int l, bool fine, int s_active, int hb,
                   const cplx<double>* omega) {
   auto& V = H.lev[l];
   ++c->launches;
-  if constexpr (std::is_same<R, double>::value) {
-    if (c->d == 2 && !H.varphi && (l == 1 || V.gok)) {
-      const cplx<double> w = omega[l - 1 + (H.L - s_active)];
-      return sweep2(c, H, l, fine, hb, hier, cd(w.x, w.y));
-    }
+  if (c->d == 3 && !H.varphi && (l == 1 || V.g3ok)) {
+    const cplx<double> w = omega[l - 1 + (H.L - s_active)];
+    return sweep3(c, H, l, fine, hb, hier, cd(w.x, w.y));
+  }
+  if (c->d == 2 && !H.varphi && (l == 1 || V.gok)) {
+    const cplx<double> w = omega[l - 1 + (H.L - s_active)];
+    return sweep2<R>(c, H, l, fine, hb, hier, cd(w.x, w.y));
   }
   mg::SweepArgs<R> A;
   std::memset(&A, 0, sizeof(A));
@@ -761,7 +876,7 @@ cudaError_t enqueue_cycle_part(mg_ctx* c, Hier<R>& H, int s, int hb, int hier,
     *nkern = 1;
     return e;
   }
-  if constexpr (std::is_same<R, double>::value) {
+  {
     bool chain_ok = c->d == 2 && !H.varphi;
     for (int l = 2; l < s && chain_ok; ++l) chain_ok = H.lev[l].gok;
     if (chain_ok) {
@@ -770,11 +885,11 @@ cudaError_t enqueue_cycle_part(mg_ctx* c, Hier<R>& H, int s, int hb, int hier,
         key.push_back(omega[l].x);
         key.push_back(omega[l].y);
       }
-      typename Hier<double>::ChainPlan* cp = nullptr;
-      if (build_chain2(c, H, s, hb, hier, omega, key, &cp) != MG_OK) return cudaErrorUnknown;
+      typename Hier<R>::ChainPlan* cp = nullptr;
+      if (build_chain2<R>(c, H, s, hb, hier, omega, key, &cp) != MG_OK) return cudaErrorUnknown;
       *nkern = 1;
       ++c->launches;
-      return launch_chain2(c, *cp);
+      return launch_chain2<R>(c, *cp);
     }
   }
   for (int l = s - 1; l >= 1 && e == cudaSuccess; --l, ++*nkern) e = sweep(c, H, l, false, s, hb, hier, omega);
@@ -837,7 +952,7 @@ int run_cycle(mg_ctx* c, Hier<R>& H, int s, int hb, int hier, const cplx<double>
     for (auto& g : H.graphs)
       if (g.key == key) { ge = &g; break; }
     if (ge == nullptr) {
-      if constexpr (std::is_same<R, double>::value) {
+      {
         // plans allocate device tables: build them before capturing
         if (c->d == 2 && !H.varphi && s > 1) {
           std::vector<double> ck = {(double)s, (double)hb, (double)hier};
@@ -847,8 +962,8 @@ int run_cycle(mg_ctx* c, Hier<R>& H, int s, int hb, int hier, const cplx<double>
           }
           bool ok = true;
           for (int l = 2; l < s && ok; ++l) ok = H.lev[l].gok;
-          typename Hier<double>::ChainPlan* cp = nullptr;
-          if (ok && build_chain2(c, H, s, hb, hier, omega, ck, &cp) != MG_OK) return MG_ERR_OOM;
+          typename Hier<R>::ChainPlan* cp = nullptr;
+          if (ok && build_chain2<R>(c, H, s, hb, hier, omega, ck, &cp) != MG_OK) return MG_ERR_OOM;
         }
       }
       typename Hier<R>::GraphEntry ne;
@@ -1346,6 +1461,16 @@ int mg_get_trace(mg_ctx* c, unsigned long long* out, int fine_slots, int chain_s
   return MG_OK;
 }
 
+int mg_last_cycle_norm(mg_ctx* c, double* abs_l2, double* rel_l2) {
+  if (check_ctx(c)) return MG_ERR_INVALID;
+  MG_CUDA(c, cudaMemcpyAsync(c->host_norm, c->h64.norm2, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  MG_CUDA(c, cudaStreamSynchronize(c->stream));
+  const double r = std::sqrt(*c->host_norm);
+  if (abs_l2) *abs_l2 = r;
+  if (rel_l2) *rel_l2 = c->r0 > 0 ? r / c->r0 : -1.0;
+  return check_timeout(c);
+}
+
 int mg_set_timing(mg_ctx* c, int enable) {
   if (check_ctx(c)) return MG_ERR_INVALID;
   c->timing = enable != 0;
@@ -1604,7 +1729,7 @@ struct mg_batch {
   // plan (item list and argument tables) of the last solve configuration
   std::vector<double> key;
   mg::ChainItem* items = nullptr;
-  mg::SweepArgs<float>* sw = nullptr;
+  mg::Sweep2Args<float>* sw = nullptr;
   mg::ResArgs* res = nullptr;
   mg::UpdArgs* upd = nullptr;
   mg::CorrArgsF* co = nullptr;
@@ -1635,7 +1760,7 @@ int bfail(mg_batch* b, int code, const std::string& m) {
 
 template <int TC>
 size_t batch_smem() {
-  size_t a = mg::sweep_smem_bytes<float, 2, TC>(0), b2 = mg::sweep_smem_bytes<float, 2, 2>(0);
+  size_t a = mg::Tile2<TC, float>::smem_bytes, b2 = mg::Tile2<2, float>::smem_bytes;
   return a > b2 ? a : b2;
 }
 
@@ -1657,39 +1782,18 @@ void free_plan(mg_batch* b) {
   b->graph_key.clear();
 }
 
-// complex64 sweep arguments of level l of problem c (inner hierarchy)
-mg::SweepArgs<float> fsweep_args(mg_ctx* c, int l, bool fine, int k, int hb, int hier, const cd& om, int tc) {
+// complex64 sweep arguments of level l of problem c (inner hierarchy): the
+// Galerkin-row 2D tile; inner cycle k of an outer step (k = 0 starts from 0)
+mg::Sweep2Args<float> fsweep_args(mg_ctx* c, int l, bool fine, int k, int hb, int hier, const cd& om, int tc) {
   auto& E = c->h32;
+  mg::Sweep2Args<float> A = sweep2_args<float>(E, l, hb, hier, om, tc);
   auto& V = E.lev[l];
-  mg::SweepArgs<float> A;
-  std::memset(&A, 0, sizeof(A));
-  A.n = V.n;
   A.fine = fine ? 1 : 0;
   A.first = (fine && k == 0) ? 1 : 0;
-  A.has_coarse = l > 1 ? 1 : 0;
-  A.hb = hb;
-  A.hier = hier;
   A.u = fine ? V.u[k % 2] : V.u[0];
   A.c = (fine && l > 1) ? E.lev[l - 1].corr : nullptr;
-  A.b = V.b;
   A.out = fine ? V.u[(k + 1) % 2] : V.t;
-  if (l > 1) {
-    A.b_coarse = E.lev[l - 1].b;
-    A.u_coarse = E.lev[l - 1].u[0];
-  }
-  A.typ = V.typ;
-  A.coef = V.coefH;
-  A.hcell = V.hcell;
-  A.omega = cplx<float>{(float)om.real(), (float)om.imag()};
-  for (size_t t = 0; t < V.diag.size() && t < (size_t)mg::kMaxTypes; ++t) {
-    const cd q = om / V.diag[t];
-    A.omd[t] = cplx<float>{(float)q.real(), (float)q.imag()};
-  }
-  const int nc = V.n / 3, tl = (nc + 1 + tc - 1) / tc;
-  A.tiles[0] = tl;
-  A.tiles[1] = tl;
-  A.tiles[2] = 1;
-  A.ntiles = tl * tl;
+  A.norm2 = nullptr;
   return A;
 }
 
@@ -1698,7 +1802,7 @@ int build_batch_plan(mg_batch* b, int hb, int hier, const cplx<double>* const* o
   if (b->key == key && b->items) return MG_OK;
   free_plan(b);
   const int np = (int)b->ctx.size();
-  std::vector<mg::SweepArgs<float>> sw;
+  std::vector<mg::Sweep2Args<float>> sw;
   std::vector<mg::ResArgs> res;
   std::vector<mg::UpdArgs> upd;
   std::vector<mg::CorrArgsF> co;
@@ -1730,6 +1834,8 @@ int build_batch_plan(mg_batch* b, int hb, int hier, const cplx<double>* const* o
       for (int t = 0; t < r.nchunks; ++t) st.push_back({mg::kBRes, p, (int)res.size() - 1, t, 0});
       S.push_back(st);
     }
+    for (int l = 2; l <= L; ++l)
+      if (!E.lev[l].gok) return bfail(b, MG_ERR_INVALID, "a level has too many Galerkin row classes for the batch");
     for (int k = 0; k < m; ++k) {
       for (int l = L; l >= 1; --l) {
         const cplx<double> w = omega[p][l - 1];
@@ -1795,7 +1901,7 @@ int build_batch_plan(mg_batch* b, int hb, int hier, const cplx<double>* const* o
     return e;
   };
   MG_BCUDA(b, up((void**)&b->items, items.data(), items.size() * sizeof(mg::ChainItem)));
-  MG_BCUDA(b, up((void**)&b->sw, sw.data(), sw.size() * sizeof(mg::SweepArgs<float>)));
+  MG_BCUDA(b, up((void**)&b->sw, sw.data(), sw.size() * sizeof(mg::Sweep2Args<float>)));
   MG_BCUDA(b, up((void**)&b->res, res.data(), res.size() * sizeof(mg::ResArgs)));
   MG_BCUDA(b, up((void**)&b->upd, upd.data(), upd.size() * sizeof(mg::UpdArgs)));
   MG_BCUDA(b, up((void**)&b->co, co.data(), co.size() * sizeof(mg::CorrArgsF)));

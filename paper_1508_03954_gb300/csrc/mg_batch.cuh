@@ -41,19 +41,14 @@ struct UpdArgs {
   const cplx<float>* c;  // pending corr on level L-1 (may be null)
 };
 
-struct CorrArgsF {
-  int s, lo;
-  const cplx<float>* t[kMaxChainLevels];
-  const cplx<float>* base;
-  cplx<float>* out;
-};
+using CorrArgsF = CorrArgs<float>;
 
 constexpr int kBatchChunk = 1024;
 
 struct BatchArgs {
   const ChainItem* items;
   int nitems;
-  const SweepArgs<float>* sw;
+  const Sweep2Args<float>* sw;
   const ResArgs* res;
   const UpdArgs* upd;
   const CorrArgsF* co;
@@ -163,7 +158,7 @@ __global__ void __launch_bounds__(NTHR) batch2_kernel(const BatchArgs A) {
   __shared__ double s_red[NTHR / 32];
   __shared__ int s_item;
   __shared__ __align__(16) union U {
-    SweepArgs<float> sw;
+    Sweep2Args<float> sw;
     ResArgs res;
     UpdArgs upd;
     CorrArgsF co;
@@ -180,7 +175,7 @@ __global__ void __launch_bounds__(NTHR) batch2_kernel(const BatchArgs A) {
         case kBRes: copy_args<ResArgs, NTHR>(&s_a.res, A.res + it.args); break;
         case kBUpd: copy_args<UpdArgs, NTHR>(&s_a.upd, A.upd + it.args); break;
         case kBCorr: copy_args<CorrArgsF, NTHR>(&s_a.co, A.co + it.args); break;
-        default: copy_args<SweepArgs<float>, NTHR>(&s_a.sw, A.sw + it.args); break;
+        default: copy_args<Sweep2Args<float>, NTHR>(&s_a.sw, A.sw + it.args); break;
       }
       if (threadIdx.x == 0 && it.need > 0) wait_counter(A.done + it.prob, it.need, A.spin_limit, A.err);
     }
@@ -190,8 +185,8 @@ __global__ void __launch_bounds__(NTHR) batch2_kernel(const BatchArgs A) {
         case kBRes: res_chunk<NTHR>(s_a.res, it.tile, s_red); break;
         case kBUpd: upd_chunk<NTHR>(s_a.upd, it.tile); break;
         case kBCorr: corrf_chunk<NTHR>(s_a.co, it.tile); break;
-        case kBSweep: sweep_tile<float, 2, TC, NTHR>(s_a.sw, it.tile, smem_raw, s_red); break;
-        default: sweep_tile<float, 2, 2, NTHR>(s_a.sw, it.tile, smem_raw, s_red); break;
+        case kBSweep: sweep2_tile<TC, NTHR, float>(s_a.sw, it.tile, smem_raw, s_red); break;
+        default: sweep2_tile<2, NTHR, float>(s_a.sw, it.tile, smem_raw, s_red); break;
       }
     }
     __syncthreads();

@@ -34,11 +34,12 @@ struct ChainItem {
   unsigned need;  // items of this problem that must be complete first
 };
 
+template <typename R>
 struct ProlongArgs {
-  int n;                       // cells per axis of the level
-  const cplx<double>* t;       // T du of the level
-  const cplx<double>* cc;      // corr of the next coarser level
-  cplx<double>* out;           // corr of the level
+  int n;                  // cells per axis of the level
+  const cplx<R>* t;       // T du of the level
+  const cplx<R>* cc;      // corr of the next coarser level
+  cplx<R>* out;           // corr of the level
 };
 
 constexpr int kProlongChunk = 2048;  // vertices per prolongation item
@@ -48,20 +49,22 @@ constexpr int kProlongChunk = 2048;  // vertices per prolongation item
 // coarser level: on nested d-linear spaces P^k is exactly the interpolation
 // over the 3^k-refined cell.  base is corr_{lo-1} (or null).
 constexpr int kMaxChainLevels = 12;
+template <typename R>
 struct CorrArgs {
-  int s, lo;                               // target level (3^s cells), first level summed
-  const cplx<double>* t[kMaxChainLevels];  // t[l] for l = lo..s (index l)
-  const cplx<double>* base;                // corr_{lo-1} or null
-  cplx<double>* out;                       // corr_s
+  int s, lo;                          // target level (3^s cells), first level summed
+  const cplx<R>* t[kMaxChainLevels];  // t[l] for l = lo..s (index l)
+  const cplx<R>* base;                // corr_{lo-1} or null
+  cplx<R>* out;                       // corr_s
 };
 constexpr int kCorrChunk = 256;          // vertices per item
 
+template <typename R>
 struct ChainArgs {
   const ChainItem* items;
   int nitems;
-  const Sweep2Args* s2;
-  const ProlongArgs* pr;
-  const CorrArgs* co;
+  const Sweep2Args<R>* s2;
+  const ProlongArgs<R>* pr;
+  const CorrArgs<R>* co;
   unsigned* head;        // queue head, zero at launch
   unsigned* done;        // per-problem completion counters, zero at launch
   unsigned* err;         // set when a bounded wait gave up
@@ -87,36 +90,37 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
 }
 
 // corr_l = t_l + P corr_{l-1} on vertices [chunk*kProlongChunk, ...) of a 2D level
-template <int NTHR>
-__device__ __forceinline__ void prolong2_chunk(const ProlongArgs& A, int chunk) {
+template <int NTHR, typename R>
+__device__ __forceinline__ void prolong2_chunk(const ProlongArgs<R>& A, int chunk) {
   const int n = A.n, N = n + 1, Nc = n / 3 + 1;
   const long long total = (long long)N * N;
   const long long beg = (long long)chunk * kProlongChunk;
   for (long long i = beg + threadIdx.x; i < beg + kProlongChunk && i < total; i += NTHR) {
     const int gx = (int)(i % N), gy = (int)(i / N);
-    cplx<double> v = cz<double>();
+    cplx<R> v = cz<R>();
     if (gx > 0 && gx < n && gy > 0 && gy < n) {
       v = ldcg(A.t + i);
       const int cx = gx / 3, cy = gy / 3, ox = gx % 3, oy = gy % 3;
-      const cplx<double>* cp = A.cc + (long long)cy * Nc + cx;
-      const cplx<double> a = lerp2(w0(ox), ldcg(cp), w1(ox), ldcg(cp + (ox ? 1 : 0)));
-      const cplx<double> b = oy ? lerp2(w0(ox), ldcg(cp + Nc), w1(ox), ldcg(cp + Nc + (ox ? 1 : 0)))
-                                : cz<double>();
-      v = lerp2acc(v, w0(oy), a, w1(oy), b);
+      const cplx<R>* cp = A.cc + (long long)cy * Nc + cx;
+      const cplx<R> a = lerp2(w0<R>(ox), ldcg(cp), w1<R>(ox), ldcg(cp + (ox ? 1 : 0)));
+      const cplx<R> b = oy ? lerp2(w0<R>(ox), ldcg(cp + Nc), w1<R>(ox), ldcg(cp + Nc + (ox ? 1 : 0)))
+                                : cz<R>();
+      v = lerp2acc(v, w0<R>(oy), a, w1<R>(oy), b);
     }
     A.out[i] = v;
   }
 }
 
-// 1/3^k for k = 0..12 (interpolation weights without FP64 division)
-__device__ __forceinline__ double inv_pow3(int k) {
-  double r = 1.0;
-  for (int i = 0; i < k; ++i) r *= (1.0 / 3.0);
+// 1/3^k for k = 0..12 (interpolation weights without division)
+template <typename R>
+__device__ __forceinline__ R inv_pow3(int k) {
+  R r = R(1);
+  for (int i = 0; i < k; ++i) r *= (R(1) / R(3));
   return r;
 }
 
-template <int NTHR>
-__device__ __forceinline__ void corr2_chunk(const CorrArgs& A, int chunk) {
+template <int NTHR, typename R>
+__device__ __forceinline__ void corr2_chunk(const CorrArgs<R>& A, int chunk) {
   const int s = A.s;
   int n = 1;
   for (int k = 0; k < s; ++k) n *= 3;
@@ -125,24 +129,24 @@ __device__ __forceinline__ void corr2_chunk(const CorrArgs& A, int chunk) {
   for (long long i = (long long)chunk * kCorrChunk + threadIdx.x;
        i < (long long)(chunk + 1) * kCorrChunk && i < total; i += NTHR) {
     const int gx = (int)(i % N), gy = (int)(i / N);
-    cplx<double> v = cz<double>();
+    cplx<R> v = cz<R>();
     if (gx > 0 && gx < n && gy > 0 && gy < n) {
       v = ldcg(A.t[s] + i);
       int f = 1, k = 0;  // f = 3^(s-l)
       for (int l = s - 1; l >= A.lo - 1 && l >= 0; --l) {
         f *= 3;
         ++k;
-        const cplx<double>* src = l >= A.lo ? A.t[l] : A.base;
+        const cplx<R>* src = l >= A.lo ? A.t[l] : A.base;
         if (src == nullptr) break;
         const int nl = n / f, Nl = nl + 1;
         const int cx = gx / f, cy = gy / f, ox = gx - cx * f, oy = gy - cy * f;
-        const double ik = inv_pow3(k);
-        const double wx1 = (double)ox * ik, wy1 = (double)oy * ik;
-        const double wx0 = 1.0 - wx1, wy0 = 1.0 - wy1;
-        const cplx<double>* tp = src + (long long)cy * Nl + cx;
-        const cplx<double> a = lerp2(wx0, ldcg(tp), wx1, ldcg(tp + (ox ? 1 : 0)));
-        const cplx<double> b = oy ? lerp2(wx0, ldcg(tp + Nl), wx1, ldcg(tp + Nl + (ox ? 1 : 0)))
-                                  : cz<double>();
+        const R ik = inv_pow3<R>(k);
+        const R wx1 = (R)ox * ik, wy1 = (R)oy * ik;
+        const R wx0 = R(1) - wx1, wy0 = R(1) - wy1;
+        const cplx<R>* tp = src + (long long)cy * Nl + cx;
+        const cplx<R> a = lerp2(wx0, ldcg(tp), wx1, ldcg(tp + (ox ? 1 : 0)));
+        const cplx<R> b = oy ? lerp2(wx0, ldcg(tp + Nl), wx1, ldcg(tp + Nl + (ox ? 1 : 0)))
+                                  : cz<R>();
         v = lerp2acc(v, wy0, a, wy1, b);
       }
     }
@@ -177,14 +181,14 @@ __device__ __forceinline__ void wait_counter(const unsigned* ctr, unsigned need,
   }
 }
 
-template <int NTHR>
-__global__ void __launch_bounds__(NTHR) chain2_kernel(const ChainArgs A) {
+template <int NTHR, typename R = double>
+__global__ void __launch_bounds__(NTHR) chain2_kernel(const ChainArgs<R> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double s_red[NTHR / 32];
   __shared__ int s_item;
-  __shared__ __align__(16) Sweep2Args s_a;
-  __shared__ __align__(16) ProlongArgs s_p;
-  __shared__ __align__(16) CorrArgs s_co;
+  __shared__ __align__(16) Sweep2Args<R> s_a;
+  __shared__ __align__(16) ProlongArgs<R> s_p;
+  __shared__ __align__(16) CorrArgs<R> s_co;
   while (true) {
     if (threadIdx.x == 0) s_item = (int)atomicAdd(A.head, 1u);
     __syncthreads();
@@ -193,20 +197,20 @@ __global__ void __launch_bounds__(NTHR) chain2_kernel(const ChainArgs A) {
     const ChainItem it = A.items[i];
     unsigned long long t0 = 0, t1 = 0;
     if (A.trace != nullptr && threadIdx.x == 0) t0 = gtimer();
-    if (it.kind == kItemSweep2 || it.kind == kItemSweep2s) copy_args<Sweep2Args, NTHR>(&s_a, A.s2 + it.args);
-    else if (it.kind == kItemProlong2) copy_args<ProlongArgs, NTHR>(&s_p, A.pr + it.args);
-    else copy_args<CorrArgs, NTHR>(&s_co, A.co + it.args);
+    if (it.kind == kItemSweep2 || it.kind == kItemSweep2s) copy_args<Sweep2Args<R>, NTHR>(&s_a, A.s2 + it.args);
+    else if (it.kind == kItemProlong2) copy_args<ProlongArgs<R>, NTHR>(&s_p, A.pr + it.args);
+    else copy_args<CorrArgs<R>, NTHR>(&s_co, A.co + it.args);
     if (threadIdx.x == 0 && it.need > 0) wait_counter(A.done + it.prob, it.need, A.spin_limit, A.err);
     if (A.trace != nullptr && threadIdx.x == 0) t1 = gtimer();
     __syncthreads();
     if (it.kind == kItemSweep2) {
-      sweep2_tile<4, NTHR>(s_a, it.tile, smem_raw, s_red);
+      sweep2_tile<4, NTHR, R>(s_a, it.tile, smem_raw, s_red);
     } else if (it.kind == kItemSweep2s) {
-      sweep2_tile<2, NTHR>(s_a, it.tile, smem_raw, s_red);
+      sweep2_tile<2, NTHR, R>(s_a, it.tile, smem_raw, s_red);
     } else if (it.kind == kItemProlong2) {
-      prolong2_chunk<NTHR>(s_p, it.tile);
+      prolong2_chunk<NTHR, R>(s_p, it.tile);
     } else {
-      corr2_chunk<NTHR>(s_co, it.tile);
+      corr2_chunk<NTHR, R>(s_co, it.tile);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -226,8 +230,8 @@ __global__ void __launch_bounds__(NTHR) chain2_kernel(const ChainArgs A) {
 // Finest-level sweep as a persistent launch: blocks take tiles from a queue
 // ordered by decreasing cost (tiles with complex rows first), so that the
 // uneven cost of scaling-layer tiles evens out over the SMs.
-template <int TC, int NTHR>
-__global__ void __launch_bounds__(NTHR) sweep2p_kernel(const Sweep2Args A, const int* order,
+template <int TC, int NTHR, typename R = double>
+__global__ void __launch_bounds__(NTHR) sweep2p_kernel(const Sweep2Args<R> A, const int* order,
                                                        unsigned* head, unsigned long long* trace) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double s_red[NTHR / 32];
@@ -238,7 +242,7 @@ __global__ void __launch_bounds__(NTHR) sweep2p_kernel(const Sweep2Args A, const
     const int k = s_k;
     if (k >= A.ntiles) break;
     const unsigned long long t0 = (trace != nullptr && threadIdx.x == 0) ? gtimer() : 0ull;
-    sweep2_tile<TC, NTHR>(A, order[k], smem_raw, s_red);
+    sweep2_tile<TC, NTHR, R>(A, order[k], smem_raw, s_red);
     __syncthreads();
     if (trace != nullptr && threadIdx.x == 0) {
       unsigned long long* tr = trace + 4ull * k;

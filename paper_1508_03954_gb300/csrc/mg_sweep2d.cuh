@@ -23,28 +23,30 @@ namespace mg {
 
 constexpr int kMaxGTypes = 8;  // 1D Galerkin row classes per axis
 
+template <typename R>
 struct Sweep2Args {
   int n, fine, has_coarse, hb, hier, tiles_x;
+  int first;              // fine: U is zero and nothing is pending (first inner cycle)
   int ntiles;             // tiles of this level (last-tile norm reduction)
   unsigned realrow;      // bit t: stencil row of vertex type t is real
   unsigned realjac;      // bit t: omega/D of type t is real
-  const cplx<double>* u;
-  const cplx<double>* c;  // pending correction on level l-1 (fine, may be null)
-  const cplx<double>* b;
-  cplx<double>* out;
-  cplx<double>* b_coarse;
-  cplx<double>* u_coarse;
+  const cplx<R>* u;
+  const cplx<R>* c;       // pending correction on level l-1 (fine, may be null)
+  const cplx<R>* b;
+  cplx<R>* out;
+  cplx<R>* b_coarse;
+  cplx<R>* u_coarse;
   const uint8_t* typ;     // vertex type per fine index (n+1)
   const uint8_t* gtyp;    // Galerkin row class per coarse index (n/3+1)
-  const cplx<double>* coef;   // [16][9]
-  const cplx<double>* gcoef;  // [kMaxGTypes^2][9], index gx + kMaxGTypes*gy
-  cplx<double> omd[16];
+  const cplx<R>* coef;    // [16][9]
+  const cplx<R>* gcoef;   // [kMaxGTypes^2][9], index gx + kMaxGTypes*gy
+  cplx<R> omd[16];
   double* partial;
   unsigned* ticket;
   double* norm2;
 };
 
-template <int TC>
+template <int TC, typename R = double>
 struct Tile2 {
   static constexpr int F = 3 * TC;
   static constexpr int SU = F + 5;   // u box [x0-3, x0+F+1]
@@ -57,25 +59,28 @@ struct Tile2 {
   static constexpr size_t A2 = (size_t)(F + 2) * TC + (size_t)SD * SD + (size_t)SD * F;
   static constexpr size_t AR = A1 > A2 ? A1 : A2;
   static constexpr size_t smem_cplx = AR + (size_t)SU * SU + (size_t)SR * SR + 16 * 9 + 16;
-  static constexpr size_t smem_bytes = smem_cplx * sizeof(cplx<double>) + 2 * SU;
+  static constexpr size_t smem_bytes = smem_cplx * sizeof(cplx<R>) + 2 * SU;
 };
 
-__device__ __forceinline__ double w0(int o) { return o == 0 ? 1.0 : (o == 1 ? 2.0 / 3.0 : 1.0 / 3.0); }
-__device__ __forceinline__ double w1(int o) { return o == 0 ? 0.0 : (o == 1 ? 1.0 / 3.0 : 2.0 / 3.0); }
+template <typename R = double>
+__device__ __forceinline__ R w0(int o) { return o == 0 ? R(1) : (o == 1 ? R(2) / R(3) : R(1) / R(3)); }
+template <typename R = double>
+__device__ __forceinline__ R w1(int o) { return o == 0 ? R(0) : (o == 1 ? R(1) / R(3) : R(2) / R(3)); }
 // a*s0 + b*s1 (real weights)
-__device__ __forceinline__ cplx<double> lerp2(double s0, cplx<double> a, double s1, cplx<double> b) {
-  return cplx<double>{fma(s1, b.x, s0 * a.x), fma(s1, b.y, s0 * a.y)};
+template <typename R>
+__device__ __forceinline__ cplx<R> lerp2(R s0, cplx<R> a, R s1, cplx<R> b) {
+  return cplx<R>{fma(s1, b.x, s0 * a.x), fma(s1, b.y, s0 * a.y)};
 }
 // acc + a*s0 + b*s1
-__device__ __forceinline__ cplx<double> lerp2acc(cplx<double> acc, double s0, cplx<double> a, double s1,
-                                                 cplx<double> b) {
-  return cplx<double>{fma(s1, b.x, fma(s0, a.x, acc.x)), fma(s1, b.y, fma(s0, a.y, acc.y))};
+template <typename R>
+__device__ __forceinline__ cplx<R> lerp2acc(cplx<R> acc, R s0, cplx<R> a, R s1, cplx<R> b) {
+  return cplx<R>{fma(s1, b.x, fma(s0, a.x, acc.x)), fma(s1, b.y, fma(s0, a.y, acc.y))};
 }
 // 1D restriction of five values at offsets -2..2: weights 1/3, 2/3, 1, 2/3, 1/3
-__device__ __forceinline__ cplx<double> restrict5(cplx<double> m2, cplx<double> m1, cplx<double> z,
-                                                  cplx<double> p1, cplx<double> p2) {
-  return cplx<double>{fma(m2.x + p2.x, 1.0 / 3.0, fma(m1.x + p1.x, 2.0 / 3.0, z.x)),
-                      fma(m2.y + p2.y, 1.0 / 3.0, fma(m1.y + p1.y, 2.0 / 3.0, z.y))};
+template <typename R>
+__device__ __forceinline__ cplx<R> restrict5(cplx<R> m2, cplx<R> m1, cplx<R> z, cplx<R> p1, cplx<R> p2) {
+  return cplx<R>{fma(m2.x + p2.x, R(1) / R(3), fma(m1.x + p1.x, R(2) / R(3), z.x)),
+                 fma(m2.y + p2.y, R(1) / R(3), fma(m1.y + p1.y, R(2) / R(3), z.y))};
 }
 
 // Loads of arrays that other blocks of the same launch may have written
@@ -91,12 +96,12 @@ template <> __device__ __forceinline__ cplx<float> ldcg(const cplx<float>* p) {
 }
 
 // One tile of the sweep; `tile` indexes the tiles of the level row by row.
-template <int TC, int NTHR>
-__device__ __forceinline__ void sweep2_tile(const Sweep2Args& A, int tile, unsigned char* smem_raw,
+template <int TC, int NTHR, typename R = double>
+__device__ __forceinline__ void sweep2_tile(const Sweep2Args<R>& A, int tile, unsigned char* smem_raw,
                                             double* s_red) {
-  using T = Tile2<TC>;
+  using T = Tile2<TC, R>;
   constexpr int F = T::F, SU = T::SU, SR = T::SR, SC = T::SC, SD = T::SD;
-  using C = cplx<double>;
+  using C = cplx<R>;
   C* s_A = reinterpret_cast<C*>(smem_raw);
   C* s_c = s_A;                  // [SC][SC]  pending correction
   C* s_X = s_c + SC * SC;        // [SC][SU]  x-interpolated pending correction
@@ -115,7 +120,7 @@ __device__ __forceinline__ void sweep2_tile(const Sweep2Args& A, int tile, unsig
   const int tile_x = tile % A.tiles_x, tile_y = tile / A.tiles_x;
   const int C0x = tile_x * TC, C0y = tile_y * TC;
   const int x0 = 3 * C0x, y0 = 3 * C0y;
-  const bool use_c = A.fine && A.c != nullptr;
+  const bool use_c = A.fine && !A.first && A.c != nullptr;
 
   // P0: tables, vertex types of the u box, pending correction
   for (int i = threadIdx.x; i < 16 * 9; i += NTHR) s_coef[i] = A.coef[i];
@@ -130,7 +135,7 @@ __device__ __forceinline__ void sweep2_tile(const Sweep2Args& A, int tile, unsig
       const int qx = i % SC, qy = i / SC;
       const int cx = C0x - 1 + qx, cy = C0y - 1 + qy;
       const bool in = cx >= 0 && cx <= nc && cy >= 0 && cy <= nc;
-      s_c[i] = in ? ldcg(A.c + (long long)cy * (nc + 1) + cx) : cz<double>();
+      s_c[i] = in ? ldcg(A.c + (long long)cy * (nc + 1) + cx) : cz<R>();
     }
   }
   __syncthreads();
@@ -140,7 +145,7 @@ __device__ __forceinline__ void sweep2_tile(const Sweep2Args& A, int tile, unsig
     for (int i = threadIdx.x; i < SC * SU; i += NTHR) {
       const int bx = i % SU, cy = i / SU;
       const int ox = bx % 3, cx = bx / 3;  // box origin x0-3 is a c-point
-      s_X[i] = lerp2(w0(ox), s_c[cy * SC + cx], w1(ox), s_c[cy * SC + cx + 1]);
+      s_X[i] = lerp2(w0<R>(ox), s_c[cy * SC + cx], w1<R>(ox), s_c[cy * SC + cx + 1]);
     }
     __syncthreads();
   }
@@ -149,12 +154,12 @@ __device__ __forceinline__ void sweep2_tile(const Sweep2Args& A, int tile, unsig
   for (int i = threadIdx.x; i < SU * SU; i += NTHR) {
     const int bx = i % SU, by = i / SU;
     const int gx = x0 - 3 + bx, gy = y0 - 3 + by;
-    C v = cz<double>();
+    C v = cz<R>();
     if (gx > 0 && gx < n && gy > 0 && gy < n) {
-      v = ldcg(A.u + (long long)gy * N + gx);
+      if (!(A.fine && A.first)) v = ldcg(A.u + (long long)gy * N + gx);
       if (use_c) {
         const int oy = by % 3, cy = by / 3;
-        v = lerp2acc(v, w0(oy), s_X[cy * SU + bx], w1(oy), s_X[(cy + 1) * SU + bx]);
+        v = lerp2acc(v, w0<R>(oy), s_X[cy * SU + bx], w1<R>(oy), s_X[(cy + 1) * SU + bx]);
       }
     }
     s_u[i] = v;
@@ -166,7 +171,7 @@ __device__ __forceinline__ void sweep2_tile(const Sweep2Args& A, int tile, unsig
   for (int i = threadIdx.x; i < SR * SR; i += NTHR) {
     const int qx = i % SR, qy = i / SR;
     const int gx = x0 - 2 + qx, gy = y0 - 2 + qy;
-    C r = cz<double>();
+    C r = cz<R>();
     if (gx > 0 && gx < n && gy > 0 && gy < n) {
       const int bx = qx + 1, by = qy + 1;  // u-box coordinates
       const int t = s_tx[bx] + 4 * s_ty[by];
@@ -177,7 +182,7 @@ __device__ __forceinline__ void sweep2_tile(const Sweep2Args& A, int tile, unsig
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
           const C uk = up[(k / 3 - 1) * SU + (k % 3 - 1)];
-          const double a = cf[k].x;
+          const R a = cf[k].x;
           r.x = fma(-a, uk.x, r.x);
           r.y = fma(-a, uk.y, r.y);
         }
@@ -192,7 +197,8 @@ __device__ __forceinline__ void sweep2_tile(const Sweep2Args& A, int tile, unsig
           r.y = fma(-a.y, uk.x, r.y);
         }
       }
-      if (qx >= 2 && qx < F + 2 && qy >= 2 && qy < F + 2) nrm = fma(r.x, r.x, fma(r.y, r.y, nrm));
+      if (qx >= 2 && qx < F + 2 && qy >= 2 && qy < F + 2)
+        nrm = fma((double)r.x, (double)r.x, fma((double)r.y, (double)r.y, nrm));
     }
     s_r[i] = r;
   }
@@ -228,7 +234,7 @@ __device__ __forceinline__ void sweep2_tile(const Sweep2Args& A, int tile, unsig
       if (cx > nc || cy > nc) continue;
       const long long ci = (long long)cy * (nc + 1) + cx;
       const bool inner = cx > 0 && cx < nc && cy > 0 && cy < nc;
-      C bs = cz<double>(), uc = cz<double>();
+      C bs = cz<R>(), uc = cz<R>();
       if (inner) {
         const C* yp = s_Y + (3 * jy + 2) * TC + jx;
         bs = restrict5(yp[-2 * TC], yp[-TC], yp[0], yp[TC], yp[2 * TC]);
@@ -247,7 +253,7 @@ __device__ __forceinline__ void sweep2_tile(const Sweep2Args& A, int tile, unsig
     for (int i = threadIdx.x; i < SD * F; i += NTHR) {
       const int qx = i % F, jy = i / F;
       const int ox = qx % 3, jx = qx / 3;
-      s_Z[i] = lerp2(w0(ox), s_dc[jy * SD + jx], w1(ox), s_dc[jy * SD + jx + 1]);
+      s_Z[i] = lerp2(w0<R>(ox), s_dc[jy * SD + jx], w1<R>(ox), s_dc[jy * SD + jx + 1]);
     }
   }
   __syncthreads();
@@ -257,17 +263,17 @@ __device__ __forceinline__ void sweep2_tile(const Sweep2Args& A, int tile, unsig
     const int qx = i % F, qy = i / F;
     const int gx = x0 + qx, gy = y0 + qy;
     if (gx > n || gy > n) continue;
-    C val = cz<double>();
+    C val = cz<R>();
     if (gx > 0 && gx < n && gy > 0 && gy < n) {
       const int t = s_tx[qx + 3] + 4 * s_ty[qy + 3];
       const C r = s_r[(qy + 2) * SR + (qx + 2)];
       const C w = s_omd[t];
       C du = ((A.realjac >> t) & 1u) ? rmul(w.x, r) : w * r;
       const int ox = qx % 3, oy = qy % 3;
-      if (A.hb && ox == 0 && oy == 0) du = cz<double>();
+      if (A.hb && ox == 0 && oy == 0) du = cz<R>();
       if (A.hier && !A.hb) {
         const int jy = qy / 3;
-        const C pi = lerp2(w0(oy), s_Z[jy * F + qx], w1(oy), s_Z[(jy + 1) * F + qx]);
+        const C pi = lerp2(w0<R>(oy), s_Z[jy * F + qx], w1<R>(oy), s_Z[(jy + 1) * F + qx]);
         du = du - pi;
       }
       val = A.fine ? s_u[(qy + 3) * SU + (qx + 3)] + du : du;
@@ -275,14 +281,15 @@ __device__ __forceinline__ void sweep2_tile(const Sweep2Args& A, int tile, unsig
     A.out[(long long)gy * N + gx] = val;
   }
 
-  if (A.fine) block_norm_finish_tile<NTHR>(nrm, s_red, A.partial, A.ticket, A.norm2, tile, A.ntiles);
+  if (A.fine && A.norm2 != nullptr)
+    block_norm_finish_tile<NTHR>(nrm, s_red, A.partial, A.ticket, A.norm2, tile, A.ntiles);
 }
 
-template <int TC, int NTHR>
-__global__ void __launch_bounds__(NTHR) sweep2_kernel(const Sweep2Args A) {
+template <int TC, int NTHR, typename R = double>
+__global__ void __launch_bounds__(NTHR) sweep2_kernel(const Sweep2Args<R> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double s_red[NTHR / 32];
-  sweep2_tile<TC, NTHR>(A, blockIdx.x, smem_raw, s_red);
+  sweep2_tile<TC, NTHR, R>(A, blockIdx.x, smem_raw, s_red);
 }
 
 }  // namespace mg

@@ -26,7 +26,7 @@ STATUS_NAMES = {0: "MG_OK", 1: "MG_ERR_INVALID", 2: "MG_ERR_CUDA", 3: "MG_ERR_OO
 
 # every symbol include/mg.h declares
 EXPORTS = ["mg_create", "mg_destroy", "mg_set_stream", "mg_set_rhs", "mg_set_solution",
-           "mg_get_solution", "mg_cycle", "mg_residual_norm", "mg_solve", "mg_set_precision",
+           "mg_get_solution", "mg_cycle", "mg_residual_norm", "mg_last_cycle_norm", "mg_solve", "mg_set_precision",
            "mg_fmg", "mg_omega_scheme", "mg_get_level", "mg_set_timing", "mg_get_stats",
            "mg_set_trace", "mg_get_trace", "mg_set_k2", "mg_set_rhs_vector", "mg_sample",
            "mg_set_rhs_samples", "mg_adjoint_grad", "mg_residual_noalloc", "mg_batch_create",
@@ -72,6 +72,7 @@ def load(path: str | None = None):
         "mg_get_solution": (ip, [vp, vp, ip]),
         "mg_cycle": (ip, [vp, ip, pc, ip]),
         "mg_residual_norm": (ip, [vp, ctypes.POINTER(dp), ctypes.POINTER(dp)]),
+        "mg_last_cycle_norm": (ip, [vp, ctypes.POINTER(dp), ctypes.POINTER(dp)]),
         "mg_solve": (ip, [vp, ip, pc, ip, dp, ip, ctypes.POINTER(ip), ctypes.POINTER(dp)]),
         "mg_set_precision": (ip, [vp, ip, ip]),
         "mg_fmg": (ip, [vp, ip, pc, ip, ip]),
@@ -228,6 +229,12 @@ class Solver:
         a, r = ctypes.c_double(), ctypes.c_double()
         self._check(self._L.mg_residual_norm(self._view, ctypes.byref(a), ctypes.byref(r)),
                     "mg_residual_norm")
+        return a.value, r.value
+
+    def last_cycle_norm(self):
+        a, r = ctypes.c_double(), ctypes.c_double()
+        self._check(self._L.mg_last_cycle_norm(self._view, ctypes.byref(a), ctypes.byref(r)),
+                    "mg_last_cycle_norm")
         return a.value, r.value
 
     def solve(self, variant, omega, transfer, tol, max_cycles):
