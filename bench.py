@@ -229,6 +229,135 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------- other forms
+def measure_forms(mg, torch, peaks):
+    """Time to 1e-8 of the refinement form against the plain complex128 cycle
+    (2D depth 6 and 3D depth 5), the batched form against sequential solves
+    (256 problems of depth 4-6), and the adjoint gradient (2D depth 6).  The
+    configured indefinite problems diverge (interior theta = 0) and the plain
+    cycle stalls where coarse cells straddle the layer edge, so times to 1e-8
+    use the definite companions k^2 -> -k^2 (same shapes and bytes)."""
+    import oracle as O  # relaxation factors only (closed form)
+    out = {}
+    stream = torch.cuda.current_stream()
+
+    def wall(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize()
+        return r, time.perf_counter() - t0
+
+    # configured problem: plain cycles from zero
+    c = W.config2()
+    s = mg.Solver(2, 6, c["k2"], c["theta"], c["layer_width"])
+    s.set_stream(stream.cuda_stream)
+    s.set_rhs(c["f"])
+    st, n, rel = s.solve(mg.MG_BPX, np.full(6, 0.6), mg.MG_HIERARCHICAL, 1e-8, 300)
+    out["configured_2d_depth6"] = {"status": mg.STATUS_NAMES[st], "cycles": n, "rel_res": rel}
+    s.close()
+    # (A) 2D depth 6 definite companion
+    c = W.definite(W.config2())
+    om = O.omega_scheme(O.EXP, 0.6, 6)
+    s = mg.Solver(2, 6, c["k2"], c["theta"], c["layer_width"])
+    s.set_stream(stream.cuda_stream)
+    s.set_rhs(c["f"])
+    s.set_precision(mg.MG_C64_REFINE, 4)
+    s.solve(mg.MG_ADD, om, mg.MG_DLINEAR, 1e-8, 4000)
+    s.set_solution(np.zeros(s.shape, complex))
+    (st, n, rel), dt = wall(lambda: s.solve(mg.MG_ADD, om, mg.MG_DLINEAR, 1e-8, 4000))
+    a = {"c64_refine": {"status": mg.STATUS_NAMES[st], "inner_cycles": n, "rel_res": rel, "seconds": dt}}
+    s.set_precision(mg.MG_C128, 4)
+    s.set_solution(np.zeros(s.shape, complex))
+    (st, n, rel), dt = wall(lambda: s.solve(mg.MG_ADD, om, mg.MG_DLINEAR, 1e-8, 300))
+    a["c128_plain"] = {"status": mg.STATUS_NAMES[st], "cycles": n, "rel_res": rel, "seconds": dt,
+                       "note": "stalls at the FAS fixed point shifted by the non-Galerkin layer edge"}
+    out["time_to_1e-8_2d_depth6_definite"] = a
+    s.close()
+    # (C) 3D depth 5 definite companion
+    c = W.definite(W.config3())
+    om = O.omega_scheme(O.EXP, 0.6, 5)
+    s = mg.Solver(3, 5, c["k2"], c["theta"], c["layer_width"])
+    s.set_stream(stream.cuda_stream)
+    s.set_rhs(c["f"])
+    s.set_precision(mg.MG_C64_REFINE, 4)
+    s.solve(mg.MG_ADD, om, mg.MG_DLINEAR, 1e-8, 4)
+    s.set_solution(np.zeros(s.shape, complex))
+    s.set_timing(True)
+    s.get_stats()
+    (st, n, rel), dt = wall(lambda: s.solve(mg.MG_ADD, om, mg.MG_DLINEAR, 1e-8, 2000))
+    _, k, ms = s.get_stats()
+    s.set_timing(False)
+    nv = (3 ** 5 + 1) ** 3
+    nbytes = 3 * 8 * nv + 3 * 8 * (3 ** 4 + 1) ** 3
+    sweep_s = ms / max(k, 1) / 1e3
+    cc = {"c64_refine": {"status": mg.STATUS_NAMES[st], "inner_cycles": n, "rel_res": rel, "seconds": dt,
+                         "fine_sweep_ms": sweep_s * 1e3,
+                         "fine_sweep_hbm": {"achieved_gbs": nbytes / sweep_s / 1e9, "peak_gbs": peaks.get("hbm_gbs"),
+                                            "frac": nbytes / sweep_s / 1e9 / peaks.get("hbm_gbs", 6800.0),
+                                            "algorithmic_bytes": nbytes}}}
+    s.set_precision(mg.MG_C128, 4)
+    s.set_solution(np.zeros(s.shape, complex))
+    (st, n, rel), dt = wall(lambda: s.solve(mg.MG_ADD, om, mg.MG_DLINEAR, 1e-8, 60))
+    cc["c128_plain"] = {"status": mg.STATUS_NAMES[st], "cycles": n, "rel_res": rel, "seconds": dt,
+                        "dof_updates_per_s": (3 ** 5 - 1) ** 3 * n / dt}
+    out["time_to_1e-8_3d_depth5_definite"] = cc
+    s.close()
+    # (B) batched: 256 problems, persistent launch vs one problem at a time
+    specs = W.config4_specs(256)
+    probs = [W.definite(W.config4_problem(sp)) for sp in specs]
+    bt = mg.Batch(probs)
+    bt.set_stream(stream.cuda_stream)
+    for p, pr in enumerate(probs):
+        bt.solvers[p].set_rhs(pr["f"])
+    oms = [O.omega_scheme(O.EXP, 0.6, pr["depth"]) for pr in probs]
+    tc, bp, ms = bt.autotune(mg.MG_ADD, oms, mg.MG_DLINEAR, 4)
+    (st, cyc, rel), dt = wall(lambda: bt.solve(mg.MG_ADD, oms, mg.MG_DLINEAR, 1e-8, 400, 4))
+    unknowns = sum((3 ** pr["depth"] - 1) ** 2 for pr in probs)
+    upd = sum((3 ** pr["depth"] - 1) ** 2 * cyc[p] for p, pr in enumerate(probs))
+    bb = {"problems": 256, "fine_unknowns": unknowns, "autotuned": {"tile": tc, "blocks_per_sm": bp,
+                                                                     "ms_per_outer_step": ms},
+          "batched": {"seconds": dt, "all_ok": all(x == mg.MG_OK for x in st), "max_rel_res": max(rel),
+                      "dof_updates_per_s": upd / dt}}
+
+    def seq():
+        res = []
+        for p in range(256):
+            sv = bt.solvers[p]
+            sv.set_solution(np.zeros(sv.shape, complex))
+            sv.set_precision(mg.MG_C64_REFINE, 4)
+            res.append(sv.solve(mg.MG_ADD, oms[p], mg.MG_DLINEAR, 1e-8, 4000))
+        return res
+    r, dt2 = wall(seq)
+    bb["sequential"] = {"seconds": dt2, "all_ok": all(x[0] == mg.MG_OK for x in r)}
+    out["batched_256_definite"] = bb
+    bt.close()
+    # (D) adjoint: forward + adjoint solve and gradients, 2D depth 6
+    from paper_1508_03954_gb300.adjoint import SolveOptions, far_field
+    import oracle.adjoint as A
+    c = W.config5()
+    E = 0.0  # definite companion (k^2 = -V)
+    s = mg.Solver(2, 6, E - c["V"], c["theta"], c["layer_width"])
+    s.set_stream(stream.cuda_stream)
+    xyz, g = A.circle_samples(256)
+    opts = SolveOptions(variant=mg.MG_ADD, transfer=mg.MG_DLINEAR, omega=O.omega_scheme(O.EXP, 0.6, 6),
+                        tol=1e-10, max_cycles=20000, precision=mg.MG_C64_REFINE, inner_cycles=4)
+    V = torch.from_numpy(c["V"]).cuda().requires_grad_(True)
+    f = torch.from_numpy(np.real(c["f"])).cuda().requires_grad_(True)
+
+    def fwd_bwd():
+        J = far_field(V, f, s, E, xyz, g, opts)
+        J.backward()
+        return J.item()
+    fwd_bwd()
+    V.grad = None
+    f.grad = None
+    Jv, dt = wall(fwd_bwd)
+    out["adjoint_2d_depth6"] = {"J": Jv, "seconds_forward_backward": dt, "tol": 1e-10}
+    s.close()
+    return out
+
+
 # ---------------------------------------------------------------- main
 def main():
     ap = argparse.ArgumentParser()
@@ -238,6 +367,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -351,7 +481,7 @@ def main():
                                     [os.path.join(csrc, f) for f in sorted(os.listdir(csrc))])
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": FP64_PEAK_FLOPS / 1e12,
                 "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_FLOPS, "traffic": traffic,
-                "kernel": "sweep2_kernel<12,256> (finest level, FP64)",
+                "kernel": "sweep2p_kernel<8,256,double> (finest level, persistent LPT, FP64)",
                 "peak_source": "FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
                 "hbm": {"achieved_gbs": nbytes / sweep_s / 1e9, "peak_gbs": peaks.get("hbm_gbs"),
                         "frac": nbytes / sweep_s / 1e9 / peaks.get("hbm_gbs", 6800.0),
@@ -374,6 +504,8 @@ def main():
                     "what": "mg_set_solution + mg_set_rhs from pinned host, mg_cycle, "
                             "mg_get_solution to pinned host"},
             "gpu_launches": launches, "clocks": clk}
+    if rank == 0 and world == 1 and not args.no_forms:
+        line["forms"] = measure_forms(mg, torch, peaks)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_line(cfg)
     if rank == 0:
