@@ -221,12 +221,35 @@ def run_reference(args, rank):
     line = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c128 (f64)", "data": "synthetic",
-            "impl": "reference",
-            "config": {"workload": "2D complex128 variant sweep (BPX cycle), k=20pi, 10% ECS layer, "
-                                   f"theta=pi/6, sampled at depth {depth}"},
+            "impl": "reference", "config": workload_config(1),
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- replicas
+def max_over_ranks(dist, x, device):
+    """The largest x over all ranks (x itself without a process group); the
+    slowest replica sets the whole job's time."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_step, steps, world, max_ms):
+    """Units all replicas processed divided by the slowest replica's time."""
+    return units_per_step * steps * world / (max_ms / 1e3)
+
+
+def workload_config(world):
+    return {"workload": "2D complex128 variant sweep: depth 6 (729^2 cells, 529,984 "
+                        "interior unknowns), k=20pi, 10% ECS layer theta=pi/6, 3 Gaussians "
+                        "(seed 1); step = one BPX additive FAS cycle, omega=0.6",
+            "l2": "flushed before every timed step (256 MB write)",
+            "parallelism": "replicas" if world > 1 else "single GPU"}
 
 
 # ---------------------------------------------------------------- other forms
@@ -427,11 +450,8 @@ def main():
     clk = clocks.stop()
     launches, _, _ = s.get_stats()
     total_ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
-    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
-    value = interior * args.steps * world / (total_ms / 1e3)
+    total_ms = max_over_ranks(dist, total_ms, "cuda")
+    value = whole_job_rate(interior, args.steps, world, total_ms)
 
     # the dominant kernel alone: the same cycles with an event pair around the
     # finest-level sweep (a separate pass, so the timed steps above run the
@@ -467,10 +487,7 @@ def main():
         if k >= 3:
             e2e_ms += a.elapsed_time(b)
         u_h.copy_(out_h)
-    te = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = interior * ne * world / (float(te.item()) / 1e3)
+    e2e_value = whole_job_rate(interior, ne, world, max_over_ranks(dist, e2e_ms, "cuda"))
 
     peaks, src = measured_peaks()
     flops, nbytes = fine_sweep_counts(d, depth, cfg["layer_width"], bpx=True, omega_real=True)
@@ -493,11 +510,7 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c128 (f64)", "data": "synthetic",
-            "config": {"workload": "2D complex128 variant sweep: depth 6 (729^2 cells, 529,984 "
-                                   "interior unknowns), k=20pi, 10% ECS layer theta=pi/6, 3 Gaussians "
-                                   "(seed 1); step = one BPX additive FAS cycle, omega=0.6",
-                       "l2": "flushed before every timed step (256 MB write)",
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "config": workload_config(world),
             "roofline": roofline,
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": 2 * 16 * s.nv, "d2h_bytes_per_step": 16 * s.nv,

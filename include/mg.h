@@ -229,6 +229,20 @@ int mg_batch_autotune(mg_batch* batch, int variant, const mg_c128* const* omega,
 long long mg_batch_launches(const mg_batch* batch);
 const char* mg_batch_last_error(const mg_batch* batch);
 
+/* Bound on every device-side wait of the persistent launches, in polls
+ * (default 2^22, about a second; each poll sleeps 64-256 ns).  When a wait
+ * runs out, the kernel records it and finishes without hanging; the next
+ * synchronising call returns MG_ERR_TIMEOUT and the results of the affected
+ * cycles are invalid.  polls >= 1. */
+int mg_set_spin_limit(mg_ctx* ctx, unsigned polls);
+
+/* Diagnostic for failure handling: while enabled, the first item of every
+ * coarse-chain launch also waits on a device counter that nothing ever
+ * increments, so the wait must run out (use a small mg_set_spin_limit).  The
+ * launch still completes; the next synchronising call reports
+ * MG_ERR_TIMEOUT.  2D contexts with a constant shift (the persistent path). */
+int mg_debug_unsatisfiable_wait(mg_ctx* ctx, int enable);
+
 /* Instrumentation.  mg_set_timing(ctx, 1) makes every later cycle record a
  * CUDA event pair around its finest-level sweep kernel on the context's
  * stream.  mg_get_stats synchronises the stream and returns, since the last

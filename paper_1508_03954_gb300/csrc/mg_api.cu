@@ -121,6 +121,7 @@ struct mg_ctx {
   unsigned* chain_ctr = nullptr;       // [0] queue head, [1..] completion counters
   unsigned* dev_err = nullptr;         // bounded-wait timeout flag (sticky until read)
   unsigned spin_limit = 1u << 22;
+  bool debug_stall = false;            // next chain launches wait on a counter nothing sets
   int chain_bpsm = 0;                  // resident chain blocks per SM
   int fine_bpsm = MG_FINE_BPSM;        // persistent fine-sweep blocks per SM
   // optional per-item trace of the persistent launches (last cycle only)
@@ -268,12 +269,17 @@ int dalloc(mg_ctx* c, Hier<R>& H, void** p, size_t bytes) {
 }
 
 template <typename R>
-void free_hier(Hier<R>& H) {
+void drop_graphs(Hier<R>& H) {
   for (auto& g : H.graphs) {
     if (g.fine) cudaGraphExecDestroy(g.fine);
     if (g.coarse) cudaGraphExecDestroy(g.coarse);
   }
   H.graphs.clear();
+}
+
+template <typename R>
+void free_hier(Hier<R>& H) {
+  drop_graphs(H);
   for (auto& cp : H.chains) {
     cudaFree(cp.items);
     cudaFree(cp.s2);
@@ -728,6 +734,7 @@ cudaError_t launch_chain2(mg_ctx* c, const typename Hier<R>::ChainPlan& cp) {
   A.err = c->dev_err;
   A.spin_limit = c->spin_limit;
   A.trace = c->tracing ? c->trace + 4 * kTraceFine : nullptr;
+  A.stall = c->debug_stall ? c->chain_ctr + 48 : nullptr;  // stays zero
   mg::chain2_kernel<256, R><<<cp.grid, 256, mg::Tile2<4, R>::smem_bytes, c->stream>>>(A);
   return cudaGetLastError();
 }
@@ -1429,6 +1436,31 @@ int mg_omega_scheme(int scheme, mg_c128 omega_s, int depth, int iter_n, int l_gr
     out[l - 1].re = v.real();
     out[l - 1].im = v.imag();
   }
+  return MG_OK;
+}
+
+namespace {
+// Captured graphs hold the kernel arguments of their launches (the wait bound,
+// the diagnostic counter), so a change of either recaptures them.
+void drop_graphs(mg_ctx* c) {
+  drop_graphs(c->h64);
+  drop_graphs(c->h32);
+}
+}  // namespace
+
+int mg_set_spin_limit(mg_ctx* c, unsigned polls) {
+  if (check_ctx(c)) return MG_ERR_INVALID;
+  if (polls == 0) return fail(c, MG_ERR_INVALID, "the wait bound must be at least one poll");
+  if (polls != c->spin_limit) drop_graphs(c);  // captured launches bake the bound
+  c->spin_limit = polls;
+  return MG_OK;
+}
+
+int mg_debug_unsatisfiable_wait(mg_ctx* c, int enable) {
+  if (check_ctx(c)) return MG_ERR_INVALID;
+  if ((enable != 0) != c->debug_stall) drop_graphs(c);
+  c->debug_stall = enable != 0;
+  MG_CUDA(c, cudaMemsetAsync(c->chain_ctr + 48, 0, sizeof(unsigned), c->stream));
   return MG_OK;
 }
 

@@ -70,6 +70,7 @@ struct ChainArgs {
   unsigned* err;         // set when a bounded wait gave up
   unsigned spin_limit;   // polls before giving up
   unsigned long long* trace;  // optional: per item {taken, ready, done, sm} (ns, globaltimer)
+  const unsigned* stall;      // diagnostic: the first item also waits for *stall >= 1 (nothing sets it)
 };
 
 __device__ __forceinline__ unsigned long long gtimer() {
@@ -201,6 +202,7 @@ __global__ void __launch_bounds__(NTHR) chain2_kernel(const ChainArgs<R> A) {
     else if (it.kind == kItemProlong2) copy_args<ProlongArgs<R>, NTHR>(&s_p, A.pr + it.args);
     else copy_args<CorrArgs<R>, NTHR>(&s_co, A.co + it.args);
     if (threadIdx.x == 0 && it.need > 0) wait_counter(A.done + it.prob, it.need, A.spin_limit, A.err);
+    if (threadIdx.x == 0 && i == 0 && A.stall != nullptr) wait_counter(A.stall, 1u, A.spin_limit, A.err);
     if (A.trace != nullptr && threadIdx.x == 0) t1 = gtimer();
     __syncthreads();
     if (it.kind == kItemSweep2) {

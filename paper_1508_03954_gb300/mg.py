@@ -28,7 +28,7 @@ STATUS_NAMES = {0: "MG_OK", 1: "MG_ERR_INVALID", 2: "MG_ERR_CUDA", 3: "MG_ERR_OO
 EXPORTS = ["mg_create", "mg_destroy", "mg_set_stream", "mg_set_rhs", "mg_set_solution",
            "mg_get_solution", "mg_cycle", "mg_residual_norm", "mg_last_cycle_norm", "mg_solve", "mg_set_precision",
            "mg_fmg", "mg_omega_scheme", "mg_get_level", "mg_set_timing", "mg_get_stats",
-           "mg_set_trace", "mg_get_trace", "mg_set_k2", "mg_set_rhs_vector", "mg_sample",
+           "mg_set_trace", "mg_get_trace", "mg_set_spin_limit", "mg_debug_unsatisfiable_wait", "mg_set_k2", "mg_set_rhs_vector", "mg_sample",
            "mg_set_rhs_samples", "mg_adjoint_grad", "mg_residual_noalloc", "mg_batch_create",
            "mg_batch_destroy", "mg_batch_get_ctx", "mg_batch_set_stream", "mg_batch_solve",
            "mg_batch_autotune", "mg_batch_launches", "mg_batch_last_error", "mg_last_error"]
@@ -83,6 +83,8 @@ def load(path: str | None = None):
                               ctypes.POINTER(dp)]),
         "mg_residual_noalloc": (ip, [vp, vp, vp, vp, vp]),
         "mg_set_trace": (ip, [vp, ip]),
+        "mg_set_spin_limit": (ip, [vp, ctypes.c_uint]),
+        "mg_debug_unsatisfiable_wait": (ip, [vp, ip]),
         "mg_set_k2": (ip, [vp, ctypes.POINTER(dp)]),
         "mg_set_rhs_vector": (ip, [vp, vp, ip]),
         "mg_sample": (ip, [vp, ip, ctypes.POINTER(dp), pc, pc]),
@@ -310,6 +312,13 @@ class Solver:
                                             ctypes.c_void_p(lam.data_ptr()),
                                             MgC128(float(np.real(s)), float(np.imag(s))), outs[0], outs[1]),
                     "mg_adjoint_grad")
+
+    def set_spin_limit(self, polls):
+        self._check(self._L.mg_set_spin_limit(self._view, int(polls)), "mg_set_spin_limit")
+
+    def debug_unsatisfiable_wait(self, enable):
+        self._check(self._L.mg_debug_unsatisfiable_wait(self._view, 1 if enable else 0),
+                    "mg_debug_unsatisfiable_wait")
 
     def set_trace(self, enable):
         self._check(self._L.mg_set_trace(self._view, 1 if enable else 0), "mg_set_trace")
