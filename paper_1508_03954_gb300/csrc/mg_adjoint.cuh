@@ -62,8 +62,8 @@ __global__ void adjoint_grad_kernel(int n, const cplx<double>* __restrict__ lam,
   for (long long vi = blockIdx.x * (long long)blockDim.x + threadIdx.x; vi < nv;
        vi += (long long)gridDim.x * blockDim.x) {
     int g[3];
-    long long r = vi;
-    for (int a = 0; a < D; ++a) { g[a] = (int)(r % N); r /= N; }
+    unsigned r = (unsigned)vi;  // vertex counts stay below 2^32
+    for (int a = 0; a < D; ++a) { g[a] = (int)(r % (unsigned)N); r /= (unsigned)N; }
     cplx<double> sq = cz<double>(), ml = cz<double>();
     for (int e = 0; e < (1 << D); ++e) {
       int c[3];

@@ -18,6 +18,8 @@
 #include "mg_kernels.cuh"
 #include "mg_sweep2d.cuh"
 #include "mg_sweep3d.cuh"
+#include "mg_sweep3s.cuh"
+#include "mg_defect3.cuh"
 #include "mg_persist.cuh"
 #include "mg_adjoint.cuh"
 #include <map>
@@ -555,6 +557,9 @@ cudaError_t configure_kernels() {
   set((const void*)mg::sweep3_kernel<double, 4, 256>, mg::Tile3<double, 4>::smem_bytes);
   set((const void*)mg::sweep3_kernel<float, 7, 512>, mg::Tile3<float, 7>::smem_bytes);
   set((const void*)mg::sweep3_kernel<float, 4, 256>, mg::Tile3<float, 4>::smem_bytes);
+  set((const void*)mg::sweep3s_kernel, sizeof(mg::Sweep3sShared));
+  set((const void*)mg::defect3_kernel<float>, sizeof(mg::Defect3Shared<float>));
+  set((const void*)mg::defect3_kernel<double>, sizeof(mg::Defect3Shared<double>));
   set((const void*)mg::chain2_kernel<256>, mg::Tile2<4>::smem_bytes);
   static_assert(mg::Tile2<2>::smem_bytes <= mg::Tile2<4>::smem_bytes, "chain smem");
   if (e == cudaSuccess && dev < 64) done |= 1ull << dev;
@@ -755,8 +760,61 @@ cudaError_t launch_sweep3(cudaStream_t s, mg::Sweep3Args<R>& A) {
   return cudaGetLastError();
 }
 
+// Large complex64 3D levels: the separable z-marching sweep, one block per SM
+// over equal ranges of (tile, coarse plane) units.
+cudaError_t launch_sweep3s(mg_ctx* c, Hier<float>& H, int l, bool fine, int hb, int hier, const cd& om) {
+  auto& V = H.lev[l];
+  mg::Sweep3sArgs A;
+  std::memset(&A, 0, sizeof(A));
+  A.n = V.n;
+  A.fine = fine ? 1 : 0;
+  A.has_coarse = 1;
+  A.hb = hb;
+  A.hier = hier;
+  const int nc = V.n / 3;
+  A.tiles_x = (nc + 8) / 9;
+  A.nunits = (long long)A.tiles_x * A.tiles_x * nc;
+  A.u = fine ? V.u[H.cur] : V.u[0];
+  A.c = fine ? H.lev[l - 1].corr : nullptr;
+  A.b = V.b;
+  A.out = fine ? V.u[1 - H.cur] : V.t;
+  A.b_coarse = H.lev[l - 1].b;
+  A.u_coarse = H.lev[l - 1].u[0];
+  A.typ = V.typ;
+  A.gtyp = V.gtyp;
+  A.gcoef = V.gcoef;
+  // 1D rows by axis class (left / right cell rotated): mass (hl/6, (hl+hr)/3,
+  // hr/6), stiffness (-1/hl, 1/hl + 1/hr, -1/hr), stiffness - phi mass
+  const double h = 1.0 / V.n, phi = c->k2[0];
+  const cd hrot = h * cd(std::cos(c->theta), std::sin(c->theta));
+  for (int t = 0; t < 4; ++t) {
+    const cd hl = (t & 1) ? hrot : cd(h), hr = (t & 2) ? hrot : cd(h);
+    const cd m[3] = {hl / 6.0, (hl + hr) / 3.0, hr / 6.0};
+    const cd k[3] = {-1.0 / hl, 1.0 / hl + 1.0 / hr, -1.0 / hr};
+    for (int j = 0; j < 3; ++j) {
+      const cd kp = k[j] - phi * m[j];
+      A.row[t][j] = cplx<float>{(float)m[j].real(), (float)m[j].imag()};
+      A.row[t][3 + j] = cplx<float>{(float)k[j].real(), (float)k[j].imag()};
+      A.row[t][6 + j] = cplx<float>{(float)kp.real(), (float)kp.imag()};
+    }
+  }
+  for (size_t t = 0; t < V.diag.size() && t < 64; ++t) {
+    const cd q = om / V.diag[t];
+    A.omd[t] = cplx<float>{(float)q.real(), (float)q.imag()};
+  }
+  A.partial = H.partial;
+  A.ticket = H.ticket;
+  A.norm2 = fine ? H.norm2 : nullptr;
+  const long long grid = std::min<long long>(152, std::max<long long>(1, (A.nunits + 3) / 4));
+  mg::sweep3s_kernel<<<(int)grid, mg::kS3sThreads, sizeof(mg::Sweep3sShared), c->stream>>>(A);
+  return cudaGetLastError();
+}
+
 template <typename R>
 cudaError_t sweep3(mg_ctx* c, Hier<R>& H, int l, bool fine, int hb, int hier, const cd& om) {
+  if constexpr (std::is_same<R, float>::value) {
+    if (l > 1 && H.lev[l].n >= 27 && H.lev[l].g3ok) return launch_sweep3s(c, H, l, fine, hb, hier, om);
+  }
   auto& V = H.lev[l];
   mg::Sweep3Args<R> A;
   std::memset(&A, 0, sizeof(A));
@@ -1053,6 +1111,52 @@ cudaError_t stencil(mg_ctx* c, Hier<R>& H, int l, int xs, const cplx<R>* x, cons
   return cudaGetLastError();
 }
 
+// 3D fine level, constant shift: u' = u + e + P cc (optional, into u_out),
+// r = b - H u' in FP64 (optional complex64 copy into r32), |r|^2 into
+// H.norm2[slot] -- the fused outer step of the defect-correction form and
+// the plain FP64 residual norm.
+template <typename RC>
+cudaError_t defect3(mg_ctx* c, int l, const cplx<double>* u, const cplx<RC>* e, const cplx<RC>* cc,
+                    cplx<double>* u_out, cplx<float>* r32, int slot) {
+  auto& H = c->h64;
+  auto& V = H.lev[l];
+  mg::Defect3Args<RC> A;
+  std::memset(&A, 0, sizeof(A));
+  A.n = V.n;
+  A.tiles_x = (V.n + 1 + 29) / 30;
+  A.tiles_y = (V.n + 1 + 13) / 14;
+  A.nunits = (long long)A.tiles_x * A.tiles_y * (V.n / 3);
+  A.u = u;
+  A.e = e;
+  A.c = cc;
+  A.b = V.b;
+  A.u_out = u_out;
+  A.r32 = r32;
+  A.typ = V.typ;
+  const double h = 1.0 / V.n, phi = c->k2[0];
+  const cd hrot = h * cd(std::cos(c->theta), std::sin(c->theta));
+  for (int t = 0; t < 4; ++t) {
+    const cd hl = (t & 1) ? hrot : cd(h), hr = (t & 2) ? hrot : cd(h);
+    const cd m[3] = {hl / 6.0, (hl + hr) / 3.0, hr / 6.0};
+    const cd k[3] = {-1.0 / hl, 1.0 / hl + 1.0 / hr, -1.0 / hr};
+    for (int j = 0; j < 3; ++j) {
+      const cd kp = k[j] - phi * m[j];
+      A.row[t][j] = cplx<double>{m[j].real(), m[j].imag()};
+      A.row[t][3 + j] = cplx<double>{k[j].real(), k[j].imag()};
+      A.row[t][6 + j] = cplx<double>{kp.real(), kp.imag()};
+    }
+  }
+  A.partial = H.partial;
+  A.ticket = H.ticket + 3;
+  A.norm2 = slot >= 0 ? H.norm2 + slot : nullptr;
+  ++c->launches;
+  const long long grid = std::min<long long>(152, std::max<long long>(1, (A.nunits + 3) / 4));
+  mg::defect3_kernel<RC><<<(int)grid, mg::kD3Threads, sizeof(mg::Defect3Shared<RC>), c->stream>>>(A);
+  return cudaGetLastError();
+}
+
+bool use_defect3(const mg_ctx* c) { return c->d == 3 && !c->h64.varphi && c->L >= 1; }
+
 int zero_pending(mg_ctx* c, Hier<double>& H, int s) {
   for (int l = 1; l < s; ++l) {
     MG_CUDA(c, cudaMemsetAsync(H.lev[l].corr, 0, H.lev[l].nv * sizeof(cplx<double>), c->stream));
@@ -1090,10 +1194,18 @@ int check_timeout(mg_ctx* c) {
 // synchronising.
 int fine_residual(mg_ctx* c, int s, double* out) {
   auto& H = c->h64;
-  cudaError_t e = materialize(c, H, s, c->scratch);
-  if (e == cudaSuccess)
-    e = stencil<double, double>(c, H, s, 1, c->scratch, H.lev[s].b, H.lev[s].coefH, true,
-                                (cplx<double>*)nullptr, 1);
+  cudaError_t e;
+  if (use_defect3(c)) {
+    // u = U + P corr_{s-1} formed in the same pass
+    const cplx<double>* nul = nullptr;
+    e = defect3<double>(c, s, H.lev[s].u[H.cur], nul, s > 1 ? H.lev[s - 1].corr : nul,
+                        (cplx<double>*)nullptr, (cplx<float>*)nullptr, 1);
+  } else {
+    e = materialize(c, H, s, c->scratch);
+    if (e == cudaSuccess)
+      e = stencil<double, double>(c, H, s, 1, c->scratch, H.lev[s].b, H.lev[s].coefH, true,
+                                  (cplx<double>*)nullptr, 1);
+  }
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->host_norm, H.norm2 + 1, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return fail(c, MG_ERR_CUDA, std::string("residual: ") + cudaGetErrorString(e));
@@ -1349,12 +1461,17 @@ int mg_solve(mg_ctx* c, int variant, const mg_c128* omega, int transfer, double 
   MG_CUDA(c, materialize(c, H, L, c->scratch));
   MG_CUDA(c, cudaMemcpyAsync(u, c->scratch, VF.nv * sizeof(cplx<double>), cudaMemcpyDeviceToDevice, c->stream));
   if ((rc = zero_pending(c, H, L)) != MG_OK) return rc;
+  const bool fused = use_defect3(c);
+  if (fused) {
+    // r = b - H u in FP64 as the complex64 rhs of the first inner problem
+    MG_CUDA(c, (defect3<float>(c, L, u, nullptr, nullptr, nullptr, EF.b, -1)));
+  }
   while (true) {
     if (diverged(rel)) return finish(MG_DIVERGED);
     if (rel <= tol) return finish(MG_OK);
     if (done >= max_cycles) return finish(MG_NOT_CONVERGED);
     // r = b - H u in FP64, stored as complex64 rhs of the inner problem
-    MG_CUDA(c, (stencil<double, float>(c, H, L, 1, u, VF.b, VF.coefH, true, EF.b, -1)));
+    if (!fused) MG_CUDA(c, (stencil<double, float>(c, H, L, 1, u, VF.b, VF.coefH, true, EF.b, -1)));
     MG_CUDA(c, cudaMemsetAsync(EF.u[E.cur], 0, EF.nv * sizeof(cplx<float>), c->stream));
     for (int l = 1; l < L; ++l) {
       MG_CUDA(c, cudaMemsetAsync(E.lev[l].corr, 0, E.lev[l].nv * sizeof(cplx<float>), c->stream));
@@ -1367,6 +1484,17 @@ int mg_solve(mg_ctx* c, int variant, const mg_c128* omega, int transfer, double 
     }
     // u += E + P corr (FP64 update)
     const cplx<float>* cc = L > 1 ? E.lev[L - 1].corr : nullptr;
+    if (fused) {
+      // u' = u + E + P corr, the next inner rhs r = b - H u' and |r|^2 in one pass
+      cplx<double>* u2 = VF.u[1 - H.cur];
+      MG_CUDA(c, (defect3<float>(c, L, u, EF.u[E.cur], cc, u2, EF.b, 1)));
+      H.cur = 1 - H.cur;
+      u = u2;
+      MG_CUDA(c, cudaMemcpyAsync(c->host_norm, H.norm2 + 1, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+      MG_CUDA(c, cudaStreamSynchronize(c->stream));
+      rel = c->r0 > 0 ? std::sqrt(*c->host_norm) / c->r0 : 0.0;
+      continue;
+    }
     ++c->launches;
     if (c->d == 2)
       mg::update_kernel<float, 2><<<grid_for(VF.nv), kThreads, 0, c->stream>>>(VF.n, u, EF.u[E.cur], cc);

@@ -66,7 +66,7 @@ __device__ __forceinline__ void res_chunk(const ResArgs& A, int chunk, double* s
   double nrm = 0.0;
   for (long long i = (long long)chunk * kBatchChunk + threadIdx.x;
        i < (long long)(chunk + 1) * kBatchChunk && i < total; i += NTHR) {
-    const int gx = (int)(i % N), gy = (int)(i / N);
+    const int gx = (int)((unsigned)i % (unsigned)N), gy = (int)((unsigned)i / (unsigned)N);
     cplx<double> r = cz<double>();
     if (gx > 0 && gx < n && gy > 0 && gy < n) {
       const int t = A.typ[gx] + 4 * A.typ[gy];
@@ -95,7 +95,7 @@ __device__ __forceinline__ void upd_chunk(const UpdArgs& A, int chunk) {
   const long long total = (long long)N * N;
   for (long long i = (long long)chunk * kBatchChunk + threadIdx.x;
        i < (long long)(chunk + 1) * kBatchChunk && i < total; i += NTHR) {
-    const int gx = (int)(i % N), gy = (int)(i / N);
+    const int gx = (int)((unsigned)i % (unsigned)N), gy = (int)((unsigned)i / (unsigned)N);
     if (!(gx > 0 && gx < n && gy > 0 && gy < n)) continue;
     cplx<float> v = ldcg_(A.e + i);
     if (A.c != nullptr) {
@@ -125,7 +125,7 @@ __device__ __forceinline__ void corrf_chunk(const CorrArgsF& A, int chunk) {
   const long long total = (long long)N * N;
   for (long long i = (long long)chunk * kBatchChunk + threadIdx.x;
        i < (long long)(chunk + 1) * kBatchChunk && i < total; i += NTHR) {
-    const int gx = (int)(i % N), gy = (int)(i / N);
+    const int gx = (int)((unsigned)i % (unsigned)N), gy = (int)((unsigned)i / (unsigned)N);
     cplx<float> v = cz<float>();
     if (gx > 0 && gx < n && gy > 0 && gy < n) {
       v = ldcg_(A.t[s] + i);

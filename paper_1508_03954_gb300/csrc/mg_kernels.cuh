@@ -656,11 +656,11 @@ __global__ void prolong_add_kernel(int n, const cplx<R>* __restrict__ t,
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
     int g[3];
-    long long r = i;
+    unsigned r = (unsigned)i;  // vertex counts stay below 2^32
     bool inner = true;
     for (int a = 0; a < D; ++a) {
-      g[a] = (int)(r % N);
-      r /= N;
+      g[a] = (int)(r % (unsigned)N);
+      r /= (unsigned)N;
       inner = inner && g[a] > 0 && g[a] < n;
     }
     cplx<R> v = cz<R>();
@@ -693,11 +693,11 @@ __global__ void materialize_kernel(int n, const cplx<R>* __restrict__ U,
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
     int g[3];
-    long long r = i;
+    unsigned r = (unsigned)i;  // vertex counts stay below 2^32
     bool inner = true;
     for (int a = 0; a < D; ++a) {
-      g[a] = (int)(r % N);
-      r /= N;
+      g[a] = (int)(r % (unsigned)N);
+      r /= (unsigned)N;
       inner = inner && g[a] > 0 && g[a] < n;
     }
     cplx<R> v = cz<R>();
@@ -742,12 +742,12 @@ __global__ void stencil_kernel(int n, int xs, const cplx<R>* __restrict__ x,
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
     int g[3];
-    long long r = i;
+    unsigned r = (unsigned)i;  // vertex counts stay below 2^32
     bool inner = true;
     int ty = 0, ts = 1;
     for (int a = 0; a < D; ++a) {
-      g[a] = (int)(r % N);
-      r /= N;
+      g[a] = (int)(r % (unsigned)N);
+      r /= (unsigned)N;
       inner = inner && g[a] > 0 && g[a] < n;
     }
     cplx<R> v = cz<R>();
@@ -814,11 +814,11 @@ __global__ void update_kernel(int n, cplx<double>* __restrict__ u, const cplx<R>
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
     int g[3];
-    long long r = i;
+    unsigned r = (unsigned)i;  // vertex counts stay below 2^32
     bool inner = true;
     for (int a = 0; a < D; ++a) {
-      g[a] = (int)(r % N);
-      r /= N;
+      g[a] = (int)(r % (unsigned)N);
+      r /= (unsigned)N;
       inner = inner && g[a] > 0 && g[a] < n;
     }
     if (!inner) continue;

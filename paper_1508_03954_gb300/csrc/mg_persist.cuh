@@ -97,7 +97,7 @@ __device__ __forceinline__ void prolong2_chunk(const ProlongArgs<R>& A, int chun
   const long long total = (long long)N * N;
   const long long beg = (long long)chunk * kProlongChunk;
   for (long long i = beg + threadIdx.x; i < beg + kProlongChunk && i < total; i += NTHR) {
-    const int gx = (int)(i % N), gy = (int)(i / N);
+    const int gx = (int)((unsigned)i % (unsigned)N), gy = (int)((unsigned)i / (unsigned)N);
     cplx<R> v = cz<R>();
     if (gx > 0 && gx < n && gy > 0 && gy < n) {
       v = ldcg(A.t + i);
@@ -129,7 +129,7 @@ __device__ __forceinline__ void corr2_chunk(const CorrArgs<R>& A, int chunk) {
   const long long total = (long long)N * N;
   for (long long i = (long long)chunk * kCorrChunk + threadIdx.x;
        i < (long long)(chunk + 1) * kCorrChunk && i < total; i += NTHR) {
-    const int gx = (int)(i % N), gy = (int)(i / N);
+    const int gx = (int)((unsigned)i % (unsigned)N), gy = (int)((unsigned)i / (unsigned)N);
     cplx<R> v = cz<R>();
     if (gx > 0 && gx < n && gy > 0 && gy < n) {
       v = ldcg(A.t[s] + i);

@@ -1,0 +1,96 @@
+"""Parity of the complex64 inner cycles of the refinement form.
+
+One outer step of the refinement form is u1 = u0 + e, where e is m complex64
+cycles on H e = r0 (r0 = b - H u0 formed in FP64) started from e = 0.  The
+oracle runs the same m cycles in FP64 on the same inner problem, so e from
+the library must agree with the oracle's e to complex64 accuracy.  The bound
+is derived from single precision: unit roundoff 2^-24 ~ 6e-8 per operation,
+a residual row of 27 terms, a few hundred operations per vertex per cycle and
+m = 3 cycles give a few 1e-6 relative; 2e-5 leaves a margin of about 5x over
+what a correct path shows and is still far below any structural mistake (a
+wrong coefficient, tap or weight moves e by 1e-3 or more).
+
+Covered: 2D (the persistent float sweep) and 3D (the separable z-marching
+sweep on levels with n >= 27, the generic sweep below), every variant, a
+layer edge that is not aligned with coarse cells, a fully scaled grid and an
+unscaled one, and a 3D size whose level splits into ranges that cross tile
+boundaries.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1508_03954_gb300 import build as B
+from paper_1508_03954_gb300 import mg
+from paper_1508_03954_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TH = math.pi / 6
+TOL64 = 2e-5
+VARIANTS = [
+    (mg.MG_ADD, mg.MG_DLINEAR, O.ADD, O.DLINEAR),
+    (mg.MG_HB, mg.MG_DLINEAR, O.HB, O.DLINEAR),
+    (mg.MG_BPX, mg.MG_HIERARCHICAL, O.ADD, O.HIERARCHICAL),
+    (mg.MG_HB, mg.MG_HIERARCHICAL, O.HB, O.HIERARCHICAL),
+]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    B.build()
+    mg.load()
+
+
+def one_outer_step(d, depth, w, var, m=3, seed=0, kk=20.0):
+    k2 = W.constant_k2(d, depth, kk)
+    f = W.random_complex(d, depth, 100 + seed)
+    u0 = W.random_complex(d, depth, 200 + seed)
+    g = mg.Solver(d, depth, k2, TH, w)
+    o = O.Hierarchy(d, depth, k2, TH, w)
+    g.set_rhs(f)
+    o.set_rhs_nodal(f)
+    g.set_solution(u0)
+    o.set_solution(u0)
+    omega = np.array([0.6 - 0.03j * l for l in range(depth)])
+    g.set_precision(mg.MG_C64_REFINE, m)
+    st, n, rel = g.solve(var[0], omega, var[1], 1e-30, m)
+    assert st == mg.MG_NOT_CONVERGED and n == m
+    # the oracle's inner problem: H e = r0 from e = 0, m cycles
+    oi = O.Hierarchy(d, depth, k2, TH, w)
+    oi.b = o.residual()
+    O.zero_boundary(oi.b)
+    for _ in range(m):
+        oi.cycle(omega, var[2], var[3])
+    e_lib = g.get_solution() - o.u
+    err = np.linalg.norm((e_lib - oi.u).ravel()) / np.linalg.norm(oi.u.ravel())
+    g.close()
+    return err
+
+
+@pytest.mark.parametrize("var", VARIANTS, ids=["add", "hb", "bpx", "hb-hier"])
+@pytest.mark.parametrize("d,depth,w", [(2, 4, 0.1), (3, 3, 4 / 27), (3, 4, 0.1), (3, 4, 0.5), (3, 3, 0.0)])
+def test_c64_outer_step_matches_oracle(var, d, depth, w):
+    err = one_outer_step(d, depth, w, var)
+    assert err <= TOL64, f"relative L2 of e: {err:.3e}"
+
+
+def test_c64_3d_refinement_reaches_fp64_tolerance():
+    """The 3D refinement form on the definite companion reaches 1e-8 as
+    measured by the oracle's FP64 residual."""
+    depth = 4
+    k2 = W.constant_k2(3, depth, -(8 * math.pi) ** 2)
+    f = W.gaussian(3, depth, (0.5, 0.5, 0.5), 0.05)
+    g = mg.Solver(3, depth, k2, TH, 0.1)
+    o = O.Hierarchy(3, depth, k2, TH, 0.1)
+    g.set_rhs(f)
+    o.set_rhs_nodal(f)
+    g.set_precision(mg.MG_C64_REFINE, 4)
+    om = O.omega_scheme(O.EXP, 0.6, depth)
+    st, n, rel = g.solve(mg.MG_BPX, om, mg.MG_HIERARCHICAL, 1e-8, 2000)
+    assert st == mg.MG_OK and rel <= 1e-8
+    r = o.residual(g.get_solution())
+    assert np.linalg.norm(r) <= 1e-8 * np.linalg.norm(o.b) * 1.01
+    g.close()
