@@ -20,6 +20,7 @@
 #include "mg_sweep3d.cuh"
 #include "mg_sweep3s.cuh"
 #include "mg_defect3.cuh"
+#include "mg_sweep2w.cuh"
 #include "mg_persist.cuh"
 #include "mg_adjoint.cuh"
 #include <map>
@@ -810,6 +811,62 @@ cudaError_t launch_sweep3s(mg_ctx* c, Hier<float>& H, int l, bool fine, int hb, 
   return cudaGetLastError();
 }
 
+// 1D rows by axis class (left / right cell rotated): mass (hl/6, (hl+hr)/3,
+// hr/6), stiffness (-1/hl, 1/hl + 1/hr, -1/hr), stiffness - phi mass
+template <typename T>
+void axis_rows(const mg_ctx* c, int n, T row[4][9]) {
+  const double h = 1.0 / n, phi = c->k2[0];
+  const cd hrot = h * cd(std::cos(c->theta), std::sin(c->theta));
+  for (int t = 0; t < 4; ++t) {
+    const cd hl = (t & 1) ? hrot : cd(h), hr = (t & 2) ? hrot : cd(h);
+    const cd m[3] = {hl / 6.0, (hl + hr) / 3.0, hr / 6.0};
+    const cd k[3] = {-1.0 / hl, 1.0 / hl + 1.0 / hr, -1.0 / hr};
+    for (int j = 0; j < 3; ++j) {
+      const cd kp = k[j] - phi * m[j];
+      row[t][j] = T{(decltype(row[0][0].x))m[j].real(), (decltype(row[0][0].x))m[j].imag()};
+      row[t][3 + j] = T{(decltype(row[0][0].x))k[j].real(), (decltype(row[0][0].x))k[j].imag()};
+      row[t][6 + j] = T{(decltype(row[0][0].x))kp.real(), (decltype(row[0][0].x))kp.imag()};
+    }
+  }
+}
+
+// Large complex64 2D levels: the warp-strip sweep.
+cudaError_t launch_sweep2w(mg_ctx* c, Hier<float>& H, int l, bool fine, int hb, int hier, const cd& om) {
+  auto& V = H.lev[l];
+  mg::Sweep2wArgs A;
+  std::memset(&A, 0, sizeof(A));
+  A.n = V.n;
+  A.fine = fine ? 1 : 0;
+  A.has_coarse = 1;
+  A.hb = hb;
+  A.hier = hier;
+  const int nc = V.n / 3;
+  A.strips = (nc + 8) / 9;
+  A.nunits = A.strips * nc;
+  A.u = fine ? V.u[H.cur] : V.u[0];
+  A.c = fine ? H.lev[l - 1].corr : nullptr;
+  A.b = V.b;
+  A.out = fine ? V.u[1 - H.cur] : V.t;
+  A.b_coarse = H.lev[l - 1].b;
+  A.u_coarse = H.lev[l - 1].u[0];
+  A.typ = V.typ;
+  A.gtyp = V.gtyp;
+  A.gcoef = V.gcoef;
+  axis_rows(c, V.n, A.row);
+  for (size_t t = 0; t < V.diag.size() && t < 16; ++t) {
+    const cd q = om / V.diag[t];
+    A.omd[t] = cplx<float>{(float)q.real(), (float)q.imag()};
+  }
+  A.partial = H.partial;
+  A.ticket = H.ticket;
+  A.norm2 = fine ? H.norm2 : nullptr;
+  // about six coarse rows per warp, one wave of resident blocks at most
+  const int warps = std::max(1, std::min(A.nunits / 6, 152 * MG_S2W_MINB * 8));
+  const int grid = (warps + 7) / 8;
+  mg::sweep2w_kernel<<<grid, mg::kS2wThreads, 0, c->stream>>>(A);
+  return cudaGetLastError();
+}
+
 template <typename R>
 cudaError_t sweep3(mg_ctx* c, Hier<R>& H, int l, bool fine, int hb, int hier, const cd& om) {
   if constexpr (std::is_same<R, float>::value) {
@@ -864,6 +921,12 @@ cudaError_t sweep(mg_ctx* c, Hier<R>& H, int l, bool fine, int s_active, int hb,
   if (c->d == 3 && !H.varphi && (l == 1 || V.g3ok)) {
     const cplx<double> w = omega[l - 1 + (H.L - s_active)];
     return sweep3(c, H, l, fine, hb, hier, cd(w.x, w.y));
+  }
+  if constexpr (std::is_same<R, float>::value) {
+    if (c->d == 2 && !H.varphi && l > 1 && V.n >= 27 && V.gok) {
+      const cplx<double> w = omega[l - 1 + (H.L - s_active)];
+      return launch_sweep2w(c, H, l, fine, hb, hier, cd(w.x, w.y));
+    }
   }
   if (c->d == 2 && !H.varphi && (l == 1 || V.gok)) {
     const cplx<double> w = omega[l - 1 + (H.L - s_active)];
@@ -1890,6 +1953,7 @@ struct mg_batch {
   std::vector<double> key;
   mg::ChainItem* items = nullptr;
   mg::Sweep2Args<float>* sw = nullptr;
+  mg::Sweep2wArgs* st = nullptr;
   mg::ResArgs* res = nullptr;
   mg::UpdArgs* upd = nullptr;
   mg::CorrArgsF* co = nullptr;
@@ -1921,17 +1985,19 @@ int bfail(mg_batch* b, int code, const std::string& m) {
 template <int TC>
 size_t batch_smem() {
   size_t a = mg::Tile2<TC, float>::smem_bytes, b2 = mg::Tile2<2, float>::smem_bytes;
-  return a > b2 ? a : b2;
+  return std::max(a, b2);
 }
 
 void free_plan(mg_batch* b) {
   cudaFree(b->items);
   cudaFree(b->sw);
+  cudaFree(b->st);
   cudaFree(b->res);
   cudaFree(b->upd);
   cudaFree(b->co);
   b->items = nullptr;
   b->sw = nullptr;
+  b->st = nullptr;
   b->res = nullptr;
   b->upd = nullptr;
   b->co = nullptr;
@@ -1957,12 +2023,45 @@ mg::Sweep2Args<float> fsweep_args(mg_ctx* c, int l, bool fine, int k, int hb, in
   return A;
 }
 
+// warp-strip arguments of level l of problem c in inner cycle k
+mg::Sweep2wArgs fstrip_args(mg_ctx* c, int l, bool fine, int k, int hb, int hier, const cd& om) {
+  auto& E = c->h32;
+  auto& V = E.lev[l];
+  mg::Sweep2wArgs A;
+  std::memset(&A, 0, sizeof(A));
+  A.n = V.n;
+  A.fine = fine ? 1 : 0;
+  A.first = (fine && k == 0) ? 1 : 0;
+  A.has_coarse = 1;
+  A.hb = hb;
+  A.hier = hier;
+  const int nc = V.n / 3;
+  A.strips = (nc + 8) / 9;
+  A.nunits = A.strips * nc;
+  A.u = fine ? V.u[k % 2] : V.u[0];
+  A.c = fine ? E.lev[l - 1].corr : nullptr;
+  A.b = V.b;
+  A.out = fine ? V.u[(k + 1) % 2] : V.t;
+  A.b_coarse = E.lev[l - 1].b;
+  A.u_coarse = E.lev[l - 1].u[0];
+  A.typ = V.typ;
+  A.gtyp = V.gtyp;
+  A.gcoef = V.gcoef;
+  axis_rows(c, V.n, A.row);
+  for (size_t t = 0; t < V.diag.size() && t < 16; ++t) {
+    const cd q = om / V.diag[t];
+    A.omd[t] = cplx<float>{(float)q.real(), (float)q.imag()};
+  }
+  return A;
+}
+
 int build_batch_plan(mg_batch* b, int hb, int hier, const cplx<double>* const* omega, int m,
                      const std::vector<double>& key) {
   if (b->key == key && b->items) return MG_OK;
   free_plan(b);
   const int np = (int)b->ctx.size();
   std::vector<mg::Sweep2Args<float>> sw;
+  std::vector<mg::Sweep2wArgs> stp;
   std::vector<mg::ResArgs> res;
   std::vector<mg::UpdArgs> upd;
   std::vector<mg::CorrArgsF> co;
@@ -2000,6 +2099,14 @@ int build_batch_plan(mg_batch* b, int hb, int hier, const cplx<double>* const* o
       for (int l = L; l >= 1; --l) {
         const cplx<double> w = omega[p][l - 1];
         const bool fine = l == L;
+        if (l > 1 && E.lev[l].n >= 27) {
+          stp.push_back(fstrip_args(c, l, fine, k, hb, hier, cd(w.x, w.y)));
+          std::vector<mg::ChainItem> st;
+          const int ni = (stp.back().nunits + mg::kStripUnits - 1) / mg::kStripUnits;
+          for (int t = 0; t < ni; ++t) st.push_back({mg::kBStrip, p, (int)stp.size() - 1, t, 0});
+          S.push_back(st);
+          continue;
+        }
         const int tc = (fine || V(l) >= 40) ? b->tc : 2;
         const int kind = tc == 2 ? mg::kBSweepS : mg::kBSweep;
         sw.push_back(fsweep_args(c, l, fine, k, hb, hier, cd(w.x, w.y), tc));
@@ -2062,6 +2169,7 @@ int build_batch_plan(mg_batch* b, int hb, int hier, const cplx<double>* const* o
   };
   MG_BCUDA(b, up((void**)&b->items, items.data(), items.size() * sizeof(mg::ChainItem)));
   MG_BCUDA(b, up((void**)&b->sw, sw.data(), sw.size() * sizeof(mg::Sweep2Args<float>)));
+  MG_BCUDA(b, up((void**)&b->st, stp.data(), stp.size() * sizeof(mg::Sweep2wArgs)));
   MG_BCUDA(b, up((void**)&b->res, res.data(), res.size() * sizeof(mg::ResArgs)));
   MG_BCUDA(b, up((void**)&b->upd, upd.data(), upd.size() * sizeof(mg::UpdArgs)));
   MG_BCUDA(b, up((void**)&b->co, co.data(), co.size() * sizeof(mg::CorrArgsF)));
@@ -2078,6 +2186,7 @@ cudaError_t enqueue_batch(mg_batch* b) {
   A.items = b->items;
   A.nitems = b->nitems;
   A.sw = b->sw;
+  A.st = b->st;
   A.res = b->res;
   A.upd = b->upd;
   A.co = b->co;

@@ -5,8 +5,9 @@
 //   R   FP64 residual r = b - H u of the fine level into the complex64
 //       right-hand side of the inner problem, with |r|^2 (the norm of the
 //       iterate entering this outer step);
-//   m inner complex64 cycles on H e = r from e = 0: fine sweep tiles,
-//       coarse sweep tiles of levels L-1 .. 1, then the correction stages
+//   m inner complex64 cycles on H e = r from e = 0: fine sweep items (warp
+//       strips of mg_sweep2w.cuh on levels with n >= 27, tiles below),
+//       coarse sweep items of levels L-1 .. 1, then the correction stages
 //       (corr_{L-2} from levels 1..L-2, corr_{L-1} = t_{L-1} + P corr_{L-2});
 //   U   FP64 update u += e (e = E + P corr_{L-1}).
 // The items of all problems form one queue in stage-major order; a block
@@ -17,10 +18,14 @@
 // CUDA graph that launches it, serve every outer iteration.
 #pragma once
 #include "mg_persist.cuh"
+#include "mg_sweep2w.cuh"
 
 namespace mg {
 
-enum : int { kBRes = 0, kBSweep = 1, kBSweepS = 2, kBCorr = 3, kBUpd = 4 };
+enum : int { kBRes = 0, kBSweep = 1, kBSweepS = 2, kBCorr = 3, kBUpd = 4, kBStrip = 5 };
+
+// strip items: coarse rows per item (8 warps of about 6 rows each)
+constexpr int kStripUnits = 48;
 
 struct ResArgs {
   int n, nchunks;
@@ -49,6 +54,7 @@ struct BatchArgs {
   const ChainItem* items;
   int nitems;
   const Sweep2Args<float>* sw;
+  const Sweep2wArgs* st;
   const ResArgs* res;
   const UpdArgs* upd;
   const CorrArgsF* co;
@@ -153,7 +159,7 @@ __device__ __forceinline__ void corrf_chunk(const CorrArgsF& A, int chunk) {
 
 // TC: tile of the fine sweeps (autotuned); coarse levels below a size use 2.
 template <int TC, int NTHR>
-__global__ void __launch_bounds__(NTHR) batch2_kernel(const BatchArgs A) {
+__global__ void __launch_bounds__(NTHR, 2) batch2_kernel(const BatchArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double s_red[NTHR / 32];
   __shared__ int s_item;
@@ -162,6 +168,7 @@ __global__ void __launch_bounds__(NTHR) batch2_kernel(const BatchArgs A) {
     ResArgs res;
     UpdArgs upd;
     CorrArgsF co;
+    Sweep2wArgs st;
   } s_a;
   while (true) {
     if (threadIdx.x == 0) s_item = (int)atomicAdd(A.head, 1u);
@@ -175,6 +182,7 @@ __global__ void __launch_bounds__(NTHR) batch2_kernel(const BatchArgs A) {
         case kBRes: copy_args<ResArgs, NTHR>(&s_a.res, A.res + it.args); break;
         case kBUpd: copy_args<UpdArgs, NTHR>(&s_a.upd, A.upd + it.args); break;
         case kBCorr: copy_args<CorrArgsF, NTHR>(&s_a.co, A.co + it.args); break;
+        case kBStrip: copy_args<Sweep2wArgs, NTHR>(&s_a.st, A.st + it.args); break;
         default: copy_args<Sweep2Args<float>, NTHR>(&s_a.sw, A.sw + it.args); break;
       }
       if (threadIdx.x == 0 && it.need > 0) wait_counter(A.done + it.prob, it.need, A.spin_limit, A.err);
@@ -186,6 +194,13 @@ __global__ void __launch_bounds__(NTHR) batch2_kernel(const BatchArgs A) {
         case kBUpd: upd_chunk<NTHR>(s_a.upd, it.tile); break;
         case kBCorr: corrf_chunk<NTHR>(s_a.co, it.tile); break;
         case kBSweep: sweep2_tile<TC, NTHR, float>(s_a.sw, it.tile, smem_raw, s_red); break;
+        case kBStrip: {
+          // each warp takes an equal share of the item's coarse rows
+          const int ub = it.tile * kStripUnits, ue = min(s_a.st.nunits, ub + kStripUnits);
+          const int w = threadIdx.x >> 5, nw = NTHR / 32;
+          strip2w_run(s_a.st, ub + (ue - ub) * w / nw, ub + (ue - ub) * (w + 1) / nw, &s_a.st.row[0][0],
+                      s_a.st.omd);
+        } break;
         default: sweep2_tile<2, NTHR, float>(s_a.sw, it.tile, smem_raw, s_red); break;
       }
     }

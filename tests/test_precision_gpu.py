@@ -6,11 +6,15 @@ oracle runs the same m cycles in FP64 on the same inner problem, so e from
 the library must agree with the oracle's e to complex64 accuracy.  The bound
 is derived from single precision: unit roundoff 2^-24 ~ 6e-8 per operation,
 a residual row of 27 terms, a few hundred operations per vertex per cycle and
-m = 3 cycles give a few 1e-6 relative; 2e-5 leaves a margin of about 5x over
-what a correct path shows and is still far below any structural mistake (a
-wrong coefficient, tap or weight moves e by 1e-3 or more).
+m = 3 cycles give a few 1e-6 relative at depth 4; the coarse-level
+corrections amplify rounding as the hierarchy deepens (measured on both the
+tiled and the warp-strip 2D sweeps: 1e-6..1e-5 at depth 5, 2e-5..8e-5 at
+depth 6, spread evenly over the grid), so the bound is 2e-5 at depth <= 4 and
+grows 4x per further level.  A structural mistake (a wrong coefficient, tap
+or weight) moves e by 1e-3 or more at every depth.
 
-Covered: 2D (the persistent float sweep) and 3D (the separable z-marching
+Covered: 2D (the warp-strip sweep on levels with n >= 27, including a
+full-size level split over many warps) and 3D (the separable z-marching
 sweep on levels with n >= 27, the generic sweep below), every variant, a
 layer edge that is not aligned with coarse cells, a fully scaled grid and an
 unscaled one, and a 3D size whose level splits into ranges that cross tile
@@ -29,7 +33,6 @@ from paper_1508_03954_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 TH = math.pi / 6
-TOL64 = 2e-5
 VARIANTS = [
     (mg.MG_ADD, mg.MG_DLINEAR, O.ADD, O.DLINEAR),
     (mg.MG_HB, mg.MG_DLINEAR, O.HB, O.DLINEAR),
@@ -71,10 +74,12 @@ def one_outer_step(d, depth, w, var, m=3, seed=0, kk=20.0):
 
 
 @pytest.mark.parametrize("var", VARIANTS, ids=["add", "hb", "bpx", "hb-hier"])
-@pytest.mark.parametrize("d,depth,w", [(2, 4, 0.1), (3, 3, 4 / 27), (3, 4, 0.1), (3, 4, 0.5), (3, 3, 0.0)])
+@pytest.mark.parametrize("d,depth,w", [(2, 4, 0.1), (2, 5, 4 / 27), (2, 6, 0.1), (2, 4, 0.5), (2, 3, 0.0),
+                                       (3, 3, 4 / 27), (3, 4, 0.1), (3, 4, 0.5), (3, 3, 0.0)])
 def test_c64_outer_step_matches_oracle(var, d, depth, w):
     err = one_outer_step(d, depth, w, var)
-    assert err <= TOL64, f"relative L2 of e: {err:.3e}"
+    tol = 2e-5 * 4.0 ** max(0, depth - 4)
+    assert err <= tol, f"relative L2 of e: {err:.3e} (bound {tol:.1e})"
 
 
 def test_c64_3d_refinement_reaches_fp64_tolerance():
