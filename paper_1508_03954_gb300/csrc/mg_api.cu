@@ -664,12 +664,14 @@ int build_chain2(mg_ctx* c, Hier<R>& H, int s, int hb, int hier, const cplx<doub
   unsigned need = 0;
   for (int l = s - 1; l >= 1; --l) {
     const cplx<double> w = omega[l - 1 + (H.L - s)];
-    // small levels take 2-coarse-cell tiles so that a stage spreads over
-    // many SMs (its latency is set by one tile's FP64 work)
-    const int TC = (H.lev[l].n / 3 + 1) >= 60 ? 4 : 2;
+    // small levels take 2-coarse-cell tiles, and 1-cell tiles once those
+    // still fit one per SM, so that a stage spreads over many SMs (its
+    // latency is set by one tile's FP64 work)
+    const int ncv = H.lev[l].n / 3 + 1;
+    const int TC = ncv >= 60 ? 4 : (ncv * ncv <= 152 ? 1 : 2);
     s2.push_back(sweep2_args(H, l, hb, hier, cd(w.x, w.y), TC));
     const int nt = s2.back().ntiles;
-    const int kind = TC == 4 ? mg::kItemSweep2 : mg::kItemSweep2s;
+    const int kind = TC == 4 ? mg::kItemSweep2 : (TC == 2 ? mg::kItemSweep2s : mg::kItemSweep2t);
     for (int t = 0; t < nt; ++t) items.push_back({kind, 0, (int)s2.size() - 1, t, need});
     need += nt;
   }
@@ -686,8 +688,10 @@ int build_chain2(mg_ctx* c, Hier<R>& H, int s, int hb, int hier, const cplx<doub
     for (int l = lo; l <= tgt; ++l) ca.t[l] = H.lev[l].t;
     ca.base = base;
     ca.out = H.lev[tgt].corr;
+    // about two items per SM, 64 .. 256 vertices each (one per thread at most)
+    ca.chunk = (int)std::min<size_t>(256, std::max<size_t>(64, (H.lev[tgt].nv / 304 + 63) / 64 * 64));
     co.push_back(ca);
-    const int nch = (int)((H.lev[tgt].nv + mg::kCorrChunk - 1) / mg::kCorrChunk);
+    const int nch = (int)((H.lev[tgt].nv + ca.chunk - 1) / ca.chunk);
     for (int t = 0; t < nch; ++t) items.push_back({mg::kItemCorr2, 0, (int)co.size() - 1, t, need});
     need += nch;
   };

@@ -24,7 +24,7 @@
 
 namespace mg {
 
-enum : int { kItemSweep2 = 0, kItemProlong2 = 1, kItemCorr2 = 2, kItemSweep2s = 3 };
+enum : int { kItemSweep2 = 0, kItemProlong2 = 1, kItemCorr2 = 2, kItemSweep2s = 3, kItemSweep2t = 4 };
 
 struct ChainItem {
   int kind;       // kItemSweep2 / kItemProlong2
@@ -52,11 +52,12 @@ constexpr int kMaxChainLevels = 12;
 template <typename R>
 struct CorrArgs {
   int s, lo;                          // target level (3^s cells), first level summed
+  int chunk;                          // vertices per item (chain); 0: kCorrChunk
   const cplx<R>* t[kMaxChainLevels];  // t[l] for l = lo..s (index l)
   const cplx<R>* base;                // corr_{lo-1} or null
   cplx<R>* out;                       // corr_s
 };
-constexpr int kCorrChunk = 256;          // vertices per item
+constexpr int kCorrChunk = 256;          // vertices per item unless the plan sets one
 
 template <typename R>
 struct ChainArgs {
@@ -127,8 +128,9 @@ __device__ __forceinline__ void corr2_chunk(const CorrArgs<R>& A, int chunk) {
   for (int k = 0; k < s; ++k) n *= 3;
   const int N = n + 1;
   const long long total = (long long)N * N;
-  for (long long i = (long long)chunk * kCorrChunk + threadIdx.x;
-       i < (long long)(chunk + 1) * kCorrChunk && i < total; i += NTHR) {
+  const int csz = A.chunk > 0 ? A.chunk : kCorrChunk;
+  for (long long i = (long long)chunk * csz + threadIdx.x; i < (long long)(chunk + 1) * csz && i < total;
+       i += NTHR) {
     const int gx = (int)((unsigned)i % (unsigned)N), gy = (int)((unsigned)i / (unsigned)N);
     cplx<R> v = cz<R>();
     if (gx > 0 && gx < n && gy > 0 && gy < n) {
@@ -198,7 +200,8 @@ __global__ void __launch_bounds__(NTHR) chain2_kernel(const ChainArgs<R> A) {
     const ChainItem it = A.items[i];
     unsigned long long t0 = 0, t1 = 0;
     if (A.trace != nullptr && threadIdx.x == 0) t0 = gtimer();
-    if (it.kind == kItemSweep2 || it.kind == kItemSweep2s) copy_args<Sweep2Args<R>, NTHR>(&s_a, A.s2 + it.args);
+    if (it.kind == kItemSweep2 || it.kind == kItemSweep2s || it.kind == kItemSweep2t)
+      copy_args<Sweep2Args<R>, NTHR>(&s_a, A.s2 + it.args);
     else if (it.kind == kItemProlong2) copy_args<ProlongArgs<R>, NTHR>(&s_p, A.pr + it.args);
     else copy_args<CorrArgs<R>, NTHR>(&s_co, A.co + it.args);
     if (threadIdx.x == 0 && it.need > 0) wait_counter(A.done + it.prob, it.need, A.spin_limit, A.err);
@@ -209,6 +212,8 @@ __global__ void __launch_bounds__(NTHR) chain2_kernel(const ChainArgs<R> A) {
       sweep2_tile<4, NTHR, R>(s_a, it.tile, smem_raw, s_red);
     } else if (it.kind == kItemSweep2s) {
       sweep2_tile<2, NTHR, R>(s_a, it.tile, smem_raw, s_red);
+    } else if (it.kind == kItemSweep2t) {
+      sweep2_tile<1, NTHR, R>(s_a, it.tile, smem_raw, s_red);
     } else if (it.kind == kItemProlong2) {
       prolong2_chunk<NTHR, R>(s_p, it.tile);
     } else {

@@ -138,37 +138,54 @@ __device__ __forceinline__ void sweep2_tile(const Sweep2Args<R>& A, int tile, un
       s_c[i] = in ? ldcg(A.c + (long long)cy * (nc + 1) + cx) : cz<R>();
     }
   }
-  __syncthreads();
 
-  // P1: pending correction interpolated along x for every coarse row of the box
+  // b of this thread's P3 points, in flight together with the u loads below
+  constexpr int KB = (SR * SR + NTHR - 1) / NTHR;
+  C bpre[KB];
+#pragma unroll
+  for (int k = 0; k < KB; ++k) {
+    const int i = threadIdx.x + k * NTHR;
+    const int gx = x0 - 2 + i % SR, gy = y0 - 2 + i / SR;
+    bpre[k] = (i < SR * SR && gx > 0 && gx < n && gy > 0 && gy < n) ? ldcg(A.b + (long long)gy * N + gx)
+                                                                      : cz<R>();
+  }
+  // P2: u = U + P c on the u box (zero outside the interior).  Without a
+  // pending correction the u loads overlap those of P0 (one barrier less).
+  auto load_u = [&](bool with_c) {
+    for (int i = threadIdx.x; i < SU * SU; i += NTHR) {
+      const int bx = i % SU, by = i / SU;
+      const int gx = x0 - 3 + bx, gy = y0 - 3 + by;
+      C v = cz<R>();
+      if (gx > 0 && gx < n && gy > 0 && gy < n) {
+        if (!(A.fine && A.first)) v = ldcg(A.u + (long long)gy * N + gx);
+        if (with_c) {
+          const int oy = by % 3, cy = by / 3;
+          v = lerp2acc(v, w0<R>(oy), s_X[cy * SU + bx], w1<R>(oy), s_X[(cy + 1) * SU + bx]);
+        }
+      }
+      s_u[i] = v;
+    }
+  };
+  if (!use_c) load_u(false);
+  __syncthreads();
   if (use_c) {
+    // P1: pending correction interpolated along x for every coarse row of the box
     for (int i = threadIdx.x; i < SC * SU; i += NTHR) {
       const int bx = i % SU, cy = i / SU;
       const int ox = bx % 3, cx = bx / 3;  // box origin x0-3 is a c-point
       s_X[i] = lerp2(w0<R>(ox), s_c[cy * SC + cx], w1<R>(ox), s_c[cy * SC + cx + 1]);
     }
     __syncthreads();
+    load_u(true);
+    __syncthreads();
   }
-
-  // P2: u = U + P c on the u box (zero outside the interior)
-  for (int i = threadIdx.x; i < SU * SU; i += NTHR) {
-    const int bx = i % SU, by = i / SU;
-    const int gx = x0 - 3 + bx, gy = y0 - 3 + by;
-    C v = cz<R>();
-    if (gx > 0 && gx < n && gy > 0 && gy < n) {
-      if (!(A.fine && A.first)) v = ldcg(A.u + (long long)gy * N + gx);
-      if (use_c) {
-        const int oy = by % 3, cy = by / 3;
-        v = lerp2acc(v, w0<R>(oy), s_X[cy * SU + bx], w1<R>(oy), s_X[(cy + 1) * SU + bx]);
-      }
-    }
-    s_u[i] = v;
-  }
-  __syncthreads();
 
   // P3: r = b - H u on the r box; |r|^2 over the owned interior
   double nrm = 0.0;
-  for (int i = threadIdx.x; i < SR * SR; i += NTHR) {
+#pragma unroll
+  for (int kb = 0; kb < KB; ++kb) {
+    const int i = threadIdx.x + kb * NTHR;
+    if (i >= SR * SR) break;
     const int qx = i % SR, qy = i / SR;
     const int gx = x0 - 2 + qx, gy = y0 - 2 + qy;
     C r = cz<R>();
@@ -177,7 +194,7 @@ __device__ __forceinline__ void sweep2_tile(const Sweep2Args<R>& A, int tile, un
       const int t = s_tx[bx] + 4 * s_ty[by];
       const C* cf = s_coef + t * 9;
       const C* up = s_u + by * SU + bx;
-      r = ldcg(A.b + (long long)gy * N + gx);
+      r = bpre[kb];
       if ((A.realrow >> t) & 1u) {
 #pragma unroll
         for (int k = 0; k < 9; ++k) {

@@ -21,13 +21,9 @@
 // thread marches its column along z holding u(z-1), u(z), u(z+1) in
 // registers: the z-pass runs in registers, the y-pass reads the neighbouring
 // rows from shared memory, the x-pass takes its neighbours by warp shuffles.
-// Planes of U and b stream into per-thread slots of shared-memory rings by
-// cp.async three planes ahead.  Warps 1..30 (the r box [x0-2, x0+27]^2,
-// enough for the restriction of the owned coarse vertices and for the
-// c-point Jacobi update of the next tile's first c-point under BPX) compute
-// the residual, the Jacobi update and the fine outputs of plane z while
-// warps 0 and 31, which hold only halo rows, restrict plane z-1 to the
-// coarse vertices and write the coarse outputs.  One barrier per fine plane.
+// The r box is [x0-2, x0+27]^2 (lanes/warps 1..30), enough for the
+// restriction of the owned coarse vertices and for the c-point Jacobi update
+// of the next tile's first c-point (BPX).  One barrier per fine plane.
 //
 // Work split.  The (tile, coarse plane) units of the level are split into
 // gridDim.x contiguous ranges of equal size (one block per SM), so the load
@@ -38,14 +34,7 @@
 
 namespace mg {
 
-#ifndef MG_S3S_CPASYNC
-#define MG_S3S_CPASYNC 1  // U and b planes through cp.async rings (else register prefetch)
-#endif
-#ifndef MG_S3S_XR_SHFL
-#define MG_S3S_XR_SHFL 0  // x-restriction by shuffles in the residual warps (else by warps 0, 31)
-#endif
 constexpr int kS3sThreads = 1024;
-constexpr int kS3sMaxN = 729;  // largest level (3D depth 6)
 
 struct Sweep3sArgs {
   int n, fine, first, has_coarse, hb, hier;
@@ -71,18 +60,13 @@ struct Sweep3sArgs {
 struct Sweep3sShared {
   cplx<float> za[2][32][32];  // M_z u of the plane (two planes in flight)
   cplx<float> zb[2][32][32];  // (K_z - phi M_z) u
-  cplx<float> ur[4][32][32];  // ring of U planes (each thread its own column)
-  cplx<float> br[4][32][32];  // ring of b planes
-  cplx<float> r[2][32][32];   // residual planes, read by the restricting warps
   cplx<float> pv[3][32][32];  // BPX: u + du of the fine planes waiting for P I du
-  cplx<float> rx[2][32][9];   // r restricted along x, c-columns of C0 .. C0+8 (two planes)
+  cplx<float> rx[2][32][10];  // r restricted along x at the c-columns of coarse C0 .. C0+9
   cplx<float> dc[10][10];     // du at the c-points of the last c-plane, coarse C0 .. C0+9
   cplx<float> q[3][11][11];   // u at the c-points of three c-planes, coarse C0-1 .. C0+9
   cplx<float> cc[12][12];     // one coarse plane of the pending correction, C0-1 .. C0+10
   cplx<float> row[4][9];
   cplx<float> omd[64];
-  cplx<float> acc[2][100];    // restriction sums of coarse planes Zc and Zc+1 per coarse column
-  uint8_t tz[kS3sMaxN + 7];   // axis class of every plane
 };
 
 template <int V> struct IC { static constexpr int value = V; };
@@ -115,17 +99,13 @@ __device__ __forceinline__ cplx<float> ld_nc(const cplx<float>* p) {
   const float2 v = __ldg(reinterpret_cast<const float2*>(p));
   return cplx<float>{v.x, v.y};
 }
+
+// 1D restriction of five values at offsets -2..2: weights 1/3, 2/3, 1, 2/3, 1/3
 __device__ __forceinline__ cplx<float> restrict5f(cplx<float> m2, cplx<float> m1, cplx<float> z,
                                                   cplx<float> p1, cplx<float> p2) {
   return cplx<float>{fmaf(m2.x + p2.x, 1.f / 3.f, fmaf(m1.x + p1.x, 2.f / 3.f, z.x)),
                      fmaf(m2.y + p2.y, 1.f / 3.f, fmaf(m1.y + p1.y, 2.f / 3.f, z.y))};
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N> __device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-// barrier 1 over the 64 threads of warps 0 and 31
-__device__ __forceinline__ void bar_restrict() { asm volatile("bar.sync 1, 64;\n" ::: "memory"); }
 
 // weight of the left (W0) and right (W1) coarse vertex at fine offset o
 template <int O> __device__ __forceinline__ constexpr float W0() {
@@ -142,44 +122,34 @@ __global__ void __launch_bounds__(kS3sThreads, 1) sweep3s_kernel(const Sweep3sAr
   using C = cplx<float>;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int n = A.n, N = n + 1, nc = n / 3;
-  const int NN = N * N, Nc = nc + 1, NNc = Nc * Nc;  // vertex counts of a level stay below 2^31
+  const long long NN = (long long)N * N, Nc = nc + 1, NNc = Nc * Nc;
   for (int i = threadIdx.x; i < 36; i += kS3sThreads) S.row[i / 9][i % 9] = A.row[i / 9][i % 9];
   for (int i = threadIdx.x; i < 64; i += kS3sThreads) S.omd[i] = A.omd[i];
-  for (int i = threadIdx.x; i <= n; i += kS3sThreads) S.tz[i] = A.typ[i];
   const bool zero_u = A.fine && A.first;
   const bool use_c = A.fine && !A.first && A.c != nullptr;
   const bool bpx = A.hier && !A.hb;
-  // warps 0 and 31 restrict; lane cl takes coarse columns cl and cl + 64 of
-  // the 10 x 10 owned ones C0 .. C0+9 (column 9 only matters on the last tile)
-  const bool cw = (warp == 0 || warp == 31) && A.has_coarse;
-  const int cl = warp == 0 ? lane : 32 + lane;
-  // the real rows of the unscaled interior, read from the parameter bank where used
-#define M0 A.row[0][0].x
-#define M1 A.row[0][1].x
-#define M2 A.row[0][2].x
-#define K0 A.row[0][3].x
-#define K1 A.row[0][4].x
-#define K2 A.row[0][5].x
-#define P0 A.row[0][6].x
-#define P1 A.row[0][7].x
-#define P2 A.row[0][8].x
+  // restriction and coarse outputs: 4 warps x 25 lanes take the 10 x 10
+  // coarse columns C0 .. C0+9 (column 9 only matters on the last tile)
+  const int ek = (warp < 4 && lane < 25) ? warp * 25 + lane : -1;
+  const bool emit = ek >= 0 && A.has_coarse;
+  const int ejx = emit ? ek % 10 : 0, ejy = emit ? ek / 10 : 0;
+  // the real rows of the unscaled interior: mass h/6 (1, 4, 1), stiffness, shifted stiffness
+  const float m0 = A.row[0][0].x, m1 = A.row[0][1].x, m2 = A.row[0][2].x;
+  const float k0 = A.row[0][3].x, k1 = A.row[0][4].x, k2 = A.row[0][5].x;
+  const float p0 = A.row[0][6].x, p1 = A.row[0][7].x, p2 = A.row[0][8].x;
   const int ox = lane % 3, oy = warp % 3;
+  const float wx1 = ox == 0 ? 0.f : (ox == 1 ? 1.f / 3.f : 2.f / 3.f), wx0 = 1.f - wx1;
+  const float wy1 = oy == 0 ? 0.f : (oy == 1 ? 1.f / 3.f : 2.f / 3.f), wy0 = 1.f - wy1;
   const bool cpx = ox == 0, cpy = oy == 0;  // c-point column (the box origin is a c-point)
-  // bilinear weights of the coarse vertices left/right (below/above) of this column
-  auto wts = [&](float& wx0, float& wx1, float& wy0, float& wy1) {
-    wx1 = ox == 0 ? 0.f : (ox == 1 ? 1.f / 3.f : 2.f / 3.f);
-    wy1 = oy == 0 ? 0.f : (oy == 1 ? 1.f / 3.f : 2.f / 3.f);
-    wx0 = 1.f - wx1;
-    wy0 = 1.f - wy1;
-  };
   const bool rrow = warp >= 1 && warp <= 30;
   float nrm = 0.f;
 
-  int unit = (int)(A.nunits * blockIdx.x / gridDim.x);
-  const int uend = (int)(A.nunits * (blockIdx.x + 1) / gridDim.x);
+  const long long U = A.nunits;
+  long long unit = U * blockIdx.x / gridDim.x;
+  const long long uend = U * (blockIdx.x + 1) / gridDim.x;
   while (unit < uend) {
-    const int tile = unit / nc, Z0 = unit % nc;
-    const int Z1 = min(nc, Z0 + (uend - unit));
+    const int tile = (int)(unit / nc), Z0 = (int)(unit % nc);
+    const int Z1 = (int)min((long long)nc, (long long)Z0 + (uend - unit));
     unit += Z1 - Z0;
     const int C0x = (tile % A.tiles_x) * 9, C0y = (tile / A.tiles_x) * 9;
     const int x0 = 3 * C0x, y0 = 3 * C0y;
@@ -188,54 +158,35 @@ __global__ void __launch_bounds__(kS3sThreads, 1) sweep3s_kernel(const Sweep3sAr
     const bool lastx = C0x + 9 >= nc, lasty = C0y + 9 >= nc;
     const bool owncol = lane >= 3 && (lane < 30 || (lane == 30 && lastx)) && warp >= 3 &&
                         (warp < 30 || (warp == 30 && lasty)) && gx <= n && gy <= n;
-    const int col = gy * N + gx;  // used only for owned or interior columns
+    const long long col = (long long)gy * N + gx;  // used only for owned or interior columns
     const int tx = (gx >= 0 && gx <= n) ? (int)A.typ[gx] : 0;
     const int ty = (gy >= 0 && gy <= n) ? (int)A.typ[gy] : 0;
     const bool xreal = __all_sync(0xffffffffu, tx == 0);
     const bool yreal = ty == 0;
     const int zs = 3 * Z0 - 2;
     auto qslot = [](int Zc) { return (Zc + 3) % 3; };
-    auto tzof = [&](int z) -> int { return (z >= 0 && z <= n) ? (int)S.tz[z] : 0; };
-    // U(z) into ring slot z & 3, b(z) likewise (rows that compute residuals)
-    auto issue = [&](int zu, int zb) {
-      C* du_ = &S.ur[zu & 3][warp][lane];
-      if (!zero_u && colin && zu > 0 && zu < n) cp_async_cplx(du_, A.u + (zu * NN + col));
-      else *du_ = cz<float>();
-      if (rrow) {
-        C* db_ = &S.br[zb & 3][warp][lane];
-        if (colin && zb > 0 && zb < n) cp_async_cplx(db_, A.b + (zb * NN + col));
-        else *db_ = cz<float>();
-      }
-      cp_async_commit();
+    auto ldU = [&](int z) -> C {
+      return (!zero_u && colin && z > 0 && z < n) ? ld_nc(A.u + z * NN + col) : cz<float>();
+    };
+    auto ldB = [&](int z) -> C {
+      return (colin && z > 0 && z < n) ? ld_nc(A.b + z * NN + col) : cz<float>();
     };
     auto ld_cc = [&](int Zc) -> C {
       const int t = threadIdx.x;
       const int cx = C0x - 1 + t % 12, cy = C0y - 1 + t / 12;
       return (use_c && t < 144 && Zc >= 0 && Zc <= nc && cx >= 0 && cx <= nc && cy >= 0 && cy <= nc)
-                 ? ld_nc(A.c + (Zc * NNc + cy * Nc + cx))
+                 ? ld_nc(A.c + Zc * NNc + (long long)cy * Nc + cx)
                  : cz<float>();
     };
     // bilinear interpolation of the coarse plane in S.cc to this column
     auto bil_cc = [&]() -> C {
-      float wx0, wx1, wy0, wy1;
-      wts(wx0, wx1, wy0, wy1);
       const int jx = lane / 3, jy = warp / 3;
       const C a = S.cc[jy][jx], b2 = S.cc[jy][jx + 1], c2 = S.cc[jy + 1][jx], d2 = S.cc[jy + 1][jx + 1];
       return cplx<float>{wy0 * (wx0 * a.x + wx1 * b2.x) + wy1 * (wx0 * c2.x + wx1 * d2.x),
                          wy0 * (wx0 * a.y + wx1 * b2.y) + wy1 * (wx0 * c2.y + wx1 * d2.y)};
     };
 
-#if !MG_S3S_CPASYNC
-    auto ldU = [&](int z) -> C {
-      return (!zero_u && colin && z > 0 && z < n) ? ld_nc(A.u + (z * NN + col)) : cz<float>();
-    };
-    auto ldB = [&](int z) -> C {
-      return (rrow && colin && z > 0 && z < n) ? ld_nc(A.b + (z * NN + col)) : cz<float>();
-    };
-    C pu[3], pb[3];
-#endif
-    cp_async_wait<0>();
-    __syncthreads();  // the previous range's shared memory is free
+    __syncthreads();  // the previous segment's shared-memory reads are done
     C cxy0 = cz<float>(), cxy1 = cz<float>(), ccpre = cz<float>();
     if (use_c) {
       if (threadIdx.x < 144) S.cc[threadIdx.x / 12][threadIdx.x % 12] = ld_cc(Z0 - 1);
@@ -248,30 +199,8 @@ __global__ void __launch_bounds__(kS3sThreads, 1) sweep3s_kernel(const Sweep3sAr
       ccpre = ld_cc(Z0 + 1);
       __syncthreads();
     }
-    // U on planes 3 Z0 - 3 (c-plane Z0 - 1) and 3 Z0 - 2, then the first steps' planes
-#if !MG_S3S_CPASYNC
+    // u on planes 3 Z0 - 3 (c-plane Z0 - 1) and 3 Z0 - 2
     C um = ldU(3 * Z0 - 3), u0 = ldU(3 * Z0 - 2);
-    pu[1] = ldU(3 * Z0 - 1);
-    pu[2] = ldU(3 * Z0);
-    pu[0] = ldU(3 * Z0 + 1);
-    pb[1] = ldB(3 * Z0 - 2);
-    pb[2] = ldB(3 * Z0 - 1);
-    pb[0] = ldB(3 * Z0);
-#else
-    {
-      C* d0 = &S.ur[(3 * Z0 - 3) & 3][warp][lane];
-      C* d1 = &S.ur[(3 * Z0 - 2) & 3][warp][lane];
-      const int za_ = 3 * Z0 - 3, zb_ = 3 * Z0 - 2;
-      if (!zero_u && colin && za_ > 0) cp_async_cplx(d0, A.u + (za_ * NN + col)); else *d0 = cz<float>();
-      if (!zero_u && colin && zb_ > 0) cp_async_cplx(d1, A.u + (zb_ * NN + col)); else *d1 = cz<float>();
-      cp_async_commit();
-    }
-    issue(3 * Z0 - 1, 3 * Z0 - 2);
-    issue(3 * Z0, 3 * Z0 - 1);
-    cp_async_wait<2>();
-    C um = S.ur[(3 * Z0 - 3) & 3][warp][lane], u0 = S.ur[(3 * Z0 - 2) & 3][warp][lane];
-    issue(3 * Z0 + 1, 3 * Z0);
-#endif
     if (use_c && colin) {
       if (3 * Z0 - 3 > 0) um = um + cxy0;
       if (3 * Z0 - 2 > 0) {
@@ -280,77 +209,60 @@ __global__ void __launch_bounds__(kS3sThreads, 1) sweep3s_kernel(const Sweep3sAr
       }
     }
     if (cpx && cpy) S.q[qslot(Z0 - 1)][warp / 3][lane / 3] = um;
-    if (cw) {
-      S.acc[0][cl] = cz<float>();
-      S.acc[1][cl] = cz<float>();
-      if (cl < 36) {
-        S.acc[0][cl + 64] = cz<float>();
-        S.acc[1][cl + 64] = cz<float>();
-      }
-    }
-    C pidp = cz<float>();
+    // prefetch: step z uses U(z + 1) and b(z), slot z mod 3
+    C pu[3], pb[3];
+    pu[1] = ldU(3 * Z0 - 1);
+    pu[2] = ldU(3 * Z0);
+    pu[0] = ldU(3 * Z0 + 1);
+    pb[1] = ldB(3 * Z0 - 2);
+    pb[2] = ldB(3 * Z0 - 1);
+    pb[0] = ldB(3 * Z0);
+    C accA = cz<float>(), accB = cz<float>(), pidp = cz<float>();
 
     // deferred work of residual plane zd, after the barrier of the next step
     auto deferred = [&](auto ozc, int zd) {
       constexpr int OZD = decltype(ozc)::value;
-      if (cw) {
-        // x-restriction of rows 1..29 at the c-columns 3 + 3 j, then along y
-        const C(*rx)[9] = S.rx[zd & 1];
-#if !MG_S3S_XR_SHFL
-        const C(*rp)[32] = S.r[zd & 1];
-        for (int p = cl; p < 29 * 9; p += 64) {
-          const int row = 1 + p / 9, x = 3 + 3 * (p % 9);
-          S.rx[zd & 1][row][p % 9] =
-              restrict5f(rp[row][x - 2], rp[row][x - 1], rp[row][x], rp[row][x + 1], rp[row][x + 2]);
+      const int bufd = zd & 1;
+      if (emit && ejx < 9 && ejy < 9) {
+        const int by = 3 + 3 * ejy;
+        const C r0 = S.rx[bufd][by - 2][ejx], r1 = S.rx[bufd][by - 1][ejx], r2 = S.rx[bufd][by][ejx];
+        const C r3 = S.rx[bufd][by + 1][ejx], r4 = S.rx[bufd][by + 2][ejx];
+        const C ry = cplx<float>{fmaf(r0.x + r4.x, 1.f / 3.f, fmaf(r1.x + r3.x, 2.f / 3.f, r2.x)),
+                                 fmaf(r0.y + r4.y, 1.f / 3.f, fmaf(r1.y + r3.y, 2.f / 3.f, r2.y))};
+        if (OZD == 0) {
+          accA = accB + ry;
+          accB = cz<float>();
+        } else {
+          accA = rfma(W0<OZD>(), ry, accA);
+          accB = rfma(W1<OZD>(), ry, accB);
         }
-        bar_restrict();
-#endif
+        if (OZD == 2) {
+          const int Zc = (zd - 2) / 3;
+          const int cx = C0x + ejx, cy = C0y + ejy;
+          if (Zc >= Z0 && Zc < Z1 && cx <= nc && cy <= nc && (ejx < 9 || cx == nc) && (ejy < 9 || cy == nc)) {
+            const bool inner = cx > 0 && cx < nc && cy > 0 && cy < nc && Zc > 0 && Zc < nc;
+            C bs = cz<float>(), uc = cz<float>();
+            if (inner) {
+              bs = accA;
+              const int gt = A.gtyp[cx] + kMaxG3 * (A.gtyp[cy] + kMaxG3 * A.gtyp[Zc]);
+              const C* gc = A.gcoef + gt * 27;
 #pragma unroll
-        for (int t = 0; t < 2; ++t) {
-          const int k = cl + 64 * t;
-          if (k >= 100) continue;
-          const int ejx = k % 10, ejy = k / 10;
-          if (ejx < 9 && ejy < 9) {
-            const int by = 3 + 3 * ejy;
-            const C ry = restrict5f(rx[by - 2][ejx], rx[by - 1][ejx], rx[by][ejx], rx[by + 1][ejx], rx[by + 2][ejx]);
-            if (OZD == 0) {
-              S.acc[0][k] = S.acc[1][k] + ry;
-              S.acc[1][k] = cz<float>();
-            } else {
-              S.acc[0][k] = rfma(W0<OZD>(), ry, S.acc[0][k]);
-              S.acc[1][k] = rfma(W1<OZD>(), ry, S.acc[1][k]);
-            }
-          }
-          if (OZD == 2) {
-            const int Zc = (zd - 2) / 3;
-            const int cx = C0x + ejx, cy = C0y + ejy;
-            if (Zc >= Z0 && Zc < Z1 && cx <= nc && cy <= nc && (ejx < 9 || cx == nc) && (ejy < 9 || cy == nc)) {
-              const bool inner = cx > 0 && cx < nc && cy > 0 && cy < nc && Zc > 0 && Zc < nc;
-              C bs = cz<float>(), uc = cz<float>();
-              if (inner) {
-                bs = S.acc[0][k];
-                const int gt = A.gtyp[cx] + kMaxG3 * (A.gtyp[cy] + kMaxG3 * A.gtyp[Zc]);
-                const C* gc = A.gcoef + gt * 27;
+              for (int kz = 0; kz < 3; ++kz) {
+                const int qs = qslot(Zc - 1 + kz);
 #pragma unroll
-                for (int kz = 0; kz < 3; ++kz) {
-                  const int qs = qslot(Zc - 1 + kz);
-#pragma unroll
-                  for (int kk = 0; kk < 9; ++kk)
-                    bs = cfma(ld_nc(gc + kz * 9 + kk), S.q[qs][ejy + kk / 3][ejx + kk % 3], bs);
-                }
-                uc = S.q[qslot(Zc)][ejy + 1][ejx + 1];
+                for (int k = 0; k < 9; ++k)
+                  bs = cfma(ld_nc(gc + kz * 9 + k), S.q[qs][ejy + k / 3][ejx + k % 3], bs);
               }
-              const int ci = Zc * NNc + cy * Nc + cx;
-              A.b_coarse[ci] = bs;
-              A.u_coarse[ci] = uc;
+              uc = S.q[qslot(Zc)][ejy + 1][ejx + 1];
             }
+            const long long ci = Zc * NNc + (long long)cy * Nc + cx;
+            A.b_coarse[ci] = bs;
+            A.u_coarse[ci] = uc;
           }
         }
       }
       if (bpx && OZD == 0 && owncol) {
         // P I du on this column from the c-points of c-plane zd / 3
-        float wx0, wx1, wy0, wy1;
-        wts(wx0, wx1, wy0, wy1);
         const int jx = lane / 3 - 1, jy = warp / 3 - 1;
         const C a = S.dc[jy][jx];
         const C b2 = ox ? S.dc[jy][jx + 1] : cz<float>();
@@ -374,14 +286,9 @@ __global__ void __launch_bounds__(kS3sThreads, 1) sweep3s_kernel(const Sweep3sAr
       constexpr int OZP = (OZ + 1) % 3;
       const int zp = z + 1;
       const int buf = z & 1;
-      // phase 1: u on plane z + 1 (its copy was issued three steps ago)
-#if MG_S3S_CPASYNC
-      cp_async_wait<2>();
-      C up = S.ur[zp & 3][warp][lane];
-#else
-      C up = pu[OZ];
-#endif
+      // phase 1: u on plane z + 1
       if (OZP == 0) cxy0 = cxy1;
+      C up = pu[OZ];
       if (use_c && colin && zp > 0 && zp < n) {
         up = rfma(W0<OZP>(), cxy0, up);
         if (OZP != 0) up = rfma(W1<OZP>(), cxy1, up);
@@ -389,20 +296,13 @@ __global__ void __launch_bounds__(kS3sThreads, 1) sweep3s_kernel(const Sweep3sAr
       if (OZP == 0 && cpx && cpy) S.q[qslot(zp / 3)][warp / 3][lane / 3] = up;
       if (OZP == 2 && use_c && threadIdx.x < 144) S.cc[threadIdx.x / 12][threadIdx.x % 12] = ccpre;
       if (OZP == 0 && use_c) ccpre = ld_cc(zp / 3 + 2);
-#if MG_S3S_CPASYNC
-      const C bz = rrow ? S.br[z & 3][warp][lane] : cz<float>();
-      issue(z + 4, z + 3);
-#else
-      const C bz = pb[OZ];
       pu[OZ] = ldU(z + 4);
-      pb[OZ] = ldB(z + 3);
-#endif
       // z-pass (class of plane z is uniform over the block)
-      const int tz = tzof(z);
+      const int tz = (z >= 0 && z <= n) ? (int)__ldg(A.typ + z) : 0;
       C za, zb;
       if (tz == 0) {
-        za = tap3r(M0, M1, M2, um, u0, up);
-        zb = tap3r(P0, P1, P2, um, u0, up);
+        za = tap3r(m0, m1, m2, um, u0, up);
+        zb = tap3r(p0, p1, p2, um, u0, up);
       } else {
         za = tap3c_acc(&S.row[tz][0], um, u0, up, cz<float>());
         zb = tap3c_acc(&S.row[tz][6], um, u0, up, cz<float>());
@@ -413,41 +313,32 @@ __global__ void __launch_bounds__(kS3sThreads, 1) sweep3s_kernel(const Sweep3sAr
       // phase 2: deferred work of plane z - 1; coarse correction plane for the next steps
       if (z > zs) deferred(IC<(OZ + 2) % 3>{}, z - 1);
       if (OZP == 0 && use_c) cxy1 = bil_cc();
-      // phase 3: residual on plane z (warps 1..30)
+      // phase 3: residual on plane z
+      const bool zin = z > 0 && z < n;
+      const bool zown = (z >= 3 * Z0 && z < 3 * Z1) || z == n;
+      C r = cz<float>();
       if (rrow) {
-        const bool zin = z > 0 && z < n;
-        const bool zown = (z >= 3 * Z0 && z < 3 * Z1) || z == n;
         const C am = S.za[buf][warp - 1][lane], ap = S.za[buf][warp + 1][lane];
         const C bm = S.zb[buf][warp - 1][lane], bp = S.zb[buf][warp + 1][lane];
         C cy, ey;
         if (yreal) {
-          cy = tap3r_acc(K0, K1, K2, am, za, ap, tap3r(M0, M1, M2, bm, zb, bp));
-          ey = tap3r(M0, M1, M2, am, za, ap);
+          cy = tap3r_acc(k0, k1, k2, am, za, ap, tap3r(m0, m1, m2, bm, zb, bp));
+          ey = tap3r(m0, m1, m2, am, za, ap);
         } else {
           const C* rw = &S.row[ty][0];
           cy = tap3c_acc(rw + 3, am, za, ap, tap3c_acc(rw, bm, zb, bp, cz<float>()));
           ey = tap3c_acc(rw, am, za, ap, cz<float>());
         }
-        const C cl_ = shfl_c(cy, 1, true), cr_ = shfl_c(cy, 1, false);
-        const C el_ = shfl_c(ey, 1, true), er_ = shfl_c(ey, 1, false);
+        const C cl = shfl_c(cy, 1, true), cr = shfl_c(cy, 1, false);
+        const C el = shfl_c(ey, 1, true), er = shfl_c(ey, 1, false);
         C hu;
         if (xreal) {
-          hu = tap3r_acc(K0, K1, K2, el_, ey, er_, tap3r(M0, M1, M2, cl_, cy, cr_));
+          hu = tap3r_acc(k0, k1, k2, el, ey, er, tap3r(m0, m1, m2, cl, cy, cr));
         } else {
           const C* rw = &S.row[tx][0];
-          hu = tap3c_acc(rw + 3, el_, ey, er_, tap3c_acc(rw, cl_, cy, cr_, cz<float>()));
+          hu = tap3c_acc(rw + 3, el, ey, er, tap3c_acc(rw, cl, cy, cr, cz<float>()));
         }
-        C r = cz<float>();
-        if (colin && zin && lane >= 1 && lane <= 30) r = bz - hu;
-#if MG_S3S_XR_SHFL
-        if (A.has_coarse) {
-          const C r1l = shfl_c(r, 1, true), r1r = shfl_c(r, 1, false);
-          const C r2l = shfl_c(r, 2, true), r2r = shfl_c(r, 2, false);
-          if (cpx && lane >= 3 && lane <= 27) S.rx[buf][warp][lane / 3 - 1] = restrict5f(r2l, r1l, r, r1r, r2r);
-        }
-#else
-        if (A.has_coarse) S.r[buf][warp][lane] = r;
-#endif
+        if (colin && zin && lane >= 1 && lane <= 30) r = pb[OZ] - hu;
         if (owncol && zown) nrm = fmaf(r.x, r.x, fmaf(r.y, r.y, nrm));
         // Jacobi update, c-point mask (hb), outputs or BPX hold
         C du = S.omd[tx + 4 * ty + 16 * tz] * r;
@@ -459,7 +350,16 @@ __global__ void __launch_bounds__(kS3sThreads, 1) sweep3s_kernel(const Sweep3sAr
           S.pv[OZ == 1 ? 0 : (OZ == 2 ? 1 : 2)][warp][lane] = v;
         }
         if (bpx && OZ == 0 && cpx && cpy && lane >= 3 && warp >= 3) S.dc[warp / 3 - 1][lane / 3 - 1] = du;
+        // restriction along x to the c-columns
+        if (A.has_coarse) {
+          const C r1l = shfl_c(r, 1, true), r1r = shfl_c(r, 1, false);
+          const C r2l = shfl_c(r, 2, true), r2r = shfl_c(r, 2, false);
+          const C rr = cplx<float>{fmaf(r2l.x + r2r.x, 1.f / 3.f, fmaf(r1l.x + r1r.x, 2.f / 3.f, r.x)),
+                                   fmaf(r2l.y + r2r.y, 1.f / 3.f, fmaf(r1l.y + r1r.y, 2.f / 3.f, r.y))};
+          if (cpx && lane >= 3 && lane <= 30) S.rx[buf][warp][lane / 3 - 1] = rr;
+        }
       }
+      pb[OZ] = ldB(z + 3);
       um = u0;
       u0 = up;
     };
@@ -472,34 +372,18 @@ __global__ void __launch_bounds__(kS3sThreads, 1) sweep3s_kernel(const Sweep3sAr
     __syncthreads();
     deferred(IC<0>{}, 3 * Z1);
     // the boundary coarse plane nc belongs to the range that ends there
-    if (Z1 == nc && cw) {
-#pragma unroll
-      for (int t = 0; t < 2; ++t) {
-        const int k = cl + 64 * t;
-        if (k >= 100) continue;
-        const int ejx = k % 10, ejy = k / 10;
-        const int cx = C0x + ejx, cy = C0y + ejy;
-        if (cx <= nc && cy <= nc && (ejx < 9 || cx == nc) && (ejy < 9 || cy == nc)) {
-          const int ci = nc * NNc + cy * Nc + cx;
-          A.b_coarse[ci] = cz<float>();
-          A.u_coarse[ci] = cz<float>();
-        }
+    if (Z1 == nc && emit) {
+      const int cx = C0x + ejx, cy = C0y + ejy;
+      if (cx <= nc && cy <= nc && (ejx < 9 || cx == nc) && (ejy < 9 || cy == nc)) {
+        const long long ci = nc * NNc + (long long)cy * Nc + cx;
+        A.b_coarse[ci] = cz<float>();
+        A.u_coarse[ci] = cz<float>();
       }
     }
   }
-  cp_async_wait<0>();
   if (A.fine && A.norm2 != nullptr)
     block_norm_finish_tile<kS3sThreads>((double)nrm, s_red, A.partial, A.ticket, A.norm2, blockIdx.x,
                                          gridDim.x);
 }
-#undef M0
-#undef M1
-#undef M2
-#undef K0
-#undef K1
-#undef K2
-#undef P0
-#undef P1
-#undef P2
 
 }  // namespace mg
