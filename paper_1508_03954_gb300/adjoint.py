@@ -22,7 +22,7 @@ from . import mg
 
 class SolveOptions:
     def __init__(self, variant=mg.MG_ADD, transfer=mg.MG_DLINEAR, omega=None, tol=1e-10,
-                 max_cycles=4000, precision=mg.MG_C64_REFINE, inner_cycles=4):
+                 max_cycles=4000, precision=mg.MG_C64_REFINE, inner_cycles=16):
         self.variant, self.transfer, self.omega = variant, transfer, omega
         self.tol, self.max_cycles = tol, max_cycles
         self.precision, self.inner_cycles = precision, inner_cycles

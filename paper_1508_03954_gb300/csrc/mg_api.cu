@@ -606,8 +606,7 @@ cudaError_t sweep2(mg_ctx* c, Hier<R>& H, int l, bool fine, int hb, int hier, co
     const int tl = (nc + 8) / 8;
     A.tiles_x = tl;
     A.ntiles = tl * tl;
-    cudaError_t e = cudaMemsetAsync(c->chain_ctr + 32, 0, sizeof(unsigned), c->stream);
-    if (e != cudaSuccess) return e;
+    // queue head chain_ctr[32] and exit counter [33] are zero between launches
     const int grid = std::min(A.ntiles, 152 * std::max(1, c->fine_bpsm));
     mg::sweep2p_kernel<8, 256, R><<<grid, 256, mg::Tile2<8, R>::smem_bytes, c->stream>>>(
         A, V.order8, c->chain_ctr + 32, c->tracing ? c->trace : nullptr);
@@ -731,22 +730,32 @@ int build_chain2(mg_ctx* c, Hier<R>& H, int s, int hb, int hier, const cplx<doub
 
 template <typename R>
 cudaError_t launch_chain2(mg_ctx* c, const typename Hier<R>::ChainPlan& cp) {
-  cudaError_t e = cudaMemsetAsync(c->chain_ctr, 0, 2 * sizeof(unsigned), c->stream);
-  if (e != cudaSuccess) return e;
   mg::ChainArgs<R> A;
   A.items = cp.items;
   A.nitems = cp.nitems;
   A.s2 = cp.s2;
   A.pr = cp.pr;
   A.co = cp.co;
-  A.head = c->chain_ctr;
+  A.head = c->chain_ctr;  // [0] head, [1] completions, [2] exits: zero between launches
   A.done = c->chain_ctr + 1;
+  A.exitc = c->chain_ctr + 2;
   A.err = c->dev_err;
   A.spin_limit = c->spin_limit;
   A.trace = c->tracing ? c->trace + 4 * kTraceFine : nullptr;
   A.stall = c->debug_stall ? c->chain_ctr + 48 : nullptr;  // stays zero
-  mg::chain2_kernel<256, R><<<cp.grid, 256, mg::Tile2<4, R>::smem_bytes, c->stream>>>(A);
-  return cudaGetLastError();
+  // programmatic dependent launch: the chain's blocks are scheduled while the
+  // fine sweep drains and wait in the kernel until its writes are visible
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(cp.grid);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = mg::Tile2<4, R>::smem_bytes;
+  cfg.stream = c->stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, mg::chain2_kernel<256, R>, A);
 }
 
 // 3D levels with a constant shift: the z-marching Galerkin-row sweep.
@@ -1341,6 +1350,7 @@ int mg_create(int d, int depth, const double* k2_field, double theta, double lay
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = configure_kernels();
     if (e == cudaSuccess) e = cudaMalloc(&c->chain_ctr, 64 * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(c->chain_ctr, 0, 64 * sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMalloc(&c->dev_err, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemset(c->dev_err, 0, sizeof(unsigned));
     if (e == cudaSuccess)

@@ -67,6 +67,7 @@ struct ChainArgs {
   const ProlongArgs<R>* pr;
   const CorrArgs<R>* co;
   unsigned* head;        // queue head, zero at launch
+  unsigned* exitc;       // blocks that left the queue; the last one zeroes the counters
   unsigned* done;        // per-problem completion counters, zero at launch
   unsigned* err;         // set when a bounded wait gave up
   unsigned spin_limit;   // polls before giving up
@@ -184,6 +185,27 @@ __device__ __forceinline__ void wait_counter(const unsigned* ctr, unsigned need,
   }
 }
 
+// Programmatic dependent launch: a dependent grid may start before the grid it
+// follows has finished; it waits here until that grid's writes are visible.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+// Lets the dependent grid be scheduled once every block has passed this point.
+__device__ __forceinline__ void pdl_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+// The last block to leave a persistent queue zeroes its counters for the
+// next launch (no memset node between launches).
+__device__ __forceinline__ void queue_exit(unsigned* exitc, unsigned* a, unsigned* b) {
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(exitc, 1u) == gridDim.x - 1) {
+      *a = 0u;
+      if (b != nullptr) *b = 0u;
+      *exitc = 0u;
+      __threadfence();
+    }
+  }
+}
+
 template <int NTHR, typename R = double>
 __global__ void __launch_bounds__(NTHR) chain2_kernel(const ChainArgs<R> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -192,11 +214,15 @@ __global__ void __launch_bounds__(NTHR) chain2_kernel(const ChainArgs<R> A) {
   __shared__ __align__(16) Sweep2Args<R> s_a;
   __shared__ __align__(16) ProlongArgs<R> s_p;
   __shared__ __align__(16) CorrArgs<R> s_co;
+  pdl_wait();
   while (true) {
     if (threadIdx.x == 0) s_item = (int)atomicAdd(A.head, 1u);
     __syncthreads();
     const int i = s_item;
-    if (i >= A.nitems) break;
+    if (i >= A.nitems) {
+      queue_exit(A.exitc, A.head, A.done);
+      break;
+    }
     const ChainItem it = A.items[i];
     unsigned long long t0 = 0, t1 = 0;
     if (A.trace != nullptr && threadIdx.x == 0) t0 = gtimer();
@@ -243,11 +269,18 @@ __global__ void __launch_bounds__(NTHR) sweep2p_kernel(const Sweep2Args<R> A, co
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double s_red[NTHR / 32];
   __shared__ int s_k;
+  // every block of this grid is resident from the start (one wave), so the
+  // coarse chain may be scheduled on SMs as soon as they free up; it waits
+  // for this grid's writes before it reads anything
+  pdl_launch_dependents();
   while (true) {
     if (threadIdx.x == 0) s_k = (int)atomicAdd(head, 1u);
     __syncthreads();
     const int k = s_k;
-    if (k >= A.ntiles) break;
+    if (k >= A.ntiles) {
+      queue_exit(head + 1, head, nullptr);
+      break;
+    }
     const unsigned long long t0 = (trace != nullptr && threadIdx.x == 0) ? gtimer() : 0ull;
     sweep2_tile<TC, NTHR, R>(A, order[k], smem_raw, s_red);
     __syncthreads();
