@@ -73,6 +73,7 @@ struct Hier {
     // 2D FP64 path: Galerkin rows of G_{l-1} = R H_l P per coarse row class
     bool gok = false;
     int* order8 = nullptr;      // fine tiles (8 coarse cells) by decreasing cost
+    unsigned* tflags = nullptr; // per such tile: generation + 1 once written (chain overlap)
     uint8_t* gtyp = nullptr;
     cplx<R>* gcoef = nullptr;
   };
@@ -433,6 +434,7 @@ int build_hier(mg_ctx* c, Hier<R>& H) {
       for (auto& pr : cost) order.push_back(pr.second);
       if ((rc = dalloc(c, H, (void**)&V.order8, order.size() * sizeof(int))) != MG_OK) return rc;
       MG_CUDA(c, cudaMemcpy(V.order8, order.data(), order.size() * sizeof(int), cudaMemcpyHostToDevice));
+      if ((rc = dalloc(c, H, (void**)&V.tflags, order.size() * sizeof(unsigned))) != MG_OK) return rc;
     }
     if (d == 2 && !H.varphi && l > 1) {
       // classes of 1D Galerkin rows along an axis (same on both axes)
@@ -609,7 +611,8 @@ cudaError_t sweep2(mg_ctx* c, Hier<R>& H, int l, bool fine, int hb, int hier, co
     // queue head chain_ctr[32] and exit counter [33] are zero between launches
     const int grid = std::min(A.ntiles, 152 * std::max(1, c->fine_bpsm));
     mg::sweep2p_kernel<8, 256, R><<<grid, 256, mg::Tile2<8, R>::smem_bytes, c->stream>>>(
-        A, V.order8, c->chain_ctr + 32, c->tracing ? c->trace : nullptr);
+        A, V.order8, c->chain_ctr + 32, c->tracing ? c->trace : nullptr, fine ? V.tflags : nullptr,
+        c->chain_ctr + 34);
     return cudaGetLastError();
   }
   A.ntiles = ((nc + 4) / 4) * ((nc + 4) / 4);
@@ -729,8 +732,19 @@ int build_chain2(mg_ctx* c, Hier<R>& H, int s, int hb, int hier, const cplx<doub
 }
 
 template <typename R>
-cudaError_t launch_chain2(mg_ctx* c, const typename Hier<R>::ChainPlan& cp) {
+cudaError_t launch_chain2(mg_ctx* c, Hier<R>& H, int s, const typename Hier<R>::ChainPlan& cp) {
   mg::ChainArgs<R> A;
+  // the first stage waits for single fine tiles when the fine sweep was the
+  // persistent LPT sweep that publishes them (levels s-1 in 4-cell tiles)
+  auto& VF = H.lev[s];
+  const int ncf = VF.n / 3;
+  // (complex64 2D levels of this size take the warp-strip sweep instead)
+  const bool tiled = std::is_same<R, double>::value && VF.tflags != nullptr && ncf + 1 >= 200 &&
+                     VF.order8 != nullptr && (H.lev[s - 1].n / 3 + 1) >= 60;
+  A.fine_flags = tiled ? VF.tflags : nullptr;
+  A.gen = c->chain_ctr + 34;
+  A.fine_tiles_x = (ncf + 8) / 8;
+  A.first_tiles_x = (H.lev[s - 1].n / 3 + 4) / 4;
   A.items = cp.items;
   A.nitems = cp.nitems;
   A.s2 = cp.s2;
@@ -1030,7 +1044,7 @@ cudaError_t enqueue_cycle_part(mg_ctx* c, Hier<R>& H, int s, int hb, int hier,
       if (build_chain2<R>(c, H, s, hb, hier, omega, key, &cp) != MG_OK) return cudaErrorUnknown;
       *nkern = 1;
       ++c->launches;
-      return launch_chain2<R>(c, *cp);
+      return launch_chain2<R>(c, H, s, *cp);
     }
   }
   for (int l = s - 1; l >= 1 && e == cudaSuccess; --l, ++*nkern) e = sweep(c, H, l, false, s, hb, hier, omega);

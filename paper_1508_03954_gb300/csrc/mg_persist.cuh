@@ -68,6 +68,13 @@ struct ChainArgs {
   const CorrArgs<R>* co;
   unsigned* head;        // queue head, zero at launch
   unsigned* exitc;       // blocks that left the queue; the last one zeroes the counters
+  // first-stage items may wait for single fine tiles instead of the whole
+  // fine sweep: fine_flags[t] >= *gen + 1 once fine tile t is written (null:
+  // wait for the whole fine grid); the chain's last block advances *gen
+  const unsigned* fine_flags;
+  unsigned* gen;
+  int fine_tiles_x;      // fine tiles (8 coarse cells) per axis
+  int first_tiles_x;     // tiles (4 cells) per axis of the first chain level
   unsigned* done;        // per-problem completion counters, zero at launch
   unsigned* err;         // set when a bounded wait gave up
   unsigned spin_limit;   // polls before giving up
@@ -194,12 +201,14 @@ __device__ __forceinline__ void pdl_launch_dependents() {
 }
 // The last block to leave a persistent queue zeroes its counters for the
 // next launch (no memset node between launches).
-__device__ __forceinline__ void queue_exit(unsigned* exitc, unsigned* a, unsigned* b) {
+__device__ __forceinline__ void queue_exit(unsigned* exitc, unsigned* a, unsigned* b,
+                                           unsigned* gen = nullptr) {
   if (threadIdx.x == 0) {
     __threadfence();
     if (atomicAdd(exitc, 1u) == gridDim.x - 1) {
       *a = 0u;
       if (b != nullptr) *b = 0u;
+      if (gen != nullptr) atomicAdd(gen, 1u);
       *exitc = 0u;
       __threadfence();
     }
@@ -214,13 +223,16 @@ __global__ void __launch_bounds__(NTHR) chain2_kernel(const ChainArgs<R> A) {
   __shared__ __align__(16) Sweep2Args<R> s_a;
   __shared__ __align__(16) ProlongArgs<R> s_p;
   __shared__ __align__(16) CorrArgs<R> s_co;
-  pdl_wait();
+  const bool tdep = A.fine_flags != nullptr;
+  if (!tdep) pdl_wait();
+  // generation of this cycle (the fine sweep read the same value)
+  const unsigned gen = (tdep && threadIdx.x == 0) ? ld_acquire_u32(A.gen) : 0u;
   while (true) {
     if (threadIdx.x == 0) s_item = (int)atomicAdd(A.head, 1u);
     __syncthreads();
     const int i = s_item;
     if (i >= A.nitems) {
-      queue_exit(A.exitc, A.head, A.done);
+      queue_exit(A.exitc, A.head, A.done, A.gen);
       break;
     }
     const ChainItem it = A.items[i];
@@ -231,6 +243,16 @@ __global__ void __launch_bounds__(NTHR) chain2_kernel(const ChainArgs<R> A) {
     else if (it.kind == kItemProlong2) copy_args<ProlongArgs<R>, NTHR>(&s_p, A.pr + it.args);
     else copy_args<CorrArgs<R>, NTHR>(&s_co, A.co + it.args);
     if (threadIdx.x == 0 && it.need > 0) wait_counter(A.done + it.prob, it.need, A.spin_limit, A.err);
+    if (threadIdx.x == 0 && tdep && it.need == 0 && it.kind == kItemSweep2) {
+      // the fine tiles (8 cells) that wrote u and b on this tile's box, fine
+      // vertices [12 t - 3, 12 t + 13] per axis of the first chain level
+      const int tx = it.tile % A.first_tiles_x, ty = it.tile / A.first_tiles_x;
+      const int fx0 = max(0, (12 * tx - 3) / 8), fx1 = min(A.fine_tiles_x - 1, (12 * tx + 13) / 8);
+      const int fy0 = max(0, (12 * ty - 3) / 8), fy1 = min(A.fine_tiles_x - 1, (12 * ty + 13) / 8);
+      for (int fy = fy0; fy <= fy1; ++fy)
+        for (int fx = fx0; fx <= fx1; ++fx)
+          wait_counter(A.fine_flags + fy * A.fine_tiles_x + fx, gen + 1u, A.spin_limit, A.err);
+    }
     if (threadIdx.x == 0 && i == 0 && A.stall != nullptr) wait_counter(A.stall, 1u, A.spin_limit, A.err);
     if (A.trace != nullptr && threadIdx.x == 0) t1 = gtimer();
     __syncthreads();
@@ -265,7 +287,8 @@ __global__ void __launch_bounds__(NTHR) chain2_kernel(const ChainArgs<R> A) {
 // uneven cost of scaling-layer tiles evens out over the SMs.
 template <int TC, int NTHR, typename R = double>
 __global__ void __launch_bounds__(NTHR) sweep2p_kernel(const Sweep2Args<R> A, const int* order,
-                                                       unsigned* head, unsigned long long* trace) {
+                                                       unsigned* head, unsigned long long* trace,
+                                                       unsigned* tflags, const unsigned* gen) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double s_red[NTHR / 32];
   __shared__ int s_k;
@@ -273,6 +296,7 @@ __global__ void __launch_bounds__(NTHR) sweep2p_kernel(const Sweep2Args<R> A, co
   // coarse chain may be scheduled on SMs as soon as they free up; it waits
   // for this grid's writes before it reads anything
   pdl_launch_dependents();
+  const unsigned g = (tflags != nullptr && threadIdx.x == 0) ? ld_acquire_u32(gen) : 0u;
   while (true) {
     if (threadIdx.x == 0) s_k = (int)atomicAdd(head, 1u);
     __syncthreads();
@@ -284,6 +308,11 @@ __global__ void __launch_bounds__(NTHR) sweep2p_kernel(const Sweep2Args<R> A, co
     const unsigned long long t0 = (trace != nullptr && threadIdx.x == 0) ? gtimer() : 0ull;
     sweep2_tile<TC, NTHR, R>(A, order[k], smem_raw, s_red);
     __syncthreads();
+    if (tflags != nullptr && threadIdx.x == 0) {
+      // publish this tile's coarse outputs to the chain's first stage
+      __threadfence();
+      atomicExch(tflags + order[k], g + 1u);
+    }
     if (trace != nullptr && threadIdx.x == 0) {
       unsigned long long* tr = trace + 4ull * k;
       tr[0] = t0;
