@@ -149,9 +149,13 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- traffic record
+FINE_SWEEP_SOURCES = ("mg_kernels.cuh", "mg_sweep2d.cuh", "mg_persist.cuh")
+
+
 def recorded_traffic(kernel_key, source_files):
     """DRAM bytes per launch of the timed kernel from the committed ncu summary,
-    if it was taken with the current source (sha256 over the CUDA sources)."""
+    if it was taken with the current source (sha256 over the CUDA sources that
+    define the kernel)."""
     h = hashlib.sha256()
     for f in source_files:
         with open(f, "rb") as fh:
@@ -505,8 +509,9 @@ def main():
     sweep_s = (sweep_ms / max(nsweeps, 1)) / 1e3
     achieved = flops / sweep_s
     csrc = os.path.join(ROOT, "paper_1508_03954_gb300", "csrc")
+    # the files that define the timed kernel (tile step, persistent queue, launch)
     traffic, sha = recorded_traffic("fine_sweep2_c128_2d_depth6",
-                                    [os.path.join(csrc, f) for f in sorted(os.listdir(csrc))])
+                                    [os.path.join(csrc, f) for f in FINE_SWEEP_SOURCES])
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": FP64_PEAK_FLOPS / 1e12,
                 "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_FLOPS, "traffic": traffic,
                 "kernel": "sweep2p_kernel<8,256,double> (finest level, persistent LPT, FP64)",

@@ -74,6 +74,7 @@ struct Hier {
     bool gok = false;
     int* order8 = nullptr;      // fine tiles (8 coarse cells) by decreasing cost
     unsigned* tflags = nullptr; // per such tile: generation + 1 once written (chain overlap)
+    unsigned* d3pref = nullptr; // 3D FP64 defect: prefix sums of the unit costs
     uint8_t* gtyp = nullptr;
     cplx<R>* gcoef = nullptr;
   };
@@ -1205,17 +1206,53 @@ cudaError_t stencil(mg_ctx* c, Hier<R>& H, int l, int xs, const cplx<R>* x, cons
 // r = b - H u' in FP64 (optional complex64 copy into r32), |r|^2 into
 // H.norm2[slot] -- the fused outer step of the defect-correction form and
 // the plain FP64 residual norm.
+// Cost of each (tile, coarse plane) unit of the 3D FP64 defect in FP64
+// operations per vertex: the real passes (z 12, y 18, x 12, update and
+// residual 12) plus what a complex coefficient row adds to each pass (z 12
+// on planes in the layer, y 18 on rows in the layer, x 12 on tiles whose
+// columns reach into it), summed over the unit's three fine planes.
+int defect3_costs(mg_ctx* c, Hier<double>& H, int l) {
+  auto& V = H.lev[l];
+  if (V.d3pref != nullptr) return MG_OK;
+  const int n = V.n, nc = n / 3;
+  std::vector<uint8_t> rot = layer_flags(n, c->w), typ(n + 1);
+  for (int i = 0; i <= n; ++i) typ[i] = (uint8_t)(rot[std::max(i - 1, 0)] + 2 * rot[std::min(i, n - 1)]);
+  const int tx_n = (n + 1 + 29) / 30, ty_n = (n + 1 + 13) / 14;
+  std::vector<unsigned> pref((size_t)tx_n * ty_n * nc + 1, 0u);
+  size_t u = 0;
+  for (int t = 0; t < tx_n * ty_n; ++t) {
+    const int x0 = (t % tx_n) * 30, y0 = (t / tx_n) * 14;
+    bool xc = false;
+    for (int g = x0 - 1; g <= x0 + 30; ++g) xc = xc || (g >= 0 && g <= n && typ[g] != 0);
+    int yc = 0, rows = 0;
+    for (int g = y0; g < y0 + 14 && g <= n; ++g, ++rows) yc += typ[g] != 0;
+    const double yfrac = rows ? (double)yc / rows : 0.0;
+    for (int Z = 0; Z < nc; ++Z, ++u) {
+      double cost = 0;
+      for (int z = 3 * Z; z < 3 * Z + 3; ++z)
+        cost += 54.0 + 12.0 * (typ[z] != 0) + 18.0 * yfrac + 12.0 * xc;
+      pref[u + 1] = pref[u] + (unsigned)std::lround(cost);
+    }
+  }
+  int rc = dalloc(c, H, (void**)&V.d3pref, pref.size() * sizeof(unsigned));
+  if (rc != MG_OK) return rc;
+  MG_CUDA(c, cudaMemcpy(V.d3pref, pref.data(), pref.size() * sizeof(unsigned), cudaMemcpyHostToDevice));
+  return MG_OK;
+}
+
 template <typename RC>
 cudaError_t defect3(mg_ctx* c, int l, const cplx<double>* u, const cplx<RC>* e, const cplx<RC>* cc,
                     cplx<double>* u_out, cplx<float>* r32, int slot) {
   auto& H = c->h64;
   auto& V = H.lev[l];
+  if (defect3_costs(c, H, l) != MG_OK) return cudaErrorMemoryAllocation;
   mg::Defect3Args<RC> A;
   std::memset(&A, 0, sizeof(A));
   A.n = V.n;
   A.tiles_x = (V.n + 1 + 29) / 30;
   A.tiles_y = (V.n + 1 + 13) / 14;
   A.nunits = (long long)A.tiles_x * A.tiles_y * (V.n / 3);
+  A.upref = V.d3pref;
   A.u = u;
   A.e = e;
   A.c = cc;

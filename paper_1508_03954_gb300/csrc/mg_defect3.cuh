@@ -18,9 +18,12 @@
 // fine columns; the block owns the inner 30 x 14 columns and marches a range
 // of coarse planes (three fine planes each) along z.  u' is recomputed on the
 // one-column halo by the neighbouring tiles, so no step reads data another
-// block writes.  The work is split into equal ranges of (tile, coarse plane)
-// units, one block per SM.  The kernel is bound by the FP64 pipe (about 50
-// FP64 operations per vertex against 2 FP64 FMA per clock per SM).
+// block writes.  The (tile, coarse plane) units are split into ranges of
+// equal FP64 cost, one block per SM: the host tabulates each unit's cost from
+// how many of its axis passes take complex coefficients (scaling layer), and
+// each block finds its range in the prefix sums.  The kernel is bound by the
+// FP64 pipe (50-90 FP64 operations per vertex against 2 FP64 FMA per clock
+// per SM).
 #pragma once
 #include "mg_kernels.cuh"
 #include "mg_sweep3s.cuh"
@@ -34,6 +37,7 @@ struct Defect3Args {
   int n;
   int tiles_x, tiles_y;     // 30-column by 14-row tiles
   long long nunits;         // tiles_x * tiles_y * (n / 3)
+  const unsigned* upref;    // prefix sums of the unit costs, nunits + 1 entries
   const cplx<double>* u;
   const cplx<RC>* e;        // fine correction (nullable)
   const cplx<RC>* c;        // pending correction on level n/3 (nullable)
@@ -107,9 +111,19 @@ __global__ void __launch_bounds__(kD3Threads, 1) defect3_kernel(const Defect3Arg
   const bool own_lane = lane >= 1 && lane <= 30, own_row = warp >= 1 && warp <= 14;
   double nrm = 0.0;
 
+  // this block's units: those whose prefix cost lies in [W b / B, W (b+1) / B)
   const long long U = A.nunits;
-  long long unit = U * blockIdx.x / gridDim.x;
-  const long long uend = U * (blockIdx.x + 1) / gridDim.x;
+  const unsigned long long W = A.upref[U];
+  auto first_at = [&](unsigned long long target) -> long long {
+    long long lo = 0, hi = U;  // first i in [0, U] with upref[i] >= target
+    while (lo < hi) {
+      const long long mid = (lo + hi) >> 1;
+      if ((unsigned long long)__ldg(A.upref + mid) >= target) hi = mid; else lo = mid + 1;
+    }
+    return lo;
+  };
+  long long unit = first_at(W * blockIdx.x / gridDim.x);
+  const long long uend = first_at(W * (blockIdx.x + 1) / gridDim.x);
   while (unit < uend) {
     const int tile = (int)(unit / nc), Z0 = (int)(unit % nc);
     const int Z1 = (int)min((long long)nc, (long long)Z0 + (uend - unit));

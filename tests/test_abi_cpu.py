@@ -60,3 +60,12 @@ def test_omega_scheme_helper(lib, scheme, oscheme):
         got = mg.omega_scheme(scheme, 0.6 + 0.1j, 5, iter_n=it, l_grid=2)
         ref = O.omega_scheme(oscheme, 0.6 + 0.1j, 5, iter_n=it, l_grid=2)
         np.testing.assert_allclose(got, ref, rtol=1e-14)
+
+
+def test_trace_stage_layout_matches_chain_rules():
+    """The trace helper's stage layout of the depth-6 chain (tiles of 4, 2, 1
+    coarse cells by level size; correction chunks of about two per SM)."""
+    from paper_1508_03954_gb300.trace import chain_stages, fine_tiles
+    assert [k for _, k in chain_stages(729)] == [441, 196, 100, 16, 4, 106, 233]
+    assert fine_tiles(729) == 961
+    assert [k for _, k in chain_stages(243)] == [196, 100, 16, 4, 13, 106]
