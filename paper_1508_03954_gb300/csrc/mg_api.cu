@@ -69,6 +69,7 @@ struct Hier {
     std::vector<cd> diag;     // D per vertex type (constant shift)
     unsigned realrow = 0;     // bit t: stencil row of type t is real (2D types)
     unsigned long long realrow3 = 0;  // same for the 64 3D types
+    unsigned long long realM = 0;     // bit t: mass row of type t is real
     bool g3ok = false;        // 3D Galerkin-row tables available
     // 2D FP64 path: Galerkin rows of G_{l-1} = R H_l P per coarse row class
     bool gok = false;
@@ -371,10 +372,12 @@ int build_hier(mg_ctx* c, Hier<R>& H) {
     V.realrow = 0;
     V.realrow3 = 0;
     for (int t = 0; t < NT; ++t) {
-      bool re = true;
+      bool re = true, rm = true;
       for (int k = 0; k < NS; ++k) re = re && Hh[(size_t)t * NS + k].imag() == 0.0;
+      for (int k = 0; k < NS; ++k) rm = rm && M[(size_t)t * NS + k].imag() == 0.0;
       if (re && t < 32) V.realrow |= 1u << t;
       if (re) V.realrow3 |= 1ull << t;
+      if (rm) V.realM |= 1ull << t;
     }
     if (d == 3 && !H.varphi && l > 1) {
       std::vector<std::array<cd, 6>> rows;
@@ -1191,13 +1194,14 @@ cudaError_t stencil(mg_ctx* c, Hier<R>& H, int l, int xs, const cplx<R>* x, cons
   ++c->launches;
   const int g = grid_for(V.nv);
   double* nrm = slot >= 0 ? H.norm2 + slot : nullptr;
+  const unsigned long long realmask = coef == V.coefH ? V.realrow3 : (coef == V.coefM ? V.realM : 0ull);
   if (c->d == 2)
     mg::stencil_kernel<R, RO, 2><<<g, kThreads, 0, c->stream>>>(
-        V.n, xs, x, b, V.typ, coef, with_phi ? V.phic : nullptr, V.hcell, y, H.partial,
+        V.n, xs, x, b, V.typ, coef, realmask, with_phi ? V.phic : nullptr, V.hcell, y, H.partial,
         H.ticket + 1, nrm);
   else
     mg::stencil_kernel<R, RO, 3><<<g, kThreads, 0, c->stream>>>(
-        V.n, xs, x, b, V.typ, coef, with_phi ? V.phic : nullptr, V.hcell, y, H.partial,
+        V.n, xs, x, b, V.typ, coef, realmask, with_phi ? V.phic : nullptr, V.hcell, y, H.partial,
         H.ticket + 1, nrm);
   return cudaGetLastError();
 }
@@ -1284,11 +1288,12 @@ cudaError_t defect3(mg_ctx* c, int l, const cplx<double>* u, const cplx<RC>* e, 
 
 bool use_defect3(const mg_ctx* c) { return c->d == 3 && !c->h64.varphi && c->L >= 1; }
 
+// The pending correction corr_{s-1} is the only coarse array a cycle reads
+// before writing it (the fine sweep forms u = U + P corr_{s-1}; every t_l and
+// the other corr_l are written by the cycle before they are read).
 int zero_pending(mg_ctx* c, Hier<double>& H, int s) {
-  for (int l = 1; l < s; ++l) {
-    MG_CUDA(c, cudaMemsetAsync(H.lev[l].corr, 0, H.lev[l].nv * sizeof(cplx<double>), c->stream));
-    MG_CUDA(c, cudaMemsetAsync(H.lev[l].t, 0, H.lev[l].nv * sizeof(cplx<double>), c->stream));
-  }
+  if (s > 1)
+    MG_CUDA(c, cudaMemsetAsync(H.lev[s - 1].corr, 0, H.lev[s - 1].nv * sizeof(cplx<double>), c->stream));
   return MG_OK;
 }
 
@@ -1456,13 +1461,14 @@ int mg_set_solution(mg_ctx* c, const mg_c128* u, int on_device) {
   if (u == nullptr) return fail(c, MG_ERR_INVALID, "u is NULL");
   auto& H = c->h64;
   auto& V = H.lev[c->L];
-  // copy, then zero the boundary through the materialise kernel (c = none)
-  MG_CUDA(c, cudaMemcpyAsync(c->scratch, u, V.nv * sizeof(mg_c128),
+  // copy into the active fine array, then zero its Dirichlet ring
+  MG_CUDA(c, cudaMemcpyAsync(V.u[H.cur], u, V.nv * sizeof(mg_c128),
                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+  const int ring = c->d == 2 ? 4 * V.n : 6 * (V.n + 1) * (V.n + 1);
   if (c->d == 2)
-    mg::materialize_kernel<double, 2><<<grid_for(V.nv), kThreads, 0, c->stream>>>(V.n, c->scratch, nullptr, V.u[H.cur]);
+    mg::zero_ring_kernel<2><<<(ring + 255) / 256, 256, 0, c->stream>>>(V.n, V.u[H.cur]);
   else
-    mg::materialize_kernel<double, 3><<<grid_for(V.nv), kThreads, 0, c->stream>>>(V.n, c->scratch, nullptr, V.u[H.cur]);
+    mg::zero_ring_kernel<3><<<(ring + 255) / 256, 256, 0, c->stream>>>(V.n, V.u[H.cur]);
   MG_CUDA(c, cudaGetLastError());
   int rc = zero_pending(c, H, c->L);
   if (rc != MG_OK) return rc;
@@ -1997,10 +2003,10 @@ extern "C" int mg_residual_noalloc(mg_ctx* c, const mg_c128* u, const mg_c128* b
   cplx<double>* y = reinterpret_cast<cplx<double>*>(r);
   if (c->d == 2)
     mg::stencil_kernel<double, double, 2><<<(unsigned)nblocks, kThreads, 0, c->stream>>>(
-        V.n, 1, x, bb, V.typ, V.coefH, V.phic, V.hcell, y, partial, ticket, norm2);
+        V.n, 1, x, bb, V.typ, V.coefH, V.realrow3, V.phic, V.hcell, y, partial, ticket, norm2);
   else
     mg::stencil_kernel<double, double, 3><<<(unsigned)nblocks, kThreads, 0, c->stream>>>(
-        V.n, 1, x, bb, V.typ, V.coefH, V.phic, V.hcell, y, partial, ticket, norm2);
+        V.n, 1, x, bb, V.typ, V.coefH, V.realrow3, V.phic, V.hcell, y, partial, ticket, norm2);
   MG_CUDA(c, cudaGetLastError());
   return MG_OK;
 }

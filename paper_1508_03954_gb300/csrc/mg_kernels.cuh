@@ -645,6 +645,40 @@ __global__ void __launch_bounds__(NTHR) sweep_kernel(const SweepArgs<R> A) {
 }
 
 // ---------------------------------------------------------------------------
+// Zeroes the Dirichlet ring of a level array (n cells per axis).  2D: 4n
+// vertices (rows 0 and n, then columns 0 and n of rows 1..n-1); 3D: the six
+// faces as (n+1)^2-vertex sheets (edges written more than once).
+// ---------------------------------------------------------------------------
+template <int D>
+__global__ void zero_ring_kernel(int n, cplx<double>* u) {
+  const int N = n + 1;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (D == 2) {
+    if (i >= 4 * n) return;
+    int x, y;
+    if (i < 2 * N) {
+      x = i % N;
+      y = (i / N) ? n : 0;
+    } else {
+      const int k = i - 2 * N;  // 0 .. 2(n-1)-1
+      y = 1 + k / 2;
+      x = (k & 1) ? n : 0;
+    }
+    u[(size_t)y * N + x] = cz<double>();
+  } else {
+    const int F = N * N;
+    if (i >= 6 * F) return;
+    const int face = i / F, a = (i % F) % N, b = (i % F) / N;
+    const int v = (face & 1) ? n : 0;
+    int x, y, z;
+    if (face < 2) { x = v; y = a; z = b; }
+    else if (face < 4) { x = a; y = v; z = b; }
+    else { x = a; y = b; z = v; }
+    u[((size_t)z * N + y) * N + x] = cz<double>();
+  }
+}
+
+// ---------------------------------------------------------------------------
 // corr_l = t_l + P corr_{l-1} on all vertices of level l (boundary stays 0).
 // ---------------------------------------------------------------------------
 template <typename R, int D>
@@ -704,17 +738,21 @@ __global__ void materialize_kernel(int n, const cplx<R>* __restrict__ U,
     if (inner) {
       if (U != nullptr) v = U[i];
       if (c != nullptr) {
+        // d-linear weights as integers over 3^D: corner e weighs
+        // prod_a (bit ? o_a : 3 - o_a), o_a the offset in the coarse cell
+        cplx<R> s = cz<R>();
         for (int e = 0; e < (1 << D); ++e) {
-          R w = R(1);
+          int iw = 1;
           long long ci = 0, cs = 1;
           for (int a = 0; a < D; ++a) {
-            int bit = (e >> a) & 1;
-            w *= pw<R>(g[a] % 3, bit);
+            const int bit = (e >> a) & 1, o = g[a] % 3;
+            iw *= bit ? o : 3 - o;
             ci += (long long)(g[a] / 3 + bit) * cs;
             cs *= Nc;
           }
-          if (w != R(0)) v = rfma(w, c[ci], v);
+          if (iw != 0) s = rfma((R)iw, c[ci], s);
         }
+        v = rfma(R(1) / R(D == 2 ? 9 : 27), s, v);
       }
     }
     out[i] = v;
@@ -730,9 +768,10 @@ __global__ void materialize_kernel(int n, const cplx<R>* __restrict__ U,
 template <typename R, typename RO, int D>
 __global__ void stencil_kernel(int n, int xs, const cplx<R>* __restrict__ x,
                                const cplx<R>* __restrict__ b, const uint8_t* __restrict__ typ,
-                               const cplx<R>* __restrict__ coef, const R* __restrict__ phic,
-                               const cplx<R>* __restrict__ hcell, cplx<RO>* __restrict__ y,
-                               double* partial, unsigned* ticket, double* norm2) {
+                               const cplx<R>* __restrict__ coef, unsigned long long realmask,
+                               const R* __restrict__ phic, const cplx<R>* __restrict__ hcell,
+                               cplx<RO>* __restrict__ y, double* partial, unsigned* ticket,
+                               double* norm2) {
   constexpr int NS = P3<D>::v;
   const int N = n + 1;
   const long long Nx = (long long)xs * n + 1;
@@ -755,16 +794,22 @@ __global__ void stencil_kernel(int n, int xs, const cplx<R>* __restrict__ x,
       for (int a = 0; a < D; ++a) { ty += (int)typ[g[a]] * ts; ts *= 4; }
       const cplx<R>* cf = coef + ty * NS;
       cplx<R> acc = cz<R>();
-#pragma unroll
-      for (int k = 0; k < NS; ++k) {
-        int kk = k;
+      // neighbour k at offset (k % 3 - 1, k / 3 % 3 - 1, k / 9 - 1), stride xs
+      auto nbr = [&](int k) -> long long {
         long long xi = 0, st = 1;
         for (int a = 0; a < D; ++a) {
-          xi += (long long)(g[a] + kk % 3 - 1) * xs * st;
-          kk /= 3;
+          xi += (long long)(g[a] + k % 3 - 1) * xs * st;
+          k /= 3;
           st *= Nx;
         }
-        acc = cfma(cf[k], x[xi], acc);
+        return xi;
+      };
+      if ((realmask >> ty) & 1ull) {  // row of an unscaled vertex: real x complex
+#pragma unroll
+        for (int k = 0; k < NS; ++k) acc = rfma(cf[k].x, x[nbr(k)], acc);
+      } else {
+#pragma unroll
+        for (int k = 0; k < NS; ++k) acc = cfma(cf[k], x[nbr(k)], acc);
       }
       if (phic != nullptr) {
         // - sum_c phi_c (M_c x)(g)
