@@ -15,12 +15,13 @@
 // and right cell plain or rotated), so seven 3-tap passes replace the
 // 27-point row, and rows in the unscaled interior take real coefficients.
 //
-// Layout.  A block of 1024 threads owns an x-y tile of 9 x 9 coarse cells
-// (27 x 27 fine vertices) and a range of coarse planes; lane = x and warp = y
-// of a 32 x 32 box of fine columns [x0-3, x0+28] x [y0-3, y0+28].  Each
-// thread marches its column along z holding u(z-1), u(z), u(z+1) in
-// registers: the z-pass runs in registers, the y-pass reads the neighbouring
-// rows from shared memory, the x-pass takes its neighbours by warp shuffles.
+// Layout.  A block of 512 threads owns an x-y tile of 9 x 9 coarse cells
+// (27 x 27 fine vertices) and a range of coarse planes; lane = x and the two
+// rows 2w, 2w+1 of warp w = y of a 32 x 32 box of fine columns
+// [x0-3, x0+28] x [y0-3, y0+28].  Each thread marches its two columns along z
+// holding u(z-1), u(z), u(z+1) in registers: the z-pass runs in registers,
+// the y-pass takes the pair's outer neighbour rows from shared memory, the
+// x-pass takes its neighbours by warp shuffles.
 // The r box is [x0-2, x0+27]^2 (lanes/warps 1..30), enough for the
 // restriction of the owned coarse vertices and for the c-point Jacobi update
 // of the next tile's first c-point (BPX).  One barrier per fine plane.
@@ -34,7 +35,6 @@
 
 namespace mg {
 
-constexpr int kS3sThreads = 1024;
 
 struct Sweep3sArgs {
   int n, fine, first, has_coarse, hb, hier;
@@ -115,14 +115,21 @@ template <int O> __device__ __forceinline__ constexpr float W1() {
   return O == 0 ? 0.f : (O == 1 ? 1.f / 3.f : 2.f / 3.f);
 }
 
+// Two vertically adjacent box rows per thread (512 threads, warp w holds rows
+// 2w and 2w+1): the per-plane control, address and barrier work is shared by
+// two columns, the y-pass of a row pair needs only the two outer neighbour
+// rows from shared memory, and 128 registers hold both columns' state (one
+// row per thread at 1024 threads was 15% slower and spilled at 64 registers).
+constexpr int kS3sThreads = 512;
+
 __global__ void __launch_bounds__(kS3sThreads, 1) sweep3s_kernel(const Sweep3sArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double s_red[32];
+  __shared__ double s_red[kS3sThreads / 32];
   Sweep3sShared& S = *reinterpret_cast<Sweep3sShared*>(smem_raw);
   using C = cplx<float>;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int n = A.n, N = n + 1, nc = n / 3;
-  const long long NN = (long long)N * N, Nc = nc + 1, NNc = Nc * Nc;
+  const int NN = N * N, Nc = nc + 1, NNc = Nc * Nc;  // level sizes stay below 2^31 vertices
   for (int i = threadIdx.x; i < 36; i += kS3sThreads) S.row[i / 9][i % 9] = A.row[i / 9][i % 9];
   for (int i = threadIdx.x; i < 64; i += kS3sThreads) S.omd[i] = A.omd[i];
   const bool zero_u = A.fine && A.first;
@@ -133,102 +140,122 @@ __global__ void __launch_bounds__(kS3sThreads, 1) sweep3s_kernel(const Sweep3sAr
   const int ek = (warp < 4 && lane < 25) ? warp * 25 + lane : -1;
   const bool emit = ek >= 0 && A.has_coarse;
   const int ejx = emit ? ek % 10 : 0, ejy = emit ? ek / 10 : 0;
-  // the real rows of the unscaled interior: mass h/6 (1, 4, 1), stiffness, shifted stiffness
   const float m0 = A.row[0][0].x, m1 = A.row[0][1].x, m2 = A.row[0][2].x;
   const float k0 = A.row[0][3].x, k1 = A.row[0][4].x, k2 = A.row[0][5].x;
   const float p0 = A.row[0][6].x, p1 = A.row[0][7].x, p2 = A.row[0][8].x;
-  const int ox = lane % 3, oy = warp % 3;
+  const int ox = lane % 3;
   const float wx1 = ox == 0 ? 0.f : (ox == 1 ? 1.f / 3.f : 2.f / 3.f), wx0 = 1.f - wx1;
-  const float wy1 = oy == 0 ? 0.f : (oy == 1 ? 1.f / 3.f : 2.f / 3.f), wy0 = 1.f - wy1;
-  const bool cpx = ox == 0, cpy = oy == 0;  // c-point column (the box origin is a c-point)
-  const bool rrow = warp >= 1 && warp <= 30;
+  const bool cpx = ox == 0;
+  int by[2], oy[2];
+  float wy0[2], wy1[2];
+  bool cpy[2], rrow[2];
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    by[r] = 2 * warp + r;  // box row
+    oy[r] = by[r] % 3;
+    wy1[r] = oy[r] == 0 ? 0.f : (oy[r] == 1 ? 1.f / 3.f : 2.f / 3.f);
+    wy0[r] = 1.f - wy1[r];
+    cpy[r] = oy[r] == 0;
+    rrow[r] = by[r] >= 1 && by[r] <= 30;
+  }
   float nrm = 0.f;
 
   const long long U = A.nunits;
-  long long unit = U * blockIdx.x / gridDim.x;
-  const long long uend = U * (blockIdx.x + 1) / gridDim.x;
+  int unit = (int)(U * blockIdx.x / gridDim.x);
+  const int uend = (int)(U * (blockIdx.x + 1) / gridDim.x);
   while (unit < uend) {
-    const int tile = (int)(unit / nc), Z0 = (int)(unit % nc);
-    const int Z1 = (int)min((long long)nc, (long long)Z0 + (uend - unit));
+    const int tile = unit / nc, Z0 = unit % nc;
+    const int Z1 = min(nc, Z0 + (uend - unit));
     unit += Z1 - Z0;
     const int C0x = (tile % A.tiles_x) * 9, C0y = (tile / A.tiles_x) * 9;
     const int x0 = 3 * C0x, y0 = 3 * C0y;
-    const int gx = x0 - 3 + lane, gy = y0 - 3 + warp;
-    const bool colin = gx > 0 && gx < n && gy > 0 && gy < n;
+    const int gx = x0 - 3 + lane;
     const bool lastx = C0x + 9 >= nc, lasty = C0y + 9 >= nc;
-    const bool owncol = lane >= 3 && (lane < 30 || (lane == 30 && lastx)) && warp >= 3 &&
-                        (warp < 30 || (warp == 30 && lasty)) && gx <= n && gy <= n;
-    const long long col = (long long)gy * N + gx;  // used only for owned or interior columns
     const int tx = (gx >= 0 && gx <= n) ? (int)A.typ[gx] : 0;
-    const int ty = (gy >= 0 && gy <= n) ? (int)A.typ[gy] : 0;
     const bool xreal = __all_sync(0xffffffffu, tx == 0);
-    const bool yreal = ty == 0;
+    int gy[2], col[2], ty[2];
+    bool colin[2], owncol[2], yreal[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      gy[r] = y0 - 3 + by[r];
+      colin[r] = gx > 0 && gx < n && gy[r] > 0 && gy[r] < n;
+      owncol[r] = lane >= 3 && (lane < 30 || (lane == 30 && lastx)) && by[r] >= 3 &&
+                  (by[r] < 30 || (by[r] == 30 && lasty)) && gx <= n && gy[r] <= n;
+      col[r] = gy[r] * N + gx;  // used only for owned or interior columns
+      ty[r] = (gy[r] >= 0 && gy[r] <= n) ? (int)A.typ[gy[r]] : 0;
+      yreal[r] = ty[r] == 0;
+    }
     const int zs = 3 * Z0 - 2;
     auto qslot = [](int Zc) { return (Zc + 3) % 3; };
-    auto ldU = [&](int z) -> C {
-      return (!zero_u && colin && z > 0 && z < n) ? ld_nc(A.u + z * NN + col) : cz<float>();
+    auto ldU = [&](int z, int r) -> C {
+      return (!zero_u && colin[r] && z > 0 && z < n) ? ld_nc(A.u + (z * NN + col[r])) : cz<float>();
     };
-    auto ldB = [&](int z) -> C {
-      return (colin && z > 0 && z < n) ? ld_nc(A.b + z * NN + col) : cz<float>();
+    auto ldB = [&](int z, int r) -> C {
+      return (rrow[r] && colin[r] && z > 0 && z < n) ? ld_nc(A.b + (z * NN + col[r])) : cz<float>();
     };
     auto ld_cc = [&](int Zc) -> C {
       const int t = threadIdx.x;
       const int cx = C0x - 1 + t % 12, cy = C0y - 1 + t / 12;
       return (use_c && t < 144 && Zc >= 0 && Zc <= nc && cx >= 0 && cx <= nc && cy >= 0 && cy <= nc)
-                 ? ld_nc(A.c + Zc * NNc + (long long)cy * Nc + cx)
+                 ? ld_nc(A.c + (Zc * NNc + cy * Nc + cx))
                  : cz<float>();
     };
-    // bilinear interpolation of the coarse plane in S.cc to this column
-    auto bil_cc = [&]() -> C {
-      const int jx = lane / 3, jy = warp / 3;
+    // bilinear interpolation of the coarse plane in S.cc to column (lane, box row r)
+    auto bil_cc = [&](int r) -> C {
+      const int jx = lane / 3, jy = by[r] / 3;
       const C a = S.cc[jy][jx], b2 = S.cc[jy][jx + 1], c2 = S.cc[jy + 1][jx], d2 = S.cc[jy + 1][jx + 1];
-      return cplx<float>{wy0 * (wx0 * a.x + wx1 * b2.x) + wy1 * (wx0 * c2.x + wx1 * d2.x),
-                         wy0 * (wx0 * a.y + wx1 * b2.y) + wy1 * (wx0 * c2.y + wx1 * d2.y)};
+      return cplx<float>{wy0[r] * (wx0 * a.x + wx1 * b2.x) + wy1[r] * (wx0 * c2.x + wx1 * d2.x),
+                         wy0[r] * (wx0 * a.y + wx1 * b2.y) + wy1[r] * (wx0 * c2.y + wx1 * d2.y)};
     };
 
-    __syncthreads();  // the previous segment's shared-memory reads are done
-    C cxy0 = cz<float>(), cxy1 = cz<float>(), ccpre = cz<float>();
+    __syncthreads();  // the previous range's shared memory is free
+    C cxy0[2] = {cz<float>(), cz<float>()}, cxy1[2] = {cz<float>(), cz<float>()}, ccpre = cz<float>();
     if (use_c) {
       if (threadIdx.x < 144) S.cc[threadIdx.x / 12][threadIdx.x % 12] = ld_cc(Z0 - 1);
       __syncthreads();
-      cxy0 = bil_cc();
+      cxy0[0] = bil_cc(0);
+      cxy0[1] = bil_cc(1);
       __syncthreads();
       if (threadIdx.x < 144) S.cc[threadIdx.x / 12][threadIdx.x % 12] = ld_cc(Z0);
       __syncthreads();
-      cxy1 = bil_cc();
+      cxy1[0] = bil_cc(0);
+      cxy1[1] = bil_cc(1);
       ccpre = ld_cc(Z0 + 1);
       __syncthreads();
     }
-    // u on planes 3 Z0 - 3 (c-plane Z0 - 1) and 3 Z0 - 2
-    C um = ldU(3 * Z0 - 3), u0 = ldU(3 * Z0 - 2);
-    if (use_c && colin) {
-      if (3 * Z0 - 3 > 0) um = um + cxy0;
-      if (3 * Z0 - 2 > 0) {
-        u0 = rfma(W0<1>(), cxy0, u0);
-        u0 = rfma(W1<1>(), cxy1, u0);
+    C um[2], u0[2], pu[3][2], pb[3][2], pidp[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      // u on planes 3 Z0 - 3 (c-plane Z0 - 1) and 3 Z0 - 2
+      um[r] = ldU(3 * Z0 - 3, r);
+      u0[r] = ldU(3 * Z0 - 2, r);
+      if (use_c && colin[r]) {
+        if (3 * Z0 - 3 > 0) um[r] = um[r] + cxy0[r];
+        if (3 * Z0 - 2 > 0) {
+          u0[r] = rfma(W0<1>(), cxy0[r], u0[r]);
+          u0[r] = rfma(W1<1>(), cxy1[r], u0[r]);
+        }
       }
+      if (cpx && cpy[r]) S.q[qslot(Z0 - 1)][by[r] / 3][lane / 3] = um[r];
+      // prefetch: step z uses U(z + 1) and b(z), slot z mod 3
+      pu[1][r] = ldU(3 * Z0 - 1, r);
+      pu[2][r] = ldU(3 * Z0, r);
+      pu[0][r] = ldU(3 * Z0 + 1, r);
+      pb[1][r] = ldB(3 * Z0 - 2, r);
+      pb[2][r] = ldB(3 * Z0 - 1, r);
+      pb[0][r] = ldB(3 * Z0, r);
+      pidp[r] = cz<float>();
     }
-    if (cpx && cpy) S.q[qslot(Z0 - 1)][warp / 3][lane / 3] = um;
-    // prefetch: step z uses U(z + 1) and b(z), slot z mod 3
-    C pu[3], pb[3];
-    pu[1] = ldU(3 * Z0 - 1);
-    pu[2] = ldU(3 * Z0);
-    pu[0] = ldU(3 * Z0 + 1);
-    pb[1] = ldB(3 * Z0 - 2);
-    pb[2] = ldB(3 * Z0 - 1);
-    pb[0] = ldB(3 * Z0);
-    C accA = cz<float>(), accB = cz<float>(), pidp = cz<float>();
+    C accA = cz<float>(), accB = cz<float>();
 
     // deferred work of residual plane zd, after the barrier of the next step
     auto deferred = [&](auto ozc, int zd) {
       constexpr int OZD = decltype(ozc)::value;
       const int bufd = zd & 1;
       if (emit && ejx < 9 && ejy < 9) {
-        const int by = 3 + 3 * ejy;
-        const C r0 = S.rx[bufd][by - 2][ejx], r1 = S.rx[bufd][by - 1][ejx], r2 = S.rx[bufd][by][ejx];
-        const C r3 = S.rx[bufd][by + 1][ejx], r4 = S.rx[bufd][by + 2][ejx];
-        const C ry = cplx<float>{fmaf(r0.x + r4.x, 1.f / 3.f, fmaf(r1.x + r3.x, 2.f / 3.f, r2.x)),
-                                 fmaf(r0.y + r4.y, 1.f / 3.f, fmaf(r1.y + r3.y, 2.f / 3.f, r2.y))};
+        const int ry_ = 3 + 3 * ejy;
+        const C ry = restrict5f(S.rx[bufd][ry_ - 2][ejx], S.rx[bufd][ry_ - 1][ejx], S.rx[bufd][ry_][ejx],
+                                S.rx[bufd][ry_ + 1][ejx], S.rx[bufd][ry_ + 2][ejx]);
         if (OZD == 0) {
           accA = accB + ry;
           accB = cz<float>();
@@ -236,47 +263,51 @@ __global__ void __launch_bounds__(kS3sThreads, 1) sweep3s_kernel(const Sweep3sAr
           accA = rfma(W0<OZD>(), ry, accA);
           accB = rfma(W1<OZD>(), ry, accB);
         }
-        if (OZD == 2) {
-          const int Zc = (zd - 2) / 3;
-          const int cx = C0x + ejx, cy = C0y + ejy;
-          if (Zc >= Z0 && Zc < Z1 && cx <= nc && cy <= nc && (ejx < 9 || cx == nc) && (ejy < 9 || cy == nc)) {
-            const bool inner = cx > 0 && cx < nc && cy > 0 && cy < nc && Zc > 0 && Zc < nc;
-            C bs = cz<float>(), uc = cz<float>();
-            if (inner) {
-              bs = accA;
-              const int gt = A.gtyp[cx] + kMaxG3 * (A.gtyp[cy] + kMaxG3 * A.gtyp[Zc]);
-              const C* gc = A.gcoef + gt * 27;
+      }
+      if (OZD == 2 && emit) {
+        const int Zc = (zd - 2) / 3;
+        const int cx = C0x + ejx, cy = C0y + ejy;
+        if (Zc >= Z0 && Zc < Z1 && cx <= nc && cy <= nc && (ejx < 9 || cx == nc) && (ejy < 9 || cy == nc)) {
+          const bool inner = cx > 0 && cx < nc && cy > 0 && cy < nc && Zc > 0 && Zc < nc;
+          C bs = cz<float>(), uc = cz<float>();
+          if (inner) {
+            bs = accA;
+            const int gt = A.gtyp[cx] + kMaxG3 * (A.gtyp[cy] + kMaxG3 * A.gtyp[Zc]);
+            const C* gc = A.gcoef + gt * 27;
 #pragma unroll
-              for (int kz = 0; kz < 3; ++kz) {
-                const int qs = qslot(Zc - 1 + kz);
+            for (int kz = 0; kz < 3; ++kz) {
+              const int qs = qslot(Zc - 1 + kz);
 #pragma unroll
-                for (int k = 0; k < 9; ++k)
-                  bs = cfma(ld_nc(gc + kz * 9 + k), S.q[qs][ejy + k / 3][ejx + k % 3], bs);
-              }
-              uc = S.q[qslot(Zc)][ejy + 1][ejx + 1];
+              for (int k = 0; k < 9; ++k)
+                bs = cfma(ld_nc(gc + kz * 9 + k), S.q[qs][ejy + k / 3][ejx + k % 3], bs);
             }
-            const long long ci = Zc * NNc + (long long)cy * Nc + cx;
-            A.b_coarse[ci] = bs;
-            A.u_coarse[ci] = uc;
+            uc = S.q[qslot(Zc)][ejy + 1][ejx + 1];
           }
+          const int ci = Zc * NNc + cy * Nc + cx;
+          A.b_coarse[ci] = bs;
+          A.u_coarse[ci] = uc;
         }
       }
-      if (bpx && OZD == 0 && owncol) {
-        // P I du on this column from the c-points of c-plane zd / 3
-        const int jx = lane / 3 - 1, jy = warp / 3 - 1;
-        const C a = S.dc[jy][jx];
-        const C b2 = ox ? S.dc[jy][jx + 1] : cz<float>();
-        const C c2 = oy ? S.dc[jy + 1][jx] : cz<float>();
-        const C d2 = (ox && oy) ? S.dc[jy + 1][jx + 1] : cz<float>();
-        const C pid = cplx<float>{wy0 * (wx0 * a.x + wx1 * b2.x) + wy1 * (wx0 * c2.x + wx1 * d2.x),
-                                  wy0 * (wx0 * a.y + wx1 * b2.y) + wy1 * (wx0 * c2.y + wx1 * d2.y)};
-        if (zd - 2 >= 3 * Z0) {
-          const C v1 = S.pv[0][warp][lane], v2 = S.pv[1][warp][lane];
-          A.out[(zd - 2) * NN + col] = v1 - (rmul(2.f / 3.f, pidp) + rmul(1.f / 3.f, pid));
-          A.out[(zd - 1) * NN + col] = v2 - (rmul(1.f / 3.f, pidp) + rmul(2.f / 3.f, pid));
+      if (bpx && OZD == 0) {
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          if (!owncol[r]) continue;
+          // P I du on this column from the c-points of c-plane zd / 3
+          const int jx = lane / 3 - 1, jy = by[r] / 3 - 1;
+          const C a = S.dc[jy][jx];
+          const C b2 = ox ? S.dc[jy][jx + 1] : cz<float>();
+          const C c2 = oy[r] ? S.dc[jy + 1][jx] : cz<float>();
+          const C d2 = (ox && oy[r]) ? S.dc[jy + 1][jx + 1] : cz<float>();
+          const C pid = cplx<float>{wy0[r] * (wx0 * a.x + wx1 * b2.x) + wy1[r] * (wx0 * c2.x + wx1 * d2.x),
+                                    wy0[r] * (wx0 * a.y + wx1 * b2.y) + wy1[r] * (wx0 * c2.y + wx1 * d2.y)};
+          if (zd - 2 >= 3 * Z0) {
+            const C v1 = S.pv[0][by[r]][lane], v2 = S.pv[1][by[r]][lane];
+            A.out[(zd - 2) * NN + col[r]] = v1 - (rmul(2.f / 3.f, pidp[r]) + rmul(1.f / 3.f, pid));
+            A.out[(zd - 1) * NN + col[r]] = v2 - (rmul(1.f / 3.f, pidp[r]) + rmul(2.f / 3.f, pid));
+          }
+          if (zd < 3 * Z1 || zd == n) A.out[zd * NN + col[r]] = S.pv[2][by[r]][lane] - pid;
+          pidp[r] = pid;
         }
-        if (zd < 3 * Z1 || zd == n) A.out[zd * NN + col] = S.pv[2][warp][lane] - pid;
-        pidp = pid;
       }
     };
 
@@ -286,48 +317,58 @@ __global__ void __launch_bounds__(kS3sThreads, 1) sweep3s_kernel(const Sweep3sAr
       constexpr int OZP = (OZ + 1) % 3;
       const int zp = z + 1;
       const int buf = z & 1;
-      // phase 1: u on plane z + 1
-      if (OZP == 0) cxy0 = cxy1;
-      C up = pu[OZ];
-      if (use_c && colin && zp > 0 && zp < n) {
-        up = rfma(W0<OZP>(), cxy0, up);
-        if (OZP != 0) up = rfma(W1<OZP>(), cxy1, up);
+      const int tz = (z >= 0 && z <= n) ? (int)__ldg(A.typ + z) : 0;
+      // phase 1: u on plane z + 1, z-pass of both rows
+      C up[2], za[2], zb[2];
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        if (OZP == 0) cxy0[r] = cxy1[r];
+        up[r] = pu[OZ][r];
+        if (use_c && colin[r] && zp > 0 && zp < n) {
+          up[r] = rfma(W0<OZP>(), cxy0[r], up[r]);
+          if (OZP != 0) up[r] = rfma(W1<OZP>(), cxy1[r], up[r]);
+        }
+        if (OZP == 0 && cpx && cpy[r]) S.q[qslot(zp / 3)][by[r] / 3][lane / 3] = up[r];
+        pu[OZ][r] = ldU(z + 4, r);
+        if (tz == 0) {
+          za[r] = tap3r(m0, m1, m2, um[r], u0[r], up[r]);
+          zb[r] = tap3r(p0, p1, p2, um[r], u0[r], up[r]);
+        } else {
+          za[r] = tap3c_acc(&S.row[tz][0], um[r], u0[r], up[r], cz<float>());
+          zb[r] = tap3c_acc(&S.row[tz][6], um[r], u0[r], up[r], cz<float>());
+        }
+        S.za[buf][by[r]][lane] = za[r];
+        S.zb[buf][by[r]][lane] = zb[r];
       }
-      if (OZP == 0 && cpx && cpy) S.q[qslot(zp / 3)][warp / 3][lane / 3] = up;
       if (OZP == 2 && use_c && threadIdx.x < 144) S.cc[threadIdx.x / 12][threadIdx.x % 12] = ccpre;
       if (OZP == 0 && use_c) ccpre = ld_cc(zp / 3 + 2);
-      pu[OZ] = ldU(z + 4);
-      // z-pass (class of plane z is uniform over the block)
-      const int tz = (z >= 0 && z <= n) ? (int)__ldg(A.typ + z) : 0;
-      C za, zb;
-      if (tz == 0) {
-        za = tap3r(m0, m1, m2, um, u0, up);
-        zb = tap3r(p0, p1, p2, um, u0, up);
-      } else {
-        za = tap3c_acc(&S.row[tz][0], um, u0, up, cz<float>());
-        zb = tap3c_acc(&S.row[tz][6], um, u0, up, cz<float>());
-      }
-      S.za[buf][warp][lane] = za;
-      S.zb[buf][warp][lane] = zb;
       __syncthreads();
       // phase 2: deferred work of plane z - 1; coarse correction plane for the next steps
       if (z > zs) deferred(IC<(OZ + 2) % 3>{}, z - 1);
-      if (OZP == 0 && use_c) cxy1 = bil_cc();
-      // phase 3: residual on plane z
+      if (OZP == 0 && use_c) {
+        cxy1[0] = bil_cc(0);
+        cxy1[1] = bil_cc(1);
+      }
+      // phase 3: residuals on plane z; the pair's outer neighbour rows from shared memory
       const bool zin = z > 0 && z < n;
       const bool zown = (z >= 3 * Z0 && z < 3 * Z1) || z == n;
-      C r = cz<float>();
-      if (rrow) {
-        const C am = S.za[buf][warp - 1][lane], ap = S.za[buf][warp + 1][lane];
-        const C bm = S.zb[buf][warp - 1][lane], bp = S.zb[buf][warp + 1][lane];
+      const C aU = warp > 0 ? S.za[buf][by[0] - 1][lane] : cz<float>();
+      const C bU = warp > 0 ? S.zb[buf][by[0] - 1][lane] : cz<float>();
+      const C aD = warp < 15 ? S.za[buf][by[1] + 1][lane] : cz<float>();
+      const C bD = warp < 15 ? S.zb[buf][by[1] + 1][lane] : cz<float>();
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        if (!rrow[r]) continue;  // warp-uniform
+        const C am = r == 0 ? aU : za[0], ap = r == 0 ? za[1] : aD;
+        const C bm = r == 0 ? bU : zb[0], bp = r == 0 ? zb[1] : bD;
         C cy, ey;
-        if (yreal) {
-          cy = tap3r_acc(k0, k1, k2, am, za, ap, tap3r(m0, m1, m2, bm, zb, bp));
-          ey = tap3r(m0, m1, m2, am, za, ap);
+        if (yreal[r]) {
+          cy = tap3r_acc(k0, k1, k2, am, za[r], ap, tap3r(m0, m1, m2, bm, zb[r], bp));
+          ey = tap3r(m0, m1, m2, am, za[r], ap);
         } else {
-          const C* rw = &S.row[ty][0];
-          cy = tap3c_acc(rw + 3, am, za, ap, tap3c_acc(rw, bm, zb, bp, cz<float>()));
-          ey = tap3c_acc(rw, am, za, ap, cz<float>());
+          const C* rw = &S.row[ty[r]][0];
+          cy = tap3c_acc(rw + 3, am, za[r], ap, tap3c_acc(rw, bm, zb[r], bp, cz<float>()));
+          ey = tap3c_acc(rw, am, za[r], ap, cz<float>());
         }
         const C cl = shfl_c(cy, 1, true), cr = shfl_c(cy, 1, false);
         const C el = shfl_c(ey, 1, true), er = shfl_c(ey, 1, false);
@@ -338,30 +379,34 @@ __global__ void __launch_bounds__(kS3sThreads, 1) sweep3s_kernel(const Sweep3sAr
           const C* rw = &S.row[tx][0];
           hu = tap3c_acc(rw + 3, el, ey, er, tap3c_acc(rw, cl, cy, cr, cz<float>()));
         }
-        if (colin && zin && lane >= 1 && lane <= 30) r = pb[OZ] - hu;
-        if (owncol && zown) nrm = fmaf(r.x, r.x, fmaf(r.y, r.y, nrm));
+        C res = cz<float>();
+        if (colin[r] && zin && lane >= 1 && lane <= 30) res = pb[OZ][r] - hu;
+        if (owncol[r] && zown) nrm = fmaf(res.x, res.x, fmaf(res.y, res.y, nrm));
         // Jacobi update, c-point mask (hb), outputs or BPX hold
-        C du = S.omd[tx + 4 * ty + 16 * tz] * r;
-        if (A.hb && OZ == 0 && cpx && cpy) du = cz<float>();
-        const C v = A.fine ? u0 + du : du;
+        C du = S.omd[tx + 4 * ty[r] + 16 * tz] * res;
+        if (A.hb && OZ == 0 && cpx && cpy[r]) du = cz<float>();
+        const C v = A.fine ? u0[r] + du : du;
         if (!bpx) {
-          if (owncol && zown) A.out[z * NN + col] = v;
-        } else if (owncol) {
-          S.pv[OZ == 1 ? 0 : (OZ == 2 ? 1 : 2)][warp][lane] = v;
+          if (owncol[r] && zown) A.out[z * NN + col[r]] = v;
+        } else if (owncol[r]) {
+          S.pv[OZ == 1 ? 0 : (OZ == 2 ? 1 : 2)][by[r]][lane] = v;
         }
-        if (bpx && OZ == 0 && cpx && cpy && lane >= 3 && warp >= 3) S.dc[warp / 3 - 1][lane / 3 - 1] = du;
+        if (bpx && OZ == 0 && cpx && cpy[r] && lane >= 3 && by[r] >= 3)
+          S.dc[by[r] / 3 - 1][lane / 3 - 1] = du;
         // restriction along x to the c-columns
         if (A.has_coarse) {
-          const C r1l = shfl_c(r, 1, true), r1r = shfl_c(r, 1, false);
-          const C r2l = shfl_c(r, 2, true), r2r = shfl_c(r, 2, false);
-          const C rr = cplx<float>{fmaf(r2l.x + r2r.x, 1.f / 3.f, fmaf(r1l.x + r1r.x, 2.f / 3.f, r.x)),
-                                   fmaf(r2l.y + r2r.y, 1.f / 3.f, fmaf(r1l.y + r1r.y, 2.f / 3.f, r.y))};
-          if (cpx && lane >= 3 && lane <= 30) S.rx[buf][warp][lane / 3 - 1] = rr;
+          const C r1l = shfl_c(res, 1, true), r1r = shfl_c(res, 1, false);
+          const C r2l = shfl_c(res, 2, true), r2r = shfl_c(res, 2, false);
+          if (cpx && lane >= 3 && lane <= 30)
+            S.rx[buf][by[r]][lane / 3 - 1] = restrict5f(r2l, r1l, res, r1r, r2r);
         }
       }
-      pb[OZ] = ldB(z + 3);
-      um = u0;
-      u0 = up;
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        pb[OZ][r] = ldB(z + 3, r);
+        um[r] = u0[r];
+        u0[r] = up[r];
+      }
     };
 
     for (int Zc = Z0 - 1; Zc < Z1; ++Zc) {
@@ -375,7 +420,7 @@ __global__ void __launch_bounds__(kS3sThreads, 1) sweep3s_kernel(const Sweep3sAr
     if (Z1 == nc && emit) {
       const int cx = C0x + ejx, cy = C0y + ejy;
       if (cx <= nc && cy <= nc && (ejx < 9 || cx == nc) && (ejy < 9 || cy == nc)) {
-        const long long ci = nc * NNc + (long long)cy * Nc + cx;
+        const int ci = nc * NNc + cy * Nc + cx;
         A.b_coarse[ci] = cz<float>();
         A.u_coarse[ci] = cz<float>();
       }
