@@ -120,18 +120,18 @@ template <int O> __device__ __forceinline__ constexpr float W1() {
 // two columns, the y-pass of a row pair needs only the two outer neighbour
 // rows from shared memory, and 128 registers hold both columns' state (one
 // row per thread at 1024 threads was 15% slower and spilled at 64 registers).
-constexpr int kS3sThreads = 512;
-
-__global__ void __launch_bounds__(kS3sThreads, 1) sweep3s_kernel(const Sweep3sArgs A) {
+template <int RPT>
+__global__ void __launch_bounds__(32 * (32 / RPT), 1) sweep3s_kernel(const Sweep3sArgs A) {
+  constexpr int NTHR = 32 * (32 / RPT), NW = 32 / RPT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double s_red[kS3sThreads / 32];
+  __shared__ double s_red[NTHR / 32];
   Sweep3sShared& S = *reinterpret_cast<Sweep3sShared*>(smem_raw);
   using C = cplx<float>;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int n = A.n, N = n + 1, nc = n / 3;
   const int NN = N * N, Nc = nc + 1, NNc = Nc * Nc;  // level sizes stay below 2^31 vertices
-  for (int i = threadIdx.x; i < 36; i += kS3sThreads) S.row[i / 9][i % 9] = A.row[i / 9][i % 9];
-  for (int i = threadIdx.x; i < 64; i += kS3sThreads) S.omd[i] = A.omd[i];
+  for (int i = threadIdx.x; i < 36; i += NTHR) S.row[i / 9][i % 9] = A.row[i / 9][i % 9];
+  for (int i = threadIdx.x; i < 64; i += NTHR) S.omd[i] = A.omd[i];
   const bool zero_u = A.fine && A.first;
   const bool use_c = A.fine && !A.first && A.c != nullptr;
   const bool bpx = A.hier && !A.hb;
@@ -146,12 +146,12 @@ __global__ void __launch_bounds__(kS3sThreads, 1) sweep3s_kernel(const Sweep3sAr
   const int ox = lane % 3;
   const float wx1 = ox == 0 ? 0.f : (ox == 1 ? 1.f / 3.f : 2.f / 3.f), wx0 = 1.f - wx1;
   const bool cpx = ox == 0;
-  int by[2], oy[2];
-  float wy0[2], wy1[2];
-  bool cpy[2], rrow[2];
+  int by[RPT], oy[RPT];
+  float wy0[RPT], wy1[RPT];
+  bool cpy[RPT], rrow[RPT];
 #pragma unroll
-  for (int r = 0; r < 2; ++r) {
-    by[r] = 2 * warp + r;  // box row
+  for (int r = 0; r < RPT; ++r) {
+    by[r] = RPT * warp + r;  // box row
     oy[r] = by[r] % 3;
     wy1[r] = oy[r] == 0 ? 0.f : (oy[r] == 1 ? 1.f / 3.f : 2.f / 3.f);
     wy0[r] = 1.f - wy1[r];
@@ -173,10 +173,10 @@ __global__ void __launch_bounds__(kS3sThreads, 1) sweep3s_kernel(const Sweep3sAr
     const bool lastx = C0x + 9 >= nc, lasty = C0y + 9 >= nc;
     const int tx = (gx >= 0 && gx <= n) ? (int)A.typ[gx] : 0;
     const bool xreal = __all_sync(0xffffffffu, tx == 0);
-    int gy[2], col[2], ty[2];
-    bool colin[2], owncol[2], yreal[2];
+    int gy[RPT], col[RPT], ty[RPT];
+    bool colin[RPT], owncol[RPT], yreal[RPT];
 #pragma unroll
-    for (int r = 0; r < 2; ++r) {
+    for (int r = 0; r < RPT; ++r) {
       gy[r] = y0 - 3 + by[r];
       colin[r] = gx > 0 && gx < n && gy[r] > 0 && gy[r] < n;
       owncol[r] = lane >= 3 && (lane < 30 || (lane == 30 && lastx)) && by[r] >= 3 &&
@@ -209,23 +209,27 @@ __global__ void __launch_bounds__(kS3sThreads, 1) sweep3s_kernel(const Sweep3sAr
     };
 
     __syncthreads();  // the previous range's shared memory is free
-    C cxy0[2] = {cz<float>(), cz<float>()}, cxy1[2] = {cz<float>(), cz<float>()}, ccpre = cz<float>();
+    C cxy0[RPT], cxy1[RPT], ccpre = cz<float>();
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) cxy0[r] = cxy1[r] = cz<float>();
+    // one coarse plane of the pending correction through S.cc: threads < 144
+    // load it (blocks have at least 256 threads)
     if (use_c) {
       if (threadIdx.x < 144) S.cc[threadIdx.x / 12][threadIdx.x % 12] = ld_cc(Z0 - 1);
       __syncthreads();
-      cxy0[0] = bil_cc(0);
-      cxy0[1] = bil_cc(1);
+#pragma unroll
+      for (int r = 0; r < RPT; ++r) cxy0[r] = bil_cc(r);
       __syncthreads();
       if (threadIdx.x < 144) S.cc[threadIdx.x / 12][threadIdx.x % 12] = ld_cc(Z0);
       __syncthreads();
-      cxy1[0] = bil_cc(0);
-      cxy1[1] = bil_cc(1);
+#pragma unroll
+      for (int r = 0; r < RPT; ++r) cxy1[r] = bil_cc(r);
       ccpre = ld_cc(Z0 + 1);
       __syncthreads();
     }
-    C um[2], u0[2], pu[3][2], pb[3][2], pidp[2];
+    C um[RPT], u0[RPT], pu[3][RPT], pb[3][RPT], pidp[RPT];
 #pragma unroll
-    for (int r = 0; r < 2; ++r) {
+    for (int r = 0; r < RPT; ++r) {
       // u on planes 3 Z0 - 3 (c-plane Z0 - 1) and 3 Z0 - 2
       um[r] = ldU(3 * Z0 - 3, r);
       u0[r] = ldU(3 * Z0 - 2, r);
@@ -290,7 +294,7 @@ __global__ void __launch_bounds__(kS3sThreads, 1) sweep3s_kernel(const Sweep3sAr
       }
       if (bpx && OZD == 0) {
 #pragma unroll
-        for (int r = 0; r < 2; ++r) {
+        for (int r = 0; r < RPT; ++r) {
           if (!owncol[r]) continue;
           // P I du on this column from the c-points of c-plane zd / 3
           const int jx = lane / 3 - 1, jy = by[r] / 3 - 1;
@@ -319,9 +323,9 @@ __global__ void __launch_bounds__(kS3sThreads, 1) sweep3s_kernel(const Sweep3sAr
       const int buf = z & 1;
       const int tz = (z >= 0 && z <= n) ? (int)__ldg(A.typ + z) : 0;
       // phase 1: u on plane z + 1, z-pass of both rows
-      C up[2], za[2], zb[2];
+      C up[RPT], za[RPT], zb[RPT];
 #pragma unroll
-      for (int r = 0; r < 2; ++r) {
+      for (int r = 0; r < RPT; ++r) {
         if (OZP == 0) cxy0[r] = cxy1[r];
         up[r] = pu[OZ][r];
         if (use_c && colin[r] && zp > 0 && zp < n) {
@@ -346,21 +350,22 @@ __global__ void __launch_bounds__(kS3sThreads, 1) sweep3s_kernel(const Sweep3sAr
       // phase 2: deferred work of plane z - 1; coarse correction plane for the next steps
       if (z > zs) deferred(IC<(OZ + 2) % 3>{}, z - 1);
       if (OZP == 0 && use_c) {
-        cxy1[0] = bil_cc(0);
-        cxy1[1] = bil_cc(1);
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) cxy1[r] = bil_cc(r);
       }
       // phase 3: residuals on plane z; the pair's outer neighbour rows from shared memory
       const bool zin = z > 0 && z < n;
       const bool zown = (z >= 3 * Z0 && z < 3 * Z1) || z == n;
       const C aU = warp > 0 ? S.za[buf][by[0] - 1][lane] : cz<float>();
       const C bU = warp > 0 ? S.zb[buf][by[0] - 1][lane] : cz<float>();
-      const C aD = warp < 15 ? S.za[buf][by[1] + 1][lane] : cz<float>();
-      const C bD = warp < 15 ? S.zb[buf][by[1] + 1][lane] : cz<float>();
+      const C aD = warp < NW - 1 ? S.za[buf][by[RPT - 1] + 1][lane] : cz<float>();
+      const C bD = warp < NW - 1 ? S.zb[buf][by[RPT - 1] + 1][lane] : cz<float>();
 #pragma unroll
-      for (int r = 0; r < 2; ++r) {
+      for (int r = 0; r < RPT; ++r) {
         if (!rrow[r]) continue;  // warp-uniform
-        const C am = r == 0 ? aU : za[0], ap = r == 0 ? za[1] : aD;
-        const C bm = r == 0 ? bU : zb[0], bp = r == 0 ? zb[1] : bD;
+        // neighbour rows: the thread's own rows, the pair's outer ones from shared memory
+        const C am = r == 0 ? aU : za[r > 0 ? r - 1 : 0], ap = r == RPT - 1 ? aD : za[r < RPT - 1 ? r + 1 : r];
+        const C bm = r == 0 ? bU : zb[r > 0 ? r - 1 : 0], bp = r == RPT - 1 ? bD : zb[r < RPT - 1 ? r + 1 : r];
         C cy, ey;
         if (yreal[r]) {
           cy = tap3r_acc(k0, k1, k2, am, za[r], ap, tap3r(m0, m1, m2, bm, zb[r], bp));
@@ -402,7 +407,7 @@ __global__ void __launch_bounds__(kS3sThreads, 1) sweep3s_kernel(const Sweep3sAr
         }
       }
 #pragma unroll
-      for (int r = 0; r < 2; ++r) {
+      for (int r = 0; r < RPT; ++r) {
         pb[OZ][r] = ldB(z + 3, r);
         um[r] = u0[r];
         u0[r] = up[r];
@@ -427,7 +432,7 @@ __global__ void __launch_bounds__(kS3sThreads, 1) sweep3s_kernel(const Sweep3sAr
     }
   }
   if (A.fine && A.norm2 != nullptr)
-    block_norm_finish_tile<kS3sThreads>((double)nrm, s_red, A.partial, A.ticket, A.norm2, blockIdx.x,
+    block_norm_finish_tile<NTHR>((double)nrm, s_red, A.partial, A.ticket, A.norm2, blockIdx.x,
                                          gridDim.x);
 }
 
