@@ -837,7 +837,10 @@ cudaError_t launch_sweep3s(mg_ctx* c, Hier<float>& H, int l, bool fine, int hb, 
   A.partial = H.partial;
   A.ticket = H.ticket;
   A.norm2 = fine ? H.norm2 : nullptr;
-  const long long grid = std::min<long long>(152, std::max<long long>(1, (A.nunits + 3) / 4));
+  // fine levels: about four coarse planes per block at least (a range's first
+  // coarse step is overhead); coarse levels: every SM that has a unit
+  const long long upb = fine ? 4 : 1;
+  const long long grid = std::min<long long>(152, std::max<long long>(1, (A.nunits + upb - 1) / upb));
   // two box rows per thread (four: 255 registers, 8 warps per SM, 17% slower)
   mg::sweep3s_kernel<2><<<(int)grid, 512, sizeof(mg::Sweep3sShared), c->stream>>>(A);
   return cudaGetLastError();
