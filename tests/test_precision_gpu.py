@@ -99,3 +99,29 @@ def test_c64_3d_refinement_reaches_fp64_tolerance():
     r = o.residual(g.get_solution())
     assert np.linalg.norm(r) <= 1e-8 * np.linalg.norm(o.b) * 1.01
     g.close()
+
+
+def test_c64_3d_full_size_refinement_checked_by_independent_residual():
+    """3D depth 5 (243^3 cells, the bench's 3D size; the oracle is too slow
+    there): the refinement form -- separable complex64 sweeps on levels 5..3,
+    the fused FP64 defect kernel for the outer steps -- reaches 1e-8, and the
+    residual of the result as computed by a different kernel (the complex128
+    z-marching sweep's fused norm, 27-point type rows) confirms it."""
+    c = W.definite(W.config3())
+    g = mg.Solver(3, 5, c["k2"], c["theta"], c["layer_width"])
+    g.set_rhs(c["f"])
+    a0, _ = g.residual_norm()  # u = 0: |b|
+    om = O.omega_scheme(O.EXP, 0.6, 5)
+    g.set_precision(mg.MG_C64_REFINE, 16)
+    st, n, rel = g.solve(mg.MG_ADD, om, mg.MG_DLINEAR, 1e-8, 2000)
+    assert st == mg.MG_OK and rel <= 1e-8
+    u = g.get_solution()
+    g.set_precision(mg.MG_C128, 1)
+    g.set_solution(u)
+    g.cycle(mg.MG_ADD, om, mg.MG_DLINEAR)
+    a_fused, _ = g.last_cycle_norm()  # residual of u, entering that cycle
+    assert a_fused <= 1.0001e-8 * a0, (a_fused / a0, rel)
+    # two FP64 evaluation orders of a residual 1e-9 the size of its terms:
+    # 27 terms x 2^-53 / 1e-9 ~ 3e-6 relative
+    assert abs(a_fused / a0 - rel) <= 1e-5 * rel
+    g.close()
