@@ -1735,14 +1735,8 @@ int mg_set_trace(mg_ctx* c, int enable) {
   if (enable && c->trace == nullptr)
     MG_CUDA(c, cudaMalloc(&c->trace, 4ull * (kTraceFine + kTraceChain) * sizeof(unsigned long long)));
   if (enable) MG_CUDA(c, cudaMemset(c->trace, 0, 4ull * (kTraceFine + kTraceChain) * sizeof(unsigned long long)));
-  // captured cycles bake the trace pointer: drop them when the switch flips
-  if ((enable != 0) != c->tracing) {
-    for (auto& g : c->h64.graphs) {
-      if (g.fine) cudaGraphExecDestroy(g.fine);
-      if (g.coarse) cudaGraphExecDestroy(g.coarse);
-    }
-    c->h64.graphs.clear();
-  }
+  // captured cycles (both precisions) bake the trace pointer: drop them when the switch flips
+  if ((enable != 0) != c->tracing) drop_graphs(c);
   c->tracing = enable != 0;
   return MG_OK;
 }
