@@ -393,7 +393,52 @@ def measure_forms(mg, torch, peaks):
     Jv, dt = wall(fwd_bwd)
     out["adjoint_2d_depth6"] = {"J": Jv, "seconds_forward_backward": dt, "tol": 1e-10}
     s.close()
+    out["csg_sweep"] = csg_sweep(mg, torch)
     return out
+
+
+def csg_sweep(mg, torch, cycles=300):
+    """The paper's complex-scaled-grid regime (Section 7.3): every cell rotated
+    (layer width 0.5), Dirichlet boundary, omega = 0.8 on every level, kh = 5/9
+    (k = 5, 15, 45, 135 on depths 2..5), rotation angles 0..45 degrees, the
+    four variants; rhs a centred Gaussian of width 0.05, u0 = 0.  Per run: the
+    cycles to a relative residual of 1e-8 (None if not reached), the relative
+    residual after the run, and the mean reduction per cycle over cycles
+    10 .. (1e-8 or the end)."""
+    variants = {"add": (mg.MG_ADD, mg.MG_DLINEAR), "hb": (mg.MG_HB, mg.MG_DLINEAR),
+                "bpx": (mg.MG_BPX, mg.MG_HIERARCHICAL), "hb-hier": (mg.MG_HB, mg.MG_HIERARCHICAL)}
+    rows = []
+    t0 = time.perf_counter()
+    for k, depth in ((5, 2), (15, 3), (45, 4), (135, 5)):
+        for deg in (0, 30, 35, 40, 45):
+            k2 = W.constant_k2(2, depth, float(k * k))
+            f = W.gaussian(2, depth, (0.5, 0.5), 0.05)
+            s = mg.Solver(2, depth, k2, math.radians(deg), 0.5)
+            s.set_rhs(f)
+            om = np.full(depth, 0.8)
+            for name, (v, t) in variants.items():
+                s.set_solution(np.zeros(s.shape, complex))
+                s.residual_norm()  # reference residual of u0
+                hist, hit = [], None
+                for c in range(cycles + 1):
+                    s.cycle(v, om, t)
+                    rel = s.last_cycle_norm()[1]  # residual of the iterate after c cycles
+                    hist.append(rel)
+                    if hit is None and rel <= 1e-8:
+                        hit = c
+                        break
+                    if not np.isfinite(rel) or rel > 1e30:
+                        break
+                end = len(hist) - 1
+                rate = float("nan")
+                if end > 10 and hist[10] > 0 and np.isfinite(hist[end]):
+                    rate = (hist[end] / hist[10]) ** (1.0 / (end - 10))
+                rows.append({"k": k, "depth": depth, "theta_deg": deg, "variant": name,
+                             "cycles_to_1e-8": hit, "rel_res": float(hist[-1]), "cycles_run": end,
+                             "rate_per_cycle": float(rate)})
+            s.close()
+    return {"cycles_max": cycles, "omega": 0.8, "layer_width": 0.5, "seconds": time.perf_counter() - t0,
+            "runs": rows}
 
 
 # ---------------------------------------------------------------- main

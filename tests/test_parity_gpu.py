@@ -238,3 +238,14 @@ def test_config3_full_size_fused_norm_matches_standalone_residual():
         g.cycle(mg.MG_BPX, om, mg.MG_HIERARCHICAL)
         a_fused, _ = g.last_cycle_norm()
         assert abs(a_fused - a_ref) <= 1e-12 * a_ref, (a_fused, a_ref)
+
+
+@pytest.mark.parametrize("var", VARIANTS, ids=["add", "hb", "bpx", "hb-hier"])
+@pytest.mark.parametrize("k,depth", [(5, 2), (15, 3), (45, 4)])
+def test_csg_regime_iterates(var, k, depth):
+    """The paper's complex-scaled-grid regime (Section 7.3): every cell rotated
+    (layer width 0.5) by 35 degrees, kh = 5/9, omega = 0.8 on every level."""
+    k2 = W.constant_k2(2, depth, float(k * k))
+    f = W.gaussian(2, depth, (0.5, 0.5), 0.05)
+    g, o = pair(2, depth, k2, math.radians(35.0), 0.5, f, W.random_complex(2, depth, 90 + depth))
+    run_iterates(g, o, var, np.full(depth, 0.8), 3)
