@@ -32,6 +32,13 @@ R1  Coordinate-wise exterior scaling: along axis j a cell's spacing is
     (Section 7.4 rotates "cells close to" the open faces; Section 7.3 scales
     h in each dimension).  w >= 0.5 rotates every cell (full complex scaled
     grid).  Membership uses the cell centre on every level.
+R1b The channel problem of Section 7.4 puts the layer at two faces only (top
+    and right, within 1/3 of the domain, 30 degrees) and rotates every other
+    cell by theta "independently of this absorbing layer": along each axis a
+    cell with centre c is in the layer when c < w_lo or 1 - c < w_hi and has
+    spacing h*e^{i theta}; every other cell has h*e^{i theta_interior}.
+    ``layer_width`` is w (both faces, w_lo = w_hi = w) or the pair
+    (w_lo, w_hi); the two layers covering the axis rotate every cell.
 R2  The cell value of the shift is the mean of its 2^d vertex values of
     phi = k^2; coarse levels sample k^2 at their own vertices (injection).
 R3  The fine right-hand side is the consistent mass product b = M f of nodal
@@ -39,6 +46,13 @@ R3  The fine right-hand side is the consistent mass product b = M f of nodal
 R4  "Iterate n" is the fine solution after n cycles with every correction
     applied (the paper's pipelined traversal lags by half a sweep).
 R5  R = P^T exactly (tripartite d-linear weights).
+R6  The Section 7.4 table (used by the tests, not by this file's cycle):
+    pure Jacobi is the cycle with zero factors below the finest level; on the
+    unrotated problem (theta = 0) it alternates the two-phase factors
+    0.01 (sqrt 3 - i) and its negated conjugate, and every Jacobi run with a
+    rotated interior uses 0.4, the factor the text fixes for Jacobi smoothers
+    that apply complex rotations.  The transition scheme and BPX use
+    omega_S = 0.4.  Reductions are max norms, |r_50| / |r_0| from u = 0.
 """
 from __future__ import annotations
 
@@ -59,27 +73,37 @@ def cells_per_axis(level: int) -> int:
     return 3 ** level
 
 
-def rotated_cells(level: int, layer_width: float) -> np.ndarray:
-    """Reading R1: flag per cell index along one axis, True inside the layer.
+def layer_widths(layer_width):
+    """(w_lo, w_hi) from a symmetric width w or a pair (readings R1, R1b)."""
+    if np.ndim(layer_width) == 0:
+        return float(layer_width), float(layer_width)
+    lo, hi = layer_width
+    return float(lo), float(hi)
 
-    Cell i has centre (i + 1/2)/n; min(c, 1 - c) < w is tested in the exact
-    integer form min(2i + 1, 2n - 2i - 1) < 2 w n.
+
+def rotated_cells(level: int, layer_width) -> np.ndarray:
+    """Readings R1/R1b: flag per cell index along one axis, True inside the
+    layer.
+
+    Cell i has centre c = (i + 1/2)/n; c < w_lo and 1 - c < w_hi are tested in
+    the exact integer forms 2i + 1 < 2 w_lo n and 2n - 2i - 1 < 2 w_hi n.
     """
     n = cells_per_axis(level)
-    if layer_width >= 0.5:
+    lo, hi = layer_widths(layer_width)
+    if lo + hi >= 1.0:
         return np.ones(n, dtype=bool)
     i = np.arange(n)
-    return np.minimum(2 * i + 1, 2 * n - 2 * i - 1) < 2.0 * layer_width * n
+    return (2 * i + 1 < 2.0 * lo * n) | (2 * n - 2 * i - 1 < 2.0 * hi * n)
 
 
-def axis_spacing(level: int, theta: float, layer_width: float) -> np.ndarray:
-    """Complex cell width per cell index along one axis: h or h e^{i theta}
-    (complex scaled grid, Section 2 and Section 7.3)."""
+def axis_spacing(level: int, theta: float, layer_width, theta_interior: float = 0.0) -> np.ndarray:
+    """Complex cell width per cell index along one axis: h e^{i theta} in the
+    layer, h e^{i theta_interior} elsewhere (complex scaled grid, Section 2,
+    Section 7.3 and Section 7.4)."""
     n = cells_per_axis(level)
     h = 1.0 / n
-    rot = complex(math.cos(theta), math.sin(theta))
-    out = np.full(n, h, dtype=np.complex128)
-    out[rotated_cells(level, layer_width)] = h * rot
+    out = np.full(n, h * complex(math.cos(theta_interior), math.sin(theta_interior)), dtype=np.complex128)
+    out[rotated_cells(level, layer_width)] = h * complex(math.cos(theta), math.sin(theta))
     return out
 
 
@@ -136,10 +160,10 @@ class Level:
     shifts phi_c and the accumulated diagonal (Section 3: diag(H_l) is
     accumulated cell by cell, which complex layers and varying phi require)."""
 
-    def __init__(self, d, level, k2_vertices, theta, layer_width):
+    def __init__(self, d, level, k2_vertices, theta, layer_width, theta_interior=0.0):
         self.d, self.level = d, level
         self.n = cells_per_axis(level)
-        self.h_axis = axis_spacing(level, theta, layer_width)
+        self.h_axis = axis_spacing(level, theta, layer_width, theta_interior)
         k2 = np.asarray(k2_vertices, dtype=np.float64)
         assert k2.shape == (self.n + 1,) * d
         # R2: cell shift = mean of the 2^d vertex values
@@ -304,16 +328,17 @@ class Hierarchy:
     state (u_L, b_L).  Coarse solutions are never stored: they are the
     injections of u_L (Lemma 1, Eq. injection)."""
 
-    def __init__(self, d, depth, k2_fine, theta, layer_width):
+    def __init__(self, d, depth, k2_fine, theta, layer_width, theta_interior=0.0):
         self.d, self.L = d, depth
         self.theta, self.layer_width = theta, layer_width
+        self.theta_interior = theta_interior
         k2 = np.asarray(k2_fine, dtype=np.float64)
         n = cells_per_axis(depth)
         assert k2.shape == (n + 1,) * d
         self.k2 = {depth: k2}
         for lev in range(depth - 1, 0, -1):
             self.k2[lev] = inject(self.k2[lev + 1])
-        self.levels = {lev: Level(d, lev, self.k2[lev], theta, layer_width)
+        self.levels = {lev: Level(d, lev, self.k2[lev], theta, layer_width, theta_interior)
                        for lev in range(1, depth + 1)}
         self.u = np.zeros((n + 1,) * d, dtype=np.complex128)
         self.b = np.zeros_like(self.u)
@@ -334,6 +359,11 @@ class Hierarchy:
     def residual(self, u=None):
         u = self.u if u is None else u
         return self.b - self.levels[self.L].apply(u)
+
+    def residual_max(self):
+        """Maximum modulus of b - H u over the vertices (the max norm of the
+        Section 7.4 table)."""
+        return float(np.abs(self.residual()).max())
 
     def residual_norm(self):
         """Euclidean norm of b - H u over the fine vertices and the same norm

@@ -118,3 +118,24 @@ def definite(cfg):
     out = dict(cfg)
     out["k2"] = -np.asarray(cfg["k2"])
     return out
+
+
+CHANNEL_OMEGA1 = 0.01 * (math.sqrt(3.0) - 1j)    # two-phase Jacobi factors (Section 7.4)
+CHANNEL_OMEGA2 = -CHANNEL_OMEGA1.conjugate()
+
+
+def channel(theta_interior_deg, depth=4):
+    """The p = 2 channel problem of Section 7.4 (Eq. 08-gaussian): nodal
+    f = chi = exp(-(125x)^2 - (125y)^2), k^2 = phi = 45^2 + 135^2 (exp(-(15x)^2)
+    + exp(-(15y)^2)), homogeneous Dirichlet values on all faces, a 30 degree
+    layer within 1/3 of the top and right faces (the high end of each axis)
+    and every other cell rotated by the given interior angle; h = 1/81 at
+    depth 4."""
+    d = 2
+    y, x = coords(d, depth)
+    phi = 45.0 ** 2 + 135.0 ** 2 * (np.exp(-(15.0 * x) ** 2) + np.exp(-(15.0 * y) ** 2))
+    chi = np.exp(-(125.0 * x) ** 2 - (125.0 * y) ** 2)
+    return dict(d=d, depth=depth, theta=math.radians(30.0), layer_width=(0.0, 1.0 / 3.0),
+                theta_interior=math.radians(theta_interior_deg),
+                k2=np.broadcast_to(phi, (3 ** depth + 1,) * d).copy(),
+                f=np.broadcast_to(chi, (3 ** depth + 1,) * d).astype(np.complex128))

@@ -5,10 +5,12 @@ independent route to the same result -- closed-form stencils and eigenvalues
 of the d-linear finite element operator, the Galerkin identity of nested
 element spaces, the textbook additive correction scheme (Algorithm 1) built
 from Kronecker products, dense direct solves, and the analytic Poisson
-solution of Section 7.1.
+solution of Section 7.1, and the residual reductions that Table 2 prints for
+the channel problem of Section 7.4.
 """
 import itertools
 import math
+import os
 
 import numpy as np
 import pytest
@@ -18,10 +20,10 @@ import oracle as O
 TH = math.pi / 6
 
 
-def dense_level(d, level, k2, theta, w):
+def dense_level(d, level, k2, theta, w, theta_interior=0.0):
     """Dense matrix of the oracle's level operator on interior unknowns,
     obtained by applying it to unit vectors."""
-    lev = O.Level(d, level, k2, theta, w)
+    lev = O.Level(d, level, k2, theta, w, theta_interior)
     n = 3 ** level
     inner = list(itertools.product(range(1, n), repeat=d))
     A = np.zeros((len(inner), len(inner)), dtype=np.complex128)
@@ -405,3 +407,136 @@ def test_omega_schemes():
     np.testing.assert_allclose(O.omega_scheme(O.TRANSITION, 0.5, 3, iter_n=2),
                                [0.5 ** 1.5, 0.5, 0.5 ** 0.5])
     np.testing.assert_allclose(O.omega_scheme(O.TRANSITION, 0.5, 3, iter_n=1), [1, 1, 1])
+
+
+# ---------------------------------------------------------------- general scaling (Section 7.4)
+def test_one_sided_layer_membership():
+    """Reading R1b: a layer within 1/3 of the high face holds the 27 cells of
+    h = 1/81 whose centre exceeds 2/3; the low-face layer is its mirror image;
+    a symmetric width w is the pair (w, w); layers covering the axis rotate
+    every cell."""
+    rot = O.rotated_cells(4, (0.0, 1 / 3))
+    assert rot.sum() == 27 and rot[54:].all() and not rot[:54].any()
+    assert (O.rotated_cells(4, (1 / 3, 0.0)) == rot[::-1]).all()
+    for lev, w in [(3, 4 / 27), (2, 0.2), (3, 0.5), (1, 0.1)]:
+        assert (O.rotated_cells(lev, w) == O.rotated_cells(lev, (w, w))).all()
+    assert O.rotated_cells(3, (0.4, 0.6)).all()
+    h = O.axis_spacing(2, math.radians(30), (0.0, 1 / 3), 0.25)
+    np.testing.assert_allclose(h[:6], np.exp(0.25j) / 9, rtol=1e-15)
+    np.testing.assert_allclose(h[6:], np.exp(1j * math.radians(30)) / 9, rtol=1e-15)
+
+
+@pytest.mark.parametrize("d,level", [(2, 2), (2, 3), (3, 2)])
+def test_operator_kronecker_general_scaling(d, level):
+    """Layer at the high face plus a rotated interior with a constant shift:
+    the oracle's operator equals the separable form built from textbook 1D
+    element matrices whose widths are taken straight from the definition
+    (centre above 2/3: h e^{i 30deg}, else h e^{i theta_I})."""
+    n = 3 ** level
+    th_l, th_i, k2 = math.radians(30), 0.4, 45.0
+    hs = np.array([np.exp(1j * (th_l if (i + 0.5) / n > 2 / 3 else th_i)) / n for i in range(n)])
+    K, M = tri_1d(hs)
+    H = -k2 * kron_all([M] * d)
+    for j in range(d):
+        H = H + kron_all([K if k == j else M for k in range(d)])
+    A, _, _ = dense_level(d, level, np.full((n + 1,) * d, k2), th_l, (0.0, 1 / 3), th_i)
+    np.testing.assert_allclose(A, H, rtol=0, atol=1e-13 * np.abs(H).max())
+
+
+@pytest.mark.parametrize("d,level", [(2, 3), (3, 2)])
+def test_sine_mode_eigenvalues_rotated_interior(d, level):
+    """No layer and an interior rotation theta: every cell has width
+    h e^{i theta}, so the Dirichlet sine modes are eigenvectors with the
+    closed-form eigenvalue of the uniformly scaled grid."""
+    n = 3 ** level
+    k2 = (3 * math.pi) ** 2
+    lev = O.Level(d, level, np.full((n + 1,) * d, k2), 1.2, 0.0, TH)
+    hc = (1 / n) * complex(math.cos(TH), math.sin(TH))
+    x = np.arange(n + 1) / n
+    for modes in [(1,) * d, (2, 5, 1)[:d]]:
+        s = np.ones((1,) * d)
+        for ax, m in enumerate(modes):
+            shape = [1] * d
+            shape[ax] = n + 1
+            s = s * np.sin(m * math.pi * x).reshape(shape)
+        kap = [(2 / hc) * (1 - math.cos(m * math.pi / n)) for m in modes]
+        mu = [(hc / 3) * (2 + math.cos(m * math.pi / n)) for m in modes]
+        lam = -k2 * np.prod(mu)
+        for j in range(d):
+            lam += kap[j] * np.prod([mu[k] for k in range(d) if k != j])
+        Hs = lev.apply(s.astype(np.complex128))
+        inner = (slice(1, -1),) * d
+        np.testing.assert_allclose(Hs[inner], lam * s[inner], rtol=1e-12, atol=1e-13 * abs(lam))
+
+
+def test_high_face_layer_is_mirror_of_low_face_layer():
+    """Reflecting x -> 1 - x and y -> 1 - y maps the operator with layers at
+    the high faces onto the one with layers at the low faces (varying shift
+    reflected too)."""
+    rng = np.random.default_rng(7)
+    n = 27
+    k2 = rng.uniform(-30, 90, size=(n + 1, n + 1))
+    u = rng.standard_normal((n + 1, n + 1)) + 1j * rng.standard_normal((n + 1, n + 1))
+    O.zero_boundary(u)
+    hi = O.Level(2, 3, k2, math.radians(30), (0.0, 1 / 3), 0.3)
+    lo = O.Level(2, 3, k2[::-1, ::-1], math.radians(30), (1 / 3, 0.0), 0.3)
+    np.testing.assert_allclose(hi.apply(u), lo.apply(u[::-1, ::-1])[::-1, ::-1], rtol=0, atol=1e-12)
+    assert np.abs(hi.apply(u) - lo.apply(u)).max() > 1e-3
+
+
+def _table2_golden():
+    path = os.path.join(os.path.dirname(__file__), "golden", "table2_regular.txt")
+    rows = {}
+    for line in open(path):
+        line = line.split("#")[0].split()
+        if line:
+            rows[int(line[0])] = [None if v == "div" else float(v) for v in line[1:]]
+    return rows
+
+
+def channel_inputs(theta_deg, depth=4):
+    """Eq. 08-gaussian sampled at the vertices of h = 3^-depth (written out
+    here, independent of the input generator module)."""
+    n = 3 ** depth
+    x = np.arange(n + 1) / n
+    X, Y = np.meshgrid(x, x)  # [y, x]
+    phi = 45.0 ** 2 + 135.0 ** 2 * (np.exp(-(15 * X) ** 2) + np.exp(-(15 * Y) ** 2))
+    chi = np.exp(-(125 * X) ** 2 - (125 * Y) ** 2)
+    return phi, chi
+
+
+def table2_reduction(theta_deg, solver, iters=50):
+    """Max-norm residual reduction of one Table 2 run (readings R1b and R6:
+    two-phase Jacobi at theta = 0, omega = 0.4 for every Jacobi with a
+    rotated interior, transition damping from 0.4, BPX with undamped coarse
+    corrections of 0.4)."""
+    phi, chi = channel_inputs(theta_deg)
+    H = O.Hierarchy(2, 4, phi, math.radians(30), (0.0, 1 / 3), math.radians(theta_deg))
+    H.set_rhs_nodal(chi)
+    r0 = H.residual_max()
+    w1 = 0.01 * (math.sqrt(3) - 1j)
+    for it in range(1, iters + 1):
+        if solver == "jacobi":
+            w = (w1 if it % 2 else -np.conj(w1)) if theta_deg == 0 else 0.4
+            H.cycle(O.omega_scheme(O.JACOBI, w, 4), O.ADD, O.DLINEAR)
+        elif solver == "transition":
+            H.cycle(O.omega_scheme(O.TRANSITION, 0.4, 4, iter_n=it), O.ADD, O.DLINEAR)
+        else:
+            H.cycle(O.omega_scheme(O.UCG, 0.4, 4), O.ADD, O.HIERARCHICAL)
+    return H.residual_max() / r0
+
+
+@pytest.mark.parametrize("theta_deg", [0, 18, 25, 35, 45])
+def test_table2_regular_column(theta_deg):
+    """Table 2, regular grid: every printed reduction is matched within a
+    factor of 2 and every divergence (bottom symbol) diverges here too.  The
+    setup leaves details open (cell shift, norm scaling), so the pin is an
+    order-of-magnitude one; a layer at the wrong faces or an interior that is
+    not rotated moves the entries by orders of magnitude or to divergence."""
+    paper = _table2_golden()[theta_deg]
+    for solver, ref in zip(["jacobi", "transition", "bpx"], paper):
+        got = table2_reduction(theta_deg, solver)
+        if ref is None:
+            assert not (got < 1.0), (solver, got)
+        else:
+            assert abs(math.log10(got / ref)) <= math.log10(2.0), (solver, got, ref)
