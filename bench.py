@@ -270,7 +270,6 @@ def measure_forms(mg, torch, peaks):
     configured indefinite problems diverge (interior theta = 0) and the plain
     cycle stalls where coarse cells straddle the layer edge, so times to 1e-8
     use the definite companions k^2 -> -k^2 (same shapes and bytes)."""
-    import oracle as O  # relaxation factors only (closed form)
     out = {}
     stream = torch.cuda.current_stream()
 
@@ -291,7 +290,7 @@ def measure_forms(mg, torch, peaks):
     s.close()
     # (A) 2D depth 6 definite companion
     c = W.definite(W.config2())
-    om = O.omega_scheme(O.EXP, 0.6, 6)
+    om = mg.omega_scheme(mg.MG_OMEGA_EXP, 0.6, 6)
     s = mg.Solver(2, 6, c["k2"], c["theta"], c["layer_width"])
     s.set_stream(stream.cuda_stream)
     s.set_rhs(c["f"])
@@ -310,7 +309,7 @@ def measure_forms(mg, torch, peaks):
     s.close()
     # (C) 3D depth 5 definite companion
     c = W.definite(W.config3())
-    om = O.omega_scheme(O.EXP, 0.6, 5)
+    om = mg.omega_scheme(mg.MG_OMEGA_EXP, 0.6, 5)
     s = mg.Solver(3, 5, c["k2"], c["theta"], c["layer_width"])
     s.set_stream(stream.cuda_stream)
     s.set_rhs(c["f"])
@@ -348,7 +347,7 @@ def measure_forms(mg, torch, peaks):
     bt.set_stream(stream.cuda_stream)
     for p, pr in enumerate(probs):
         bt.solvers[p].set_rhs(pr["f"])
-    oms = [O.omega_scheme(O.EXP, 0.6, pr["depth"]) for pr in probs]
+    oms = [mg.omega_scheme(mg.MG_OMEGA_EXP, 0.6, pr["depth"]) for pr in probs]
     tc, bp, ms = bt.autotune(mg.MG_ADD, oms, mg.MG_DLINEAR, INNER)
     (st, cyc, rel), dt = wall(lambda: bt.solve(mg.MG_ADD, oms, mg.MG_DLINEAR, 1e-8, 400, INNER))
     unknowns = sum((3 ** pr["depth"] - 1) ** 2 for pr in probs)
@@ -372,13 +371,12 @@ def measure_forms(mg, torch, peaks):
     bt.close()
     # (D) adjoint: forward + adjoint solve and gradients, 2D depth 6
     from paper_1508_03954_gb300.adjoint import SolveOptions, far_field
-    import oracle.adjoint as A
     c = W.config5()
     E = 0.0  # definite companion (k^2 = -V)
     s = mg.Solver(2, 6, E - c["V"], c["theta"], c["layer_width"])
     s.set_stream(stream.cuda_stream)
-    xyz, g = A.circle_samples(256)
-    opts = SolveOptions(variant=mg.MG_ADD, transfer=mg.MG_DLINEAR, omega=O.omega_scheme(O.EXP, 0.6, 6),
+    xyz, g = W.circle_samples(256)
+    opts = SolveOptions(variant=mg.MG_ADD, transfer=mg.MG_DLINEAR, omega=mg.omega_scheme(mg.MG_OMEGA_EXP, 0.6, 6),
                         tol=1e-10, max_cycles=20000, precision=mg.MG_C64_REFINE, inner_cycles=INNER)
     V = torch.from_numpy(c["V"]).cuda().requires_grad_(True)
     f = torch.from_numpy(np.real(c["f"])).cuda().requires_grad_(True)
@@ -394,6 +392,7 @@ def measure_forms(mg, torch, peaks):
     out["adjoint_2d_depth6"] = {"J": Jv, "seconds_forward_backward": dt, "tol": 1e-10}
     s.close()
     out["csg_sweep"] = csg_sweep(mg, torch)
+    out["channel_table2"] = channel_table2(mg, torch)
     return out
 
 
@@ -441,6 +440,47 @@ def csg_sweep(mg, torch, cycles=300):
             "runs": rows}
 
 
+def channel_table2(mg, torch, iters=50):
+    """The channel problem of Section 7.4 on h = 1/81 (Table 2, regular
+    grid): a 30 degree layer within 1/3 of the top and right faces, the
+    interior rotated by theta, varying phi and the Gaussian source chi of
+    Eq. 08-gaussian, u0 = 0, 50 iterations of pure Jacobi (two-phase factors
+    at theta = 0, 0.4 otherwise), the additive transition scheme (0.4) and BPX
+    (0.4).  Per run: the max-norm residual reduction and the device time per
+    iteration (CUDA events around the 50 cycles)."""
+    rows = []
+    t0 = time.perf_counter()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    for deg in (0, 18, 25, 35, 45):
+        c = W.channel(deg)
+        s = mg.Solver(2, c["depth"], c["k2"], c["theta"], c["layer_width"], c["theta_interior"])
+        s.set_stream(torch.cuda.current_stream().cuda_stream)
+        s.set_rhs(c["f"])
+        for solver in ("jacobi", "transition", "bpx"):
+            s.set_solution(np.zeros(s.shape, complex))
+            r0 = s.residual_max()
+            sched = []
+            for it in range(1, iters + 1):
+                if solver == "jacobi":
+                    w = (W.CHANNEL_OMEGA1 if it % 2 else W.CHANNEL_OMEGA2) if deg == 0 else 0.4
+                    sched.append((mg.omega_scheme(mg.MG_OMEGA_JACOBI, w, 4), mg.MG_ADD, mg.MG_DLINEAR))
+                elif solver == "transition":
+                    sched.append((mg.omega_scheme(mg.MG_OMEGA_TRANSITION, 0.4, 4, it), mg.MG_ADD, mg.MG_DLINEAR))
+                else:
+                    sched.append((mg.omega_scheme(mg.MG_OMEGA_UCG, 0.4, 4), mg.MG_ADD, mg.MG_HIERARCHICAL))
+            torch.cuda.synchronize()
+            ev[0].record()
+            for om, v, t in sched:
+                s.cycle(v, om, t)
+            ev[1].record()
+            torch.cuda.synchronize()
+            red = s.residual_max() / r0
+            rows.append({"theta_deg": deg, "solver": solver, "reduction_max_norm": float(red),
+                         "diverged": bool(not red < 1.0), "us_per_iteration": ev[0].elapsed_time(ev[1]) * 1e3 / iters})
+        s.close()
+    return {"iterations": iters, "depth": 4, "seconds": time.perf_counter() - t0, "runs": rows}
+
+
 # ---------------------------------------------------------------- main
 def main():
     ap = argparse.ArgumentParser()
@@ -451,6 +491,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--form", choices=["csg_sweep", "channel_table2"], default=None,
+                    help="run only this form and print its result (profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -474,6 +516,10 @@ def main():
     from paper_1508_03954_gb300 import mg
     B.build()
     mg.load()
+    if args.form is not None:
+        fn = {"csg_sweep": csg_sweep, "channel_table2": channel_table2}[args.form]
+        print(json.dumps({"form": args.form, "result": fn(mg, torch)}), flush=True)
+        return
 
     cfg = W.config2()
     d, depth = cfg["d"], cfg["depth"]

@@ -83,6 +83,23 @@ enum { MG_OMEGA_JACOBI = 0, MG_OMEGA_UCG = 1, MG_OMEGA_LGRID = 2, MG_OMEGA_EXP =
 int mg_create(int d, int depth, const double* k2_field, double theta,
               double layer_width, mg_ctx** out);
 
+/* Same as mg_create with a general coordinate-wise scaling (the channel
+ * problem of Section 7.4: a 30 degree layer at the two open faces and an
+ * interior rotation theta applied independently of it).  Along every axis a
+ * cell whose centre c satisfies c < width_lo or 1 - c < width_hi lies in the
+ * layer and has spacing h e^{i theta_layer}; every other cell has spacing
+ * h e^{i theta_interior}.  Layers that together cover the axis
+ * (width_lo + width_hi >= 1) rotate every cell.  mg_create(d, depth, k2,
+ * theta, w) is mg_create_ecs(d, depth, k2, theta, 0, w, w).
+ *  theta_layer, theta_interior   in [0, pi/2)
+ *  width_lo, width_hi            in [0, 1]
+ * A rotated interior makes every stencil row complex, so the fast kernels
+ * that take the interior rows as real are not used.
+ * Errors: as mg_create. */
+int mg_create_ecs(int d, int depth, const double* k2_field, double theta_layer,
+                  double theta_interior, double width_lo, double width_hi,
+                  mg_ctx** out);
+
 /* Releases every device buffer of the context (NULL is ignored). */
 void mg_destroy(mg_ctx* ctx);
 
@@ -114,6 +131,13 @@ int mg_cycle(mg_ctx* ctx, int variant, const mg_c128* omega_per_level, int trans
  * its ratio to the residual of the starting solution (Section 7 norms; on a
  * regular grid the h-weighted norm gives the same ratio).  Synchronising. */
 int mg_residual_norm(mg_ctx* ctx, double* abs_l2, double* rel_l2);
+
+/* Maximum modulus of the fine residual b - H u over the vertices (the max
+ * norm of the Section 7.4 table), computed on the device; a non-finite
+ * entry gives +infinity.  The first call allocates one fine-size complex128
+ * buffer.  Synchronises the stream.
+ * Errors: MG_ERR_INVALID (NULL), MG_ERR_OOM, MG_ERR_CUDA, MG_ERR_TIMEOUT. */
+int mg_residual_max(mg_ctx* ctx, double* abs_max);
 
 /* Residual norm of the iterate that entered the last complex128 cycle, as
  * fused into that cycle's finest-level sweep (no extra pass); rel_l2 is -1

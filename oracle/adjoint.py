@@ -25,13 +25,6 @@ import numpy as np
 from .helmholtz import Level, cells_per_axis
 
 
-def circle_samples(npts=256, radius=0.35, centre=(0.5, 0.5), m=2):
-    """Points x_q on a circle (x first) and weights g_q = e^{i m phi_q}."""
-    phi = 2.0 * math.pi * np.arange(npts) / npts
-    xy = np.stack([centre[0] + radius * np.cos(phi), centre[1] + radius * np.sin(phi)], axis=1)
-    return xy, np.exp(1j * m * phi)
-
-
 def sample_vector(d, depth, xyz, w):
     """a with s = a . u: a_v = sum_q w_q psi_v(x_q) over the vertex array
     (numpy axis order, last axis = x), d-linear nodal basis psi_v."""

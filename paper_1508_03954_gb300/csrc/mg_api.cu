@@ -35,6 +35,14 @@ constexpr int kMaxDepth3 = 6;  // (3^6+1)^3 vertices: 389 M
 constexpr int kThreads = 256;
 constexpr int kTC2 = 8;        // coarse cells per tile edge, 2D
 constexpr int kTC3 = 2;        // coarse cells per tile edge, 3D
+// 2D levels whose 8-cell tiles would not give every SM a block take 2-cell
+// tiles (a latency-bound level gains more from spreading than it loses to
+// the wider halo).
+inline int tc2_for(int n) {
+  const int t8 = (n / 3 + 1 + kTC2 - 1) / kTC2;
+  return t8 * t8 < 152 ? 2 : kTC2;
+}
+
 // resident blocks per SM of the persistent launches
 #ifndef MG_FINE_BPSM
 #define MG_FINE_BPSM 4
@@ -103,7 +111,7 @@ struct Hier {
   std::vector<ChainPlan> chains;
   double* partial = nullptr;
   unsigned* ticket = nullptr;
-  double* norm2 = nullptr;   // [0] cycle norm, [1] standalone norm
+  double* norm2 = nullptr;   // [0] cycle norm, [1] standalone norm, [2] max modulus (bits)
   std::vector<void*> allocs;
 };
 
@@ -111,7 +119,8 @@ struct Hier {
 
 struct mg_ctx {
   int d = 0, L = 0;
-  double theta = 0, w = 0;
+  double theta = 0, theta_in = 0;      // layer / interior rotation of the cell widths
+  double wlo = 0, whi = 0;             // layer widths at the low / high face of every axis
   cudaStream_t stream = 0;
   Hier<double> h64;
   Hier<float> h32;
@@ -121,6 +130,7 @@ struct mg_ctx {
   std::vector<double> k2;              // fine k^2 (host copy)
   cplx<double>* f_dev = nullptr;       // nodal f (fine)
   cplx<double>* scratch = nullptr;     // fine-size FP64 scratch
+  cplx<double>* rvec = nullptr;        // fine residual vector (allocated on first use)
   double* host_norm = nullptr;         // pinned
   std::string err;
   cudaStream_t cap_stream = nullptr;   // private stream the cycle graphs are captured on
@@ -161,28 +171,45 @@ int fail(mg_ctx* c, int code, const std::string& m) {
 
 // ------------------------------------------------------------------ geometry
 // Along one axis a cell of level l lies in the scaling layer when its centre
-// (i + 1/2)/n is closer than w to a face: min(2i+1, 2n-2i-1) < 2 w n
-// (integer form); w >= 0.5 scales every cell (complex scaled grid).
-std::vector<uint8_t> layer_flags(int n, double w) {
+// (i + 1/2)/n is closer than wlo to the low face or closer than whi to the
+// high face: 2i+1 < 2 wlo n or 2n-2i-1 < 2 whi n (integer form); layers that
+// cover the axis (wlo + whi >= 1) scale every cell (complex scaled grid).
+std::vector<uint8_t> layer_flags(int n, double wlo, double whi) {
   std::vector<uint8_t> rot(n);
   for (int i = 0; i < n; ++i) {
     long long a = 2LL * i + 1, b = 2LL * n - 2LL * i - 1;
-    rot[i] = (w >= 0.5) || ((double)std::min(a, b) < 2.0 * w * (double)n);
+    rot[i] = (wlo + whi >= 1.0) || ((double)a < 2.0 * wlo * (double)n) || ((double)b < 2.0 * whi * (double)n);
   }
   return rot;
 }
+
+std::vector<uint8_t> layer_flags(const mg_ctx* c, int n) { return layer_flags(n, c->wlo, c->whi); }
+
+// The two complex cell widths of a level with n cells per axis: h e^{i theta}
+// in the scaling layer, h e^{i theta_in} elsewhere (theta_in = 0 gives the
+// real h exactly).
+struct Widths {
+  cd in, rot;
+};
+Widths widths(const mg_ctx* c, int n) {
+  const double h = 1.0 / n;
+  return {h * cd(std::cos(c->theta_in), std::sin(c->theta_in)), h * cd(std::cos(c->theta), std::sin(c->theta))};
+}
+
+// The fast separable kernels (warp-strip 2D, z-marching 3D, fused 3D defect)
+// take the rows of cells outside the layer as real; a rotated interior makes
+// them complex and sends every level to the kernels with complex rows.
+bool interior_real(const mg_ctx* c) { return c->theta_in == 0.0; }
 
 // Stencil rows of the d-linear element operator for every vertex type.  A
 // vertex of type t has left/right cell widths hl, hr along each axis; its
 // assembled 1D stiffness row is (-1/hl, 1/hl + 1/hr, -1/hr) and its 1D mass
 // row (hl/6, (hl+hr)/3, hr/6).  The d-dimensional rows are the tensor
 // products K = sum_j (x)_a (K if a == j else M), M = (x)_a M (Section 3).
-void type_tables(int d, int n, double theta, std::vector<cd>& K, std::vector<cd>& M) {
-  const double h = 1.0 / n;
-  const cd hrot = h * cd(std::cos(theta), std::sin(theta));
+void type_tables(int d, const Widths& wd, std::vector<cd>& K, std::vector<cd>& M) {
   cd KX[4][3], MX[4][3];
   for (int t = 0; t < 4; ++t) {
-    cd hl = (t & 1) ? hrot : cd(h), hr = (t & 2) ? hrot : cd(h);
+    cd hl = (t & 1) ? wd.rot : wd.in, hr = (t & 2) ? wd.rot : wd.in;
     KX[t][0] = -1.0 / hl;
     KX[t][1] = 1.0 / hl + 1.0 / hr;
     KX[t][2] = -1.0 / hr;
@@ -215,43 +242,35 @@ void type_tables(int d, int n, double theta, std::vector<cd>& K, std::vector<cd>
 // mass (A = M) on the coarse indices of level l-1, with P1 the tripartite
 // interpolation (weights 1 - |o|/3).  Entry [C][0..2] is the coupling of
 // coarse C with C-1, C, C+1 (interior C only; the rest stays zero).
-void galerkin_rows_1d(int n, const std::vector<uint8_t>& rot, double theta,
+// The coarse hat of C rises by 1/3 per fine cell over the three cells
+// 3C-3..3C-1 (left, widths l0..l2) and falls by 1/3 over 3C..3C+2 (right,
+// r0..r2), so with the linear element integrals of each fine cell
+//   K: (-sum 1/l / 9, (sum 1/l + sum 1/r) / 9, -sum 1/r / 9)
+//   M: ((7 l0 + 13 l1 + 7 l2) / 54,
+//       (l0 + 7 l1 + 19 l2 + 19 r0 + 7 r1 + r2) / 27,
+//       (7 r0 + 13 r1 + 7 r2) / 54).
+// Written this way the stiffness row sums to zero up to one rounding per
+// entry (exactly, for real widths h = 3^-l), which keeps the rounding of
+// G u_{l-1} -- a sum that cancels to O(h^2) for smooth u -- near that of
+// the fine stencil.  Couplings to boundary neighbours are formed like the
+// others (they multiply Dirichlet zeros), so they do not split row classes.
+void galerkin_rows_1d(int n, const std::vector<uint8_t>& rot, const Widths& wd,
                       std::vector<std::array<cd, 6>>& rows) {
-  const double h = 1.0 / n;
-  const cd hrot = h * cd(std::cos(theta), std::sin(theta));
-  auto hw = [&](int cell) { return rot[cell] ? hrot : cd(h); };
-  auto Kf = [&](int f, int g) -> cd {
-    if (g == f) return 1.0 / hw(f - 1) + 1.0 / hw(f);
-    if (g == f - 1) return -1.0 / hw(f - 1);
-    return -1.0 / hw(f);
-  };
-  auto Mf = [&](int f, int g) -> cd {
-    if (g == f) return (hw(f - 1) + hw(f)) / 3.0;
-    if (g == f - 1) return hw(f - 1) / 6.0;
-    return hw(f) / 6.0;
-  };
-  auto P1 = [](int f, int c) -> double {
-    const int o = f - 3 * c;
-    return (o < -2 || o > 2) ? 0.0 : 1.0 - std::abs(o) / 3.0;
-  };
+  auto hw = [&](int cell) { return rot[cell] ? wd.rot : wd.in; };
   const int nc = n / 3;
   rows.assign(nc + 1, std::array<cd, 6>{});
-  // couplings to boundary neighbours are formed like the others (they
-  // multiply Dirichlet zeros), so they do not split row classes
-  for (int c = 1; c < nc; ++c)
-    for (int dl = -1; dl <= 1; ++dl) {
-      const int c2 = c + dl;
-      cd k(0), m(0);
-      for (int f = 3 * c - 2; f <= 3 * c + 2; ++f)
-        for (int g = f - 1; g <= f + 1; ++g) {
-          const double pf = P1(f, c), pg = P1(g, c2);
-          if (pf == 0.0 || pg == 0.0) continue;
-          k += pf * Kf(f, g) * pg;
-          m += pf * Mf(f, g) * pg;
-        }
-      rows[c][dl + 1] = k;
-      rows[c][dl + 4] = m;
-    }
+  for (int c = 1; c < nc; ++c) {
+    const cd l0 = hw(3 * c - 3), l1 = hw(3 * c - 2), l2 = hw(3 * c - 1);
+    const cd r0 = hw(3 * c), r1 = hw(3 * c + 1), r2 = hw(3 * c + 2);
+    const cd aL = 1.0 / l0 + 1.0 / l1 + 1.0 / l2, aR = 1.0 / r0 + 1.0 / r1 + 1.0 / r2;
+    auto& row = rows[c];
+    row[0] = -aL / 9.0;
+    row[1] = (aL + aR) / 9.0;
+    row[2] = -aR / 9.0;
+    row[3] = (7.0 * l0 + 13.0 * l1 + 7.0 * l2) / 54.0;
+    row[4] = (l0 + 7.0 * l1 + 19.0 * l2 + 19.0 * r0 + 7.0 * r1 + r2) / 27.0;
+    row[5] = (7.0 * r0 + 13.0 * r1 + 7.0 * r2) / 54.0;
+  }
 }
 
 template <typename R>
@@ -355,7 +374,8 @@ int build_hier(mg_ctx* c, Hier<R>& H) {
       return rc;
     }
     // vertex types
-    std::vector<uint8_t> rot = layer_flags(V.n, c->w), typ(V.n + 1);
+    std::vector<uint8_t> rot = layer_flags(c, V.n), typ(V.n + 1);
+    const Widths wd = widths(c, V.n);
     for (int i = 0; i <= V.n; ++i) {
       int left = rot[std::max(i - 1, 0)], right = rot[std::min(i, V.n - 1)];
       typ[i] = (uint8_t)(left + 2 * right);
@@ -363,7 +383,7 @@ int build_hier(mg_ctx* c, Hier<R>& H) {
     if ((rc = dalloc(c, H, (void**)&V.typ, typ.size())) != MG_OK) return rc;
     MG_CUDA(c, cudaMemcpy(V.typ, typ.data(), typ.size(), cudaMemcpyHostToDevice));
     std::vector<cd> K, M;
-    type_tables(d, V.n, c->theta, K, M);
+    type_tables(d, wd, K, M);
     std::vector<cd> Hh(K.size());
     for (size_t i = 0; i < K.size(); ++i) Hh[i] = H.varphi ? K[i] : K[i] - phi0 * M[i];
     const int NT = (int)ipow(4, d), NS = (int)ipow(3, d);
@@ -381,7 +401,7 @@ int build_hier(mg_ctx* c, Hier<R>& H) {
     }
     if (d == 3 && !H.varphi && l > 1) {
       std::vector<std::array<cd, 6>> rows;
-      galerkin_rows_1d(V.n, rot, c->theta, rows);
+      galerkin_rows_1d(V.n, rot, wd, rows);
       std::vector<std::array<cd, 6>> cls;
       std::vector<uint8_t> gt(rows.size(), 0);
       bool ok = true;
@@ -443,7 +463,7 @@ int build_hier(mg_ctx* c, Hier<R>& H) {
     if (d == 2 && !H.varphi && l > 1) {
       // classes of 1D Galerkin rows along an axis (same on both axes)
       std::vector<std::array<cd, 6>> rows;
-      galerkin_rows_1d(V.n, rot, c->theta, rows);
+      galerkin_rows_1d(V.n, rot, wd, rows);
       std::vector<std::array<cd, 6>> cls;
       std::vector<uint8_t> gt(rows.size(), 0);
       bool ok = true;
@@ -488,15 +508,13 @@ int build_hier(mg_ctx* c, Hier<R>& H) {
     }
     {
       // complex cell width per axis index (per-cell shift and adjoint kernels)
-      const double h = 1.0 / V.n;
-      const cd hrot = h * cd(std::cos(c->theta), std::sin(c->theta));
       std::vector<cd> hc(V.n);
-      for (int i = 0; i < V.n; ++i) hc[i] = rot[i] ? hrot : cd(h);
+      for (int i = 0; i < V.n; ++i) hc[i] = rot[i] ? wd.rot : wd.in;
       auto hcd = to_dev_type<R>(hc);
       if ((rc = dalloc(c, H, (void**)&V.hcell, hcd.size() * sizeof(cplx<R>))) != MG_OK) return rc;
       MG_CUDA(c, cudaMemcpy(V.hcell, hcd.data(), hcd.size() * sizeof(cplx<R>), cudaMemcpyHostToDevice));
     }
-    const int TC = d == 2 ? kTC2 : kTC3;
+    const int TC = d == 2 ? tc2_for(V.n) : kTC3;
     size_t nb = (size_t)ipow((V.n / 3 + 1 + TC - 1) / TC, d);
     max_blocks = std::max(max_blocks, nb);
   }
@@ -510,9 +528,8 @@ int build_hier(mg_ctx* c, Hier<R>& H) {
 }
 
 // ------------------------------------------------------------------ launches
-template <typename R, int D>
-cudaError_t launch_sweep(cudaStream_t s, mg::SweepArgs<R>& A) {
-  constexpr int TC = D == 2 ? kTC2 : kTC3;
+template <typename R, int D, int TC>
+cudaError_t launch_sweep_tc(cudaStream_t s, mg::SweepArgs<R>& A) {
   const int nc = A.n / 3;
   const int tiles = (nc + 1 + TC - 1) / TC;
   int nblk = 1;
@@ -523,6 +540,16 @@ cudaError_t launch_sweep(cudaStream_t s, mg::SweepArgs<R>& A) {
   auto kern = mg::sweep_kernel<R, D, TC, kThreads>;
   kern<<<nblk, kThreads, smem, s>>>(A);
   return cudaGetLastError();
+}
+
+template <typename R, int D>
+cudaError_t launch_sweep(cudaStream_t s, mg::SweepArgs<R>& A) {
+  if constexpr (D == 2) {
+    if (tc2_for(A.n) == 2) return launch_sweep_tc<R, 2, 2>(s, A);
+    return launch_sweep_tc<R, 2, kTC2>(s, A);
+  } else {
+    return launch_sweep_tc<R, D, kTC3>(s, A);
+  }
 }
 
 template <int TC, int NTHR, typename R>
@@ -724,6 +751,8 @@ int build_chain2(mg_ctx* c, Hier<R>& H, int s, int hb, int hier, const cplx<doub
     MG_CUDA(c, cudaMemcpy(cp.pr, pr.data(), pr.size() * sizeof(mg::ProlongArgs<R>), cudaMemcpyHostToDevice));
   cp.grid = std::max(1, std::min(cp.nitems, 152 * std::min(MG_CHAIN_BPSM, std::max(1, c->chain_bpsm))));
   if (H.chains.size() >= 32) {
+    // cached cycle graphs may launch the plan about to be freed
+    drop_graphs(H);
     cudaFree(H.chains.front().items);
     cudaFree(H.chains.front().s2);
     cudaFree(H.chains.front().pr);
@@ -792,6 +821,25 @@ cudaError_t launch_sweep3(cudaStream_t s, mg::Sweep3Args<R>& A) {
   return cudaGetLastError();
 }
 
+// 1D rows by axis class (left / right cell rotated): mass (hl/6, (hl+hr)/3,
+// hr/6), stiffness (-1/hl, 1/hl + 1/hr, -1/hr), stiffness - phi mass
+template <typename T>
+void axis_rows(const mg_ctx* c, int n, T row[4][9]) {
+  const double phi = c->k2[0];
+  const Widths wd = widths(c, n);
+  for (int t = 0; t < 4; ++t) {
+    const cd hl = (t & 1) ? wd.rot : wd.in, hr = (t & 2) ? wd.rot : wd.in;
+    const cd m[3] = {hl / 6.0, (hl + hr) / 3.0, hr / 6.0};
+    const cd k[3] = {-1.0 / hl, 1.0 / hl + 1.0 / hr, -1.0 / hr};
+    for (int j = 0; j < 3; ++j) {
+      const cd kp = k[j] - phi * m[j];
+      row[t][j] = T{(decltype(row[0][0].x))m[j].real(), (decltype(row[0][0].x))m[j].imag()};
+      row[t][3 + j] = T{(decltype(row[0][0].x))k[j].real(), (decltype(row[0][0].x))k[j].imag()};
+      row[t][6 + j] = T{(decltype(row[0][0].x))kp.real(), (decltype(row[0][0].x))kp.imag()};
+    }
+  }
+}
+
 // Large complex64 3D levels: the separable z-marching sweep, one block per SM
 // over equal ranges of (tile, coarse plane) units.
 cudaError_t launch_sweep3s(mg_ctx* c, Hier<float>& H, int l, bool fine, int hb, int hier, const cd& om) {
@@ -815,21 +863,7 @@ cudaError_t launch_sweep3s(mg_ctx* c, Hier<float>& H, int l, bool fine, int hb, 
   A.typ = V.typ;
   A.gtyp = V.gtyp;
   A.gcoef = V.gcoef;
-  // 1D rows by axis class (left / right cell rotated): mass (hl/6, (hl+hr)/3,
-  // hr/6), stiffness (-1/hl, 1/hl + 1/hr, -1/hr), stiffness - phi mass
-  const double h = 1.0 / V.n, phi = c->k2[0];
-  const cd hrot = h * cd(std::cos(c->theta), std::sin(c->theta));
-  for (int t = 0; t < 4; ++t) {
-    const cd hl = (t & 1) ? hrot : cd(h), hr = (t & 2) ? hrot : cd(h);
-    const cd m[3] = {hl / 6.0, (hl + hr) / 3.0, hr / 6.0};
-    const cd k[3] = {-1.0 / hl, 1.0 / hl + 1.0 / hr, -1.0 / hr};
-    for (int j = 0; j < 3; ++j) {
-      const cd kp = k[j] - phi * m[j];
-      A.row[t][j] = cplx<float>{(float)m[j].real(), (float)m[j].imag()};
-      A.row[t][3 + j] = cplx<float>{(float)k[j].real(), (float)k[j].imag()};
-      A.row[t][6 + j] = cplx<float>{(float)kp.real(), (float)kp.imag()};
-    }
-  }
+  axis_rows(c, V.n, A.row);
   for (size_t t = 0; t < V.diag.size() && t < 64; ++t) {
     const cd q = om / V.diag[t];
     A.omd[t] = cplx<float>{(float)q.real(), (float)q.imag()};
@@ -846,24 +880,6 @@ cudaError_t launch_sweep3s(mg_ctx* c, Hier<float>& H, int l, bool fine, int hb, 
   return cudaGetLastError();
 }
 
-// 1D rows by axis class (left / right cell rotated): mass (hl/6, (hl+hr)/3,
-// hr/6), stiffness (-1/hl, 1/hl + 1/hr, -1/hr), stiffness - phi mass
-template <typename T>
-void axis_rows(const mg_ctx* c, int n, T row[4][9]) {
-  const double h = 1.0 / n, phi = c->k2[0];
-  const cd hrot = h * cd(std::cos(c->theta), std::sin(c->theta));
-  for (int t = 0; t < 4; ++t) {
-    const cd hl = (t & 1) ? hrot : cd(h), hr = (t & 2) ? hrot : cd(h);
-    const cd m[3] = {hl / 6.0, (hl + hr) / 3.0, hr / 6.0};
-    const cd k[3] = {-1.0 / hl, 1.0 / hl + 1.0 / hr, -1.0 / hr};
-    for (int j = 0; j < 3; ++j) {
-      const cd kp = k[j] - phi * m[j];
-      row[t][j] = T{(decltype(row[0][0].x))m[j].real(), (decltype(row[0][0].x))m[j].imag()};
-      row[t][3 + j] = T{(decltype(row[0][0].x))k[j].real(), (decltype(row[0][0].x))k[j].imag()};
-      row[t][6 + j] = T{(decltype(row[0][0].x))kp.real(), (decltype(row[0][0].x))kp.imag()};
-    }
-  }
-}
 
 // Large complex64 2D levels: the warp-strip sweep.
 cudaError_t launch_sweep2w(mg_ctx* c, Hier<float>& H, int l, bool fine, int hb, int hier, const cd& om) {
@@ -905,7 +921,8 @@ cudaError_t launch_sweep2w(mg_ctx* c, Hier<float>& H, int l, bool fine, int hb, 
 template <typename R>
 cudaError_t sweep3(mg_ctx* c, Hier<R>& H, int l, bool fine, int hb, int hier, const cd& om) {
   if constexpr (std::is_same<R, float>::value) {
-    if (l > 1 && H.lev[l].n >= 27 && H.lev[l].g3ok) return launch_sweep3s(c, H, l, fine, hb, hier, om);
+    if (l > 1 && H.lev[l].n >= 27 && H.lev[l].g3ok && interior_real(c))
+      return launch_sweep3s(c, H, l, fine, hb, hier, om);
   }
   auto& V = H.lev[l];
   mg::Sweep3Args<R> A;
@@ -958,7 +975,7 @@ cudaError_t sweep(mg_ctx* c, Hier<R>& H, int l, bool fine, int s_active, int hb,
     return sweep3(c, H, l, fine, hb, hier, cd(w.x, w.y));
   }
   if constexpr (std::is_same<R, float>::value) {
-    if (c->d == 2 && !H.varphi && l > 1 && V.n >= 27 && V.gok) {
+    if (c->d == 2 && !H.varphi && l > 1 && V.n >= 27 && V.gok && interior_real(c)) {
       const cplx<double> w = omega[l - 1 + (H.L - s_active)];
       return launch_sweep2w(c, H, l, fine, hb, hier, cd(w.x, w.y));
     }
@@ -1063,8 +1080,8 @@ cudaError_t enqueue_cycle_part(mg_ctx* c, Hier<R>& H, int s, int hb, int hier,
 // Captures one part of the cycle as a graph on the private capture stream.
 template <typename R>
 cudaError_t capture_part(mg_ctx* c, Hier<R>& H, int s, int hb, int hier, const cplx<double>* omega,
-                         int part, cudaGraphExec_t* exec, int* nkern) {
-  *exec = nullptr;
+                         int part, cudaGraph_t* graph, int* nkern) {
+  *graph = nullptr;
   cudaStream_t user = c->stream;
   c->stream = c->cap_stream;
   const long long before = c->launches;
@@ -1076,14 +1093,30 @@ cudaError_t capture_part(mg_ctx* c, Hier<R>& H, int s, int hb, int hier, const c
   c->stream = user;
   c->launches = before;  // kernels count when the graph runs
   if (e == cudaSuccess) e = ek != cudaSuccess ? ek : ee;
-  if (e == cudaSuccess) e = cudaGraphInstantiate(exec, g, 0);
-  if (g) cudaGraphDestroy(g);
   if (e != cudaSuccess) {
-    if (*exec) cudaGraphExecDestroy(*exec);
-    *exec = nullptr;
+    if (g) cudaGraphDestroy(g);
     cudaGetLastError();
+    return e;
   }
-  return e;
+  *graph = g;
+  return cudaSuccess;
+}
+
+// An executable whole-cycle graph of the same stage, variant, transfer and
+// buffer parity whose factors differ, once four such graphs are cached:
+// alternating schedules keep their graphs, a schedule whose factors change
+// every cycle (transition damping) updates the oldest one in place.
+template <typename R>
+int reusable_graph(Hier<R>& H, const std::vector<double>& key) {
+  int first = -1, same = 0;
+  for (size_t i = 0; i < H.graphs.size(); ++i) {
+    const auto& g = H.graphs[i];
+    if (g.coarse == nullptr && std::equal(key.begin(), key.begin() + 5, g.key.begin())) {
+      if (first < 0) first = (int)i;
+      ++same;
+    }
+  }
+  return same >= 4 ? first : -1;
 }
 
 // One cycle on levels 1..s (s = active finest level).  The two parts run as
@@ -1131,15 +1164,44 @@ int run_cycle(mg_ctx* c, Hier<R>& H, int s, int hb, int hier, const cplx<double>
       }
       typename Hier<R>::GraphEntry ne;
       ne.key = key;
+      cudaGraph_t gf = nullptr, gc = nullptr;
       cudaError_t e;
       if (c->timing) {
-        e = capture_part(c, H, s, hb, hier, omega, 0, &ne.fine, &ne.nfine);
-        if (e == cudaSuccess && s > 1) e = capture_part(c, H, s, hb, hier, omega, 1, &ne.coarse, &ne.ncoarse);
+        e = capture_part(c, H, s, hb, hier, omega, 0, &gf, &ne.nfine);
+        if (e == cudaSuccess && s > 1) e = capture_part(c, H, s, hb, hier, omega, 1, &gc, &ne.ncoarse);
       } else {
-        e = capture_part(c, H, s, hb, hier, omega, 2, &ne.fine, &ne.nfine);  // whole cycle
+        e = capture_part(c, H, s, hb, hier, omega, 2, &gf, &ne.nfine);  // whole cycle
       }
-      if (e != cudaSuccess) {
+      const int reuse = (e == cudaSuccess && gc == nullptr) ? reusable_graph(H, key) : -1;
+      if (reuse >= 0) {
+        // same kernels with other arguments: update the executable in place;
+        // an executable whose update fails is dropped and a new one built
+        auto& old = H.graphs[reuse];
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(old.fine, gf, &info) == cudaSuccess) {
+          old.key = key;
+          old.nfine = ne.nfine;
+          // most recently used last: the next reuse takes the oldest
+          std::rotate(H.graphs.begin() + reuse, H.graphs.begin() + reuse + 1, H.graphs.end());
+          ge = &H.graphs.back();
+        } else {
+          cudaGetLastError();
+          cudaGraphExecDestroy(old.fine);
+          H.graphs.erase(H.graphs.begin() + reuse);
+        }
+      }
+      if (ge == nullptr && e == cudaSuccess) {
+        e = cudaGraphInstantiate(&ne.fine, gf, 0);
+        if (e == cudaSuccess && gc) e = cudaGraphInstantiate(&ne.coarse, gc, 0);
+      }
+      if (gf) cudaGraphDestroy(gf);
+      if (gc) cudaGraphDestroy(gc);
+      if (ge != nullptr) {
+        // updated in place
+      } else if (e != cudaSuccess) {
         if (ne.fine) cudaGraphExecDestroy(ne.fine);
+        if (ne.coarse) cudaGraphExecDestroy(ne.coarse);
+        cudaGetLastError();
         c->use_graphs = false;  // run this context's cycles as plain launches
       } else {
         if (H.graphs.size() >= 32) {
@@ -1223,7 +1285,7 @@ int defect3_costs(mg_ctx* c, Hier<double>& H, int l) {
   auto& V = H.lev[l];
   if (V.d3pref != nullptr) return MG_OK;
   const int n = V.n, nc = n / 3;
-  std::vector<uint8_t> rot = layer_flags(n, c->w), typ(n + 1);
+  std::vector<uint8_t> rot = layer_flags(c, n), typ(n + 1);
   for (int i = 0; i <= n; ++i) typ[i] = (uint8_t)(rot[std::max(i - 1, 0)] + 2 * rot[std::min(i, n - 1)]);
   const int tx_n = (n + 1 + 29) / 30, ty_n = (n + 1 + 13) / 14;
   std::vector<unsigned> pref((size_t)tx_n * ty_n * nc + 1, 0u);
@@ -1268,19 +1330,7 @@ cudaError_t defect3(mg_ctx* c, int l, const cplx<double>* u, const cplx<RC>* e, 
   A.u_out = u_out;
   A.r32 = r32;
   A.typ = V.typ;
-  const double h = 1.0 / V.n, phi = c->k2[0];
-  const cd hrot = h * cd(std::cos(c->theta), std::sin(c->theta));
-  for (int t = 0; t < 4; ++t) {
-    const cd hl = (t & 1) ? hrot : cd(h), hr = (t & 2) ? hrot : cd(h);
-    const cd m[3] = {hl / 6.0, (hl + hr) / 3.0, hr / 6.0};
-    const cd k[3] = {-1.0 / hl, 1.0 / hl + 1.0 / hr, -1.0 / hr};
-    for (int j = 0; j < 3; ++j) {
-      const cd kp = k[j] - phi * m[j];
-      A.row[t][j] = cplx<double>{m[j].real(), m[j].imag()};
-      A.row[t][3 + j] = cplx<double>{k[j].real(), k[j].imag()};
-      A.row[t][6 + j] = cplx<double>{kp.real(), kp.imag()};
-    }
-  }
+  axis_rows(c, V.n, A.row);
   A.partial = H.partial;
   A.ticket = H.ticket + 3;
   A.norm2 = slot >= 0 ? H.norm2 + slot : nullptr;
@@ -1290,7 +1340,7 @@ cudaError_t defect3(mg_ctx* c, int l, const cplx<double>* u, const cplx<RC>* e, 
   return cudaGetLastError();
 }
 
-bool use_defect3(const mg_ctx* c) { return c->d == 3 && !c->h64.varphi && c->L >= 1; }
+bool use_defect3(const mg_ctx* c) { return c->d == 3 && !c->h64.varphi && c->L >= 1 && interior_real(c); }
 
 // The pending correction corr_{s-1} is the only coarse array a cycle reads
 // before writing it (the fine sweep forms u = U + P corr_{s-1}; every t_l and
@@ -1375,15 +1425,28 @@ extern "C" {
 int mg_create(int d, int depth, const double* k2_field, double theta, double layer_width,
               mg_ctx** out) {
   g_create_err.clear();
+  if (!(layer_width >= 0.0 && layer_width <= 0.5)) {
+    if (out != nullptr) *out = nullptr;
+    return fail(nullptr, MG_ERR_INVALID, "layer_width must be in [0, 0.5]");
+  }
+  return mg_create_ecs(d, depth, k2_field, theta, 0.0, layer_width, layer_width, out);
+}
+
+int mg_create_ecs(int d, int depth, const double* k2_field, double theta_layer, double theta_interior,
+                  double width_lo, double width_hi, mg_ctx** out) {
+  g_create_err.clear();
   if (out == nullptr) return fail(nullptr, MG_ERR_INVALID, "out is NULL");
   *out = nullptr;
   if (d != 2 && d != 3) return fail(nullptr, MG_ERR_INVALID, "d must be 2 or 3");
   if (depth < 1 || depth > (d == 2 ? kMaxDepth2 : kMaxDepth3))
     return fail(nullptr, MG_ERR_INVALID, "depth out of range");
   if (k2_field == nullptr) return fail(nullptr, MG_ERR_INVALID, "k2_field is NULL");
-  if (!(theta >= 0.0 && theta < M_PI / 2)) return fail(nullptr, MG_ERR_INVALID, "theta must be in [0, pi/2)");
-  if (!(layer_width >= 0.0 && layer_width <= 0.5))
-    return fail(nullptr, MG_ERR_INVALID, "layer_width must be in [0, 0.5]");
+  if (!(theta_layer >= 0.0 && theta_layer < M_PI / 2))
+    return fail(nullptr, MG_ERR_INVALID, "theta must be in [0, pi/2)");
+  if (!(theta_interior >= 0.0 && theta_interior < M_PI / 2))
+    return fail(nullptr, MG_ERR_INVALID, "theta_interior must be in [0, pi/2)");
+  if (!(width_lo >= 0.0 && width_lo <= 1.0 && width_hi >= 0.0 && width_hi <= 1.0))
+    return fail(nullptr, MG_ERR_INVALID, "layer widths must be in [0, 1]");
   const size_t nvf = (size_t)ipow(ipow(3, depth) + 1, d);
   for (size_t i = 0; i < nvf; ++i)
     if (!std::isfinite(k2_field[i])) return fail(nullptr, MG_ERR_INVALID, "k2_field holds a non-finite value");
@@ -1398,8 +1461,10 @@ int mg_create(int d, int depth, const double* k2_field, double theta, double lay
   if (c == nullptr) return fail(nullptr, MG_ERR_OOM, "host allocation failed");
   c->d = d;
   c->L = depth;
-  c->theta = theta;
-  c->w = layer_width;
+  c->theta = theta_layer;
+  c->theta_in = theta_interior;
+  c->wlo = width_lo;
+  c->whi = width_hi;
   c->k2.assign(k2_field, k2_field + nvf);
   int rc = build_hier<double>(c, c->h64);
   if (rc == MG_OK) {
@@ -1438,6 +1503,7 @@ void mg_destroy(mg_ctx* c) {
   free_hier(c->h32);
   if (c->f_dev) cudaFree(c->f_dev);
   if (c->scratch) cudaFree(c->scratch);
+  if (c->rvec) cudaFree(c->rvec);
   if (c->host_norm) cudaFreeHost(c->host_norm);
   delete c;
 }
@@ -1525,6 +1591,25 @@ int mg_residual_norm(mg_ctx* c, double* abs_l2, double* rel_l2) {
   if (abs_l2) *abs_l2 = r;
   if (rel_l2) *rel_l2 = c->r0 > 0 ? r / c->r0 : 0.0;
   return MG_OK;
+}
+
+int mg_residual_max(mg_ctx* c, double* abs_max) {
+  if (check_ctx(c)) return MG_ERR_INVALID;
+  if (abs_max == nullptr) return fail(c, MG_ERR_INVALID, "abs_max is NULL");
+  auto& H = c->h64;
+  auto& V = H.lev[c->L];
+  if (c->rvec == nullptr) MG_CUDA(c, cudaMalloc(&c->rvec, V.nv * sizeof(cplx<double>)));
+  unsigned long long* mx = reinterpret_cast<unsigned long long*>(H.norm2 + 2);
+  MG_CUDA(c, materialize(c, H, c->L, c->scratch));
+  MG_CUDA(c, (stencil<double, double>(c, H, c->L, 1, c->scratch, V.b, V.coefH, true, c->rvec, -1)));
+  MG_CUDA(c, cudaMemsetAsync(mx, 0, sizeof(unsigned long long), c->stream));
+  ++c->launches;
+  mg::max_abs_kernel<<<grid_for(V.nv), kThreads, 0, c->stream>>>(c->rvec, (long long)V.nv, mx);
+  MG_CUDA(c, cudaGetLastError());
+  MG_CUDA(c, cudaMemcpyAsync(c->host_norm, mx, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  MG_CUDA(c, cudaStreamSynchronize(c->stream));
+  *abs_max = *c->host_norm;
+  return check_timeout(c);
 }
 
 int mg_set_precision(mg_ctx* c, int precision, int inner_cycles) {

@@ -25,8 +25,8 @@ STATUS_NAMES = {0: "MG_OK", 1: "MG_ERR_INVALID", 2: "MG_ERR_CUDA", 3: "MG_ERR_OO
                 4: "MG_DIVERGED", 5: "MG_NOT_CONVERGED", 6: "MG_ERR_TIMEOUT"}
 
 # every symbol include/mg.h declares
-EXPORTS = ["mg_create", "mg_destroy", "mg_set_stream", "mg_set_rhs", "mg_set_solution",
-           "mg_get_solution", "mg_cycle", "mg_residual_norm", "mg_last_cycle_norm", "mg_solve", "mg_set_precision",
+EXPORTS = ["mg_create", "mg_create_ecs", "mg_destroy", "mg_set_stream", "mg_set_rhs", "mg_set_solution",
+           "mg_get_solution", "mg_cycle", "mg_residual_norm", "mg_residual_max", "mg_last_cycle_norm", "mg_solve", "mg_set_precision",
            "mg_fmg", "mg_omega_scheme", "mg_get_level", "mg_set_timing", "mg_get_stats",
            "mg_set_trace", "mg_get_trace", "mg_set_spin_limit", "mg_debug_unsatisfiable_wait", "mg_set_k2", "mg_set_rhs_vector", "mg_sample",
            "mg_set_rhs_samples", "mg_adjoint_grad", "mg_residual_noalloc", "mg_batch_create",
@@ -65,6 +65,7 @@ def load(path: str | None = None):
     pc = ctypes.POINTER(MgC128)
     sig = {
         "mg_create": (ip, [ip, ip, ctypes.POINTER(dp), dp, dp, ctypes.POINTER(vp)]),
+        "mg_create_ecs": (ip, [ip, ip, ctypes.POINTER(dp), dp, dp, dp, dp, ctypes.POINTER(vp)]),
         "mg_destroy": (None, [vp]),
         "mg_set_stream": (ip, [vp, vp]),
         "mg_set_rhs": (ip, [vp, vp, ip]),
@@ -73,6 +74,7 @@ def load(path: str | None = None):
         "mg_cycle": (ip, [vp, ip, pc, ip]),
         "mg_residual_norm": (ip, [vp, ctypes.POINTER(dp), ctypes.POINTER(dp)]),
         "mg_last_cycle_norm": (ip, [vp, ctypes.POINTER(dp), ctypes.POINTER(dp)]),
+        "mg_residual_max": (ip, [vp, ctypes.POINTER(dp)]),
         "mg_solve": (ip, [vp, ip, pc, ip, dp, ip, ctypes.POINTER(ip), ctypes.POINTER(dp)]),
         "mg_set_precision": (ip, [vp, ip, ip]),
         "mg_fmg": (ip, [vp, ip, pc, ip, ip]),
@@ -162,7 +164,10 @@ class Solver:
         self._L = load()
         return self
 
-    def __init__(self, d, depth, k2_field, theta, layer_width):
+    def __init__(self, d, depth, k2_field, theta, layer_width, theta_interior=0.0):
+        """layer_width: w (a layer of width w at both faces of every axis,
+        mg_create) or a pair (w_lo, w_hi) of one-sided widths; with a pair or
+        a nonzero theta_interior the context comes from mg_create_ecs."""
         L = load()
         self.d, self.depth = d, depth
         self.n = 3 ** depth
@@ -172,8 +177,13 @@ class Solver:
         if k2.size != self.nv:
             raise ValueError(f"k2_field needs {self.nv} values")
         h = ctypes.c_void_p()
-        rc = L.mg_create(d, depth, k2.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                         float(theta), float(layer_width), ctypes.byref(h))
+        kp = k2.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        if np.ndim(layer_width) == 0 and theta_interior == 0.0:
+            rc = L.mg_create(d, depth, kp, float(theta), float(layer_width), ctypes.byref(h))
+        else:
+            lo, hi = (layer_width, layer_width) if np.ndim(layer_width) == 0 else layer_width
+            rc = L.mg_create_ecs(d, depth, kp, float(theta), float(theta_interior), float(lo), float(hi),
+                                 ctypes.byref(h))
         if rc != MG_OK:
             raise MgError(rc, L.mg_last_error(None).decode())
         self._h = h
@@ -232,6 +242,12 @@ class Solver:
         self._check(self._L.mg_residual_norm(self._view, ctypes.byref(a), ctypes.byref(r)),
                     "mg_residual_norm")
         return a.value, r.value
+
+    def residual_max(self):
+        """Maximum modulus of the fine residual (mg_residual_max)."""
+        a = ctypes.c_double()
+        self._check(self._L.mg_residual_max(self._view, ctypes.byref(a)), "mg_residual_max")
+        return a.value
 
     def last_cycle_norm(self):
         a, r = ctypes.c_double(), ctypes.c_double()

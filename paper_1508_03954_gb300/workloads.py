@@ -120,6 +120,14 @@ def definite(cfg):
     return out
 
 
+def circle_samples(npts=256, radius=0.35, centre=(0.5, 0.5), m=2):
+    """Sample points x_q on a circle (x first) and weights g_q = e^{i m phi_q}
+    of the far-field functional of the adjoint form."""
+    phi = 2.0 * math.pi * np.arange(npts) / npts
+    xy = np.stack([centre[0] + radius * np.cos(phi), centre[1] + radius * np.sin(phi)], axis=1)
+    return xy, np.exp(1j * m * phi)
+
+
 CHANNEL_OMEGA1 = 0.01 * (math.sqrt(3.0) - 1j)    # two-phase Jacobi factors (Section 7.4)
 CHANNEL_OMEGA2 = -CHANNEL_OMEGA1.conjugate()
 

@@ -43,7 +43,7 @@ def test_gradient_kernel_matches_dense_adjoint():
     c = W.config5(depth=3)
     E, V, th, w = c["E"], c["V"], c["theta"], c["layer_width"]
     f = np.real(c["f"])
-    xyz, g = A.circle_samples(256)
+    xyz, g = W.circle_samples(256)
     G = A.adjoint_gradients(2, 3, E, V, th, w, f, xyz, g)
     s = mg.Solver(2, 3, E - V, th, w)
     u = torch.from_numpy(G["u"].reshape(-1)).cuda()
@@ -67,7 +67,7 @@ def test_end_to_end_gradients_match_dense_adjoint_depth3():
     E = 0.0  # definite companion
     V0, th, w = c["V"], c["theta"], c["layer_width"]
     f0 = np.real(c["f"])
-    xyz, g = A.circle_samples(256)
+    xyz, g = W.circle_samples(256)
     G = A.adjoint_gradients(2, 3, E, V0, th, w, f0, xyz, g)
     s = mg.Solver(2, 3, E - V0, th, w)
     s.set_stream(torch.cuda.current_stream().cuda_stream)
@@ -90,7 +90,7 @@ def test_full_size_gradients_match_directional_differences():
     E = 0.0
     V0, th, w = c["V"], c["theta"], c["layer_width"]
     f0 = np.real(c["f"])
-    xyz, g = A.circle_samples(256)
+    xyz, g = W.circle_samples(256)
     s = mg.Solver(2, 6, E - V0, th, w)
     s.set_stream(torch.cuda.current_stream().cuda_stream)
     opts = _opts(6)

@@ -10,6 +10,7 @@ import pytest
 
 import oracle.adjoint as A
 import oracle as O
+from paper_1508_03954_gb300 import workloads as W
 
 
 def _setup(d, depth, seed):
@@ -18,9 +19,9 @@ def _setup(d, depth, seed):
     V = rng.uniform(0.0, 10.0, size=(n + 1,) * d)
     f = rng.uniform(-1.0, 1.0, size=(n + 1,) * d)
     if d == 2:
-        xyz, g = A.circle_samples(64)
+        xyz, g = W.circle_samples(64)
     else:
-        xyz2, g = A.circle_samples(32)
+        xyz2, g = W.circle_samples(32)
         xyz = np.concatenate([xyz2, np.full((len(g), 1), 0.45)], axis=1)
     return V, f, xyz, g
 
@@ -55,7 +56,7 @@ def test_sample_vector_reproduces_interpolation_of_linear_fields():
     Y, X = np.meshgrid(x, x, indexing="ij")
     u = (2 * X - 3 * Y + 5 * X * Y).astype(complex)
     O.zero_boundary(u)
-    xyz, g = A.circle_samples(40, radius=0.3)
+    xyz, g = W.circle_samples(40, radius=0.3)
     a = A.sample_vector(d, depth, xyz, g)
     exact = np.sum(g * (2 * xyz[:, 0] - 3 * xyz[:, 1] + 5 * xyz[:, 0] * xyz[:, 1]))
     assert abs(np.sum(a * u) - exact) <= 1e-12 * abs(exact)
