@@ -23,6 +23,7 @@
 #include "mg_sweep2w.cuh"
 #include "mg_persist.cuh"
 #include "mg_adjoint.cuh"
+#include "mg_maxnorm.cuh"
 #include <map>
 
 using mg::cplx;
