@@ -540,3 +540,120 @@ def test_table2_regular_column(theta_deg):
             assert not (got < 1.0), (solver, got)
         else:
             assert abs(math.log10(got / ref)) <= math.log10(2.0), (solver, got, ref)
+
+
+# ---------------------------------------------------------------- four dimensions (Section 7.1, p = 4)
+def _sparse_kron_all(mats):
+    import scipy.sparse as sp
+    out = sp.csr_matrix(mats[0])
+    for m in mats[1:]:
+        out = sp.kron(out, sp.csr_matrix(m), format="csr")
+    return out
+
+
+def _sparse_operator(d, level, theta, w, k2, theta_interior=0.0):
+    hs = O.axis_spacing(level, theta, w, theta_interior)
+    K, M = tri_1d(hs)
+    H = -k2 * _sparse_kron_all([M] * d)
+    for j in range(d):
+        H = H + _sparse_kron_all([K if k == j else M for k in range(d)])
+    return H
+
+
+def _inner(x, d):
+    return x[(slice(1, -1),) * d].reshape(-1)
+
+
+@pytest.mark.parametrize("level,w", [(1, 0.2), (2, 0.2), (2, 0.5)])
+def test_operator_4d_equals_kronecker_of_1d_elements(level, w):
+    """d = 4: the oracle's cell-by-cell operator applied to random vectors
+    equals the separable Kronecker form of textbook 1D element matrices."""
+    n = 3 ** level
+    k2 = 17.0
+    lev = O.Level(4, level, np.full((n + 1,) * 4, k2), TH, w)
+    H = _sparse_operator(4, level, TH, w, k2)
+    rng = np.random.default_rng(level)
+    for _ in range(2):
+        u = rng.standard_normal((n + 1,) * 4) + 1j * rng.standard_normal((n + 1,) * 4)
+        O.zero_boundary(u)
+        ref = H @ _inner(u, 4)
+        np.testing.assert_allclose(_inner(lev.apply(u), 4), ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+
+
+def test_sine_mode_eigenvalues_4d():
+    """d = 4, every cell rotated: Dirichlet sine modes are eigenvectors with
+    the closed-form eigenvalue sum_j kappa_j prod_{k != j} mu_k - k^2 prod mu."""
+    n, d = 9, 4
+    k2 = (2 * math.pi) ** 2
+    lev = O.Level(d, 2, np.full((n + 1,) * d, k2), TH, 0.5)
+    hc = (1 / n) * complex(math.cos(TH), math.sin(TH))
+    x = np.arange(n + 1) / n
+    for modes in [(1, 1, 1, 1), (2, 1, 3, 8)]:
+        s = np.ones((1,) * d)
+        for ax, m in enumerate(modes):
+            shape = [1] * d
+            shape[ax] = n + 1
+            s = s * np.sin(m * math.pi * x).reshape(shape)
+        kap = [(2 / hc) * (1 - math.cos(m * math.pi / n)) for m in modes]
+        mu = [(hc / 3) * (2 + math.cos(m * math.pi / n)) for m in modes]
+        lam = -k2 * np.prod(mu)
+        for j in range(d):
+            lam += kap[j] * np.prod([mu[k] for k in range(d) if k != j])
+        Hs = lev.apply(s.astype(np.complex128))
+        inner = (slice(1, -1),) * d
+        np.testing.assert_allclose(Hs[inner], lam * s[inner], rtol=1e-12, atol=1e-13 * abs(lam))
+
+
+@pytest.mark.parametrize("variant,transfer", [(O.ADD, O.DLINEAR), (O.HB, O.DLINEAR), (O.ADD, O.HIERARCHICAL)])
+def test_fas_cycle_4d_equals_additive_correction_scheme(variant, transfer):
+    """d = 4, depth 2: Lemma 2 / Theorem 2 with sparse Kronecker operators and
+    interpolation, as in the 2D/3D pin."""
+    d, depth, k2 = 4, 2, 25.0
+    Hh = _problem(d, depth, k2, TH, 0.5)
+    omega = np.array([0.55 + 0.05j, 0.6])
+    Hs = {lev: _sparse_operator(d, lev, TH, 0.5, k2) for lev in (1, 2)}
+    P = _sparse_kron_all([interp_1d(3)] * d)
+    u = _inner(Hh.u, d)
+    b = _inner(Hh.b, d)
+    r = b - Hs[2] @ u
+    corr = np.zeros_like(u)
+    for lev in (2, 1):
+        rl = r if lev == 2 else P.T @ r
+        du = omega[lev - 1] * rl / Hs[lev].diagonal()
+        idx = list(itertools.product(range(1, 3 ** lev), repeat=d))
+        cp = np.array([all(i % 3 == 0 for i in t) for t in idx])
+        if variant == O.HB:
+            du = np.where(cp, 0, du)
+        if transfer == O.HIERARCHICAL and lev > 1:
+            du = du - P @ du[cp]
+        if lev == 1:
+            du = P @ du
+        corr += du
+    Hh.cycle(omega, variant, transfer)
+    got = _inner(Hh.u, d)
+    np.testing.assert_allclose(got, u + corr, rtol=0, atol=1e-12 * np.abs(u + corr).max())
+
+
+def test_poisson_analytic_discrete_solution_4d():
+    """Section 7.1 in four dimensions: rhs 4 pi^2 prod sin(pi x_i), phi = 0;
+    the discrete solution pi^2 (mu/kappa) prod sin(pi x_i) makes the
+    residual vanish and the cycle converges to it."""
+    d, depth = 4, 2
+    n = 3 ** depth
+    h = 1 / n
+    x = np.arange(n + 1) / n
+    s = np.ones((1,) * d)
+    for ax in range(d):
+        shape = [1] * d
+        shape[ax] = n + 1
+        s = s * np.sin(math.pi * x).reshape(shape)
+    H = O.Hierarchy(d, depth, np.zeros((n + 1,) * d), 0.0, 0.0)
+    H.set_rhs_nodal(d * math.pi ** 2 * s)
+    kap = (2 / h) * (1 - math.cos(math.pi * h))
+    mu = (h / 3) * (2 + math.cos(math.pi * h))
+    exact = math.pi ** 2 * (mu / kap) * s
+    np.testing.assert_allclose(H.residual(exact.astype(complex)), 0, atol=1e-12)
+    om = O.omega_scheme(O.EXP, 0.8, depth)
+    for _ in range(60):
+        H.cycle(om, O.ADD, O.DLINEAR)
+    np.testing.assert_allclose(H.u.real, exact, rtol=0, atol=1e-8)
