@@ -24,6 +24,7 @@
 #include "mg_persist.cuh"
 #include "mg_adjoint.cuh"
 #include "mg_maxnorm.cuh"
+#include "mg_dim4.cuh"
 #include <map>
 
 using mg::cplx;
@@ -33,6 +34,7 @@ namespace {
 
 constexpr int kMaxDepth2 = 9;  // (3^9+1)^2 vertices: 387 M
 constexpr int kMaxDepth3 = 6;  // (3^6+1)^3 vertices: 389 M
+constexpr int kMaxDepth4 = 4;  // (3^4+1)^4 vertices: 45 M (five fine-size temporaries)
 constexpr int kThreads = 256;
 constexpr int kTC2 = 8;        // coarse cells per tile edge, 2D
 constexpr int kTC3 = 2;        // coarse cells per tile edge, 3D
@@ -116,6 +118,34 @@ struct Hier {
   std::vector<void*> allocs;
 };
 
+// Four-dimensional hierarchy (mg_dim4.cuh): per level the solution (coarse:
+// the injected copy), b, T du, the correction, and the separable operator
+// as per-index 1D rows; fine-size temporaries for the pass chains.
+struct Lev4 {
+  int n = 0;
+  size_t nv = 0;
+  cplx<double>* u = nullptr;
+  cplx<double>* b = nullptr;
+  cplx<double>* t = nullptr;
+  cplx<double>* corr = nullptr;  // level 1: aliases t
+  uint8_t* typ = nullptr;        // vertex type per axis index
+  cplx<double>* rows = nullptr;  // [M, K, K - phi M][n + 1][3] of this level's operator
+  cplx<double>* grows = nullptr; // same for G = R H P on level l - 1 (l > 1)
+  cplx<double>* invd = nullptr;  // [256] inverse diagonal by vertex type
+};
+
+struct Hier4 {
+  std::vector<Lev4> lev;      // 1..L
+  cplx<double>* T[5] = {};    // fine-size temporaries; T[4] holds the residual
+  double* partial = nullptr;  // block partials of the norms
+  unsigned* ticket = nullptr;
+  double* norm2 = nullptr;    // [0] cycle norm, [1] standalone norm
+  std::vector<void*> allocs;
+  cudaGraphExec_t exec = nullptr;  // the last captured cycle
+  std::vector<double> key;
+  long long nkern = 0;
+};
+
 }  // namespace
 
 struct mg_ctx {
@@ -125,6 +155,7 @@ struct mg_ctx {
   cudaStream_t stream = 0;
   Hier<double> h64;
   Hier<float> h32;
+  Hier4* h4 = nullptr;                 // d = 4
   int precision = MG_C128;
   int inner_cycles = 4;
   double r0 = -1.0;                    // reference residual norm
@@ -1379,7 +1410,18 @@ int check_timeout(mg_ctx* c) {
 
 // ||b_s - H_s u_s|| of the materialised fine solution of level s (FP64),
 // synchronising.
+cudaError_t d4_residual(mg_ctx* c, int slot);
+
 int fine_residual(mg_ctx* c, int s, double* out) {
+  if (c->d == 4) {
+    cudaError_t e4 = d4_residual(c, 1);
+    if (e4 == cudaSuccess)
+      e4 = cudaMemcpyAsync(c->host_norm, c->h4->norm2 + 1, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e4 == cudaSuccess) e4 = cudaStreamSynchronize(c->stream);
+    if (e4 != cudaSuccess) return fail(c, MG_ERR_CUDA, std::string("residual: ") + cudaGetErrorString(e4));
+    *out = std::sqrt(*c->host_norm);
+    return MG_OK;
+  }
   auto& H = c->h64;
   cudaError_t e;
   if (use_defect3(c)) {
@@ -1418,6 +1460,337 @@ int set_level_rhs(mg_ctx* c, int s) {
   return MG_OK;
 }
 
+// ------------------------------------------------------------------ d = 4
+int d4_alloc(mg_ctx* c, Hier4& H, void** p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return fail(c, e == cudaErrorMemoryAllocation ? MG_ERR_OOM : MG_ERR_CUDA,
+                std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  H.allocs.push_back(*p);
+  MG_CUDA(c, cudaMemset(*p, 0, bytes));
+  return MG_OK;
+}
+
+void d4_free(Hier4* H) {
+  if (H == nullptr) return;
+  if (H->exec) cudaGraphExecDestroy(H->exec);
+  for (void* p : H->allocs) cudaFree(p);
+  delete H;
+}
+
+template <typename T>
+int d4_upload(mg_ctx* c, Hier4& H, T** dst, const std::vector<T>& v) {
+  int rc = d4_alloc(c, H, (void**)dst, v.size() * sizeof(T));
+  if (rc != MG_OK) return rc;
+  MG_CUDA(c, cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return MG_OK;
+}
+
+// Per-level arrays and the separable operator tables: the rows of each axis
+// index are those of its vertex type (left / right cell in the layer), the
+// Galerkin rows those of galerkin_rows_1d, the diagonal of vertex type
+// (t0, t1, t2, t3) is sum_j prod_a (K if a == j else M)[t_a] centre entries
+// minus phi prod_a M[t_a] centre (the tensor-product form of Section 3).
+int d4_build(mg_ctx* c) {
+  Hier4* H = new (std::nothrow) Hier4();
+  if (H == nullptr) return fail(c, MG_ERR_OOM, "host allocation failed");
+  c->h4 = H;
+  const int L = c->L;
+  const double phi = c->k2[0];
+  H->lev.resize(L + 1);
+  int rc;
+  for (int l = 1; l <= L; ++l) {
+    Lev4& V = H->lev[l];
+    V.n = (int)ipow(3, l);
+    V.nv = (size_t)ipow(V.n + 1, 4);
+    const size_t bytes = V.nv * sizeof(cplx<double>);
+    if ((rc = d4_alloc(c, *H, (void**)&V.u, bytes)) != MG_OK) return rc;
+    if ((rc = d4_alloc(c, *H, (void**)&V.b, bytes)) != MG_OK) return rc;
+    if ((rc = d4_alloc(c, *H, (void**)&V.t, bytes)) != MG_OK) return rc;
+    if (l == 1) {
+      V.corr = V.t;
+    } else if ((rc = d4_alloc(c, *H, (void**)&V.corr, bytes)) != MG_OK) {
+      return rc;
+    }
+    std::vector<uint8_t> rot = layer_flags(c, V.n), typ(V.n + 1);
+    for (int i = 0; i <= V.n; ++i) typ[i] = (uint8_t)(rot[std::max(i - 1, 0)] + 2 * rot[std::min(i, V.n - 1)]);
+    if ((rc = d4_upload(c, *H, &V.typ, typ)) != MG_OK) return rc;
+    cplx<double> row[4][9];
+    axis_rows(c, V.n, row);
+    std::vector<cplx<double>> rows((size_t)3 * (V.n + 1) * 3);
+    for (int k = 0; k < 3; ++k)
+      for (int i = 0; i <= V.n; ++i)
+        for (int j = 0; j < 3; ++j) rows[((size_t)k * (V.n + 1) + i) * 3 + j] = row[typ[i]][3 * k + j];
+    if ((rc = d4_upload(c, *H, &V.rows, rows)) != MG_OK) return rc;
+    std::vector<cplx<double>> invd(256);
+    for (int ty = 0; ty < 256; ++ty) {
+      cd mprod(1.0), kterm(0.0);
+      for (int j = 0; j < 4; ++j) {
+        cd p(1.0);
+        for (int a = 0; a < 4; ++a) {
+          const auto& r = row[(ty >> (2 * a)) & 3];
+          p *= a == j ? cd(r[4].x, r[4].y) : cd(r[1].x, r[1].y);
+        }
+        kterm += p;
+      }
+      for (int a = 0; a < 4; ++a) {
+        const auto& r = row[(ty >> (2 * a)) & 3];
+        mprod *= cd(r[1].x, r[1].y);
+      }
+      const cd q = 1.0 / (kterm - phi * mprod);
+      invd[ty] = cplx<double>{q.real(), q.imag()};
+    }
+    if ((rc = d4_upload(c, *H, &V.invd, invd)) != MG_OK) return rc;
+    if (l > 1) {
+      std::vector<std::array<cd, 6>> g;
+      galerkin_rows_1d(V.n, rot, widths(c, V.n), g);
+      const int nc = V.n / 3;
+      std::vector<cplx<double>> gr((size_t)3 * (nc + 1) * 3);
+      for (int i = 0; i <= nc; ++i)
+        for (int j = 0; j < 3; ++j) {
+          const cd m = g[i][3 + j], k = g[i][j], kp = k - phi * m;
+          gr[((size_t)0 * (nc + 1) + i) * 3 + j] = cplx<double>{m.real(), m.imag()};
+          gr[((size_t)1 * (nc + 1) + i) * 3 + j] = cplx<double>{k.real(), k.imag()};
+          gr[((size_t)2 * (nc + 1) + i) * 3 + j] = cplx<double>{kp.real(), kp.imag()};
+        }
+      if ((rc = d4_upload(c, *H, &V.grows, gr)) != MG_OK) return rc;
+    }
+  }
+  const size_t fb = H->lev[L].nv * sizeof(cplx<double>);
+  for (int k = 0; k < 5; ++k)
+    if ((rc = d4_alloc(c, *H, (void**)&H->T[k], fb)) != MG_OK) return rc;
+  if ((rc = d4_alloc(c, *H, (void**)&H->partial, 152 * 16 * sizeof(double))) != MG_OK) return rc;
+  if ((rc = d4_alloc(c, *H, (void**)&H->ticket, 4 * sizeof(unsigned))) != MG_OK) return rc;
+  if ((rc = d4_alloc(c, *H, (void**)&H->norm2, 4 * sizeof(double))) != MG_OK) return rc;
+  return MG_OK;
+}
+
+mg::Box4 box4(int n0, int n1, int n2, int n3) { return mg::Box4{{n0, n1, n2, n3}}; }
+
+size_t box4_size(const mg::Box4& B) { return (size_t)B.n[0] * B.n[1] * B.n[2] * B.n[3]; }
+
+// y = beta b + sgn (A x): A the separable operator with rows [M, K, K - phi M]
+// per index on a grid of n cells per axis (ten passes through T[0..3]).
+cudaError_t d4_apply(mg_ctx* c, int n, const cplx<double>* rows, const cplx<double>* x, const cplx<double>* b,
+                     cplx<double>* y, double sgn) {
+  Hier4& H = *c->h4;
+  const int N = n + 1;
+  const mg::Box4 B = box4(N, N, N, N);
+  const int g = grid_for(box4_size(B));
+  const cplx<double>* M = rows;
+  const cplx<double>* K = rows + 3 * N;
+  const cplx<double>* KP = rows + 6 * N;
+  cplx<double>** T = H.T;
+  const cplx<double>* nul = nullptr;
+  auto pass = [&](int axis, const cplx<double>* r, const cplx<double>* in, const cplx<double>* z,
+                  const cplx<double>* bb, cplx<double>* out, double sg) {
+    ++c->launches;
+    mg::pass4_kernel<<<g, kThreads, 0, c->stream>>>(B, axis, r, in, z, bb, out, sg);
+  };
+  pass(3, M, x, nul, nul, T[0], 1.0);            // A = M3 x
+  pass(3, KP, x, nul, nul, T[1], 1.0);           // B = (K3 - phi M3) x
+  pass(2, M, T[0], nul, nul, T[2], 1.0);         // C = M2 A
+  pass(2, M, T[1], nul, nul, T[3], 1.0);         // M2 B
+  pass(2, K, T[0], T[3], nul, T[1], 1.0);        // D = K2 A + M2 B
+  pass(1, M, T[1], nul, nul, T[3], 1.0);         // M1 D
+  pass(1, K, T[2], T[3], nul, T[0], 1.0);        // E = K1 C + M1 D
+  pass(1, M, T[2], nul, nul, T[1], 1.0);         // F = M1 C
+  pass(0, K, T[1], nul, nul, T[2], 1.0);         // K0 F
+  pass(0, M, T[0], T[2], b, y, sgn);             // y = b + sgn (M0 E + K0 F)
+  return cudaGetLastError();
+}
+
+// b = M f on the finest level (four mass passes).
+cudaError_t d4_mass(mg_ctx* c, const cplx<double>* f, cplx<double>* b) {
+  Hier4& H = *c->h4;
+  const Lev4& V = H.lev[c->L];
+  const int N = V.n + 1;
+  const mg::Box4 B = box4(N, N, N, N);
+  const int g = grid_for(box4_size(B));
+  const cplx<double>* nul = nullptr;
+  const cplx<double>* in[4] = {f, H.T[0], H.T[1], H.T[0]};
+  cplx<double>* out[4] = {H.T[0], H.T[1], H.T[0], b};
+  for (int k = 0; k < 4; ++k) {
+    ++c->launches;
+    mg::pass4_kernel<<<g, kThreads, 0, c->stream>>>(B, 3 - k, V.rows, in[k], nul, nul, out[k], 1.0);
+  }
+  return cudaGetLastError();
+}
+
+// Restriction of a level-l array (n fine cells per axis) to level l - 1,
+// axis by axis through T[0], T[1].
+cudaError_t d4_restrict(mg_ctx* c, int n, const cplx<double>* x, cplx<double>* y) {
+  Hier4& H = *c->h4;
+  const int N = n + 1, Nc = n / 3 + 1;
+  int ext[4] = {N, N, N, N};
+  const cplx<double>* src = x;
+  cplx<double>* dst[4] = {H.T[0], H.T[1], H.T[0], y};
+  for (int a = 0; a < 4; ++a) {
+    ext[a] = Nc;
+    const mg::Box4 B = box4(ext[0], ext[1], ext[2], ext[3]);
+    ++c->launches;
+    mg::restrict4_kernel<<<grid_for(box4_size(B)), kThreads, 0, c->stream>>>(B, a, N, src, dst[a]);
+    src = dst[a];
+  }
+  return cudaGetLastError();
+}
+
+// y = base + sgn P x for x on level l - 1 (n fine cells per axis), through
+// T[1], T[2].
+cudaError_t d4_prolong(mg_ctx* c, int n, const cplx<double>* x, const cplx<double>* base, cplx<double>* y,
+                       double sgn) {
+  Hier4& H = *c->h4;
+  const int N = n + 1, Nc = n / 3 + 1;
+  int ext[4] = {Nc, Nc, Nc, Nc};
+  const cplx<double>* src = x;
+  cplx<double>* dst[4] = {H.T[1], H.T[2], H.T[1], y};
+  for (int a = 0; a < 4; ++a) {
+    ext[a] = N;
+    const mg::Box4 B = box4(ext[0], ext[1], ext[2], ext[3]);
+    const bool last = a == 3;
+    ++c->launches;
+    mg::prolong4_kernel<<<grid_for(box4_size(B)), kThreads, 0, c->stream>>>(
+        B, a, src, last ? base : nullptr, dst[a], last ? sgn : 1.0);
+    src = dst[a];
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t d4_inject(mg_ctx* c, int n, const cplx<double>* x, cplx<double>* y) {
+  const int Nc = n / 3 + 1;
+  const mg::Box4 B = box4(Nc, Nc, Nc, Nc);
+  ++c->launches;
+  mg::inject4_kernel<<<grid_for(box4_size(B)), kThreads, 0, c->stream>>>(B, x, y);
+  return cudaGetLastError();
+}
+
+// One additive FAS cycle in four dimensions (Appendix A, Algorithm 4 with the
+// coarse right-hand side b_{l-1} = R r_l + G u_{l-1}): residual, Jacobi and
+// restriction from the finest level down, then the corrections
+// corr_l = T_l du_l + P corr_{l-1} and u_L += corr_L.  The fine level is
+// read by the residual and updated at the end (no pending correction).
+cudaError_t d4_enqueue_cycle(mg_ctx* c, int hb, int hier, const cplx<double>* omega) {
+  Hier4& H = *c->h4;
+  const int L = c->L;
+  cudaError_t e = cudaSuccess;
+  for (int l = L; l >= 1 && e == cudaSuccess; --l) {
+    Lev4& V = H.lev[l];
+    if (l == L && c->timing) e = cudaEventRecord(c->ev[c->ev_used], c->stream);
+    if (e == cudaSuccess) e = d4_apply(c, V.n, V.rows, V.u, V.b, H.T[4], -1.0);  // r_l
+    if (l == L && c->timing && e == cudaSuccess) e = cudaEventRecord(c->ev[c->ev_used + 1], c->stream);
+    if (e != cudaSuccess) break;
+    ++c->launches;
+    const cplx<double> w = omega[l - 1];
+    mg::jacobi4_kernel<<<grid_for(V.nv), kThreads, 0, c->stream>>>(
+        V.n, H.T[4], V.t, V.typ, V.invd, w, hb, H.partial, H.ticket, l == L ? H.norm2 : nullptr);
+    if (l > 1) {
+      Lev4& W = H.lev[l - 1];
+      e = d4_inject(c, V.n, V.u, W.u);
+      if (e == cudaSuccess) e = d4_restrict(c, V.n, H.T[4], W.b);
+      if (e == cudaSuccess) e = d4_apply(c, W.n, V.grows, W.u, W.b, W.b, 1.0);  // + G u_{l-1}
+      if (hier && e == cudaSuccess) {
+        // BPX transfer: T du = du - P I du
+        e = d4_inject(c, V.n, V.t, H.T[0]);
+        if (e == cudaSuccess) e = d4_prolong(c, V.n, H.T[0], V.t, V.t, -1.0);
+      }
+    }
+    if (e == cudaSuccess) e = cudaGetLastError();
+  }
+  for (int l = 2; l <= L && e == cudaSuccess; ++l)
+    e = d4_prolong(c, H.lev[l].n, H.lev[l - 1].corr, H.lev[l].t, H.lev[l].corr, 1.0);
+  if (e == cudaSuccess) {
+    const Lev4& F = H.lev[L];
+    ++c->launches;
+    mg::update4_kernel<<<grid_for(F.nv), kThreads, 0, c->stream>>>(F.n, F.u, F.corr);
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
+int d4_cycle(mg_ctx* c, int hb, int hier, const cplx<double>* omega) {
+  Hier4& H = *c->h4;
+  cudaError_t e = cudaSuccess;
+  if (c->timing) {
+    if (c->ev_used + 2 > c->ev.size()) {
+      for (int k = 0; k < 64; ++k) {
+        cudaEvent_t ev;
+        if (cudaEventCreate(&ev) != cudaSuccess) return fail(c, MG_ERR_CUDA, "cudaEventCreate failed");
+        c->ev.push_back(ev);
+      }
+    }
+    e = d4_enqueue_cycle(c, hb, hier, omega);
+    c->ev_used += 2;
+    if (e != cudaSuccess) return fail(c, MG_ERR_CUDA, std::string("cycle launch: ") + cudaGetErrorString(e));
+    return MG_OK;
+  }
+  if (c->use_graphs) {
+    std::vector<double> key = {(double)hb, (double)hier};
+    for (int l = 0; l < c->L; ++l) {
+      key.push_back(omega[l].x);
+      key.push_back(omega[l].y);
+    }
+    if (H.exec == nullptr || H.key != key) {
+      cudaStream_t user = c->stream;
+      c->stream = c->cap_stream;
+      const long long before = c->launches;
+      cudaGraph_t g = nullptr;
+      e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+      cudaError_t ek = e == cudaSuccess ? d4_enqueue_cycle(c, hb, hier, omega) : e;
+      cudaError_t ee = e == cudaSuccess ? cudaStreamEndCapture(c->cap_stream, &g) : e;
+      c->stream = user;
+      const long long nk = c->launches - before;
+      c->launches = before;
+      e = ek != cudaSuccess ? ek : ee;
+      if (e == cudaSuccess) {
+        cudaGraphExecUpdateResultInfo info;
+        if (H.exec == nullptr || cudaGraphExecUpdate(H.exec, g, &info) != cudaSuccess) {
+          cudaGetLastError();
+          if (H.exec) cudaGraphExecDestroy(H.exec);
+          H.exec = nullptr;
+          e = cudaGraphInstantiate(&H.exec, g, 0);
+        }
+      }
+      if (g) cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (H.exec) cudaGraphExecDestroy(H.exec);
+        H.exec = nullptr;
+        c->use_graphs = false;
+      } else {
+        H.key = key;
+        H.nkern = nk;
+      }
+    }
+    if (H.exec != nullptr) {
+      e = cudaGraphLaunch(H.exec, c->stream);
+      c->launches += H.nkern;
+      if (e != cudaSuccess) return fail(c, MG_ERR_CUDA, std::string("cycle launch: ") + cudaGetErrorString(e));
+      return MG_OK;
+    }
+  }
+  e = d4_enqueue_cycle(c, hb, hier, omega);
+  if (e != cudaSuccess) return fail(c, MG_ERR_CUDA, std::string("cycle launch: ") + cudaGetErrorString(e));
+  return MG_OK;
+}
+
+// Fine residual r = b - H u into T[4]; |r|^2 into norm2[slot] when slot >= 0.
+cudaError_t d4_residual(mg_ctx* c, int slot) {
+  Hier4& H = *c->h4;
+  const Lev4& V = H.lev[c->L];
+  cudaError_t e = d4_apply(c, V.n, V.rows, V.u, V.b, H.T[4], -1.0);
+  if (e == cudaSuccess && slot >= 0) {
+    ++c->launches;
+    mg::norm4_kernel<<<grid_for(V.nv), kThreads, 0, c->stream>>>(V.n, H.T[4], H.partial, H.ticket + 1,
+                                                                   H.norm2 + slot);
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
+const char* kNot4 = " is not available for d = 4 (the four-dimensional path runs complex128 cycles)";
+
 }  // namespace
 
 // =========================================================================
@@ -1438,8 +1811,8 @@ int mg_create_ecs(int d, int depth, const double* k2_field, double theta_layer, 
   g_create_err.clear();
   if (out == nullptr) return fail(nullptr, MG_ERR_INVALID, "out is NULL");
   *out = nullptr;
-  if (d != 2 && d != 3) return fail(nullptr, MG_ERR_INVALID, "d must be 2 or 3");
-  if (depth < 1 || depth > (d == 2 ? kMaxDepth2 : kMaxDepth3))
+  if (d != 2 && d != 3 && d != 4) return fail(nullptr, MG_ERR_INVALID, "d must be 2, 3 or 4");
+  if (depth < 1 || depth > (d == 2 ? kMaxDepth2 : (d == 3 ? kMaxDepth3 : kMaxDepth4)))
     return fail(nullptr, MG_ERR_INVALID, "depth out of range");
   if (k2_field == nullptr) return fail(nullptr, MG_ERR_INVALID, "k2_field is NULL");
   if (!(theta_layer >= 0.0 && theta_layer < M_PI / 2))
@@ -1451,11 +1824,16 @@ int mg_create_ecs(int d, int depth, const double* k2_field, double theta_layer, 
   const size_t nvf = (size_t)ipow(ipow(3, depth) + 1, d);
   for (size_t i = 0; i < nvf; ++i)
     if (!std::isfinite(k2_field[i])) return fail(nullptr, MG_ERR_INVALID, "k2_field holds a non-finite value");
+  if (d == 4)
+    for (size_t i = 1; i < nvf; ++i)
+      if (k2_field[i] != k2_field[0])
+        return fail(nullptr, MG_ERR_INVALID, "d = 4 takes a constant k2_field (separable operator)");
   // memory estimate: 5 fine-size c128 arrays per level plus scratch and f
+  // (d = 4: 4 level arrays and 5 temporaries)
   {
     size_t fr = 0, tot = 0;
     if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return fail(nullptr, MG_ERR_CUDA, "cudaMemGetInfo failed");
-    const double need = (double)nvf * 16.0 * 5.0 * 1.2 + (double)nvf * 32.0;
+    const double need = (double)nvf * 16.0 * (d == 4 ? 9.0 : 5.0) * 1.2 + (double)nvf * 32.0;
     if (need > (double)fr) return fail(nullptr, MG_ERR_OOM, "grid too large for free device memory");
   }
   mg_ctx* c = new (std::nothrow) mg_ctx();
@@ -1467,7 +1845,7 @@ int mg_create_ecs(int d, int depth, const double* k2_field, double theta_layer, 
   c->wlo = width_lo;
   c->whi = width_hi;
   c->k2.assign(k2_field, k2_field + nvf);
-  int rc = build_hier<double>(c, c->h64);
+  int rc = d == 4 ? d4_build(c) : build_hier<double>(c, c->h64);
   if (rc == MG_OK) {
     cudaError_t e = cudaMalloc(&c->f_dev, nvf * sizeof(cplx<double>));
     if (e == cudaSuccess) e = cudaMemset(c->f_dev, 0, nvf * sizeof(cplx<double>));
@@ -1502,6 +1880,7 @@ void mg_destroy(mg_ctx* c) {
   if (c->dev_err) cudaFree(c->dev_err);
   free_hier(c->h64);
   free_hier(c->h32);
+  d4_free(c->h4);
   if (c->f_dev) cudaFree(c->f_dev);
   if (c->scratch) cudaFree(c->scratch);
   if (c->rvec) cudaFree(c->rvec);
@@ -1518,6 +1897,14 @@ int mg_set_stream(mg_ctx* c, void* s) {
 int mg_set_rhs(mg_ctx* c, const mg_c128* f, int on_device) {
   if (check_ctx(c)) return MG_ERR_INVALID;
   if (f == nullptr) return fail(c, MG_ERR_INVALID, "f is NULL");
+  if (c->d == 4) {
+    const Lev4& V = c->h4->lev[c->L];
+    MG_CUDA(c, cudaMemcpyAsync(c->f_dev, f, V.nv * sizeof(mg_c128),
+                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    MG_CUDA(c, d4_mass(c, c->f_dev, V.b));
+    c->r0 = -1.0;
+    return MG_OK;
+  }
   const size_t nv = c->h64.lev[c->L].nv;
   MG_CUDA(c, cudaMemcpyAsync(c->f_dev, f, nv * sizeof(mg_c128),
                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
@@ -1530,6 +1917,16 @@ int mg_set_rhs(mg_ctx* c, const mg_c128* f, int on_device) {
 int mg_set_solution(mg_ctx* c, const mg_c128* u, int on_device) {
   if (check_ctx(c)) return MG_ERR_INVALID;
   if (u == nullptr) return fail(c, MG_ERR_INVALID, "u is NULL");
+  if (c->d == 4) {
+    const Lev4& V = c->h4->lev[c->L];
+    MG_CUDA(c, cudaMemcpyAsync(V.u, u, V.nv * sizeof(mg_c128),
+                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    ++c->launches;
+    mg::update4_kernel<<<grid_for(V.nv), kThreads, 0, c->stream>>>(V.n, V.u, nullptr);  // zero boundary
+    MG_CUDA(c, cudaGetLastError());
+    c->r0 = -1.0;
+    return MG_OK;
+  }
   auto& H = c->h64;
   auto& V = H.lev[c->L];
   // copy into the active fine array, then zero its Dirichlet ring
@@ -1550,6 +1947,13 @@ int mg_set_solution(mg_ctx* c, const mg_c128* u, int on_device) {
 int mg_get_solution(mg_ctx* c, mg_c128* out, int on_device) {
   if (check_ctx(c)) return MG_ERR_INVALID;
   if (out == nullptr) return fail(c, MG_ERR_INVALID, "out is NULL");
+  if (c->d == 4) {
+    const Lev4& V = c->h4->lev[c->L];
+    MG_CUDA(c, cudaMemcpyAsync(out, V.u, V.nv * sizeof(mg_c128),
+                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    if (!on_device) MG_CUDA(c, cudaStreamSynchronize(c->stream));
+    return MG_OK;
+  }
   auto& H = c->h64;
   const size_t nv = H.lev[c->L].nv;
   if (on_device) {
@@ -1567,6 +1971,13 @@ int mg_get_level(mg_ctx* c, int level, int which, mg_c128* out, int on_device) {
   if (out == nullptr || level < 1 || level > c->L || (which != 0 && which != 1))
     return fail(c, MG_ERR_INVALID, "bad level/which/out");
   if (level == c->L && which == 0) return mg_get_solution(c, out, on_device);
+  if (c->d == 4) {
+    const Lev4& V = c->h4->lev[level];
+    MG_CUDA(c, cudaMemcpyAsync(out, which == 0 ? V.u : V.b, V.nv * sizeof(mg_c128),
+                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    if (!on_device) MG_CUDA(c, cudaStreamSynchronize(c->stream));
+    return MG_OK;
+  }
   auto& V = c->h64.lev[level];
   const void* src = which == 0 ? (const void*)V.u[0] : (const void*)V.b;
   MG_CUDA(c, cudaMemcpyAsync(out, src, V.nv * sizeof(mg_c128),
@@ -1580,6 +1991,7 @@ int mg_cycle(mg_ctx* c, int variant, const mg_c128* omega, int transfer) {
   if (omega == nullptr) return fail(c, MG_ERR_INVALID, "omega is NULL");
   int hb, hier;
   if (decode_variant(c, variant, transfer, &hb, &hier)) return MG_ERR_INVALID;
+  if (c->d == 4) return d4_cycle(c, hb, hier, reinterpret_cast<const cplx<double>*>(omega));
   return run_cycle(c, c->h64, c->L, hb, hier, reinterpret_cast<const cplx<double>*>(omega));
 }
 
@@ -1597,6 +2009,20 @@ int mg_residual_norm(mg_ctx* c, double* abs_l2, double* rel_l2) {
 int mg_residual_max(mg_ctx* c, double* abs_max) {
   if (check_ctx(c)) return MG_ERR_INVALID;
   if (abs_max == nullptr) return fail(c, MG_ERR_INVALID, "abs_max is NULL");
+  if (c->d == 4) {
+    Hier4& H4 = *c->h4;
+    unsigned long long* mx = reinterpret_cast<unsigned long long*>(H4.norm2 + 2);
+    MG_CUDA(c, d4_residual(c, -1));
+    MG_CUDA(c, cudaMemsetAsync(mx, 0, sizeof(unsigned long long), c->stream));
+    ++c->launches;
+    const size_t nv = H4.lev[c->L].nv;
+    mg::max_abs_kernel<<<grid_for(nv), kThreads, 0, c->stream>>>(H4.T[4], (long long)nv, mx);
+    MG_CUDA(c, cudaGetLastError());
+    MG_CUDA(c, cudaMemcpyAsync(c->host_norm, mx, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    MG_CUDA(c, cudaStreamSynchronize(c->stream));
+    *abs_max = *c->host_norm;
+    return MG_OK;
+  }
   auto& H = c->h64;
   auto& V = H.lev[c->L];
   if (c->rvec == nullptr) MG_CUDA(c, cudaMalloc(&c->rvec, V.nv * sizeof(cplx<double>)));
@@ -1617,6 +2043,7 @@ int mg_set_precision(mg_ctx* c, int precision, int inner_cycles) {
   if (check_ctx(c)) return MG_ERR_INVALID;
   if (precision != MG_C128 && precision != MG_C64_REFINE) return fail(c, MG_ERR_INVALID, "bad precision");
   if (inner_cycles < 1 || inner_cycles > 1000) return fail(c, MG_ERR_INVALID, "inner_cycles out of range");
+  if (c->d == 4 && precision != MG_C128) return fail(c, MG_ERR_INVALID, std::string("MG_C64_REFINE") + kNot4);
   c->precision = precision;
   c->inner_cycles = inner_cycles;
   if (precision == MG_C64_REFINE && !c->h32.ready) {
@@ -1659,10 +2086,12 @@ int mg_solve(mg_ctx* c, int variant, const mg_c128* omega, int transfer, double 
       if (done >= max_cycles) return finish(MG_NOT_CONVERGED);
       const int m = std::min(check, max_cycles - done);
       for (int k = 0; k < m; ++k) {
-        if ((rc = run_cycle(c, c->h64, L, hb, hier, om)) != MG_OK) return rc;
+        rc = c->d == 4 ? d4_cycle(c, hb, hier, om) : run_cycle(c, c->h64, L, hb, hier, om);
+        if (rc != MG_OK) return rc;
         ++done;
       }
-      MG_CUDA(c, cudaMemcpyAsync(c->host_norm, c->h64.norm2, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+      MG_CUDA(c, cudaMemcpyAsync(c->host_norm, c->d == 4 ? c->h4->norm2 : c->h64.norm2, sizeof(double),
+                                 cudaMemcpyDeviceToHost, c->stream));
       MG_CUDA(c, cudaStreamSynchronize(c->stream));
       if ((rc = check_timeout(c)) != MG_OK) return finish(rc);
       const double prev = std::sqrt(*c->host_norm) / (c->r0 > 0 ? c->r0 : 1.0);
@@ -1736,6 +2165,7 @@ int mg_solve(mg_ctx* c, int variant, const mg_c128* omega, int transfer, double 
 
 int mg_fmg(mg_ctx* c, int variant, const mg_c128* omega, int transfer, int cycles_per_stage) {
   if (check_ctx(c)) return MG_ERR_INVALID;
+  if (c->d == 4) return fail(c, MG_ERR_INVALID, std::string("mg_fmg") + kNot4);
   if (omega == nullptr || cycles_per_stage < 0) return fail(c, MG_ERR_INVALID, "bad omega/cycles_per_stage");
   int hb, hier;
   if (decode_variant(c, variant, transfer, &hb, &hier)) return MG_ERR_INVALID;
@@ -1818,6 +2248,7 @@ int mg_debug_unsatisfiable_wait(mg_ctx* c, int enable) {
 
 int mg_set_trace(mg_ctx* c, int enable) {
   if (check_ctx(c)) return MG_ERR_INVALID;
+  if (c->d == 4) return fail(c, MG_ERR_INVALID, std::string("mg_set_trace") + kNot4);
   if (enable && c->trace == nullptr)
     MG_CUDA(c, cudaMalloc(&c->trace, 4ull * (kTraceFine + kTraceChain) * sizeof(unsigned long long)));
   if (enable) MG_CUDA(c, cudaMemset(c->trace, 0, 4ull * (kTraceFine + kTraceChain) * sizeof(unsigned long long)));
@@ -1841,7 +2272,8 @@ int mg_get_trace(mg_ctx* c, unsigned long long* out, int fine_slots, int chain_s
 
 int mg_last_cycle_norm(mg_ctx* c, double* abs_l2, double* rel_l2) {
   if (check_ctx(c)) return MG_ERR_INVALID;
-  MG_CUDA(c, cudaMemcpyAsync(c->host_norm, c->h64.norm2, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  MG_CUDA(c, cudaMemcpyAsync(c->host_norm, c->d == 4 ? c->h4->norm2 : c->h64.norm2, sizeof(double),
+                             cudaMemcpyDeviceToHost, c->stream));
   MG_CUDA(c, cudaStreamSynchronize(c->stream));
   const double r = std::sqrt(*c->host_norm);
   if (abs_l2) *abs_l2 = r;
@@ -1876,6 +2308,7 @@ int mg_get_stats(mg_ctx* c, long long* launches, int* fine_sweeps, double* fine_
 
 int mg_set_k2(mg_ctx* c, const double* k2) {
   if (check_ctx(c)) return MG_ERR_INVALID;
+  if (c->d == 4) return fail(c, MG_ERR_INVALID, std::string("mg_set_k2") + kNot4);
   if (k2 == nullptr) return fail(c, MG_ERR_INVALID, "k2 is NULL");
   if (!c->h64.varphi)
     return fail(c, MG_ERR_INVALID, "the context was created with a constant k^2; create a new context");
@@ -1899,6 +2332,16 @@ int mg_set_k2(mg_ctx* c, const double* k2) {
 int mg_set_rhs_vector(mg_ctx* c, const mg_c128* b, int on_device) {
   if (check_ctx(c)) return MG_ERR_INVALID;
   if (b == nullptr) return fail(c, MG_ERR_INVALID, "b is NULL");
+  if (c->d == 4) {
+    const Lev4& V = c->h4->lev[c->L];
+    MG_CUDA(c, cudaMemcpyAsync(V.b, b, V.nv * sizeof(mg_c128),
+                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    ++c->launches;
+    mg::update4_kernel<<<grid_for(V.nv), kThreads, 0, c->stream>>>(V.n, V.b, nullptr);  // zero boundary
+    MG_CUDA(c, cudaGetLastError());
+    c->r0 = -1.0;
+    return MG_OK;
+  }
   auto& V = c->h64.lev[c->L];
   MG_CUDA(c, cudaMemcpyAsync(c->scratch, b, V.nv * sizeof(mg_c128),
                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
@@ -1950,6 +2393,7 @@ int sample_stencil(mg_ctx* c, int npts, const double* xyz, const mg_c128* w,
 
 int mg_sample(mg_ctx* c, int npts, const double* xyz, const mg_c128* w, mg_c128* out) {
   if (check_ctx(c)) return MG_ERR_INVALID;
+  if (c->d == 4) return fail(c, MG_ERR_INVALID, std::string("mg_sample") + kNot4);
   if (npts < 1 || xyz == nullptr || w == nullptr || out == nullptr)
     return fail(c, MG_ERR_INVALID, "bad sample arguments");
   std::map<long long, cd> acc;
@@ -1974,6 +2418,7 @@ int mg_sample(mg_ctx* c, int npts, const double* xyz, const mg_c128* w, mg_c128*
 
 int mg_set_rhs_samples(mg_ctx* c, int npts, const double* xyz, const mg_c128* w) {
   if (check_ctx(c)) return MG_ERR_INVALID;
+  if (c->d == 4) return fail(c, MG_ERR_INVALID, std::string("mg_set_rhs_samples") + kNot4);
   if (npts < 1 || xyz == nullptr || w == nullptr) return fail(c, MG_ERR_INVALID, "bad sample arguments");
   std::map<long long, cd> acc;
   int rc = sample_stencil(c, npts, xyz, w, acc);
@@ -1986,6 +2431,7 @@ int mg_set_rhs_samples(mg_ctx* c, int npts, const double* xyz, const mg_c128* w)
 int mg_adjoint_grad(mg_ctx* c, const mg_c128* u, const mg_c128* lambda, mg_c128 s, double* dJdV,
                     double* dJdf) {
   if (check_ctx(c)) return MG_ERR_INVALID;
+  if (c->d == 4) return fail(c, MG_ERR_INVALID, std::string("mg_adjoint_grad") + kNot4);
   if (u == nullptr || lambda == nullptr || (dJdV == nullptr && dJdf == nullptr))
     return fail(c, MG_ERR_INVALID, "u, lambda and at least one output are required");
   auto& V = c->h64.lev[c->L];
@@ -2064,6 +2510,7 @@ int noalloc_scratch(mg_ctx* c, unsigned char** out) {
 extern "C" int mg_residual_noalloc(mg_ctx* c, const mg_c128* u, const mg_c128* b, mg_c128* r,
                                    double* norm2) {
   if (check_ctx(c)) return MG_ERR_INVALID;
+  if (c->d == 4) return fail(c, MG_ERR_INVALID, std::string("mg_residual_noalloc") + kNot4);
   if (u == nullptr || b == nullptr || norm2 == nullptr)
     return fail(c, MG_ERR_INVALID, "u, b and norm2 must be device pointers");
   auto& H = c->h64;

@@ -1,0 +1,210 @@
+// mg_dim4.cuh -- the cycle in four dimensions (p = 4 of Section 7.1), FP64,
+// constant shift, sm_103a.
+//
+// A d-linear 4D stencil row has 81 points and 256 vertex types, too many for
+// the shared-memory tiles of the 2D/3D sweeps.  With coordinate-wise scaling
+// and a constant shift the operator is a sum of tensor products of assembled
+// 1D rows (Section 3 element matrices, one factor per axis):
+//   H = M0 [M1 [M2 (K3 - phi M3) + K2 M3] + K1 M2 M3] + K0 M1 M2 M3,
+// so H u is ten 3-tap passes along single axes; the Galerkin operator
+// G = R H P of the coarse right-hand side has the same form with the 1D
+// Galerkin rows, and R, P, I act axis by axis.  Every kernel here is one such
+// pass over a 4D box (axis 0 fastest): coalesced, HBM-bound, one thread per
+// output vertex.  A pass zeroes its outputs on the two boundary planes of its
+// own axis; the other coordinates carry through, so a chain of passes gives
+// the interior rows of the product and zero Dirichlet rows.
+#pragma once
+#include "mg_kernels.cuh"
+
+namespace mg {
+
+struct Box4 {
+  int n[4];  // extent per axis, axis 0 fastest
+};
+
+__device__ __forceinline__ unsigned box4_total(const Box4& B) {
+  return (unsigned)B.n[0] * B.n[1] * B.n[2] * B.n[3];
+}
+
+__device__ __forceinline__ void box4_coords(unsigned i, const Box4& B, int* c) {
+  c[0] = (int)(i % (unsigned)B.n[0]);
+  i /= (unsigned)B.n[0];
+  c[1] = (int)(i % (unsigned)B.n[1]);
+  i /= (unsigned)B.n[1];
+  c[2] = (int)(i % (unsigned)B.n[2]);
+  c[3] = (int)(i / (unsigned)B.n[2]);
+}
+
+__device__ __forceinline__ unsigned box4_index(const Box4& B, const int* c) {
+  return (((unsigned)c[3] * B.n[2] + c[2]) * B.n[1] + c[1]) * B.n[0] + c[0];
+}
+
+// y = beta b + sgn (A x + z), A the 3-tap rows along `axis` (rows[3 i + k]
+// couples coordinate i with i - 1 + k); zero on the axis' boundary planes.
+// b and z may be null; y may alias b (element-wise update).
+__global__ void pass4_kernel(Box4 B, int axis, const cplx<double>* __restrict__ rows,
+                             const cplx<double>* __restrict__ x, const cplx<double>* __restrict__ z,
+                             const cplx<double>* b, cplx<double>* y, double sgn) {
+  const unsigned total = box4_total(B);
+  unsigned s = 1;
+  for (int a = 0; a < axis; ++a) s *= (unsigned)B.n[a];
+  const int na = B.n[axis];
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    const int ca = (int)((i / s) % (unsigned)na);
+    cplx<double> v = cz<double>();
+    if (ca > 0 && ca < na - 1) {
+      const cplx<double>* r = rows + 3 * ca;
+      v = r[0] * x[i - s];
+      v = cfma(r[1], x[i], v);
+      v = cfma(r[2], x[i + s], v);
+      if (z != nullptr) v = v + z[i];
+    }
+    v = rmul(sgn, v);
+    if (b != nullptr) v = b[i] + v;
+    y[i] = v;
+  }
+}
+
+// Restriction R = P^T along `axis`: the output box is the input box with
+// (n_f - 1)/3 + 1 points along the axis; coarse c collects fine 3c + o,
+// o = -2..2, with weights 1 - |o|/3.  Zero on the axis' boundary planes.
+__global__ void restrict4_kernel(Box4 Bout, int axis, int nf, const cplx<double>* __restrict__ x,
+                                 cplx<double>* __restrict__ y) {
+  const unsigned total = box4_total(Bout);
+  Box4 Bin = Bout;
+  Bin.n[axis] = nf;
+  unsigned s = 1;
+  for (int a = 0; a < axis; ++a) s *= (unsigned)Bin.n[a];
+  const int nc = Bout.n[axis];
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    int c[4];
+    box4_coords(i, Bout, c);
+    const int ca = c[axis];
+    cplx<double> v = cz<double>();
+    if (ca > 0 && ca < nc - 1) {
+      c[axis] = 3 * ca;
+      const unsigned j = box4_index(Bin, c);
+      v = x[j];
+      v = rfma(2.0 / 3.0, x[j - s], v);
+      v = rfma(2.0 / 3.0, x[j + s], v);
+      v = rfma(1.0 / 3.0, x[j - 2 * s], v);
+      v = rfma(1.0 / 3.0, x[j + 2 * s], v);
+    }
+    y[i] = v;
+  }
+}
+
+// d-linear interpolation along `axis`: the output box has n_f = 3 (n_c - 1) + 1
+// points along the axis; fine 3c + o takes (1 - o/3) x[c] + (o/3) x[c+1].
+// y = base + sgn P x (base may be null; y may alias base).
+__global__ void prolong4_kernel(Box4 Bout, int axis, const cplx<double>* __restrict__ x,
+                                const cplx<double>* base, cplx<double>* y, double sgn) {
+  const unsigned total = box4_total(Bout);
+  Box4 Bin = Bout;
+  Bin.n[axis] = (Bout.n[axis] - 1) / 3 + 1;
+  unsigned s = 1;
+  for (int a = 0; a < axis; ++a) s *= (unsigned)Bin.n[a];
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    int c[4];
+    box4_coords(i, Bout, c);
+    const int f = c[axis], o = f % 3;
+    c[axis] = f / 3;
+    const unsigned j = box4_index(Bin, c);
+    cplx<double> v;
+    if (o == 0) {
+      v = x[j];
+    } else {
+      const double w1 = o == 1 ? 1.0 / 3.0 : 2.0 / 3.0;
+      v = rmul(1.0 - w1, x[j]);
+      v = rfma(w1, x[j + s], v);
+    }
+    v = rmul(sgn, v);
+    if (base != nullptr) v = base[i] + v;
+    y[i] = v;
+  }
+}
+
+// Injection u_{l-1} = I u_l: coarse vertex C copies fine vertex 3C.
+__global__ void inject4_kernel(Box4 Bc, const cplx<double>* __restrict__ x, cplx<double>* __restrict__ y) {
+  const unsigned total = box4_total(Bc);
+  Box4 Bf;
+  for (int a = 0; a < 4; ++a) Bf.n[a] = 3 * (Bc.n[a] - 1) + 1;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    int c[4];
+    box4_coords(i, Bc, c);
+    for (int a = 0; a < 4; ++a) c[a] *= 3;
+    y[i] = x[box4_index(Bf, c)];
+  }
+}
+
+// du = omega D^{-1} r at interior vertices (D from the 256-entry table of
+// inverse diagonals by vertex type), zero at c-points for the hierarchical
+// basis variant and on the boundary; |r|^2 over the interior into *norm2
+// (deterministic last-block sum) when norm2 is not null.
+__global__ void __launch_bounds__(256) jacobi4_kernel(int n, const cplx<double>* __restrict__ r,
+                                                      cplx<double>* __restrict__ t,
+                                                      const uint8_t* __restrict__ typ,
+                                                      const cplx<double>* __restrict__ invd,
+                                                      cplx<double> omega, int hb, double* partial,
+                                                      unsigned* ticket, double* norm2) {
+  Box4 B;
+  for (int a = 0; a < 4; ++a) B.n[a] = n + 1;
+  const unsigned total = box4_total(B);
+  double nrm = 0.0;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    int c[4];
+    box4_coords(i, B, c);
+    bool inner = true, cpt = true;
+    int ty = 0;
+#pragma unroll
+    for (int a = 3; a >= 0; --a) {
+      inner = inner && c[a] > 0 && c[a] < n;
+      cpt = cpt && (c[a] % 3 == 0);
+    }
+    cplx<double> du = cz<double>();
+    if (inner) {
+#pragma unroll
+      for (int a = 3; a >= 0; --a) ty = 4 * ty + (int)typ[c[a]];
+      const cplx<double> ri = r[i];
+      nrm = fma(ri.x, ri.x, fma(ri.y, ri.y, nrm));
+      if (!(hb && cpt)) du = (omega * invd[ty]) * ri;
+    }
+    t[i] = du;
+  }
+  if (norm2 != nullptr) {
+    __shared__ double s_red[8];
+    block_norm_finish<256>(nrm, s_red, partial, ticket, norm2, gridDim.x);
+  }
+}
+
+// |x|^2 over the interior of a level array (deterministic).
+__global__ void __launch_bounds__(256) norm4_kernel(int n, const cplx<double>* __restrict__ x, double* partial,
+                                                    unsigned* ticket, double* norm2) {
+  Box4 B;
+  for (int a = 0; a < 4; ++a) B.n[a] = n + 1;
+  const unsigned total = box4_total(B);
+  double nrm = 0.0;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    const cplx<double> v = x[i];
+    nrm = fma(v.x, v.x, fma(v.y, v.y, nrm));
+  }
+  __shared__ double s_red[8];
+  block_norm_finish<256>(nrm, s_red, partial, ticket, norm2, gridDim.x);
+}
+
+// u += c at interior vertices; boundary vertices of u are set to zero.
+__global__ void update4_kernel(int n, cplx<double>* __restrict__ u, const cplx<double>* __restrict__ c) {
+  Box4 B;
+  for (int a = 0; a < 4; ++a) B.n[a] = n + 1;
+  const unsigned total = box4_total(B);
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    int q[4];
+    box4_coords(i, B, q);
+    bool inner = true;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) inner = inner && q[a] > 0 && q[a] < n;
+    u[i] = inner ? (c != nullptr ? u[i] + c[i] : u[i]) : cz<double>();
+  }
+}
+
+}  // namespace mg

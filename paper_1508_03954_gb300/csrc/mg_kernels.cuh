@@ -230,8 +230,26 @@ size_t sweep_smem_bytes(int varphi) {
   return b;
 }
 
+// 6^D and 3^D: the mass of a d-linear cell is prod_a h_a / 6^D times the
+// integer weight prod_a (2 if the two corners agree along a, else 1); its
+// diagonal entry is prod_a h_a / 3^D.
+template <int D> struct MassScale {
+  static constexpr double inv6 = D == 1 ? 1.0 / 6.0 : (D == 2 ? 1.0 / 36.0 : 1.0 / 216.0);
+  static constexpr double inv3 = D == 1 ? 1.0 / 3.0 : (D == 2 ? 1.0 / 9.0 : 1.0 / 27.0);
+};
+
+// Integer mass weight of corner q in the row of corner g (bit a of each is
+// the local coordinate along axis a).
+template <int D>
+__host__ __device__ constexpr int mass_weight(int g, int q) {
+  int w = 1;
+  for (int a = 0; a < D; ++a) w *= (((g >> a) & 1) == ((q >> a) & 1)) ? 2 : 1;
+  return w;
+}
+
 // Per-cell shift term: sum over the 2^d cells c around vertex g of
-// phi_c (M_c u)(g), with M_c the tensor product of 1D masses h/6 [[2,1],[1,2]].
+// phi_c (M_c u)(g), with M_c the tensor product of 1D masses h/6 [[2,1],[1,2]]:
+// per cell one product of the d complex widths and 2^d real-weighted adds.
 template <typename R, int D, int TC>
 __device__ __forceinline__ cplx<R> mass_phi(const cplx<R>* s, int pbox /*index in u box*/,
                                             const int* bc /*u-box coords of g*/,
@@ -240,35 +258,32 @@ __device__ __forceinline__ cplx<R> mass_phi(const cplx<R>* s, int pbox /*index i
   cplx<R> acc = cz<R>();
 #pragma unroll
   for (int e = 0; e < (1 << D); ++e) {
-    // cell = g - 1 + bit along each axis; its u-box cell index = bc - 1 + bit
-    int cell[3] = {0, 0, 0};
+    // cell = g - 1 + bit along each axis; its u-box cell index = bc - 1 + bit;
+    // g sits at local coordinate 1 - bit along each axis
     int cidx = 0, cstride = 1;
+    cplx<R> hp{R(1), R(0)};
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-      cell[a] = bc[a] - 1 + ((e >> a) & 1);
-      cidx += cell[a] * cstride;
+      const int ca = bc[a] - 1 + ((e >> a) & 1);
+      cidx += ca * cstride;
       cstride *= G::NCELL;
+      hp = a == 0 ? s_h[ca] : hp * s_h[a * G::NCELL + ca];
     }
+    const int gl = ((1 << D) - 1) ^ e;
     cplx<R> loc = cz<R>();
 #pragma unroll
     for (int q = 0; q < (1 << D); ++q) {
-      // corner q of the cell; g sits at local coordinate (1 - bit_a(e))
-      cplx<R> w{R(1), R(0)};
       int off = 0, ostride = 1;
 #pragma unroll
       for (int a = 0; a < D; ++a) {
-        int ag = 1 - ((e >> a) & 1), aq = (q >> a) & 1;
-        cplx<R> h = s_h[a * G::NCELL + cell[a]];
-        R f = (ag == aq ? R(2) : R(1)) / R(6);
-        w = w * rmul(f, h);
-        off += (cell[a] + aq - bc[a]) * ostride;
+        off += (((q >> a) & 1) - ((gl >> a) & 1)) * ostride;
         ostride *= G::SU;
       }
-      loc = cfma(w, s[pbox + off], loc);
+      loc = rfma(R(mass_weight<D>(gl, q)), s[pbox + off], loc);
     }
-    acc = acc + rmul(s_phi[cidx], loc);
+    acc = cfma(rmul(s_phi[cidx], hp), loc, acc);
   }
-  return acc;
+  return rmul(R(MassScale<D>::inv6), acc);
 }
 
 template <typename R, int D, int TC>
@@ -277,18 +292,18 @@ __device__ __forceinline__ cplx<R> diag_phi(const int* bc, const R* s_phi, const
   cplx<R> acc = cz<R>();
 #pragma unroll
   for (int e = 0; e < (1 << D); ++e) {
-    cplx<R> w{R(1), R(0)};
+    cplx<R> hp{R(1), R(0)};
     int cidx = 0, cstride = 1;
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-      int ca = bc[a] - 1 + ((e >> a) & 1);
-      w = w * rmul(R(2) / R(6), s_h[a * G::NCELL + ca]);
+      const int ca = bc[a] - 1 + ((e >> a) & 1);
+      hp = a == 0 ? s_h[ca] : hp * s_h[a * G::NCELL + ca];
       cidx += ca * cstride;
       cstride *= G::NCELL;
     }
-    acc = acc + rmul(s_phi[cidx], w);
+    acc = acc + rmul(s_phi[cidx], hp);
   }
-  return acc;
+  return rmul(R(MassScale<D>::inv3), acc);
 }
 
 // Loads of arrays that other blocks of the same launch may have written
@@ -812,31 +827,35 @@ __global__ void stencil_kernel(int n, int xs, const cplx<R>* __restrict__ x,
         for (int k = 0; k < NS; ++k) acc = cfma(cf[k], x[nbr(k)], acc);
       }
       if (phic != nullptr) {
-        // - sum_c phi_c (M_c x)(g)
+        // - sum_c phi_c (M_c x)(g), M_c = prod_a h_a / 6^D x integer weights
         cplx<R> m = cz<R>();
+#pragma unroll
         for (int e = 0; e < (1 << D); ++e) {
           int cell[3];
           long long cidx = 0, cst = 1;
+          cplx<R> hp{R(1), R(0)};
+#pragma unroll
           for (int a = 0; a < D; ++a) {
             cell[a] = g[a] - 1 + ((e >> a) & 1);
             cidx += (long long)cell[a] * cst;
             cst *= n;
+            hp = a == 0 ? hcell[cell[a]] : hp * hcell[cell[a]];
           }
+          const int gl = ((1 << D) - 1) ^ e;
           cplx<R> loc = cz<R>();
+#pragma unroll
           for (int q = 0; q < (1 << D); ++q) {
-            cplx<R> w{R(1), R(0)};
             long long xi = 0, st = 1;
+#pragma unroll
             for (int a = 0; a < D; ++a) {
-              int ag = 1 - ((e >> a) & 1), aq = (q >> a) & 1;
-              w = w * rmul((ag == aq ? R(2) : R(1)) / R(6), hcell[cell[a]]);
-              xi += (long long)(cell[a] + aq) * xs * st;
+              xi += (long long)(cell[a] + ((q >> a) & 1)) * xs * st;
               st *= Nx;
             }
-            loc = cfma(w, x[xi], loc);
+            loc = rfma(R(mass_weight<D>(gl, q)), x[xi], loc);
           }
-          m = m + rmul(phic[cidx], loc);
+          m = cfma(rmul(phic[cidx], hp), loc, m);
         }
-        acc = acc - m;
+        acc = acc - rmul(R(MassScale<D>::inv6), m);
       }
       v = (b != nullptr) ? b[i] - acc : acc;
       nrm += (double)v.x * (double)v.x + (double)v.y * (double)v.y;
