@@ -393,6 +393,8 @@ def measure_forms(mg, torch, peaks):
     s.close()
     out["csg_sweep"] = csg_sweep(mg, torch)
     out["channel_table2"] = channel_table2(mg, torch)
+    out["four_d"] = four_d(mg, torch, peaks)
+    out["dimension_study"] = dimension_study(mg, torch)
     return out
 
 
@@ -481,6 +483,105 @@ def channel_table2(mg, torch, iters=50):
     return {"iterations": iters, "depth": 4, "seconds": time.perf_counter() - t0, "runs": rows}
 
 
+def poisson_rhs(d, depth):
+    """Section 7.1: f = d pi^2 prod_i sin(pi x_i) (phi = 0, theta = 0)."""
+    n = 3 ** depth
+    s1 = np.sin(math.pi * np.arange(n + 1) / n)
+    s = np.ones((1,) * d)
+    for ax in range(d):
+        shape = [1] * d
+        shape[ax] = n + 1
+        s = s * s1.reshape(shape)
+    return (d * math.pi ** 2 * s).astype(np.complex128)
+
+
+def four_d(mg, torch, peaks, depth=4, cycles=50):
+    """The four-dimensional path at depth 4 (82^4 vertices, 80^4 unknowns):
+    device time per additive cycle (exponential damping, omega = 0.8, one
+    CUDA graph per cycle) and the fine operator's ten-pass chain timed alone
+    with events (instrumented pass).  The chain moves 384 B per vertex
+    (7 passes read 1 and write 1 array, 2 read 2, the last reads 3), the
+    operator's own operands are 48 B (u, b read, r written).  It is bound by
+    FP64 issue: with real rows (Poisson, no layer) a pass is 3 real x complex
+    taps (10 flops), plus 3 complex adds of partial sums and the subtraction
+    from b: 108 FP64 flops per vertex."""
+    d = 4
+    s = mg.Solver(d, depth, W.constant_k2(d, depth, 0.0), 0.0, 0.0)
+    stream = torch.cuda.current_stream()
+    s.set_stream(stream.cuda_stream)
+    s.set_rhs(poisson_rhs(d, depth))
+    om = mg.omega_scheme(mg.MG_OMEGA_EXP, 0.8, depth)
+    for _ in range(3):
+        s.cycle(mg.MG_ADD, om, mg.MG_DLINEAR)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for _ in range(cycles):
+        s.cycle(mg.MG_ADD, om, mg.MG_DLINEAR)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    ms = ev[0].elapsed_time(ev[1]) / cycles
+    s.get_stats()
+    s.set_timing(True)
+    for _ in range(10):
+        s.cycle(mg.MG_ADD, om, mg.MG_DLINEAR)
+    _, nfine, fine_ms = s.get_stats()
+    s.set_timing(False)
+    apply_ms = fine_ms / max(nfine, 1)
+    nv = (3 ** depth + 1) ** d
+    interior = (3 ** depth - 1) ** d
+    chain_gbs = 384.0 * nv / (apply_ms / 1e3) / 1e9
+    _, rel = s.last_cycle_norm()
+    s.close()
+    flops = 108.0 * nv
+    return {"depth": depth, "vertices": nv, "ms_per_cycle": ms, "dof_updates_per_s": interior / (ms / 1e3),
+            "fine_apply_ms": apply_ms, "fine_apply_fp64_tflops": flops / (apply_ms / 1e3) / 1e12,
+            "fine_apply_frac_of_fp64_peak": flops / (apply_ms / 1e3) / FP64_PEAK_FLOPS,
+            "fine_apply_chain_gbs": chain_gbs,
+            "fine_apply_chain_frac_of_hbm": chain_gbs / peaks.get("hbm_gbs", 6800.0),
+            "fine_apply_operand_gbs": 48.0 * nv / (apply_ms / 1e3) / 1e9, "rel_res_after": rel}
+
+
+def dimension_study(mg, torch, cycles=300):
+    """Regular-grid counterpart of the dimension study of Section 7.1: the
+    Poisson problem (phi = 0, theta = 0, f = d pi^2 prod sin(pi x_i), u0 = 0)
+    for p = 2, 3, 4 on every depth up to the largest of each dimension,
+    additive multigrid with exponential damping, the transition scheme and
+    undamped coarse grid corrections for omega = 0.6, 0.8, 1.0.  Per run:
+    cycles to a relative residual of 1e-8 (None if not within the limit or
+    diverged) and the mean reduction per cycle from cycle 5 on."""
+    rows = []
+    t0 = time.perf_counter()
+    depths = {2: (2, 3, 4, 5, 6), 3: (2, 3, 4, 5), 4: (2, 3, 4)}
+    schemes = {"exp": mg.MG_OMEGA_EXP, "transition": mg.MG_OMEGA_TRANSITION, "ucg": mg.MG_OMEGA_UCG}
+    for d, ds in depths.items():
+        for depth in ds:
+            s = mg.Solver(d, depth, W.constant_k2(d, depth, 0.0), 0.0, 0.0)
+            s.set_rhs(poisson_rhs(d, depth))
+            for name, sch in schemes.items():
+                for w in (0.6, 0.8, 1.0):
+                    s.set_solution(np.zeros(s.shape, complex))
+                    s.residual_norm()
+                    hist, hit = [], None
+                    for k in range(1, cycles + 2):
+                        s.cycle(mg.MG_ADD, mg.omega_scheme(sch, w, depth, k), mg.MG_DLINEAR)
+                        rel = s.last_cycle_norm()[1]  # residual after k - 1 cycles
+                        hist.append(rel)
+                        if rel <= 1e-8:
+                            hit = k - 1
+                            break
+                        if not np.isfinite(rel) or rel > 1e6:
+                            break
+                    end = len(hist) - 1
+                    rate = float("nan")
+                    if end > 5 and hist[5] > 0 and np.isfinite(hist[end]):
+                        rate = (hist[end] / hist[5]) ** (1.0 / (end - 5))
+                    rows.append({"p": d, "depth": depth, "scheme": name, "omega": w, "cycles_to_1e-8": hit,
+                                 "rel_res": float(hist[-1]), "rate_per_cycle": float(rate)})
+            s.close()
+    return {"cycles_max": cycles, "variant": "add, d-linear", "seconds": time.perf_counter() - t0, "runs": rows}
+
+
 # ---------------------------------------------------------------- main
 def main():
     ap = argparse.ArgumentParser()
@@ -491,7 +592,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
-    ap.add_argument("--form", choices=["csg_sweep", "channel_table2"], default=None,
+    ap.add_argument("--form", choices=["csg_sweep", "channel_table2", "four_d", "dimension_study"], default=None,
                     help="run only this form and print its result (profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -517,7 +618,10 @@ def main():
     B.build()
     mg.load()
     if args.form is not None:
-        fn = {"csg_sweep": csg_sweep, "channel_table2": channel_table2}[args.form]
+        peaks, _ = measured_peaks()
+        fn = {"csg_sweep": lambda m, t: csg_sweep(m, t), "channel_table2": lambda m, t: channel_table2(m, t),
+              "four_d": lambda m, t: four_d(m, t, peaks),
+              "dimension_study": lambda m, t: dimension_study(m, t)}[args.form]
         print(json.dumps({"form": args.form, "result": fn(mg, torch)}), flush=True)
         return
 

@@ -132,6 +132,9 @@ struct Lev4 {
   cplx<double>* rows = nullptr;  // [M, K, K - phi M][n + 1][3] of this level's operator
   cplx<double>* grows = nullptr; // same for G = R H P on level l - 1 (l > 1)
   cplx<double>* invd = nullptr;  // [256] inverse diagonal by vertex type
+  cplx<double>* omd = nullptr;   // [256] omega / D of the current cycle
+  bool real = false;             // every row of `rows` is real
+  bool greal = false;            // every row of `grows` is real
 };
 
 struct Hier4 {
@@ -1524,6 +1527,7 @@ int d4_build(mg_ctx* c) {
       for (int i = 0; i <= V.n; ++i)
         for (int j = 0; j < 3; ++j) rows[((size_t)k * (V.n + 1) + i) * 3 + j] = row[typ[i]][3 * k + j];
     if ((rc = d4_upload(c, *H, &V.rows, rows)) != MG_OK) return rc;
+    V.real = std::all_of(rows.begin(), rows.end(), [](const cplx<double>& v) { return v.y == 0.0; });
     std::vector<cplx<double>> invd(256);
     for (int ty = 0; ty < 256; ++ty) {
       cd mprod(1.0), kterm(0.0);
@@ -1543,6 +1547,7 @@ int d4_build(mg_ctx* c) {
       invd[ty] = cplx<double>{q.real(), q.imag()};
     }
     if ((rc = d4_upload(c, *H, &V.invd, invd)) != MG_OK) return rc;
+    if ((rc = d4_alloc(c, *H, (void**)&V.omd, 256 * sizeof(cplx<double>))) != MG_OK) return rc;
     if (l > 1) {
       std::vector<std::array<cd, 6>> g;
       galerkin_rows_1d(V.n, rot, widths(c, V.n), g);
@@ -1556,6 +1561,7 @@ int d4_build(mg_ctx* c) {
           gr[((size_t)2 * (nc + 1) + i) * 3 + j] = cplx<double>{kp.real(), kp.imag()};
         }
       if ((rc = d4_upload(c, *H, &V.grows, gr)) != MG_OK) return rc;
+      V.greal = std::all_of(gr.begin(), gr.end(), [](const cplx<double>& v) { return v.y == 0.0; });
     }
   }
   const size_t fb = H->lev[L].nv * sizeof(cplx<double>);
@@ -1573,8 +1579,8 @@ size_t box4_size(const mg::Box4& B) { return (size_t)B.n[0] * B.n[1] * B.n[2] * 
 
 // y = beta b + sgn (A x): A the separable operator with rows [M, K, K - phi M]
 // per index on a grid of n cells per axis (ten passes through T[0..3]).
-cudaError_t d4_apply(mg_ctx* c, int n, const cplx<double>* rows, const cplx<double>* x, const cplx<double>* b,
-                     cplx<double>* y, double sgn) {
+cudaError_t d4_apply(mg_ctx* c, int n, const cplx<double>* rows, bool real, const cplx<double>* x,
+                     const cplx<double>* b, cplx<double>* y, double sgn) {
   Hier4& H = *c->h4;
   const int N = n + 1;
   const mg::Box4 B = box4(N, N, N, N);
@@ -1585,20 +1591,23 @@ cudaError_t d4_apply(mg_ctx* c, int n, const cplx<double>* rows, const cplx<doub
   cplx<double>** T = H.T;
   const cplx<double>* nul = nullptr;
   auto pass = [&](int axis, const cplx<double>* r, const cplx<double>* in, const cplx<double>* z,
-                  const cplx<double>* bb, cplx<double>* out, double sg) {
+                  const cplx<double>* bb, cplx<double>* out, int neg) {
     ++c->launches;
-    mg::pass4_kernel<<<g, kThreads, 0, c->stream>>>(B, axis, r, in, z, bb, out, sg);
+    if (real)
+      mg::pass4_kernel<true><<<g, kThreads, 0, c->stream>>>(B, axis, r, in, z, bb, out, neg);
+    else
+      mg::pass4_kernel<false><<<g, kThreads, 0, c->stream>>>(B, axis, r, in, z, bb, out, neg);
   };
-  pass(3, M, x, nul, nul, T[0], 1.0);            // A = M3 x
-  pass(3, KP, x, nul, nul, T[1], 1.0);           // B = (K3 - phi M3) x
-  pass(2, M, T[0], nul, nul, T[2], 1.0);         // C = M2 A
-  pass(2, M, T[1], nul, nul, T[3], 1.0);         // M2 B
-  pass(2, K, T[0], T[3], nul, T[1], 1.0);        // D = K2 A + M2 B
-  pass(1, M, T[1], nul, nul, T[3], 1.0);         // M1 D
-  pass(1, K, T[2], T[3], nul, T[0], 1.0);        // E = K1 C + M1 D
-  pass(1, M, T[2], nul, nul, T[1], 1.0);         // F = M1 C
-  pass(0, K, T[1], nul, nul, T[2], 1.0);         // K0 F
-  pass(0, M, T[0], T[2], b, y, sgn);             // y = b + sgn (M0 E + K0 F)
+  pass(3, M, x, nul, nul, T[0], 0);              // A = M3 x
+  pass(3, KP, x, nul, nul, T[1], 0);             // B = (K3 - phi M3) x
+  pass(2, M, T[0], nul, nul, T[2], 0);           // C = M2 A
+  pass(2, M, T[1], nul, nul, T[3], 0);           // M2 B
+  pass(2, K, T[0], T[3], nul, T[1], 0);          // D = K2 A + M2 B
+  pass(1, M, T[1], nul, nul, T[3], 0);           // M1 D
+  pass(1, K, T[2], T[3], nul, T[0], 0);          // E = K1 C + M1 D
+  pass(1, M, T[2], nul, nul, T[1], 0);           // F = M1 C
+  pass(0, K, T[1], nul, nul, T[2], 0);           // K0 F
+  pass(0, M, T[0], T[2], b, y, sgn < 0 ? 1 : 0); // y = b -+ (M0 E + K0 F)
   return cudaGetLastError();
 }
 
@@ -1614,7 +1623,10 @@ cudaError_t d4_mass(mg_ctx* c, const cplx<double>* f, cplx<double>* b) {
   cplx<double>* out[4] = {H.T[0], H.T[1], H.T[0], b};
   for (int k = 0; k < 4; ++k) {
     ++c->launches;
-    mg::pass4_kernel<<<g, kThreads, 0, c->stream>>>(B, 3 - k, V.rows, in[k], nul, nul, out[k], 1.0);
+    if (V.real)
+      mg::pass4_kernel<true><<<g, kThreads, 0, c->stream>>>(B, 3 - k, V.rows, in[k], nul, nul, out[k], 0);
+    else
+      mg::pass4_kernel<false><<<g, kThreads, 0, c->stream>>>(B, 3 - k, V.rows, in[k], nul, nul, out[k], 0);
   }
   return cudaGetLastError();
 }
@@ -1637,10 +1649,10 @@ cudaError_t d4_restrict(mg_ctx* c, int n, const cplx<double>* x, cplx<double>* y
   return cudaGetLastError();
 }
 
-// y = base + sgn P x for x on level l - 1 (n fine cells per axis), through
-// T[1], T[2].
+// y = base + P x (or base - P x with neg) for x on level l - 1 (n fine cells
+// per axis), through T[1], T[2].
 cudaError_t d4_prolong(mg_ctx* c, int n, const cplx<double>* x, const cplx<double>* base, cplx<double>* y,
-                       double sgn) {
+                       int neg) {
   Hier4& H = *c->h4;
   const int N = n + 1, Nc = n / 3 + 1;
   int ext[4] = {Nc, Nc, Nc, Nc};
@@ -1652,7 +1664,7 @@ cudaError_t d4_prolong(mg_ctx* c, int n, const cplx<double>* x, const cplx<doubl
     const bool last = a == 3;
     ++c->launches;
     mg::prolong4_kernel<<<grid_for(box4_size(B)), kThreads, 0, c->stream>>>(
-        B, a, src, last ? base : nullptr, dst[a], last ? sgn : 1.0);
+        B, a, src, last ? base : nullptr, dst[a], last ? neg : 0);
     src = dst[a];
   }
   return cudaGetLastError();
@@ -1678,28 +1690,28 @@ cudaError_t d4_enqueue_cycle(mg_ctx* c, int hb, int hier, const cplx<double>* om
   for (int l = L; l >= 1 && e == cudaSuccess; --l) {
     Lev4& V = H.lev[l];
     if (l == L && c->timing) e = cudaEventRecord(c->ev[c->ev_used], c->stream);
-    if (e == cudaSuccess) e = d4_apply(c, V.n, V.rows, V.u, V.b, H.T[4], -1.0);  // r_l
+    if (e == cudaSuccess) e = d4_apply(c, V.n, V.rows, V.real, V.u, V.b, H.T[4], -1.0);  // r_l
     if (l == L && c->timing && e == cudaSuccess) e = cudaEventRecord(c->ev[c->ev_used + 1], c->stream);
     if (e != cudaSuccess) break;
-    ++c->launches;
-    const cplx<double> w = omega[l - 1];
+    c->launches += 2;
+    mg::omega_table4_kernel<<<1, 256, 0, c->stream>>>(V.invd, omega[l - 1], V.omd);
     mg::jacobi4_kernel<<<grid_for(V.nv), kThreads, 0, c->stream>>>(
-        V.n, H.T[4], V.t, V.typ, V.invd, w, hb, H.partial, H.ticket, l == L ? H.norm2 : nullptr);
+        V.n, H.T[4], V.t, V.typ, V.omd, hb, H.partial, H.ticket, l == L ? H.norm2 : nullptr);
     if (l > 1) {
       Lev4& W = H.lev[l - 1];
       e = d4_inject(c, V.n, V.u, W.u);
       if (e == cudaSuccess) e = d4_restrict(c, V.n, H.T[4], W.b);
-      if (e == cudaSuccess) e = d4_apply(c, W.n, V.grows, W.u, W.b, W.b, 1.0);  // + G u_{l-1}
+      if (e == cudaSuccess) e = d4_apply(c, W.n, V.grows, V.greal, W.u, W.b, W.b, 1.0);  // + G u_{l-1}
       if (hier && e == cudaSuccess) {
         // BPX transfer: T du = du - P I du
         e = d4_inject(c, V.n, V.t, H.T[0]);
-        if (e == cudaSuccess) e = d4_prolong(c, V.n, H.T[0], V.t, V.t, -1.0);
+        if (e == cudaSuccess) e = d4_prolong(c, V.n, H.T[0], V.t, V.t, 1);
       }
     }
     if (e == cudaSuccess) e = cudaGetLastError();
   }
   for (int l = 2; l <= L && e == cudaSuccess; ++l)
-    e = d4_prolong(c, H.lev[l].n, H.lev[l - 1].corr, H.lev[l].t, H.lev[l].corr, 1.0);
+    e = d4_prolong(c, H.lev[l].n, H.lev[l - 1].corr, H.lev[l].t, H.lev[l].corr, 0);
   if (e == cudaSuccess) {
     const Lev4& F = H.lev[L];
     ++c->launches;
@@ -1779,7 +1791,7 @@ int d4_cycle(mg_ctx* c, int hb, int hier, const cplx<double>* omega) {
 cudaError_t d4_residual(mg_ctx* c, int slot) {
   Hier4& H = *c->h4;
   const Lev4& V = H.lev[c->L];
-  cudaError_t e = d4_apply(c, V.n, V.rows, V.u, V.b, H.T[4], -1.0);
+  cudaError_t e = d4_apply(c, V.n, V.rows, V.real, V.u, V.b, H.T[4], -1.0);
   if (e == cudaSuccess && slot >= 0) {
     ++c->launches;
     mg::norm4_kernel<<<grid_for(V.nv), kThreads, 0, c->stream>>>(V.n, H.T[4], H.partial, H.ticket + 1,

@@ -9,10 +9,13 @@
 // so H u is ten 3-tap passes along single axes; the Galerkin operator
 // G = R H P of the coarse right-hand side has the same form with the 1D
 // Galerkin rows, and R, P, I act axis by axis.  Every kernel here is one such
-// pass over a 4D box (axis 0 fastest): coalesced, HBM-bound, one thread per
-// output vertex.  A pass zeroes its outputs on the two boundary planes of its
-// own axis; the other coordinates carry through, so a chain of passes gives
-// the interior rows of the product and zero Dirichlet rows.
+// pass over a 4D box (axis 0 fastest): coalesced, one thread per output
+// vertex.  GB300 issues 2 FP64 FMA per clock per SM, about 3 per 32 bytes of
+// HBM traffic, so the passes are bound by their FP64 work, not by memory:
+// they count FP64 operations (real rows take real x complex products).  A
+// pass zeroes its outputs on the two boundary planes of its own axis; the
+// other coordinates carry through, so a chain of passes gives the interior
+// rows of the product and zero Dirichlet rows.
 #pragma once
 #include "mg_kernels.cuh"
 
@@ -39,12 +42,22 @@ __device__ __forceinline__ unsigned box4_index(const Box4& B, const int* c) {
   return (((unsigned)c[3] * B.n[2] + c[2]) * B.n[1] + c[1]) * B.n[0] + c[0];
 }
 
-// y = beta b + sgn (A x + z), A the 3-tap rows along `axis` (rows[3 i + k]
-// couples coordinate i with i - 1 + k); zero on the axis' boundary planes.
-// b and z may be null; y may alias b (element-wise update).
+// True when the double is +0 or -0, tested on its bits: an FP64 comparison
+// issues on the FP64 pipe, which these kernels are bound by (measured: a
+// three-way imaginary-part test doubled the time of a pass).
+__device__ __forceinline__ bool zero_bits(double v) {
+  return (static_cast<unsigned long long>(__double_as_longlong(v)) << 1) == 0ull;
+}
+
+// y = b + (A x + z) or y = b - (A x + z) (neg), A the 3-tap rows along
+// `axis` (rows[3 i + k] couples coordinate i with i - 1 + k); zero on the
+// axis' boundary planes.  b and z may be null; y may alias b (element-wise
+// update).  Real rows (cells outside the layer) take real x complex products,
+// half the FMAs: REAL when every row of the table is real, else per row.
+template <bool REAL>
 __global__ void pass4_kernel(Box4 B, int axis, const cplx<double>* __restrict__ rows,
                              const cplx<double>* __restrict__ x, const cplx<double>* __restrict__ z,
-                             const cplx<double>* b, cplx<double>* y, double sgn) {
+                             const cplx<double>* b, cplx<double>* y, int neg) {
   const unsigned total = box4_total(B);
   unsigned s = 1;
   for (int a = 0; a < axis; ++a) s *= (unsigned)B.n[a];
@@ -53,14 +66,25 @@ __global__ void pass4_kernel(Box4 B, int axis, const cplx<double>* __restrict__ 
     const int ca = (int)((i / s) % (unsigned)na);
     cplx<double> v = cz<double>();
     if (ca > 0 && ca < na - 1) {
-      const cplx<double>* r = rows + 3 * ca;
-      v = r[0] * x[i - s];
-      v = cfma(r[1], x[i], v);
-      v = cfma(r[2], x[i + s], v);
+      const cplx<double> r0 = rows[3 * ca], r1 = rows[3 * ca + 1], r2 = rows[3 * ca + 2];
+      const cplx<double> xm = x[i - s], x0 = x[i], xp = x[i + s];
+      if (REAL || (zero_bits(r0.y) && zero_bits(r1.y) && zero_bits(r2.y))) {
+        v = rmul(r0.x, xm);
+        v = rfma(r1.x, x0, v);
+        v = rfma(r2.x, xp, v);
+      } else {
+        v = r0 * xm;
+        v = cfma(r1, x0, v);
+        v = cfma(r2, xp, v);
+      }
       if (z != nullptr) v = v + z[i];
     }
-    v = rmul(sgn, v);
-    if (b != nullptr) v = b[i] + v;
+    if (b != nullptr) {
+      const cplx<double> bi = b[i];
+      v = neg ? cplx<double>{bi.x - v.x, bi.y - v.y} : bi + v;
+    } else if (neg) {
+      v = cplx<double>{-v.x, -v.y};
+    }
     y[i] = v;
   }
 }
@@ -96,9 +120,9 @@ __global__ void restrict4_kernel(Box4 Bout, int axis, int nf, const cplx<double>
 
 // d-linear interpolation along `axis`: the output box has n_f = 3 (n_c - 1) + 1
 // points along the axis; fine 3c + o takes (1 - o/3) x[c] + (o/3) x[c+1].
-// y = base + sgn P x (base may be null; y may alias base).
+// y = base + P x or base - P x (neg); base may be null, y may alias base.
 __global__ void prolong4_kernel(Box4 Bout, int axis, const cplx<double>* __restrict__ x,
-                                const cplx<double>* base, cplx<double>* y, double sgn) {
+                                const cplx<double>* base, cplx<double>* y, int neg) {
   const unsigned total = box4_total(Bout);
   Box4 Bin = Bout;
   Bin.n[axis] = (Bout.n[axis] - 1) / 3 + 1;
@@ -114,12 +138,16 @@ __global__ void prolong4_kernel(Box4 Bout, int axis, const cplx<double>* __restr
     if (o == 0) {
       v = x[j];
     } else {
-      const double w1 = o == 1 ? 1.0 / 3.0 : 2.0 / 3.0;
-      v = rmul(1.0 - w1, x[j]);
+      const double w0 = o == 1 ? 2.0 / 3.0 : 1.0 / 3.0, w1 = o == 1 ? 1.0 / 3.0 : 2.0 / 3.0;
+      v = rmul(w0, x[j]);
       v = rfma(w1, x[j + s], v);
     }
-    v = rmul(sgn, v);
-    if (base != nullptr) v = base[i] + v;
+    if (base != nullptr) {
+      const cplx<double> bi = base[i];
+      v = neg ? cplx<double>{bi.x - v.x, bi.y - v.y} : bi + v;
+    } else if (neg) {
+      v = cplx<double>{-v.x, -v.y};
+    }
     y[i] = v;
   }
 }
@@ -137,16 +165,22 @@ __global__ void inject4_kernel(Box4 Bc, const cplx<double>* __restrict__ x, cplx
   }
 }
 
-// du = omega D^{-1} r at interior vertices (D from the 256-entry table of
-// inverse diagonals by vertex type), zero at c-points for the hierarchical
-// basis variant and on the boundary; |r|^2 over the interior into *norm2
-// (deterministic last-block sum) when norm2 is not null.
+// omd[t] = omega / D_t for the 256 vertex types of a level (one block).
+__global__ void omega_table4_kernel(const cplx<double>* __restrict__ invd, cplx<double> omega,
+                                    cplx<double>* __restrict__ omd) {
+  const int t = threadIdx.x;
+  if (t < 256) omd[t] = omega * invd[t];
+}
+
+// du = omega D^{-1} r at interior vertices (omd: omega / D by vertex type),
+// zero at c-points for the hierarchical basis variant and on the boundary;
+// |r|^2 over the interior into *norm2 (deterministic last-block sum) when
+// norm2 is not null.
 __global__ void __launch_bounds__(256) jacobi4_kernel(int n, const cplx<double>* __restrict__ r,
                                                       cplx<double>* __restrict__ t,
                                                       const uint8_t* __restrict__ typ,
-                                                      const cplx<double>* __restrict__ invd,
-                                                      cplx<double> omega, int hb, double* partial,
-                                                      unsigned* ticket, double* norm2) {
+                                                      const cplx<double>* __restrict__ omd, int hb,
+                                                      double* partial, unsigned* ticket, double* norm2) {
   Box4 B;
   for (int a = 0; a < 4; ++a) B.n[a] = n + 1;
   const unsigned total = box4_total(B);
@@ -167,7 +201,10 @@ __global__ void __launch_bounds__(256) jacobi4_kernel(int n, const cplx<double>*
       for (int a = 3; a >= 0; --a) ty = 4 * ty + (int)typ[c[a]];
       const cplx<double> ri = r[i];
       nrm = fma(ri.x, ri.x, fma(ri.y, ri.y, nrm));
-      if (!(hb && cpt)) du = (omega * invd[ty]) * ri;
+      if (!(hb && cpt)) {
+        const cplx<double> q = omd[ty];
+        du = zero_bits(q.y) ? rmul(q.x, ri) : q * ri;
+      }
     }
     t[i] = du;
   }
