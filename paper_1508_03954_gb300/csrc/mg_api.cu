@@ -118,31 +118,34 @@ struct Hier {
   std::vector<void*> allocs;
 };
 
-// Four-dimensional hierarchy (mg_dim4.cuh): per level the solution (coarse:
-// the injected copy), b, T du, the correction, and the separable operator
-// as per-index 1D rows; fine-size temporaries for the pass chains.
+// Four-dimensional hierarchy (mg_dim4.cuh) in precision R: per level the
+// solution (coarse: the injected copy), b, T du, the correction, and the
+// separable operator as per-index 1D rows; fine-size temporaries for the
+// pass chains.
+template <typename R>
 struct Lev4 {
   int n = 0;
   size_t nv = 0;
-  cplx<double>* u = nullptr;
-  cplx<double>* b = nullptr;
-  cplx<double>* t = nullptr;
-  cplx<double>* corr = nullptr;  // level 1: aliases t
-  uint8_t* typ = nullptr;        // vertex type per axis index
-  cplx<double>* rows = nullptr;  // [M, K, K - phi M][n + 1][3] of this level's operator
-  cplx<double>* grows = nullptr; // same for G = R H P on level l - 1 (l > 1)
-  cplx<double>* invd = nullptr;  // [256] inverse diagonal by vertex type
-  cplx<double>* omd = nullptr;   // [256] omega / D of the current cycle
-  bool real = false;             // every row of `rows` is real
-  bool greal = false;            // every row of `grows` is real
+  cplx<R>* u = nullptr;
+  cplx<R>* b = nullptr;
+  cplx<R>* t = nullptr;
+  cplx<R>* corr = nullptr;   // level 1: aliases t
+  uint8_t* typ = nullptr;    // vertex type per axis index
+  cplx<R>* rows = nullptr;   // [M, K, K - phi M][n + 1][3] of this level's operator
+  cplx<R>* grows = nullptr;  // same for G = R H P on level l - 1 (l > 1)
+  cplx<R>* invd = nullptr;   // [256] inverse diagonal by vertex type
+  cplx<R>* omd = nullptr;    // [256] omega / D of the current cycle
+  bool real = false;         // every row of `rows` is real
+  bool greal = false;        // every row of `grows` is real
 };
 
+template <typename R>
 struct Hier4 {
-  std::vector<Lev4> lev;      // 1..L
-  cplx<double>* T[5] = {};    // fine-size temporaries; T[4] holds the residual
+  std::vector<Lev4<R>> lev;   // 1..L
+  cplx<R>* T[5] = {};         // fine-size temporaries; T[4] holds the residual
   double* partial = nullptr;  // block partials of the norms
   unsigned* ticket = nullptr;
-  double* norm2 = nullptr;    // [0] cycle norm, [1] standalone norm
+  double* norm2 = nullptr;    // [0] cycle norm, [1] standalone norm, [2] max modulus (bits)
   std::vector<void*> allocs;
   cudaGraphExec_t exec = nullptr;  // the last captured cycle
   std::vector<double> key;
@@ -158,7 +161,8 @@ struct mg_ctx {
   cudaStream_t stream = 0;
   Hier<double> h64;
   Hier<float> h32;
-  Hier4* h4 = nullptr;                 // d = 4
+  Hier4<double>* h4 = nullptr;         // d = 4
+  Hier4<float>* h4f = nullptr;         // d = 4, complex64 inner cycles
   int precision = MG_C128;
   int inner_cycles = 4;
   double r0 = -1.0;                    // reference residual norm
@@ -1464,51 +1468,60 @@ int set_level_rhs(mg_ctx* c, int s) {
 }
 
 // ------------------------------------------------------------------ d = 4
-int d4_alloc(mg_ctx* c, Hier4& H, void** p, size_t bytes) {
+template <typename H>
+int d4_alloc(mg_ctx* c, H& h, void** p, size_t bytes) {
   cudaError_t e = cudaMalloc(p, bytes);
   if (e != cudaSuccess) {
     *p = nullptr;
     return fail(c, e == cudaErrorMemoryAllocation ? MG_ERR_OOM : MG_ERR_CUDA,
                 std::string("cudaMalloc: ") + cudaGetErrorString(e));
   }
-  H.allocs.push_back(*p);
+  h.allocs.push_back(*p);
   MG_CUDA(c, cudaMemset(*p, 0, bytes));
   return MG_OK;
 }
 
-void d4_free(Hier4* H) {
+template <typename R>
+void d4_free(Hier4<R>* H) {
   if (H == nullptr) return;
   if (H->exec) cudaGraphExecDestroy(H->exec);
   for (void* p : H->allocs) cudaFree(p);
   delete H;
 }
 
-template <typename T>
-int d4_upload(mg_ctx* c, Hier4& H, T** dst, const std::vector<T>& v) {
-  int rc = d4_alloc(c, H, (void**)dst, v.size() * sizeof(T));
+template <typename H, typename T>
+int d4_upload(mg_ctx* c, H& h, T** dst, const std::vector<T>& v) {
+  int rc = d4_alloc(c, h, (void**)dst, v.size() * sizeof(T));
   if (rc != MG_OK) return rc;
   MG_CUDA(c, cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
   return MG_OK;
 }
 
-// Per-level arrays and the separable operator tables: the rows of each axis
-// index are those of its vertex type (left / right cell in the layer), the
-// Galerkin rows those of galerkin_rows_1d, the diagonal of vertex type
-// (t0, t1, t2, t3) is sum_j prod_a (K if a == j else M)[t_a] centre entries
-// minus phi prod_a M[t_a] centre (the tensor-product form of Section 3).
-int d4_build(mg_ctx* c) {
-  Hier4* H = new (std::nothrow) Hier4();
+template <typename R>
+cplx<R> to_r(const cd& v) {
+  return cplx<R>{(R)v.real(), (R)v.imag()};
+}
+
+// Per-level arrays and the separable operator tables, formed in FP64 and
+// stored in R: the rows of each axis index are those of its vertex type
+// (left / right cell in the layer), the Galerkin rows those of
+// galerkin_rows_1d, the diagonal of vertex type (t0, t1, t2, t3) is
+// sum_j prod_a (K if a == j else M)[t_a] centre entries minus
+// phi prod_a M[t_a] centre (the tensor-product form of Section 3).
+template <typename R>
+int d4_build(mg_ctx* c, Hier4<R>*& out) {
+  Hier4<R>* H = new (std::nothrow) Hier4<R>();
   if (H == nullptr) return fail(c, MG_ERR_OOM, "host allocation failed");
-  c->h4 = H;
+  out = H;
   const int L = c->L;
   const double phi = c->k2[0];
   H->lev.resize(L + 1);
   int rc;
   for (int l = 1; l <= L; ++l) {
-    Lev4& V = H->lev[l];
+    Lev4<R>& V = H->lev[l];
     V.n = (int)ipow(3, l);
     V.nv = (size_t)ipow(V.n + 1, 4);
-    const size_t bytes = V.nv * sizeof(cplx<double>);
+    const size_t bytes = V.nv * sizeof(cplx<R>);
     if ((rc = d4_alloc(c, *H, (void**)&V.u, bytes)) != MG_OK) return rc;
     if ((rc = d4_alloc(c, *H, (void**)&V.b, bytes)) != MG_OK) return rc;
     if ((rc = d4_alloc(c, *H, (void**)&V.t, bytes)) != MG_OK) return rc;
@@ -1522,13 +1535,16 @@ int d4_build(mg_ctx* c) {
     if ((rc = d4_upload(c, *H, &V.typ, typ)) != MG_OK) return rc;
     cplx<double> row[4][9];
     axis_rows(c, V.n, row);
-    std::vector<cplx<double>> rows((size_t)3 * (V.n + 1) * 3);
+    std::vector<cplx<R>> rows((size_t)3 * (V.n + 1) * 3);
     for (int k = 0; k < 3; ++k)
       for (int i = 0; i <= V.n; ++i)
-        for (int j = 0; j < 3; ++j) rows[((size_t)k * (V.n + 1) + i) * 3 + j] = row[typ[i]][3 * k + j];
+        for (int j = 0; j < 3; ++j) {
+          const cplx<double>& v = row[typ[i]][3 * k + j];
+          rows[((size_t)k * (V.n + 1) + i) * 3 + j] = cplx<R>{(R)v.x, (R)v.y};
+        }
     if ((rc = d4_upload(c, *H, &V.rows, rows)) != MG_OK) return rc;
-    V.real = std::all_of(rows.begin(), rows.end(), [](const cplx<double>& v) { return v.y == 0.0; });
-    std::vector<cplx<double>> invd(256);
+    V.real = std::all_of(rows.begin(), rows.end(), [](const cplx<R>& v) { return v.y == R(0); });
+    std::vector<cplx<R>> invd(256);
     for (int ty = 0; ty < 256; ++ty) {
       cd mprod(1.0), kterm(0.0);
       for (int j = 0; j < 4; ++j) {
@@ -1543,28 +1559,27 @@ int d4_build(mg_ctx* c) {
         const auto& r = row[(ty >> (2 * a)) & 3];
         mprod *= cd(r[1].x, r[1].y);
       }
-      const cd q = 1.0 / (kterm - phi * mprod);
-      invd[ty] = cplx<double>{q.real(), q.imag()};
+      invd[ty] = to_r<R>(1.0 / (kterm - phi * mprod));
     }
     if ((rc = d4_upload(c, *H, &V.invd, invd)) != MG_OK) return rc;
-    if ((rc = d4_alloc(c, *H, (void**)&V.omd, 256 * sizeof(cplx<double>))) != MG_OK) return rc;
+    if ((rc = d4_alloc(c, *H, (void**)&V.omd, 256 * sizeof(cplx<R>))) != MG_OK) return rc;
     if (l > 1) {
       std::vector<std::array<cd, 6>> g;
       galerkin_rows_1d(V.n, rot, widths(c, V.n), g);
       const int nc = V.n / 3;
-      std::vector<cplx<double>> gr((size_t)3 * (nc + 1) * 3);
+      std::vector<cplx<R>> gr((size_t)3 * (nc + 1) * 3);
       for (int i = 0; i <= nc; ++i)
         for (int j = 0; j < 3; ++j) {
           const cd m = g[i][3 + j], k = g[i][j], kp = k - phi * m;
-          gr[((size_t)0 * (nc + 1) + i) * 3 + j] = cplx<double>{m.real(), m.imag()};
-          gr[((size_t)1 * (nc + 1) + i) * 3 + j] = cplx<double>{k.real(), k.imag()};
-          gr[((size_t)2 * (nc + 1) + i) * 3 + j] = cplx<double>{kp.real(), kp.imag()};
+          gr[((size_t)0 * (nc + 1) + i) * 3 + j] = to_r<R>(m);
+          gr[((size_t)1 * (nc + 1) + i) * 3 + j] = to_r<R>(k);
+          gr[((size_t)2 * (nc + 1) + i) * 3 + j] = to_r<R>(kp);
         }
       if ((rc = d4_upload(c, *H, &V.grows, gr)) != MG_OK) return rc;
-      V.greal = std::all_of(gr.begin(), gr.end(), [](const cplx<double>& v) { return v.y == 0.0; });
+      V.greal = std::all_of(gr.begin(), gr.end(), [](const cplx<R>& v) { return v.y == R(0); });
     }
   }
-  const size_t fb = H->lev[L].nv * sizeof(cplx<double>);
+  const size_t fb = H->lev[L].nv * sizeof(cplx<R>);
   for (int k = 0; k < 5; ++k)
     if ((rc = d4_alloc(c, *H, (void**)&H->T[k], fb)) != MG_OK) return rc;
   if ((rc = d4_alloc(c, *H, (void**)&H->partial, 152 * 16 * sizeof(double))) != MG_OK) return rc;
@@ -1577,73 +1592,69 @@ mg::Box4 box4(int n0, int n1, int n2, int n3) { return mg::Box4{{n0, n1, n2, n3}
 
 size_t box4_size(const mg::Box4& B) { return (size_t)B.n[0] * B.n[1] * B.n[2] * B.n[3]; }
 
-// y = beta b + sgn (A x): A the separable operator with rows [M, K, K - phi M]
-// per index on a grid of n cells per axis (ten passes through T[0..3]).
-cudaError_t d4_apply(mg_ctx* c, int n, const cplx<double>* rows, bool real, const cplx<double>* x,
-                     const cplx<double>* b, cplx<double>* y, double sgn) {
-  Hier4& H = *c->h4;
+template <typename R>
+void pass4(mg_ctx* c, const mg::Box4& B, int axis, bool real, const cplx<R>* rows, const cplx<R>* x,
+           const cplx<R>* z, const cplx<R>* b, cplx<R>* y, int neg) {
+  ++c->launches;
+  const int g = grid_for(box4_size(B));
+  if (real)
+    mg::pass4_kernel<R, true><<<g, kThreads, 0, c->stream>>>(B, axis, rows, x, z, b, y, neg);
+  else
+    mg::pass4_kernel<R, false><<<g, kThreads, 0, c->stream>>>(B, axis, rows, x, z, b, y, neg);
+}
+
+// y = b + A x or b - A x (neg): A the separable operator with rows
+// [M, K, K - phi M] per index on a grid of n cells per axis (ten passes
+// through T[0..3]).
+template <typename R>
+cudaError_t d4_apply(mg_ctx* c, Hier4<R>& H, int n, const cplx<R>* rows, bool real, const cplx<R>* x,
+                     const cplx<R>* b, cplx<R>* y, int neg) {
   const int N = n + 1;
   const mg::Box4 B = box4(N, N, N, N);
-  const int g = grid_for(box4_size(B));
-  const cplx<double>* M = rows;
-  const cplx<double>* K = rows + 3 * N;
-  const cplx<double>* KP = rows + 6 * N;
-  cplx<double>** T = H.T;
-  const cplx<double>* nul = nullptr;
-  auto pass = [&](int axis, const cplx<double>* r, const cplx<double>* in, const cplx<double>* z,
-                  const cplx<double>* bb, cplx<double>* out, int neg) {
-    ++c->launches;
-    if (real)
-      mg::pass4_kernel<true><<<g, kThreads, 0, c->stream>>>(B, axis, r, in, z, bb, out, neg);
-    else
-      mg::pass4_kernel<false><<<g, kThreads, 0, c->stream>>>(B, axis, r, in, z, bb, out, neg);
-  };
-  pass(3, M, x, nul, nul, T[0], 0);              // A = M3 x
-  pass(3, KP, x, nul, nul, T[1], 0);             // B = (K3 - phi M3) x
-  pass(2, M, T[0], nul, nul, T[2], 0);           // C = M2 A
-  pass(2, M, T[1], nul, nul, T[3], 0);           // M2 B
-  pass(2, K, T[0], T[3], nul, T[1], 0);          // D = K2 A + M2 B
-  pass(1, M, T[1], nul, nul, T[3], 0);           // M1 D
-  pass(1, K, T[2], T[3], nul, T[0], 0);          // E = K1 C + M1 D
-  pass(1, M, T[2], nul, nul, T[1], 0);           // F = M1 C
-  pass(0, K, T[1], nul, nul, T[2], 0);           // K0 F
-  pass(0, M, T[0], T[2], b, y, sgn < 0 ? 1 : 0); // y = b -+ (M0 E + K0 F)
+  const cplx<R>* M = rows;
+  const cplx<R>* K = rows + 3 * N;
+  const cplx<R>* KP = rows + 6 * N;
+  cplx<R>** T = H.T;
+  const cplx<R>* nul = nullptr;
+  pass4(c, B, 3, real, M, x, nul, nul, T[0], 0);       // A = M3 x
+  pass4(c, B, 3, real, KP, x, nul, nul, T[1], 0);      // B = (K3 - phi M3) x
+  pass4(c, B, 2, real, M, T[0], nul, nul, T[2], 0);    // C = M2 A
+  pass4(c, B, 2, real, M, T[1], nul, nul, T[3], 0);    // M2 B
+  pass4(c, B, 2, real, K, T[0], T[3], nul, T[1], 0);   // D = K2 A + M2 B
+  pass4(c, B, 1, real, M, T[1], nul, nul, T[3], 0);    // M1 D
+  pass4(c, B, 1, real, K, T[2], T[3], nul, T[0], 0);   // E = K1 C + M1 D
+  pass4(c, B, 1, real, M, T[2], nul, nul, T[1], 0);    // F = M1 C
+  pass4(c, B, 0, real, K, T[1], nul, nul, T[2], 0);    // K0 F
+  pass4(c, B, 0, real, M, T[0], T[2], b, y, neg);      // y = b -+ (M0 E + K0 F)
   return cudaGetLastError();
 }
 
 // b = M f on the finest level (four mass passes).
 cudaError_t d4_mass(mg_ctx* c, const cplx<double>* f, cplx<double>* b) {
-  Hier4& H = *c->h4;
-  const Lev4& V = H.lev[c->L];
+  Hier4<double>& H = *c->h4;
+  const Lev4<double>& V = H.lev[c->L];
   const int N = V.n + 1;
   const mg::Box4 B = box4(N, N, N, N);
-  const int g = grid_for(box4_size(B));
   const cplx<double>* nul = nullptr;
   const cplx<double>* in[4] = {f, H.T[0], H.T[1], H.T[0]};
   cplx<double>* out[4] = {H.T[0], H.T[1], H.T[0], b};
-  for (int k = 0; k < 4; ++k) {
-    ++c->launches;
-    if (V.real)
-      mg::pass4_kernel<true><<<g, kThreads, 0, c->stream>>>(B, 3 - k, V.rows, in[k], nul, nul, out[k], 0);
-    else
-      mg::pass4_kernel<false><<<g, kThreads, 0, c->stream>>>(B, 3 - k, V.rows, in[k], nul, nul, out[k], 0);
-  }
+  for (int k = 0; k < 4; ++k) pass4(c, B, 3 - k, V.real, V.rows, in[k], nul, nul, out[k], 0);
   return cudaGetLastError();
 }
 
 // Restriction of a level-l array (n fine cells per axis) to level l - 1,
 // axis by axis through T[0], T[1].
-cudaError_t d4_restrict(mg_ctx* c, int n, const cplx<double>* x, cplx<double>* y) {
-  Hier4& H = *c->h4;
+template <typename R>
+cudaError_t d4_restrict(mg_ctx* c, Hier4<R>& H, int n, const cplx<R>* x, cplx<R>* y) {
   const int N = n + 1, Nc = n / 3 + 1;
   int ext[4] = {N, N, N, N};
-  const cplx<double>* src = x;
-  cplx<double>* dst[4] = {H.T[0], H.T[1], H.T[0], y};
+  const cplx<R>* src = x;
+  cplx<R>* dst[4] = {H.T[0], H.T[1], H.T[0], y};
   for (int a = 0; a < 4; ++a) {
     ext[a] = Nc;
     const mg::Box4 B = box4(ext[0], ext[1], ext[2], ext[3]);
     ++c->launches;
-    mg::restrict4_kernel<<<grid_for(box4_size(B)), kThreads, 0, c->stream>>>(B, a, N, src, dst[a]);
+    mg::restrict4_kernel<R><<<grid_for(box4_size(B)), kThreads, 0, c->stream>>>(B, a, N, src, dst[a]);
     src = dst[a];
   }
   return cudaGetLastError();
@@ -1651,30 +1662,31 @@ cudaError_t d4_restrict(mg_ctx* c, int n, const cplx<double>* x, cplx<double>* y
 
 // y = base + P x (or base - P x with neg) for x on level l - 1 (n fine cells
 // per axis), through T[1], T[2].
-cudaError_t d4_prolong(mg_ctx* c, int n, const cplx<double>* x, const cplx<double>* base, cplx<double>* y,
+template <typename R>
+cudaError_t d4_prolong(mg_ctx* c, Hier4<R>& H, int n, const cplx<R>* x, const cplx<R>* base, cplx<R>* y,
                        int neg) {
-  Hier4& H = *c->h4;
   const int N = n + 1, Nc = n / 3 + 1;
   int ext[4] = {Nc, Nc, Nc, Nc};
-  const cplx<double>* src = x;
-  cplx<double>* dst[4] = {H.T[1], H.T[2], H.T[1], y};
+  const cplx<R>* src = x;
+  cplx<R>* dst[4] = {H.T[1], H.T[2], H.T[1], y};
   for (int a = 0; a < 4; ++a) {
     ext[a] = N;
     const mg::Box4 B = box4(ext[0], ext[1], ext[2], ext[3]);
     const bool last = a == 3;
     ++c->launches;
-    mg::prolong4_kernel<<<grid_for(box4_size(B)), kThreads, 0, c->stream>>>(
+    mg::prolong4_kernel<R><<<grid_for(box4_size(B)), kThreads, 0, c->stream>>>(
         B, a, src, last ? base : nullptr, dst[a], last ? neg : 0);
     src = dst[a];
   }
   return cudaGetLastError();
 }
 
-cudaError_t d4_inject(mg_ctx* c, int n, const cplx<double>* x, cplx<double>* y) {
+template <typename R>
+cudaError_t d4_inject(mg_ctx* c, int n, const cplx<R>* x, cplx<R>* y) {
   const int Nc = n / 3 + 1;
   const mg::Box4 B = box4(Nc, Nc, Nc, Nc);
   ++c->launches;
-  mg::inject4_kernel<<<grid_for(box4_size(B)), kThreads, 0, c->stream>>>(B, x, y);
+  mg::inject4_kernel<R><<<grid_for(box4_size(B)), kThreads, 0, c->stream>>>(B, x, y);
   return cudaGetLastError();
 }
 
@@ -1682,47 +1694,52 @@ cudaError_t d4_inject(mg_ctx* c, int n, const cplx<double>* x, cplx<double>* y) 
 // coarse right-hand side b_{l-1} = R r_l + G u_{l-1}): residual, Jacobi and
 // restriction from the finest level down, then the corrections
 // corr_l = T_l du_l + P corr_{l-1} and u_L += corr_L.  The fine level is
-// read by the residual and updated at the end (no pending correction).
-cudaError_t d4_enqueue_cycle(mg_ctx* c, int hb, int hier, const cplx<double>* omega) {
-  Hier4& H = *c->h4;
+// read by the residual and updated at the end (no pending correction).  The
+// fine residual norm is fused into the Jacobi step (complex128 only).
+template <typename R>
+cudaError_t d4_enqueue_cycle(mg_ctx* c, Hier4<R>& H, int hb, int hier, const cplx<double>* omega) {
   const int L = c->L;
+  const bool f64 = std::is_same<R, double>::value;
   cudaError_t e = cudaSuccess;
   for (int l = L; l >= 1 && e == cudaSuccess; --l) {
-    Lev4& V = H.lev[l];
+    Lev4<R>& V = H.lev[l];
     if (l == L && c->timing) e = cudaEventRecord(c->ev[c->ev_used], c->stream);
-    if (e == cudaSuccess) e = d4_apply(c, V.n, V.rows, V.real, V.u, V.b, H.T[4], -1.0);  // r_l
+    if (e == cudaSuccess) e = d4_apply(c, H, V.n, V.rows, V.real, V.u, V.b, H.T[4], 1);  // r_l
     if (l == L && c->timing && e == cudaSuccess) e = cudaEventRecord(c->ev[c->ev_used + 1], c->stream);
     if (e != cudaSuccess) break;
     c->launches += 2;
-    mg::omega_table4_kernel<<<1, 256, 0, c->stream>>>(V.invd, omega[l - 1], V.omd);
-    mg::jacobi4_kernel<<<grid_for(V.nv), kThreads, 0, c->stream>>>(
-        V.n, H.T[4], V.t, V.typ, V.omd, hb, H.partial, H.ticket, l == L ? H.norm2 : nullptr);
+    mg::omega_table4_kernel<R><<<1, 256, 0, c->stream>>>(V.invd, omega[l - 1], V.omd);
+    mg::jacobi4_kernel<R><<<grid_for(V.nv), kThreads, 0, c->stream>>>(
+        V.n, H.T[4], V.t, V.typ, V.omd, hb, H.partial, H.ticket, (l == L && f64) ? H.norm2 : nullptr);
     if (l > 1) {
-      Lev4& W = H.lev[l - 1];
+      Lev4<R>& W = H.lev[l - 1];
       e = d4_inject(c, V.n, V.u, W.u);
-      if (e == cudaSuccess) e = d4_restrict(c, V.n, H.T[4], W.b);
-      if (e == cudaSuccess) e = d4_apply(c, W.n, V.grows, V.greal, W.u, W.b, W.b, 1.0);  // + G u_{l-1}
+      if (e == cudaSuccess) e = d4_restrict(c, H, V.n, H.T[4], W.b);
+      if (e == cudaSuccess) e = d4_apply(c, H, W.n, V.grows, V.greal, W.u, W.b, W.b, 0);  // + G u_{l-1}
       if (hier && e == cudaSuccess) {
         // BPX transfer: T du = du - P I du
         e = d4_inject(c, V.n, V.t, H.T[0]);
-        if (e == cudaSuccess) e = d4_prolong(c, V.n, H.T[0], V.t, V.t, 1);
+        if (e == cudaSuccess) e = d4_prolong(c, H, V.n, H.T[0], V.t, V.t, 1);
       }
     }
     if (e == cudaSuccess) e = cudaGetLastError();
   }
   for (int l = 2; l <= L && e == cudaSuccess; ++l)
-    e = d4_prolong(c, H.lev[l].n, H.lev[l - 1].corr, H.lev[l].t, H.lev[l].corr, 0);
+    e = d4_prolong(c, H, H.lev[l].n, H.lev[l - 1].corr, H.lev[l].t, H.lev[l].corr, 0);
   if (e == cudaSuccess) {
-    const Lev4& F = H.lev[L];
+    const Lev4<R>& F = H.lev[L];
     ++c->launches;
-    mg::update4_kernel<<<grid_for(F.nv), kThreads, 0, c->stream>>>(F.n, F.u, F.corr);
+    mg::update4_kernel<R, R><<<grid_for(F.nv), kThreads, 0, c->stream>>>(F.n, F.u, F.corr);
     e = cudaGetLastError();
   }
   return e;
 }
 
-int d4_cycle(mg_ctx* c, int hb, int hier, const cplx<double>* omega) {
-  Hier4& H = *c->h4;
+// One cycle as a CUDA graph: captured on first use and updated in place when
+// the variant, transfer or factors change; with timing on, plain launches
+// with an event pair around the finest level's residual.
+template <typename R>
+int d4_cycle(mg_ctx* c, Hier4<R>& H, int hb, int hier, const cplx<double>* omega) {
   cudaError_t e = cudaSuccess;
   if (c->timing) {
     if (c->ev_used + 2 > c->ev.size()) {
@@ -1732,7 +1749,7 @@ int d4_cycle(mg_ctx* c, int hb, int hier, const cplx<double>* omega) {
         c->ev.push_back(ev);
       }
     }
-    e = d4_enqueue_cycle(c, hb, hier, omega);
+    e = d4_enqueue_cycle(c, H, hb, hier, omega);
     c->ev_used += 2;
     if (e != cudaSuccess) return fail(c, MG_ERR_CUDA, std::string("cycle launch: ") + cudaGetErrorString(e));
     return MG_OK;
@@ -1749,7 +1766,7 @@ int d4_cycle(mg_ctx* c, int hb, int hier, const cplx<double>* omega) {
       const long long before = c->launches;
       cudaGraph_t g = nullptr;
       e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
-      cudaError_t ek = e == cudaSuccess ? d4_enqueue_cycle(c, hb, hier, omega) : e;
+      cudaError_t ek = e == cudaSuccess ? d4_enqueue_cycle(c, H, hb, hier, omega) : e;
       cudaError_t ee = e == cudaSuccess ? cudaStreamEndCapture(c->cap_stream, &g) : e;
       c->stream = user;
       const long long nk = c->launches - before;
@@ -1782,16 +1799,16 @@ int d4_cycle(mg_ctx* c, int hb, int hier, const cplx<double>* omega) {
       return MG_OK;
     }
   }
-  e = d4_enqueue_cycle(c, hb, hier, omega);
+  e = d4_enqueue_cycle(c, H, hb, hier, omega);
   if (e != cudaSuccess) return fail(c, MG_ERR_CUDA, std::string("cycle launch: ") + cudaGetErrorString(e));
   return MG_OK;
 }
 
 // Fine residual r = b - H u into T[4]; |r|^2 into norm2[slot] when slot >= 0.
 cudaError_t d4_residual(mg_ctx* c, int slot) {
-  Hier4& H = *c->h4;
-  const Lev4& V = H.lev[c->L];
-  cudaError_t e = d4_apply(c, V.n, V.rows, V.real, V.u, V.b, H.T[4], -1.0);
+  Hier4<double>& H = *c->h4;
+  const Lev4<double>& V = H.lev[c->L];
+  cudaError_t e = d4_apply(c, H, V.n, V.rows, V.real, V.u, V.b, H.T[4], 1);
   if (e == cudaSuccess && slot >= 0) {
     ++c->launches;
     mg::norm4_kernel<<<grid_for(V.nv), kThreads, 0, c->stream>>>(V.n, H.T[4], H.partial, H.ticket + 1,
@@ -1799,6 +1816,42 @@ cudaError_t d4_residual(mg_ctx* c, int slot) {
     e = cudaGetLastError();
   }
   return e;
+}
+
+// The defect-correction form in four dimensions: per outer step the FP64
+// residual (norm fused) becomes the complex64 rhs of H e = r, `inner` complex64
+// cycles from e = 0 follow, and u += e in FP64.
+int d4_refine(mg_ctx* c, int hb, int hier, const cplx<double>* omega, double tol, int max_cycles, int* done,
+              double* rel) {
+  Hier4<double>& H = *c->h4;
+  Hier4<float>& E = *c->h4f;
+  const int L = c->L;
+  Lev4<double>& F = H.lev[L];
+  Lev4<float>& EF = E.lev[L];
+  auto diverged = [&](double x) { return !std::isfinite(x) || x > 1e6; };
+  // r = b - H u and its norm
+  MG_CUDA(c, d4_residual(c, 1));
+  while (true) {
+    MG_CUDA(c, cudaMemcpyAsync(c->host_norm, H.norm2 + 1, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    MG_CUDA(c, cudaStreamSynchronize(c->stream));
+    *rel = c->r0 > 0 ? std::sqrt(*c->host_norm) / c->r0 : 0.0;
+    if (diverged(*rel)) return MG_DIVERGED;
+    if (*rel <= tol) return MG_OK;
+    if (*done >= max_cycles) return MG_NOT_CONVERGED;
+    ++c->launches;
+    mg::to_c64_kernel<<<grid_for(F.nv), kThreads, 0, c->stream>>>((long long)F.nv, H.T[4], EF.b);
+    MG_CUDA(c, cudaMemsetAsync(EF.u, 0, EF.nv * sizeof(cplx<float>), c->stream));
+    const int m = std::min(c->inner_cycles, std::max(1, max_cycles - *done));
+    for (int k = 0; k < m; ++k) {
+      int rc = d4_cycle(c, E, hb, hier, omega);
+      if (rc != MG_OK) return rc;
+      ++*done;
+    }
+    ++c->launches;
+    mg::update4_kernel<double, float><<<grid_for(F.nv), kThreads, 0, c->stream>>>(F.n, F.u, EF.u);
+    MG_CUDA(c, cudaGetLastError());
+    MG_CUDA(c, d4_residual(c, 1));
+  }
 }
 
 const char* kNot4 = " is not available for d = 4 (the four-dimensional path runs complex128 cycles)";
@@ -1857,7 +1910,7 @@ int mg_create_ecs(int d, int depth, const double* k2_field, double theta_layer, 
   c->wlo = width_lo;
   c->whi = width_hi;
   c->k2.assign(k2_field, k2_field + nvf);
-  int rc = d == 4 ? d4_build(c) : build_hier<double>(c, c->h64);
+  int rc = d == 4 ? d4_build<double>(c, c->h4) : build_hier<double>(c, c->h64);
   if (rc == MG_OK) {
     cudaError_t e = cudaMalloc(&c->f_dev, nvf * sizeof(cplx<double>));
     if (e == cudaSuccess) e = cudaMemset(c->f_dev, 0, nvf * sizeof(cplx<double>));
@@ -1893,6 +1946,7 @@ void mg_destroy(mg_ctx* c) {
   free_hier(c->h64);
   free_hier(c->h32);
   d4_free(c->h4);
+  d4_free(c->h4f);
   if (c->f_dev) cudaFree(c->f_dev);
   if (c->scratch) cudaFree(c->scratch);
   if (c->rvec) cudaFree(c->rvec);
@@ -1910,7 +1964,7 @@ int mg_set_rhs(mg_ctx* c, const mg_c128* f, int on_device) {
   if (check_ctx(c)) return MG_ERR_INVALID;
   if (f == nullptr) return fail(c, MG_ERR_INVALID, "f is NULL");
   if (c->d == 4) {
-    const Lev4& V = c->h4->lev[c->L];
+    const Lev4<double>& V = c->h4->lev[c->L];
     MG_CUDA(c, cudaMemcpyAsync(c->f_dev, f, V.nv * sizeof(mg_c128),
                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
     MG_CUDA(c, d4_mass(c, c->f_dev, V.b));
@@ -1930,11 +1984,11 @@ int mg_set_solution(mg_ctx* c, const mg_c128* u, int on_device) {
   if (check_ctx(c)) return MG_ERR_INVALID;
   if (u == nullptr) return fail(c, MG_ERR_INVALID, "u is NULL");
   if (c->d == 4) {
-    const Lev4& V = c->h4->lev[c->L];
+    const Lev4<double>& V = c->h4->lev[c->L];
     MG_CUDA(c, cudaMemcpyAsync(V.u, u, V.nv * sizeof(mg_c128),
                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
     ++c->launches;
-    mg::update4_kernel<<<grid_for(V.nv), kThreads, 0, c->stream>>>(V.n, V.u, nullptr);  // zero boundary
+    mg::update4_kernel<double, double><<<grid_for(V.nv), kThreads, 0, c->stream>>>(V.n, V.u, (const cplx<double>*)nullptr);  // zero boundary
     MG_CUDA(c, cudaGetLastError());
     c->r0 = -1.0;
     return MG_OK;
@@ -1960,7 +2014,7 @@ int mg_get_solution(mg_ctx* c, mg_c128* out, int on_device) {
   if (check_ctx(c)) return MG_ERR_INVALID;
   if (out == nullptr) return fail(c, MG_ERR_INVALID, "out is NULL");
   if (c->d == 4) {
-    const Lev4& V = c->h4->lev[c->L];
+    const Lev4<double>& V = c->h4->lev[c->L];
     MG_CUDA(c, cudaMemcpyAsync(out, V.u, V.nv * sizeof(mg_c128),
                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
     if (!on_device) MG_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -1984,7 +2038,7 @@ int mg_get_level(mg_ctx* c, int level, int which, mg_c128* out, int on_device) {
     return fail(c, MG_ERR_INVALID, "bad level/which/out");
   if (level == c->L && which == 0) return mg_get_solution(c, out, on_device);
   if (c->d == 4) {
-    const Lev4& V = c->h4->lev[level];
+    const Lev4<double>& V = c->h4->lev[level];
     MG_CUDA(c, cudaMemcpyAsync(out, which == 0 ? V.u : V.b, V.nv * sizeof(mg_c128),
                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
     if (!on_device) MG_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -2003,7 +2057,7 @@ int mg_cycle(mg_ctx* c, int variant, const mg_c128* omega, int transfer) {
   if (omega == nullptr) return fail(c, MG_ERR_INVALID, "omega is NULL");
   int hb, hier;
   if (decode_variant(c, variant, transfer, &hb, &hier)) return MG_ERR_INVALID;
-  if (c->d == 4) return d4_cycle(c, hb, hier, reinterpret_cast<const cplx<double>*>(omega));
+  if (c->d == 4) return d4_cycle(c, *c->h4, hb, hier, reinterpret_cast<const cplx<double>*>(omega));
   return run_cycle(c, c->h64, c->L, hb, hier, reinterpret_cast<const cplx<double>*>(omega));
 }
 
@@ -2022,7 +2076,7 @@ int mg_residual_max(mg_ctx* c, double* abs_max) {
   if (check_ctx(c)) return MG_ERR_INVALID;
   if (abs_max == nullptr) return fail(c, MG_ERR_INVALID, "abs_max is NULL");
   if (c->d == 4) {
-    Hier4& H4 = *c->h4;
+    Hier4<double>& H4 = *c->h4;
     unsigned long long* mx = reinterpret_cast<unsigned long long*>(H4.norm2 + 2);
     MG_CUDA(c, d4_residual(c, -1));
     MG_CUDA(c, cudaMemsetAsync(mx, 0, sizeof(unsigned long long), c->stream));
@@ -2055,9 +2109,20 @@ int mg_set_precision(mg_ctx* c, int precision, int inner_cycles) {
   if (check_ctx(c)) return MG_ERR_INVALID;
   if (precision != MG_C128 && precision != MG_C64_REFINE) return fail(c, MG_ERR_INVALID, "bad precision");
   if (inner_cycles < 1 || inner_cycles > 1000) return fail(c, MG_ERR_INVALID, "inner_cycles out of range");
-  if (c->d == 4 && precision != MG_C128) return fail(c, MG_ERR_INVALID, std::string("MG_C64_REFINE") + kNot4);
   c->precision = precision;
   c->inner_cycles = inner_cycles;
+  if (c->d == 4) {
+    if (precision == MG_C64_REFINE && c->h4f == nullptr) {
+      int rc = d4_build<float>(c, c->h4f);
+      if (rc != MG_OK) {
+        d4_free(c->h4f);
+        c->h4f = nullptr;
+        c->precision = MG_C128;
+        return rc;
+      }
+    }
+    return MG_OK;
+  }
   if (precision == MG_C64_REFINE && !c->h32.ready) {
     int rc = build_hier<float>(c, c->h32);
     if (rc != MG_OK) { free_hier(c->h32); return rc; }
@@ -2098,7 +2163,7 @@ int mg_solve(mg_ctx* c, int variant, const mg_c128* omega, int transfer, double 
       if (done >= max_cycles) return finish(MG_NOT_CONVERGED);
       const int m = std::min(check, max_cycles - done);
       for (int k = 0; k < m; ++k) {
-        rc = c->d == 4 ? d4_cycle(c, hb, hier, om) : run_cycle(c, c->h64, L, hb, hier, om);
+        rc = c->d == 4 ? d4_cycle(c, *c->h4, hb, hier, om) : run_cycle(c, c->h64, L, hb, hier, om);
         if (rc != MG_OK) return rc;
         ++done;
       }
@@ -2117,6 +2182,11 @@ int mg_solve(mg_ctx* c, int variant, const mg_c128* omega, int transfer, double 
     }
   }
   // complex64 cycles inside FP64 defect correction
+  if (c->d == 4) {
+    const int st = d4_refine(c, hb, hier, om, tol, max_cycles, &done, &rel);
+    if (st == MG_OK || st == MG_DIVERGED || st == MG_NOT_CONVERGED) return finish(st);
+    return st;
+  }
   auto& H = c->h64;
   auto& E = c->h32;
   auto& VF = H.lev[L];
@@ -2345,11 +2415,11 @@ int mg_set_rhs_vector(mg_ctx* c, const mg_c128* b, int on_device) {
   if (check_ctx(c)) return MG_ERR_INVALID;
   if (b == nullptr) return fail(c, MG_ERR_INVALID, "b is NULL");
   if (c->d == 4) {
-    const Lev4& V = c->h4->lev[c->L];
+    const Lev4<double>& V = c->h4->lev[c->L];
     MG_CUDA(c, cudaMemcpyAsync(V.b, b, V.nv * sizeof(mg_c128),
                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
     ++c->launches;
-    mg::update4_kernel<<<grid_for(V.nv), kThreads, 0, c->stream>>>(V.n, V.b, nullptr);  // zero boundary
+    mg::update4_kernel<double, double><<<grid_for(V.nv), kThreads, 0, c->stream>>>(V.n, V.b, (const cplx<double>*)nullptr);  // zero boundary
     MG_CUDA(c, cudaGetLastError());
     c->r0 = -1.0;
     return MG_OK;

@@ -6,8 +6,8 @@ variant, with and without a scaling layer, a one-sided layer with a rotated
 interior, and on depths 1-3 (the oracle is generic in d and pinned in four
 dimensions in the CPU suite).  At the full size (depth 4, 82^4 vertices) the
 oracle is too slow; there the checks are properties: the analytic discrete
-Poisson solution of Section 7.1 has a zero residual, and the cycle converges
-to it.
+Poisson solution of Section 7.1 has a zero residual, and the cycle (complex128
+and the complex64 refinement form) converges to it.
 """
 import math
 
@@ -159,6 +159,60 @@ def test_poisson_4d_full_size():
     g.close()
 
 
+@pytest.mark.parametrize("depth,m,var", [(2, 3, VARIANTS[0]), (2, 3, VARIANTS[1]), (2, 3, VARIANTS[2]),
+                                         (3, 1, VARIANTS[2])])
+def test_c64_outer_step_4d(depth, m, var):
+    """One outer step of the refinement form in four dimensions: the complex64
+    correction e of m inner cycles on H e = r0 against the oracle's m FP64
+    cycles on the same inner problem, to the complex64 bound of the 2D/3D
+    test (2e-5 up to depth 4)."""
+    kf = W.constant_k2(4, depth, 18.0)
+    f = W.random_complex(4, depth, 100)
+    u0 = W.random_complex(4, depth, 200)
+    g = mg.Solver(4, depth, kf, TH, 0.2)
+    o = O.Hierarchy(4, depth, kf, TH, 0.2)
+    g.set_rhs(f)
+    o.set_rhs_nodal(f)
+    g.set_solution(u0)
+    o.set_solution(u0)
+    omega = np.array([0.6 - 0.03j * l for l in range(depth)])
+    g.set_precision(mg.MG_C64_REFINE, m)
+    st, n, _ = g.solve(var[0], omega, var[1], 1e-30, m)
+    assert st == mg.MG_NOT_CONVERGED and n == m
+    oi = O.Hierarchy(4, depth, kf, TH, 0.2)
+    oi.b = o.residual()
+    O.zero_boundary(oi.b)
+    for _ in range(m):
+        oi.cycle(omega, var[2], var[3])
+    err = rel_l2(g.get_solution() - o.u, oi.u)
+    assert err <= 2e-5, f"relative L2 of e: {err:.3e}"
+    g.close()
+
+
+def test_c64_refinement_4d_full_size():
+    """Depth 4: the refinement form reaches 1e-8 (FP64 residual, checked
+    again by mg_residual_norm) on the Section 7.1 Poisson problem and lands on
+    the discrete solution."""
+    depth, d = 4, 4
+    n = 3 ** depth
+    h = 1.0 / n
+    s1 = np.sin(math.pi * np.arange(n + 1) / n)
+    s = s1[:, None, None, None] * s1[None, :, None, None] * s1[None, None, :, None] * s1[None, None, None, :]
+    kap = (2 / h) * (1 - math.cos(math.pi * h))
+    mu = (h / 3) * (2 + math.cos(math.pi * h))
+    exact = math.pi ** 2 * (mu / kap) * s
+    g = mg.Solver(d, depth, W.constant_k2(d, depth, 0.0), 0.0, 0.0)
+    g.set_rhs((d * math.pi ** 2 * s).astype(np.complex128))
+    g.set_precision(mg.MG_C64_REFINE, 16)
+    st, cycles, rel = g.solve(mg.MG_ADD, mg.omega_scheme(mg.MG_OMEGA_EXP, 0.8, depth), mg.MG_DLINEAR, 1e-8, 1000)
+    assert st == mg.MG_OK and rel <= 1e-8, (st, cycles, rel)
+    _, rel2 = g.residual_norm()
+    assert abs(rel2 - rel) <= 1e-6 * rel
+    err = np.abs(g.get_solution() - exact).max() / np.abs(exact).max()
+    assert err <= 1e-6, err
+    g.close()
+
+
 def test_4d_rejects_what_it_does_not_run():
     k2 = W.constant_k2(4, 1, 1.0)
     k2v = k2.copy()
@@ -166,8 +220,6 @@ def test_4d_rejects_what_it_does_not_run():
     with pytest.raises(mg.MgError):
         mg.Solver(4, 1, k2v, 0.0, 0.0)  # varying shift
     g = mg.Solver(4, 1, k2, 0.0, 0.0)
-    with pytest.raises(mg.MgError):
-        g.set_precision(mg.MG_C64_REFINE, 4)
     with pytest.raises(mg.MgError):
         g.fmg(mg.MG_BPX, np.full(1, 0.6), mg.MG_HIERARCHICAL, 3)
     g.close()
