@@ -25,6 +25,7 @@
 #include "mg_adjoint.cuh"
 #include "mg_maxnorm.cuh"
 #include "mg_dim4.cuh"
+#include "mg_io.cuh"
 #include <map>
 
 using mg::cplx;
@@ -1063,6 +1064,20 @@ int grid_for(size_t nv) {
   return (int)std::min<size_t>(std::max<size_t>(b, 1), 152 * 16);
 }
 
+// Device address of a page-locked host buffer (cudaHostAlloc, or registered
+// with cudaHostRegister), or null for pageable memory.  Kernels read and
+// write such a buffer directly over the host link (mg_io.cuh).
+template <typename T>
+T* pinned_view(T* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, (const void*)p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (a.type != cudaMemoryTypeHost || a.devicePointer == nullptr) return nullptr;
+  return reinterpret_cast<T*>(a.devicePointer);
+}
+
 template <typename R>
 cudaError_t prolong(mg_ctx* c, Hier<R>& H, int l) {
   auto& V = H.lev[l];
@@ -1963,17 +1978,21 @@ int mg_set_stream(mg_ctx* c, void* s) {
 int mg_set_rhs(mg_ctx* c, const mg_c128* f, int on_device) {
   if (check_ctx(c)) return MG_ERR_INVALID;
   if (f == nullptr) return fail(c, MG_ERR_INVALID, "f is NULL");
-  if (c->d == 4) {
-    const Lev4<double>& V = c->h4->lev[c->L];
-    MG_CUDA(c, cudaMemcpyAsync(c->f_dev, f, V.nv * sizeof(mg_c128),
+  const size_t nv = c->d == 4 ? c->h4->lev[c->L].nv : c->h64.lev[c->L].nv;
+  const cplx<double>* fv = on_device ? nullptr : pinned_view(reinterpret_cast<const cplx<double>*>(f));
+  if (fv != nullptr) {
+    ++c->launches;
+    mg::copy_c128_kernel<<<grid_for(nv), kThreads, 0, c->stream>>>((long long)nv, fv, c->f_dev);
+    MG_CUDA(c, cudaGetLastError());
+  } else {
+    MG_CUDA(c, cudaMemcpyAsync(c->f_dev, f, nv * sizeof(mg_c128),
                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
-    MG_CUDA(c, d4_mass(c, c->f_dev, V.b));
+  }
+  if (c->d == 4) {
+    MG_CUDA(c, d4_mass(c, c->f_dev, c->h4->lev[c->L].b));
     c->r0 = -1.0;
     return MG_OK;
   }
-  const size_t nv = c->h64.lev[c->L].nv;
-  MG_CUDA(c, cudaMemcpyAsync(c->f_dev, f, nv * sizeof(mg_c128),
-                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
   int rc = set_level_rhs(c, c->L);
   if (rc != MG_OK) return rc;
   c->r0 = -1.0;
@@ -1995,14 +2014,24 @@ int mg_set_solution(mg_ctx* c, const mg_c128* u, int on_device) {
   }
   auto& H = c->h64;
   auto& V = H.lev[c->L];
-  // copy into the active fine array, then zero its Dirichlet ring
-  MG_CUDA(c, cudaMemcpyAsync(V.u[H.cur], u, V.nv * sizeof(mg_c128),
-                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
-  const int ring = c->d == 2 ? 4 * V.n : 6 * (V.n + 1) * (V.n + 1);
-  if (c->d == 2)
-    mg::zero_ring_kernel<2><<<(ring + 255) / 256, 256, 0, c->stream>>>(V.n, V.u[H.cur]);
-  else
-    mg::zero_ring_kernel<3><<<(ring + 255) / 256, 256, 0, c->stream>>>(V.n, V.u[H.cur]);
+  const cplx<double>* uv = on_device ? nullptr : pinned_view(reinterpret_cast<const cplx<double>*>(u));
+  ++c->launches;
+  if (uv != nullptr) {
+    // page-locked host buffer: read over the host link, ring zeroed on the way
+    if (c->d == 2)
+      mg::copy_zero_ring_kernel<2><<<grid_for(V.nv), kThreads, 0, c->stream>>>(V.n, uv, V.u[H.cur]);
+    else
+      mg::copy_zero_ring_kernel<3><<<grid_for(V.nv), kThreads, 0, c->stream>>>(V.n, uv, V.u[H.cur]);
+  } else {
+    // copy into the active fine array, then zero its Dirichlet ring
+    MG_CUDA(c, cudaMemcpyAsync(V.u[H.cur], u, V.nv * sizeof(mg_c128),
+                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    const int ring = c->d == 2 ? 4 * V.n : 6 * (V.n + 1) * (V.n + 1);
+    if (c->d == 2)
+      mg::zero_ring_kernel<2><<<(ring + 255) / 256, 256, 0, c->stream>>>(V.n, V.u[H.cur]);
+    else
+      mg::zero_ring_kernel<3><<<(ring + 255) / 256, 256, 0, c->stream>>>(V.n, V.u[H.cur]);
+  }
   MG_CUDA(c, cudaGetLastError());
   int rc = zero_pending(c, H, c->L);
   if (rc != MG_OK) return rc;
@@ -2024,6 +2053,12 @@ int mg_get_solution(mg_ctx* c, mg_c128* out, int on_device) {
   const size_t nv = H.lev[c->L].nv;
   if (on_device) {
     MG_CUDA(c, materialize(c, H, c->L, (cplx<double>*)out));
+    return MG_OK;
+  }
+  if (cplx<double>* ov = pinned_view(reinterpret_cast<cplx<double>*>(out))) {
+    // page-locked host buffer: U + P corr written straight over the host link
+    MG_CUDA(c, materialize(c, H, c->L, ov));
+    MG_CUDA(c, cudaStreamSynchronize(c->stream));
     return MG_OK;
   }
   MG_CUDA(c, materialize(c, H, c->L, c->scratch));
