@@ -606,6 +606,7 @@ def main():
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--form", choices=["csg_sweep", "channel_table2", "four_d", "dimension_study"], default=None,
                     help="run only this form and print its result (profiling)")
+    ap.add_argument("--four-d-depth", type=int, default=4, help="depth of the four_d form (profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -632,7 +633,7 @@ def main():
     if args.form is not None:
         peaks, _ = measured_peaks()
         fn = {"csg_sweep": lambda m, t: csg_sweep(m, t), "channel_table2": lambda m, t: channel_table2(m, t),
-              "four_d": lambda m, t: four_d(m, t, peaks),
+              "four_d": lambda m, t: four_d(m, t, peaks, depth=args.four_d_depth),
               "dimension_study": lambda m, t: dimension_study(m, t)}[args.form]
         print(json.dumps({"form": args.form, "result": fn(mg, torch)}), flush=True)
         return

@@ -138,6 +138,7 @@ struct Lev4 {
   cplx<R>* omd = nullptr;    // [256] omega / D of the current cycle
   bool real = false;         // every row of `rows` is real
   bool greal = false;        // every row of `grows` is real
+  bool dreal = false;        // every entry of `invd` is real
 };
 
 template <typename R>
@@ -1577,6 +1578,7 @@ int d4_build(mg_ctx* c, Hier4<R>*& out) {
       invd[ty] = to_r<R>(1.0 / (kterm - phi * mprod));
     }
     if ((rc = d4_upload(c, *H, &V.invd, invd)) != MG_OK) return rc;
+    V.dreal = std::all_of(invd.begin(), invd.end(), [](const cplx<R>& v) { return v.y == R(0); });
     if ((rc = d4_alloc(c, *H, (void**)&V.omd, 256 * sizeof(cplx<R>))) != MG_OK) return rc;
     if (l > 1) {
       std::vector<std::array<cd, 6>> g;
@@ -1724,8 +1726,13 @@ cudaError_t d4_enqueue_cycle(mg_ctx* c, Hier4<R>& H, int hb, int hier, const cpl
     if (e != cudaSuccess) break;
     c->launches += 2;
     mg::omega_table4_kernel<R><<<1, 256, 0, c->stream>>>(V.invd, omega[l - 1], V.omd);
-    mg::jacobi4_kernel<R><<<grid_for(V.nv), kThreads, 0, c->stream>>>(
-        V.n, H.T[4], V.t, V.typ, V.omd, hb, H.partial, H.ticket, (l == L && f64) ? H.norm2 : nullptr);
+    double* nrm = (l == L && f64) ? H.norm2 : nullptr;
+    if (V.dreal && omega[l - 1].y == 0.0)
+      mg::jacobi4_kernel<R, true><<<grid_for(V.nv), kThreads, 0, c->stream>>>(V.n, H.T[4], V.t, V.typ, V.omd, hb,
+                                                                             H.partial, H.ticket, nrm);
+    else
+      mg::jacobi4_kernel<R, false><<<grid_for(V.nv), kThreads, 0, c->stream>>>(V.n, H.T[4], V.t, V.typ, V.omd, hb,
+                                                                              H.partial, H.ticket, nrm);
     if (l > 1) {
       Lev4<R>& W = H.lev[l - 1];
       e = d4_inject(c, V.n, V.u, W.u);

@@ -183,8 +183,10 @@ __global__ void omega_table4_kernel(const cplx<R>* __restrict__ invd, cplx<doubl
 // du = omega D^{-1} r at interior vertices (omd: omega / D by vertex type),
 // zero at c-points for the hierarchical basis variant and on the boundary;
 // |r|^2 over the interior into *norm2 (deterministic last-block sum) when
-// norm2 is not null.
-template <typename R>
+// norm2 is not null.  REAL: every omega / D is real (real factor, no layer),
+// two multiplies per vertex instead of a complex product -- the complex128
+// step is bound by its FP64 operations, not by its 32 bytes per vertex.
+template <typename R, bool REAL>
 __global__ void __launch_bounds__(256) jacobi4_kernel(int n, const cplx<R>* __restrict__ r,
                                                       cplx<R>* __restrict__ t,
                                                       const uint8_t* __restrict__ typ,
@@ -212,7 +214,7 @@ __global__ void __launch_bounds__(256) jacobi4_kernel(int n, const cplx<R>* __re
       if (norm2 != nullptr) nrm = fma((double)ri.x, (double)ri.x, fma((double)ri.y, (double)ri.y, nrm));
       if (!(hb && cpt)) {
         const cplx<R> q = omd[ty];
-        du = zero_bits(q.y) ? rmul(q.x, ri) : q * ri;
+        du = REAL ? rmul(q.x, ri) : q * ri;
       }
     }
     t[i] = du;
