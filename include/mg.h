@@ -13,10 +13,18 @@
  * prolongation back to the fine grid.
  *
  * Conventions shared by every call
- *  - d is 2 or 3; level l has n = 3^l cells per axis and (n+1)^d vertices
- *    including the Dirichlet ring.  Vertex arrays are row-major with x
- *    fastest: index = x + (n+1)*(y + (n+1)*z).  Complex values are
- *    interleaved (re, im) FP64 pairs (mg_c128).  Boundary entries are zero.
+ *  - d is 2, 3 or 4; level l has n = 3^l cells per axis and (n+1)^d
+ *    vertices including the Dirichlet ring.  Vertex arrays are row-major with
+ *    x fastest: index = x + (n+1)*(y + (n+1)*(z + (n+1)*w)).  Complex values
+ *    are interleaved (re, im) FP64 pairs (mg_c128).  Boundary entries are
+ *    zero.
+ *  - d = 4 (p = 4 of Section 7.1) takes a constant k2_field and depth <= 4,
+ *    runs mg_set_rhs/_vector, mg_set_solution, mg_get_solution, mg_get_level,
+ *    mg_cycle, mg_residual_norm/_max, mg_last_cycle_norm, mg_solve and
+ *    mg_set_precision; the other calls return MG_ERR_INVALID for it.
+ *  - A host pointer to page-locked memory (cudaHostAlloc, cudaHostRegister)
+ *    is read or written by kernels directly over the host link; pageable
+ *    memory is staged through cudaMemcpyAsync.
  *  - Pointers marked "host or device" are read on the host when the
  *    accompanying on_device flag is 0 and as device pointers of the current
  *    CUDA device otherwise.  The caller keeps ownership of every array it
@@ -78,8 +86,9 @@ enum { MG_OMEGA_JACOBI = 0, MG_OMEGA_UCG = 1, MG_OMEGA_LGRID = 2, MG_OMEGA_EXP =
  *             (coordinate-wise exterior scaling); w = 0.5 rotates every cell
  *             (the complex scaled grid of Section 7.3).
  * The solution starts at zero and the rhs at zero.
- * Errors: MG_ERR_INVALID (d not in {2,3}, depth < 1 or too deep for the
- * device, theta or w out of range, NULL pointers), MG_ERR_OOM, MG_ERR_CUDA. */
+ * Errors: MG_ERR_INVALID (d not in {2,3,4}, depth < 1 or too deep for the
+ * device, theta or w out of range, a varying k2_field with d = 4, NULL
+ * pointers), MG_ERR_OOM, MG_ERR_CUDA. */
 int mg_create(int d, int depth, const double* k2_field, double theta,
               double layer_width, mg_ctx** out);
 

@@ -1936,7 +1936,7 @@ int mg_create_ecs(int d, int depth, const double* k2_field, double theta_layer, 
   if (rc == MG_OK) {
     cudaError_t e = cudaMalloc(&c->f_dev, nvf * sizeof(cplx<double>));
     if (e == cudaSuccess) e = cudaMemset(c->f_dev, 0, nvf * sizeof(cplx<double>));
-    if (e == cudaSuccess) e = cudaMalloc(&c->scratch, nvf * sizeof(cplx<double>));
+    if (e == cudaSuccess && d != 4) e = cudaMalloc(&c->scratch, nvf * sizeof(cplx<double>));  // d = 4 uses its own temporaries
     if (e == cudaSuccess) e = cudaMallocHost(&c->host_norm, 4 * sizeof(double));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = configure_kernels();

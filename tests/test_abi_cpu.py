@@ -69,3 +69,24 @@ def test_trace_stage_layout_matches_chain_rules():
     assert [k for _, k in chain_stages(729)] == [441, 196, 100, 16, 4, 106, 233]
     assert fine_tiles(729) == 961
     assert [k for _, k in chain_stages(243)] == [196, 100, 16, 4, 13, 106]
+
+
+def build_c_client(root, out_path):
+    """Compiles tests/c_api/solve_c.c against include/mg.h and links it with
+    the in-tree libmg.so (no Python, no torch in the client)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    cuda = os.environ.get("CUDA_HOME", "/usr/local/cuda")
+    cmd = [cc, "-std=c11", "-Wall", "-Wextra", "-Werror", "-O2", "-I", os.path.join(root, "include"),
+           "-I", os.path.join(cuda, "include"), os.path.join(root, "tests", "c_api", "solve_c.c"), "-o", out_path,
+           "-L", os.path.dirname(B.LIB), "-lmg", "-L", os.path.join(cuda, "lib64"), "-lcudart", "-lm"]
+    subprocess.run(cmd, check=True)
+    return out_path
+
+
+def test_plain_c_client_compiles_and_links(lib, root_dir, tmp_path):
+    exe = build_c_client(root_dir, str(tmp_path / "solve_c"))
+    assert os.path.exists(exe)
