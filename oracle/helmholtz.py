@@ -29,12 +29,12 @@ design notes):
 
 R1  Coordinate-wise exterior scaling: along axis j a cell's spacing is
     h*e^{i theta} when its centre c_j satisfies min(c_j, 1-c_j) < w, else h
-    (Section 7.4 rotates "cells close to" the open faces; Section 7.3 scales
-    h in each dimension).  w >= 0.5 rotates every cell (full complex scaled
-    grid).  Membership uses the cell centre on every level.
+    (Section 7.4 rotates the cells near the open faces; Section 7.3 scales
+    the spacing along every axis).  w >= 0.5 rotates every cell (full complex
+    scaled grid).  Membership uses the cell centre on every level.
 R1b The channel problem of Section 7.4 puts the layer at two faces only (top
     and right, within 1/3 of the domain, 30 degrees) and rotates every other
-    cell by theta "independently of this absorbing layer": along each axis a
+    cell by theta, whatever the layer does: along each axis a
     cell with centre c is in the layer when c < w_lo or 1 - c < w_hi and has
     spacing h*e^{i theta}; every other cell has h*e^{i theta_interior}.
     ``layer_width`` is w (both faces, w_lo = w_hi = w) or the pair
