@@ -109,6 +109,30 @@ int mg_create_ecs(int d, int depth, const double* k2_field, double theta_layer,
                   double theta_interior, double width_lo, double width_hi,
                   mg_ctx** out);
 
+/* A solver on an adaptive spacetree with hanging vertices (Section 4.3,
+ * static refinement).  Level 1 has all 3^d cells; a level-l cell flagged in
+ * refine splits into 3^d level-(l+1) cells.  A vertex whose 2^d cells of its
+ * level do not all exist is hanging: its value is the d-linear interpolation
+ * from the next coarser level.  The cycle is the additive correction scheme
+ * on the hierarchical generating system (the form Lemma 2 / Theorem 2 prove
+ * the FAS cycle equal to): every level's residual is the cell-wise residual
+ * of its leaves plus the restricted residual of the next finer level
+ * (including the partial residuals of hanging vertices).
+ *  d          2 or 3;  k2_field, theta, layer_width: as mg_create.
+ *  refine     host, the flags of levels 1..depth-1 concatenated: level l's
+ *             (3^l)^d bytes (x fastest), nonzero = refine; flags of cells
+ *             that do not exist are ignored.
+ * Runs mg_set_rhs, mg_set_solution and mg_get_solution (nodal values on the
+ * uniform finest grid; mg_get_solution returns the fine-grid function, d-
+ * linear on each leaf), mg_get_level (which = 0: the level's values, 1: its
+ * residual of the last cycle), mg_cycle, mg_residual_norm (over the fine-grid
+ * unknowns), mg_last_cycle_norm and mg_solve in complex128; the other calls
+ * return MG_ERR_INVALID.  Arrays are dense over every level's full grid.
+ * Errors: as mg_create, and MG_ERR_INVALID for a NULL refine or d = 4. */
+int mg_create_adaptive(int d, int depth, const double* k2_field, double theta,
+                       double layer_width, const unsigned char* refine,
+                       mg_ctx** out);
+
 /* Releases every device buffer of the context (NULL is ignored). */
 void mg_destroy(mg_ctx* ctx);
 

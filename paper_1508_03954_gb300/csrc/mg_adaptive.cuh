@@ -1,0 +1,341 @@
+// mg_adaptive.cuh -- the additive cycle on an adaptive spacetree with hanging
+// vertices (Section 4.3 and the hanging-vertex treatment of Section 3),
+// FP64, d = 2 or 3, sm_103a.
+//
+// Every level keeps dense arrays over its full grid plus a flag per cell
+// (bit 0: the cell exists, bit 1: it is refined) and a class per vertex
+// (0: no existing cell around it, 1: hanging or Dirichlet, 2: unknown = all
+// 2^d cells exist).  Kernels skip what does not exist, so the FP64 work --
+// what bounds these kernels on GB300 -- follows the adaptive grid.
+//
+// The cycle is the additive correction scheme on the hierarchical
+// generating system of the adaptive grid (Lemma 2 / Theorem 2 form):
+//   r_l = sum over the level-l leaves around v of (M_c f - H_c u)_v + R r_{l+1}
+// (the restriction carries the partial residuals of hanging vertices),
+//   du_l = omega_l r_l / H_l[v, v] at unknowns, hb mask / BPX (id - P I),
+//   corr_l = T du_l + P corr_{l-1},  u_l += corr_l on every level,
+// then hanging values := P u_{l-1} (coarse to fine) and coarse values at
+// vertices with an unknown on the next finer level := that value (fine to
+// coarse).
+#pragma once
+#include "mg_kernels.cuh"
+
+namespace mg {
+
+enum : uint8_t { kCellExists = 1, kCellRefined = 2 };
+enum : uint8_t { kVertNone = 0, kVertBound = 1, kVertUnknown = 2 };
+
+template <int D>
+__device__ __forceinline__ void ada_coords(unsigned i, int N, int* g) {
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    g[a] = (int)(i % (unsigned)N);
+    i /= (unsigned)N;
+  }
+}
+
+// Entry [a][b] of the element matrices of a cell with per-axis widths h and
+// inverse widths hi (corner bits a, b): M = prod h/6 (2 or 1), K = sum_j of
+// the same product with axis j's factor replaced by (+1 or -1)/h.
+template <int D>
+__device__ __forceinline__ void element_entry(const cplx<double>* h, const cplx<double>* hi, int a, int b,
+                                              cplx<double>& m, cplx<double>& k) {
+  cplx<double> mf[3], kf[3];
+#pragma unroll
+  for (int ax = 0; ax < D; ++ax) {
+    const bool same = ((a >> ax) & 1) == ((b >> ax) & 1);
+    mf[ax] = rmul(same ? 1.0 / 3.0 : 1.0 / 6.0, h[ax]);
+    kf[ax] = rmul(same ? 1.0 : -1.0, hi[ax]);
+  }
+  m = mf[0];
+#pragma unroll
+  for (int ax = 1; ax < D; ++ax) m = m * mf[ax];
+  k = cz<double>();
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    cplx<double> p = j == 0 ? kf[0] : mf[0];
+#pragma unroll
+    for (int ax = 1; ax < D; ++ax) p = p * (ax == j ? kf[ax] : mf[ax]);
+    k = k + p;
+  }
+}
+
+// r_l(v) = sum over the leaves around v of (M_c f - H_c u)_v, plus R r_{l+1}
+// (rf, the finer level's residual, may be null), zero where no cell exists
+// and on the Dirichlet boundary.
+template <int D>
+__global__ void ada_residual_kernel(int n, const cplx<double>* __restrict__ u, const cplx<double>* __restrict__ f,
+                                    const uint8_t* __restrict__ cellf, const uint8_t* __restrict__ vcls,
+                                    const cplx<double>* __restrict__ hcell, const cplx<double>* __restrict__ hinv,
+                                    const double* __restrict__ phic, double phi0,
+                                    const cplx<double>* __restrict__ rf, cplx<double>* __restrict__ r) {
+  const int N = n + 1, Nf = 3 * n + 1;
+  unsigned total = 1;
+  for (int a = 0; a < D; ++a) total *= (unsigned)N;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    int g[3];
+    ada_coords<D>(i, N, g);
+    bool inner = true;
+#pragma unroll
+    for (int a = 0; a < D; ++a) inner = inner && g[a] > 0 && g[a] < n;
+    cplx<double> acc = cz<double>();
+    if (inner && vcls[i] != kVertNone) {
+#pragma unroll
+      for (int e = 0; e < (1 << D); ++e) {
+        int c[3];
+        unsigned ci = 0, cs = 1;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          c[a] = g[a] - 1 + ((e >> a) & 1);
+          ci += (unsigned)c[a] * cs;
+          cs *= (unsigned)n;
+        }
+        if ((cellf[ci] & (kCellExists | kCellRefined)) != kCellExists) continue;  // leaves only
+        cplx<double> h[3], hi[3];
+#pragma unroll
+        for (int a = 0; a < D; ++a) { h[a] = hcell[c[a]]; hi[a] = hinv[c[a]]; }
+        const double phi = phic != nullptr ? phic[ci] : phi0;
+        const int av = ((1 << D) - 1) ^ e;  // v's corner in the cell
+#pragma unroll
+        for (int b = 0; b < (1 << D); ++b) {
+          unsigned vi = 0, vs = 1;
+#pragma unroll
+          for (int a = 0; a < D; ++a) {
+            vi += (unsigned)(c[a] + ((b >> a) & 1)) * vs;
+            vs *= (unsigned)N;
+          }
+          cplx<double> m, k;
+          element_entry<D>(h, hi, av, b, m, k);
+          acc = acc + m * f[vi];
+          acc = acc - (k - rmul(phi, m)) * u[vi];
+        }
+      }
+      if (rf != nullptr) {
+        // R = P^T: fine 3v + o, o in [-2, 2]^D, weight prod (1 - |o|/3)
+#pragma unroll 1
+        for (int o = 0; o < (D == 2 ? 25 : 125); ++o) {
+          int q = o;
+          double w = 1.0;
+          unsigned fi = 0, fs = 1;
+#pragma unroll
+          for (int a = 0; a < D; ++a) {
+            const int oa = q % 5 - 2;
+            q /= 5;
+            const int x = 3 * g[a] + oa;
+            w *= oa == 0 ? 1.0 : (oa == -1 || oa == 1 ? 2.0 / 3.0 : 1.0 / 3.0);
+            fi += (unsigned)x * fs;
+            fs *= (unsigned)Nf;
+          }
+          acc = rfma(w, rf[fi], acc);
+        }
+      }
+    }
+    r[i] = acc;
+  }
+}
+
+// t = omega r / H_l[v, v] at unknowns (the diagonal summed over the 2^D
+// cells, which all exist), zero elsewhere; hb: zero at c-points.
+template <int D>
+__global__ void ada_jacobi_kernel(int n, const cplx<double>* __restrict__ r, const uint8_t* __restrict__ vcls,
+                                  const cplx<double>* __restrict__ hcell, const cplx<double>* __restrict__ hinv,
+                                  const double* __restrict__ phic, double phi0, cplx<double> omega, int hb,
+                                  cplx<double>* __restrict__ t) {
+  const int N = n + 1;
+  unsigned total = 1;
+  for (int a = 0; a < D; ++a) total *= (unsigned)N;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    cplx<double> v = cz<double>();
+    if (vcls[i] == kVertUnknown) {
+      int g[3];
+      ada_coords<D>(i, N, g);
+      bool cpt = true;
+#pragma unroll
+      for (int a = 0; a < D; ++a) cpt = cpt && (g[a] % 3 == 0);
+      if (!(hb && cpt)) {
+        cplx<double> dg = cz<double>();
+#pragma unroll
+        for (int e = 0; e < (1 << D); ++e) {
+          cplx<double> h[3], hi[3];
+          unsigned ci = 0, cs = 1;
+#pragma unroll
+          for (int a = 0; a < D; ++a) {
+            const int ca = g[a] - 1 + ((e >> a) & 1);
+            h[a] = hcell[ca];
+            hi[a] = hinv[ca];
+            ci += (unsigned)ca * cs;
+            cs *= (unsigned)n;
+          }
+          const int av = ((1 << D) - 1) ^ e;
+          cplx<double> m, k;
+          element_entry<D>(h, hi, av, av, m, k);
+          dg = dg + (k - rmul(phic != nullptr ? phic[ci] : phi0, m));
+        }
+        v = cdiv(omega * r[i], dg);
+      }
+    }
+    t[i] = v;
+  }
+}
+
+// y[C] = x[3C] (injection to the next coarser level, n_c cells per axis).
+template <int D>
+__global__ void ada_inject_kernel(int nc, const cplx<double>* __restrict__ x, cplx<double>* __restrict__ y) {
+  const int Nc = nc + 1, Nf = 3 * nc + 1;
+  unsigned total = 1;
+  for (int a = 0; a < D; ++a) total *= (unsigned)Nc;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    int g[3];
+    ada_coords<D>(i, Nc, g);
+    unsigned fi = 0, fs = 1;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      fi += (unsigned)(3 * g[a]) * fs;
+      fs *= (unsigned)Nf;
+    }
+    y[i] = x[fi];
+  }
+}
+
+// y = base + P x or base - P x (neg) on a level with n cells per axis, x on
+// the next coarser level; base may be null.  Integer d-linear weights over 3^D.
+template <int D>
+__global__ void ada_prolong_kernel(int n, const cplx<double>* __restrict__ x, const cplx<double>* base,
+                                   cplx<double>* y, int neg) {
+  const int N = n + 1, Nc = n / 3 + 1;
+  unsigned total = 1;
+  for (int a = 0; a < D; ++a) total *= (unsigned)N;
+  const double inv = D == 2 ? 1.0 / 9.0 : 1.0 / 27.0;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    int g[3];
+    ada_coords<D>(i, N, g);
+    cplx<double> s = cz<double>();
+#pragma unroll
+    for (int e = 0; e < (1 << D); ++e) {
+      int iw = 1;
+      unsigned ci = 0, cs = 1;
+      bool ok = true;
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        const int bit = (e >> a) & 1, o = g[a] % 3;
+        iw *= bit ? o : 3 - o;
+        const int cc = g[a] / 3 + bit;
+        ok = ok && cc < Nc;
+        ci += (unsigned)(ok ? cc : 0) * cs;
+        cs *= (unsigned)Nc;
+      }
+      if (iw != 0 && ok) s = rfma((double)iw, x[ci], s);
+    }
+    s = rmul(inv, s);
+    cplx<double> v = s;
+    if (base != nullptr) {
+      const cplx<double> bi = base[i];
+      v = neg ? cplx<double>{bi.x - s.x, bi.y - s.y} : bi + s;
+    } else if (neg) {
+      v = cplx<double>{-s.x, -s.y};
+    }
+    y[i] = v;
+  }
+}
+
+// u += c on the interior, zero on the Dirichlet boundary.
+template <int D>
+__global__ void ada_update_kernel(int n, cplx<double>* __restrict__ u, const cplx<double>* __restrict__ c) {
+  const int N = n + 1;
+  unsigned total = 1;
+  for (int a = 0; a < D; ++a) total *= (unsigned)N;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    int g[3];
+    ada_coords<D>(i, N, g);
+    bool inner = true;
+#pragma unroll
+    for (int a = 0; a < D; ++a) inner = inner && g[a] > 0 && g[a] < n;
+    u[i] = inner ? u[i] + c[i] : cz<double>();
+  }
+}
+
+// Hanging values: u(w) = (P u_c)(w) at interior vertices of existing cells
+// that carry no unknown (pu: P u_c on this level).
+template <int D>
+__global__ void ada_set_hanging_kernel(int n, const uint8_t* __restrict__ vcls, const cplx<double>* __restrict__ pu,
+                                       cplx<double>* __restrict__ u) {
+  const int N = n + 1;
+  unsigned total = 1;
+  for (int a = 0; a < D; ++a) total *= (unsigned)N;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    if (vcls[i] != kVertBound) continue;
+    int g[3];
+    ada_coords<D>(i, N, g);
+    bool inner = true;
+#pragma unroll
+    for (int a = 0; a < D; ++a) inner = inner && g[a] > 0 && g[a] < n;
+    if (inner) u[i] = pu[i];
+  }
+}
+
+// Coarse values at vertices carrying an unknown on the finer level take the
+// finer value (Eq. injection).
+template <int D>
+__global__ void ada_inject_unknown_kernel(int nc, const uint8_t* __restrict__ vcls_f,
+                                          const cplx<double>* __restrict__ uf, cplx<double>* __restrict__ uc) {
+  const int Nc = nc + 1, Nf = 3 * nc + 1;
+  unsigned total = 1;
+  for (int a = 0; a < D; ++a) total *= (unsigned)Nc;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    int g[3];
+    ada_coords<D>(i, Nc, g);
+    unsigned fi = 0, fs = 1;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      fi += (unsigned)(3 * g[a]) * fs;
+      fs *= (unsigned)Nf;
+    }
+    if (vcls_f[fi] == kVertUnknown) uc[i] = uf[fi];
+  }
+}
+
+// sum |r|^2 over the unknowns of this level that carry no unknown on the
+// next finer level (vcls_f, null on the finest level): the fine-grid
+// unknowns of the adaptive grid.  Deterministic last-block sum into *norm2.
+template <int D>
+__global__ void __launch_bounds__(256) ada_norm_kernel(int n, const cplx<double>* __restrict__ r,
+                                                       const uint8_t* __restrict__ vcls,
+                                                       const uint8_t* __restrict__ vcls_f, double* partial,
+                                                       unsigned* ticket, double* norm2) {
+  const int N = n + 1, Nf = 3 * n + 1;
+  unsigned total = 1;
+  for (int a = 0; a < D; ++a) total *= (unsigned)N;
+  double nrm = 0.0;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    if (vcls[i] != kVertUnknown) continue;
+    if (vcls_f != nullptr) {
+      int g[3];
+      ada_coords<D>(i, N, g);
+      unsigned fi = 0, fs = 1;
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        fi += (unsigned)(3 * g[a]) * fs;
+        fs *= (unsigned)Nf;
+      }
+      if (vcls_f[fi] == kVertUnknown) continue;
+    }
+    const cplx<double> v = r[i];
+    nrm = fma(v.x, v.x, fma(v.y, v.y, nrm));
+  }
+  __shared__ double s_red[8];
+  block_norm_finish<256>(nrm, s_red, partial, ticket, norm2, gridDim.x);
+}
+
+// y = x where the level's cells exist around the vertex (vcls != 0), else
+// keep y (assembling the fine-grid function level by level).
+template <int D>
+__global__ void ada_overwrite_kernel(int n, const uint8_t* __restrict__ vcls, const cplx<double>* __restrict__ x,
+                                     cplx<double>* __restrict__ y) {
+  const int N = n + 1;
+  unsigned total = 1;
+  for (int a = 0; a < D; ++a) total *= (unsigned)N;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x)
+    if (vcls[i] != kVertNone) y[i] = x[i];
+}
+
+}  // namespace mg

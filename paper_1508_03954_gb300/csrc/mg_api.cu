@@ -26,6 +26,7 @@
 #include "mg_maxnorm.cuh"
 #include "mg_dim4.cuh"
 #include "mg_io.cuh"
+#include "mg_adaptive.cuh"
 #include <map>
 
 using mg::cplx;
@@ -154,6 +155,34 @@ struct Hier4 {
   long long nkern = 0;
 };
 
+// Adaptive spacetree (mg_adaptive.cuh): dense arrays over each level's full
+// grid with a flag per cell and a class per vertex.
+struct LevA {
+  int n = 0;
+  size_t nv = 0;
+  cplx<double>* u = nullptr;
+  cplx<double>* f = nullptr;     // nodal f sampled on this level
+  cplx<double>* r = nullptr;     // generating-system residual
+  cplx<double>* t = nullptr;     // T du
+  cplx<double>* corr = nullptr;  // level 1: aliases t
+  uint8_t* cellf = nullptr;      // kCellExists | kCellRefined per cell
+  uint8_t* vcls = nullptr;       // kVertNone / kVertBound / kVertUnknown per vertex
+  cplx<double>* hcell = nullptr; // complex width per axis index
+  cplx<double>* hinv = nullptr;  // its inverse
+  double* phic = nullptr;        // per-cell shift (null: constant)
+  size_t unknowns = 0;           // vertices carrying an unknown
+  size_t leaf_unknowns = 0;      // ... and none on the next finer level
+};
+
+struct HierA {
+  std::vector<LevA> lev;       // 1..L
+  cplx<double>* T[2] = {};     // fine-size temporaries
+  double* partial = nullptr;
+  unsigned* ticket = nullptr;
+  double* norm2 = nullptr;     // [l]: |r_l|^2 over the level's fine-grid unknowns
+  std::vector<void*> allocs;
+};
+
 }  // namespace
 
 struct mg_ctx {
@@ -165,6 +194,7 @@ struct mg_ctx {
   Hier<float> h32;
   Hier4<double>* h4 = nullptr;         // d = 4
   Hier4<float>* h4f = nullptr;         // d = 4, complex64 inner cycles
+  HierA* ada = nullptr;                // adaptive spacetree (mg_create_adaptive)
   int precision = MG_C128;
   int inner_cycles = 4;
   double r0 = -1.0;                    // reference residual norm
@@ -1435,7 +1465,10 @@ int check_timeout(mg_ctx* c) {
 // synchronising.
 cudaError_t d4_residual(mg_ctx* c, int slot);
 
+int ada_residual_norm(mg_ctx* c, double* out);
+
 int fine_residual(mg_ctx* c, int s, double* out) {
+  if (c->ada != nullptr) return ada_residual_norm(c, out);
   if (c->d == 4) {
     cudaError_t e4 = d4_residual(c, 1);
     if (e4 == cudaSuccess)
@@ -1876,7 +1909,242 @@ int d4_refine(mg_ctx* c, int hb, int hier, const cplx<double>* omega, double tol
   }
 }
 
+// ------------------------------------------------------------------ adaptive
+void ada_free(HierA* H) {
+  if (H == nullptr) return;
+  for (void* p : H->allocs) cudaFree(p);
+  delete H;
+}
+
+// Cells, vertex classes and operator data of every level of the adaptive
+// tree.  refine: the flags of levels 1..L-1, level l's (3^l)^d cells x fastest,
+// concatenated; flags of cells that do not exist are ignored.
+int ada_build(mg_ctx* c, const unsigned char* refine) {
+  HierA* H = new (std::nothrow) HierA();
+  if (H == nullptr) return fail(c, MG_ERR_OOM, "host allocation failed");
+  c->ada = H;
+  const int d = c->d, L = c->L;
+  bool varphi = false;
+  for (size_t i = 1; i < c->k2.size() && !varphi; ++i) varphi = c->k2[i] != c->k2[0];
+  H->lev.resize(L + 1);
+  std::vector<uint8_t> cells(ipow(3, d), 1);  // level 1: every cell
+  size_t off = 0;
+  int rc;
+  for (int l = 1; l <= L; ++l) {
+    LevA& V = H->lev[l];
+    V.n = (int)ipow(3, l);
+    const int n = V.n, N = n + 1;
+    V.nv = (size_t)ipow(N, d);
+    const size_t ncell = (size_t)ipow(n, d);
+    std::vector<uint8_t> cellf(ncell, 0);
+    for (size_t ci = 0; ci < ncell; ++ci) {
+      const bool ex = cells[ci] != 0;
+      const bool rf = l < L && ex && refine[off + ci] != 0;
+      cellf[ci] = (uint8_t)((ex ? mg::kCellExists : 0) | (rf ? mg::kCellRefined : 0));
+    }
+    if (l < L) off += ncell;
+    // vertex classes from the number of existing cells around each vertex
+    std::vector<uint8_t> vcls(V.nv, 0);
+    for (size_t vi = 0; vi < V.nv; ++vi) {
+      int g[3] = {0, 0, 0};
+      size_t r = vi;
+      bool inner = true;
+      for (int a = 0; a < d; ++a) {
+        g[a] = (int)(r % N);
+        r /= N;
+        inner = inner && g[a] > 0 && g[a] < n;
+      }
+      int cnt = 0, tot = 0;
+      for (int e = 0; e < (1 << d); ++e) {
+        size_t ci = 0, cs = 1;
+        bool in = true;
+        for (int a = 0; a < d; ++a) {
+          const int ca = g[a] - 1 + ((e >> a) & 1);
+          in = in && ca >= 0 && ca < n;
+          ci += (size_t)(in ? ca : 0) * cs;
+          cs *= (size_t)n;
+        }
+        if (!in) continue;
+        ++tot;
+        cnt += (cellf[ci] & mg::kCellExists) ? 1 : 0;
+      }
+      vcls[vi] = cnt == 0 ? mg::kVertNone : ((inner && cnt == (1 << d)) ? mg::kVertUnknown : mg::kVertBound);
+      (void)tot;
+    }
+    for (size_t vi = 0; vi < V.nv; ++vi) V.unknowns += vcls[vi] == mg::kVertUnknown;
+    const size_t bytes = V.nv * sizeof(cplx<double>);
+    for (cplx<double>** p : {&V.u, &V.f, &V.r, &V.t}) {
+      if ((rc = d4_alloc(c, *H, (void**)p, bytes)) != MG_OK) return rc;
+    }
+    if (l == 1) {
+      V.corr = V.t;
+    } else if ((rc = d4_alloc(c, *H, (void**)&V.corr, bytes)) != MG_OK) {
+      return rc;
+    }
+    if ((rc = d4_upload(c, *H, &V.cellf, cellf)) != MG_OK) return rc;
+    if ((rc = d4_upload(c, *H, &V.vcls, vcls)) != MG_OK) return rc;
+    const std::vector<uint8_t> rot = layer_flags(c, n);
+    const Widths wd = widths(c, n);
+    std::vector<cplx<double>> hc(n), hi(n);
+    for (int k = 0; k < n; ++k) {
+      const cd h = rot[k] ? wd.rot : wd.in;
+      hc[k] = cplx<double>{h.real(), h.imag()};
+      const cd q = 1.0 / h;
+      hi[k] = cplx<double>{q.real(), q.imag()};
+    }
+    if ((rc = d4_upload(c, *H, &V.hcell, hc)) != MG_OK) return rc;
+    if ((rc = d4_upload(c, *H, &V.hinv, hi)) != MG_OK) return rc;
+    if (varphi) {
+      std::vector<double> ph = cell_shift<double>(c, l);
+      if ((rc = d4_upload(c, *H, &V.phic, ph)) != MG_OK) return rc;
+    }
+    // children of refined cells exist on the next level
+    if (l < L) {
+      const int nf = 3 * n;
+      std::vector<uint8_t> next((size_t)ipow(nf, d), 0);
+      for (size_t fi = 0; fi < next.size(); ++fi) {
+        size_t r = fi, ci = 0, cs = 1;
+        for (int a = 0; a < d; ++a) {
+          ci += (r % nf) / 3 * cs;
+          r /= nf;
+          cs *= (size_t)n;
+        }
+        next[fi] = (cellf[ci] & mg::kCellRefined) ? 1 : 0;
+      }
+      cells.swap(next);
+    }
+  }
+  const size_t fb = H->lev[L].nv * sizeof(cplx<double>);
+  for (int k = 0; k < 2; ++k)
+    if ((rc = d4_alloc(c, *H, (void**)&H->T[k], fb)) != MG_OK) return rc;
+  if ((rc = d4_alloc(c, *H, (void**)&H->partial, 152 * 16 * sizeof(double))) != MG_OK) return rc;
+  if ((rc = d4_alloc(c, *H, (void**)&H->ticket, 4 * sizeof(unsigned))) != MG_OK) return rc;
+  if ((rc = d4_alloc(c, *H, (void**)&H->norm2, 32 * sizeof(double))) != MG_OK) return rc;
+  return MG_OK;
+}
+
+template <int D>
+cudaError_t ada_residuals(mg_ctx* c) {
+  HierA& H = *c->ada;
+  const int L = c->L;
+  const double phi0 = c->k2[0];
+  for (int l = L; l >= 1; --l) {
+    LevA& V = H.lev[l];
+    c->launches += 2;
+    mg::ada_residual_kernel<D><<<grid_for(V.nv), kThreads, 0, c->stream>>>(
+        V.n, V.u, V.f, V.cellf, V.vcls, V.hcell, V.hinv, V.phic, phi0, l < L ? H.lev[l + 1].r : nullptr, V.r);
+    mg::ada_norm_kernel<D><<<grid_for(V.nv), kThreads, 0, c->stream>>>(
+        V.n, V.r, V.vcls, l < L ? H.lev[l + 1].vcls : nullptr, H.partial, H.ticket, H.norm2 + l);
+  }
+  return cudaGetLastError();
+}
+
+// Hanging values from the coarser level (coarse to fine), then injection of
+// values that carry an unknown on the finer level (fine to coarse).
+template <int D>
+cudaError_t ada_invariants(mg_ctx* c) {
+  HierA& H = *c->ada;
+  const int L = c->L;
+  for (int l = 2; l <= L; ++l) {
+    LevA& V = H.lev[l];
+    c->launches += 2;
+    mg::ada_prolong_kernel<D><<<grid_for(V.nv), kThreads, 0, c->stream>>>(V.n, H.lev[l - 1].u, nullptr, H.T[0], 0);
+    mg::ada_set_hanging_kernel<D><<<grid_for(V.nv), kThreads, 0, c->stream>>>(V.n, V.vcls, H.T[0], V.u);
+  }
+  for (int l = L - 1; l >= 1; --l) {
+    LevA& V = H.lev[l];
+    ++c->launches;
+    mg::ada_inject_unknown_kernel<D><<<grid_for(V.nv), kThreads, 0, c->stream>>>(V.n, H.lev[l + 1].vcls,
+                                                                                 H.lev[l + 1].u, V.u);
+  }
+  return cudaGetLastError();
+}
+
+template <int D>
+cudaError_t ada_enqueue_cycle(mg_ctx* c, int hb, int hier, const cplx<double>* omega) {
+  HierA& H = *c->ada;
+  const int L = c->L;
+  const double phi0 = c->k2[0];
+  cudaError_t e = ada_residuals<D>(c);
+  for (int l = 1; l <= L && e == cudaSuccess; ++l) {
+    LevA& V = H.lev[l];
+    ++c->launches;
+    mg::ada_jacobi_kernel<D><<<grid_for(V.nv), kThreads, 0, c->stream>>>(V.n, V.r, V.vcls, V.hcell, V.hinv, V.phic,
+                                                                       phi0, omega[l - 1], hb, V.t);
+    if (l > 1) {
+      LevA& W = H.lev[l - 1];
+      if (hier) {
+        // BPX transfer: T du = du - P I du
+        c->launches += 2;
+        mg::ada_inject_kernel<D><<<grid_for(W.nv), kThreads, 0, c->stream>>>(W.n, V.t, H.T[0]);
+        mg::ada_prolong_kernel<D><<<grid_for(V.nv), kThreads, 0, c->stream>>>(V.n, H.T[0], V.t, V.t, 1);
+      }
+      ++c->launches;
+      mg::ada_prolong_kernel<D><<<grid_for(V.nv), kThreads, 0, c->stream>>>(V.n, W.corr, V.t, V.corr, 0);
+    }
+    e = cudaGetLastError();
+  }
+  for (int l = 1; l <= L && e == cudaSuccess; ++l) {
+    LevA& V = H.lev[l];
+    ++c->launches;
+    mg::ada_update_kernel<D><<<grid_for(V.nv), kThreads, 0, c->stream>>>(V.n, V.u, V.corr);
+  }
+  if (e == cudaSuccess) e = ada_invariants<D>(c);
+  return e == cudaSuccess ? cudaGetLastError() : e;
+}
+
+int ada_norm_host(mg_ctx* c, double* out) {
+  HierA& H = *c->ada;
+  // the pinned buffer holds 4 doubles: copy the level norms in groups
+  double tot = 0.0;
+  for (int l0 = 1; l0 <= c->L; l0 += 4) {
+    const int cnt = std::min(4, c->L - l0 + 1);
+    MG_CUDA(c, cudaMemcpyAsync(c->host_norm, H.norm2 + l0, sizeof(double) * cnt, cudaMemcpyDeviceToHost,
+                               c->stream));
+    MG_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < cnt; ++k) tot += c->host_norm[k];
+  }
+  *out = std::sqrt(tot);
+  return MG_OK;
+}
+
+int ada_residual_norm(mg_ctx* c, double* out) {
+  cudaError_t e = c->d == 2 ? ada_residuals<2>(c) : ada_residuals<3>(c);
+  if (e != cudaSuccess) return fail(c, MG_ERR_CUDA, std::string("residual: ") + cudaGetErrorString(e));
+  return ada_norm_host(c, out);
+}
+
+int ada_cycle(mg_ctx* c, int hb, int hier, const cplx<double>* omega) {
+  cudaError_t e = c->d == 2 ? ada_enqueue_cycle<2>(c, hb, hier, omega) : ada_enqueue_cycle<3>(c, hb, hier, omega);
+  if (e != cudaSuccess) return fail(c, MG_ERR_CUDA, std::string("cycle launch: ") + cudaGetErrorString(e));
+  return MG_OK;
+}
+
+// The fine-grid function on the uniform finest grid: level 1 interpolated
+// up, each level's values written where its cells exist.
+template <int D>
+cudaError_t ada_composite(mg_ctx* c, cplx<double>* out) {
+  HierA& H = *c->ada;
+  const int L = c->L;
+  cudaError_t e = cudaMemcpyAsync(H.T[0], H.lev[1].u, H.lev[1].nv * sizeof(cplx<double>), cudaMemcpyDeviceToDevice,
+                                  c->stream);
+  int cur = 0;
+  for (int l = 2; l <= L && e == cudaSuccess; ++l) {
+    LevA& V = H.lev[l];
+    cplx<double>* dst = l == L ? out : H.T[1 - cur];
+    c->launches += 2;
+    mg::ada_prolong_kernel<D><<<grid_for(V.nv), kThreads, 0, c->stream>>>(V.n, H.T[cur], nullptr, dst, 0);
+    mg::ada_overwrite_kernel<D><<<grid_for(V.nv), kThreads, 0, c->stream>>>(V.n, V.vcls, V.u, dst);
+    cur = 1 - cur;
+    e = cudaGetLastError();
+  }
+  if (L == 1 && e == cudaSuccess)
+    e = cudaMemcpyAsync(out, H.T[0], H.lev[1].nv * sizeof(cplx<double>), cudaMemcpyDeviceToDevice, c->stream);
+  return e;
+}
+
 const char* kNot4 = " is not available for d = 4 (the four-dimensional path runs complex128 cycles)";
+const char* kNotA = " is not available for an adaptive grid (mg_create_adaptive contexts run complex128 cycles)";
 
 }  // namespace
 
@@ -1893,8 +2161,8 @@ int mg_create(int d, int depth, const double* k2_field, double theta, double lay
   return mg_create_ecs(d, depth, k2_field, theta, 0.0, layer_width, layer_width, out);
 }
 
-int mg_create_ecs(int d, int depth, const double* k2_field, double theta_layer, double theta_interior,
-                  double width_lo, double width_hi, mg_ctx** out) {
+static int create_ctx(int d, int depth, const double* k2_field, double theta_layer, double theta_interior,
+                      double width_lo, double width_hi, const unsigned char* refine, mg_ctx** out) {
   g_create_err.clear();
   if (out == nullptr) return fail(nullptr, MG_ERR_INVALID, "out is NULL");
   *out = nullptr;
@@ -1932,7 +2200,8 @@ int mg_create_ecs(int d, int depth, const double* k2_field, double theta_layer, 
   c->wlo = width_lo;
   c->whi = width_hi;
   c->k2.assign(k2_field, k2_field + nvf);
-  int rc = d == 4 ? d4_build<double>(c, c->h4) : build_hier<double>(c, c->h64);
+  int rc = refine != nullptr ? ada_build(c, refine)
+                              : (d == 4 ? d4_build<double>(c, c->h4) : build_hier<double>(c, c->h64));
   if (rc == MG_OK) {
     cudaError_t e = cudaMalloc(&c->f_dev, nvf * sizeof(cplx<double>));
     if (e == cudaSuccess) e = cudaMemset(c->f_dev, 0, nvf * sizeof(cplx<double>));
@@ -1958,6 +2227,22 @@ int mg_create_ecs(int d, int depth, const double* k2_field, double theta_layer, 
   return MG_OK;
 }
 
+int mg_create_ecs(int d, int depth, const double* k2_field, double theta_layer, double theta_interior,
+                  double width_lo, double width_hi, mg_ctx** out) {
+  return create_ctx(d, depth, k2_field, theta_layer, theta_interior, width_lo, width_hi, nullptr, out);
+}
+
+int mg_create_adaptive(int d, int depth, const double* k2_field, double theta, double layer_width,
+                       const unsigned char* refine, mg_ctx** out) {
+  g_create_err.clear();
+  if (out != nullptr) *out = nullptr;
+  if (refine == nullptr) return fail(nullptr, MG_ERR_INVALID, "refine is NULL");
+  if (d != 2 && d != 3) return fail(nullptr, MG_ERR_INVALID, "an adaptive grid takes d = 2 or 3");
+  if (!(layer_width >= 0.0 && layer_width <= 0.5))
+    return fail(nullptr, MG_ERR_INVALID, "layer_width must be in [0, 0.5]");
+  return create_ctx(d, depth, k2_field, theta, 0.0, layer_width, layer_width, refine, out);
+}
+
 void mg_destroy(mg_ctx* c) {
   if (c == nullptr) return;
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
@@ -1969,6 +2254,7 @@ void mg_destroy(mg_ctx* c) {
   free_hier(c->h32);
   d4_free(c->h4);
   d4_free(c->h4f);
+  ada_free(c->ada);
   if (c->f_dev) cudaFree(c->f_dev);
   if (c->scratch) cudaFree(c->scratch);
   if (c->rvec) cudaFree(c->rvec);
@@ -1985,6 +2271,24 @@ int mg_set_stream(mg_ctx* c, void* s) {
 int mg_set_rhs(mg_ctx* c, const mg_c128* f, int on_device) {
   if (check_ctx(c)) return MG_ERR_INVALID;
   if (f == nullptr) return fail(c, MG_ERR_INVALID, "f is NULL");
+  if (c->ada != nullptr) {
+    HierA& H = *c->ada;
+    const LevA& F = H.lev[c->L];
+    MG_CUDA(c, cudaMemcpyAsync(F.f, f, F.nv * sizeof(mg_c128),
+                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    for (int l = c->L - 1; l >= 1; --l) {
+      ++c->launches;
+      if (c->d == 2)
+        mg::ada_inject_kernel<2><<<grid_for(H.lev[l].nv), kThreads, 0, c->stream>>>(H.lev[l].n, H.lev[l + 1].f,
+                                                                                   H.lev[l].f);
+      else
+        mg::ada_inject_kernel<3><<<grid_for(H.lev[l].nv), kThreads, 0, c->stream>>>(H.lev[l].n, H.lev[l + 1].f,
+                                                                                   H.lev[l].f);
+    }
+    MG_CUDA(c, cudaGetLastError());
+    c->r0 = -1.0;
+    return MG_OK;
+  }
   const size_t nv = c->d == 4 ? c->h4->lev[c->L].nv : c->h64.lev[c->L].nv;
   const cplx<double>* fv = on_device ? nullptr : pinned_view(reinterpret_cast<const cplx<double>*>(f));
   if (fv != nullptr) {
@@ -2009,6 +2313,35 @@ int mg_set_rhs(mg_ctx* c, const mg_c128* f, int on_device) {
 int mg_set_solution(mg_ctx* c, const mg_c128* u, int on_device) {
   if (check_ctx(c)) return MG_ERR_INVALID;
   if (u == nullptr) return fail(c, MG_ERR_INVALID, "u is NULL");
+  if (c->ada != nullptr) {
+    // the uniform fine-grid samples on every level, then the invariants
+    HierA& H = *c->ada;
+    const LevA& F = H.lev[c->L];
+    MG_CUDA(c, cudaMemcpyAsync(F.u, u, F.nv * sizeof(mg_c128),
+                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    for (int l = c->L; l >= 1; --l) {
+      const LevA& V = H.lev[l];
+      if (l < c->L) {
+        ++c->launches;
+        if (c->d == 2)
+          mg::ada_inject_kernel<2><<<grid_for(V.nv), kThreads, 0, c->stream>>>(V.n, H.lev[l + 1].u, V.u);
+        else
+          mg::ada_inject_kernel<3><<<grid_for(V.nv), kThreads, 0, c->stream>>>(V.n, H.lev[l + 1].u, V.u);
+      }
+    }
+    for (int l = 1; l <= c->L; ++l) {
+      const LevA& V = H.lev[l];
+      const int ring = c->d == 2 ? 4 * V.n : 6 * (V.n + 1) * (V.n + 1);
+      ++c->launches;
+      if (c->d == 2)
+        mg::zero_ring_kernel<2><<<(ring + 255) / 256, 256, 0, c->stream>>>(V.n, V.u);
+      else
+        mg::zero_ring_kernel<3><<<(ring + 255) / 256, 256, 0, c->stream>>>(V.n, V.u);
+    }
+    MG_CUDA(c, c->d == 2 ? ada_invariants<2>(c) : ada_invariants<3>(c));
+    c->r0 = -1.0;
+    return MG_OK;
+  }
   if (c->d == 4) {
     const Lev4<double>& V = c->h4->lev[c->L];
     MG_CUDA(c, cudaMemcpyAsync(V.u, u, V.nv * sizeof(mg_c128),
@@ -2049,6 +2382,17 @@ int mg_set_solution(mg_ctx* c, const mg_c128* u, int on_device) {
 int mg_get_solution(mg_ctx* c, mg_c128* out, int on_device) {
   if (check_ctx(c)) return MG_ERR_INVALID;
   if (out == nullptr) return fail(c, MG_ERR_INVALID, "out is NULL");
+  if (c->ada != nullptr) {
+    const size_t nv = c->ada->lev[c->L].nv;
+    if (on_device) {
+      MG_CUDA(c, c->d == 2 ? ada_composite<2>(c, (cplx<double>*)out) : ada_composite<3>(c, (cplx<double>*)out));
+      return MG_OK;
+    }
+    MG_CUDA(c, c->d == 2 ? ada_composite<2>(c, c->scratch) : ada_composite<3>(c, c->scratch));
+    MG_CUDA(c, cudaMemcpyAsync(out, c->scratch, nv * sizeof(mg_c128), cudaMemcpyDeviceToHost, c->stream));
+    MG_CUDA(c, cudaStreamSynchronize(c->stream));
+    return MG_OK;
+  }
   if (c->d == 4) {
     const Lev4<double>& V = c->h4->lev[c->L];
     MG_CUDA(c, cudaMemcpyAsync(out, V.u, V.nv * sizeof(mg_c128),
@@ -2078,6 +2422,14 @@ int mg_get_level(mg_ctx* c, int level, int which, mg_c128* out, int on_device) {
   if (check_ctx(c)) return MG_ERR_INVALID;
   if (out == nullptr || level < 1 || level > c->L || (which != 0 && which != 1))
     return fail(c, MG_ERR_INVALID, "bad level/which/out");
+  if (c->ada != nullptr) {
+    // which = 0: the level's values, 1: its generating-system residual
+    const LevA& V = c->ada->lev[level];
+    MG_CUDA(c, cudaMemcpyAsync(out, which == 0 ? V.u : V.r, V.nv * sizeof(mg_c128),
+                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    if (!on_device) MG_CUDA(c, cudaStreamSynchronize(c->stream));
+    return MG_OK;
+  }
   if (level == c->L && which == 0) return mg_get_solution(c, out, on_device);
   if (c->d == 4) {
     const Lev4<double>& V = c->h4->lev[level];
@@ -2099,6 +2451,7 @@ int mg_cycle(mg_ctx* c, int variant, const mg_c128* omega, int transfer) {
   if (omega == nullptr) return fail(c, MG_ERR_INVALID, "omega is NULL");
   int hb, hier;
   if (decode_variant(c, variant, transfer, &hb, &hier)) return MG_ERR_INVALID;
+  if (c->ada != nullptr) return ada_cycle(c, hb, hier, reinterpret_cast<const cplx<double>*>(omega));
   if (c->d == 4) return d4_cycle(c, *c->h4, hb, hier, reinterpret_cast<const cplx<double>*>(omega));
   return run_cycle(c, c->h64, c->L, hb, hier, reinterpret_cast<const cplx<double>*>(omega));
 }
@@ -2116,6 +2469,7 @@ int mg_residual_norm(mg_ctx* c, double* abs_l2, double* rel_l2) {
 
 int mg_residual_max(mg_ctx* c, double* abs_max) {
   if (check_ctx(c)) return MG_ERR_INVALID;
+  if (c->ada != nullptr) return fail(c, MG_ERR_INVALID, std::string("mg_residual_max") + kNotA);
   if (abs_max == nullptr) return fail(c, MG_ERR_INVALID, "abs_max is NULL");
   if (c->d == 4) {
     Hier4<double>& H4 = *c->h4;
@@ -2151,6 +2505,7 @@ int mg_set_precision(mg_ctx* c, int precision, int inner_cycles) {
   if (check_ctx(c)) return MG_ERR_INVALID;
   if (precision != MG_C128 && precision != MG_C64_REFINE) return fail(c, MG_ERR_INVALID, "bad precision");
   if (inner_cycles < 1 || inner_cycles > 1000) return fail(c, MG_ERR_INVALID, "inner_cycles out of range");
+  if (c->ada != nullptr && precision != MG_C128) return fail(c, MG_ERR_INVALID, std::string("MG_C64_REFINE") + kNotA);
   c->precision = precision;
   c->inner_cycles = inner_cycles;
   if (c->d == 4) {
@@ -2205,9 +2560,23 @@ int mg_solve(mg_ctx* c, int variant, const mg_c128* omega, int transfer, double 
       if (done >= max_cycles) return finish(MG_NOT_CONVERGED);
       const int m = std::min(check, max_cycles - done);
       for (int k = 0; k < m; ++k) {
-        rc = c->d == 4 ? d4_cycle(c, *c->h4, hb, hier, om) : run_cycle(c, c->h64, L, hb, hier, om);
+        rc = c->ada != nullptr ? ada_cycle(c, hb, hier, om)
+                               : (c->d == 4 ? d4_cycle(c, *c->h4, hb, hier, om) : run_cycle(c, c->h64, L, hb, hier, om));
         if (rc != MG_OK) return rc;
         ++done;
+      }
+      if (c->ada != nullptr) {
+        // the residual of the iterate that entered the last cycle
+        double r;
+        if ((rc = ada_norm_host(c, &r)) != MG_OK) return rc;
+        const double prev = r / (c->r0 > 0 ? c->r0 : 1.0);
+        if (diverged(prev) || prev <= tol || done >= max_cycles) {
+          if ((rc = fine_residual(c, L, &r)) != MG_OK) return rc;
+          rel = c->r0 > 0 ? r / c->r0 : 0.0;
+        } else {
+          rel = prev;
+        }
+        continue;
       }
       MG_CUDA(c, cudaMemcpyAsync(c->host_norm, c->d == 4 ? c->h4->norm2 : c->h64.norm2, sizeof(double),
                                  cudaMemcpyDeviceToHost, c->stream));
@@ -2290,6 +2659,7 @@ int mg_solve(mg_ctx* c, int variant, const mg_c128* omega, int transfer, double 
 int mg_fmg(mg_ctx* c, int variant, const mg_c128* omega, int transfer, int cycles_per_stage) {
   if (check_ctx(c)) return MG_ERR_INVALID;
   if (c->d == 4) return fail(c, MG_ERR_INVALID, std::string("mg_fmg") + kNot4);
+  if (c->ada != nullptr) return fail(c, MG_ERR_INVALID, std::string("mg_fmg") + kNotA);
   if (omega == nullptr || cycles_per_stage < 0) return fail(c, MG_ERR_INVALID, "bad omega/cycles_per_stage");
   int hb, hier;
   if (decode_variant(c, variant, transfer, &hb, &hier)) return MG_ERR_INVALID;
@@ -2373,6 +2743,7 @@ int mg_debug_unsatisfiable_wait(mg_ctx* c, int enable) {
 int mg_set_trace(mg_ctx* c, int enable) {
   if (check_ctx(c)) return MG_ERR_INVALID;
   if (c->d == 4) return fail(c, MG_ERR_INVALID, std::string("mg_set_trace") + kNot4);
+  if (c->ada != nullptr) return fail(c, MG_ERR_INVALID, std::string("mg_set_trace") + kNotA);
   if (enable && c->trace == nullptr)
     MG_CUDA(c, cudaMalloc(&c->trace, 4ull * (kTraceFine + kTraceChain) * sizeof(unsigned long long)));
   if (enable) MG_CUDA(c, cudaMemset(c->trace, 0, 4ull * (kTraceFine + kTraceChain) * sizeof(unsigned long long)));
@@ -2396,6 +2767,14 @@ int mg_get_trace(mg_ctx* c, unsigned long long* out, int fine_slots, int chain_s
 
 int mg_last_cycle_norm(mg_ctx* c, double* abs_l2, double* rel_l2) {
   if (check_ctx(c)) return MG_ERR_INVALID;
+  if (c->ada != nullptr) {
+    double r;
+    int rc = ada_norm_host(c, &r);
+    if (rc != MG_OK) return rc;
+    if (abs_l2) *abs_l2 = r;
+    if (rel_l2) *rel_l2 = c->r0 > 0 ? r / c->r0 : -1.0;
+    return MG_OK;
+  }
   MG_CUDA(c, cudaMemcpyAsync(c->host_norm, c->d == 4 ? c->h4->norm2 : c->h64.norm2, sizeof(double),
                              cudaMemcpyDeviceToHost, c->stream));
   MG_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -2433,6 +2812,7 @@ int mg_get_stats(mg_ctx* c, long long* launches, int* fine_sweeps, double* fine_
 int mg_set_k2(mg_ctx* c, const double* k2) {
   if (check_ctx(c)) return MG_ERR_INVALID;
   if (c->d == 4) return fail(c, MG_ERR_INVALID, std::string("mg_set_k2") + kNot4);
+  if (c->ada != nullptr) return fail(c, MG_ERR_INVALID, std::string("mg_set_k2") + kNotA);
   if (k2 == nullptr) return fail(c, MG_ERR_INVALID, "k2 is NULL");
   if (!c->h64.varphi)
     return fail(c, MG_ERR_INVALID, "the context was created with a constant k^2; create a new context");
@@ -2455,6 +2835,7 @@ int mg_set_k2(mg_ctx* c, const double* k2) {
 
 int mg_set_rhs_vector(mg_ctx* c, const mg_c128* b, int on_device) {
   if (check_ctx(c)) return MG_ERR_INVALID;
+  if (c->ada != nullptr) return fail(c, MG_ERR_INVALID, std::string("mg_set_rhs_vector") + kNotA);
   if (b == nullptr) return fail(c, MG_ERR_INVALID, "b is NULL");
   if (c->d == 4) {
     const Lev4<double>& V = c->h4->lev[c->L];
@@ -2518,6 +2899,7 @@ int sample_stencil(mg_ctx* c, int npts, const double* xyz, const mg_c128* w,
 int mg_sample(mg_ctx* c, int npts, const double* xyz, const mg_c128* w, mg_c128* out) {
   if (check_ctx(c)) return MG_ERR_INVALID;
   if (c->d == 4) return fail(c, MG_ERR_INVALID, std::string("mg_sample") + kNot4);
+  if (c->ada != nullptr) return fail(c, MG_ERR_INVALID, std::string("mg_sample") + kNotA);
   if (npts < 1 || xyz == nullptr || w == nullptr || out == nullptr)
     return fail(c, MG_ERR_INVALID, "bad sample arguments");
   std::map<long long, cd> acc;
@@ -2543,6 +2925,7 @@ int mg_sample(mg_ctx* c, int npts, const double* xyz, const mg_c128* w, mg_c128*
 int mg_set_rhs_samples(mg_ctx* c, int npts, const double* xyz, const mg_c128* w) {
   if (check_ctx(c)) return MG_ERR_INVALID;
   if (c->d == 4) return fail(c, MG_ERR_INVALID, std::string("mg_set_rhs_samples") + kNot4);
+  if (c->ada != nullptr) return fail(c, MG_ERR_INVALID, std::string("mg_set_rhs_samples") + kNotA);
   if (npts < 1 || xyz == nullptr || w == nullptr) return fail(c, MG_ERR_INVALID, "bad sample arguments");
   std::map<long long, cd> acc;
   int rc = sample_stencil(c, npts, xyz, w, acc);
@@ -2556,6 +2939,7 @@ int mg_adjoint_grad(mg_ctx* c, const mg_c128* u, const mg_c128* lambda, mg_c128 
                     double* dJdf) {
   if (check_ctx(c)) return MG_ERR_INVALID;
   if (c->d == 4) return fail(c, MG_ERR_INVALID, std::string("mg_adjoint_grad") + kNot4);
+  if (c->ada != nullptr) return fail(c, MG_ERR_INVALID, std::string("mg_adjoint_grad") + kNotA);
   if (u == nullptr || lambda == nullptr || (dJdV == nullptr && dJdf == nullptr))
     return fail(c, MG_ERR_INVALID, "u, lambda and at least one output are required");
   auto& V = c->h64.lev[c->L];
@@ -2635,6 +3019,7 @@ extern "C" int mg_residual_noalloc(mg_ctx* c, const mg_c128* u, const mg_c128* b
                                    double* norm2) {
   if (check_ctx(c)) return MG_ERR_INVALID;
   if (c->d == 4) return fail(c, MG_ERR_INVALID, std::string("mg_residual_noalloc") + kNot4);
+  if (c->ada != nullptr) return fail(c, MG_ERR_INVALID, std::string("mg_residual_noalloc") + kNotA);
   if (u == nullptr || b == nullptr || norm2 == nullptr)
     return fail(c, MG_ERR_INVALID, "u, b and norm2 must be device pointers");
   auto& H = c->h64;

@@ -25,7 +25,7 @@ STATUS_NAMES = {0: "MG_OK", 1: "MG_ERR_INVALID", 2: "MG_ERR_CUDA", 3: "MG_ERR_OO
                 4: "MG_DIVERGED", 5: "MG_NOT_CONVERGED", 6: "MG_ERR_TIMEOUT"}
 
 # every symbol include/mg.h declares
-EXPORTS = ["mg_create", "mg_create_ecs", "mg_destroy", "mg_set_stream", "mg_set_rhs", "mg_set_solution",
+EXPORTS = ["mg_create", "mg_create_ecs", "mg_create_adaptive", "mg_destroy", "mg_set_stream", "mg_set_rhs", "mg_set_solution",
            "mg_get_solution", "mg_cycle", "mg_residual_norm", "mg_residual_max", "mg_last_cycle_norm", "mg_solve", "mg_set_precision",
            "mg_fmg", "mg_omega_scheme", "mg_get_level", "mg_set_timing", "mg_get_stats",
            "mg_set_trace", "mg_get_trace", "mg_set_spin_limit", "mg_debug_unsatisfiable_wait", "mg_set_k2", "mg_set_rhs_vector", "mg_sample",
@@ -66,6 +66,7 @@ def load(path: str | None = None):
     sig = {
         "mg_create": (ip, [ip, ip, ctypes.POINTER(dp), dp, dp, ctypes.POINTER(vp)]),
         "mg_create_ecs": (ip, [ip, ip, ctypes.POINTER(dp), dp, dp, dp, dp, ctypes.POINTER(vp)]),
+        "mg_create_adaptive": (ip, [ip, ip, ctypes.POINTER(dp), dp, dp, ctypes.c_char_p, ctypes.POINTER(vp)]),
         "mg_destroy": (None, [vp]),
         "mg_set_stream": (ip, [vp, vp]),
         "mg_set_rhs": (ip, [vp, vp, ip]),
@@ -189,6 +190,35 @@ class Solver:
         self._h = h
         self._view = h
         self._L = L
+
+    @classmethod
+    def adaptive(cls, d, depth, k2_field, theta, layer_width, refine):
+        """A solver on an adaptive spacetree (mg_create_adaptive): refine maps
+        level l = 1..depth-1 to a boolean array of its (3^l,)*d cells (numpy
+        axis order, last axis = x)."""
+        L = load()
+        self = cls.__new__(cls)
+        self.d, self.depth = d, depth
+        self.n = 3 ** depth
+        self.shape = (self.n + 1,) * d
+        self.nv = (self.n + 1) ** d
+        k2 = np.ascontiguousarray(np.asarray(k2_field, dtype=np.float64))
+        if k2.size != self.nv:
+            raise ValueError(f"k2_field needs {self.nv} values")
+        flags = b"".join(np.ascontiguousarray(np.asarray(refine[lev], dtype=np.uint8)).tobytes()
+                         for lev in range(1, depth))
+        for lev in range(1, depth):
+            if np.asarray(refine[lev]).size != 3 ** (lev * d):
+                raise ValueError(f"refine[{lev}] needs {3 ** (lev * d)} flags")
+        h = ctypes.c_void_p()
+        rc = L.mg_create_adaptive(d, depth, k2.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(theta),
+                                  float(layer_width), flags if flags else b"\0", ctypes.byref(h))
+        if rc != MG_OK:
+            raise MgError(rc, L.mg_last_error(None).decode())
+        self._h = h
+        self._view = h
+        self._L = L
+        return self
 
     # -- helpers
     def _check(self, rc, what):
