@@ -147,3 +147,22 @@ def channel(theta_interior_deg, depth=4):
                 theta_interior=math.radians(theta_interior_deg),
                 k2=np.broadcast_to(phi, (3 ** depth + 1,) * d).copy(),
                 f=np.broadcast_to(chi, (3 ** depth + 1,) * d).astype(np.complex128))
+
+
+def source_refinement(d, depth, centre=(0.0, 0.0, 0.0), radius=0.7, shrink=0.7):
+    """Refinement flags of an adaptive grid that resolves a localised feature
+    at ``centre`` (x first): a level-l cell is refined when its centre lies
+    within radius * shrink^(l-1) of the feature (so each level covers a
+    smaller region; levels 1..depth-1).  Input data only: the solver reads
+    the flags as the mesh."""
+    out = {}
+    for lev in range(1, depth):
+        n = 3 ** lev
+        c = (np.arange(n) + 0.5) / n
+        r2 = 0.0
+        for ax in range(d):
+            shape = [1] * d
+            shape[ax] = n
+            r2 = r2 + (c.reshape(shape) - centre[d - 1 - ax]) ** 2
+        out[lev] = np.broadcast_to(r2 < (radius * shrink ** (lev - 1)) ** 2, (n,) * d).copy()
+    return out
