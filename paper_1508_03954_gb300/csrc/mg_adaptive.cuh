@@ -16,7 +16,9 @@
 //   corr_l = T du_l + P corr_{l-1},  u_l += corr_l on every level,
 // then hanging values := P u_{l-1} (coarse to fine) and coarse values at
 // vertices with an unknown on the next finer level := that value (fine to
-// coarse).
+// coarse).  A cycle is three passes: the residuals fine to coarse (norm
+// fused), one fused kernel per level coarse to fine, the injection fine to
+// coarse -- 3L - 1 launches in one CUDA graph.
 #pragma once
 #include "mg_kernels.cuh"
 
@@ -63,15 +65,20 @@ __device__ __forceinline__ void element_entry(const cplx<double>* h, const cplx<
 // r_l(v) = sum over the leaves around v of (M_c f - H_c u)_v, plus R r_{l+1}
 // (rf, the finer level's residual, may be null), zero where no cell exists
 // and on the Dirichlet boundary.
+// The level's fine-grid unknowns (unknown here, none on the next finer
+// level at the same point; vcls_f null on the finest level) add |r|^2 into
+// *norm2 (deterministic last-block sum) when norm2 is not null.
 template <int D>
-__global__ void ada_residual_kernel(int n, const cplx<double>* __restrict__ u, const cplx<double>* __restrict__ f,
-                                    const uint8_t* __restrict__ cellf, const uint8_t* __restrict__ vcls,
-                                    const cplx<double>* __restrict__ hcell, const cplx<double>* __restrict__ hinv,
-                                    const double* __restrict__ phic, double phi0,
-                                    const cplx<double>* __restrict__ rf, cplx<double>* __restrict__ r) {
+__global__ void __launch_bounds__(256) ada_residual_kernel(
+    int n, const cplx<double>* __restrict__ u, const cplx<double>* __restrict__ f,
+    const uint8_t* __restrict__ cellf, const uint8_t* __restrict__ vcls, const cplx<double>* __restrict__ hcell,
+    const cplx<double>* __restrict__ hinv, const double* __restrict__ phic, double phi0,
+    const cplx<double>* __restrict__ rf, cplx<double>* __restrict__ r, const uint8_t* __restrict__ vcls_f,
+    double* partial, unsigned* ticket, double* norm2) {
   const int N = n + 1, Nf = 3 * n + 1;
   unsigned total = 1;
   for (int a = 0; a < D; ++a) total *= (unsigned)N;
+  double nrm = 0.0;
   for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
     int g[3];
     ada_coords<D>(i, N, g);
@@ -129,18 +136,34 @@ __global__ void ada_residual_kernel(int n, const cplx<double>* __restrict__ u, c
           acc = rfma(w, rf[fi], acc);
         }
       }
+      if (vcls[i] == kVertUnknown) {
+        bool own = true;
+        if (vcls_f != nullptr) {
+          unsigned fi = 0, fs = 1;
+#pragma unroll
+          for (int a = 0; a < D; ++a) {
+            fi += (unsigned)(3 * g[a]) * fs;
+            fs *= (unsigned)Nf;
+          }
+          own = vcls_f[fi] != kVertUnknown;
+        }
+        if (own) nrm = fma(acc.x, acc.x, fma(acc.y, acc.y, nrm));
+      }
     }
     r[i] = acc;
   }
+  if (norm2 != nullptr) {
+    __shared__ double s_red[8];
+    block_norm_finish<256>(nrm, s_red, partial, ticket, norm2, gridDim.x);
+  }
 }
 
-// t = omega r / H_l[v, v] at unknowns (the diagonal summed over the 2^D
-// cells, which all exist), zero elsewhere; hb: zero at c-points.
+// invd(v) = 1 / H_l[v, v] at unknowns (the diagonal summed over the 2^D
+// cells), zero elsewhere; formed once per level.
 template <int D>
-__global__ void ada_jacobi_kernel(int n, const cplx<double>* __restrict__ r, const uint8_t* __restrict__ vcls,
-                                  const cplx<double>* __restrict__ hcell, const cplx<double>* __restrict__ hinv,
-                                  const double* __restrict__ phic, double phi0, cplx<double> omega, int hb,
-                                  cplx<double>* __restrict__ t) {
+__global__ void ada_diag_kernel(int n, const uint8_t* __restrict__ vcls, const cplx<double>* __restrict__ hcell,
+                                const cplx<double>* __restrict__ hinv, const double* __restrict__ phic,
+                                double phi0, cplx<double>* __restrict__ invd) {
   const int N = n + 1;
   unsigned total = 1;
   for (int a = 0; a < D; ++a) total *= (unsigned)N;
@@ -149,32 +172,92 @@ __global__ void ada_jacobi_kernel(int n, const cplx<double>* __restrict__ r, con
     if (vcls[i] == kVertUnknown) {
       int g[3];
       ada_coords<D>(i, N, g);
-      bool cpt = true;
+      cplx<double> dg = cz<double>();
 #pragma unroll
-      for (int a = 0; a < D; ++a) cpt = cpt && (g[a] % 3 == 0);
-      if (!(hb && cpt)) {
-        cplx<double> dg = cz<double>();
+      for (int e = 0; e < (1 << D); ++e) {
+        cplx<double> h[3], hi[3];
+        unsigned ci = 0, cs = 1;
 #pragma unroll
-        for (int e = 0; e < (1 << D); ++e) {
-          cplx<double> h[3], hi[3];
-          unsigned ci = 0, cs = 1;
-#pragma unroll
-          for (int a = 0; a < D; ++a) {
-            const int ca = g[a] - 1 + ((e >> a) & 1);
-            h[a] = hcell[ca];
-            hi[a] = hinv[ca];
-            ci += (unsigned)ca * cs;
-            cs *= (unsigned)n;
-          }
-          const int av = ((1 << D) - 1) ^ e;
-          cplx<double> m, k;
-          element_entry<D>(h, hi, av, av, m, k);
-          dg = dg + (k - rmul(phic != nullptr ? phic[ci] : phi0, m));
+        for (int a = 0; a < D; ++a) {
+          const int ca = g[a] - 1 + ((e >> a) & 1);
+          h[a] = hcell[ca];
+          hi[a] = hinv[ca];
+          ci += (unsigned)ca * cs;
+          cs *= (unsigned)n;
         }
-        v = cdiv(omega * r[i], dg);
+        const int av = ((1 << D) - 1) ^ e;
+        cplx<double> m, k;
+        element_entry<D>(h, hi, av, av, m, k);
+        dg = dg + (k - rmul(phic != nullptr ? phic[ci] : phi0, m));
+      }
+      v = cdiv(cplx<double>{1.0, 0.0}, dg);
+    }
+    invd[i] = v;
+  }
+}
+
+// One level of the coarse-to-fine half of the cycle, fused: at every vertex
+// of an existing cell
+//   t = omega r invd at unknowns (zero at c-points for hb),
+//   corr = t - [BPX] P I t + P corr_{l-1}     (corr_{l-1} null on level 1),
+//   u += corr at unknowns, u = P u_{l-1} at hanging vertices,
+// with I t read at the c-points of this level (their t recomputed locally)
+// and u_{l-1}, corr_{l-1} already final (levels run coarse to fine).
+template <int D>
+__global__ void ada_down_kernel(int n, const cplx<double>* __restrict__ r, const cplx<double>* __restrict__ invd,
+                                const uint8_t* __restrict__ vcls, cplx<double> omega, int hb, int hier,
+                                const cplx<double>* __restrict__ corr_c, const cplx<double>* __restrict__ u_c,
+                                cplx<double>* __restrict__ corr, cplx<double>* __restrict__ u) {
+  const int N = n + 1, Nc = n / 3 + 1;
+  unsigned total = 1;
+  for (int a = 0; a < D; ++a) total *= (unsigned)N;
+  const double inv = D == 2 ? 1.0 / 9.0 : 1.0 / 27.0;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    const uint8_t cls = vcls[i];
+    if (cls == kVertNone) continue;
+    int g[3];
+    ada_coords<D>(i, N, g);
+    bool inner = true, cpt = true;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      inner = inner && g[a] > 0 && g[a] < n;
+      cpt = cpt && (g[a] % 3 == 0);
+    }
+    if (!inner) {
+      corr[i] = cz<double>();
+      u[i] = cz<double>();
+      continue;
+    }
+    cplx<double> c = cz<double>();
+    if (cls == kVertUnknown && !(hb && cpt)) c = omega * (r[i] * invd[i]);
+    cplx<double> pc = cz<double>(), pt = cz<double>(), pu = cz<double>();
+    if (corr_c != nullptr) {
+#pragma unroll
+      for (int e = 0; e < (1 << D); ++e) {
+        int iw = 1;
+        unsigned ci = 0, cs = 1, fi = 0, fs = 1;
+        bool ok = true;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          const int bit = (e >> a) & 1, o = g[a] % 3;
+          iw *= bit ? o : 3 - o;
+          const int cc = g[a] / 3 + bit;
+          ok = ok && cc < Nc;
+          ci += (unsigned)(ok ? cc : 0) * cs;
+          cs *= (unsigned)Nc;
+          fi += (unsigned)(ok ? 3 * cc : 0) * fs;
+          fs *= (unsigned)N;
+        }
+        if (iw == 0 || !ok) continue;
+        const double w = (double)iw;
+        pc = rfma(w, corr_c[ci], pc);
+        pu = rfma(w, u_c[ci], pu);
+        if (hier && !hb && vcls[fi] == kVertUnknown) pt = rfma(w, omega * (r[fi] * invd[fi]), pt);
       }
     }
-    t[i] = v;
+    c = c - rmul(inv, pt) + rmul(inv, pc);
+    corr[i] = c;
+    u[i] = cls == kVertUnknown ? u[i] + c : rmul(inv, pu);
   }
 }
 
@@ -238,22 +321,6 @@ __global__ void ada_prolong_kernel(int n, const cplx<double>* __restrict__ x, co
   }
 }
 
-// u += c on the interior, zero on the Dirichlet boundary.
-template <int D>
-__global__ void ada_update_kernel(int n, cplx<double>* __restrict__ u, const cplx<double>* __restrict__ c) {
-  const int N = n + 1;
-  unsigned total = 1;
-  for (int a = 0; a < D; ++a) total *= (unsigned)N;
-  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
-    int g[3];
-    ada_coords<D>(i, N, g);
-    bool inner = true;
-#pragma unroll
-    for (int a = 0; a < D; ++a) inner = inner && g[a] > 0 && g[a] < n;
-    u[i] = inner ? u[i] + c[i] : cz<double>();
-  }
-}
-
 // Hanging values: u(w) = (P u_c)(w) at interior vertices of existing cells
 // that carry no unknown (pu: P u_c on this level).
 template <int D>
@@ -292,38 +359,6 @@ __global__ void ada_inject_unknown_kernel(int nc, const uint8_t* __restrict__ vc
     }
     if (vcls_f[fi] == kVertUnknown) uc[i] = uf[fi];
   }
-}
-
-// sum |r|^2 over the unknowns of this level that carry no unknown on the
-// next finer level (vcls_f, null on the finest level): the fine-grid
-// unknowns of the adaptive grid.  Deterministic last-block sum into *norm2.
-template <int D>
-__global__ void __launch_bounds__(256) ada_norm_kernel(int n, const cplx<double>* __restrict__ r,
-                                                       const uint8_t* __restrict__ vcls,
-                                                       const uint8_t* __restrict__ vcls_f, double* partial,
-                                                       unsigned* ticket, double* norm2) {
-  const int N = n + 1, Nf = 3 * n + 1;
-  unsigned total = 1;
-  for (int a = 0; a < D; ++a) total *= (unsigned)N;
-  double nrm = 0.0;
-  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
-    if (vcls[i] != kVertUnknown) continue;
-    if (vcls_f != nullptr) {
-      int g[3];
-      ada_coords<D>(i, N, g);
-      unsigned fi = 0, fs = 1;
-#pragma unroll
-      for (int a = 0; a < D; ++a) {
-        fi += (unsigned)(3 * g[a]) * fs;
-        fs *= (unsigned)Nf;
-      }
-      if (vcls_f[fi] == kVertUnknown) continue;
-    }
-    const cplx<double> v = r[i];
-    nrm = fma(v.x, v.x, fma(v.y, v.y, nrm));
-  }
-  __shared__ double s_red[8];
-  block_norm_finish<256>(nrm, s_red, partial, ticket, norm2, gridDim.x);
 }
 
 // y = x where the level's cells exist around the vertex (vcls != 0), else

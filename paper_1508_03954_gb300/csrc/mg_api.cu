@@ -170,8 +170,7 @@ struct LevA {
   cplx<double>* hcell = nullptr; // complex width per axis index
   cplx<double>* hinv = nullptr;  // its inverse
   double* phic = nullptr;        // per-cell shift (null: constant)
-  size_t unknowns = 0;           // vertices carrying an unknown
-  size_t leaf_unknowns = 0;      // ... and none on the next finer level
+  cplx<double>* invd = nullptr;  // 1 / H_l[v, v] at unknowns
 };
 
 struct HierA {
@@ -181,6 +180,9 @@ struct HierA {
   unsigned* ticket = nullptr;
   double* norm2 = nullptr;     // [l]: |r_l|^2 over the level's fine-grid unknowns
   std::vector<void*> allocs;
+  cudaGraphExec_t exec = nullptr;  // the last captured cycle
+  std::vector<double> key;
+  long long nkern = 0;
 };
 
 }  // namespace
@@ -1912,6 +1914,7 @@ int d4_refine(mg_ctx* c, int hb, int hier, const cplx<double>* omega, double tol
 // ------------------------------------------------------------------ adaptive
 void ada_free(HierA* H) {
   if (H == nullptr) return;
+  if (H->exec) cudaGraphExecDestroy(H->exec);
   for (void* p : H->allocs) cudaFree(p);
   delete H;
 }
@@ -1971,9 +1974,8 @@ int ada_build(mg_ctx* c, const unsigned char* refine) {
       vcls[vi] = cnt == 0 ? mg::kVertNone : ((inner && cnt == (1 << d)) ? mg::kVertUnknown : mg::kVertBound);
       (void)tot;
     }
-    for (size_t vi = 0; vi < V.nv; ++vi) V.unknowns += vcls[vi] == mg::kVertUnknown;
     const size_t bytes = V.nv * sizeof(cplx<double>);
-    for (cplx<double>** p : {&V.u, &V.f, &V.r, &V.t}) {
+    for (cplx<double>** p : {&V.u, &V.f, &V.r, &V.t, &V.invd}) {
       if ((rc = d4_alloc(c, *H, (void**)p, bytes)) != MG_OK) return rc;
     }
     if (l == 1) {
@@ -1998,6 +2000,12 @@ int ada_build(mg_ctx* c, const unsigned char* refine) {
       std::vector<double> ph = cell_shift<double>(c, l);
       if ((rc = d4_upload(c, *H, &V.phic, ph)) != MG_OK) return rc;
     }
+    if (d == 2)
+      mg::ada_diag_kernel<2><<<grid_for(V.nv), kThreads>>>(n, V.vcls, V.hcell, V.hinv, V.phic, c->k2[0], V.invd);
+    else
+      mg::ada_diag_kernel<3><<<grid_for(V.nv), kThreads>>>(n, V.vcls, V.hcell, V.hinv, V.phic, c->k2[0], V.invd);
+    MG_CUDA(c, cudaGetLastError());
+    MG_CUDA(c, cudaDeviceSynchronize());
     // children of refined cells exist on the next level
     if (l < L) {
       const int nf = 3 * n;
@@ -2030,11 +2038,10 @@ cudaError_t ada_residuals(mg_ctx* c) {
   const double phi0 = c->k2[0];
   for (int l = L; l >= 1; --l) {
     LevA& V = H.lev[l];
-    c->launches += 2;
+    ++c->launches;
     mg::ada_residual_kernel<D><<<grid_for(V.nv), kThreads, 0, c->stream>>>(
-        V.n, V.u, V.f, V.cellf, V.vcls, V.hcell, V.hinv, V.phic, phi0, l < L ? H.lev[l + 1].r : nullptr, V.r);
-    mg::ada_norm_kernel<D><<<grid_for(V.nv), kThreads, 0, c->stream>>>(
-        V.n, V.r, V.vcls, l < L ? H.lev[l + 1].vcls : nullptr, H.partial, H.ticket, H.norm2 + l);
+        V.n, V.u, V.f, V.cellf, V.vcls, V.hcell, V.hinv, V.phic, phi0, l < L ? H.lev[l + 1].r : nullptr, V.r,
+        l < L ? H.lev[l + 1].vcls : nullptr, H.partial, H.ticket, H.norm2 + l);
   }
   return cudaGetLastError();
 }
@@ -2060,37 +2067,30 @@ cudaError_t ada_invariants(mg_ctx* c) {
   return cudaGetLastError();
 }
 
+// One cycle: the residuals bottom-up (norm fused), the fused coarse-to-fine
+// pass (Jacobi, transfer, correction, update, hanging values) and the
+// injection bottom-up: 3L - 1 launches.
 template <int D>
 cudaError_t ada_enqueue_cycle(mg_ctx* c, int hb, int hier, const cplx<double>* omega) {
   HierA& H = *c->ada;
   const int L = c->L;
-  const double phi0 = c->k2[0];
   cudaError_t e = ada_residuals<D>(c);
   for (int l = 1; l <= L && e == cudaSuccess; ++l) {
     LevA& V = H.lev[l];
+    const LevA* W = l > 1 ? &H.lev[l - 1] : nullptr;
     ++c->launches;
-    mg::ada_jacobi_kernel<D><<<grid_for(V.nv), kThreads, 0, c->stream>>>(V.n, V.r, V.vcls, V.hcell, V.hinv, V.phic,
-                                                                       phi0, omega[l - 1], hb, V.t);
-    if (l > 1) {
-      LevA& W = H.lev[l - 1];
-      if (hier) {
-        // BPX transfer: T du = du - P I du
-        c->launches += 2;
-        mg::ada_inject_kernel<D><<<grid_for(W.nv), kThreads, 0, c->stream>>>(W.n, V.t, H.T[0]);
-        mg::ada_prolong_kernel<D><<<grid_for(V.nv), kThreads, 0, c->stream>>>(V.n, H.T[0], V.t, V.t, 1);
-      }
-      ++c->launches;
-      mg::ada_prolong_kernel<D><<<grid_for(V.nv), kThreads, 0, c->stream>>>(V.n, W.corr, V.t, V.corr, 0);
-    }
+    mg::ada_down_kernel<D><<<grid_for(V.nv), kThreads, 0, c->stream>>>(
+        V.n, V.r, V.invd, V.vcls, omega[l - 1], hb, hier, W ? W->corr : nullptr, W ? W->u : nullptr, V.corr, V.u);
     e = cudaGetLastError();
   }
-  for (int l = 1; l <= L && e == cudaSuccess; ++l) {
+  for (int l = L - 1; l >= 1 && e == cudaSuccess; --l) {
     LevA& V = H.lev[l];
     ++c->launches;
-    mg::ada_update_kernel<D><<<grid_for(V.nv), kThreads, 0, c->stream>>>(V.n, V.u, V.corr);
+    mg::ada_inject_unknown_kernel<D><<<grid_for(V.nv), kThreads, 0, c->stream>>>(V.n, H.lev[l + 1].vcls,
+                                                                                 H.lev[l + 1].u, V.u);
+    e = cudaGetLastError();
   }
-  if (e == cudaSuccess) e = ada_invariants<D>(c);
-  return e == cudaSuccess ? cudaGetLastError() : e;
+  return e;
 }
 
 int ada_norm_host(mg_ctx* c, double* out) {
@@ -2114,8 +2114,60 @@ int ada_residual_norm(mg_ctx* c, double* out) {
   return ada_norm_host(c, out);
 }
 
+// One cycle as a CUDA graph, captured on first use and updated in place when
+// the variant, transfer or factors change.
 int ada_cycle(mg_ctx* c, int hb, int hier, const cplx<double>* omega) {
-  cudaError_t e = c->d == 2 ? ada_enqueue_cycle<2>(c, hb, hier, omega) : ada_enqueue_cycle<3>(c, hb, hier, omega);
+  HierA& H = *c->ada;
+  auto enqueue = [&]() {
+    return c->d == 2 ? ada_enqueue_cycle<2>(c, hb, hier, omega) : ada_enqueue_cycle<3>(c, hb, hier, omega);
+  };
+  cudaError_t e = cudaSuccess;
+  if (c->use_graphs && !c->timing) {
+    std::vector<double> key = {(double)hb, (double)hier};
+    for (int l = 0; l < c->L; ++l) {
+      key.push_back(omega[l].x);
+      key.push_back(omega[l].y);
+    }
+    if (H.exec == nullptr || H.key != key) {
+      cudaStream_t user = c->stream;
+      c->stream = c->cap_stream;
+      const long long before = c->launches;
+      cudaGraph_t g = nullptr;
+      e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+      cudaError_t ek = e == cudaSuccess ? enqueue() : e;
+      cudaError_t ee = e == cudaSuccess ? cudaStreamEndCapture(c->cap_stream, &g) : e;
+      c->stream = user;
+      const long long nk = c->launches - before;
+      c->launches = before;
+      e = ek != cudaSuccess ? ek : ee;
+      if (e == cudaSuccess) {
+        cudaGraphExecUpdateResultInfo info;
+        if (H.exec == nullptr || cudaGraphExecUpdate(H.exec, g, &info) != cudaSuccess) {
+          cudaGetLastError();
+          if (H.exec) cudaGraphExecDestroy(H.exec);
+          H.exec = nullptr;
+          e = cudaGraphInstantiate(&H.exec, g, 0);
+        }
+      }
+      if (g) cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (H.exec) cudaGraphExecDestroy(H.exec);
+        H.exec = nullptr;
+        c->use_graphs = false;
+      } else {
+        H.key = key;
+        H.nkern = nk;
+      }
+    }
+    if (H.exec != nullptr) {
+      e = cudaGraphLaunch(H.exec, c->stream);
+      c->launches += H.nkern;
+      if (e != cudaSuccess) return fail(c, MG_ERR_CUDA, std::string("cycle launch: ") + cudaGetErrorString(e));
+      return MG_OK;
+    }
+  }
+  e = enqueue();
   if (e != cudaSuccess) return fail(c, MG_ERR_CUDA, std::string("cycle launch: ") + cudaGetErrorString(e));
   return MG_OK;
 }
