@@ -27,6 +27,34 @@ namespace mg {
 enum : uint8_t { kCellExists = 1, kCellRefined = 2 };
 enum : uint8_t { kVertNone = 0, kVertBound = 1, kVertUnknown = 2 };
 
+// Bounding box of a level's vertices of existing cells: the cycle kernels
+// run over it instead of the level's full grid.
+struct AdaBox {
+  int lo[3], ext[3];
+};
+
+// Coordinates g and level-grid index of the t-th vertex of the box.
+template <int D>
+__device__ __forceinline__ unsigned box_vertex(unsigned t, const AdaBox& B, int N, int* g) {
+  unsigned i = 0, s = 1;
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    g[a] = B.lo[a] + (int)(t % (unsigned)B.ext[a]);
+    t /= (unsigned)B.ext[a];
+    i += (unsigned)g[a] * s;
+    s *= (unsigned)N;
+  }
+  return i;
+}
+
+template <int D>
+__device__ __forceinline__ unsigned box_volume(const AdaBox& B) {
+  unsigned v = 1;
+#pragma unroll
+  for (int a = 0; a < D; ++a) v *= (unsigned)B.ext[a];
+  return v;
+}
+
 template <int D>
 __device__ __forceinline__ void ada_coords(unsigned i, int N, int* g) {
 #pragma unroll
@@ -74,14 +102,13 @@ __global__ void __launch_bounds__(256) ada_residual_kernel(
     const uint8_t* __restrict__ cellf, const uint8_t* __restrict__ vcls, const cplx<double>* __restrict__ hcell,
     const cplx<double>* __restrict__ hinv, const double* __restrict__ phic, double phi0,
     const cplx<double>* __restrict__ rf, cplx<double>* __restrict__ r, const uint8_t* __restrict__ vcls_f,
-    double* partial, unsigned* ticket, double* norm2) {
+    double* partial, unsigned* ticket, double* norm2, AdaBox box) {
   const int N = n + 1, Nf = 3 * n + 1;
-  unsigned total = 1;
-  for (int a = 0; a < D; ++a) total *= (unsigned)N;
+  const unsigned vol = box_volume<D>(box);
   double nrm = 0.0;
-  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < vol; t += gridDim.x * blockDim.x) {
     int g[3];
-    ada_coords<D>(i, N, g);
+    const unsigned i = box_vertex<D>(t, box, N, g);
     bool inner = true;
 #pragma unroll
     for (int a = 0; a < D; ++a) inner = inner && g[a] > 0 && g[a] < n;
@@ -207,16 +234,15 @@ template <int D>
 __global__ void ada_down_kernel(int n, const cplx<double>* __restrict__ r, const cplx<double>* __restrict__ invd,
                                 const uint8_t* __restrict__ vcls, cplx<double> omega, int hb, int hier,
                                 const cplx<double>* __restrict__ corr_c, const cplx<double>* __restrict__ u_c,
-                                cplx<double>* __restrict__ corr, cplx<double>* __restrict__ u) {
+                                cplx<double>* __restrict__ corr, cplx<double>* __restrict__ u, AdaBox box) {
   const int N = n + 1, Nc = n / 3 + 1;
-  unsigned total = 1;
-  for (int a = 0; a < D; ++a) total *= (unsigned)N;
+  const unsigned vol = box_volume<D>(box);
   const double inv = D == 2 ? 1.0 / 9.0 : 1.0 / 27.0;
-  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < vol; t += gridDim.x * blockDim.x) {
+    int g[3];
+    const unsigned i = box_vertex<D>(t, box, N, g);
     const uint8_t cls = vcls[i];
     if (cls == kVertNone) continue;
-    int g[3];
-    ada_coords<D>(i, N, g);
     bool inner = true, cpt = true;
 #pragma unroll
     for (int a = 0; a < D; ++a) {
@@ -344,13 +370,13 @@ __global__ void ada_set_hanging_kernel(int n, const uint8_t* __restrict__ vcls, 
 // finer value (Eq. injection).
 template <int D>
 __global__ void ada_inject_unknown_kernel(int nc, const uint8_t* __restrict__ vcls_f,
-                                          const cplx<double>* __restrict__ uf, cplx<double>* __restrict__ uc) {
+                                          const cplx<double>* __restrict__ uf, cplx<double>* __restrict__ uc,
+                                          AdaBox box) {
   const int Nc = nc + 1, Nf = 3 * nc + 1;
-  unsigned total = 1;
-  for (int a = 0; a < D; ++a) total *= (unsigned)Nc;
-  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+  const unsigned vol = box_volume<D>(box);
+  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < vol; t += gridDim.x * blockDim.x) {
     int g[3];
-    ada_coords<D>(i, Nc, g);
+    const unsigned i = box_vertex<D>(t, box, Nc, g);
     unsigned fi = 0, fs = 1;
 #pragma unroll
     for (int a = 0; a < D; ++a) {

@@ -171,6 +171,8 @@ struct LevA {
   cplx<double>* hinv = nullptr;  // its inverse
   double* phic = nullptr;        // per-cell shift (null: constant)
   cplx<double>* invd = nullptr;  // 1 / H_l[v, v] at unknowns
+  mg::AdaBox box{};              // bounding box of the vertices of existing cells
+  size_t boxvol = 0;
 };
 
 struct HierA {
@@ -1974,6 +1976,25 @@ int ada_build(mg_ctx* c, const unsigned char* refine) {
       vcls[vi] = cnt == 0 ? mg::kVertNone : ((inner && cnt == (1 << d)) ? mg::kVertUnknown : mg::kVertBound);
       (void)tot;
     }
+    {
+      int lo[3] = {N, N, N}, hi[3] = {-1, -1, -1};
+      for (size_t vi = 0; vi < V.nv; ++vi) {
+        if (vcls[vi] == mg::kVertNone) continue;
+        size_t r = vi;
+        for (int a = 0; a < d; ++a) {
+          const int g = (int)(r % N);
+          r /= N;
+          lo[a] = std::min(lo[a], g);
+          hi[a] = std::max(hi[a], g);
+        }
+      }
+      V.boxvol = 1;
+      for (int a = 0; a < 3; ++a) {
+        V.box.lo[a] = a < d ? lo[a] : 0;
+        V.box.ext[a] = a < d ? hi[a] - lo[a] + 1 : 1;
+        V.boxvol *= (size_t)V.box.ext[a];
+      }
+    }
     const size_t bytes = V.nv * sizeof(cplx<double>);
     for (cplx<double>** p : {&V.u, &V.f, &V.r, &V.t, &V.invd}) {
       if ((rc = d4_alloc(c, *H, (void**)p, bytes)) != MG_OK) return rc;
@@ -2039,9 +2060,9 @@ cudaError_t ada_residuals(mg_ctx* c) {
   for (int l = L; l >= 1; --l) {
     LevA& V = H.lev[l];
     ++c->launches;
-    mg::ada_residual_kernel<D><<<grid_for(V.nv), kThreads, 0, c->stream>>>(
+    mg::ada_residual_kernel<D><<<grid_for(V.boxvol), kThreads, 0, c->stream>>>(
         V.n, V.u, V.f, V.cellf, V.vcls, V.hcell, V.hinv, V.phic, phi0, l < L ? H.lev[l + 1].r : nullptr, V.r,
-        l < L ? H.lev[l + 1].vcls : nullptr, H.partial, H.ticket, H.norm2 + l);
+        l < L ? H.lev[l + 1].vcls : nullptr, H.partial, H.ticket, H.norm2 + l, V.box);
   }
   return cudaGetLastError();
 }
@@ -2061,8 +2082,8 @@ cudaError_t ada_invariants(mg_ctx* c) {
   for (int l = L - 1; l >= 1; --l) {
     LevA& V = H.lev[l];
     ++c->launches;
-    mg::ada_inject_unknown_kernel<D><<<grid_for(V.nv), kThreads, 0, c->stream>>>(V.n, H.lev[l + 1].vcls,
-                                                                                 H.lev[l + 1].u, V.u);
+    mg::ada_inject_unknown_kernel<D><<<grid_for(V.boxvol), kThreads, 0, c->stream>>>(V.n, H.lev[l + 1].vcls,
+                                                                                     H.lev[l + 1].u, V.u, V.box);
   }
   return cudaGetLastError();
 }
@@ -2079,15 +2100,16 @@ cudaError_t ada_enqueue_cycle(mg_ctx* c, int hb, int hier, const cplx<double>* o
     LevA& V = H.lev[l];
     const LevA* W = l > 1 ? &H.lev[l - 1] : nullptr;
     ++c->launches;
-    mg::ada_down_kernel<D><<<grid_for(V.nv), kThreads, 0, c->stream>>>(
-        V.n, V.r, V.invd, V.vcls, omega[l - 1], hb, hier, W ? W->corr : nullptr, W ? W->u : nullptr, V.corr, V.u);
+    mg::ada_down_kernel<D><<<grid_for(V.boxvol), kThreads, 0, c->stream>>>(
+        V.n, V.r, V.invd, V.vcls, omega[l - 1], hb, hier, W ? W->corr : nullptr, W ? W->u : nullptr, V.corr, V.u,
+        V.box);
     e = cudaGetLastError();
   }
   for (int l = L - 1; l >= 1 && e == cudaSuccess; --l) {
     LevA& V = H.lev[l];
     ++c->launches;
-    mg::ada_inject_unknown_kernel<D><<<grid_for(V.nv), kThreads, 0, c->stream>>>(V.n, H.lev[l + 1].vcls,
-                                                                                 H.lev[l + 1].u, V.u);
+    mg::ada_inject_unknown_kernel<D><<<grid_for(V.boxvol), kThreads, 0, c->stream>>>(V.n, H.lev[l + 1].vcls,
+                                                                                     H.lev[l + 1].u, V.u, V.box);
     e = cudaGetLastError();
   }
   return e;

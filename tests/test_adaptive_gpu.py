@@ -76,8 +76,11 @@ def pair(d, depth, k2, theta, w, refine, f, u0):
 
 
 def check_state(g, o, depth, what):
+    """Every level's values at the vertices of its existing cells (values
+    elsewhere are never read), and the fine-grid function."""
     for lev in range(1, depth + 1):
-        e = rel_l2(g.get_level(lev, 0), o.u[lev])
+        m = o.exists[lev]
+        e = rel_l2(g.get_level(lev, 0)[m], o.u[lev][m])
         assert e <= TOL, f"{what}: level {lev} rel L2 {e:.3e}"
     e = rel_l2(g.get_solution(), o.composite_on_fine())
     assert e <= TOL, f"{what}: fine-grid function rel L2 {e:.3e}"
