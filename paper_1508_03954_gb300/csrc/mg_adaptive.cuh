@@ -102,7 +102,8 @@ __global__ void __launch_bounds__(256) ada_residual_kernel(
     const uint8_t* __restrict__ cellf, const uint8_t* __restrict__ vcls, const cplx<double>* __restrict__ hcell,
     const cplx<double>* __restrict__ hinv, const double* __restrict__ phic, double phi0,
     const cplx<double>* __restrict__ rf, cplx<double>* __restrict__ r, const uint8_t* __restrict__ vcls_f,
-    double* partial, unsigned* ticket, double* norm2, AdaBox box) {
+    double* partial, unsigned* ticket, double* norm2, AdaBox box, const uint8_t* __restrict__ rotf,
+    const cplx<double>* __restrict__ emat) {
   const int N = n + 1, Nf = 3 * n + 1;
   const unsigned vol = box_volume<D>(box);
   double nrm = 0.0;
@@ -125,11 +126,15 @@ __global__ void __launch_bounds__(256) ada_residual_kernel(
           cs *= (unsigned)n;
         }
         if ((cellf[ci] & (kCellExists | kCellRefined)) != kCellExists) continue;  // leaves only
-        cplx<double> h[3], hi[3];
+        // the cell's element matrices from the table of its width class
+        // (which axes lie in the layer): rows of M and of K - phi0 M
+        int cls = 0;
 #pragma unroll
-        for (int a = 0; a < D; ++a) { h[a] = hcell[c[a]]; hi[a] = hinv[c[a]]; }
-        const double phi = phic != nullptr ? phic[ci] : phi0;
+        for (int a = 0; a < D; ++a) cls |= (int)rotf[c[a]] << a;
         const int av = ((1 << D) - 1) ^ e;  // v's corner in the cell
+        const cplx<double>* Mrow = emat + ((size_t)(2 * cls) << (2 * D)) + (av << D);
+        const cplx<double>* Hrow = Mrow + (1 << (2 * D));
+        const double dphi = phic != nullptr ? phic[ci] - phi0 : 0.0;
 #pragma unroll
         for (int b = 0; b < (1 << D); ++b) {
           unsigned vi = 0, vs = 1;
@@ -138,15 +143,17 @@ __global__ void __launch_bounds__(256) ada_residual_kernel(
             vi += (unsigned)(c[a] + ((b >> a) & 1)) * vs;
             vs *= (unsigned)N;
           }
-          cplx<double> m, k;
-          element_entry<D>(h, hi, av, b, m, k);
-          acc = acc + m * f[vi];
-          acc = acc - (k - rmul(phi, m)) * u[vi];
+          const cplx<double> m = Mrow[b];
+          acc = cfma(m, f[vi], acc);
+          cplx<double> hm = Hrow[b];
+          if (phic != nullptr) hm = hm - rmul(dphi, m);
+          acc = acc - hm * u[vi];
         }
       }
       if (rf != nullptr) {
-        // R = P^T: fine 3v + o, o in [-2, 2]^D, weight prod (1 - |o|/3)
-#pragma unroll 1
+        // R = P^T: fine 3v + o, o in [-2, 2]^D, weight prod (1 - |o|/3);
+        // unrolled so that the loads are in flight together
+#pragma unroll
         for (int o = 0; o < (D == 2 ? 25 : 125); ++o) {
           int q = o;
           double w = 1.0;

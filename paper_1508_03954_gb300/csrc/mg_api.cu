@@ -173,6 +173,8 @@ struct LevA {
   cplx<double>* invd = nullptr;  // 1 / H_l[v, v] at unknowns
   mg::AdaBox box{};              // bounding box of the vertices of existing cells
   size_t boxvol = 0;
+  uint8_t* rotf = nullptr;       // per axis index: the cell lies in the layer
+  cplx<double>* emat = nullptr;  // per width class: M, then K - phi0 M (2^d x 2^d each)
 };
 
 struct HierA {
@@ -2017,6 +2019,36 @@ int ada_build(mg_ctx* c, const unsigned char* refine) {
     }
     if ((rc = d4_upload(c, *H, &V.hcell, hc)) != MG_OK) return rc;
     if ((rc = d4_upload(c, *H, &V.hinv, hi)) != MG_OK) return rc;
+    if ((rc = d4_upload(c, *H, &V.rotf, rot)) != MG_OK) return rc;
+    {
+      // element matrices of the 2^d width classes (Section 3): M = prod_a m1,
+      // K = sum_j prod_a (k1 if a == j else m1), m1(h) = h/6 [2 1; 1 2],
+      // k1(h) = 1/h [1 -1; -1 1]; stored as M and K - phi0 M
+      const int nc = 1 << d, ne = nc * nc;
+      std::vector<cplx<double>> em((size_t)(1 << d) * 2 * ne);
+      for (int cls = 0; cls < (1 << d); ++cls)
+        for (int a = 0; a < nc; ++a)
+          for (int b = 0; b < nc; ++b) {
+            cd m(1.0), k(0.0);
+            for (int ax = 0; ax < d; ++ax) {
+              const cd h = ((cls >> ax) & 1) ? wd.rot : wd.in;
+              m *= h * ((((a >> ax) & 1) == ((b >> ax) & 1)) ? 1.0 / 3.0 : 1.0 / 6.0);
+            }
+            for (int j = 0; j < d; ++j) {
+              cd p(1.0);
+              for (int ax = 0; ax < d; ++ax) {
+                const cd h = ((cls >> ax) & 1) ? wd.rot : wd.in;
+                const bool same = ((a >> ax) & 1) == ((b >> ax) & 1);
+                p *= ax == j ? (same ? 1.0 : -1.0) / h : h * (same ? 1.0 / 3.0 : 1.0 / 6.0);
+              }
+              k += p;
+            }
+            const cd hm = k - c->k2[0] * m;
+            em[(size_t)(2 * cls) * ne + a * nc + b] = cplx<double>{m.real(), m.imag()};
+            em[(size_t)(2 * cls + 1) * ne + a * nc + b] = cplx<double>{hm.real(), hm.imag()};
+          }
+      if ((rc = d4_upload(c, *H, &V.emat, em)) != MG_OK) return rc;
+    }
     if (varphi) {
       std::vector<double> ph = cell_shift<double>(c, l);
       if ((rc = d4_upload(c, *H, &V.phic, ph)) != MG_OK) return rc;
@@ -2062,7 +2094,7 @@ cudaError_t ada_residuals(mg_ctx* c) {
     ++c->launches;
     mg::ada_residual_kernel<D><<<grid_for(V.boxvol), kThreads, 0, c->stream>>>(
         V.n, V.u, V.f, V.cellf, V.vcls, V.hcell, V.hinv, V.phic, phi0, l < L ? H.lev[l + 1].r : nullptr, V.r,
-        l < L ? H.lev[l + 1].vcls : nullptr, H.partial, H.ticket, H.norm2 + l, V.box);
+        l < L ? H.lev[l + 1].vcls : nullptr, H.partial, H.ticket, H.norm2 + l, V.box, V.rotf, V.emat);
   }
   return cudaGetLastError();
 }
