@@ -60,7 +60,7 @@ enum {
   MG_ERR_TIMEOUT = 6     /* a bounded device-side wait gave up               */
 };
 
-/* Relaxation variant (Section 4.2): MG_HB masks the Jacobi update at
+/* Relaxation variant (Section 5.2): MG_HB masks the Jacobi update at
  * c-points, Eq. hb-omega.  Transfer: MG_DLINEAR adds the update as is
  * (T = id); MG_HIERARCHICAL adds only its hierarchical surplus
  * T = (id - P I), the BPX prolongation of Appendix A.  MG_BPX is
@@ -71,13 +71,13 @@ enum { MG_DLINEAR = 0, MG_HIERARCHICAL = 1 };
  * FP32 accumulation inside an FP64 defect-correction loop (fine residual,
  * solution update and norms in FP64). */
 enum { MG_C128 = 0, MG_C64_REFINE = 1 };
-/* Relaxation schemes of the Section 4.1 table (succ = L - l on a regular grid). */
+/* Relaxation schemes of the Section 5.1 table (succ = L - l on a regular grid). */
 enum { MG_OMEGA_JACOBI = 0, MG_OMEGA_UCG = 1, MG_OMEGA_LGRID = 2, MG_OMEGA_EXP = 3,
        MG_OMEGA_TRANSITION = 4 };
 
 /* Creates a solver for the hierarchy of depth L = depth (levels 1..L).
  *  k2_field   host, (3^L+1)^d FP64 values of phi = k^2 at the fine vertices
- *             (Section 3: phi is a per-vertex weight).  Coarse levels sample
+ *             (Section 4: phi is a per-vertex weight).  Coarse levels sample
  *             it at their own vertices (injection); a cell uses the mean of
  *             its 2^d vertex values.  A constant field takes a faster path.
  *  theta      rotation angle of the complex spacing, 0 <= theta < pi/2.
@@ -141,7 +141,7 @@ int mg_set_stream(mg_ctx* ctx, void* cuda_stream);
 
 /* Nodal right-hand side f (host or device, fine-vertex layout).  The library
  * forms b_L = M_L f with the consistent, complex-scaled mass matrix
- * (Section 3: chi holds the weight of the discretised right-hand side).
+ * (Section 4: chi holds the weight of the discretised right-hand side).
  * Resets the reference residual used by relative norms. */
 int mg_set_rhs(mg_ctx* ctx, const mg_c128* f_nodal, int on_device);
 
@@ -156,7 +156,7 @@ int mg_get_solution(mg_ctx* ctx, mg_c128* out, int on_device);
 
 /* One additive FAS cycle (Algorithm 2; Appendix A Algorithm 4) on levels
  * 1..L.  omega_per_level: host, L complex relaxation factors, index l-1
- * (Section 4.1: one factor per level).  variant MG_ADD/MG_HB/MG_BPX and
+ * (Section 5.1: one factor per level).  variant MG_ADD/MG_HB/MG_BPX and
  * transfer MG_DLINEAR/MG_HIERARCHICAL as above.  Asynchronous. */
 int mg_cycle(mg_ctx* ctx, int variant, const mg_c128* omega_per_level, int transfer);
 
@@ -191,7 +191,7 @@ int mg_solve(mg_ctx* ctx, int variant, const mg_c128* omega, int transfer, doubl
  * e = 0, and adds e to u in FP64. */
 int mg_set_precision(mg_ctx* ctx, int precision, int inner_cycles);
 
-/* Grid unfolding (Section 4 remark on FMG; Section 7.1): stages s = 1..L-1
+/* Grid unfolding (Section 5 remark on FMG; Section 7.1): stages s = 1..L-1
  * solve on levels 1..s with b_s = M_s f_s and run cycles_per_stage cycles,
  * each stage starting from the d-linear interpolation of the previous one;
  * the fine solution is then set to the interpolation of stage L-1.  Level
@@ -199,7 +199,7 @@ int mg_set_precision(mg_ctx* ctx, int precision, int inner_cycles);
 int mg_fmg(mg_ctx* ctx, int variant, const mg_c128* omega, int transfer, int cycles_per_stage);
 
 /* Host helper: fills out[0..depth-1] with the relaxation factors of one
- * Section 4.1 scheme, succ = depth - l: Jacobi only, undamped coarse grid,
+ * Section 5.1 scheme, succ = depth - l: Jacobi only, undamped coarse grid,
  * undamped L-grid (l_grid), exponential omega_s^(succ+1) or transition
  * omega_s^((1-1/iter_n)(succ+1)). */
 int mg_omega_scheme(int scheme, mg_c128 omega_s, int depth, int iter_n, int l_grid,

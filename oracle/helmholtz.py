@@ -11,12 +11,12 @@ CUDA path produced.
 Everything is complex128 (FP64), slow and literal:
 
 * the operator is assembled cell by cell from 2^d x 2^d element matrices
-  (Section 3 "Multigrid realisation" and Appendix B: every cell applies its
+  (Section 4 "Multigrid realisation" and Appendix B: every cell applies its
   local matrix to its 2^d vertex values and scatters into the residual and
   diagonal accumulators of its vertices);
 * the cycle is the bottom-up FAS form of additive multigrid (Appendix A,
-  Algorithm 4 ``buFAS``) with one relaxation factor per level (Section 4.1),
-  the hierarchical-basis mask (Section 4.2, Eq. hb-omega) and the BPX
+  Algorithm 4 ``buFAS``) with one relaxation factor per level (Section 5.1),
+  the hierarchical-basis mask (Section 5.2, Eq. hb-omega) and the BPX
   prolongation of Appendix A (``P(u_{l-1} - I(u_l + du_l))``).
 
 Grid conventions (regular levels of a tripartitioned spacetree, Section 3):
@@ -108,7 +108,7 @@ def axis_spacing(level: int, theta: float, layer_width, theta_interior: float = 
 
 
 # ----------------------------------------------------------------------------
-# Element matrices (Section 3: Ritz-Galerkin p-linear elements; Appendix B)
+# Element matrices (Section 4: Ritz-Galerkin p-linear elements; Appendix B)
 # ----------------------------------------------------------------------------
 def element_matrices_1d(h):
     """1D linear element on a cell of (complex) width h:
@@ -157,7 +157,7 @@ def _slab(shape_cells, offset):
 
 class Level:
     """Operator data of one regular level l: per-axis complex widths, cell
-    shifts phi_c and the accumulated diagonal (Section 3: diag(H_l) is
+    shifts phi_c and the accumulated diagonal (Section 4: diag(H_l) is
     accumulated cell by cell, which complex layers and varying phi require)."""
 
     def __init__(self, d, level, k2_vertices, theta, layer_width, theta_interior=0.0):
@@ -239,7 +239,7 @@ def zero_boundary(x):
 
 
 # ----------------------------------------------------------------------------
-# Grid transfer (Section 3: d-linear P, R = P^T, injection I)
+# Grid transfer (Section 4: d-linear P, R = P^T, injection I)
 # ----------------------------------------------------------------------------
 def prolong(xc):
     """d-linear interpolation from level l-1 to level l on the tripartitioned
@@ -280,7 +280,7 @@ def inject(xf):
 
 
 def cpoint_mask(d, level):
-    """cPoint(v) (Section 4.1): the vertex coincides with a vertex of the next
+    """cPoint(v) (Section 5.1): the vertex coincides with a vertex of the next
     coarser level, i.e. all of its level-l indices are multiples of 3."""
     n = cells_per_axis(level)
     m = np.zeros((n + 1,) * d, dtype=bool)
@@ -289,14 +289,14 @@ def cpoint_mask(d, level):
 
 
 # ----------------------------------------------------------------------------
-# Relaxation schemes (Section 4.1 table) on a regular grid: succ(v) = L - l
+# Relaxation schemes (Section 5.1 table) on a regular grid: succ(v) = L - l
 # ----------------------------------------------------------------------------
 JACOBI, UCG, LGRID, EXP, TRANSITION = 0, 1, 2, 3, 4
 
 
 def omega_scheme(scheme, omega_s, depth, iter_n=1, l_grid=0):
     """Per-level factors omega_l, index l-1, from the five schemes of the
-    Section 4.1 table with succ = L - l on a regular grid:
+    Section 5.1 table with succ = L - l on a regular grid:
     Jacobi only (succ = 0 gets omega_S, others 0), undamped coarse grid
     (omega_S everywhere), undamped L-grid (omega_S while succ <= L_g),
     exponential damping omega_S^(succ+1) and transition
@@ -378,7 +378,7 @@ class Hierarchy:
         """One additive FAS cycle, Appendix A Algorithm 4 (buFAS) unrolled:
 
         fine to coarse, l = L..1:
-            du_l   = omega_l diag(H_l)^{-1} (b_l - H_l u_l)       (Section 3 S)
+            du_l   = omega_l diag(H_l)^{-1} (b_l - H_l u_l)       (Section 4 S)
             if l > 1:  u_{l-1} = I u_l
                        uhat_l  = u_l - P u_{l-1}                   (surplus)
                        rhat_l  = b_l - H_l uhat_l                  (Eq. HTMG)
@@ -447,7 +447,7 @@ class Hierarchy:
 
 def fmg_start(d, depth, k2_fine, theta, layer_width, f_fine, omega,
               variant=ADD, transfer=DLINEAR, cycles_per_stage=3):
-    """Grid unfolding (Remark on FMG, Section 4; Section 7.1): stage s = 1..L
+    """Grid unfolding (Remark on FMG, Section 5; Section 7.1): stage s = 1..L
     solves on levels 1..s with b_s = M_s f (f and k^2 sampled at level-s
     vertices), starts from P u_{s-1}, and runs ``cycles_per_stage`` cycles on
     every stage but the last.  Level l of stage s uses the factor that level

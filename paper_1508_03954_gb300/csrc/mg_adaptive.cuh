@@ -1,5 +1,6 @@
 // mg_adaptive.cuh -- the additive cycle on an adaptive spacetree with hanging
-// vertices (Section 4.3 and the hanging-vertex treatment of Section 3),
+// vertices (adaptive Cartesian grids of Section 3, hanging vertices and FAS
+// injection of Section 4, relaxation factors of Section 5.1),
 // FP64, d = 2 or 3, sm_103a.
 //
 // Every level keeps dense arrays over its full grid plus a flag per cell

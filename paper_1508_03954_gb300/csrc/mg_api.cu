@@ -282,7 +282,7 @@ bool interior_real(const mg_ctx* c) { return c->theta_in == 0.0; }
 // vertex of type t has left/right cell widths hl, hr along each axis; its
 // assembled 1D stiffness row is (-1/hl, 1/hl + 1/hr, -1/hr) and its 1D mass
 // row (hl/6, (hl+hr)/3, hr/6).  The d-dimensional rows are the tensor
-// products K = sum_j (x)_a (K if a == j else M), M = (x)_a M (Section 3).
+// products K = sum_j (x)_a (K if a == j else M), M = (x)_a M (Section 4).
 void type_tables(int d, const Widths& wd, std::vector<cd>& K, std::vector<cd>& M) {
   cd KX[4][3], MX[4][3];
   for (int t = 0; t < 4; ++t) {
@@ -1562,7 +1562,7 @@ cplx<R> to_r(const cd& v) {
 // (left / right cell in the layer), the Galerkin rows those of
 // galerkin_rows_1d, the diagonal of vertex type (t0, t1, t2, t3) is
 // sum_j prod_a (K if a == j else M)[t_a] centre entries minus
-// phi prod_a M[t_a] centre (the tensor-product form of Section 3).
+// phi prod_a M[t_a] centre (the tensor-product form of Section 4).
 template <typename R>
 int d4_build(mg_ctx* c, Hier4<R>*& out) {
   Hier4<R>* H = new (std::nothrow) Hier4<R>();
@@ -2021,7 +2021,7 @@ int ada_build(mg_ctx* c, const unsigned char* refine) {
     if ((rc = d4_upload(c, *H, &V.hinv, hi)) != MG_OK) return rc;
     if ((rc = d4_upload(c, *H, &V.rotf, rot)) != MG_OK) return rc;
     {
-      // element matrices of the 2^d width classes (Section 3): M = prod_a m1,
+      // element matrices of the 2^d width classes (Section 4): M = prod_a m1,
       // K = sum_j prod_a (k1 if a == j else m1), m1(h) = h/6 [2 1; 1 2],
       // k1(h) = 1/h [1 -1; -1 1]; stored as M and K - phi0 M
       const int nc = 1 << d, ne = nc * nc;

@@ -5,7 +5,7 @@
 // A d-linear 4D stencil row has 81 points and 256 vertex types, too many for
 // the shared-memory tiles of the 2D/3D sweeps.  With coordinate-wise scaling
 // and a constant shift the operator is a sum of tensor products of assembled
-// 1D rows (Section 3 element matrices, one factor per axis):
+// 1D rows (Section 4 element matrices, one factor per axis):
 //   H = M0 [M1 [M2 (K3 - phi M3) + K2 M3] + K1 M2 M3] + K0 M1 M2 M3,
 // so H u is ten 3-tap passes along single axes; the Galerkin operator
 // G = R H P of the coarse right-hand side has the same form with the 1D

@@ -16,7 +16,7 @@
 // until the next sweep.  So the fine level reads U and b once and writes U'
 // once per cycle.
 //
-// Operator: H_l = sum over cells of K_c - phi_c M_c (Section 3, Appendix B).
+// Operator: H_l = sum over cells of K_c - phi_c M_c (Section 4, Appendix B).
 // With coordinate-wise exterior scaling every vertex has one of 4^d
 // "types" (the scaling class of its left/right cell along each axis), and
 // its 3^d stencil row is a table entry of that type, assembled on the host

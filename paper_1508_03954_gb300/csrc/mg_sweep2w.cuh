@@ -9,7 +9,7 @@
 //  * lane = x: a warp owns 27 fine columns (9 coarse cells) of a strip,
 //    [x0-3, x0+28] with a 3-column halo before and 2 after, and marches a
 //    range of coarse rows along y holding u(y-1), u(y), u(y+1) in registers;
-//  * operator: H u = M_x (K_y - phi M_y) u + K_x (M_y u) (Section 3, the 2D
+//  * operator: H u = M_x (K_y - phi M_y) u + K_x (M_y u) (Section 4, the 2D
 //    element operator as a tensor product of 1D rows): the y-pass runs in
 //    registers, the x-pass takes its neighbours by shuffles; interior rows
 //    take real coefficients;

@@ -9,7 +9,7 @@
 // Operator.  With coordinate-wise exterior scaling every cell is a tensor
 // product of 1D cells, so the assembled level operator with a constant shift
 // phi is a sum of tensor products of assembled 1D tridiagonal rows
-// (Section 3: K_c = sum_j (x)_a (K if a == j else M), M_c = (x)_a M):
+// (Section 4: K_c = sum_j (x)_a (K if a == j else M), M_c = (x)_a M):
 //     H u = M_x [ M_y (K_z - phi M_z) u + K_y M_z u ] + K_x (M_y M_z u).
 // The rows depend only on the vertex's scaling class along that axis (left
 // and right cell plain or rotated), so seven 3-tap passes replace the

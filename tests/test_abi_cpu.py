@@ -1,7 +1,7 @@
 """Host-side checks of the C ABI that need no GPU: the library builds and
 loads, exports every function include/mg.h declares, validates arguments
 before touching the device, and its host helper matches the relaxation
-schemes of Section 4.1."""
+schemes of Section 5.1."""
 import ctypes
 import os
 import re

@@ -256,7 +256,7 @@ def test_prolongation_reproduces_dlinear_functions():
 
 @pytest.mark.parametrize("d,level,k2", [(2, 2, 30.0), (2, 3, (4 * math.pi) ** 2), (3, 2, -40.0)])
 def test_galerkin_identity_uniform_scaling(d, level, k2):
-    """H_{l-1} = R H_l P for invariant scaling and shift (Section 3)."""
+    """H_{l-1} = R H_l P for invariant scaling and shift (Section 4)."""
     nf, nc = 3 ** level, 3 ** (level - 1)
     Hf, _, _ = dense_level(d, level, np.full((nf + 1,) * d, k2), TH, 0.5)
     Hc, _, _ = dense_level(d, level - 1, np.full((nc + 1,) * d, k2), TH, 0.5)
@@ -384,7 +384,7 @@ def test_poisson_analytic_discrete_solution():
 
 def test_bpx_and_hb_cpoint_structure():
     """BPX: (id - P I) vanishes at c-points, so corr_l there equals P corr_{l-1}
-    (Section 4.2); hb: the masked update leaves corr_l = P corr_{l-1} at
+    (Section 5.2); hb: the masked update leaves corr_l = P corr_{l-1} at
     c-points as well, while f-point updates pass unchanged."""
     for variant, transfer in [(O.ADD, O.HIERARCHICAL), (O.HB, O.DLINEAR)]:
         H = _problem(2, 3, 10.0, TH, 0.2)
