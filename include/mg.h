@@ -109,29 +109,82 @@ int mg_create_ecs(int d, int depth, const double* k2_field, double theta_layer,
                   double theta_interior, double width_lo, double width_hi,
                   mg_ctx** out);
 
-/* A solver on an adaptive spacetree with hanging vertices (Section 4.3,
- * static refinement).  Level 1 has all 3^d cells; a level-l cell flagged in
- * refine splits into 3^d level-(l+1) cells.  A vertex whose 2^d cells of its
- * level do not all exist is hanging: its value is the d-linear interpolation
- * from the next coarser level.  The cycle is the additive correction scheme
- * on the hierarchical generating system (the form Lemma 2 / Theorem 2 prove
+/* A solver on an adaptive spacetree with hanging vertices (the adaptive
+ * Cartesian grids of Section 3; hanging vertices and FAS injection of
+ * Section 4).  Level 1 has all 3^d cells; a level-l cell flagged in refine
+ * splits into 3^d level-(l+1) cells.  A vertex whose 2^d cells of its level
+ * do not all exist is hanging: its value is the d-linear interpolation from
+ * the next coarser level.  The cycle is the additive correction scheme on
+ * the hierarchical generating system (the form Lemma 2 / Theorem 2 prove
  * the FAS cycle equal to): every level's residual is the cell-wise residual
  * of its leaves plus the restricted residual of the next finer level
- * (including the partial residuals of hanging vertices).
- *  d          2 or 3;  k2_field, theta, layer_width: as mg_create.
+ * (including the partial residuals of hanging vertices).  Relaxation factors
+ * are per vertex (Section 5.1 table): mg_cycle's omega[depth - 1 - s] is the
+ * factor of the vertices with succ(v) = s, where succ(v) = 0 unless all 2^d
+ * cells around v are refined, else 1 + the minimum of succ over v's children
+ * that carry unknowns; on a fully refined tree succ = depth - l, the regular
+ * grid's level factors.
+ *  d          2 or 3;  k2_field, theta_layer, theta_interior, width_lo,
+ *             width_hi: as mg_create_ecs.
  *  refine     host, the flags of levels 1..depth-1 concatenated: level l's
  *             (3^l)^d bytes (x fastest), nonzero = refine; flags of cells
- *             that do not exist are ignored.
+ *             that do not exist are ignored.  The deepest levels may hold
+ *             no cells yet (mg_adapt can fill them).
  * Runs mg_set_rhs, mg_set_solution and mg_get_solution (nodal values on the
  * uniform finest grid; mg_get_solution returns the fine-grid function, d-
  * linear on each leaf), mg_get_level (which = 0: the level's values, 1: its
- * residual of the last cycle), mg_cycle, mg_residual_norm (over the fine-grid
- * unknowns), mg_last_cycle_norm and mg_solve in complex128; the other calls
- * return MG_ERR_INVALID.  Arrays are dense over every level's full grid.
- * Errors: as mg_create, and MG_ERR_INVALID for a NULL refine or d = 4. */
-int mg_create_adaptive(int d, int depth, const double* k2_field, double theta,
-                       double layer_width, const unsigned char* refine,
-                       mg_ctx** out);
+ * residual of the last cycle), mg_cycle, mg_residual_norm and mg_residual_max
+ * (over the fine-grid vertices: unknowns with no unknown at the same point on
+ * the next finer level), mg_last_cycle_norm, mg_solve in complex128,
+ * mg_adapt and mg_get_refinement; the other calls return MG_ERR_INVALID.
+ * Arrays are dense over every level's full grid; kernels run over the
+ * bounding box of each level's existing vertices.
+ * Errors: as mg_create_ecs, and MG_ERR_INVALID for a NULL refine or d = 4. */
+int mg_create_adaptive(int d, int depth, const double* k2_field, double theta_layer,
+                       double theta_interior, double width_lo, double width_hi,
+                       const unsigned char* refine, mg_ctx** out);
+
+/* One step of feature-based dynamic refinement and erasing (Section 5.3) on
+ * an adaptive context, all on the device but for choosing the bins:
+ *  1. s(v) = max over the axes of |u(v - e) - 2 u(v) + u(v + e)| (undivided
+ *     second differences of the level's values) at every fine-grid vertex;
+ *  2. the span [min s, max s] is split into `bins` equal subranges; the k top
+ *     bins whose vertex count is closest to refine_frac x (fine-grid
+ *     vertices) are refined, the k' bottom bins closest to erase_frac x
+ *     (fine-grid vertices) erased (the smallest k, k' on ties; a vertex in
+ *     both sets is refined);
+ *  3. vetoes: |r(v) / H_l[v, v]| > veto (the vertex still changes: r is the
+ *     current generating-system residual), refining on level depth (h_min),
+ *     and erasing below min_level + 1 (h_max: min_level is the level of the
+ *     coarsest admissible grid, whose cells stay);
+ *  4. refining a vertex refines its 2^d cells; a refined cell of level
+ *     l >= min_level loses its children when they are leaves, none is being
+ *     refined and every fine-grid vertex of level l + 1 on the closed cell is
+ *     erased (one level of coarsening per step);
+ *  5. vertices that exist after the step and did not carry an unknown both
+ *     before and after it take P u_(l-1) (zero hierarchical surplus), then
+ *     coarse copies of finer unknowns are injected.  Pure refinement leaves
+ *     the fine-grid function unchanged.
+ *  refine_frac, erase_frac   in [0, 1] (the paper: 0.1, 0.02)
+ *  bins                      in [1, 64] (the paper: 20)
+ *  veto                      > 0 (the paper: 1e-2; +inf disables it)
+ *  min_level                 in [1, depth]
+ *  stats                     host long long[4] or NULL: vertices selected for
+ *                            refining, for erasing, fine-grid vertices after
+ *                            the step, finest level holding cells.
+ * Synchronises the stream twice (bin counts, new bounding boxes); the next
+ * mg_cycle captures a new graph.
+ * Errors: MG_ERR_INVALID (not adaptive, arguments out of range),
+ * MG_DIVERGED (a non-finite indicator: the grid is left as it is),
+ * MG_ERR_CUDA. */
+int mg_adapt(mg_ctx* ctx, double refine_frac, double erase_frac, int bins, double veto, int min_level,
+             long long* stats);
+
+/* The current refine flags of an adaptive context in mg_create_adaptive's
+ * layout (levels 1..depth-1 concatenated, x fastest, 1 = refined).
+ *  refine   host, sum over l < depth of (3^l)^d bytes.  Synchronising.
+ * Errors: MG_ERR_INVALID (NULL, not adaptive), MG_ERR_CUDA. */
+int mg_get_refinement(mg_ctx* ctx, unsigned char* refine);
 
 /* Releases every device buffer of the context (NULL is ignored). */
 void mg_destroy(mg_ctx* ctx);
@@ -168,7 +221,8 @@ int mg_residual_norm(mg_ctx* ctx, double* abs_l2, double* rel_l2);
 /* Maximum modulus of the fine residual b - H u over the vertices (the max
  * norm of the Section 7.4 table), computed on the device; a non-finite
  * entry gives +infinity.  The first call allocates one fine-size complex128
- * buffer.  Synchronises the stream.
+ * buffer (an adaptive context: the max over its fine-grid vertices, fused
+ * into the residual pass, no allocation).  Synchronises the stream.
  * Errors: MG_ERR_INVALID (NULL), MG_ERR_OOM, MG_ERR_CUDA, MG_ERR_TIMEOUT. */
 int mg_residual_max(mg_ctx* ctx, double* abs_max);
 

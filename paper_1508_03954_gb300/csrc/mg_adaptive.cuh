@@ -20,6 +20,18 @@
 // coarse).  A cycle is three passes: the residuals fine to coarse (norm
 // fused), one fused kernel per level coarse to fine, the injection fine to
 // coarse -- 3L - 1 launches in one CUDA graph.
+//
+// Relaxation factors are per vertex (the Section 5.1 table): omega(v) is
+// looked up by succ(v), 0 unless all 2^d cells of v's level are refined,
+// else 1 + the minimum over v's children that carry unknowns.
+//
+// Feature-based dynamic refinement (Section 5.3) runs on the device too: the
+// indicator s(v) = max over the axes of the undivided second difference at
+// the fine-grid vertices, its global span and a histogram over equal bins
+// (the host picks how many top / bottom bins to refine / erase), marks on
+// cells and vertices, the new cell flags (fine to coarse, then existence
+// coarse to fine), the new vertex classes with zero hierarchical surplus on
+// new vertices, and succ.
 #pragma once
 #include "mg_kernels.cuh"
 
@@ -33,6 +45,14 @@ enum : uint8_t { kVertNone = 0, kVertBound = 1, kVertUnknown = 2 };
 struct AdaBox {
   int lo[3], ext[3];
 };
+
+// omega by succ: w[s] is the factor of a vertex with succ(v) = s.
+constexpr int kAdaMaxLevels = 16;
+struct AdaOmega {
+  cplx<double> w[kAdaMaxLevels];
+};
+
+enum : uint8_t { kCellNewRef = 4 };  // scratch bit: refined after the step
 
 // Coordinates g and level-grid index of the t-th vertex of the box.
 template <int D>
@@ -104,10 +124,10 @@ __global__ void __launch_bounds__(256) ada_residual_kernel(
     const cplx<double>* __restrict__ hinv, const double* __restrict__ phic, double phi0,
     const cplx<double>* __restrict__ rf, cplx<double>* __restrict__ r, const uint8_t* __restrict__ vcls_f,
     double* partial, unsigned* ticket, double* norm2, AdaBox box, const uint8_t* __restrict__ rotf,
-    const cplx<double>* __restrict__ emat) {
+    const cplx<double>* __restrict__ emat, unsigned long long* maxabs) {
   const int N = n + 1, Nf = 3 * n + 1;
   const unsigned vol = box_volume<D>(box);
-  double nrm = 0.0;
+  double nrm = 0.0, mx = 0.0;
   for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < vol; t += gridDim.x * blockDim.x) {
     int g[3];
     const unsigned i = box_vertex<D>(t, box, N, g);
@@ -182,10 +202,25 @@ __global__ void __launch_bounds__(256) ada_residual_kernel(
           }
           own = vcls_f[fi] != kVertUnknown;
         }
-        if (own) nrm = fma(acc.x, acc.x, fma(acc.y, acc.y, nrm));
+        if (own) {
+          nrm = fma(acc.x, acc.x, fma(acc.y, acc.y, nrm));
+          if (maxabs != nullptr) {
+            const double m = sqrt(fma(acc.x, acc.x, acc.y * acc.y));
+            mx = m == m ? fmax(mx, m) : __longlong_as_double(0x7ff0000000000000LL);  // NaN counts as +inf
+          }
+        }
       }
     }
     r[i] = acc;
+  }
+  if (maxabs != nullptr) {
+    // non-negative doubles order like their bit patterns
+    unsigned long long b = (unsigned long long)__double_as_longlong(mx);
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long q = __shfl_xor_sync(0xffffffffu, b, o);
+      b = q > b ? q : b;
+    }
+    if ((threadIdx.x & 31) == 0 && b != 0ull) atomicMax(maxabs, b);
   }
   if (norm2 != nullptr) {
     __shared__ double s_red[8];
@@ -240,7 +275,8 @@ __global__ void ada_diag_kernel(int n, const uint8_t* __restrict__ vcls, const c
 // and u_{l-1}, corr_{l-1} already final (levels run coarse to fine).
 template <int D>
 __global__ void ada_down_kernel(int n, const cplx<double>* __restrict__ r, const cplx<double>* __restrict__ invd,
-                                const uint8_t* __restrict__ vcls, cplx<double> omega, int hb, int hier,
+                                const uint8_t* __restrict__ vcls, const uint8_t* __restrict__ succ, AdaOmega om,
+                                int hb, int hier,
                                 const cplx<double>* __restrict__ corr_c, const cplx<double>* __restrict__ u_c,
                                 cplx<double>* __restrict__ corr, cplx<double>* __restrict__ u, AdaBox box) {
   const int N = n + 1, Nc = n / 3 + 1;
@@ -263,7 +299,7 @@ __global__ void ada_down_kernel(int n, const cplx<double>* __restrict__ r, const
       continue;
     }
     cplx<double> c = cz<double>();
-    if (cls == kVertUnknown && !(hb && cpt)) c = omega * (r[i] * invd[i]);
+    if (cls == kVertUnknown && !(hb && cpt)) c = om.w[succ[i]] * (r[i] * invd[i]);
     cplx<double> pc = cz<double>(), pt = cz<double>(), pu = cz<double>();
     if (corr_c != nullptr) {
 #pragma unroll
@@ -286,7 +322,7 @@ __global__ void ada_down_kernel(int n, const cplx<double>* __restrict__ r, const
         const double w = (double)iw;
         pc = rfma(w, corr_c[ci], pc);
         pu = rfma(w, u_c[ci], pu);
-        if (hier && !hb && vcls[fi] == kVertUnknown) pt = rfma(w, omega * (r[fi] * invd[fi]), pt);
+        if (hier && !hb && vcls[fi] == kVertUnknown) pt = rfma(w, om.w[succ[fi]] * (r[fi] * invd[fi]), pt);
       }
     }
     c = c - rmul(inv, pt) + rmul(inv, pc);
@@ -405,6 +441,370 @@ __global__ void ada_overwrite_kernel(int n, const uint8_t* __restrict__ vcls, co
   for (int a = 0; a < D; ++a) total *= (unsigned)N;
   for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x)
     if (vcls[i] != kVertNone) y[i] = x[i];
+}
+
+// ---------------------------------------------------------------------------
+// Feature-based dynamic refinement (Section 5.3)
+
+// Fine-grid vertex: an unknown with no unknown at the same point on the
+// next finer level (vcls_f null: this is the finest level).
+template <int D>
+__device__ __forceinline__ bool ada_fine_grid(const uint8_t* vcls, const uint8_t* vcls_f, unsigned i, const int* g,
+                                              int Nf) {
+  if (vcls[i] != kVertUnknown) return false;
+  if (vcls_f == nullptr) return true;
+  unsigned fi = 0, fs = 1;
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    fi += (unsigned)(3 * g[a]) * fs;
+    fs *= (unsigned)Nf;
+  }
+  return vcls_f[fi] != kVertUnknown;
+}
+
+// The bin of s among `bins` equal subranges of [lo, hi], rounded as written
+// (no contraction), the top value in the last bin.
+__device__ __forceinline__ int ada_bin(double s, double lo, double hi, int bins) {
+  if (!(hi > lo)) return 0;
+  const double q = __dmul_rn(__ddiv_rn(__dsub_rn(s, lo), __dsub_rn(hi, lo)), (double)bins);
+  if (!(q >= 0.0)) return 0;
+  if (q >= (double)(bins - 1)) return bins - 1;
+  return (int)floor(q);
+}
+
+__device__ __forceinline__ void warp_minmax_atomic(unsigned long long lo, unsigned long long hi,
+                                                   unsigned long long* mm) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long a = __shfl_xor_sync(0xffffffffu, lo, o);
+    const unsigned long long b = __shfl_xor_sync(0xffffffffu, hi, o);
+    lo = a < lo ? a : lo;
+    hi = b > hi ? b : hi;
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (lo != ~0ull) atomicMin(mm, lo);
+    if (hi != 0ull) atomicMax(mm + 1, hi);
+  }
+}
+
+// s(v) = max over the axes of |u(v - e) - 2 u(v) + u(v + e)| at the
+// fine-grid vertices of the level's box (sums rounded as written), -1
+// elsewhere; the span over all levels into mm (bit patterns of non-negative
+// doubles: min in mm[0], max in mm[1]) and the number of fine-grid vertices
+// into *cnt.  One thread per box vertex: every lane reaches the warp
+// reductions.
+template <int D>
+__global__ void ada_indicator_kernel(int n, const cplx<double>* __restrict__ u, const uint8_t* __restrict__ vcls,
+                                     const uint8_t* __restrict__ vcls_f, double* __restrict__ s_out, AdaBox box,
+                                     unsigned long long* mm, unsigned long long* cnt) {
+  const int N = n + 1, Nf = 3 * n + 1;
+  const unsigned vol = box_volume<D>(box);
+  unsigned long long lo = ~0ull, hi = 0ull;
+  unsigned mine = 0;
+  for (unsigned t0 = blockIdx.x * blockDim.x; t0 < vol; t0 += gridDim.x * blockDim.x) {
+    const unsigned t = t0 + threadIdx.x;
+    if (t < vol) {
+      int g[3];
+      const unsigned i = box_vertex<D>(t, box, N, g);
+      double sv = -1.0;
+      if (ada_fine_grid<D>(vcls, vcls_f, i, g, Nf)) {
+        sv = 0.0;
+        unsigned st = 1;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          const cplx<double> um = u[i - st], up = u[i + st], u0 = u[i];
+          const double sx = __dsub_rn(__dadd_rn(um.x, up.x), __dmul_rn(2.0, u0.x));
+          const double sy = __dsub_rn(__dadd_rn(um.y, up.y), __dmul_rn(2.0, u0.y));
+          sv = fmax(sv, sqrt(__dadd_rn(__dmul_rn(sx, sx), __dmul_rn(sy, sy))));
+          st *= (unsigned)N;
+        }
+        const unsigned long long b = (unsigned long long)__double_as_longlong(sv);
+        lo = b < lo ? b : lo;
+        hi = b > hi ? b : hi;
+        ++mine;
+      }
+      s_out[i] = sv;
+    }
+  }
+  warp_minmax_atomic(lo, hi, mm);
+  for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+  if ((threadIdx.x & 31) == 0 && mine != 0u) atomicAdd(cnt, (unsigned long long)mine);
+}
+
+// Histogram of the fine-grid vertices over the bins (bins <= 64).
+template <int D>
+__global__ void ada_hist_kernel(int n, const double* __restrict__ s, AdaBox box, const unsigned long long* mm,
+                                int bins, unsigned long long* counts) {
+  __shared__ unsigned h[64];
+  for (int k = threadIdx.x; k < 64; k += blockDim.x) h[k] = 0u;
+  __syncthreads();
+  const int N = n + 1;
+  const double lo = __longlong_as_double((long long)mm[0]), hi = __longlong_as_double((long long)mm[1]);
+  const unsigned vol = box_volume<D>(box);
+  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < vol; t += gridDim.x * blockDim.x) {
+    int g[3];
+    const unsigned i = box_vertex<D>(t, box, N, g);
+    const double sv = s[i];
+    if (sv >= 0.0) atomicAdd(&h[ada_bin(sv, lo, hi, bins)], 1u);
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < bins; k += blockDim.x)
+    if (h[k] != 0u) atomicAdd(counts + k, (unsigned long long)h[k]);
+}
+
+// Selection: a fine-grid vertex in the top bins (bin >= ref_from) that is
+// not vetoed (|r / H[v, v]| <= veto) is refined -- its 2^D cells get
+// rmark -- when can_refine; one in the bottom bins (bin < er_below), not in
+// the top ones and not vetoed gets emark when can_erase.  sel[0], sel[1]
+// count them.
+template <int D>
+__global__ void ada_mark_kernel(int n, const double* __restrict__ s, const cplx<double>* __restrict__ r,
+                                const cplx<double>* __restrict__ invd, AdaBox box, const unsigned long long* mm,
+                                int bins, int ref_from, int er_below, double veto, int can_refine, int can_erase,
+                                uint8_t* __restrict__ rmark, uint8_t* __restrict__ emark,
+                                unsigned long long* sel) {
+  const int N = n + 1;
+  const double lo = __longlong_as_double((long long)mm[0]), hi = __longlong_as_double((long long)mm[1]);
+  const unsigned vol = box_volume<D>(box);
+  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < vol; t += gridDim.x * blockDim.x) {
+    int g[3];
+    const unsigned i = box_vertex<D>(t, box, N, g);
+    const double sv = s[i];
+    if (!(sv >= 0.0)) continue;
+    const int b = ada_bin(sv, lo, hi, bins);
+    const cplx<double> q = r[i] * invd[i];
+    const bool vetoed = sqrt(fma(q.x, q.x, q.y * q.y)) > veto;
+    const bool top = b >= ref_from && !vetoed;
+    if (top && can_refine) {
+#pragma unroll
+      for (int e = 0; e < (1 << D); ++e) {
+        unsigned ci = 0, cs = 1;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          ci += (unsigned)(g[a] - 1 + ((e >> a) & 1)) * cs;
+          cs *= (unsigned)n;
+        }
+        rmark[ci] = 1;
+      }
+      atomicAdd(sel, 1ull);
+    } else if (!top && b < er_below && !vetoed && can_erase) {
+      emark[i] = 1;
+      atomicAdd(sel + 1, 1ull);
+    }
+  }
+}
+
+// New refine bit (kCellNewRef) of the level's cells, levels fine to coarse:
+// refined after the step when marked, or refined before and not coarsened.
+// A cell is coarsened (allow: its level is at least the h_max level) when it
+// is refined, none of its 3^D children is refined or marked, and every
+// fine-grid vertex of the next level on the closed cell carries emark.
+// rmark_f, vcls_ff may be null (the next level is the finest).
+template <int D>
+__global__ void ada_coarsen_kernel(int n, uint8_t* __restrict__ cellf, const uint8_t* __restrict__ rmark,
+                                   const uint8_t* __restrict__ cellf_f, const uint8_t* __restrict__ rmark_f,
+                                   const uint8_t* __restrict__ vcls_f, const uint8_t* __restrict__ vcls_ff,
+                                   const uint8_t* __restrict__ emark_f, int allow) {
+  unsigned total = 1;
+  for (int a = 0; a < D; ++a) total *= (unsigned)n;
+  const int nf = 3 * n, Nf = nf + 1, Nff = 3 * nf + 1;
+  for (unsigned ci = blockIdx.x * blockDim.x + threadIdx.x; ci < total; ci += gridDim.x * blockDim.x) {
+    const uint8_t old = cellf[ci] & (kCellExists | kCellRefined);
+    int c[3];
+    ada_coords<D>(ci, n, c);
+    bool coarsen = false;
+    if (allow && (old & kCellRefined)) {
+      coarsen = true;
+      for (int o = 0; o < (D == 2 ? 9 : 27) && coarsen; ++o) {
+        unsigned k = 0, ks = 1;
+        int q = o;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          k += (unsigned)(3 * c[a] + q % 3) * ks;
+          q /= 3;
+          ks *= (unsigned)nf;
+        }
+        if ((cellf_f[k] & kCellRefined) || (rmark_f != nullptr && rmark_f[k])) coarsen = false;
+      }
+      for (int o = 0; o < (D == 2 ? 16 : 64) && coarsen; ++o) {
+        int w[3];
+        unsigned wi = 0, ws = 1;
+        int q = o;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          w[a] = 3 * c[a] + q % 4;
+          q /= 4;
+          wi += (unsigned)w[a] * ws;
+          ws *= (unsigned)Nf;
+        }
+        if (ada_fine_grid<D>(vcls_f, vcls_ff, wi, w, Nff) && !emark_f[wi]) coarsen = false;
+      }
+    }
+    const bool nr = (old & kCellExists) && (rmark[ci] || ((old & kCellRefined) && !coarsen));
+    cellf[ci] = old | (nr ? kCellNewRef : 0);
+  }
+}
+
+// Final flags, levels coarse to fine: a cell exists on level 1 or when its
+// parent (final) is refined; it is refined when it exists and carries
+// kCellNewRef.
+template <int D>
+__global__ void ada_finalize_cells_kernel(int n, uint8_t* __restrict__ cellf, const uint8_t* __restrict__ cellf_p) {
+  unsigned total = 1;
+  for (int a = 0; a < D; ++a) total *= (unsigned)n;
+  const int np = n / 3;
+  for (unsigned ci = blockIdx.x * blockDim.x + threadIdx.x; ci < total; ci += gridDim.x * blockDim.x) {
+    bool ex = true;
+    if (cellf_p != nullptr) {
+      int c[3];
+      ada_coords<D>(ci, n, c);
+      unsigned pi = 0, ps = 1;
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        pi += (unsigned)(c[a] / 3) * ps;
+        ps *= (unsigned)np;
+      }
+      ex = (cellf_p[pi] & kCellRefined) != 0;
+    }
+    const bool rf = ex && (cellf[ci] & kCellNewRef);
+    cellf[ci] = (uint8_t)((ex ? kCellExists : 0) | (rf ? kCellRefined : 0));
+  }
+}
+
+// New vertex classes of a level from its final cells (levels coarse to
+// fine), with zero hierarchical surplus on vertices that exist after the
+// step and did not carry an unknown both before and after it: u = P u_c
+// (u_c final; null on level 1), zero on the Dirichlet boundary.  The bounding
+// box of the vertices of existing cells goes to box6 (min x, y, z, max x, y, z).
+template <int D>
+__global__ void ada_reclass_kernel(int n, const uint8_t* __restrict__ cellf, uint8_t* __restrict__ vcls,
+                                   cplx<double>* __restrict__ u, const cplx<double>* __restrict__ u_c, int* box6) {
+  const int N = n + 1, Nc = n / 3 + 1;
+  unsigned total = 1;
+  for (int a = 0; a < D; ++a) total *= (unsigned)N;
+  const double inv = D == 2 ? 1.0 / 9.0 : 1.0 / 27.0;
+  int lo[3] = {N, N, N}, hi[3] = {-1, -1, -1};
+  for (unsigned t0 = blockIdx.x * blockDim.x; t0 < total; t0 += gridDim.x * blockDim.x) {
+    const unsigned i = t0 + threadIdx.x;
+    if (i < total) {
+      int g[3];
+      ada_coords<D>(i, N, g);
+      int cnt = 0;
+      bool inner = true;
+#pragma unroll
+      for (int e = 0; e < (1 << D); ++e) {
+        unsigned ci = 0, cs = 1;
+        bool in = true;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          const int ca = g[a] - 1 + ((e >> a) & 1);
+          in = in && ca >= 0 && ca < n;
+          ci += (unsigned)(in ? ca : 0) * cs;
+          cs *= (unsigned)n;
+        }
+        if (in && (cellf[ci] & kCellExists)) ++cnt;
+      }
+#pragma unroll
+      for (int a = 0; a < D; ++a) inner = inner && g[a] > 0 && g[a] < n;
+      const uint8_t nc = cnt == 0 ? kVertNone : ((inner && cnt == (1 << D)) ? kVertUnknown : kVertBound);
+      const uint8_t oc = vcls[i];
+      if (nc != kVertNone) {
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          lo[a] = min(lo[a], g[a]);
+          hi[a] = max(hi[a], g[a]);
+        }
+        if (u_c != nullptr && !(nc == kVertUnknown && oc == kVertUnknown)) {
+          cplx<double> pu = cz<double>();
+          if (inner) {
+#pragma unroll
+            for (int e = 0; e < (1 << D); ++e) {
+              int iw = 1;
+              unsigned ci = 0, cs = 1;
+              bool ok = true;
+#pragma unroll
+              for (int a = 0; a < D; ++a) {
+                const int bit = (e >> a) & 1, o = g[a] % 3;
+                iw *= bit ? o : 3 - o;
+                const int cc = g[a] / 3 + bit;
+                ok = ok && cc < Nc;
+                ci += (unsigned)(ok ? cc : 0) * cs;
+                cs *= (unsigned)Nc;
+              }
+              if (iw != 0 && ok) pu = rfma((double)iw, u_c[ci], pu);
+            }
+            pu = rmul(inv, pu);
+          }
+          u[i] = pu;
+        }
+      }
+      vcls[i] = nc;
+    }
+  }
+  for (int a = 0; a < D; ++a) {
+    int l = lo[a], h = hi[a];
+    for (int o = 16; o > 0; o >>= 1) {
+      l = min(l, __shfl_xor_sync(0xffffffffu, l, o));
+      h = max(h, __shfl_xor_sync(0xffffffffu, h, o));
+    }
+    if ((threadIdx.x & 31) == 0 && h >= 0) {
+      atomicMin(box6 + a, l);
+      atomicMax(box6 + 3 + a, h);
+    }
+  }
+}
+
+// succ(v) at the unknowns of a level (levels fine to coarse; succ_f null on
+// the finest level): 0 unless all 2^D cells around v are refined, else 1 +
+// the minimum of succ over the unknowns of the next level at 3v + o,
+// o in [-3, 3]^D.  The level's fine-grid vertices are counted into *nfine.
+template <int D>
+__global__ void ada_succ_kernel(int n, const uint8_t* __restrict__ cellf, const uint8_t* __restrict__ vcls,
+                                const uint8_t* __restrict__ vcls_f, const uint8_t* __restrict__ succ_f,
+                                uint8_t* __restrict__ succ, unsigned long long* nfine) {
+  const int N = n + 1, Nf = 3 * n + 1;
+  unsigned total = 1;
+  for (int a = 0; a < D; ++a) total *= (unsigned)N;
+  unsigned mine = 0;
+  for (unsigned t0 = blockIdx.x * blockDim.x; t0 < total; t0 += gridDim.x * blockDim.x) {
+    const unsigned i = t0 + threadIdx.x;
+    if (i < total) {
+      uint8_t sv = 0;
+      if (vcls[i] == kVertUnknown) {
+        int g[3];
+        ada_coords<D>(i, N, g);
+        if (ada_fine_grid<D>(vcls, vcls_f, i, g, Nf)) ++mine;
+        bool refined = succ_f != nullptr;
+#pragma unroll
+        for (int e = 0; e < (1 << D); ++e) {
+          unsigned ci = 0, cs = 1;
+#pragma unroll
+          for (int a = 0; a < D; ++a) {
+            ci += (unsigned)(g[a] - 1 + ((e >> a) & 1)) * cs;
+            cs *= (unsigned)n;
+          }
+          refined = refined && (cellf[ci] & kCellRefined);
+        }
+        if (refined) {
+          int m = 255;
+          for (int o = 0; o < (D == 2 ? 49 : 343); ++o) {
+            unsigned fi = 0, fs = 1;
+            int q = o;
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+              fi += (unsigned)(3 * g[a] + q % 7 - 3) * fs;
+              q /= 7;
+              fs *= (unsigned)Nf;
+            }
+            if (vcls_f[fi] == kVertUnknown) m = min(m, (int)succ_f[fi]);
+          }
+          sv = (uint8_t)(m + 1);
+        }
+      }
+      succ[i] = sv;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+  if ((threadIdx.x & 31) == 0 && mine != 0u) atomicAdd(nfine, (unsigned long long)mine);
 }
 
 }  // namespace mg

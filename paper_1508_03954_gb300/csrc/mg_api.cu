@@ -175,10 +175,31 @@ struct LevA {
   size_t boxvol = 0;
   uint8_t* rotf = nullptr;       // per axis index: the cell lies in the layer
   cplx<double>* emat = nullptr;  // per width class: M, then K - phi0 M (2^d x 2^d each)
+  uint8_t* succ = nullptr;       // succ(v) at unknowns (Section 5.1)
+  double* s = nullptr;           // refinement indicator (-1: not a fine-grid vertex)
+  uint8_t* rmark = nullptr;      // per cell: refined by this step's selection
+  uint8_t* emark = nullptr;      // per vertex: selected for erasing
+};
+
+// Device scratch of the adaptive context (unsigned long long slots).
+enum : int {
+  kAbMinMax = 0,   // [2] span of the indicator (bit patterns)
+  kAbCount = 2,    // fine-grid vertices seen by the indicator
+  kAbSel = 3,      // [2] vertices selected for refining, erasing
+  kAbFine = 5,     // fine-grid vertices after the step
+  kAbMax = 8,      // [kAdaMaxSlots] per-level max |r| (bit patterns)
+  kAbCounts = 32,  // [64] histogram
+  kAbSlots = 96,
+  kAdaMaxSlots = 16
 };
 
 struct HierA {
   std::vector<LevA> lev;       // 1..L
+  int Lf = 1;                  // finest level with cells
+  long long version = 0;       // structure changes (adaptation steps)
+  unsigned long long* abuf = nullptr;  // kAb* slots
+  int* box6 = nullptr;                 // per level: min x, y, z, max x, y, z
+  void* hbuf = nullptr;                // page-locked host mirror (4 KB)
   cplx<double>* T[2] = {};     // fine-size temporaries
   double* partial = nullptr;
   unsigned* ticket = nullptr;
@@ -1916,9 +1937,27 @@ int d4_refine(mg_ctx* c, int hb, int hier, const cplx<double>* omega, double tol
 }
 
 // ------------------------------------------------------------------ adaptive
+// succ of every level, fine to coarse (Section 5.1); the fine-grid
+// vertices are counted into *nfine when it is not null.
+template <int D>
+cudaError_t ada_succ_all(mg_ctx* c, unsigned long long* nfine) {
+  HierA& H = *c->ada;
+  const int L = c->L;
+  for (int l = L; l >= 1; --l) {
+    LevA& V = H.lev[l];
+    const LevA* F = l < L ? &H.lev[l + 1] : nullptr;
+    ++c->launches;
+    mg::ada_succ_kernel<D><<<grid_for(V.nv), kThreads, 0, c->stream>>>(
+        V.n, V.cellf, V.vcls, F ? F->vcls : nullptr, F ? F->succ : nullptr, V.succ,
+        nfine != nullptr ? nfine : H.abuf + kAbFine);
+  }
+  return cudaGetLastError();
+}
+
 void ada_free(HierA* H) {
   if (H == nullptr) return;
   if (H->exec) cudaGraphExecDestroy(H->exec);
+  if (H->hbuf) cudaFreeHost(H->hbuf);
   for (void* p : H->allocs) cudaFree(p);
   delete H;
 }
@@ -1990,12 +2029,14 @@ int ada_build(mg_ctx* c, const unsigned char* refine) {
           hi[a] = std::max(hi[a], g);
         }
       }
+      const bool empty = hi[0] < 0;
       V.boxvol = 1;
       for (int a = 0; a < 3; ++a) {
-        V.box.lo[a] = a < d ? lo[a] : 0;
-        V.box.ext[a] = a < d ? hi[a] - lo[a] + 1 : 1;
+        V.box.lo[a] = a < d && !empty ? lo[a] : 0;
+        V.box.ext[a] = empty ? 0 : (a < d ? hi[a] - lo[a] + 1 : 1);
         V.boxvol *= (size_t)V.box.ext[a];
       }
+      if (!empty) H->Lf = l;
     }
     const size_t bytes = V.nv * sizeof(cplx<double>);
     for (cplx<double>** p : {&V.u, &V.f, &V.r, &V.t, &V.invd}) {
@@ -2008,6 +2049,10 @@ int ada_build(mg_ctx* c, const unsigned char* refine) {
     }
     if ((rc = d4_upload(c, *H, &V.cellf, cellf)) != MG_OK) return rc;
     if ((rc = d4_upload(c, *H, &V.vcls, vcls)) != MG_OK) return rc;
+    if ((rc = d4_alloc(c, *H, (void**)&V.succ, V.nv)) != MG_OK) return rc;
+    if ((rc = d4_alloc(c, *H, (void**)&V.s, V.nv * sizeof(double))) != MG_OK) return rc;
+    if ((rc = d4_alloc(c, *H, (void**)&V.rmark, ncell)) != MG_OK) return rc;
+    if ((rc = d4_alloc(c, *H, (void**)&V.emark, V.nv)) != MG_OK) return rc;
     const std::vector<uint8_t> rot = layer_flags(c, n);
     const Widths wd = widths(c, n);
     std::vector<cplx<double>> hc(n), hi(n);
@@ -2081,20 +2126,29 @@ int ada_build(mg_ctx* c, const unsigned char* refine) {
   if ((rc = d4_alloc(c, *H, (void**)&H->partial, 152 * 16 * sizeof(double))) != MG_OK) return rc;
   if ((rc = d4_alloc(c, *H, (void**)&H->ticket, 4 * sizeof(unsigned))) != MG_OK) return rc;
   if ((rc = d4_alloc(c, *H, (void**)&H->norm2, 32 * sizeof(double))) != MG_OK) return rc;
+  if ((rc = d4_alloc(c, *H, (void**)&H->abuf, kAbSlots * sizeof(unsigned long long))) != MG_OK) return rc;
+  if ((rc = d4_alloc(c, *H, (void**)&H->box6, 6 * (L + 1) * sizeof(int))) != MG_OK) return rc;
+  MG_CUDA(c, cudaMallocHost(&H->hbuf, 4096));
+  MG_CUDA(c, d == 2 ? ada_succ_all<2>(c, nullptr) : ada_succ_all<3>(c, nullptr));
+  MG_CUDA(c, cudaDeviceSynchronize());
   return MG_OK;
 }
 
+// The residuals of levels Lf..1 (levels above Lf hold no cells), their
+// fused norms and, when maxabs is requested, per-level max |r| into
+// abuf[kAbMax + l].
 template <int D>
-cudaError_t ada_residuals(mg_ctx* c) {
+cudaError_t ada_residuals(mg_ctx* c, bool maxabs = false) {
   HierA& H = *c->ada;
-  const int L = c->L;
+  const int Lf = H.Lf;
   const double phi0 = c->k2[0];
-  for (int l = L; l >= 1; --l) {
+  for (int l = Lf; l >= 1; --l) {
     LevA& V = H.lev[l];
     ++c->launches;
     mg::ada_residual_kernel<D><<<grid_for(V.boxvol), kThreads, 0, c->stream>>>(
-        V.n, V.u, V.f, V.cellf, V.vcls, V.hcell, V.hinv, V.phic, phi0, l < L ? H.lev[l + 1].r : nullptr, V.r,
-        l < L ? H.lev[l + 1].vcls : nullptr, H.partial, H.ticket, H.norm2 + l, V.box, V.rotf, V.emat);
+        V.n, V.u, V.f, V.cellf, V.vcls, V.hcell, V.hinv, V.phic, phi0, l < Lf ? H.lev[l + 1].r : nullptr, V.r,
+        l < Lf ? H.lev[l + 1].vcls : nullptr, H.partial, H.ticket, H.norm2 + l, V.box, V.rotf, V.emat,
+        maxabs ? H.abuf + kAbMax + l : nullptr);
   }
   return cudaGetLastError();
 }
@@ -2126,18 +2180,22 @@ cudaError_t ada_invariants(mg_ctx* c) {
 template <int D>
 cudaError_t ada_enqueue_cycle(mg_ctx* c, int hb, int hier, const cplx<double>* omega) {
   HierA& H = *c->ada;
-  const int L = c->L;
+  const int L = c->L, Lf = H.Lf;
+  // omega by succ (Section 5.1): the per-level array's entry for the
+  // distance L - l to the finest level serves succ = L - l
+  mg::AdaOmega om{};
+  for (int s = 0; s < L; ++s) om.w[s] = omega[L - 1 - s];
   cudaError_t e = ada_residuals<D>(c);
-  for (int l = 1; l <= L && e == cudaSuccess; ++l) {
+  for (int l = 1; l <= Lf && e == cudaSuccess; ++l) {
     LevA& V = H.lev[l];
     const LevA* W = l > 1 ? &H.lev[l - 1] : nullptr;
     ++c->launches;
     mg::ada_down_kernel<D><<<grid_for(V.boxvol), kThreads, 0, c->stream>>>(
-        V.n, V.r, V.invd, V.vcls, omega[l - 1], hb, hier, W ? W->corr : nullptr, W ? W->u : nullptr, V.corr, V.u,
+        V.n, V.r, V.invd, V.vcls, V.succ, om, hb, hier, W ? W->corr : nullptr, W ? W->u : nullptr, V.corr, V.u,
         V.box);
     e = cudaGetLastError();
   }
-  for (int l = L - 1; l >= 1 && e == cudaSuccess; --l) {
+  for (int l = Lf - 1; l >= 1 && e == cudaSuccess; --l) {
     LevA& V = H.lev[l];
     ++c->launches;
     mg::ada_inject_unknown_kernel<D><<<grid_for(V.boxvol), kThreads, 0, c->stream>>>(V.n, H.lev[l + 1].vcls,
@@ -2151,8 +2209,8 @@ int ada_norm_host(mg_ctx* c, double* out) {
   HierA& H = *c->ada;
   // the pinned buffer holds 4 doubles: copy the level norms in groups
   double tot = 0.0;
-  for (int l0 = 1; l0 <= c->L; l0 += 4) {
-    const int cnt = std::min(4, c->L - l0 + 1);
+  for (int l0 = 1; l0 <= H.Lf; l0 += 4) {
+    const int cnt = std::min(4, H.Lf - l0 + 1);
     MG_CUDA(c, cudaMemcpyAsync(c->host_norm, H.norm2 + l0, sizeof(double) * cnt, cudaMemcpyDeviceToHost,
                                c->stream));
     MG_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -2177,7 +2235,7 @@ int ada_cycle(mg_ctx* c, int hb, int hier, const cplx<double>* omega) {
   };
   cudaError_t e = cudaSuccess;
   if (c->use_graphs && !c->timing) {
-    std::vector<double> key = {(double)hb, (double)hier};
+    std::vector<double> key = {(double)hb, (double)hier, (double)H.version};
     for (int l = 0; l < c->L; ++l) {
       key.push_back(omega[l].x);
       key.push_back(omega[l].y);
@@ -2247,6 +2305,149 @@ cudaError_t ada_composite(mg_ctx* c, cplx<double>* out) {
   if (L == 1 && e == cudaSuccess)
     e = cudaMemcpyAsync(out, H.T[0], H.lev[1].nv * sizeof(cplx<double>), cudaMemcpyDeviceToDevice, c->stream);
   return e;
+}
+
+// The number k of bins, taken from the front of counts, whose vertex total
+// is closest to goal (the smallest such k).
+int closest_bins(const unsigned long long* counts, int bins, bool from_top, double goal) {
+  int best_k = 0;
+  double best = std::fabs(goal);
+  unsigned long long acc = 0;
+  for (int k = 1; k <= bins; ++k) {
+    acc += counts[from_top ? bins - k : k - 1];
+    const double dist = std::fabs((double)acc - goal);
+    if (dist < best) {
+      best = dist;
+      best_k = k;
+    }
+  }
+  return best_k;
+}
+
+// One step of feature-based refinement (Section 5.3): indicator, span and
+// histogram on the device, the bin counts to the host, then marks, new cell
+// flags, vertex classes with zero-surplus values, diagonals, succ and the
+// injection on the device; the new bounding boxes come back with the
+// counts.  stats: vertices selected for refining and erasing, fine-grid
+// vertices after the step, finest level with cells.
+template <int D>
+int ada_adapt(mg_ctx* c, double refine_frac, double erase_frac, int bins, double veto, int min_level,
+              long long* stats) {
+  HierA& H = *c->ada;
+  const int L = c->L, Lf = H.Lf;
+  cudaStream_t st = c->stream;
+  unsigned long long* hb = static_cast<unsigned long long*>(H.hbuf);
+  // 1. residuals (the veto), indicator, span, histogram
+  MG_CUDA(c, cudaMemsetAsync(H.abuf, 0, kAbSlots * sizeof(unsigned long long), st));
+  MG_CUDA(c, cudaMemsetAsync(H.abuf + kAbMinMax, 0xff, sizeof(unsigned long long), st));
+  MG_CUDA(c, ada_residuals<D>(c));
+  for (int l = 1; l <= Lf; ++l) {
+    LevA& V = H.lev[l];
+    ++c->launches;
+    mg::ada_indicator_kernel<D><<<grid_for(V.boxvol), kThreads, 0, st>>>(
+        V.n, V.u, V.vcls, l < Lf ? H.lev[l + 1].vcls : nullptr, V.s, V.box, H.abuf + kAbMinMax, H.abuf + kAbCount);
+  }
+  for (int l = 1; l <= Lf; ++l) {
+    LevA& V = H.lev[l];
+    ++c->launches;
+    mg::ada_hist_kernel<D><<<grid_for(V.boxvol), kThreads, 0, st>>>(V.n, V.s, V.box, H.abuf + kAbMinMax, bins,
+                                                                    H.abuf + kAbCounts);
+  }
+  MG_CUDA(c, cudaGetLastError());
+  MG_CUDA(c, cudaMemcpyAsync(hb, H.abuf, kAbSlots * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+  MG_CUDA(c, cudaStreamSynchronize(st));
+  const unsigned long long nfine = hb[kAbCount];
+  double hi;
+  std::memcpy(&hi, hb + kAbMinMax + 1, sizeof hi);
+  if (nfine == 0) return MG_OK;
+  if (!std::isfinite(hi)) return MG_DIVERGED;  // the grid is left as it is
+  const int k_ref = closest_bins(hb + kAbCounts, bins, true, refine_frac * (double)nfine);
+  const int k_er = closest_bins(hb + kAbCounts, bins, false, erase_frac * (double)nfine);
+  // 2. marks
+  for (int l = 1; l <= L; ++l) {
+    LevA& V = H.lev[l];
+    MG_CUDA(c, cudaMemsetAsync(V.rmark, 0, (size_t)ipow(V.n, D), st));
+    MG_CUDA(c, cudaMemsetAsync(V.emark, 0, V.nv, st));
+  }
+  for (int l = 1; l <= Lf; ++l) {
+    LevA& V = H.lev[l];
+    ++c->launches;
+    mg::ada_mark_kernel<D><<<grid_for(V.boxvol), kThreads, 0, st>>>(
+        V.n, V.s, V.r, V.invd, V.box, H.abuf + kAbMinMax, bins, bins - k_ref, k_er, veto, l < L ? 1 : 0,
+        l >= min_level + 1 ? 1 : 0, V.rmark, V.emark, H.abuf + kAbSel);
+  }
+  // 3. new refine bits fine to coarse, then existence coarse to fine
+  for (int l = std::min(Lf, L - 1); l >= 1; --l) {
+    LevA& V = H.lev[l];
+    const LevA& F = H.lev[l + 1];
+    ++c->launches;
+    mg::ada_coarsen_kernel<D><<<grid_for((size_t)ipow(V.n, D)), kThreads, 0, st>>>(
+        V.n, V.cellf, V.rmark, F.cellf, l + 1 < L ? F.rmark : nullptr, F.vcls,
+        l + 2 <= L ? H.lev[l + 2].vcls : nullptr, F.emark, l >= min_level ? 1 : 0);
+  }
+  const int Lt = std::min(Lf + 1, L);  // levels that may hold cells after the step
+  for (int l = 1; l <= Lt; ++l) {
+    LevA& V = H.lev[l];
+    ++c->launches;
+    mg::ada_finalize_cells_kernel<D><<<grid_for((size_t)ipow(V.n, D)), kThreads, 0, st>>>(
+        V.n, V.cellf, l > 1 ? H.lev[l - 1].cellf : nullptr);
+  }
+  // 4. vertex classes and zero-surplus values coarse to fine, boxes
+  std::vector<int> b0(6 * (L + 1));
+  for (int l = 0; l <= L; ++l)
+    for (int a = 0; a < 3; ++a) {
+      b0[6 * l + a] = 1 << 30;
+      b0[6 * l + 3 + a] = -1;
+    }
+  std::memcpy(static_cast<char*>(H.hbuf) + 2048, b0.data(), b0.size() * sizeof(int));
+  MG_CUDA(c, cudaMemcpyAsync(H.box6, static_cast<char*>(H.hbuf) + 2048, b0.size() * sizeof(int),
+                             cudaMemcpyHostToDevice, st));
+  for (int l = 1; l <= Lt; ++l) {
+    LevA& V = H.lev[l];
+    ++c->launches;
+    mg::ada_reclass_kernel<D><<<grid_for(V.nv), kThreads, 0, st>>>(V.n, V.cellf, V.vcls, V.u,
+                                                                   l > 1 ? H.lev[l - 1].u : nullptr, H.box6 + 6 * l);
+    ++c->launches;
+    mg::ada_diag_kernel<D><<<grid_for(V.nv), kThreads, 0, st>>>(V.n, V.vcls, V.hcell, V.hinv, V.phic, c->k2[0],
+                                                                V.invd);
+  }
+  MG_CUDA(c, cudaGetLastError());
+  MG_CUDA(c, ada_succ_all<D>(c, H.abuf + kAbFine));
+  // 5. coarse copies of finer unknowns (fine to coarse), stale residuals
+  for (int l = Lt - 1; l >= 1; --l) {
+    LevA& V = H.lev[l];
+    mg::AdaBox full{};
+    for (int a = 0; a < 3; ++a) full.ext[a] = a < D ? V.n + 1 : 1;
+    ++c->launches;
+    mg::ada_inject_unknown_kernel<D><<<grid_for(V.nv), kThreads, 0, st>>>(V.n, H.lev[l + 1].vcls,
+                                                                          H.lev[l + 1].u, V.u, full);
+  }
+  for (int l = 1; l <= L; ++l)
+    MG_CUDA(c, cudaMemsetAsync(H.lev[l].r, 0, H.lev[l].nv * sizeof(cplx<double>), st));
+  MG_CUDA(c, cudaGetLastError());
+  MG_CUDA(c, cudaMemcpyAsync(hb, H.abuf, kAbSlots * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+  MG_CUDA(c, cudaMemcpyAsync(static_cast<char*>(H.hbuf) + 2048, H.box6, b0.size() * sizeof(int),
+                             cudaMemcpyDeviceToHost, st));
+  MG_CUDA(c, cudaStreamSynchronize(st));
+  const int* bx = reinterpret_cast<const int*>(static_cast<const char*>(H.hbuf) + 2048);
+  H.Lf = 1;
+  for (int l = 1; l <= L; ++l) {
+    LevA& V = H.lev[l];
+    const bool empty = l > Lt || bx[6 * l + 3] < 0;
+    V.boxvol = 1;
+    for (int a = 0; a < 3; ++a) {
+      V.box.lo[a] = a < D && !empty ? bx[6 * l + a] : 0;
+      V.box.ext[a] = empty ? 0 : (a < D ? bx[6 * l + 3 + a] - bx[6 * l + a] + 1 : 1);
+      V.boxvol *= (size_t)V.box.ext[a];
+    }
+    if (!empty) H.Lf = l;
+  }
+  ++H.version;
+  stats[0] = (long long)hb[kAbSel];
+  stats[1] = (long long)hb[kAbSel + 1];
+  stats[2] = (long long)hb[kAbFine];
+  stats[3] = H.Lf;
+  return MG_OK;
 }
 
 const char* kNot4 = " is not available for d = 4 (the four-dimensional path runs complex128 cycles)";
@@ -2338,15 +2539,48 @@ int mg_create_ecs(int d, int depth, const double* k2_field, double theta_layer, 
   return create_ctx(d, depth, k2_field, theta_layer, theta_interior, width_lo, width_hi, nullptr, out);
 }
 
-int mg_create_adaptive(int d, int depth, const double* k2_field, double theta, double layer_width,
-                       const unsigned char* refine, mg_ctx** out) {
+int mg_create_adaptive(int d, int depth, const double* k2_field, double theta_layer, double theta_interior,
+                       double width_lo, double width_hi, const unsigned char* refine, mg_ctx** out) {
   g_create_err.clear();
   if (out != nullptr) *out = nullptr;
   if (refine == nullptr) return fail(nullptr, MG_ERR_INVALID, "refine is NULL");
   if (d != 2 && d != 3) return fail(nullptr, MG_ERR_INVALID, "an adaptive grid takes d = 2 or 3");
-  if (!(layer_width >= 0.0 && layer_width <= 0.5))
-    return fail(nullptr, MG_ERR_INVALID, "layer_width must be in [0, 0.5]");
-  return create_ctx(d, depth, k2_field, theta, 0.0, layer_width, layer_width, refine, out);
+  return create_ctx(d, depth, k2_field, theta_layer, theta_interior, width_lo, width_hi, refine, out);
+}
+
+int mg_adapt(mg_ctx* c, double refine_frac, double erase_frac, int bins, double veto, int min_level,
+             long long* stats) {
+  if (check_ctx(c)) return MG_ERR_INVALID;
+  if (c->ada == nullptr) return fail(c, MG_ERR_INVALID, "mg_adapt takes an adaptive context (mg_create_adaptive)");
+  if (!(refine_frac >= 0.0 && refine_frac <= 1.0 && erase_frac >= 0.0 && erase_frac <= 1.0))
+    return fail(c, MG_ERR_INVALID, "refine_frac and erase_frac must be in [0, 1]");
+  if (bins < 1 || bins > 64) return fail(c, MG_ERR_INVALID, "bins must be in [1, 64]");
+  if (!(veto > 0.0)) return fail(c, MG_ERR_INVALID, "veto must be > 0");
+  if (min_level < 1 || min_level > c->L) return fail(c, MG_ERR_INVALID, "min_level must be in [1, depth]");
+  long long st[4] = {0, 0, 0, 0};
+  const int rc = c->d == 2 ? ada_adapt<2>(c, refine_frac, erase_frac, bins, veto, min_level, st)
+                           : ada_adapt<3>(c, refine_frac, erase_frac, bins, veto, min_level, st);
+  if (rc != MG_OK && rc != MG_DIVERGED) return rc;
+  if (stats != nullptr) std::memcpy(stats, st, sizeof st);
+  return rc;
+}
+
+int mg_get_refinement(mg_ctx* c, unsigned char* refine) {
+  if (check_ctx(c)) return MG_ERR_INVALID;
+  if (c->ada == nullptr) return fail(c, MG_ERR_INVALID, "mg_get_refinement takes an adaptive context");
+  if (refine == nullptr) return fail(c, MG_ERR_INVALID, "refine is NULL");
+  HierA& H = *c->ada;
+  size_t off = 0;
+  std::vector<uint8_t> fl;
+  for (int l = 1; l < c->L; ++l) {
+    const size_t ncell = (size_t)ipow(H.lev[l].n, c->d);
+    fl.resize(ncell);
+    MG_CUDA(c, cudaMemcpyAsync(fl.data(), H.lev[l].cellf, ncell, cudaMemcpyDeviceToHost, c->stream));
+    MG_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (size_t i = 0; i < ncell; ++i) refine[off + i] = (fl[i] & mg::kCellRefined) ? 1 : 0;
+    off += ncell;
+  }
+  return MG_OK;
 }
 
 void mg_destroy(mg_ctx* c) {
@@ -2575,8 +2809,23 @@ int mg_residual_norm(mg_ctx* c, double* abs_l2, double* rel_l2) {
 
 int mg_residual_max(mg_ctx* c, double* abs_max) {
   if (check_ctx(c)) return MG_ERR_INVALID;
-  if (c->ada != nullptr) return fail(c, MG_ERR_INVALID, std::string("mg_residual_max") + kNotA);
   if (abs_max == nullptr) return fail(c, MG_ERR_INVALID, "abs_max is NULL");
+  if (c->ada != nullptr) {
+    // max |r| over the fine-grid vertices, fused into the residual pass
+    HierA& H = *c->ada;
+    MG_CUDA(c, cudaMemsetAsync(H.abuf + kAbMax, 0, kAdaMaxSlots * sizeof(unsigned long long), c->stream));
+    MG_CUDA(c, c->d == 2 ? ada_residuals<2>(c, true) : ada_residuals<3>(c, true));
+    MG_CUDA(c, cudaMemcpyAsync(H.hbuf, H.abuf + kAbMax, kAdaMaxSlots * sizeof(unsigned long long),
+                               cudaMemcpyDeviceToHost, c->stream));
+    MG_CUDA(c, cudaStreamSynchronize(c->stream));
+    const unsigned long long* b = static_cast<const unsigned long long*>(H.hbuf);
+    unsigned long long m = 0;
+    for (int l = 1; l <= H.Lf; ++l) m = std::max(m, b[l]);
+    double v;
+    std::memcpy(&v, &m, sizeof v);
+    *abs_max = v;
+    return MG_OK;
+  }
   if (c->d == 4) {
     Hier4<double>& H4 = *c->h4;
     unsigned long long* mx = reinterpret_cast<unsigned long long*>(H4.norm2 + 2);

@@ -25,7 +25,7 @@ STATUS_NAMES = {0: "MG_OK", 1: "MG_ERR_INVALID", 2: "MG_ERR_CUDA", 3: "MG_ERR_OO
                 4: "MG_DIVERGED", 5: "MG_NOT_CONVERGED", 6: "MG_ERR_TIMEOUT"}
 
 # every symbol include/mg.h declares
-EXPORTS = ["mg_create", "mg_create_ecs", "mg_create_adaptive", "mg_destroy", "mg_set_stream", "mg_set_rhs", "mg_set_solution",
+EXPORTS = ["mg_create", "mg_create_ecs", "mg_create_adaptive", "mg_adapt", "mg_get_refinement", "mg_destroy", "mg_set_stream", "mg_set_rhs", "mg_set_solution",
            "mg_get_solution", "mg_cycle", "mg_residual_norm", "mg_residual_max", "mg_last_cycle_norm", "mg_solve", "mg_set_precision",
            "mg_fmg", "mg_omega_scheme", "mg_get_level", "mg_set_timing", "mg_get_stats",
            "mg_set_trace", "mg_get_trace", "mg_set_spin_limit", "mg_debug_unsatisfiable_wait", "mg_set_k2", "mg_set_rhs_vector", "mg_sample",
@@ -66,7 +66,9 @@ def load(path: str | None = None):
     sig = {
         "mg_create": (ip, [ip, ip, ctypes.POINTER(dp), dp, dp, ctypes.POINTER(vp)]),
         "mg_create_ecs": (ip, [ip, ip, ctypes.POINTER(dp), dp, dp, dp, dp, ctypes.POINTER(vp)]),
-        "mg_create_adaptive": (ip, [ip, ip, ctypes.POINTER(dp), dp, dp, ctypes.c_char_p, ctypes.POINTER(vp)]),
+        "mg_create_adaptive": (ip, [ip, ip, ctypes.POINTER(dp), dp, dp, dp, dp, ctypes.c_char_p, ctypes.POINTER(vp)]),
+        "mg_adapt": (ip, [vp, dp, dp, ip, dp, ip, ctypes.POINTER(ctypes.c_longlong)]),
+        "mg_get_refinement": (ip, [vp, ctypes.c_char_p]),
         "mg_destroy": (None, [vp]),
         "mg_set_stream": (ip, [vp, vp]),
         "mg_set_rhs": (ip, [vp, vp, ip]),
@@ -192,10 +194,11 @@ class Solver:
         self._L = L
 
     @classmethod
-    def adaptive(cls, d, depth, k2_field, theta, layer_width, refine):
+    def adaptive(cls, d, depth, k2_field, theta, layer_width, refine, theta_interior=0.0):
         """A solver on an adaptive spacetree (mg_create_adaptive): refine maps
         level l = 1..depth-1 to a boolean array of its (3^l,)*d cells (numpy
-        axis order, last axis = x)."""
+        axis order, last axis = x); layer_width is w or a pair (w_lo, w_hi)
+        as for the regular solver."""
         L = load()
         self = cls.__new__(cls)
         self.d, self.depth = d, depth
@@ -211,8 +214,10 @@ class Solver:
             if np.asarray(refine[lev]).size != 3 ** (lev * d):
                 raise ValueError(f"refine[{lev}] needs {3 ** (lev * d)} flags")
         h = ctypes.c_void_p()
+        lo, hi = (layer_width, layer_width) if np.ndim(layer_width) == 0 else layer_width
         rc = L.mg_create_adaptive(d, depth, k2.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(theta),
-                                  float(layer_width), flags if flags else b"\0", ctypes.byref(h))
+                                  float(theta_interior), float(lo), float(hi), flags if flags else b"\0",
+                                  ctypes.byref(h))
         if rc != MG_OK:
             raise MgError(rc, L.mg_last_error(None).decode())
         self._h = h
@@ -272,6 +277,28 @@ class Solver:
         self._check(self._L.mg_residual_norm(self._view, ctypes.byref(a), ctypes.byref(r)),
                     "mg_residual_norm")
         return a.value, r.value
+
+    def adapt(self, min_level, refine_frac=0.1, erase_frac=0.02, bins=20, veto=1e-2):
+        """One step of feature-based refinement (mg_adapt).  Returns (vertices
+        selected for refining, for erasing, fine-grid vertices after the
+        step, finest level with cells); raises MgError on MG_DIVERGED."""
+        st = (ctypes.c_longlong * 4)()
+        self._check(self._L.mg_adapt(self._view, float(refine_frac), float(erase_frac), int(bins), float(veto),
+                                     int(min_level), st), "mg_adapt")
+        return tuple(int(x) for x in st)
+
+    def refinement(self):
+        """The current refine flags {l: bool array of level l's cells}
+        (mg_get_refinement), levels 1..depth-1."""
+        sizes = [3 ** (lev * self.d) for lev in range(1, self.depth)]
+        buf = ctypes.create_string_buffer(max(1, sum(sizes)))
+        self._check(self._L.mg_get_refinement(self._view, buf), "mg_get_refinement")
+        raw = np.frombuffer(buf.raw, dtype=np.uint8)
+        out, off = {}, 0
+        for lev, sz in zip(range(1, self.depth), sizes):
+            out[lev] = raw[off:off + sz].reshape((3 ** lev,) * self.d).astype(bool)
+            off += sz
+        return out
 
     def residual_max(self):
         """Maximum modulus of the fine residual (mg_residual_max)."""

@@ -174,7 +174,105 @@ def test_adaptive_rejects_what_it_does_not_run():
     with pytest.raises(mg.MgError):
         g.set_precision(mg.MG_C64_REFINE, 4)
     with pytest.raises(mg.MgError):
-        g.residual_max()
+        g.fmg(mg.MG_BPX, np.full(depth, 0.6), mg.MG_HIERARCHICAL, 3)
     g.close()
     with pytest.raises(mg.MgError):
         mg.Solver.adaptive(4, 1, W.constant_k2(4, 1, 1.0), 0.0, 0.0, {})
+
+
+def test_residual_max_matches_the_oracle():
+    d, depth = 2, 4
+    k2 = W.constant_k2(d, depth, 30.0)
+    g, o = pair(d, depth, k2, TH, 0.2, corner_refinement(d, depth), W.random_complex(d, depth, 21),
+                W.random_complex(d, depth, 22))
+    om = np.full(depth, 0.6)
+    for _ in range(2):
+        g.cycle(mg.MG_BPX, om, mg.MG_HIERARCHICAL)
+        o.cycle(om, O.ADD, O.HIERARCHICAL)
+    a, b = g.residual_max(), o.residual_max()
+    assert abs(a - b) <= 1e-12 * b
+    g.close()
+
+
+def decision_margins(o, bins, veto):
+    """How far the oracle's state is from flipping a decision: the distance
+    of every fine-grid vertex's scaled indicator to the interior bin edges,
+    and of |r / diag| to the veto (relative).  The parity of the flags
+    below needs both well above the rounding difference of the two sides."""
+    s = o.refinement_indicator()
+    r = o.level_residuals()
+    vals = np.concatenate([s[lev][o.fine_grid(lev)] for lev in range(1, o.L + 1)])
+    lo, hi = vals.min(), vals.max()
+    mb = mv = np.inf
+    for lev in range(1, o.L + 1):
+        f = o.fine_grid(lev)
+        q = ((s[lev][f] - lo) / (hi - lo)) * bins
+        mb = min(mb, np.abs(q - np.clip(np.round(q), 1, bins - 1)).min(initial=np.inf))
+        ratio = np.abs(r[lev][f] / o.levels[lev].diag[f])
+        mv = min(mv, (np.abs(ratio - veto) / veto).min(initial=np.inf))
+    return mb, mv
+
+
+def check_flags_and_state(g, o, depth, what):
+    got = g.refinement()
+    for lev in range(1, depth):
+        np.testing.assert_array_equal(got[lev], o.refined[lev], err_msg=f"{what}: refine flags of level {lev}")
+    check_state(g, o, depth, what)
+
+
+@pytest.mark.parametrize("d,depth,steps", [(2, 5, 6), (3, 3, 3)])
+def test_dynamic_refinement_matches_the_oracle(d, depth, steps):
+    """Feature-based refinement (Section 5.3) from the regular level-2 grid:
+    cycle, then mg_adapt, repeatedly (erasing a large fraction every other
+    step).  Every step selects the same vertices, yields the same refine
+    flags and fine-grid vertex count, and the values of every level and the
+    fine-grid function match the oracle to 1e-12."""
+    k2 = W.constant_k2(d, depth, 25.0)
+    ref = {1: np.ones((3,) * d, dtype=bool)}
+    for lev in range(2, depth):
+        ref[lev] = np.zeros((3 ** lev,) * d, dtype=bool)
+    f = W.gaussian(d, depth, (0.3, 0.6, 0.45)[:d], 0.05)
+    g, o = pair(d, depth, k2, TH, 0.2, ref, f, np.zeros((3 ** depth + 1,) * d, complex))
+    om = np.full(depth, 0.6)
+    erased = 0
+    for k in range(steps):
+        g.cycle(mg.MG_BPX, om, mg.MG_HIERARCHICAL)
+        o.cycle(om, O.ADD, O.HIERARCHICAL)
+        mb, mv = decision_margins(o, 20, 1e-2)
+        assert mb > 1e-9 and mv > 1e-9, (mb, mv)
+        ef = 0.3 if k % 2 else 0.02
+        st = g.adapt(2, 0.1, ef, 20, 1e-2)
+        ost = o.adapt(2, 0.1, ef, 20, 1e-2)
+        assert st[:3] == ost, (k, st, ost)
+        assert st[3] == max(lev for lev in range(1, depth + 1) if o.cells[lev].any())
+        erased += st[1]
+        check_flags_and_state(g, o, depth, f"step {k + 1}")
+    assert erased > 0
+    # cycles on the final grid still agree
+    for k in range(2):
+        g.cycle(mg.MG_BPX, om, mg.MG_HIERARCHICAL)
+        o.cycle(om, O.ADD, O.HIERARCHICAL)
+    check_state(g, o, depth, "after the last step")
+    a, b = g.residual_max(), o.residual_max()
+    assert abs(a - b) <= 1e-12 * b
+    g.close()
+
+
+def test_adapt_arguments_and_refinement_roundtrip():
+    d, depth = 2, 3
+    k2 = W.constant_k2(d, depth, 1.0)
+    ref = corner_refinement(d, depth)
+    g = mg.Solver.adaptive(d, depth, k2, 0.0, 0.0, ref)
+    o = AdaptiveHierarchy(d, depth, k2, 0.0, 0.0, ref)
+    got = g.refinement()
+    for lev in range(1, depth):
+        np.testing.assert_array_equal(got[lev], o.refined[lev])
+    for bad in [dict(min_level=0), dict(min_level=2, bins=0), dict(min_level=2, bins=65),
+                dict(min_level=2, refine_frac=1.5), dict(min_level=2, veto=0.0)]:
+        with pytest.raises(mg.MgError):
+            g.adapt(**bad)
+    g.close()
+    r = mg.Solver(d, depth, k2, 0.0, 0.0)
+    with pytest.raises(mg.MgError):
+        r.adapt(1)
+    r.close()
