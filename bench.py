@@ -495,10 +495,11 @@ def channel_table2_adaptive(mg, torch, iters=50, depth=7, min_level=3):
     as on the regular grid, looked up by succ(v).  Per run: max-norm
     residual reduction after 50 iterations against the start grid's initial
     residual, fine-grid vertices at the end, finest level reached, and the
-    device time per iteration (cycle + adaptation step, CUDA events)."""
+    time per iteration (CUDA events: cycle, adaptation step with its host
+    round trip, total)."""
     rows = []
     t0 = time.perf_counter()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     for deg in (0, 18, 25, 35, 45):
         c = W.channel(deg, depth)
         ref = {lev: np.full((3 ** lev,) * 2, lev < min_level) for lev in range(1, depth)}
@@ -512,7 +513,9 @@ def channel_table2_adaptive(mg, torch, iters=50, depth=7, min_level=3):
             ev[0].record()
             st = (0, 0, 0, 0)
             diverged = False
+            t_cycle = t_adapt = 0.0
             for it in range(1, iters + 1):
+                ev[2].record()
                 if solver == "jacobi":
                     w = (W.CHANNEL_OMEGA1 if it % 2 else W.CHANNEL_OMEGA2) if deg == 0 else 0.4
                     s.cycle(mg.MG_ADD, mg.omega_scheme(mg.MG_OMEGA_JACOBI, w, depth), mg.MG_DLINEAR)
@@ -520,16 +523,20 @@ def channel_table2_adaptive(mg, torch, iters=50, depth=7, min_level=3):
                     s.cycle(mg.MG_ADD, mg.omega_scheme(mg.MG_OMEGA_TRANSITION, 0.4, depth, it), mg.MG_DLINEAR)
                 else:
                     s.cycle(mg.MG_ADD, mg.omega_scheme(mg.MG_OMEGA_UCG, 0.4, depth), mg.MG_HIERARCHICAL)
+                ev[3].record()
                 try:
                     st = s.adapt(min_level, 0.1, 0.02, 20, 1e-2)
                 except mg.MgError:
                     diverged = True  # non-finite indicator: the grid stays
-            ev[1].record()
-            torch.cuda.synchronize()
+                ev[1].record()
+                torch.cuda.synchronize()
+                t_cycle += ev[2].elapsed_time(ev[3])
+                t_adapt += ev[3].elapsed_time(ev[1])
             red = s.residual_max() / r0
             rows.append({"theta_deg": deg, "solver": solver, "reduction_max_norm": float(red),
                          "diverged": bool(diverged or not red < 1.0), "fine_vertices": st[2],
-                         "finest_level": st[3], "ms_per_iteration": ev[0].elapsed_time(ev[1]) / iters})
+                         "finest_level": st[3], "ms_per_iteration": ev[0].elapsed_time(ev[1]) / iters,
+                         "ms_cycle": t_cycle / iters, "ms_adapt": t_adapt / iters})
             s.close()
     return {"iterations": iters, "depth": depth, "min_level": min_level, "seconds": time.perf_counter() - t0,
             "runs": rows}

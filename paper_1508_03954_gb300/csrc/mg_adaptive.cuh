@@ -551,19 +551,52 @@ __global__ void ada_hist_kernel(int n, const double* __restrict__ s, AdaBox box,
     if (h[k] != 0u) atomicAdd(counts + k, (unsigned long long)h[k]);
 }
 
-// Selection: a fine-grid vertex in the top bins (bin >= ref_from) that is
+// The numbers of top and bottom bins to refine and erase: for each, the
+// smallest k whose vertex total is closest to frac x (fine-grid vertices),
+// written to kb[0] (first refined bin: bins - k) and kb[1] (bins below k are
+// erased).  A non-finite indicator span selects nothing.  One thread.
+__global__ void ada_choose_bins_kernel(const unsigned long long* counts, const unsigned long long* nfine,
+                                       const unsigned long long* mm, int bins, double refine_frac,
+                                       double erase_frac, int* kb) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (!isfinite(__longlong_as_double((long long)mm[1]))) {
+    kb[0] = bins;
+    kb[1] = 0;
+    return;
+  }
+  const double n = (double)*nfine;
+  for (int side = 0; side < 2; ++side) {
+    const double goal = (side == 0 ? refine_frac : erase_frac) * n;
+    int best_k = 0;
+    double best = fabs(goal);
+    unsigned long long acc = 0;
+    for (int k = 1; k <= bins; ++k) {
+      acc += counts[side == 0 ? bins - k : k - 1];
+      const double dist = fabs((double)acc - goal);
+      if (dist < best) {
+        best = dist;
+        best_k = k;
+      }
+    }
+    kb[side] = side == 0 ? bins - best_k : best_k;
+  }
+}
+
+// Selection: a fine-grid vertex in the top bins (bin >= kb[0]) that is
 // not vetoed (|r / H[v, v]| <= veto) is refined -- its 2^D cells get
-// rmark -- when can_refine; one in the bottom bins (bin < er_below), not in
+// rmark -- when can_refine; one in the bottom bins (bin < kb[1]), not in
 // the top ones and not vetoed gets emark when can_erase.  sel[0], sel[1]
-// count them.
+// count them.  The marks start at zero (the kernels that consume them
+// clear them).
 template <int D>
 __global__ void ada_mark_kernel(int n, const double* __restrict__ s, const cplx<double>* __restrict__ r,
                                 const cplx<double>* __restrict__ invd, AdaBox box, const unsigned long long* mm,
-                                int bins, int ref_from, int er_below, double veto, int can_refine, int can_erase,
+                                int bins, const int* kb, double veto, int can_refine, int can_erase,
                                 uint8_t* __restrict__ rmark, uint8_t* __restrict__ emark,
                                 unsigned long long* sel) {
   const int N = n + 1;
   const double lo = __longlong_as_double((long long)mm[0]), hi = __longlong_as_double((long long)mm[1]);
+  const int ref_from = kb[0], er_below = kb[1];
   const unsigned vol = box_volume<D>(box);
   for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < vol; t += gridDim.x * blockDim.x) {
     int g[3];
@@ -646,9 +679,10 @@ __global__ void ada_coarsen_kernel(int n, uint8_t* __restrict__ cellf, const uin
 
 // Final flags, levels coarse to fine: a cell exists on level 1 or when its
 // parent (final) is refined; it is refined when it exists and carries
-// kCellNewRef.
+// kCellNewRef.  Clears the level's refine marks.
 template <int D>
-__global__ void ada_finalize_cells_kernel(int n, uint8_t* __restrict__ cellf, const uint8_t* __restrict__ cellf_p) {
+__global__ void ada_finalize_cells_kernel(int n, uint8_t* __restrict__ cellf, const uint8_t* __restrict__ cellf_p,
+                                          uint8_t* __restrict__ rmark) {
   unsigned total = 1;
   for (int a = 0; a < D; ++a) total *= (unsigned)n;
   const int np = n / 3;
@@ -667,6 +701,7 @@ __global__ void ada_finalize_cells_kernel(int n, uint8_t* __restrict__ cellf, co
     }
     const bool rf = ex && (cellf[ci] & kCellNewRef);
     cellf[ci] = (uint8_t)((ex ? kCellExists : 0) | (rf ? kCellRefined : 0));
+    rmark[ci] = 0;
   }
 }
 
@@ -675,9 +710,12 @@ __global__ void ada_finalize_cells_kernel(int n, uint8_t* __restrict__ cellf, co
 // step and did not carry an unknown both before and after it: u = P u_c
 // (u_c final; null on level 1), zero on the Dirichlet boundary.  The bounding
 // box of the vertices of existing cells goes to box6 (min x, y, z, max x, y, z).
+// Clears the level's erase marks and the residual of vertices that vanish
+// (the restriction of the next coarser level reads it).
 template <int D>
 __global__ void ada_reclass_kernel(int n, const uint8_t* __restrict__ cellf, uint8_t* __restrict__ vcls,
-                                   cplx<double>* __restrict__ u, const cplx<double>* __restrict__ u_c, int* box6) {
+                                   cplx<double>* __restrict__ u, const cplx<double>* __restrict__ u_c, int* box6,
+                                   uint8_t* __restrict__ emark, cplx<double>* __restrict__ r) {
   const int N = n + 1, Nc = n / 3 + 1;
   unsigned total = 1;
   for (int a = 0; a < D; ++a) total *= (unsigned)N;
@@ -738,6 +776,8 @@ __global__ void ada_reclass_kernel(int n, const uint8_t* __restrict__ cellf, uin
         }
       }
       vcls[i] = nc;
+      emark[i] = 0;
+      if (nc == kVertNone && oc != kVertNone) r[i] = cz<double>();  // no stale residual outside the boxes
     }
   }
   for (int a = 0; a < D; ++a) {

@@ -187,6 +187,7 @@ enum : int {
   kAbCount = 2,    // fine-grid vertices seen by the indicator
   kAbSel = 3,      // [2] vertices selected for refining, erasing
   kAbFine = 5,     // fine-grid vertices after the step
+  kAbBins = 6,     // [2] (as 4 ints) first refined bin, bins erased below
   kAbMax = 8,      // [kAdaMaxSlots] per-level max |r| (bit patterns)
   kAbCounts = 32,  // [64] histogram
   kAbSlots = 96,
@@ -207,6 +208,7 @@ struct HierA {
   std::vector<void*> allocs;
   cudaGraphExec_t exec = nullptr;  // the last captured cycle
   std::vector<double> key;
+  std::vector<double> seen;    // a key run once without a graph (captured when it repeats)
   long long nkern = 0;
 };
 
@@ -2226,8 +2228,8 @@ int ada_residual_norm(mg_ctx* c, double* out) {
   return ada_norm_host(c, out);
 }
 
-// One cycle as a CUDA graph, captured on first use and updated in place when
-// the variant, transfer or factors change.
+// One cycle as a CUDA graph of one launch per pass, captured when the same
+// cycle repeats and updated in place when the factors or the grid change.
 int ada_cycle(mg_ctx* c, int hb, int hier, const cplx<double>* omega) {
   HierA& H = *c->ada;
   auto enqueue = [&]() {
@@ -2240,7 +2242,13 @@ int ada_cycle(mg_ctx* c, int hb, int hier, const cplx<double>* omega) {
       key.push_back(omega[l].x);
       key.push_back(omega[l].y);
     }
-    if (H.exec == nullptr || H.key != key) {
+    const bool fresh = H.exec == nullptr || H.key != key;
+    if (fresh && H.seen != key) {
+      // a new grid or new factors runs once without a graph: capturing pays
+      // off only when the same cycle repeats (a dynamically refined grid
+      // changes every step)
+      H.seen = key;
+    } else if (fresh) {
       cudaStream_t user = c->stream;
       c->stream = c->cap_stream;
       const long long before = c->launches;
@@ -2272,7 +2280,7 @@ int ada_cycle(mg_ctx* c, int hb, int hier, const cplx<double>* omega) {
         H.nkern = nk;
       }
     }
-    if (H.exec != nullptr) {
+    if (H.exec != nullptr && H.key == key) {
       e = cudaGraphLaunch(H.exec, c->stream);
       c->launches += H.nkern;
       if (e != cudaSuccess) return fail(c, MG_ERR_CUDA, std::string("cycle launch: ") + cudaGetErrorString(e));
@@ -2307,28 +2315,10 @@ cudaError_t ada_composite(mg_ctx* c, cplx<double>* out) {
   return e;
 }
 
-// The number k of bins, taken from the front of counts, whose vertex total
-// is closest to goal (the smallest such k).
-int closest_bins(const unsigned long long* counts, int bins, bool from_top, double goal) {
-  int best_k = 0;
-  double best = std::fabs(goal);
-  unsigned long long acc = 0;
-  for (int k = 1; k <= bins; ++k) {
-    acc += counts[from_top ? bins - k : k - 1];
-    const double dist = std::fabs((double)acc - goal);
-    if (dist < best) {
-      best = dist;
-      best_k = k;
-    }
-  }
-  return best_k;
-}
-
-// One step of feature-based refinement (Section 5.3): indicator, span and
-// histogram on the device, the bin counts to the host, then marks, new cell
-// flags, vertex classes with zero-surplus values, diagonals, succ and the
-// injection on the device; the new bounding boxes come back with the
-// counts.  stats: vertices selected for refining and erasing, fine-grid
+// One step of feature-based refinement (Section 5.3), all on the device:
+// indicator, span, histogram and bin choice, marks, new cell flags, vertex
+// classes with zero-surplus values, diagonals, succ and the injection; the
+// new bounding boxes and the counts come back in one synchronisation.  stats: vertices selected for refining and erasing, fine-grid
 // vertices after the step, finest level with cells.
 template <int D>
 int ada_adapt(mg_ctx* c, double refine_frac, double erase_frac, int bins, double veto, int min_level,
@@ -2353,27 +2343,16 @@ int ada_adapt(mg_ctx* c, double refine_frac, double erase_frac, int bins, double
     mg::ada_hist_kernel<D><<<grid_for(V.boxvol), kThreads, 0, st>>>(V.n, V.s, V.box, H.abuf + kAbMinMax, bins,
                                                                     H.abuf + kAbCounts);
   }
-  MG_CUDA(c, cudaGetLastError());
-  MG_CUDA(c, cudaMemcpyAsync(hb, H.abuf, kAbSlots * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
-  MG_CUDA(c, cudaStreamSynchronize(st));
-  const unsigned long long nfine = hb[kAbCount];
-  double hi;
-  std::memcpy(&hi, hb + kAbMinMax + 1, sizeof hi);
-  if (nfine == 0) return MG_OK;
-  if (!std::isfinite(hi)) return MG_DIVERGED;  // the grid is left as it is
-  const int k_ref = closest_bins(hb + kAbCounts, bins, true, refine_frac * (double)nfine);
-  const int k_er = closest_bins(hb + kAbCounts, bins, false, erase_frac * (double)nfine);
-  // 2. marks
-  for (int l = 1; l <= L; ++l) {
-    LevA& V = H.lev[l];
-    MG_CUDA(c, cudaMemsetAsync(V.rmark, 0, (size_t)ipow(V.n, D), st));
-    MG_CUDA(c, cudaMemsetAsync(V.emark, 0, V.nv, st));
-  }
+  int* kb = reinterpret_cast<int*>(H.abuf + kAbBins);
+  ++c->launches;
+  mg::ada_choose_bins_kernel<<<1, 32, 0, st>>>(H.abuf + kAbCounts, H.abuf + kAbCount, H.abuf + kAbMinMax, bins,
+                                               refine_frac, erase_frac, kb);
+  // 2. marks (zero on entry: the kernels that consume them clear them)
   for (int l = 1; l <= Lf; ++l) {
     LevA& V = H.lev[l];
     ++c->launches;
     mg::ada_mark_kernel<D><<<grid_for(V.boxvol), kThreads, 0, st>>>(
-        V.n, V.s, V.r, V.invd, V.box, H.abuf + kAbMinMax, bins, bins - k_ref, k_er, veto, l < L ? 1 : 0,
+        V.n, V.s, V.r, V.invd, V.box, H.abuf + kAbMinMax, bins, kb, veto, l < L ? 1 : 0,
         l >= min_level + 1 ? 1 : 0, V.rmark, V.emark, H.abuf + kAbSel);
   }
   // 3. new refine bits fine to coarse, then existence coarse to fine
@@ -2390,7 +2369,7 @@ int ada_adapt(mg_ctx* c, double refine_frac, double erase_frac, int bins, double
     LevA& V = H.lev[l];
     ++c->launches;
     mg::ada_finalize_cells_kernel<D><<<grid_for((size_t)ipow(V.n, D)), kThreads, 0, st>>>(
-        V.n, V.cellf, l > 1 ? H.lev[l - 1].cellf : nullptr);
+        V.n, V.cellf, l > 1 ? H.lev[l - 1].cellf : nullptr, V.rmark);
   }
   // 4. vertex classes and zero-surplus values coarse to fine, boxes
   std::vector<int> b0(6 * (L + 1));
@@ -2405,8 +2384,8 @@ int ada_adapt(mg_ctx* c, double refine_frac, double erase_frac, int bins, double
   for (int l = 1; l <= Lt; ++l) {
     LevA& V = H.lev[l];
     ++c->launches;
-    mg::ada_reclass_kernel<D><<<grid_for(V.nv), kThreads, 0, st>>>(V.n, V.cellf, V.vcls, V.u,
-                                                                   l > 1 ? H.lev[l - 1].u : nullptr, H.box6 + 6 * l);
+    mg::ada_reclass_kernel<D><<<grid_for(V.nv), kThreads, 0, st>>>(
+        V.n, V.cellf, V.vcls, V.u, l > 1 ? H.lev[l - 1].u : nullptr, H.box6 + 6 * l, V.emark, V.r);
     ++c->launches;
     mg::ada_diag_kernel<D><<<grid_for(V.nv), kThreads, 0, st>>>(V.n, V.vcls, V.hcell, V.hinv, V.phic, c->k2[0],
                                                                 V.invd);
@@ -2422,8 +2401,6 @@ int ada_adapt(mg_ctx* c, double refine_frac, double erase_frac, int bins, double
     mg::ada_inject_unknown_kernel<D><<<grid_for(V.nv), kThreads, 0, st>>>(V.n, H.lev[l + 1].vcls,
                                                                           H.lev[l + 1].u, V.u, full);
   }
-  for (int l = 1; l <= L; ++l)
-    MG_CUDA(c, cudaMemsetAsync(H.lev[l].r, 0, H.lev[l].nv * sizeof(cplx<double>), st));
   MG_CUDA(c, cudaGetLastError());
   MG_CUDA(c, cudaMemcpyAsync(hb, H.abuf, kAbSlots * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
   MG_CUDA(c, cudaMemcpyAsync(static_cast<char*>(H.hbuf) + 2048, H.box6, b0.size() * sizeof(int),
@@ -2443,11 +2420,13 @@ int ada_adapt(mg_ctx* c, double refine_frac, double erase_frac, int bins, double
     if (!empty) H.Lf = l;
   }
   ++H.version;
+  double hi;
+  std::memcpy(&hi, hb + kAbMinMax + 1, sizeof hi);
   stats[0] = (long long)hb[kAbSel];
   stats[1] = (long long)hb[kAbSel + 1];
   stats[2] = (long long)hb[kAbFine];
   stats[3] = H.Lf;
-  return MG_OK;
+  return hb[kAbCount] != 0 && !std::isfinite(hi) ? MG_DIVERGED : MG_OK;  // a non-finite span selects nothing
 }
 
 const char* kNot4 = " is not available for d = 4 (the four-dimensional path runs complex128 cycles)";
