@@ -123,8 +123,9 @@ __global__ void __launch_bounds__(256) ada_residual_kernel(
     const uint8_t* __restrict__ cellf, const uint8_t* __restrict__ vcls, const cplx<double>* __restrict__ hcell,
     const cplx<double>* __restrict__ hinv, const double* __restrict__ phic, double phi0,
     const cplx<double>* __restrict__ rf, cplx<double>* __restrict__ r, const uint8_t* __restrict__ vcls_f,
-    double* partial, unsigned* ticket, double* norm2, AdaBox box, const uint8_t* __restrict__ rotf,
-    const cplx<double>* __restrict__ emat, unsigned long long* maxabs) {
+    double* partial, unsigned* ticket, double* norm2, const AdaBox* __restrict__ boxp,
+    const uint8_t* __restrict__ rotf, const cplx<double>* __restrict__ emat, unsigned long long* maxabs) {
+  const AdaBox box = *boxp;
   const int N = n + 1, Nf = 3 * n + 1;
   const unsigned vol = box_volume<D>(box);
   double nrm = 0.0, mx = 0.0;
@@ -278,7 +279,9 @@ __global__ void ada_down_kernel(int n, const cplx<double>* __restrict__ r, const
                                 const uint8_t* __restrict__ vcls, const uint8_t* __restrict__ succ, AdaOmega om,
                                 int hb, int hier,
                                 const cplx<double>* __restrict__ corr_c, const cplx<double>* __restrict__ u_c,
-                                cplx<double>* __restrict__ corr, cplx<double>* __restrict__ u, AdaBox box) {
+                                cplx<double>* __restrict__ corr, cplx<double>* __restrict__ u,
+                                const AdaBox* __restrict__ boxp) {
+  const AdaBox box = *boxp;
   const int N = n + 1, Nc = n / 3 + 1;
   const unsigned vol = box_volume<D>(box);
   const double inv = D == 2 ? 1.0 / 9.0 : 1.0 / 27.0;
@@ -415,7 +418,8 @@ __global__ void ada_set_hanging_kernel(int n, const uint8_t* __restrict__ vcls, 
 template <int D>
 __global__ void ada_inject_unknown_kernel(int nc, const uint8_t* __restrict__ vcls_f,
                                           const cplx<double>* __restrict__ uf, cplx<double>* __restrict__ uc,
-                                          AdaBox box) {
+                                          const AdaBox* __restrict__ boxp) {
+  const AdaBox box = *boxp;
   const int Nc = nc + 1, Nf = 3 * nc + 1;
   const unsigned vol = box_volume<D>(box);
   for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < vol; t += gridDim.x * blockDim.x) {
@@ -494,8 +498,10 @@ __device__ __forceinline__ void warp_minmax_atomic(unsigned long long lo, unsign
 // reductions.
 template <int D>
 __global__ void ada_indicator_kernel(int n, const cplx<double>* __restrict__ u, const uint8_t* __restrict__ vcls,
-                                     const uint8_t* __restrict__ vcls_f, double* __restrict__ s_out, AdaBox box,
-                                     unsigned long long* mm, unsigned long long* cnt) {
+                                     const uint8_t* __restrict__ vcls_f, double* __restrict__ s_out,
+                                     const AdaBox* __restrict__ boxp, unsigned long long* mm,
+                                     unsigned long long* cnt) {
+  const AdaBox box = *boxp;
   const int N = n + 1, Nf = 3 * n + 1;
   const unsigned vol = box_volume<D>(box);
   unsigned long long lo = ~0ull, hi = 0ull;
@@ -532,8 +538,9 @@ __global__ void ada_indicator_kernel(int n, const cplx<double>* __restrict__ u, 
 
 // Histogram of the fine-grid vertices over the bins (bins <= 64).
 template <int D>
-__global__ void ada_hist_kernel(int n, const double* __restrict__ s, AdaBox box, const unsigned long long* mm,
-                                int bins, unsigned long long* counts) {
+__global__ void ada_hist_kernel(int n, const double* __restrict__ s, const AdaBox* __restrict__ boxp,
+                                const unsigned long long* mm, int bins, unsigned long long* counts) {
+  const AdaBox box = *boxp;
   __shared__ unsigned h[64];
   for (int k = threadIdx.x; k < 64; k += blockDim.x) h[k] = 0u;
   __syncthreads();
@@ -590,10 +597,12 @@ __global__ void ada_choose_bins_kernel(const unsigned long long* counts, const u
 // clear them).
 template <int D>
 __global__ void ada_mark_kernel(int n, const double* __restrict__ s, const cplx<double>* __restrict__ r,
-                                const cplx<double>* __restrict__ invd, AdaBox box, const unsigned long long* mm,
+                                const cplx<double>* __restrict__ invd, const AdaBox* __restrict__ boxp,
+                                const unsigned long long* mm,
                                 int bins, const int* kb, double veto, int can_refine, int can_erase,
                                 uint8_t* __restrict__ rmark, uint8_t* __restrict__ emark,
                                 unsigned long long* sel) {
+  const AdaBox box = *boxp;
   const int N = n + 1;
   const double lo = __longlong_as_double((long long)mm[0]), hi = __longlong_as_double((long long)mm[1]);
   const int ref_from = kb[0], er_below = kb[1];
@@ -790,6 +799,28 @@ __global__ void ada_reclass_kernel(int n, const uint8_t* __restrict__ cellf, uin
       atomicMin(box6 + a, l);
       atomicMax(box6 + 3 + a, h);
     }
+  }
+}
+
+// box6 of levels 0..nlev-1 before the reclass passes: min = large, max = -1.
+__global__ void ada_box_init_kernel(int* box6, int nlev) {
+  for (int k = threadIdx.x; k < 6 * nlev; k += blockDim.x) box6[k] = k % 6 < 3 ? (1 << 30) : -1;
+}
+
+// The bounding boxes of levels 1..L from box6 (an empty level gets a box of
+// zero volume).  One thread.
+template <int D>
+__global__ void ada_boxes_kernel(const int* __restrict__ box6, int L, AdaBox* __restrict__ boxes) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int l = 1; l <= L; ++l) {
+    const int* b = box6 + 6 * l;
+    const bool empty = b[3] < 0;
+    AdaBox B;
+    for (int a = 0; a < 3; ++a) {
+      B.lo[a] = a < D && !empty ? b[a] : 0;
+      B.ext[a] = empty ? 0 : (a < D ? b[3 + a] - b[a] + 1 : 1);
+    }
+    boxes[l] = B;
   }
 }
 

@@ -200,7 +200,12 @@ struct HierA {
   long long version = 0;       // structure changes (adaptation steps)
   unsigned long long* abuf = nullptr;  // kAb* slots
   int* box6 = nullptr;                 // per level: min x, y, z, max x, y, z
+  mg::AdaBox* boxes = nullptr;         // per level: the bounding box, read by the kernels
+  std::vector<int> gcap;               // per level: grid of the box kernels (grows, never shrinks)
   void* hbuf = nullptr;                // page-locked host mirror (4 KB)
+  cudaGraphExec_t aexec = nullptr;     // the last captured refinement step
+  std::vector<double> akey, aseen;
+  long long ankern = 0;
   cplx<double>* T[2] = {};     // fine-size temporaries
   double* partial = nullptr;
   unsigned* ticket = nullptr;
@@ -1959,6 +1964,7 @@ cudaError_t ada_succ_all(mg_ctx* c, unsigned long long* nfine) {
 void ada_free(HierA* H) {
   if (H == nullptr) return;
   if (H->exec) cudaGraphExecDestroy(H->exec);
+  if (H->aexec) cudaGraphExecDestroy(H->aexec);
   if (H->hbuf) cudaFreeHost(H->hbuf);
   for (void* p : H->allocs) cudaFree(p);
   delete H;
@@ -2130,6 +2136,15 @@ int ada_build(mg_ctx* c, const unsigned char* refine) {
   if ((rc = d4_alloc(c, *H, (void**)&H->norm2, 32 * sizeof(double))) != MG_OK) return rc;
   if ((rc = d4_alloc(c, *H, (void**)&H->abuf, kAbSlots * sizeof(unsigned long long))) != MG_OK) return rc;
   if ((rc = d4_alloc(c, *H, (void**)&H->box6, 6 * (L + 1) * sizeof(int))) != MG_OK) return rc;
+  {
+    std::vector<mg::AdaBox> bx(L + 1);
+    H->gcap.assign(L + 1, 1);
+    for (int l = 1; l <= L; ++l) {
+      bx[l] = H->lev[l].box;
+      H->gcap[l] = grid_for(H->lev[l].boxvol);
+    }
+    if ((rc = d4_upload(c, *H, &H->boxes, bx)) != MG_OK) return rc;
+  }
   MG_CUDA(c, cudaMallocHost(&H->hbuf, 4096));
   MG_CUDA(c, d == 2 ? ada_succ_all<2>(c, nullptr) : ada_succ_all<3>(c, nullptr));
   MG_CUDA(c, cudaDeviceSynchronize());
@@ -2147,9 +2162,9 @@ cudaError_t ada_residuals(mg_ctx* c, bool maxabs = false) {
   for (int l = Lf; l >= 1; --l) {
     LevA& V = H.lev[l];
     ++c->launches;
-    mg::ada_residual_kernel<D><<<grid_for(V.boxvol), kThreads, 0, c->stream>>>(
+    mg::ada_residual_kernel<D><<<H.gcap[l], kThreads, 0, c->stream>>>(
         V.n, V.u, V.f, V.cellf, V.vcls, V.hcell, V.hinv, V.phic, phi0, l < Lf ? H.lev[l + 1].r : nullptr, V.r,
-        l < Lf ? H.lev[l + 1].vcls : nullptr, H.partial, H.ticket, H.norm2 + l, V.box, V.rotf, V.emat,
+        l < Lf ? H.lev[l + 1].vcls : nullptr, H.partial, H.ticket, H.norm2 + l, H.boxes + l, V.rotf, V.emat,
         maxabs ? H.abuf + kAbMax + l : nullptr);
   }
   return cudaGetLastError();
@@ -2170,8 +2185,8 @@ cudaError_t ada_invariants(mg_ctx* c) {
   for (int l = L - 1; l >= 1; --l) {
     LevA& V = H.lev[l];
     ++c->launches;
-    mg::ada_inject_unknown_kernel<D><<<grid_for(V.boxvol), kThreads, 0, c->stream>>>(V.n, H.lev[l + 1].vcls,
-                                                                                     H.lev[l + 1].u, V.u, V.box);
+    mg::ada_inject_unknown_kernel<D><<<H.gcap[l], kThreads, 0, c->stream>>>(V.n, H.lev[l + 1].vcls,
+                                                                           H.lev[l + 1].u, V.u, H.boxes + l);
   }
   return cudaGetLastError();
 }
@@ -2192,16 +2207,16 @@ cudaError_t ada_enqueue_cycle(mg_ctx* c, int hb, int hier, const cplx<double>* o
     LevA& V = H.lev[l];
     const LevA* W = l > 1 ? &H.lev[l - 1] : nullptr;
     ++c->launches;
-    mg::ada_down_kernel<D><<<grid_for(V.boxvol), kThreads, 0, c->stream>>>(
+    mg::ada_down_kernel<D><<<H.gcap[l], kThreads, 0, c->stream>>>(
         V.n, V.r, V.invd, V.vcls, V.succ, om, hb, hier, W ? W->corr : nullptr, W ? W->u : nullptr, V.corr, V.u,
-        V.box);
+        H.boxes + l);
     e = cudaGetLastError();
   }
   for (int l = Lf - 1; l >= 1 && e == cudaSuccess; --l) {
     LevA& V = H.lev[l];
     ++c->launches;
-    mg::ada_inject_unknown_kernel<D><<<grid_for(V.boxvol), kThreads, 0, c->stream>>>(V.n, H.lev[l + 1].vcls,
-                                                                                     H.lev[l + 1].u, V.u, V.box);
+    mg::ada_inject_unknown_kernel<D><<<H.gcap[l], kThreads, 0, c->stream>>>(V.n, H.lev[l + 1].vcls,
+                                                                           H.lev[l + 1].u, V.u, H.boxes + l);
     e = cudaGetLastError();
   }
   return e;
@@ -2237,7 +2252,10 @@ int ada_cycle(mg_ctx* c, int hb, int hier, const cplx<double>* omega) {
   };
   cudaError_t e = cudaSuccess;
   if (c->use_graphs && !c->timing) {
-    std::vector<double> key = {(double)hb, (double)hier, (double)H.version};
+    // the boxes live on the device: a captured cycle stays valid while the
+    // finest level and the grid capacities stay
+    std::vector<double> key = {(double)hb, (double)hier, (double)H.Lf};
+    for (int l = 1; l <= c->L; ++l) key.push_back((double)H.gcap[l]);
     for (int l = 0; l < c->L; ++l) {
       key.push_back(omega[l].x);
       key.push_back(omega[l].y);
@@ -2317,31 +2335,33 @@ cudaError_t ada_composite(mg_ctx* c, cplx<double>* out) {
 
 // One step of feature-based refinement (Section 5.3), all on the device:
 // indicator, span, histogram and bin choice, marks, new cell flags, vertex
-// classes with zero-surplus values, diagonals, succ and the injection; the
-// new bounding boxes and the counts come back in one synchronisation.  stats: vertices selected for refining and erasing, fine-grid
-// vertices after the step, finest level with cells.
+// classes with zero-surplus values, diagonals, succ, the new boxes and the
+// injection; the counts and boxes are copied to the page-locked mirror.
+// Every launch reads its box on the device, so the sequence replays as a
+// graph while the finest level and the grid capacities stay.
 template <int D>
-int ada_adapt(mg_ctx* c, double refine_frac, double erase_frac, int bins, double veto, int min_level,
-              long long* stats) {
+cudaError_t ada_enqueue_adapt(mg_ctx* c, double refine_frac, double erase_frac, int bins, double veto,
+                              int min_level) {
   HierA& H = *c->ada;
   const int L = c->L, Lf = H.Lf;
   cudaStream_t st = c->stream;
-  unsigned long long* hb = static_cast<unsigned long long*>(H.hbuf);
-  // 1. residuals (the veto), indicator, span, histogram
-  MG_CUDA(c, cudaMemsetAsync(H.abuf, 0, kAbSlots * sizeof(unsigned long long), st));
-  MG_CUDA(c, cudaMemsetAsync(H.abuf + kAbMinMax, 0xff, sizeof(unsigned long long), st));
-  MG_CUDA(c, ada_residuals<D>(c));
+  cudaError_t e;
+  // 1. residuals (the veto), indicator, span, histogram, bin choice
+  if ((e = cudaMemsetAsync(H.abuf, 0, kAbSlots * sizeof(unsigned long long), st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(H.abuf + kAbMinMax, 0xff, sizeof(unsigned long long), st)) != cudaSuccess) return e;
+  if ((e = ada_residuals<D>(c)) != cudaSuccess) return e;
   for (int l = 1; l <= Lf; ++l) {
     LevA& V = H.lev[l];
     ++c->launches;
-    mg::ada_indicator_kernel<D><<<grid_for(V.boxvol), kThreads, 0, st>>>(
-        V.n, V.u, V.vcls, l < Lf ? H.lev[l + 1].vcls : nullptr, V.s, V.box, H.abuf + kAbMinMax, H.abuf + kAbCount);
+    mg::ada_indicator_kernel<D><<<H.gcap[l], kThreads, 0, st>>>(V.n, V.u, V.vcls,
+                                                                l < Lf ? H.lev[l + 1].vcls : nullptr, V.s,
+                                                                H.boxes + l, H.abuf + kAbMinMax, H.abuf + kAbCount);
   }
   for (int l = 1; l <= Lf; ++l) {
     LevA& V = H.lev[l];
     ++c->launches;
-    mg::ada_hist_kernel<D><<<grid_for(V.boxvol), kThreads, 0, st>>>(V.n, V.s, V.box, H.abuf + kAbMinMax, bins,
-                                                                    H.abuf + kAbCounts);
+    mg::ada_hist_kernel<D><<<H.gcap[l], kThreads, 0, st>>>(V.n, V.s, H.boxes + l, H.abuf + kAbMinMax, bins,
+                                                           H.abuf + kAbCounts);
   }
   int* kb = reinterpret_cast<int*>(H.abuf + kAbBins);
   ++c->launches;
@@ -2351,9 +2371,9 @@ int ada_adapt(mg_ctx* c, double refine_frac, double erase_frac, int bins, double
   for (int l = 1; l <= Lf; ++l) {
     LevA& V = H.lev[l];
     ++c->launches;
-    mg::ada_mark_kernel<D><<<grid_for(V.boxvol), kThreads, 0, st>>>(
-        V.n, V.s, V.r, V.invd, V.box, H.abuf + kAbMinMax, bins, kb, veto, l < L ? 1 : 0,
-        l >= min_level + 1 ? 1 : 0, V.rmark, V.emark, H.abuf + kAbSel);
+    mg::ada_mark_kernel<D><<<H.gcap[l], kThreads, 0, st>>>(V.n, V.s, V.r, V.invd, H.boxes + l, H.abuf + kAbMinMax,
+                                                           bins, kb, veto, l < L ? 1 : 0, l >= min_level + 1 ? 1 : 0,
+                                                           V.rmark, V.emark, H.abuf + kAbSel);
   }
   // 3. new refine bits fine to coarse, then existence coarse to fine
   for (int l = std::min(Lf, L - 1); l >= 1; --l) {
@@ -2372,45 +2392,98 @@ int ada_adapt(mg_ctx* c, double refine_frac, double erase_frac, int bins, double
         V.n, V.cellf, l > 1 ? H.lev[l - 1].cellf : nullptr, V.rmark);
   }
   // 4. vertex classes and zero-surplus values coarse to fine, boxes
-  std::vector<int> b0(6 * (L + 1));
-  for (int l = 0; l <= L; ++l)
-    for (int a = 0; a < 3; ++a) {
-      b0[6 * l + a] = 1 << 30;
-      b0[6 * l + 3 + a] = -1;
-    }
-  std::memcpy(static_cast<char*>(H.hbuf) + 2048, b0.data(), b0.size() * sizeof(int));
-  MG_CUDA(c, cudaMemcpyAsync(H.box6, static_cast<char*>(H.hbuf) + 2048, b0.size() * sizeof(int),
-                             cudaMemcpyHostToDevice, st));
+  ++c->launches;
+  mg::ada_box_init_kernel<<<1, 128, 0, st>>>(H.box6, L + 1);
   for (int l = 1; l <= Lt; ++l) {
     LevA& V = H.lev[l];
-    ++c->launches;
+    c->launches += 2;
     mg::ada_reclass_kernel<D><<<grid_for(V.nv), kThreads, 0, st>>>(
         V.n, V.cellf, V.vcls, V.u, l > 1 ? H.lev[l - 1].u : nullptr, H.box6 + 6 * l, V.emark, V.r);
-    ++c->launches;
     mg::ada_diag_kernel<D><<<grid_for(V.nv), kThreads, 0, st>>>(V.n, V.vcls, V.hcell, V.hinv, V.phic, c->k2[0],
                                                                 V.invd);
   }
-  MG_CUDA(c, cudaGetLastError());
-  MG_CUDA(c, ada_succ_all<D>(c, H.abuf + kAbFine));
-  // 5. coarse copies of finer unknowns (fine to coarse), stale residuals
+  ++c->launches;
+  mg::ada_boxes_kernel<D><<<1, 32, 0, st>>>(H.box6, L, H.boxes);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = ada_succ_all<D>(c, H.abuf + kAbFine)) != cudaSuccess) return e;
+  // 5. coarse copies of finer unknowns (fine to coarse) over the new boxes
   for (int l = Lt - 1; l >= 1; --l) {
     LevA& V = H.lev[l];
-    mg::AdaBox full{};
-    for (int a = 0; a < 3; ++a) full.ext[a] = a < D ? V.n + 1 : 1;
     ++c->launches;
     mg::ada_inject_unknown_kernel<D><<<grid_for(V.nv), kThreads, 0, st>>>(V.n, H.lev[l + 1].vcls,
-                                                                          H.lev[l + 1].u, V.u, full);
+                                                                          H.lev[l + 1].u, V.u, H.boxes + l);
   }
-  MG_CUDA(c, cudaGetLastError());
-  MG_CUDA(c, cudaMemcpyAsync(hb, H.abuf, kAbSlots * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
-  MG_CUDA(c, cudaMemcpyAsync(static_cast<char*>(H.hbuf) + 2048, H.box6, b0.size() * sizeof(int),
-                             cudaMemcpyDeviceToHost, st));
-  MG_CUDA(c, cudaStreamSynchronize(st));
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(H.hbuf, H.abuf, kAbSlots * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st)) !=
+      cudaSuccess)
+    return e;
+  return cudaMemcpyAsync(static_cast<char*>(H.hbuf) + 2048, H.box6, 6 * (L + 1) * sizeof(int),
+                         cudaMemcpyDeviceToHost, st);
+}
+
+// Runs one step (directly the first time, then as a graph while the same
+// step repeats on the same finest level and capacities), synchronises, and
+// takes the new boxes: finest level, grid capacities (grown when a box
+// outgrows its grid).  stats: vertices selected for refining and erasing,
+// fine-grid vertices after the step, finest level with cells.
+template <int D>
+int ada_adapt(mg_ctx* c, double refine_frac, double erase_frac, int bins, double veto, int min_level,
+              long long* stats) {
+  HierA& H = *c->ada;
+  const int L = c->L;
+  auto enqueue = [&]() { return ada_enqueue_adapt<D>(c, refine_frac, erase_frac, bins, veto, min_level); };
+  std::vector<double> key = {refine_frac, erase_frac, (double)bins, veto, (double)min_level, (double)H.Lf};
+  for (int l = 1; l <= L; ++l) key.push_back((double)H.gcap[l]);
+  bool launched = false;
+  if (c->use_graphs) {
+    const bool fresh = H.aexec == nullptr || H.akey != key;
+    if (fresh && H.aseen != key) {
+      H.aseen = key;  // first time: run directly
+    } else if (fresh) {
+      cudaStream_t user = c->stream;
+      c->stream = c->cap_stream;
+      const long long before = c->launches;
+      cudaGraph_t g = nullptr;
+      cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+      cudaError_t ek = e == cudaSuccess ? enqueue() : e;
+      cudaError_t ee = e == cudaSuccess ? cudaStreamEndCapture(c->cap_stream, &g) : e;
+      c->stream = user;
+      const long long nk = c->launches - before;
+      c->launches = before;
+      e = ek != cudaSuccess ? ek : ee;
+      if (e == cudaSuccess) {
+        cudaGraphExecUpdateResultInfo info;
+        if (H.aexec == nullptr || cudaGraphExecUpdate(H.aexec, g, &info) != cudaSuccess) {
+          cudaGetLastError();
+          if (H.aexec) cudaGraphExecDestroy(H.aexec);
+          H.aexec = nullptr;
+          e = cudaGraphInstantiate(&H.aexec, g, 0);
+        }
+      }
+      if (g) cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (H.aexec) cudaGraphExecDestroy(H.aexec);
+        H.aexec = nullptr;
+      } else {
+        H.akey = key;
+        H.ankern = nk;
+      }
+    }
+    if (H.aexec != nullptr && H.akey == key) {
+      MG_CUDA(c, cudaGraphLaunch(H.aexec, c->stream));
+      c->launches += H.ankern;
+      launched = true;
+    }
+  }
+  if (!launched) MG_CUDA(c, enqueue());
+  MG_CUDA(c, cudaStreamSynchronize(c->stream));
+  const unsigned long long* hb = static_cast<const unsigned long long*>(H.hbuf);
   const int* bx = reinterpret_cast<const int*>(static_cast<const char*>(H.hbuf) + 2048);
   H.Lf = 1;
   for (int l = 1; l <= L; ++l) {
     LevA& V = H.lev[l];
-    const bool empty = l > Lt || bx[6 * l + 3] < 0;
+    const bool empty = bx[6 * l + 3] < 0;
     V.boxvol = 1;
     for (int a = 0; a < 3; ++a) {
       V.box.lo[a] = a < D && !empty ? bx[6 * l + a] : 0;
@@ -2418,6 +2491,8 @@ int ada_adapt(mg_ctx* c, double refine_frac, double erase_frac, int bins, double
       V.boxvol *= (size_t)V.box.ext[a];
     }
     if (!empty) H.Lf = l;
+    const int need = grid_for(V.boxvol);
+    if (need > H.gcap[l]) H.gcap[l] = std::min(152 * 16, std::max(need, 2 * H.gcap[l]));
   }
   ++H.version;
   double hi;
