@@ -20,6 +20,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import itertools
 import json
 import math
 import os
@@ -391,12 +392,17 @@ def measure_forms(mg, torch, peaks):
     Jv, dt = wall(fwd_bwd)
     out["adjoint_2d_depth6"] = {"J": Jv, "seconds_forward_backward": dt, "tol": 1e-10}
     s.close()
-    out["csg_sweep"] = csg_sweep(mg, torch)
-    out["channel_table2"] = channel_table2(mg, torch)
-    out["four_d"] = four_d(mg, torch, peaks)
-    out["dimension_study"] = dimension_study(mg, torch)
-    out["adaptive"] = adaptive(mg, torch)
-    out["channel_table2_adaptive"] = channel_table2_adaptive(mg, torch)
+    for name, fn in [("csg_sweep", lambda: csg_sweep(mg, torch)),
+                     ("channel_table2", lambda: channel_table2(mg, torch)),
+                     ("four_d", lambda: four_d(mg, torch, peaks)),
+                     ("dimension_study", lambda: dimension_study(mg, torch)),
+                     ("adaptive", lambda: adaptive(mg, torch)),
+                     ("adaptive_3d", lambda: adaptive(mg, torch, d=3, depth=5, cycles=30)),
+                     ("channel_table2_adaptive", lambda: channel_table2_adaptive(mg, torch))]:
+        try:
+            out[name] = fn()
+        except Exception as e:  # a failing secondary form must not cost the headline line
+            out[name] = {"error": f"{type(e).__name__}: {e}"}
     return out
 
 
@@ -653,21 +659,25 @@ def dimension_study(mg, torch, cycles=300):
     return {"cycles_max": cycles, "variant": "add, d-linear", "seconds": time.perf_counter() - t0, "runs": rows}
 
 
-def adaptive(mg, torch, depth=6, cycles=100):
+def adaptive(mg, torch, d=2, depth=6, cycles=100):
     """Adaptive spacetree against the regular grid of the same finest depth
-    (2D depth 6, h_min = 1/729): a definite problem (k^2 = -(15 pi)^2, no
-    layer) with the localised source chi of Eq. 08-gaussian at the origin;
-    the adaptive grid refines level-l cells whose centre lies within
-    0.7 * 0.7^(l-1) of the origin (2.5% of the regular unknowns).  BPX with
-    undamped factors 0.6.  Per grid: fine-grid unknowns, device time per
-    cycle (CUDA events around `cycles` cycles), cycles and seconds to 1e-8,
-    and the adaptive solution's largest deviation from the regular one at
-    the vertices of the finest adaptive level."""
-    d = 2
+    (2D depth 6, h_min = 1/729; 3D depth 5, h_min = 1/243): a definite
+    problem (k^2 = -(15 pi)^2, no layer) with the localised source
+    exp(-sum (125 x_a)^2) of Eq. 08-gaussian at the origin; the adaptive grid
+    refines level-l cells whose centre lies within 0.7 * 0.7^(l-1) of the
+    origin (2D: 2.5% of the regular unknowns).  BPX with undamped factors
+    0.6.  Per grid: fine-grid unknowns, device time per cycle (CUDA events
+    around `cycles` cycles), cycles and seconds to 1e-8, and the adaptive
+    solution's largest deviation from the regular one at the vertices of
+    the finest adaptive level."""
     n = 3 ** depth
     x = np.arange(n + 1) / n
-    X, Y = np.meshgrid(x, x)
-    f = np.exp(-(125.0 * X) ** 2 - (125.0 * Y) ** 2).astype(np.complex128)
+    r2 = np.zeros((n + 1,) * d)
+    for ax in range(d):
+        shape = [1] * d
+        shape[ax] = n + 1
+        r2 = r2 + (125.0 * x.reshape(shape)) ** 2
+    f = np.exp(-r2).astype(np.complex128)
     k2 = W.constant_k2(d, depth, -(15 * math.pi) ** 2)
     ref = W.source_refinement(d, depth)
     om = mg.omega_scheme(mg.MG_OMEGA_UCG, 0.6, depth)
@@ -698,24 +708,25 @@ def adaptive(mg, torch, depth=6, cycles=100):
                      "seconds_to_1e-8": sec}
         s.close()
     # grid structure from the flags: cells of level l + 1 are the children of
-    # refined level-l cells; a vertex carries an unknown when its 4 cells exist
-    cells = np.ones((3, 3), dtype=bool)
+    # refined level-l cells; a vertex carries an unknown when its 2^d cells exist
+    cells = np.ones((3,) * d, dtype=bool)
     unknown, exists = {}, {}
     for lev in range(1, depth + 1):
         m = 3 ** lev
-        cnt = np.zeros((m + 1, m + 1), dtype=int)
-        for oy in (0, 1):
-            for ox in (0, 1):
-                cnt[oy:oy + m, ox:ox + m] += cells
+        cnt = np.zeros((m + 1,) * d, dtype=int)
+        for corner in itertools.product((0, 1), repeat=d):
+            cnt[tuple(slice(o, o + m) for o in corner)] += cells
         inner = np.zeros_like(cnt, dtype=bool)
-        inner[1:-1, 1:-1] = True
-        unknown[lev], exists[lev] = inner & (cnt == 4), cnt > 0
+        inner[(slice(1, -1),) * d] = True
+        unknown[lev], exists[lev] = inner & (cnt == 2 ** d), cnt > 0
         if lev < depth:
-            cells = np.repeat(np.repeat(cells & ref[lev], 3, axis=0), 3, axis=1)
-    own = sum(int((unknown[lev] & ~unknown[lev + 1][::3, ::3]).sum()) for lev in range(1, depth))
+            cells = cells & ref[lev]
+            for ax in range(d):
+                cells = np.repeat(cells, 3, axis=ax)
+    own = sum(int((unknown[lev] & ~unknown[lev + 1][(slice(None, None, 3),) * d]).sum()) for lev in range(1, depth))
     own += int(unknown[depth].sum())
     out["adaptive"]["fine_unknowns"] = own
-    out["regular"]["fine_unknowns"] = (n - 1) ** 2
+    out["regular"]["fine_unknowns"] = (n - 1) ** d
     for name in out:
         out[name]["dof_updates_per_s"] = out[name]["fine_unknowns"] / (out[name]["ms_per_cycle"] / 1e3)
     m = exists[depth]
@@ -735,7 +746,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--form", choices=["csg_sweep", "channel_table2", "four_d", "dimension_study", "adaptive",
-                                       "channel_table2_adaptive"],
+                                       "adaptive_3d", "channel_table2_adaptive"],
                     default=None,
                     help="run only this form and print its result (profiling)")
     ap.add_argument("--four-d-depth", type=int, default=4, help="depth of the four_d form (profiling)")
@@ -768,6 +779,7 @@ def main():
               "four_d": lambda m, t: four_d(m, t, peaks, depth=args.four_d_depth),
               "dimension_study": lambda m, t: dimension_study(m, t),
               "adaptive": lambda m, t: adaptive(m, t),
+              "adaptive_3d": lambda m, t: adaptive(m, t, d=3, depth=5, cycles=30),
               "channel_table2_adaptive": lambda m, t: channel_table2_adaptive(m, t)}[args.form]
         print(json.dumps({"form": args.form, "result": fn(mg, torch)}), flush=True)
         return
@@ -876,7 +888,10 @@ def main():
                             "mg_get_solution to pinned host"},
             "gpu_launches": launches, "clocks": clk}
     if rank == 0 and world == 1 and not args.no_forms:
-        line["forms"] = measure_forms(mg, torch, peaks)
+        try:
+            line["forms"] = measure_forms(mg, torch, peaks)
+        except Exception as e:  # the headline line is printed regardless
+            line["forms"] = {"error": f"{type(e).__name__}: {e}"}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_line(cfg)
     if rank == 0:
