@@ -3,7 +3,9 @@
  * Solves a definite 2D problem (k^2 = -30, Gaussian source, a layer of width
  * 1/3) to a relative residual of 1e-10 with BPX (undamped factors 0.6;
  * the oracle needs 80 cycles on this problem), runs one BPX cycle of a 3D problem from a
- * page-locked host buffer, and checks the argument validation of mg_create.
+ * page-locked host buffer, refines an adaptive 2D grid dynamically (cycles and
+ * refinement steps from the regular level-2 grid), and checks the argument
+ * validation of mg_create and mg_adapt.
  * Exit status 0 on success. */
 #include <math.h>
 #include <stdio.h>
@@ -73,5 +75,45 @@ int main(void) {
   mg_destroy(c3);
   cudaFreeHost(u);
   free(k3);
-  return finite ? 0 : 1;
+  if (!finite) return 1;
+
+  /* adaptive 2D grid, depth 4: level 1 refined, the rest grows by feature-based refinement */
+  const int da = 4, na = 81, Na = na + 1;
+  const size_t nva = (size_t)Na * Na;
+  double* ka = (double*)malloc(nva * sizeof(double));
+  mg_c128* fa = (mg_c128*)malloc(nva * sizeof(mg_c128));
+  for (int j = 0; j < Na; ++j)
+    for (int i = 0; i < Na; ++i) {
+      const double x = (double)i / na - 0.3, y = (double)j / na - 0.6;
+      ka[(size_t)j * Na + i] = 25.0;
+      fa[(size_t)j * Na + i].re = exp(-(x * x + y * y) / (2.0 * 0.05 * 0.05));
+      fa[(size_t)j * Na + i].im = 0.0;
+    }
+  const size_t nflags = 9 + 81 + 729; /* levels 1..3 */
+  unsigned char* refine = (unsigned char*)calloc(nflags, 1);
+  for (int k = 0; k < 9; ++k) refine[k] = 1;
+  mg_ctx* ca = NULL;
+  if (check(mg_create_adaptive(2, da, ka, 0.5235987755982988, 0.0, 0.2, 0.2, refine, &ca), "mg_create_adaptive",
+            NULL))
+    return 1;
+  if (check(mg_set_rhs(ca, fa, 0), "mg_set_rhs adaptive", ca)) return 1;
+  const mg_c128 oma[4] = {{0.6, 0.0}, {0.6, 0.0}, {0.6, 0.0}, {0.6, 0.0}};
+  long long st[4] = {0, 0, 0, 0};
+  for (int it = 0; it < 5; ++it) {
+    if (check(mg_cycle(ca, MG_BPX, oma, MG_HIERARCHICAL), "mg_cycle adaptive", ca)) return 1;
+    if (check(mg_adapt(ca, 0.1, 0.02, 20, 1e-2, 2, st), "mg_adapt", ca)) return 1;
+  }
+  if (check(mg_get_refinement(ca, refine), "mg_get_refinement", ca)) return 1;
+  int refined2 = 0;
+  for (int k = 9; k < 90; ++k) refined2 += refine[k];
+  double rmax = 0.0;
+  if (check(mg_residual_max(ca, &rmax), "mg_residual_max adaptive", ca)) return 1;
+  printf("adaptive depth %d: 5 steps, %lld fine-grid vertices, finest level %lld, %d refined level-2 cells, "
+         "max |r| %.3e\n", da, st[2], st[3], refined2, rmax);
+  if (mg_adapt(ca, 0.1, 0.02, 0, 1e-2, 2, st) != MG_ERR_INVALID) return 1; /* bins out of range */
+  mg_destroy(ca);
+  free(refine);
+  free(fa);
+  free(ka);
+  return (refined2 > 0 && st[2] > 49 && isfinite(rmax)) ? 0 : 1;
 }
