@@ -427,3 +427,49 @@ def test_vetoes():
         old = ada.refine_flags()
         ada.adapt(min_level=1, refine_frac=0.1, erase_frac=0.02, veto=veto)
         assert (ada.refine_flags() != old).any() == changes
+
+
+def bump3(x, y, z):
+    return x + 0.5 * y + 0.25 * z + 10.0 * np.exp(-((x - 0.8) ** 2 + (y - 0.75) ** 2 + (z - 0.7) ** 2) / 0.004)
+
+
+def test_refining_and_erasing_in_three_dimensions():
+    """The 3D counterparts of the two tests above (children, closures and
+    corners over 3 axes): pure refinement refines exactly the cells around
+    the hand-selected vertices and keeps the fine-grid function; erasing the
+    bottom bins coarsens the refined patch where u is linear and keeps the
+    one at the bump."""
+    d, depth = 3, 3
+    n = 3 ** depth
+    ref = {1: np.ones((3, 3, 3), dtype=bool), 2: np.zeros((9, 9, 9), dtype=bool)}
+    ref[2][1:3, 1:3, 1:3] = True  # flat patch (u linear there)
+    ref[2][5:8, 6:8, 6:8] = True  # at the bump (z, y, x order: x = last axis)
+    k2 = np.full((n + 1,) * d, -10.0)
+    # pure refinement
+    ada = AdaptiveHierarchy(d, depth, k2, 0.0, 0.0, ref)
+    set_levels_from(ada, bump3)
+    before = ada.composite_on_fine()
+    sel, _ = selection_by_hand(ada, 2, 0.1, 0.0, 20)
+    old = {lev: ada.refined[lev].copy() for lev in range(1, depth)}
+    n_ref, n_er, _ = ada.adapt(min_level=2, refine_frac=0.1, erase_frac=0.0, veto=np.inf)
+    assert n_er == 0 and n_ref == sum(1 for lev, _ in sel if lev < depth) > 0
+    expect = {lev: old[lev].copy() for lev in old}
+    for lev, v in sel:
+        if lev == depth:
+            continue
+        for e in itertools.product((0, 1), repeat=d):
+            expect[lev][tuple(v[a] - 1 + e[a] for a in range(d))] = True
+    for lev in range(1, depth):
+        np.testing.assert_array_equal(ada.refined[lev], expect[lev] & ada.cells[lev])
+    np.testing.assert_allclose(ada.composite_on_fine(), before, rtol=0, atol=1e-14 * np.abs(before).max())
+    # erasing
+    ada = AdaptiveHierarchy(d, depth, k2, 0.0, 0.0, ref)
+    set_levels_from(ada, bump3)
+    _, er = selection_by_hand(ada, 2, 0.0, 0.5, 20)
+    assert er
+    before = ada.composite_on_fine()
+    ada.adapt(min_level=2, refine_frac=0.0, erase_frac=0.5, veto=np.inf)
+    assert not ada.refined[2][1:3, 1:3, 1:3].any()
+    assert ada.refined[2][5:8, 6:8, 6:8].all()
+    sl = (slice(3, 10), slice(3, 10), slice(3, 10))
+    np.testing.assert_allclose(ada.composite_on_fine()[sl], before[sl], rtol=0, atol=1e-13)
