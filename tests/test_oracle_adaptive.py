@@ -242,7 +242,10 @@ def generating_system_cycle(ada, omega, transfer, f_fine, k2):
     and shift, so every level's diagonal is that of the prolongated basis
     function): du_(l,v) = omega[L-1-succ(v)] (G^T (b - H u))_(l,v) / (G^T H G)
     diagonal, T_l on each level's vector, and the prolongated sum added to
-    the fine-grid function u.  succ comes from its definition."""
+    the fine-grid function u.  succ comes from its definition.  With a
+    constant shift and no scaling the operator is translation invariant, so
+    the diagonal is formed once per level (from the level's first unknown;
+    every unknown's hat lies inside the domain)."""
     d, L = ada.d, ada.L
     n = 3 ** L
     lev_L = O.Level(d, L, np.full((n + 1,) * d, k2), 0.0, 0.0)
@@ -252,13 +255,15 @@ def generating_system_cycle(ada, omega, transfer, f_fine, k2):
     corr = np.zeros_like(u)
     for lev in range(1, L + 1):
         t = np.zeros((3 ** lev + 1,) * d, dtype=np.complex128)
+        a = None
         for v, s in succ[lev].items():
             e = np.zeros_like(t)
             e[v] = 1.0
             for _ in range(L - lev):
                 e = O.prolong(e)
             g = np.vdot(e, res)  # e is real: e^T res
-            a = np.vdot(e, lev_L.apply(e))
+            if a is None:
+                a = np.vdot(e, lev_L.apply(e))
             t[v] = omega[L - 1 - s] * g / a
         if transfer == O.HIERARCHICAL:
             t = t - O.prolong(O.inject(t))
@@ -288,6 +293,25 @@ def test_cycle_is_the_generating_system_correction_with_succ_factors(transfer):
         ada.cycle(om, O.ADD, transfer)
     want = generating_system_cycle(ada, om, transfer, f, k2)
     ada.cycle(om, O.ADD, transfer)
+    got = ada.composite_on_fine()
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-12 * np.abs(want).max())
+
+
+def test_cycle_is_the_generating_system_correction_in_3d():
+    """The same dense check in three dimensions (depth 3, three refined
+    level-1 cells and a level-2 block: hanging vertices on two levels),
+    BPX transfer and distinct factors per succ."""
+    d, depth, k2 = 3, 3, -15.0
+    n = 3 ** depth
+    x = np.arange(n + 1) / n
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    f = (1.0 + X + 2.0 * Y - Z + 3.0 * X * Y * Z).astype(np.complex128)  # trilinear
+    ada = AdaptiveHierarchy(d, depth, np.full((n + 1,) * d, k2), 0.0, 0.0, corner_refinement_3d(depth))
+    ada.set_rhs_nodal(f)
+    om = np.array([0.35, 0.5 - 0.05j, 0.65])
+    ada.cycle(om, O.ADD, O.HIERARCHICAL)
+    want = generating_system_cycle(ada, om, O.HIERARCHICAL, f, k2)
+    ada.cycle(om, O.ADD, O.HIERARCHICAL)
     got = ada.composite_on_fine()
     np.testing.assert_allclose(got, want, rtol=0, atol=1e-12 * np.abs(want).max())
 
