@@ -172,8 +172,11 @@ int mg_create_adaptive(int d, int depth, const double* k2_field, double theta_la
  *  stats                     host long long[4] or NULL: vertices selected for
  *                            refining, for erasing, fine-grid vertices after
  *                            the step, finest level holding cells.
- * Synchronises the stream twice (bin counts, new bounding boxes); the next
- * mg_cycle captures a new graph.
+ * Synchronises the stream once (counts and new bounding boxes); the step and
+ * the cycles run as CUDA graphs again once they repeat on the same finest
+ * level and grid capacities.  The reference residual of mg_solve and
+ * mg_residual_norm (the first one after mg_set_rhs or mg_set_solution) is
+ * kept across steps, so relative residuals compare with the start grid.
  * Errors: MG_ERR_INVALID (not adaptive, arguments out of range),
  * MG_DIVERGED (a non-finite indicator: the grid is left as it is),
  * MG_ERR_CUDA. */
