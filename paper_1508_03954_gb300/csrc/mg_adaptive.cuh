@@ -85,6 +85,58 @@ __device__ __forceinline__ void ada_coords(unsigned i, int N, int* g) {
   }
 }
 
+// Regions of a level that a refinement step can change, from bounding
+// boxes of vertices (null: the level's whole grid).  Iterated like boxes,
+// with box_vertex over n cells or n + 1 vertices per axis.
+template <int D>
+__device__ __forceinline__ AdaBox region_full(int m) {
+  AdaBox R;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    R.lo[a] = 0;
+    R.ext[a] = a < D ? m : 1;
+  }
+  return R;
+}
+// the cells among the vertices of vb
+template <int D>
+__device__ __forceinline__ AdaBox cell_region(const AdaBox* vb, int n) {
+  if (vb == nullptr) return region_full<D>(n);
+  AdaBox R = *vb;
+#pragma unroll
+  for (int a = 0; a < D; ++a) R.ext[a] = R.ext[a] > 0 ? R.ext[a] - 1 : 0;
+  return R;
+}
+// the children of the cells among the vertices of pvb (next coarser level)
+template <int D>
+__device__ __forceinline__ AdaBox child_cell_region(const AdaBox* pvb, int n) {
+  if (pvb == nullptr) return region_full<D>(n);
+  AdaBox R = *pvb;
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    R.lo[a] *= 3;
+    R.ext[a] = R.ext[a] > 0 ? 3 * (R.ext[a] - 1) : 0;
+  }
+  return R;
+}
+// the vertices of those children
+template <int D>
+__device__ __forceinline__ AdaBox child_vertex_region(const AdaBox* pvb, int n) {
+  if (pvb == nullptr) return region_full<D>(n + 1);
+  AdaBox R = *pvb;
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    R.lo[a] *= 3;
+    R.ext[a] = R.ext[a] > 0 ? 3 * (R.ext[a] - 1) + 1 : 0;
+  }
+  return R;
+}
+// the vertices of vb itself
+template <int D>
+__device__ __forceinline__ AdaBox vertex_region(const AdaBox* vb, int n) {
+  return vb == nullptr ? region_full<D>(n + 1) : *vb;
+}
+
 // Entry [a][b] of the element matrices of a cell with per-axis widths h and
 // inverse widths hi (corner bits a, b): M = prod h/6 (2 or 1), K = sum_j of
 // the same product with axis j's factor replaced by (+1 or -1)/h.
@@ -234,15 +286,15 @@ __global__ void __launch_bounds__(256) ada_residual_kernel(
 template <int D>
 __global__ void ada_diag_kernel(int n, const uint8_t* __restrict__ vcls, const cplx<double>* __restrict__ hcell,
                                 const cplx<double>* __restrict__ hinv, const double* __restrict__ phic,
-                                double phi0, cplx<double>* __restrict__ invd) {
+                                double phi0, cplx<double>* __restrict__ invd, const AdaBox* vb) {
   const int N = n + 1;
-  unsigned total = 1;
-  for (int a = 0; a < D; ++a) total *= (unsigned)N;
-  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+  const AdaBox R = vertex_region<D>(vb, n);
+  const unsigned total = box_volume<D>(R);
+  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+    int g[3];
+    const unsigned i = box_vertex<D>(t, R, N, g);
     cplx<double> v = cz<double>();
     if (vcls[i] == kVertUnknown) {
-      int g[3];
-      ada_coords<D>(i, N, g);
       cplx<double> dg = cz<double>();
 #pragma unroll
       for (int e = 0; e < (1 << D); ++e) {
@@ -645,14 +697,14 @@ template <int D>
 __global__ void ada_coarsen_kernel(int n, uint8_t* __restrict__ cellf, const uint8_t* __restrict__ rmark,
                                    const uint8_t* __restrict__ cellf_f, const uint8_t* __restrict__ rmark_f,
                                    const uint8_t* __restrict__ vcls_f, const uint8_t* __restrict__ vcls_ff,
-                                   const uint8_t* __restrict__ emark_f, int allow) {
-  unsigned total = 1;
-  for (int a = 0; a < D; ++a) total *= (unsigned)n;
+                                   const uint8_t* __restrict__ emark_f, int allow, const AdaBox* vb) {
+  const AdaBox R = cell_region<D>(vb, n);  // cells that exist or carry marks lie among the old box's vertices
+  const unsigned total = box_volume<D>(R);
   const int nf = 3 * n, Nf = nf + 1, Nff = 3 * nf + 1;
-  for (unsigned ci = blockIdx.x * blockDim.x + threadIdx.x; ci < total; ci += gridDim.x * blockDim.x) {
-    const uint8_t old = cellf[ci] & (kCellExists | kCellRefined);
+  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
     int c[3];
-    ada_coords<D>(ci, n, c);
+    const unsigned ci = box_vertex<D>(t, R, n, c);
+    const uint8_t old = cellf[ci] & (kCellExists | kCellRefined);
     bool coarsen = false;
     if (allow && (old & kCellRefined)) {
       coarsen = true;
@@ -691,15 +743,17 @@ __global__ void ada_coarsen_kernel(int n, uint8_t* __restrict__ cellf, const uin
 // kCellNewRef.  Clears the level's refine marks.
 template <int D>
 __global__ void ada_finalize_cells_kernel(int n, uint8_t* __restrict__ cellf, const uint8_t* __restrict__ cellf_p,
-                                          uint8_t* __restrict__ rmark) {
-  unsigned total = 1;
-  for (int a = 0; a < D; ++a) total *= (unsigned)n;
+                                          uint8_t* __restrict__ rmark, const AdaBox* pvb) {
+  // the level's cells before and after the step are children of cells that
+  // existed on the next coarser level (old box pvb; null on level 1)
+  const AdaBox R = child_cell_region<D>(pvb, n);
+  const unsigned total = box_volume<D>(R);
   const int np = n / 3;
-  for (unsigned ci = blockIdx.x * blockDim.x + threadIdx.x; ci < total; ci += gridDim.x * blockDim.x) {
+  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+    int c[3];
+    const unsigned ci = box_vertex<D>(t, R, n, c);
     bool ex = true;
     if (cellf_p != nullptr) {
-      int c[3];
-      ada_coords<D>(ci, n, c);
       unsigned pi = 0, ps = 1;
 #pragma unroll
       for (int a = 0; a < D; ++a) {
@@ -724,17 +778,20 @@ __global__ void ada_finalize_cells_kernel(int n, uint8_t* __restrict__ cellf, co
 template <int D>
 __global__ void ada_reclass_kernel(int n, const uint8_t* __restrict__ cellf, uint8_t* __restrict__ vcls,
                                    cplx<double>* __restrict__ u, const cplx<double>* __restrict__ u_c, int* box6,
-                                   uint8_t* __restrict__ emark, cplx<double>* __restrict__ r) {
+                                   uint8_t* __restrict__ emark, cplx<double>* __restrict__ r, const AdaBox* pvb) {
+  // vertices of the level's cells before and after the step: those of the
+  // children of the cells that existed on the next coarser level (old box
+  // pvb; null on level 1)
+  const AdaBox R = child_vertex_region<D>(pvb, n);
   const int N = n + 1, Nc = n / 3 + 1;
-  unsigned total = 1;
-  for (int a = 0; a < D; ++a) total *= (unsigned)N;
+  const unsigned total = box_volume<D>(R);
   const double inv = D == 2 ? 1.0 / 9.0 : 1.0 / 27.0;
   int lo[3] = {N, N, N}, hi[3] = {-1, -1, -1};
   for (unsigned t0 = blockIdx.x * blockDim.x; t0 < total; t0 += gridDim.x * blockDim.x) {
-    const unsigned i = t0 + threadIdx.x;
-    if (i < total) {
+    const unsigned t = t0 + threadIdx.x;
+    if (t < total) {
       int g[3];
-      ada_coords<D>(i, N, g);
+      const unsigned i = box_vertex<D>(t, R, N, g);
       int cnt = 0;
       bool inner = true;
 #pragma unroll
@@ -831,18 +888,18 @@ __global__ void ada_boxes_kernel(const int* __restrict__ box6, int L, AdaBox* __
 template <int D>
 __global__ void ada_succ_kernel(int n, const uint8_t* __restrict__ cellf, const uint8_t* __restrict__ vcls,
                                 const uint8_t* __restrict__ vcls_f, const uint8_t* __restrict__ succ_f,
-                                uint8_t* __restrict__ succ, unsigned long long* nfine) {
+                                uint8_t* __restrict__ succ, unsigned long long* nfine, const AdaBox* vb) {
   const int N = n + 1, Nf = 3 * n + 1;
-  unsigned total = 1;
-  for (int a = 0; a < D; ++a) total *= (unsigned)N;
+  const AdaBox R = vertex_region<D>(vb, n);  // the unknowns lie in the level's (new) box
+  const unsigned total = box_volume<D>(R);
   unsigned mine = 0;
   for (unsigned t0 = blockIdx.x * blockDim.x; t0 < total; t0 += gridDim.x * blockDim.x) {
-    const unsigned i = t0 + threadIdx.x;
-    if (i < total) {
+    const unsigned t = t0 + threadIdx.x;
+    if (t < total) {
+      int g[3];
+      const unsigned i = box_vertex<D>(t, R, N, g);
       uint8_t sv = 0;
       if (vcls[i] == kVertUnknown) {
-        int g[3];
-        ada_coords<D>(i, N, g);
         if (ada_fine_grid<D>(vcls, vcls_f, i, g, Nf)) ++mine;
         bool refined = succ_f != nullptr;
 #pragma unroll

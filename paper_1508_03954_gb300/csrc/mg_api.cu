@@ -1956,7 +1956,7 @@ cudaError_t ada_succ_all(mg_ctx* c, unsigned long long* nfine) {
     ++c->launches;
     mg::ada_succ_kernel<D><<<grid_for(V.nv), kThreads, 0, c->stream>>>(
         V.n, V.cellf, V.vcls, F ? F->vcls : nullptr, F ? F->succ : nullptr, V.succ,
-        nfine != nullptr ? nfine : H.abuf + kAbFine);
+        nfine != nullptr ? nfine : H.abuf + kAbFine, H.boxes + l);
   }
   return cudaGetLastError();
 }
@@ -2107,9 +2107,11 @@ int ada_build(mg_ctx* c, const unsigned char* refine) {
       if ((rc = d4_upload(c, *H, &V.phic, ph)) != MG_OK) return rc;
     }
     if (d == 2)
-      mg::ada_diag_kernel<2><<<grid_for(V.nv), kThreads>>>(n, V.vcls, V.hcell, V.hinv, V.phic, c->k2[0], V.invd);
+      mg::ada_diag_kernel<2><<<grid_for(V.nv), kThreads>>>(n, V.vcls, V.hcell, V.hinv, V.phic, c->k2[0], V.invd,
+                                                           nullptr);
     else
-      mg::ada_diag_kernel<3><<<grid_for(V.nv), kThreads>>>(n, V.vcls, V.hcell, V.hinv, V.phic, c->k2[0], V.invd);
+      mg::ada_diag_kernel<3><<<grid_for(V.nv), kThreads>>>(n, V.vcls, V.hcell, V.hinv, V.phic, c->k2[0], V.invd,
+                                                           nullptr);
     MG_CUDA(c, cudaGetLastError());
     MG_CUDA(c, cudaDeviceSynchronize());
     // children of refined cells exist on the next level
@@ -2382,28 +2384,34 @@ cudaError_t ada_enqueue_adapt(mg_ctx* c, double refine_frac, double erase_frac, 
     ++c->launches;
     mg::ada_coarsen_kernel<D><<<grid_for((size_t)ipow(V.n, D)), kThreads, 0, st>>>(
         V.n, V.cellf, V.rmark, F.cellf, l + 1 < L ? F.rmark : nullptr, F.vcls,
-        l + 2 <= L ? H.lev[l + 2].vcls : nullptr, F.emark, l >= min_level ? 1 : 0);
+        l + 2 <= L ? H.lev[l + 2].vcls : nullptr, F.emark, l >= min_level ? 1 : 0, H.boxes + l);
   }
   const int Lt = std::min(Lf + 1, L);  // levels that may hold cells after the step
   for (int l = 1; l <= Lt; ++l) {
     LevA& V = H.lev[l];
     ++c->launches;
     mg::ada_finalize_cells_kernel<D><<<grid_for((size_t)ipow(V.n, D)), kThreads, 0, st>>>(
-        V.n, V.cellf, l > 1 ? H.lev[l - 1].cellf : nullptr, V.rmark);
+        V.n, V.cellf, l > 1 ? H.lev[l - 1].cellf : nullptr, V.rmark, l > 1 ? H.boxes + (l - 1) : nullptr);
   }
   // 4. vertex classes and zero-surplus values coarse to fine, boxes
   ++c->launches;
   mg::ada_box_init_kernel<<<1, 128, 0, st>>>(H.box6, L + 1);
+  // (the old boxes are read until ada_boxes_kernel replaces them)
   for (int l = 1; l <= Lt; ++l) {
     LevA& V = H.lev[l];
-    c->launches += 2;
+    ++c->launches;
     mg::ada_reclass_kernel<D><<<grid_for(V.nv), kThreads, 0, st>>>(
-        V.n, V.cellf, V.vcls, V.u, l > 1 ? H.lev[l - 1].u : nullptr, H.box6 + 6 * l, V.emark, V.r);
-    mg::ada_diag_kernel<D><<<grid_for(V.nv), kThreads, 0, st>>>(V.n, V.vcls, V.hcell, V.hinv, V.phic, c->k2[0],
-                                                                V.invd);
+        V.n, V.cellf, V.vcls, V.u, l > 1 ? H.lev[l - 1].u : nullptr, H.box6 + 6 * l, V.emark, V.r,
+        l > 1 ? H.boxes + (l - 1) : nullptr);
   }
   ++c->launches;
   mg::ada_boxes_kernel<D><<<1, 32, 0, st>>>(H.box6, L, H.boxes);
+  for (int l = 1; l <= Lt; ++l) {
+    LevA& V = H.lev[l];
+    ++c->launches;
+    mg::ada_diag_kernel<D><<<grid_for(V.nv), kThreads, 0, st>>>(V.n, V.vcls, V.hcell, V.hinv, V.phic, c->k2[0],
+                                                                V.invd, H.boxes + l);
+  }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = ada_succ_all<D>(c, H.abuf + kAbFine)) != cudaSuccess) return e;
   // 5. coarse copies of finer unknowns (fine to coarse) over the new boxes
