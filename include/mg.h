@@ -212,8 +212,10 @@ int mg_get_solution(mg_ctx* ctx, mg_c128* out, int on_device);
 
 /* One additive FAS cycle (Algorithm 2; Appendix A Algorithm 4) on levels
  * 1..L.  omega_per_level: host, L complex relaxation factors, index l-1
- * (Section 5.1: one factor per level).  variant MG_ADD/MG_HB/MG_BPX and
- * transfer MG_DLINEAR/MG_HIERARCHICAL as above.  Asynchronous. */
+ * (Section 5.1: one factor per level; on an adaptive context entry
+ * L - 1 - s serves the vertices with succ(v) = s, see mg_create_adaptive).
+ * variant MG_ADD/MG_HB/MG_BPX and transfer MG_DLINEAR/MG_HIERARCHICAL as
+ * above.  Asynchronous. */
 int mg_cycle(mg_ctx* ctx, int variant, const mg_c128* omega_per_level, int transfer);
 
 /* Euclidean norm of the fine residual b - H u over the fine vertices and
