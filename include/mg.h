@@ -154,7 +154,9 @@ int mg_create_adaptive(int d, int depth, const double* k2_field, double theta_la
  *     (fine-grid vertices) erased (the smallest k, k' on ties; a vertex in
  *     both sets is refined);
  *  3. vetoes: |r(v) / H_l[v, v]| > veto (the vertex still changes: r is the
- *     current generating-system residual), refining on level depth (h_min),
+ *     current generating-system residual; with veto_relative nonzero, >
+ *     veto |u(v)|: the update exceeds that fraction of the value), refining
+ *     on level depth (h_min),
  *     and erasing below min_level + 1 (h_max: min_level is the level of the
  *     coarsest admissible grid, whose cells stay);
  *  4. refining a vertex refines its 2^d cells; a refined cell of level
@@ -168,6 +170,7 @@ int mg_create_adaptive(int d, int depth, const double* k2_field, double theta_la
  *  refine_frac, erase_frac   in [0, 1] (the paper: 0.1, 0.02)
  *  bins                      in [1, 64] (the paper: 20)
  *  veto                      > 0 (the paper: 1e-2; +inf disables it)
+ *  veto_relative             0: absolute bound, nonzero: relative to |u(v)|
  *  min_level                 in [1, depth]
  *  stats                     host long long[4] or NULL: vertices selected for
  *                            refining, for erasing, fine-grid vertices after
@@ -180,8 +183,8 @@ int mg_create_adaptive(int d, int depth, const double* k2_field, double theta_la
  * Errors: MG_ERR_INVALID (not adaptive, arguments out of range),
  * MG_DIVERGED (a non-finite indicator: the grid is left as it is),
  * MG_ERR_CUDA. */
-int mg_adapt(mg_ctx* ctx, double refine_frac, double erase_frac, int bins, double veto, int min_level,
-             long long* stats);
+int mg_adapt(mg_ctx* ctx, double refine_frac, double erase_frac, int bins, double veto, int veto_relative,
+             int min_level, long long* stats);
 
 /* The current refine flags of an adaptive context in mg_create_adaptive's
  * layout (levels 1..depth-1 concatenated, x fastest, 1 = refined).

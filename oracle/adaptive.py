@@ -58,7 +58,9 @@ A6  Selection: the span [min s, max s] over all fine-grid vertices is split
     smallest count whose vertex total is closest to refine_frac times the
     number of fine-grid vertices; erasing the k' bottom bins for erase_frac
     (a vertex in both sets is refined).  Both are vetoed where
-    |r(v) / H_l[v, v]| > veto (r the generating-system residual of A2).
+    |r(v) / H_l[v, v]| > veto (r the generating-system residual of A2), or,
+    read relative to the vertex's value, where |r(v) / H_l[v, v]| >
+    veto |u(v)| (an update above that fraction of the value is a major one).
 A7  Refining a vertex refines its 2^d cells (it becomes a refined vertex);
     vertices on the finest admissible level (h_min) are not refined.
     Erasing acts on the cells of the next coarser level: a refined
@@ -313,7 +315,7 @@ class AdaptiveHierarchy:
             out[lev] = np.where(self.fine_grid(lev), full, -1.0)
         return out
 
-    def adapt(self, min_level, refine_frac=0.1, erase_frac=0.02, bins=20, veto=1e-2):
+    def adapt(self, min_level, refine_frac=0.1, erase_frac=0.02, bins=20, veto=1e-2, veto_relative=False):
         """One step of feature-based refinement and erasing (readings A5-A8).
         Returns (vertices selected for refinement, for erasing, fine-grid
         vertices after the step)."""
@@ -337,7 +339,8 @@ class AdaptiveHierarchy:
         k_er = choose_bins(counts, erase_frac * nfine)
         refsel, ersel = {}, {}
         for lev in range(1, L + 1):
-            vetoed = np.abs(r[lev] / self.levels[lev].diag) > veto
+            bound = veto * np.abs(self.u[lev]) if veto_relative else veto
+            vetoed = np.abs(r[lev] / self.levels[lev].diag) > bound
             top = fine[lev] & (binof[lev] >= bins - k_ref) & ~vetoed
             refsel[lev] = top & (lev < L)
             ersel[lev] = fine[lev] & (binof[lev] < k_er) & ~vetoed & ~top & (lev >= min_level + 1)

@@ -642,7 +642,8 @@ __global__ void ada_choose_bins_kernel(const unsigned long long* counts, const u
 }
 
 // Selection: a fine-grid vertex in the top bins (bin >= kb[0]) that is
-// not vetoed (|r / H[v, v]| <= veto) is refined -- its 2^D cells get
+// not vetoed (|r / H[v, v]| <= veto, or <= veto |u(v)| with veto_relative)
+// is refined -- its 2^D cells get
 // rmark -- when can_refine; one in the bottom bins (bin < kb[1]), not in
 // the top ones and not vetoed gets emark when can_erase.  sel[0], sel[1]
 // count them.  The marks start at zero (the kernels that consume them
@@ -650,8 +651,8 @@ __global__ void ada_choose_bins_kernel(const unsigned long long* counts, const u
 template <int D>
 __global__ void ada_mark_kernel(int n, const double* __restrict__ s, const cplx<double>* __restrict__ r,
                                 const cplx<double>* __restrict__ invd, const AdaBox* __restrict__ boxp,
-                                const unsigned long long* mm,
-                                int bins, const int* kb, double veto, int can_refine, int can_erase,
+                                const unsigned long long* mm, const cplx<double>* __restrict__ u,
+                                int bins, const int* kb, double veto, int veto_relative, int can_refine, int can_erase,
                                 uint8_t* __restrict__ rmark, uint8_t* __restrict__ emark,
                                 unsigned long long* sel) {
   const AdaBox box = *boxp;
@@ -666,7 +667,12 @@ __global__ void ada_mark_kernel(int n, const double* __restrict__ s, const cplx<
     if (!(sv >= 0.0)) continue;
     const int b = ada_bin(sv, lo, hi, bins);
     const cplx<double> q = r[i] * invd[i];
-    const bool vetoed = sqrt(fma(q.x, q.x, q.y * q.y)) > veto;
+    double bound = veto;
+    if (veto_relative) {
+      const cplx<double> uv = u[i];
+      bound = veto * sqrt(fma(uv.x, uv.x, uv.y * uv.y));
+    }
+    const bool vetoed = sqrt(fma(q.x, q.x, q.y * q.y)) > bound;
     const bool top = b >= ref_from && !vetoed;
     if (top && can_refine) {
 #pragma unroll

@@ -2343,7 +2343,7 @@ cudaError_t ada_composite(mg_ctx* c, cplx<double>* out) {
 // graph while the finest level and the grid capacities stay.
 template <int D>
 cudaError_t ada_enqueue_adapt(mg_ctx* c, double refine_frac, double erase_frac, int bins, double veto,
-                              int min_level) {
+                              int veto_relative, int min_level) {
   HierA& H = *c->ada;
   const int L = c->L, Lf = H.Lf;
   cudaStream_t st = c->stream;
@@ -2374,8 +2374,9 @@ cudaError_t ada_enqueue_adapt(mg_ctx* c, double refine_frac, double erase_frac, 
     LevA& V = H.lev[l];
     ++c->launches;
     mg::ada_mark_kernel<D><<<H.gcap[l], kThreads, 0, st>>>(V.n, V.s, V.r, V.invd, H.boxes + l, H.abuf + kAbMinMax,
-                                                           bins, kb, veto, l < L ? 1 : 0, l >= min_level + 1 ? 1 : 0,
-                                                           V.rmark, V.emark, H.abuf + kAbSel);
+                                                           V.u, bins, kb, veto, veto_relative, l < L ? 1 : 0,
+                                                           l >= min_level + 1 ? 1 : 0, V.rmark, V.emark,
+                                                           H.abuf + kAbSel);
   }
   // 3. new refine bits fine to coarse, then existence coarse to fine
   for (int l = std::min(Lf, L - 1); l >= 1; --l) {
@@ -2435,12 +2436,15 @@ cudaError_t ada_enqueue_adapt(mg_ctx* c, double refine_frac, double erase_frac, 
 // outgrows its grid).  stats: vertices selected for refining and erasing,
 // fine-grid vertices after the step, finest level with cells.
 template <int D>
-int ada_adapt(mg_ctx* c, double refine_frac, double erase_frac, int bins, double veto, int min_level,
-              long long* stats) {
+int ada_adapt(mg_ctx* c, double refine_frac, double erase_frac, int bins, double veto, int veto_relative,
+              int min_level, long long* stats) {
   HierA& H = *c->ada;
   const int L = c->L;
-  auto enqueue = [&]() { return ada_enqueue_adapt<D>(c, refine_frac, erase_frac, bins, veto, min_level); };
-  std::vector<double> key = {refine_frac, erase_frac, (double)bins, veto, (double)min_level, (double)H.Lf};
+  auto enqueue = [&]() {
+    return ada_enqueue_adapt<D>(c, refine_frac, erase_frac, bins, veto, veto_relative, min_level);
+  };
+  std::vector<double> key = {refine_frac, erase_frac, (double)bins, veto, (double)veto_relative,
+                             (double)min_level, (double)H.Lf};
   for (int l = 1; l <= L; ++l) key.push_back((double)H.gcap[l]);
   bool launched = false;
   if (c->use_graphs) {
@@ -2610,8 +2614,8 @@ int mg_create_adaptive(int d, int depth, const double* k2_field, double theta_la
   return create_ctx(d, depth, k2_field, theta_layer, theta_interior, width_lo, width_hi, refine, out);
 }
 
-int mg_adapt(mg_ctx* c, double refine_frac, double erase_frac, int bins, double veto, int min_level,
-             long long* stats) {
+int mg_adapt(mg_ctx* c, double refine_frac, double erase_frac, int bins, double veto, int veto_relative,
+             int min_level, long long* stats) {
   if (check_ctx(c)) return MG_ERR_INVALID;
   if (c->ada == nullptr) return fail(c, MG_ERR_INVALID, "mg_adapt takes an adaptive context (mg_create_adaptive)");
   if (!(refine_frac >= 0.0 && refine_frac <= 1.0 && erase_frac >= 0.0 && erase_frac <= 1.0))
@@ -2620,8 +2624,8 @@ int mg_adapt(mg_ctx* c, double refine_frac, double erase_frac, int bins, double 
   if (!(veto > 0.0)) return fail(c, MG_ERR_INVALID, "veto must be > 0");
   if (min_level < 1 || min_level > c->L) return fail(c, MG_ERR_INVALID, "min_level must be in [1, depth]");
   long long st[4] = {0, 0, 0, 0};
-  const int rc = c->d == 2 ? ada_adapt<2>(c, refine_frac, erase_frac, bins, veto, min_level, st)
-                           : ada_adapt<3>(c, refine_frac, erase_frac, bins, veto, min_level, st);
+  const int rc = c->d == 2 ? ada_adapt<2>(c, refine_frac, erase_frac, bins, veto, veto_relative != 0, min_level, st)
+                           : ada_adapt<3>(c, refine_frac, erase_frac, bins, veto, veto_relative != 0, min_level, st);
   if (rc != MG_OK && rc != MG_DIVERGED) return rc;
   if (stats != nullptr) std::memcpy(stats, st, sizeof st);
   return rc;

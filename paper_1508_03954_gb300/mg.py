@@ -67,7 +67,7 @@ def load(path: str | None = None):
         "mg_create": (ip, [ip, ip, ctypes.POINTER(dp), dp, dp, ctypes.POINTER(vp)]),
         "mg_create_ecs": (ip, [ip, ip, ctypes.POINTER(dp), dp, dp, dp, dp, ctypes.POINTER(vp)]),
         "mg_create_adaptive": (ip, [ip, ip, ctypes.POINTER(dp), dp, dp, dp, dp, ctypes.c_char_p, ctypes.POINTER(vp)]),
-        "mg_adapt": (ip, [vp, dp, dp, ip, dp, ip, ctypes.POINTER(ctypes.c_longlong)]),
+        "mg_adapt": (ip, [vp, dp, dp, ip, dp, ip, ip, ctypes.POINTER(ctypes.c_longlong)]),
         "mg_get_refinement": (ip, [vp, ctypes.c_char_p]),
         "mg_destroy": (None, [vp]),
         "mg_set_stream": (ip, [vp, vp]),
@@ -278,13 +278,13 @@ class Solver:
                     "mg_residual_norm")
         return a.value, r.value
 
-    def adapt(self, min_level, refine_frac=0.1, erase_frac=0.02, bins=20, veto=1e-2):
+    def adapt(self, min_level, refine_frac=0.1, erase_frac=0.02, bins=20, veto=1e-2, veto_relative=False):
         """One step of feature-based refinement (mg_adapt).  Returns (vertices
         selected for refining, for erasing, fine-grid vertices after the
         step, finest level with cells); raises MgError on MG_DIVERGED."""
         st = (ctypes.c_longlong * 4)()
         self._check(self._L.mg_adapt(self._view, float(refine_frac), float(erase_frac), int(bins), float(veto),
-                                     int(min_level), st), "mg_adapt")
+                                     1 if veto_relative else 0, int(min_level), st), "mg_adapt")
         return tuple(int(x) for x in st)
 
     def refinement(self):

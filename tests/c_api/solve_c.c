@@ -101,7 +101,7 @@ int main(void) {
   long long st[4] = {0, 0, 0, 0};
   for (int it = 0; it < 5; ++it) {
     if (check(mg_cycle(ca, MG_BPX, oma, MG_HIERARCHICAL), "mg_cycle adaptive", ca)) return 1;
-    if (check(mg_adapt(ca, 0.1, 0.02, 20, 1e-2, 2, st), "mg_adapt", ca)) return 1;
+    if (check(mg_adapt(ca, 0.1, 0.02, 20, 1e-2, it % 2, 2, st), "mg_adapt", ca)) return 1;
   }
   if (check(mg_get_refinement(ca, refine), "mg_get_refinement", ca)) return 1;
   int refined2 = 0;
@@ -110,7 +110,7 @@ int main(void) {
   if (check(mg_residual_max(ca, &rmax), "mg_residual_max adaptive", ca)) return 1;
   printf("adaptive depth %d: 5 steps, %lld fine-grid vertices, finest level %lld, %d refined level-2 cells, "
          "max |r| %.3e\n", da, st[2], st[3], refined2, rmax);
-  if (mg_adapt(ca, 0.1, 0.02, 0, 1e-2, 2, st) != MG_ERR_INVALID) return 1; /* bins out of range */
+  if (mg_adapt(ca, 0.1, 0.02, 0, 1e-2, 0, 2, st) != MG_ERR_INVALID) return 1; /* bins out of range */
   mg_destroy(ca);
   free(refine);
   free(fa);

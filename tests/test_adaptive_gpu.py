@@ -194,7 +194,7 @@ def test_residual_max_matches_the_oracle():
     g.close()
 
 
-def decision_margins(o, bins, veto):
+def decision_margins(o, bins, veto, relative=False):
     """How far the oracle's state is from flipping a decision: the distance
     of every fine-grid vertex's scaled indicator to the interior bin edges,
     and of |r / diag| to the veto (relative).  The parity of the flags
@@ -209,7 +209,8 @@ def decision_margins(o, bins, veto):
         q = ((s[lev][f] - lo) / (hi - lo)) * bins
         mb = min(mb, np.abs(q - np.clip(np.round(q), 1, bins - 1)).min(initial=np.inf))
         ratio = np.abs(r[lev][f] / o.levels[lev].diag[f])
-        mv = min(mv, (np.abs(ratio - veto) / veto).min(initial=np.inf))
+        bound = veto * np.abs(o.u[lev][f]) if relative else veto
+        mv = min(mv, (np.abs(ratio - bound) / bound).min(initial=np.inf))
     return mb, mv
 
 
@@ -220,8 +221,9 @@ def check_flags_and_state(g, o, depth, what):
     check_state(g, o, depth, what)
 
 
-@pytest.mark.parametrize("d,depth,steps", [(2, 5, 6), (3, 3, 3)])
-def test_dynamic_refinement_matches_the_oracle(d, depth, steps):
+@pytest.mark.parametrize("d,depth,steps,relative,veto", [(2, 5, 6, False, 1e-2), (3, 3, 3, False, 1e-2),
+                                                         (2, 5, 6, True, 0.3)])
+def test_dynamic_refinement_matches_the_oracle(d, depth, steps, relative, veto):
     """Feature-based refinement (Section 5.3) from the regular level-2 grid:
     cycle, then mg_adapt, repeatedly (erasing a large fraction every other
     step).  Every step selects the same vertices, yields the same refine
@@ -238,11 +240,11 @@ def test_dynamic_refinement_matches_the_oracle(d, depth, steps):
     for k in range(steps):
         g.cycle(mg.MG_BPX, om, mg.MG_HIERARCHICAL)
         o.cycle(om, O.ADD, O.HIERARCHICAL)
-        mb, mv = decision_margins(o, 20, 1e-2)
+        mb, mv = decision_margins(o, 20, veto, relative)
         assert mb > 1e-9 and mv > 1e-9, (mb, mv)
         ef = 0.3 if k % 2 else 0.02
-        st = g.adapt(2, 0.1, ef, 20, 1e-2)
-        ost = o.adapt(2, 0.1, ef, 20, 1e-2)
+        st = g.adapt(2, 0.1, ef, 20, veto, veto_relative=relative)
+        ost = o.adapt(2, 0.1, ef, 20, veto, veto_relative=relative)
         assert st[:3] == ost, (k, st, ost)
         assert st[3] == max(lev for lev in range(1, depth + 1) if o.cells[lev].any())
         erased += st[1]

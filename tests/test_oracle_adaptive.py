@@ -453,6 +453,43 @@ def test_vetoes():
         assert (ada.refine_flags() != old).any() == changes
 
 
+def test_relative_veto():
+    """Read relative to the vertex's value, the veto blocks the vertices whose
+    Jacobi update |r / diag| exceeds veto |u(v)|: with veto 1e300 (an update
+    never exceeds it) it selects what no veto selects; with a veto below
+    every |r / diag| / |u| nothing changes; in between exactly the vertices
+    above the bound are spared."""
+    d, depth = 2, 3
+    n = 3 ** depth
+    ref = {1: np.ones((3, 3), dtype=bool), 2: np.zeros((9, 9), dtype=bool)}
+    ref[2][6:8, 6:8] = True
+
+    def make():
+        ada = AdaptiveHierarchy(d, depth, np.full((n + 1,) * d, -10.0), 0.0, 0.0, ref)
+        ada.set_rhs_nodal(np.ones((n + 1,) * d, dtype=np.complex128))
+        set_levels_from(ada, bump)
+        return ada
+
+    free = make()
+    free.adapt(min_level=1, refine_frac=0.1, erase_frac=0.02, veto=np.inf)
+    loose = make()
+    loose.adapt(min_level=1, refine_frac=0.1, erase_frac=0.02, veto=1e300, veto_relative=True)
+    np.testing.assert_array_equal(loose.refine_flags(), free.refine_flags())
+    tight = make()
+    old = tight.refine_flags()
+    tight.adapt(min_level=1, refine_frac=0.1, erase_frac=0.02, veto=1e-300, veto_relative=True)
+    np.testing.assert_array_equal(tight.refine_flags(), old)
+    # a bound between: the selected set shrinks to the vertices under the bound
+    mid = make()
+    r = mid.level_residuals()
+    ratios = np.concatenate([np.abs(r[l] / mid.levels[l].diag)[mid.fine_grid(l)] /
+                             np.abs(mid.u[l])[mid.fine_grid(l)] for l in range(1, depth + 1)])
+    veto = float(np.median(ratios))
+    n_ref_free = make().adapt(min_level=1, refine_frac=0.1, erase_frac=0.0, veto=np.inf)[0]
+    n_ref_mid = mid.adapt(min_level=1, refine_frac=0.1, erase_frac=0.0, veto=veto, veto_relative=True)[0]
+    assert 0 <= n_ref_mid < n_ref_free
+
+
 def bump3(x, y, z):
     return x + 0.5 * y + 0.25 * z + 10.0 * np.exp(-((x - 0.8) ** 2 + (y - 0.75) ** 2 + (z - 0.7) ** 2) / 0.004)
 
