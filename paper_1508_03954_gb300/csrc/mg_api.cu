@@ -197,7 +197,6 @@ enum : int {
 struct HierA {
   std::vector<LevA> lev;       // 1..L
   int Lf = 1;                  // finest level with cells
-  long long version = 0;       // structure changes (adaptation steps)
   unsigned long long* abuf = nullptr;  // kAb* slots
   int* box6 = nullptr;                 // per level: min x, y, z, max x, y, z
   mg::AdaBox* boxes = nullptr;         // per level: the bounding box, read by the kernels
@@ -2506,7 +2505,6 @@ int ada_adapt(mg_ctx* c, double refine_frac, double erase_frac, int bins, double
     const int need = grid_for(V.boxvol);
     if (need > H.gcap[l]) H.gcap[l] = std::min(152 * 16, std::max(need, 2 * H.gcap[l]));
   }
-  ++H.version;
   double hi;
   std::memcpy(&hi, hb + kAbMinMax + 1, sizeof hi);
   stats[0] = (long long)hb[kAbSel];
