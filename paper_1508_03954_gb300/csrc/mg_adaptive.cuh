@@ -6,8 +6,9 @@
 // Every level keeps dense arrays over its full grid plus a flag per cell
 // (bit 0: the cell exists, bit 1: it is refined) and a class per vertex
 // (0: no existing cell around it, 1: hanging or Dirichlet, 2: unknown = all
-// 2^d cells exist).  Kernels skip what does not exist, so the FP64 work --
-// what bounds these kernels on GB300 -- follows the adaptive grid.
+// 2^d cells exist).  The cycle kernels run over the bounding box of each
+// level's existing vertices, read from device memory, and skip what does
+// not exist, so their work follows the adaptive grid.
 //
 // The cycle is the additive correction scheme on the hierarchical
 // generating system of the adaptive grid (Lemma 2 / Theorem 2 form):
@@ -27,11 +28,13 @@
 //
 // Feature-based dynamic refinement (Section 5.3) runs on the device too: the
 // indicator s(v) = max over the axes of the undivided second difference at
-// the fine-grid vertices, its global span and a histogram over equal bins
-// (the host picks how many top / bottom bins to refine / erase), marks on
-// cells and vertices, the new cell flags (fine to coarse, then existence
-// coarse to fine), the new vertex classes with zero hierarchical surplus on
-// new vertices, and succ.
+// the fine-grid vertices, its global span, a histogram over equal bins and
+// the choice of how many top / bottom bins to refine / erase, marks on cells
+// and vertices (with the residual veto, absolute or relative to |u(v)|), the
+// new cell flags (fine to coarse, then existence coarse to fine), the new
+// vertex classes with zero hierarchical surplus on new vertices, the new
+// bounding boxes, diagonals and succ -- each over the region of its level
+// that a step can change.
 #pragma once
 #include "mg_kernels.cuh"
 
