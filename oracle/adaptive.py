@@ -325,6 +325,8 @@ class AdaptiveHierarchy:
         fine = {lev: self.fine_grid(lev) for lev in range(1, L + 1)}
         vals = np.concatenate([s[lev][fine[lev]] for lev in range(1, L + 1)])
         nfine = vals.size
+        if nfine == 0:
+            return 0, 0, 0  # no fine-grid vertex: nothing to select
         smin, smax = vals.min(), vals.max()
         binof = {}
         for lev in range(1, L + 1):
