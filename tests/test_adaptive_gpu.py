@@ -4,7 +4,9 @@ regular oracle and to the conforming finite-element solution): every
 level's values and the fine-grid function after each cycle to 1e-12, the
 residual norms, a converged solve, and full refinement against the regular
 library path."""
+import json
 import math
+import os
 
 import numpy as np
 import pytest
@@ -278,3 +280,39 @@ def test_adapt_arguments_and_refinement_roundtrip():
     with pytest.raises(mg.MgError):
         r.adapt(1)
     r.close()
+
+
+GOLDEN_T2A = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "table2_adaptive_oracle.txt")
+
+
+def test_table2_adaptive_runs_match_the_stored_oracle_runs():
+    """The dynamic path at the size the bench measures (depth 7: 50 cycles and
+    50 refinement steps per run, the schedule of forms.channel_table2_adaptive):
+    every stored oracle run (tests/golden/table2_adaptive_oracle.txt, written
+    by make_table2_adaptive.py) ends on the same grid and with the same
+    max-norm reduction."""
+    rows = [json.loads(ln) for ln in open(GOLDEN_T2A) if ln.strip() and not ln.startswith("#")]
+    assert rows
+    depth, min_level = 7, 3
+    for row in rows:
+        deg, solver = row["theta_deg"], row["solver"]
+        c = W.channel(deg, depth)
+        ref = {lev: np.full((3 ** lev,) * 2, lev < min_level) for lev in range(1, depth)}
+        s = mg.Solver.adaptive(2, depth, c["k2"], c["theta"], c["layer_width"], ref, c["theta_interior"])
+        s.set_rhs(c["f"])
+        s.set_solution(np.zeros(s.shape, complex))
+        r0 = s.residual_max()
+        st = None
+        for it in range(1, 51):
+            if solver == "jacobi":
+                w = (W.CHANNEL_OMEGA1 if it % 2 else W.CHANNEL_OMEGA2) if deg == 0 else 0.4
+                s.cycle(mg.MG_ADD, mg.omega_scheme(mg.MG_OMEGA_JACOBI, w, depth), mg.MG_DLINEAR)
+            elif solver == "transition":
+                s.cycle(mg.MG_ADD, mg.omega_scheme(mg.MG_OMEGA_TRANSITION, 0.4, depth, it), mg.MG_DLINEAR)
+            else:
+                s.cycle(mg.MG_ADD, mg.omega_scheme(mg.MG_OMEGA_UCG, 0.4, depth), mg.MG_HIERARCHICAL)
+            st = s.adapt(min_level, 0.1, 0.02, 20, 1e-2)
+        red = s.residual_max() / r0
+        s.close()
+        assert st[2] == row["fine_vertices"], (deg, solver, st, row)
+        assert abs(red - row["reduction_max_norm"]) <= 1e-10 * abs(row["reduction_max_norm"]), (deg, solver, red)
