@@ -101,6 +101,65 @@ def fine_sweep_counts(d, depth, w, bpx, omega_real, word=16, galerkin=True):
     return flops, nbytes
 
 
+def axis_complex_fraction(depth, w):
+    """Fraction of interior indices of one axis whose 1D rows are complex
+    (a neighbouring cell of that axis lies in the scaling layer)."""
+    n = 3 ** depth
+    if w >= 0.5:
+        return 1.0
+    i = np.arange(n)
+    rot = np.minimum(2 * i + 1, 2 * n - 2 * i - 1) < 2.0 * w * n
+    v = np.arange(1, n)
+    return float((rot[v - 1] | rot[v]).mean())
+
+
+def fine_sweep3_counts(depth, w, bpx=True):
+    """(FP64 flops, bytes) the separable 3D complex128 fine sweep needs per
+    launch, per owned vertex and without halo recomputation (an FMA is 2
+    flops, an add or a multiply 1; a complex x complex MAC is 8 flops).
+    Per interior vertex and complex value:
+      residual H = M_x[M_y(K_z - phi M_z) + K_y M_z] + K_x M_y M_z with
+        symmetric real rows: z-pair 14, y-pair 24, x-pass with b - 20
+        (complex rows along an axis: 48, 72, 50);
+      pending correction u = U + P c: bilinear per coarse plane + z weights, 12.7;
+      Jacobi 2 (6 with a complex factor), update 2, |r|^2 4;
+      restriction R r (separable, x at c-columns, y at c-rows, z by
+        accumulation), 7.6;
+      Galerkin rows G u_{l-1}: 27 real MACs per coarse vertex, 4;
+      BPX P I du: bilinear per c-plane + two weights per plane, 12.
+    Bytes: U, b read and U' written (3 x 16 B per fine vertex); pending
+    correction read, b and u written on the next coarser level (3 x 16 B per
+    coarse vertex)."""
+    n = 3 ** depth
+    f = axis_complex_fraction(depth, w)
+    per = 14 + 24 + 20 + f * ((48 - 14) + (72 - 24) + (50 - 20))
+    per += 12.7 + 2 + 4 * (1 - (1 - f) ** 3) + 2 + 4 + 7.6 + 4 + (12 if bpx else 0)
+    flops = per * (n - 1) ** 3
+    nbytes = 3 * 16 * (n + 1) ** 3 + 3 * 16 * (n // 3 + 1) ** 3
+    return flops, nbytes
+
+
+FINE_SWEEP3_SOURCES = ("mg_sweep3sd.cuh", "mg_sweep3s.cuh", "mg_defect3.cuh", "mg_kernels.cuh")
+
+
+def fine_sweep3_roofline(cfg, sweep_ms, peaks, peak_src):
+    """Roofline of the dominant kernel of the headline cycle: the finest
+    level's separable complex128 sweep, bound by the FP64 pipe."""
+    flops, nbytes = fine_sweep3_counts(cfg["depth"], cfg["layer_width"], bpx=True)
+    t = sweep_ms / 1e3
+    achieved = flops / t
+    csrc = os.path.join(ROOT, "paper_1508_03954_gb300", "csrc")
+    traffic, sha = recorded_traffic("fine_sweep3_c128_3d_depth5", [os.path.join(csrc, f) for f in FINE_SWEEP3_SOURCES])
+    return {"bound": "alu", "achieved": achieved / 1e12, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_FLOPS, "traffic": traffic,
+            "kernel": "sweep3sd_kernel (finest level, separable, FP64)",
+            "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (derived)",
+            "sweep_ms": sweep_ms, "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": nbytes,
+            "hbm": {"achieved_gbs": nbytes / t / 1e9, "peak_gbs": peaks.get("hbm_gbs"),
+                    "frac": nbytes / t / 1e9 / peaks.get("hbm_gbs", 6800.0), "peak_source": peak_src},
+            "source_sha256_16": sha}
+
+
 # ---------------------------------------------------------------- clocks
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -174,10 +233,25 @@ def recorded_traffic(kernel_key, source_files):
 
 
 # ---------------------------------------------------------------- oracle timing
-def oracle_cycles(cfg, ncycles, omega, budget_s=None):
+# The oracle (numpy, FP64) is far too slow for the full 3D depth-5 workload
+# (about two minutes and 3 GB per cycle on one core), so its timings run the
+# depth-4 instance of the same workload (k = 8 pi, 10% layer, centred
+# Gaussian; 512,000 interior unknowns) and report DoF-updates/s.
+ORACLE_CYCLE_S = {5: 115.0, 4: 3.4, 3: 0.13}   # one host core, per cycle
+
+
+def _oracle_problem(depth):
     import oracle as O
-    o = O.Hierarchy(cfg["d"], cfg["depth"], cfg["k2"], cfg["theta"], cfg["layer_width"])
+    cfg = W.config3(depth)
+    o = O.Hierarchy(cfg["d"], depth, cfg["k2"], cfg["theta"], cfg["layer_width"])
     o.set_rhs_nodal(cfg["f"])
+    return O, o
+
+
+def _oracle_cycles(depth, ncycles, budget_s):
+    """Oracle cycles (BPX, omega = 0.6) on one core: (cycles done, seconds)."""
+    O, o = _oracle_problem(depth)
+    omega = np.full(depth, 0.6)
     done, t0 = 0, time.perf_counter()
     while done < ncycles:
         o.cycle(omega, O.ADD, O.HIERARCHICAL)
@@ -187,47 +261,90 @@ def oracle_cycles(cfg, ncycles, omega, budget_s=None):
     return done, time.perf_counter() - t0
 
 
-def cpu_baseline_line(cfg, budget_s=15.0):
-    depth = cfg["depth"]
-    omega = np.full(depth, 0.6)
-    done, dt = oracle_cycles(cfg, 1000, omega, budget_s)
-    units = (3 ** depth - 1) ** cfg["d"] * done
-    return {"value": units / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{done} BPX cycles of the depth-{depth} 2D workload "
-                      f"({dt:.1f} s, numpy FP64, one thread)"}
+_WORKER = {}
+
+
+def _oracle_worker_init(depth):
+    _WORKER["p"] = _oracle_problem(depth)
+    _WORKER["depth"] = depth
+
+
+def _oracle_worker_cycles(ncycles):
+    O, o = _WORKER["p"]
+    omega = np.full(_WORKER["depth"], 0.6)
+    t0 = time.perf_counter()
+    for _ in range(ncycles):
+        o.cycle(omega, O.ADD, O.HIERARCHICAL)
+    return ncycles, time.perf_counter() - t0
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def _oracle_pool(depth, cores):
+    """One oracle process per host core (spawned: no CUDA state is
+    inherited), each holding its own copy of the problem."""
+    import multiprocessing as mp
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+    return mp.get_context("spawn").Pool(cores, initializer=_oracle_worker_init, initargs=(depth,))
+
+
+def cpu_baseline_line(budget_s=12.0, depth=4):
+    """The oracle on the host: one core (about budget_s of cycles) and every
+    core of the process's affinity mask (one independent copy of the problem
+    per core, cycles timed in parallel; throughput = all cycles / the slowest
+    copy's time)."""
+    units = (3 ** depth - 1) ** 3
+    done1, dt1 = _oracle_cycles(depth, 1000, budget_s)
+    single = units * done1 / dt1
+    cores = host_cores()
+    per = max(1, int(budget_s / max(dt1 / done1, 1e-3)))
+    with _oracle_pool(depth, cores) as pool:
+        pool.map(_oracle_worker_cycles, [0] * cores)        # set-up done in every worker
+        res = pool.map(_oracle_worker_cycles, [per] * cores)
+    dt_all = max(r[1] for r in res)
+    allc = units * sum(r[0] for r in res) / dt_all
+    return {"value": allc, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"BPX cycles (omega 0.6) of the depth-4 instance of the 3D workload ({units} "
+                      f"interior unknowns): {per} per core on {cores} cores in {dt_all:.1f} s "
+                      f"(one copy per core); one core alone: {done1} cycles in {dt1:.1f} s",
+            "single_core": {"value": single, "cores": 1}}
 
 
 def run_reference(args, rank):
+    """The oracle as the reference arm: each step runs one cycle on every
+    host core (one copy of the problem per core), on the deepest instance
+    of the 3D workload whose steps fit in about two and a half minutes."""
     if rank != 0:
         return
-    os.environ.setdefault("OMP_NUM_THREADS", "1")
-    # size one step so that warmup + steps fit in about two minutes
-    est = {6: 1.6, 5: 0.2, 4: 0.025, 3: 0.004}
-    depth = 6
-    for dd in (6, 5, 4, 3):
+    depth = 3
+    for dd in (4, 3):
         depth = dd
-        if (args.steps + args.warmup) * est[dd] <= 120:
+        if (args.steps + args.warmup) * ORACLE_CYCLE_S[dd] * 1.3 <= 150:
             break
-    cfg = W.config2(depth=depth)
-    omega = np.full(depth, 0.6)
-    import oracle as O
-    o = O.Hierarchy(cfg["d"], depth, cfg["k2"], cfg["theta"], cfg["layer_width"])
-    o.set_rhs_nodal(cfg["f"])
-    for _ in range(args.warmup):
-        o.cycle(omega, O.ADD, O.HIERARCHICAL)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        o.cycle(omega, O.ADD, O.HIERARCHICAL)
-    dt = time.perf_counter() - t0
-    units = (3 ** depth - 1) ** 2 * args.steps
-    val = units / dt
-    sample = (f"one FP64 oracle BPX cycle per step on the depth-{depth} instance of the "
-              f"workload ({(3 ** depth - 1) ** 2} interior unknowns)")
+    cores = host_cores()
+    units = (3 ** depth - 1) ** 3
+    with _oracle_pool(depth, cores) as pool:
+        pool.map(_oracle_worker_cycles, [0] * cores)
+        for _ in range(args.warmup):
+            pool.map(_oracle_worker_cycles, [1] * cores)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            pool.map(_oracle_worker_cycles, [1] * cores)
+        dt = time.perf_counter() - t0
+    val = units * cores * args.steps / dt
+    sample = (f"one FP64 oracle BPX cycle per step on each of {cores} host cores (one copy each) on the "
+              f"depth-{depth} instance of the 3D workload ({units} interior unknowns)")
     line = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c128 (f64)", "data": "synthetic",
             "impl": "reference", "config": workload_config(1),
-            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -250,10 +367,10 @@ def whole_job_rate(units_per_step, steps, world, max_ms):
 
 
 def workload_config(world):
-    return {"workload": "2D complex128 variant sweep: depth 6 (729^2 cells, 529,984 "
-                        "interior unknowns), k=20pi, 10% ECS layer theta=pi/6, 3 Gaussians "
-                        "(seed 1); step = one BPX additive FAS cycle, omega=0.6",
-            "l2": "flushed before every timed step (256 MB write)",
+    return {"workload": "3D complex128 cycle: depth 5 (243^3 cells, 14,172,488 interior unknowns), "
+                        "k=8pi, 10% ECS layer theta=pi/6, centred Gaussian width 0.05; step = one BPX "
+                        "additive FAS cycle, omega=0.6 on every level",
+            "l2": "inputs larger than L2 (232 MB per fine array); L2 also flushed before every timed step",
             "parallelism": "replicas" if world > 1 else "single GPU"}
 
 
@@ -264,97 +381,172 @@ def workload_config(world):
 INNER = 16
 
 
-def measure_forms(mg, torch, peaks):
-    """Time to 1e-8 of the refinement form against the plain complex128 cycle
-    (2D depth 6 and 3D depth 5), the batched form against sequential solves
-    (256 problems of depth 4-6), and the adjoint gradient (2D depth 6).  The
-    configured indefinite problems diverge (interior theta = 0) and the plain
-    cycle stalls where coarse cells straddle the layer edge, so times to 1e-8
-    use the definite companions k^2 -> -k^2 (same shapes and bytes)."""
-    out = {}
+def _wall(torch, fn):
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r = fn()
+    torch.cuda.synchronize()
+    return r, time.perf_counter() - t0
+
+
+def time_cycles(torch, s, variant, omega, transfer, steps, warmup, flush=None, clocks=None, dist=None):
+    """Device time of `steps` cycles (CUDA events on the solver's stream
+    around each cycle, L2 flushed before each), after `warmup` untimed ones.
+    Returns (total ms, launches in the timed region, clock record)."""
     stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        s.cycle(variant, omega, transfer)
+    torch.cuda.synchronize()
+    s.get_stats()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if clocks is not None:
+        clocks.start()
+    for k in range(steps):
+        if flush is not None:
+            flush.fill_(float(k & 7))
+        starts[k].record(stream)
+        s.cycle(variant, omega, transfer)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clk = clocks.stop() if clocks is not None else None
+    launches, _, _ = s.get_stats()
+    return sum(a.elapsed_time(b) for a, b in zip(starts, ends)), launches, clk
 
-    def wall(fn):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        r = fn()
-        torch.cuda.synchronize()
-        return r, time.perf_counter() - t0
 
-    # configured problem: plain cycles from zero
+def fine_sweep_ms(torch, s, variant, omega, transfer, cycles, flush=None):
+    """The finest-level sweep alone: the same cycles with an event pair
+    around the fine sweep (instrumented pass; mean ms per sweep)."""
+    s.set_timing(True)
+    for _ in range(3):
+        s.cycle(variant, omega, transfer)
+    torch.cuda.synchronize()
+    s.get_stats()
+    for k in range(cycles):
+        if flush is not None:
+            flush.fill_(float(k & 7))
+        s.cycle(variant, omega, transfer)
+    _, nsweeps, ms = s.get_stats()
+    s.set_timing(False)
+    return ms / max(nsweeps, 1)
+
+
+def form_cycle_2d(mg, torch, peaks, steps=500):
+    """The 2D complex128 variant-sweep workload (depth 6, 529,984 interior
+    unknowns, k = 20 pi, 10% layer, three Gaussians of seed 1): device time
+    per BPX cycle (omega 0.6, L2 flushed before each), and the fine sweep
+    against the FP64 roofline.  The level is L2-resident between cycles."""
+    cfg = W.config2()
+    d, depth = cfg["d"], cfg["depth"]
+    s = mg.Solver(d, depth, cfg["k2"], cfg["theta"], cfg["layer_width"])
+    s.set_stream(torch.cuda.current_stream().cuda_stream)
+    s.set_rhs(cfg["f"])
+    omega = np.full(depth, 0.6)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    total, _, _ = time_cycles(torch, s, mg.MG_BPX, omega, mg.MG_HIERARCHICAL, steps, 20, flush)
+    sweep = fine_sweep_ms(torch, s, mg.MG_BPX, omega, mg.MG_HIERARCHICAL, min(steps, 300), flush)
+    s.close()
+    flops, nbytes = fine_sweep_counts(d, depth, cfg["layer_width"], bpx=True, omega_real=True)
+    interior = (3 ** depth - 1) ** d
+    return {"ms_per_cycle": total / steps, "dof_updates_per_s": interior * steps / (total / 1e3),
+            "fine_sweep_ms": sweep, "fine_sweep_fp64_tflops": flops / (sweep / 1e3) / 1e12,
+            "fine_sweep_frac_of_fp64_peak": flops / (sweep / 1e3) / FP64_PEAK_FLOPS,
+            "fine_sweep_hbm_frac": nbytes / (sweep / 1e3) / 1e9 / peaks.get("hbm_gbs", 6800.0)}
+
+
+def form_configured_2d(mg, torch):
+    """The configured indefinite 2D depth-6 problem from u = 0 (it diverges:
+    interior theta = 0)."""
     c = W.config2()
     s = mg.Solver(2, 6, c["k2"], c["theta"], c["layer_width"])
-    s.set_stream(stream.cuda_stream)
+    s.set_stream(torch.cuda.current_stream().cuda_stream)
     s.set_rhs(c["f"])
     st, n, rel = s.solve(mg.MG_BPX, np.full(6, 0.6), mg.MG_HIERARCHICAL, 1e-8, 300)
-    out["configured_2d_depth6"] = {"status": mg.STATUS_NAMES[st], "cycles": n, "rel_res": rel}
     s.close()
-    # (A) 2D depth 6 definite companion
+    return {"status": mg.STATUS_NAMES[st], "cycles": n, "rel_res": rel}
+
+
+def form_refine_2d(mg, torch):
+    """Time to 1e-8 on the 2D depth-6 definite companion (k^2 -> -k^2):
+    complex64 cycles in FP64 defect correction against plain complex128
+    cycles."""
     c = W.definite(W.config2())
     om = mg.omega_scheme(mg.MG_OMEGA_EXP, 0.6, 6)
     s = mg.Solver(2, 6, c["k2"], c["theta"], c["layer_width"])
-    s.set_stream(stream.cuda_stream)
+    s.set_stream(torch.cuda.current_stream().cuda_stream)
     s.set_rhs(c["f"])
     s.set_precision(mg.MG_C64_REFINE, INNER)
     s.solve(mg.MG_ADD, om, mg.MG_DLINEAR, 1e-8, 4000)
     s.set_solution(np.zeros(s.shape, complex))
-    (st, n, rel), dt = wall(lambda: s.solve(mg.MG_ADD, om, mg.MG_DLINEAR, 1e-8, 4000))
+    (st, n, rel), dt = _wall(torch, lambda: s.solve(mg.MG_ADD, om, mg.MG_DLINEAR, 1e-8, 4000))
     a = {"c64_refine": {"status": mg.STATUS_NAMES[st], "inner_cycles": n, "inner_per_outer": INNER,
                         "rel_res": rel, "seconds": dt}}
     s.set_precision(mg.MG_C128, 4)
     s.set_solution(np.zeros(s.shape, complex))
-    (st, n, rel), dt = wall(lambda: s.solve(mg.MG_ADD, om, mg.MG_DLINEAR, 1e-8, 300))
+    (st, n, rel), dt = _wall(torch, lambda: s.solve(mg.MG_ADD, om, mg.MG_DLINEAR, 1e-8, 300))
     a["c128_plain"] = {"status": mg.STATUS_NAMES[st], "cycles": n, "rel_res": rel, "seconds": dt,
                        "note": "stalls at the FAS fixed point shifted by the non-Galerkin layer edge"}
-    out["time_to_1e-8_2d_depth6_definite"] = a
     s.close()
-    # (C) 3D depth 5 definite companion
+    return a
+
+
+def form_refine_3d(mg, torch, peaks):
+    """Time to 1e-8 on the 3D depth-5 definite companion: complex64 cycles in
+    FP64 defect correction against plain complex128 cycles, with the
+    complex64 fine sweep's HBM fraction from an event-timed pass."""
     c = W.definite(W.config3())
     om = mg.omega_scheme(mg.MG_OMEGA_EXP, 0.6, 5)
     s = mg.Solver(3, 5, c["k2"], c["theta"], c["layer_width"])
-    s.set_stream(stream.cuda_stream)
+    s.set_stream(torch.cuda.current_stream().cuda_stream)
     s.set_rhs(c["f"])
     s.set_precision(mg.MG_C64_REFINE, INNER)
     s.solve(mg.MG_ADD, om, mg.MG_DLINEAR, 1e-8, INNER)
     s.set_solution(np.zeros(s.shape, complex))
-    (st, n, rel), dt = wall(lambda: s.solve(mg.MG_ADD, om, mg.MG_DLINEAR, 1e-8, 2000))
-    # the fine sweep alone: events around it on a separate pass
+    (st, n, rel), dt = _wall(torch, lambda: s.solve(mg.MG_ADD, om, mg.MG_DLINEAR, 1e-8, 2000))
     s.set_solution(np.zeros(s.shape, complex))
     s.set_timing(True)
     s.get_stats()
     s.solve(mg.MG_ADD, om, mg.MG_DLINEAR, 1e-30, 2 * INNER)
     _, k, ms = s.get_stats()
     s.set_timing(False)
-    nv = (3 ** 5 + 1) ** 3
-    nbytes = 3 * 8 * nv + 3 * 8 * (3 ** 4 + 1) ** 3
+    nbytes = 3 * 8 * (3 ** 5 + 1) ** 3 + 3 * 8 * (3 ** 4 + 1) ** 3
     sweep_s = ms / max(k, 1) / 1e3
     cc = {"c64_refine": {"status": mg.STATUS_NAMES[st], "inner_cycles": n, "inner_per_outer": INNER,
-                         "rel_res": rel, "seconds": dt,
-                         "fine_sweep_ms": sweep_s * 1e3,
-                         "fine_sweep_hbm": {"achieved_gbs": nbytes / sweep_s / 1e9, "peak_gbs": peaks.get("hbm_gbs"),
+                         "rel_res": rel, "seconds": dt, "fine_sweep_ms": sweep_s * 1e3,
+                         "fine_sweep_hbm": {"achieved_gbs": nbytes / sweep_s / 1e9,
+                                            "peak_gbs": peaks.get("hbm_gbs"),
                                             "frac": nbytes / sweep_s / 1e9 / peaks.get("hbm_gbs", 6800.0),
                                             "algorithmic_bytes": nbytes}}}
     s.set_precision(mg.MG_C128, 4)
     s.set_solution(np.zeros(s.shape, complex))
-    (st, n, rel), dt = wall(lambda: s.solve(mg.MG_ADD, om, mg.MG_DLINEAR, 1e-8, 60))
+    (st, n, rel), dt = _wall(torch, lambda: s.solve(mg.MG_ADD, om, mg.MG_DLINEAR, 1e-8, 60))
     cc["c128_plain"] = {"status": mg.STATUS_NAMES[st], "cycles": n, "rel_res": rel, "seconds": dt,
                         "dof_updates_per_s": (3 ** 5 - 1) ** 3 * n / dt}
-    out["time_to_1e-8_3d_depth5_definite"] = cc
     s.close()
-    # (B) batched: 256 problems, persistent launch vs one problem at a time
+    return cc
+
+
+def form_batched(mg, torch):
+    """256 problems of depth 4-6 (definite companions) in one persistent
+    launch per outer step against the same problems one after another."""
     specs = W.config4_specs(256)
     probs = [W.definite(W.config4_problem(sp)) for sp in specs]
     bt = mg.Batch(probs)
-    bt.set_stream(stream.cuda_stream)
+    bt.set_stream(torch.cuda.current_stream().cuda_stream)
     for p, pr in enumerate(probs):
         bt.solvers[p].set_rhs(pr["f"])
     oms = [mg.omega_scheme(mg.MG_OMEGA_EXP, 0.6, pr["depth"]) for pr in probs]
     tc, bp, ms = bt.autotune(mg.MG_ADD, oms, mg.MG_DLINEAR, INNER)
-    (st, cyc, rel), dt = wall(lambda: bt.solve(mg.MG_ADD, oms, mg.MG_DLINEAR, 1e-8, 400, INNER))
+    (st, cyc, rel), dt = _wall(torch, lambda: bt.solve(mg.MG_ADD, oms, mg.MG_DLINEAR, 1e-8, 400, INNER))
     unknowns = sum((3 ** pr["depth"] - 1) ** 2 for pr in probs)
     upd = sum((3 ** pr["depth"] - 1) ** 2 * cyc[p] for p, pr in enumerate(probs))
-    bb = {"problems": 256, "fine_unknowns": unknowns, "autotuned": {"tile": tc, "blocks_per_sm": bp,
-                                                                     "ms_per_outer_step": ms},
+    bb = {"problems": 256, "fine_unknowns": unknowns,
+          "autotuned": {"tile": tc, "blocks_per_sm": bp, "ms_per_outer_step": ms},
           "batched": {"seconds": dt, "all_ok": all(x == mg.MG_OK for x in st), "max_rel_res": max(rel),
                       "dof_updates_per_s": upd / dt}}
 
@@ -366,16 +558,20 @@ def measure_forms(mg, torch, peaks):
             sv.set_precision(mg.MG_C64_REFINE, INNER)
             res.append(sv.solve(mg.MG_ADD, oms[p], mg.MG_DLINEAR, 1e-8, 4000))
         return res
-    r, dt2 = wall(seq)
+    r, dt2 = _wall(torch, seq)
     bb["sequential"] = {"seconds": dt2, "all_ok": all(x[0] == mg.MG_OK for x in r)}
-    out["batched_256_definite"] = bb
     bt.close()
-    # (D) adjoint: forward + adjoint solve and gradients, 2D depth 6
+    return bb
+
+
+def form_adjoint(mg, torch):
+    """Forward and adjoint solves with the gradients of J (2D depth 6, the
+    definite companion E = 0 of the adjoint workload, tolerance 1e-10)."""
     from paper_1508_03954_gb300.adjoint import SolveOptions, far_field
     c = W.config5()
     E = 0.0  # definite companion (k^2 = -V)
     s = mg.Solver(2, 6, E - c["V"], c["theta"], c["layer_width"])
-    s.set_stream(stream.cuda_stream)
+    s.set_stream(torch.cuda.current_stream().cuda_stream)
     xyz, g = W.circle_samples(256)
     opts = SolveOptions(variant=mg.MG_ADD, transfer=mg.MG_DLINEAR, omega=mg.omega_scheme(mg.MG_OMEGA_EXP, 0.6, 6),
                         tol=1e-10, max_cycles=20000, precision=mg.MG_C64_REFINE, inner_cycles=INNER)
@@ -389,21 +585,47 @@ def measure_forms(mg, torch, peaks):
     fwd_bwd()
     V.grad = None
     f.grad = None
-    Jv, dt = wall(fwd_bwd)
-    out["adjoint_2d_depth6"] = {"J": Jv, "seconds_forward_backward": dt, "tol": 1e-10}
+    Jv, dt = _wall(torch, fwd_bwd)
     s.close()
-    for name, fn in [("csg_sweep", lambda: csg_sweep(mg, torch)),
-                     ("channel_table2", lambda: channel_table2(mg, torch)),
-                     ("four_d", lambda: four_d(mg, torch, peaks)),
-                     ("dimension_study", lambda: dimension_study(mg, torch)),
-                     ("adaptive", lambda: adaptive(mg, torch)),
-                     ("adaptive_3d", lambda: adaptive(mg, torch, d=3, depth=5, cycles=30)),
-                     ("channel_table2_adaptive", lambda: channel_table2_adaptive(mg, torch))]:
+    return {"J": Jv, "seconds_forward_backward": dt, "tol": 1e-10}
+
+
+def form_table(mg, torch, peaks):
+    """Every secondary form by name (each printed on a line of its own)."""
+    return {"cycle_2d_depth6": lambda: form_cycle_2d(mg, torch, peaks),
+            "configured_2d_depth6": lambda: form_configured_2d(mg, torch),
+            "time_to_1e-8_2d_depth6_definite": lambda: form_refine_2d(mg, torch),
+            "time_to_1e-8_3d_depth5_definite": lambda: form_refine_3d(mg, torch, peaks),
+            "batched_256_definite": lambda: form_batched(mg, torch),
+            "adjoint_2d_depth6": lambda: form_adjoint(mg, torch),
+            "csg_sweep": lambda: csg_sweep(mg, torch),
+            "channel_table2": lambda: channel_table2(mg, torch),
+            "four_d": lambda: four_d(mg, torch, peaks),
+            "dimension_study": lambda: dimension_study(mg, torch),
+            "adaptive": lambda: adaptive(mg, torch),
+            "adaptive_3d": lambda: adaptive(mg, torch, d=3, depth=5, cycles=30),
+            "channel_table2_adaptive": lambda: channel_table2_adaptive(mg, torch)}
+
+
+def run_forms(mg, torch, peaks, names, out_path=None):
+    """Run the named forms, each guarded (an exception is recorded as its
+    result), print each as one compact JSON line and optionally collect them
+    in a file.  Returns {name: seconds}."""
+    table = form_table(mg, torch, peaks)
+    collected, secs = {}, {}
+    for name in names:
+        t0 = time.perf_counter()
         try:
-            out[name] = fn()
-        except Exception as e:  # a failing secondary form must not cost the headline line
-            out[name] = {"error": f"{type(e).__name__}: {e}"}
-    return out
+            res = table[name]()
+        except Exception as e:  # a failing form must not cost the headline line
+            res = {"error": f"{type(e).__name__}: {e}"}
+        secs[name] = round(time.perf_counter() - t0, 2)
+        collected[name] = res
+        print(json.dumps({"form": name, "result": res}, separators=(",", ":")), flush=True)
+    if out_path:
+        with open(out_path, "w") as fh:
+            json.dump(collected, fh, indent=1)
+    return secs
 
 
 def csg_sweep(mg, torch, cycles=300):
@@ -739,18 +961,37 @@ def adaptive(mg, torch, d=2, depth=6, cycles=100):
 
 
 # ---------------------------------------------------------------- main
+FORMS_DEFAULT = ("cycle_2d_depth6", "configured_2d_depth6", "time_to_1e-8_2d_depth6_definite",
+                 "time_to_1e-8_3d_depth5_definite", "batched_256_definite", "adjoint_2d_depth6",
+                 "csg_sweep", "channel_table2", "four_d", "adaptive", "adaptive_3d")
+
+
+def headline_line(value, steps, warmup, total_ms, world, roofline, e2e, launches, clk, cpu=None):
+    """The one JSON line the run ends with (compact: a few hundred bytes of
+    numbers; every secondary form goes on a line of its own before it)."""
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
+            "warmup": warmup, "ms_per_step": total_ms / steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c128 (f64)", "data": "synthetic",
+            "config": workload_config(world), "roofline": roofline, "e2e": e2e,
+            "gpu_launches": launches, "clocks": clk}
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    return line
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
-    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--e2e-steps", type=int, default=200)
+    ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
-    ap.add_argument("--form", choices=["csg_sweep", "channel_table2", "four_d", "dimension_study", "adaptive",
-                                       "adaptive_3d", "channel_table2_adaptive"],
-                    default=None,
+    ap.add_argument("--forms", default=",".join(FORMS_DEFAULT),
+                    help="comma-separated secondary forms to run after the headline")
+    ap.add_argument("--forms-out", default=None, help="also write the forms' results to this JSON file")
+    ap.add_argument("--form", choices=sorted(form_table(None, None, {}).keys()), default=None,
                     help="run only this form and print its result (profiling)")
     ap.add_argument("--four-d-depth", type=int, default=4, help="depth of the four_d form (profiling)")
     args = ap.parse_args()
@@ -776,74 +1017,39 @@ def main():
     from paper_1508_03954_gb300 import mg
     B.build()
     mg.load()
+    peaks, peak_src = measured_peaks()
     if args.form is not None:
-        peaks, _ = measured_peaks()
-        fn = {"csg_sweep": lambda m, t: csg_sweep(m, t), "channel_table2": lambda m, t: channel_table2(m, t),
-              "four_d": lambda m, t: four_d(m, t, peaks, depth=args.four_d_depth),
-              "dimension_study": lambda m, t: dimension_study(m, t),
-              "adaptive": lambda m, t: adaptive(m, t),
-              "adaptive_3d": lambda m, t: adaptive(m, t, d=3, depth=5, cycles=30),
-              "channel_table2_adaptive": lambda m, t: channel_table2_adaptive(m, t)}[args.form]
-        print(json.dumps({"form": args.form, "result": fn(mg, torch)}), flush=True)
+        if args.form == "four_d":
+            res = four_d(mg, torch, peaks, depth=args.four_d_depth)
+        else:
+            res = form_table(mg, torch, peaks)[args.form]()
+        print(json.dumps({"form": args.form, "result": res}), flush=True)
         return
 
-    cfg = W.config2()
+    # headline: the 3D complex128 cycle (depth 5), one BPX cycle per step
+    cfg = W.config3()
     d, depth = cfg["d"], cfg["depth"]
     s = mg.Solver(d, depth, cfg["k2"], cfg["theta"], cfg["layer_width"])
     stream = torch.cuda.current_stream()
     s.set_stream(stream.cuda_stream)
-    f_dev = torch.from_numpy(cfg["f"]).cuda()
-    s.set_rhs(f_dev)
+    s.set_rhs(torch.from_numpy(cfg["f"]).cuda())
     omega = np.full(depth, 0.6)
     variant, transfer = mg.MG_BPX, mg.MG_HIERARCHICAL
     interior = (3 ** depth - 1) ** d
-
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
-    for _ in range(args.warmup):
-        s.cycle(variant, omega, transfer)
-    torch.cuda.synchronize()
-    s.get_stats()
-
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    clocks = ClockSampler(local_rank)
-    if dist is not None:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    for k in range(args.steps):
-        flush.fill_(float(k & 7))
-        starts[k].record(stream)
-        s.cycle(variant, omega, transfer)
-        ends[k].record(stream)
-    torch.cuda.synchronize()
-    if dist is not None:
-        dist.barrier()
-    clk = clocks.stop()
-    launches, _, _ = s.get_stats()
-    total_ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
+    total_ms, launches, clk = time_cycles(torch, s, variant, omega, transfer, args.steps, args.warmup,
+                                          flush, ClockSampler(local_rank), dist)
     total_ms = max_over_ranks(dist, total_ms, "cuda")
     value = whole_job_rate(interior, args.steps, world, total_ms)
 
-    # the dominant kernel alone: the same cycles with an event pair around the
-    # finest-level sweep (a separate pass, so the timed steps above run the
-    # whole cycle as one graph)
-    s.set_timing(True)
-    for _ in range(3):
-        s.cycle(variant, omega, transfer)
-    torch.cuda.synchronize()
-    s.get_stats()
-    for k in range(min(args.steps, 500)):
-        flush.fill_(float(k & 7))
-        s.cycle(variant, omega, transfer)
-    _, nsweeps, sweep_ms = s.get_stats()
-    s.set_timing(False)
+    # the dominant kernel alone: event pair around the fine sweep (separate pass)
+    sweep = fine_sweep_ms(torch, s, variant, omega, transfer, min(max(args.steps, 10), 100), flush)
 
-    # end to end through the public API with pinned host buffers
+    # end to end through the public API with page-locked host buffers
     u_h = torch.zeros(s.shape, dtype=torch.complex128).pin_memory()
     f_h = torch.from_numpy(cfg["f"]).pin_memory()
     out_h = torch.empty(s.shape, dtype=torch.complex128).pin_memory()
-    s.get_solution(u_h)
+    s.set_solution(u_h)
     e2e_ms = 0.0
     ne = max(1, args.e2e_steps)
     for k in range(ne + 3):
@@ -858,48 +1064,25 @@ def main():
         b.synchronize()
         if k >= 3:
             e2e_ms += a.elapsed_time(b)
-        u_h.copy_(out_h)
     e2e_value = whole_job_rate(interior, ne, world, max_over_ranks(dist, e2e_ms, "cuda"))
-
-    peaks, src = measured_peaks()
-    flops, nbytes = fine_sweep_counts(d, depth, cfg["layer_width"], bpx=True, omega_real=True)
-    sweep_s = (sweep_ms / max(nsweeps, 1)) / 1e3
-    achieved = flops / sweep_s
-    csrc = os.path.join(ROOT, "paper_1508_03954_gb300", "csrc")
-    # the files that define the timed kernel (tile step, persistent queue, launch)
-    traffic, sha = recorded_traffic("fine_sweep2_c128_2d_depth6",
-                                    [os.path.join(csrc, f) for f in FINE_SWEEP_SOURCES])
-    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": FP64_PEAK_FLOPS / 1e12,
-                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_FLOPS, "traffic": traffic,
-                "kernel": "sweep2p_kernel<8,256,double> (finest level, persistent LPT, FP64)",
-                "peak_source": "FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
-                "hbm": {"achieved_gbs": nbytes / sweep_s / 1e9, "peak_gbs": peaks.get("hbm_gbs"),
-                        "frac": nbytes / sweep_s / 1e9 / peaks.get("hbm_gbs", 6800.0),
-                        "peak_source": src},
-                "sweep_ms": sweep_ms / max(nsweeps, 1),
-                "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": nbytes,
-                "source_sha256_16": sha}
-
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "c128 (f64)", "data": "synthetic",
-            "config": workload_config(world),
-            "roofline": roofline,
-            "e2e": {"value": e2e_value, "unit": UNIT,
-                    "h2d_bytes_per_step": 2 * 16 * s.nv, "d2h_bytes_per_step": 16 * s.nv,
-                    "what": "mg_set_solution + mg_set_rhs from pinned host, mg_cycle, "
-                            "mg_get_solution to pinned host"},
-            "gpu_launches": launches, "clocks": clk}
-    if rank == 0 and world == 1 and not args.no_forms:
-        try:
-            line["forms"] = measure_forms(mg, torch, peaks)
-        except Exception as e:  # the headline line is printed regardless
-            line["forms"] = {"error": f"{type(e).__name__}: {e}"}
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_line(cfg)
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * 16 * s.nv,
+           "d2h_bytes_per_step": 16 * s.nv,
+           "what": "mg_set_solution + mg_set_rhs from pinned host, mg_cycle, mg_get_solution to pinned host"}
     s.close()
+
+    roofline = fine_sweep3_roofline(cfg, sweep, peaks, peak_src)
+    if rank == 0 and world == 1 and not args.no_forms:
+        names = [x for x in args.forms.split(",") if x]
+        run_forms(mg, torch, peaks, names, args.forms_out)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            cpu = cpu_baseline_line()
+        except Exception as e:
+            cpu = {"error": f"{type(e).__name__}: {e}"}
+    if rank == 0:
+        line = headline_line(value, args.steps, args.warmup, total_ms, world, roofline, e2e, launches, clk, cpu)
+        print(json.dumps(line, separators=(",", ":")), flush=True)
     if dist is not None:
         dist.destroy_process_group()
 

@@ -20,6 +20,7 @@
 #include "mg_sweep3d.cuh"
 #include "mg_sweep3s.cuh"
 #include "mg_defect3.cuh"
+#include "mg_sweep3sd.cuh"
 #include "mg_sweep2w.cuh"
 #include "mg_persist.cuh"
 #include "mg_adjoint.cuh"
@@ -84,6 +85,7 @@ struct Hier {
     unsigned long long realrow3 = 0;  // same for the 64 3D types
     unsigned long long realM = 0;     // bit t: mass row of type t is real
     bool g3ok = false;        // 3D Galerkin-row tables available
+    unsigned greal = 0;       // bit k: 1D Galerkin row class k is real (3D)
     // 2D FP64 path: Galerkin rows of G_{l-1} = R H_l P per coarse row class
     bool gok = false;
     int* order8 = nullptr;      // fine tiles (8 coarse cells) by decreasing cost
@@ -518,6 +520,11 @@ int build_hier(mg_ctx* c, Hier<R>& H) {
         }
         gt[ci] = (uint8_t)k;
       }
+      for (size_t k = 0; k < cls.size() && ok; ++k) {
+        bool re = true;
+        for (int j = 0; j < 6; ++j) re = re && cls[k][j].imag() == 0.0;
+        if (re) V.greal |= 1u << k;
+      }
       if (ok) {
         const int G = mg::kMaxG3;
         std::vector<cd> gc((size_t)G * G * G * 27, cd(0));
@@ -696,6 +703,7 @@ cudaError_t configure_kernels() {
   set((const void*)mg::sweep3_kernel<float, 7, 512>, mg::Tile3<float, 7>::smem_bytes);
   set((const void*)mg::sweep3_kernel<float, 4, 256>, mg::Tile3<float, 4>::smem_bytes);
   set((const void*)mg::sweep3s_kernel<2>, sizeof(mg::Sweep3sShared));
+  set((const void*)mg::sweep3sd_kernel, sizeof(mg::Sweep3sdShared));
   set((const void*)mg::defect3_kernel<float>, sizeof(mg::Defect3Shared<float>));
   set((const void*)mg::defect3_kernel<double>, sizeof(mg::Defect3Shared<double>));
   set((const void*)mg::chain2_kernel<256>, mg::Tile2<4>::smem_bytes);
@@ -984,6 +992,45 @@ cudaError_t launch_sweep3s(mg_ctx* c, Hier<float>& H, int l, bool fine, int hb, 
   return cudaGetLastError();
 }
 
+// Large complex128 3D levels: the separable z-marching sweep in FP64, one
+// block per SM over equal ranges of (tile, coarse plane) units.
+cudaError_t launch_sweep3sd(mg_ctx* c, Hier<double>& H, int l, bool fine, int hb, int hier, const cd& om) {
+  auto& V = H.lev[l];
+  mg::Sweep3sdArgs A;
+  std::memset(&A, 0, sizeof(A));
+  A.n = V.n;
+  A.fine = fine ? 1 : 0;
+  A.has_coarse = 1;
+  A.hb = hb;
+  A.hier = hier;
+  const int nc = V.n / 3;
+  A.tiles_x = (nc + 8) / 9;
+  A.nunits = (long long)A.tiles_x * A.tiles_x * nc;
+  A.u = fine ? V.u[H.cur] : V.u[0];
+  A.c = fine ? H.lev[l - 1].corr : nullptr;
+  A.b = V.b;
+  A.out = fine ? V.u[1 - H.cur] : V.t;
+  A.b_coarse = H.lev[l - 1].b;
+  A.u_coarse = H.lev[l - 1].u[0];
+  A.typ = V.typ;
+  A.gtyp = V.gtyp;
+  A.gcoef = V.gcoef;
+  A.greal = V.greal;
+  axis_rows(c, V.n, A.row);
+  for (size_t t = 0; t < V.diag.size() && t < 64; ++t) {
+    const cd q = om / V.diag[t];
+    A.omd[t] = cplx<double>{q.real(), q.imag()};
+  }
+  A.partial = H.partial;
+  A.ticket = H.ticket;
+  A.norm2 = fine ? H.norm2 : nullptr;
+  // fine levels: about four coarse planes per block at least (a range's first
+  // coarse step is overhead); coarse levels: every SM that has a unit
+  const long long upb = fine ? 4 : 1;
+  const long long grid = std::min<long long>(152, std::max<long long>(1, (A.nunits + upb - 1) / upb));
+  mg::sweep3sd_kernel<<<(int)grid, 512, sizeof(mg::Sweep3sdShared), c->stream>>>(A);
+  return cudaGetLastError();
+}
 
 // Large complex64 2D levels: the warp-strip sweep.
 cudaError_t launch_sweep2w(mg_ctx* c, Hier<float>& H, int l, bool fine, int hb, int hier, const cd& om) {
@@ -1024,9 +1071,11 @@ cudaError_t launch_sweep2w(mg_ctx* c, Hier<float>& H, int l, bool fine, int hb, 
 
 template <typename R>
 cudaError_t sweep3(mg_ctx* c, Hier<R>& H, int l, bool fine, int hb, int hier, const cd& om) {
-  if constexpr (std::is_same<R, float>::value) {
-    if (l > 1 && H.lev[l].n >= 27 && H.lev[l].g3ok && interior_real(c))
+  if (l > 1 && H.lev[l].n >= 27 && H.lev[l].g3ok && interior_real(c)) {
+    if constexpr (std::is_same<R, float>::value)
       return launch_sweep3s(c, H, l, fine, hb, hier, om);
+    else
+      return launch_sweep3sd(c, H, l, fine, hb, hier, om);
   }
   auto& V = H.lev[l];
   mg::Sweep3Args<R> A;

@@ -657,3 +657,63 @@ def test_poisson_analytic_discrete_solution_4d():
     for _ in range(60):
         H.cycle(om, O.ADD, O.DLINEAR)
     np.testing.assert_allclose(H.u.real, exact, rtol=0, atol=1e-8)
+
+
+def _sine_mode(d, n):
+    x = np.arange(n + 1) / n
+    s = np.ones((1,) * d)
+    for ax in range(d):
+        shape = [1] * d
+        shape[ax] = n + 1
+        s = s * np.sin(math.pi * x).reshape(shape)
+    return s
+
+
+def test_fmg_start_first_stage_is_one_jacobi_step_with_the_finest_factor():
+    """FMG (Section 5 remark, Section 7.1): with one cycle per stage on a
+    depth-2 Poisson problem, stage 1 is a single level, i.e. one damped
+    Jacobi step from zero with the factor the finest level of the full
+    hierarchy has (reading 9: level l of stage s takes omega[l - 1 + L - s]);
+    its rhs is the closed-form 2D Q1 mass stencil h^2/36 [1 4 1]^2 applied to
+    f sampled at the level-1 vertices, its diagonal the Q1 stiffness centre
+    8/3.  The stage-2 start is P of that step.  Distinct factors per level
+    catch a wrong factor slice; f sampled anywhere but at every third fine
+    vertex changes b_1."""
+    d, depth = 2, 2
+    n = 3 ** depth
+    f = d * math.pi ** 2 * _sine_mode(d, n)
+    om = np.array([0.3, 0.7])
+    hs = O.fmg_start(d, depth, np.zeros((n + 1,) * d), 0.0, 0.0, f.astype(complex), om, O.ADD, O.DLINEAR,
+                     cycles_per_stage=1)
+    h = 1 / 3
+    f1 = f[::3, ::3]
+    w = np.array([1.0, 4.0, 1.0])
+    b1 = np.zeros((4, 4))
+    for i in (1, 2):
+        for j in (1, 2):
+            b1[i, j] = h * h / 36 * sum(w[a] * w[b] * f1[i - 1 + a, j - 1 + b] for a in range(3) for b in range(3))
+    u1 = om[1] * b1 / (8.0 / 3.0)
+    np.testing.assert_allclose(hs.u, O.prolong(u1.astype(complex)), rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("d,depth", [(2, 4), (3, 3)])
+def test_fmg_start_is_the_prolongated_discrete_solution_of_the_coarser_stage(d, depth):
+    """FMG with every stage solved (Poisson, Section 7.1 rhs, theta = 0,
+    phi = 0): the start handed to the finest stage is P applied to the
+    discrete solution of level L - 1, which is pi^2 (mu / kappa) prod sin(pi x)
+    at h = 3^-(L - 1) in 2D (mode (1,..,1) diagonalises K and M; the 3D
+    analogue divides by the sum over axes).  A wrong stage count, a wrong f
+    sampling or a missing prolongation moves the start by far more than the
+    tolerance."""
+    n = 3 ** depth
+    f = d * math.pi ** 2 * _sine_mode(d, n)
+    om = O.omega_scheme(O.UCG, 0.8 if d == 2 else 0.6, depth)
+    hs = O.fmg_start(d, depth, np.zeros((n + 1,) * d), 0.0, 0.0, f.astype(complex), om, O.ADD,
+                     O.HIERARCHICAL, cycles_per_stage=250)
+    m = 3 ** (depth - 1)
+    h = 1 / m
+    kap = (2 / h) * (1 - math.cos(math.pi * h))
+    mu = (h / 3) * (2 + math.cos(math.pi * h))
+    # H s = d kappa mu^(d-1) s and M s = mu^d s for the sine mode s
+    exact = d * math.pi ** 2 * mu ** d / (d * kap * mu ** (d - 1)) * _sine_mode(d, m)
+    np.testing.assert_allclose(hs.u, O.prolong(exact.astype(complex)), rtol=0, atol=1e-9)

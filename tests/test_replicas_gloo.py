@@ -57,9 +57,12 @@ def test_reference_arm_other_ranks_do_no_work(capsys):
     assert capsys.readouterr().out == ""
 
 
-def test_reference_arm_line_shape(capsys):
+def test_reference_arm_line_shape(capsys, monkeypatch):
     class A:
         steps, warmup, gpus = 2, 3, 1
+    # the depth-3 instance on two spawned oracle processes keeps this quick
+    monkeypatch.setattr(bench, "ORACLE_CYCLE_S", {5: 1e9, 4: 1e9, 3: 0.13})
+    monkeypatch.setattr(bench, "host_cores", lambda: 2)
     bench.run_reference(A, rank=0)
     line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
     assert line["impl"] == "reference"
@@ -67,3 +70,24 @@ def test_reference_arm_line_shape(capsys):
     assert line["config"] == bench.workload_config(1)
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
+
+
+def test_headline_line_is_compact_and_complete():
+    """The line the run ends with stays a few KB (a driver keeps only the
+    tail of stdout) and carries the contract's keys."""
+    roof = {"bound": "alu", "achieved": 1.0, "peak": 1.259, "unit": "TFLOP/s", "frac": 0.8, "traffic": None,
+            "kernel": "k" * 60, "peak_source": "p" * 80, "sweep_ms": 1.0, "algorithmic_flops_per_launch": 1e9,
+            "algorithmic_bytes_per_launch": 7e8, "hbm": {"achieved_gbs": 1.0, "peak_gbs": 6700.0, "frac": 0.1,
+                                                         "peak_source": "measured"}, "source_sha256_16": "0" * 16}
+    e2e = {"value": 1e9, "unit": bench.UNIT, "h2d_bytes_per_step": 1, "d2h_bytes_per_step": 1, "what": "w" * 100}
+    cpu = {"value": 1e6, "unit": bench.UNIT, "cores": 72, "kind": "oracle", "sample": "s" * 300,
+           "single_core": {"value": 1e5, "cores": 1}}
+    clk = {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 100}
+    line = bench.headline_line(3.1e9, 20, 5, 80.0, 1, roof, e2e, 400, clk, cpu)
+    txt = json.dumps(line, separators=(",", ":"))
+    assert len(txt) < 4096
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "roofline", "e2e", "gpu_launches", "clocks",
+              "cpu_baseline"):
+        assert k in line
+    assert line["ms_per_step"] == 4.0 and "forms" not in line

@@ -1,0 +1,110 @@
+"""Parity of the separable complex128 3D sweep (levels with 27 or more cells
+per axis) with the FP64 oracle, through the C ABI.
+
+Per-iterate relative L2 against the oracle within 1e-12 (the complex128
+contract) over several cycles, every variant and transfer, at depths 3 and 4
+(the finest level and its coarse levels run the separable kernel; the tiles
+of 9 coarse cells leave a ragged last tile at both depths), with layers that
+make some, none or all axis rows complex, real and complex relaxation
+factors.  At the full 3D size (depth 5, 14.5 M vertices) the oracle's two
+iterates are stored at 1024 seeded sample vertices (written by
+tests/golden/make_config3_samples.py, which calls only the oracle).
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1508_03954_gb300 import build as B
+from paper_1508_03954_gb300 import mg
+from paper_1508_03954_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+TH = math.pi / 6
+VARIANTS = [  # (library variant, library transfer, oracle variant, oracle transfer)
+    (mg.MG_ADD, mg.MG_DLINEAR, O.ADD, O.DLINEAR),
+    (mg.MG_HB, mg.MG_DLINEAR, O.HB, O.DLINEAR),
+    (mg.MG_BPX, mg.MG_HIERARCHICAL, O.ADD, O.HIERARCHICAL),
+    (mg.MG_HB, mg.MG_HIERARCHICAL, O.HB, O.HIERARCHICAL),
+]
+IDS = ["add", "hb", "bpx", "hb-hier"]
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "config3_oracle_samples.txt")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    B.build()
+    mg.load()
+
+
+def rel_l2(a, b):
+    den = np.linalg.norm(np.ravel(b))
+    return np.linalg.norm(np.ravel(a) - np.ravel(b)) / (den if den > 0 else 1.0)
+
+
+def run(depth, w, k2, var, omega, cycles, seed):
+    f = W.random_complex(3, depth, seed)
+    u0 = W.random_complex(3, depth, seed + 1)
+    g = mg.Solver(3, depth, W.constant_k2(3, depth, k2), TH, w)
+    o = O.Hierarchy(3, depth, W.constant_k2(3, depth, k2), TH, w)
+    g.set_rhs(f)
+    o.set_rhs_nodal(f)
+    g.set_solution(u0)
+    o.set_solution(u0)
+    worst = 0.0
+    for n in range(cycles):
+        g.cycle(var[0], omega, var[1])
+        o.cycle(omega, var[2], var[3])
+        e = rel_l2(g.get_solution(), o.u)
+        worst = max(worst, e)
+        assert e <= TOL, f"iterate {n + 1}: rel L2 {e:.3e}"
+        # the fused norm of the iterate that entered this cycle
+    a_g, _ = g.residual_norm()
+    a_o, _ = o.residual_norm()
+    assert abs(a_g - a_o) <= 1e-12 * a_o
+    g.close()
+    return worst
+
+
+@pytest.mark.parametrize("var", VARIANTS, ids=IDS)
+@pytest.mark.parametrize("w", [0.1, 0.5, 0.0], ids=["layer", "all-scaled", "no-layer"])
+def test_depth3_iterates(var, w):
+    run(3, w, -30.0 if w == 0.0 else 40.0, var, np.array([0.5, 0.6 + 0.05j, 0.7]), 4, 100)
+
+
+@pytest.mark.parametrize("var", VARIANTS, ids=IDS)
+@pytest.mark.parametrize("omega", [np.array([0.55, 0.6, 0.6, 0.65]),
+                                   np.array([0.5 - 0.02j, 0.6, 0.6 + 0.03j, 0.65 - 0.01j])], ids=["real", "complex"])
+def test_depth4_iterates(var, omega):
+    run(4, 0.1, 25.0, var, omega, 2, 200)
+
+
+def test_config3_full_size_iterates_match_stored_oracle_samples():
+    """Full-size 3D workload: two BPX cycles from the stored seeded start;
+    the iterates at the oracle's sample vertices and the residual norms."""
+    with open(GOLDEN) as fh:
+        head = json.loads(fh.readline()[2:])
+        rows = np.loadtxt(fh, comments="#")
+    flat = rows[:, 0].astype(np.int64)
+    u1 = rows[:, 1] + 1j * rows[:, 2]
+    u2 = rows[:, 3] + 1j * rows[:, 4]
+    c = W.config3(head["depth"])
+    g = mg.Solver(3, head["depth"], c["k2"], c["theta"], c["layer_width"])
+    g.set_rhs(c["f"])
+    g.set_solution(W.random_complex(3, head["depth"], 7) * 1e-3)
+    a0, _ = g.residual_norm()
+    norms = head["residual_norms"]
+    assert abs(a0 - norms[0]) <= 1e-12 * norms[0]
+    om = np.full(head["depth"], head["omega"])
+    for k, ref in enumerate((u1, u2)):
+        g.cycle(mg.MG_BPX, om, mg.MG_HIERARCHICAL)
+        u = np.ravel(g.get_solution())[flat]
+        assert rel_l2(u, ref) <= TOL, (k, rel_l2(u, ref))
+        a, _ = g.residual_norm()
+        assert abs(a - norms[k + 1]) <= 1e-12 * norms[k + 1], (k, a, norms[k + 1])
+    g.close()
