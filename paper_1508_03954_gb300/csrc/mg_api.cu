@@ -86,6 +86,7 @@ struct Hier {
     unsigned long long realM = 0;     // bit t: mass row of type t is real
     bool g3ok = false;        // 3D Galerkin-row tables available
     unsigned greal = 0;       // bit k: 1D Galerkin row class k is real (3D)
+    unsigned* s3pref = nullptr; // 3D FP64 separable sweep: prefix sums of the unit costs
     // 2D FP64 path: Galerkin rows of G_{l-1} = R H_l P per coarse row class
     bool gok = false;
     int* order8 = nullptr;      // fine tiles (8 coarse cells) by decreasing cost
@@ -547,6 +548,30 @@ int build_hier(mg_ctx* c, Hier<R>& H) {
         MG_CUDA(c, cudaMemcpy(V.gcoef, gcd.data(), gcd.size() * sizeof(cplx<R>), cudaMemcpyHostToDevice));
         V.g3ok = true;
       }
+    }
+    if (std::is_same<R, double>::value && d == 3 && !H.varphi && l > 1 && V.n >= 27 && V.g3ok) {
+      // FP64 cost of each (9 x 9 coarse-cell tile, coarse plane) unit of the
+      // separable sweep, in FP64 operations per lane: z-pair on the 32 box
+      // rows (10 real, 24 complex), y-pair (16 / 36), x-pass (12 / 26) and the
+      // rest (~30) on the 30 residual rows; blocks take ranges of equal cost
+      const int n = V.n, nc = n / 3, tl = (nc + 8) / 9;
+      std::vector<unsigned> pref((size_t)tl * tl * nc + 1, 0u);
+      size_t u = 0;
+      for (int t = 0; t < tl * tl; ++t) {
+        const int x0 = (t % tl) * 27, y0 = (t / tl) * 27;
+        bool xc = false;
+        for (int g = x0 - 2; g <= x0 + 27; ++g) xc = xc || (g >= 0 && g <= n && typ[g] != 0);
+        int yc = 0;
+        for (int g = y0 - 2; g <= y0 + 27; ++g) yc += (g >= 0 && g <= n && typ[g] != 0) ? 1 : 0;
+        for (int Z = 0; Z < nc; ++Z, ++u) {
+          unsigned cost = 0;
+          for (int z = 3 * Z; z < 3 * Z + 3; ++z)
+            cost += 32u * (typ[z] != 0 ? 24u : 10u) + 30u * (58u + (xc ? 14u : 0u)) + 20u * (unsigned)yc;
+          pref[u + 1] = pref[u] + cost;
+        }
+      }
+      if ((rc = dalloc(c, H, (void**)&V.s3pref, pref.size() * sizeof(unsigned))) != MG_OK) return rc;
+      MG_CUDA(c, cudaMemcpy(V.s3pref, pref.data(), pref.size() * sizeof(unsigned), cudaMemcpyHostToDevice));
     }
     if (d == 2 && !H.varphi && V.n / 3 + 1 >= 200) {
       // LPT order of the 8-coarse-cell tiles: interior vertices weighted by
@@ -1016,6 +1041,7 @@ cudaError_t launch_sweep3sd(mg_ctx* c, Hier<double>& H, int l, bool fine, int hb
   A.gtyp = V.gtyp;
   A.gcoef = V.gcoef;
   A.greal = V.greal;
+  A.upref = V.s3pref;
   axis_rows(c, V.n, A.row);
   for (size_t t = 0; t < V.diag.size() && t < 64; ++t) {
     const cd q = om / V.diag[t];

@@ -33,8 +33,9 @@
 // planes; lane = x and warp w holds rows 2w, 2w+1 of the 32 x 32 box of fine
 // columns [x0-3, x0+28] x [y0-3, y0+28], marching z with u(z-1), u(z), u(z+1)
 // in registers.  The residual box is [x0-2, x0+27]^2.  One barrier per fine
-// plane; the (tile, coarse plane) units are split into equal contiguous
-// ranges, one block per SM.  Level sizes stay below 2^31 vertices.
+// plane; the (tile, coarse plane) units are split into contiguous ranges of
+// equal FP64 cost (tabulated on the host: units with scaled rows cost more),
+// one block per SM.  Level sizes stay below 2^31 vertices.
 #pragma once
 #include "mg_kernels.cuh"
 #include "mg_sweep3s.cuh"
@@ -46,6 +47,7 @@ struct Sweep3sdArgs {
   int n, fine, has_coarse, hb, hier;
   int tiles_x;              // x-y tiles per axis (9 coarse cells each)
   long long nunits;         // tiles_x^2 * (n / 3)
+  const unsigned* upref;    // prefix sums of the unit costs, nunits + 1 entries
   const cplx<double>* u;    // fine: pending U; coarse: u_l
   const cplx<double>* c;    // pending correction on level l-1 (fine only; may be null)
   const cplx<double>* b;
@@ -72,6 +74,7 @@ struct Sweep3sdShared {
   cplx<double> dc[10][10];     // du at the c-points of the last c-plane
   cplx<double> q[3][11][11];   // u at the c-points of three c-planes, C0-1 .. C0+9
   cplx<double> cc[12][12];     // one coarse plane of the pending correction, C0-1 .. C0+10
+  cplx<double> ccx[12][32];    // that plane interpolated along x to the box's columns
   cplx<double> cxy[2][32][32]; // P c at this column on the two coarse planes bracketing z + 1
   cplx<double> pidp[32][32];   // BPX: P I du of the previous c-plane at this column
   cplx<double> pu[32][32];     // U(z + 1), copied asynchronously one step ahead
@@ -156,9 +159,19 @@ __global__ void __launch_bounds__(512, 1) sweep3sd_kernel(const Sweep3sdArgs A) 
   const bool xr_act = lane < 20;
   double nrm = 0.0;
 
+  // this block's units: those whose prefix cost lies in [W b / B, W (b+1) / B)
   const long long U = A.nunits;
-  int unit = (int)(U * blockIdx.x / gridDim.x);
-  const int uend = (int)(U * (blockIdx.x + 1) / gridDim.x);
+  const unsigned long long Wt = A.upref[U];
+  auto first_at = [&](unsigned long long target) -> int {
+    long long lo = 0, hi = U;  // first i in [0, U] with upref[i] >= target
+    while (lo < hi) {
+      const long long mid = (lo + hi) >> 1;
+      if ((unsigned long long)__ldg(A.upref + mid) >= target) hi = mid; else lo = mid + 1;
+    }
+    return (int)lo;
+  };
+  int unit = first_at(Wt * blockIdx.x / gridDim.x);
+  const int uend = first_at(Wt * (blockIdx.x + 1) / gridDim.x);
   while (unit < uend) {
     const int tile = unit / nc, Z0 = unit % nc;
     const int Z1 = min(nc, Z0 + (uend - unit));
@@ -168,7 +181,8 @@ __global__ void __launch_bounds__(512, 1) sweep3sd_kernel(const Sweep3sdArgs A) 
     const int gx = x0 - 3 + lane;
     const bool lastx = C0x + 9 >= nc, lasty = C0y + 9 >= nc;
     const int tx = (gx >= 0 && gx <= n) ? (int)A.typ[gx] : 0;
-    const bool xreal = __all_sync(0xffffffffu, tx == 0);
+    // only the residual box (lanes 1..30) takes x-rows
+    const bool xreal = __all_sync(0xffffffffu, tx == 0 || lane == 0 || lane == 31);
     int gy[RPT], col[RPT], ty[RPT];
     bool colin[RPT], owncol[RPT], yreal[RPT];
 #pragma unroll
@@ -204,10 +218,21 @@ __global__ void __launch_bounds__(512, 1) sweep3sd_kernel(const Sweep3sdArgs A) 
                  ? ldg_c(A.c + (Zc * NNc + cy * Nc + cx))
                  : cz<double>();
     };
-    // bilinear interpolation of the coarse plane in S.cc to column (lane, box row r)
+    // the coarse plane in S.cc interpolated separably: along x to the box's
+    // lanes by 384 threads (S.ccx), then along y per column
+    auto xint_cc = [&]() {
+      if (threadIdx.x < 384) {
+        const int jy = threadIdx.x >> 5, jx = lane / 3;
+        const double wx1 = w1(ox), wx0 = 1.0 - wx1;
+        const C a = S.cc[jy][jx], b2 = S.cc[jy][jx + 1];
+        S.ccx[jy][lane] = C{fma(wx1, b2.x, wx0 * a.x), fma(wx1, b2.y, wx0 * a.y)};
+      }
+    };
     auto bil_cc = [&](int r) -> C {
-      const int jx = lane / 3, jy = by[r] / 3;
-      return bil(oy[r], S.cc[jy][jx], S.cc[jy][jx + 1], S.cc[jy + 1][jx], S.cc[jy + 1][jx + 1]);
+      const int jy = by[r] / 3;
+      const double wy1 = w1(oy[r]), wy0 = 1.0 - wy1;
+      const C a = S.ccx[jy][lane], c2 = S.ccx[jy + 1][lane];
+      return C{fma(wy1, c2.x, wy0 * a.x), fma(wy1, c2.y, wy0 * a.y)};
     };
 
     __syncthreads();  // the previous range's shared memory is free
@@ -224,10 +249,14 @@ __global__ void __launch_bounds__(512, 1) sweep3sd_kernel(const Sweep3sdArgs A) 
     if (use_c) {
       if (threadIdx.x < 144) S.cc[threadIdx.x / 12][threadIdx.x % 12] = ld_cc(Z0 - 1);
       __syncthreads();
+      xint_cc();
+      __syncthreads();
 #pragma unroll
       for (int r = 0; r < RPT; ++r) cxy0[32 * r] = bil_cc(r);
       __syncthreads();
       if (threadIdx.x < 144) S.cc[threadIdx.x / 12][threadIdx.x % 12] = ld_cc(Z0);
+      __syncthreads();
+      xint_cc();
       __syncthreads();
 #pragma unroll
       for (int r = 0; r < RPT; ++r) cxy1[32 * r] = bil_cc(r);
@@ -382,6 +411,7 @@ __global__ void __launch_bounds__(512, 1) sweep3sd_kernel(const Sweep3sdArgs A) 
       __syncthreads();
       // phase 2: deferred work of plane z - 1; coarse correction plane for the next steps
       if (z > zs) deferred(IC<(OZ + 2) % 3>{}, z - 1);
+      if (OZP == 2 && use_c) xint_cc();  // S.cc was refilled before the barrier
       if (OZP == 0 && use_c) {
 #pragma unroll
         for (int r = 0; r < RPT; ++r) cxy1[32 * r] = bil_cc(r);
