@@ -1050,9 +1050,9 @@ cudaError_t launch_sweep3sd(mg_ctx* c, Hier<double>& H, int l, bool fine, int hb
   A.partial = H.partial;
   A.ticket = H.ticket;
   A.norm2 = fine ? H.norm2 : nullptr;
-  // fine levels: about four coarse planes per block at least (a range's first
-  // coarse step is overhead); coarse levels: every SM that has a unit
-  const long long upb = fine ? 4 : 1;
+  // at least two coarse planes per block: a range starts with two fine
+  // planes of overhead (the restriction's lower halo)
+  const long long upb = fine ? 4 : 2;
   const long long grid = std::min<long long>(152, std::max<long long>(1, (A.nunits + upb - 1) / upb));
   mg::sweep3sd_kernel<<<(int)grid, 512, sizeof(mg::Sweep3sdShared), c->stream>>>(A);
   return cudaGetLastError();
@@ -1097,11 +1097,16 @@ cudaError_t launch_sweep2w(mg_ctx* c, Hier<float>& H, int l, bool fine, int hb, 
 
 template <typename R>
 cudaError_t sweep3(mg_ctx* c, Hier<R>& H, int l, bool fine, int hb, int hier, const cd& om) {
-  if (l > 1 && H.lev[l].n >= 27 && H.lev[l].g3ok && interior_real(c)) {
-    if constexpr (std::is_same<R, float>::value)
-      return launch_sweep3s(c, H, l, fine, hb, hier, om);
-    else
-      return launch_sweep3sd(c, H, l, fine, hb, hier, om);
+  if (l > 1 && H.lev[l].g3ok && interior_real(c)) {
+    // complex64: the separable sweep from 27 cells per axis; complex128: from
+    // 27 on the finest level, from 81 on coarse levels (a 27-cell level has
+    // nine units of the separable layout, too few for the FP64 pipes of the
+    // GPU: within a cycle the small-tile sweep is faster there)
+    if constexpr (std::is_same<R, float>::value) {
+      if (H.lev[l].n >= 27) return launch_sweep3s(c, H, l, fine, hb, hier, om);
+    } else {
+      if (H.lev[l].n >= (fine ? 27 : 81)) return launch_sweep3sd(c, H, l, fine, hb, hier, om);
+    }
   }
   auto& V = H.lev[l];
   mg::Sweep3Args<R> A;
