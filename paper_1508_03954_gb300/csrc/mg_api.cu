@@ -1,6 +1,7 @@
 // mg_api.cu -- C ABI of the GB300 additive multilevel Helmholtz solver
 // (declarations and argument contracts in include/mg.h).
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <array>
@@ -549,11 +550,12 @@ int build_hier(mg_ctx* c, Hier<R>& H) {
         V.g3ok = true;
       }
     }
-    if (std::is_same<R, double>::value && d == 3 && !H.varphi && l > 1 && V.n >= 27 && V.g3ok) {
-      // FP64 cost of each (9 x 9 coarse-cell tile, coarse plane) unit of the
-      // separable sweep, in FP64 operations per lane: z-pair on the 32 box
-      // rows (10 real, 24 complex), y-pair (16 / 36), x-pass (12 / 26) and the
-      // rest (~30) on the 30 residual rows; blocks take ranges of equal cost
+    if (d == 3 && !H.varphi && l > 1 && V.n >= 27 && V.g3ok) {
+      // cost of each (9 x 9 coarse-cell tile, coarse plane) unit of the
+      // separable sweeps, in floating-point operations per lane: z-pair on the
+      // 32 box rows (10 real, 24 complex), y-pair (16 / 36), x-pass (12 / 26)
+      // and the rest (~30) on the 30 residual rows; blocks take ranges of
+      // equal cost
       const int n = V.n, nc = n / 3, tl = (nc + 8) / 9;
       std::vector<unsigned> pref((size_t)tl * tl * nc + 1, 0u);
       size_t u = 0;
@@ -727,7 +729,7 @@ cudaError_t configure_kernels() {
   set((const void*)mg::sweep3_kernel<double, 4, 256>, mg::Tile3<double, 4>::smem_bytes);
   set((const void*)mg::sweep3_kernel<float, 7, 512>, mg::Tile3<float, 7>::smem_bytes);
   set((const void*)mg::sweep3_kernel<float, 4, 256>, mg::Tile3<float, 4>::smem_bytes);
-  set((const void*)mg::sweep3s_kernel<2>, sizeof(mg::Sweep3sShared));
+  set((const void*)mg::sweep3s_kernel<2>, sizeof(mg::Sweep3sShared) + 128);
   set((const void*)mg::sweep3sd_kernel, sizeof(mg::Sweep3sdShared));
   set((const void*)mg::defect3_kernel<float>, sizeof(mg::Defect3Shared<float>));
   set((const void*)mg::defect3_kernel<double>, sizeof(mg::Defect3Shared<double>));
@@ -977,8 +979,44 @@ void axis_rows(const mg_ctx* c, int n, T row[4][9]) {
   }
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library); null when the driver does not provide it.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// Tensor map of a 3D level array ((n+1)^3 complex values of T, x fastest) as
+// 2(n+1) x (n+1) x (n+1) reals, with boxes of bw complex columns, 32 rows and
+// one plane; elements outside the array read as zero.  Row and plane strides
+// are multiples of 16 bytes because n + 1 is even (n = 3^l).
+template <typename T>
+bool plane_map(CUtensorMap* m, const void* base, int n, int bw) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (enc == nullptr) return false;
+  const cuuint64_t N = (cuuint64_t)n + 1;
+  const cuuint64_t dims[3] = {2 * N, N, N};
+  const cuuint64_t strides[2] = {2 * N * sizeof(T), 2 * N * N * sizeof(T)};
+  const cuuint32_t box[3] = {(cuuint32_t)(2 * bw), 32u, 1u};
+  const cuuint32_t es[3] = {1u, 1u, 1u};
+  const CUtensorMapDataType ty = sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+  return enc(m, ty, 3, const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // Large complex64 3D levels: the separable z-marching sweep, one block per SM
-// over equal ranges of (tile, coarse plane) units.
+// over ranges of (tile, coarse plane) units of equal cost.
 cudaError_t launch_sweep3s(mg_ctx* c, Hier<float>& H, int l, bool fine, int hb, int hier, const cd& om) {
   auto& V = H.lev[l];
   mg::Sweep3sArgs A;
@@ -1008,12 +1046,19 @@ cudaError_t launch_sweep3s(mg_ctx* c, Hier<float>& H, int l, bool fine, int hb, 
   A.partial = H.partial;
   A.ticket = H.ticket;
   A.norm2 = fine ? H.norm2 : nullptr;
+  A.upref = V.s3pref;
+  A.spin_limit = c->spin_limit;
+  A.err = c->dev_err;
+  // the u and b planes come in by TMA: 34-column boxes of 32 rows
+  CUtensorMap tmU, tmB;
+  if (!plane_map<float>(&tmU, A.u, V.n, mg::kS3BoxW) || !plane_map<float>(&tmB, A.b, V.n, mg::kS3BoxW))
+    return cudaErrorNotSupported;
   // fine levels: about four coarse planes per block at least (a range's first
   // coarse step is overhead); coarse levels: every SM that has a unit
   const long long upb = fine ? 4 : 1;
   const long long grid = std::min<long long>(152, std::max<long long>(1, (A.nunits + upb - 1) / upb));
   // two box rows per thread (four: 255 registers, 8 warps per SM, 17% slower)
-  mg::sweep3s_kernel<2><<<(int)grid, 512, sizeof(mg::Sweep3sShared), c->stream>>>(A);
+  mg::sweep3s_kernel<2><<<(int)grid, 512, sizeof(mg::Sweep3sShared) + 128, c->stream>>>(A, tmU, tmB);
   return cudaGetLastError();
 }
 

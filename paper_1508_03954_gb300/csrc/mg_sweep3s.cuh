@@ -26,12 +26,24 @@
 // restriction of the owned coarse vertices and for the c-point Jacobi update
 // of the next tile's first c-point (BPX).  One barrier per fine plane.
 //
+// Plane staging by TMA.  The u and b planes of the box come into shared
+// memory as tensor-map box loads (mg_tma.cuh): rings of four planes, each
+// slot with an mbarrier that the load completes.  Thread 0 issues u(z + 3)
+// and b(z + 2) at fine step z (the slots they overwrite were last read before
+// the previous step's barrier); every thread waits (bounded) for u(z + 1)
+// and b(z).  The hardware zero-fills what lies outside the level array, so
+// the loads carry no per-thread address or bounds work.  A box starts on an
+// even column (16-byte rule for the x coordinate), so it is 34 columns wide
+// and the tile's columns sit at offset 0 or 1.
+//
 // Work split.  The (tile, coarse plane) units of the level are split into
-// gridDim.x contiguous ranges of equal size (one block per SM), so the load
-// is balanced to one coarse plane; a range may continue into the next tile.
+// gridDim.x contiguous ranges of equal cost (tabulated on the host: units
+// with scaled rows cost more; one block per SM); a range may continue into
+// the next tile.
 #pragma once
 #include "mg_kernels.cuh"
 #include "mg_sweep3d.cuh"
+#include "mg_tma.cuh"
 
 namespace mg {
 
@@ -40,6 +52,9 @@ struct Sweep3sArgs {
   int n, fine, first, has_coarse, hb, hier;
   int tiles_x;          // x-y tiles per axis (9 coarse cells each)
   long long nunits;     // tiles_x^2 * (n / 3)
+  const unsigned* upref;    // prefix sums of the unit costs, nunits + 1 entries
+  unsigned spin_limit;      // polls before a plane wait gives up
+  unsigned* err;            // sticky error flag (bit 2: a plane wait gave up)
   const cplx<float>* u;     // fine: pending U; coarse: u_l
   const cplx<float>* c;     // pending correction on level l-1 (fine, may be null)
   const cplx<float>* b;
@@ -57,7 +72,14 @@ struct Sweep3sArgs {
   double* norm2;
 };
 
+constexpr int kS3Ring = 4;   // planes of u and of b in flight
+constexpr int kS3BoxW = 34;  // box columns (start rounded down to an even column)
+constexpr unsigned kS3PlaneBytes = 32u * kS3BoxW * 8u;  // 8704 = 68 x 128
+
 struct Sweep3sShared {
+  cplx<float> ub[kS3Ring][32][kS3BoxW];  // TMA destinations (128-byte aligned)
+  cplx<float> bb[kS3Ring][32][kS3BoxW];
+  unsigned long long bar_u[kS3Ring], bar_b[kS3Ring];
   cplx<float> za[2][32][32];  // M_z u of the plane (two planes in flight)
   cplx<float> zb[2][32][32];  // (K_z - phi M_z) u
   cplx<float> pv[3][32][32];  // BPX: u + du of the fine planes waiting for P I du
@@ -121,17 +143,29 @@ template <int O> __device__ __forceinline__ constexpr float W1() {
 // rows from shared memory, and 128 registers hold both columns' state (one
 // row per thread at 1024 threads was 15% slower and spilled at 64 registers).
 template <int RPT>
-__global__ void __launch_bounds__(32 * (32 / RPT), 1) sweep3s_kernel(const Sweep3sArgs A) {
+__global__ void __launch_bounds__(32 * (32 / RPT), 1)
+    sweep3s_kernel(const Sweep3sArgs A, const __grid_constant__ CUtensorMap tmU,
+                   const __grid_constant__ CUtensorMap tmB) {
   constexpr int NTHR = 32 * (32 / RPT), NW = 32 / RPT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double s_red[NTHR / 32];
-  Sweep3sShared& S = *reinterpret_cast<Sweep3sShared*>(smem_raw);
+  // TMA destinations need 128-byte alignment: the launch adds 128 bytes
+  Sweep3sShared& S = *reinterpret_cast<Sweep3sShared*>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
   using C = cplx<float>;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int n = A.n, N = n + 1, nc = n / 3;
   const int NN = N * N, Nc = nc + 1, NNc = Nc * Nc;  // level sizes stay below 2^31 vertices
   for (int i = threadIdx.x; i < 36; i += NTHR) S.row[i / 9][i % 9] = A.row[i / 9][i % 9];
   for (int i = threadIdx.x; i < 64; i += NTHR) S.omd[i] = A.omd[i];
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < kS3Ring; ++k) {
+      mbar_init(&S.bar_u[k], 1);
+      mbar_init(&S.bar_b[k], 1);
+    }
+    fence_mbar_init();
+  }
+  __syncthreads();
+  unsigned ph_u = 0, ph_b = 0;  // parity of the next wait, one bit per slot
   const bool zero_u = A.fine && A.first;
   const bool use_c = A.fine && !A.first && A.c != nullptr;
   const bool bpx = A.hier && !A.hb;
@@ -160,9 +194,19 @@ __global__ void __launch_bounds__(32 * (32 / RPT), 1) sweep3s_kernel(const Sweep
   }
   float nrm = 0.f;
 
+  // this block's units: those whose prefix cost lies in [W b / B, W (b+1) / B)
   const long long U = A.nunits;
-  int unit = (int)(U * blockIdx.x / gridDim.x);
-  const int uend = (int)(U * (blockIdx.x + 1) / gridDim.x);
+  const unsigned long long Wt = A.upref[U];
+  auto first_at = [&](unsigned long long target) -> int {
+    long long lo = 0, hi = U;  // first i in [0, U] with upref[i] >= target
+    while (lo < hi) {
+      const long long mid = (lo + hi) >> 1;
+      if ((unsigned long long)__ldg(A.upref + mid) >= target) hi = mid; else lo = mid + 1;
+    }
+    return (int)lo;
+  };
+  int unit = first_at(Wt * blockIdx.x / gridDim.x);
+  const int uend = first_at(Wt * (blockIdx.x + 1) / gridDim.x);
   while (unit < uend) {
     const int tile = unit / nc, Z0 = unit % nc;
     const int Z1 = min(nc, Z0 + (uend - unit));
@@ -187,12 +231,6 @@ __global__ void __launch_bounds__(32 * (32 / RPT), 1) sweep3s_kernel(const Sweep
     }
     const int zs = 3 * Z0 - 2;
     auto qslot = [](int Zc) { return (Zc + 3) % 3; };
-    auto ldU = [&](int z, int r) -> C {
-      return (!zero_u && colin[r] && z > 0 && z < n) ? ld_nc(A.u + (z * NN + col[r])) : cz<float>();
-    };
-    auto ldB = [&](int z, int r) -> C {
-      return (rrow[r] && colin[r] && z > 0 && z < n) ? ld_nc(A.b + (z * NN + col[r])) : cz<float>();
-    };
     auto ld_cc = [&](int Zc) -> C {
       const int t = threadIdx.x;
       const int cx = C0x - 1 + t % 12, cy = C0y - 1 + t / 12;
@@ -208,7 +246,46 @@ __global__ void __launch_bounds__(32 * (32 / RPT), 1) sweep3s_kernel(const Sweep
                          wy0[r] * (wx0 * a.y + wx1 * b2.y) + wy1[r] * (wx0 * c2.y + wx1 * d2.y)};
     };
 
+    // plane rings: box columns from the even column xs, the tile's box
+    // column 0 (fine x0 - 3) at offset xsh
+    const int xs = (x0 - 3) - ((x0 - 3) & 1), xsh = (x0 - 3) - xs;
+    auto issueU = [&](int z) {  // thread 0
+      const int k = (z + 8) & (kS3Ring - 1);
+      mbar_arrive_expect_tx(&S.bar_u[k], kS3PlaneBytes);
+      tma_load_plane(&S.ub[k][0][0], &tmU, &S.bar_u[k], 2 * xs, y0 - 3, z);
+    };
+    auto issueB = [&](int z) {
+      const int k = (z + 8) & (kS3Ring - 1);
+      mbar_arrive_expect_tx(&S.bar_b[k], kS3PlaneBytes);
+      tma_load_plane(&S.bb[k][0][0], &tmB, &S.bar_b[k], 2 * xs, y0 - 3, z);
+    };
+    auto waitU = [&](int z) -> const C* {  // every thread; returns the plane's row 0 at the tile's column 0
+      const int k = (z + 8) & (kS3Ring - 1);
+      mbar_wait_bounded(&S.bar_u[k], (ph_u >> k) & 1u, A.spin_limit, A.err);
+      ph_u ^= 1u << k;
+      return &S.ub[k][0][xsh];
+    };
+    auto waitB = [&](int z) -> const C* {
+      const int k = (z + 8) & (kS3Ring - 1);
+      mbar_wait_bounded(&S.bar_b[k], (ph_b >> k) & 1u, A.spin_limit, A.err);
+      ph_b ^= 1u << k;
+      return &S.bb[k][0][xsh];
+    };
+    auto plane_val = [&](const C* pl, int r) -> C {
+      return zero_u ? cz<float>() : pl[by[r] * kS3BoxW + lane];
+    };
+
     __syncthreads();  // the previous range's shared memory is free
+    if (threadIdx.x == 0) {
+      // the planes of the first steps: u(zs - 1 .. zs + 2), b(zs, zs + 1)
+      fence_proxy_async_smem();
+      issueU(3 * Z0 - 3);
+      issueU(3 * Z0 - 2);
+      issueU(3 * Z0 - 1);
+      issueU(3 * Z0);
+      issueB(3 * Z0 - 2);
+      issueB(3 * Z0 - 1);
+    }
     C cxy0[RPT], cxy1[RPT], ccpre = cz<float>();
 #pragma unroll
     for (int r = 0; r < RPT; ++r) cxy0[r] = cxy1[r] = cz<float>();
@@ -227,12 +304,14 @@ __global__ void __launch_bounds__(32 * (32 / RPT), 1) sweep3s_kernel(const Sweep
       ccpre = ld_cc(Z0 + 1);
       __syncthreads();
     }
-    C um[RPT], u0[RPT], pu[3][RPT], pb[3][RPT], pidp[RPT];
+    C um[RPT], u0[RPT], pidp[RPT];
+    const C* plm = waitU(3 * Z0 - 3);
+    const C* pl0 = waitU(3 * Z0 - 2);
 #pragma unroll
     for (int r = 0; r < RPT; ++r) {
       // u on planes 3 Z0 - 3 (c-plane Z0 - 1) and 3 Z0 - 2
-      um[r] = ldU(3 * Z0 - 3, r);
-      u0[r] = ldU(3 * Z0 - 2, r);
+      um[r] = plane_val(plm, r);
+      u0[r] = plane_val(pl0, r);
       if (use_c && colin[r]) {
         if (3 * Z0 - 3 > 0) um[r] = um[r] + cxy0[r];
         if (3 * Z0 - 2 > 0) {
@@ -241,13 +320,6 @@ __global__ void __launch_bounds__(32 * (32 / RPT), 1) sweep3s_kernel(const Sweep
         }
       }
       if (cpx && cpy[r]) S.q[qslot(Z0 - 1)][by[r] / 3][lane / 3] = um[r];
-      // prefetch: step z uses U(z + 1) and b(z), slot z mod 3
-      pu[1][r] = ldU(3 * Z0 - 1, r);
-      pu[2][r] = ldU(3 * Z0, r);
-      pu[0][r] = ldU(3 * Z0 + 1, r);
-      pb[1][r] = ldB(3 * Z0 - 2, r);
-      pb[2][r] = ldB(3 * Z0 - 1, r);
-      pb[0][r] = ldB(3 * Z0, r);
       pidp[r] = cz<float>();
     }
     C accA = cz<float>(), accB = cz<float>();
@@ -322,18 +394,25 @@ __global__ void __launch_bounds__(32 * (32 / RPT), 1) sweep3s_kernel(const Sweep
       const int zp = z + 1;
       const int buf = z & 1;
       const int tz = (z >= 0 && z <= n) ? (int)__ldg(A.typ + z) : 0;
+      // staging: u(z + 3) and b(z + 2) into the slots of u(z - 1) and b(z - 2),
+      // both last read before the previous step's barrier
+      if (threadIdx.x == 0) {
+        fence_proxy_async_smem();
+        if (z + 3 <= 3 * Z1 + 1) issueU(z + 3);
+        if (z + 2 <= 3 * Z1) issueB(z + 2);
+      }
       // phase 1: u on plane z + 1, z-pass of both rows
       C up[RPT], za[RPT], zb[RPT];
+      const C* plp = waitU(z + 1);
 #pragma unroll
       for (int r = 0; r < RPT; ++r) {
         if (OZP == 0) cxy0[r] = cxy1[r];
-        up[r] = pu[OZ][r];
+        up[r] = plane_val(plp, r);
         if (use_c && colin[r] && zp > 0 && zp < n) {
           up[r] = rfma(W0<OZP>(), cxy0[r], up[r]);
           if (OZP != 0) up[r] = rfma(W1<OZP>(), cxy1[r], up[r]);
         }
         if (OZP == 0 && cpx && cpy[r]) S.q[qslot(zp / 3)][by[r] / 3][lane / 3] = up[r];
-        pu[OZ][r] = ldU(z + 4, r);
         if (tz == 0) {
           za[r] = tap3r(m0, m1, m2, um[r], u0[r], up[r]);
           zb[r] = tap3r(p0, p1, p2, um[r], u0[r], up[r]);
@@ -356,6 +435,7 @@ __global__ void __launch_bounds__(32 * (32 / RPT), 1) sweep3s_kernel(const Sweep
       // phase 3: residuals on plane z; the pair's outer neighbour rows from shared memory
       const bool zin = z > 0 && z < n;
       const bool zown = (z >= 3 * Z0 && z < 3 * Z1) || z == n;
+      const C* plb = waitB(z);
       const C aU = warp > 0 ? S.za[buf][by[0] - 1][lane] : cz<float>();
       const C bU = warp > 0 ? S.zb[buf][by[0] - 1][lane] : cz<float>();
       const C aD = warp < NW - 1 ? S.za[buf][by[RPT - 1] + 1][lane] : cz<float>();
@@ -385,7 +465,7 @@ __global__ void __launch_bounds__(32 * (32 / RPT), 1) sweep3s_kernel(const Sweep
           hu = tap3c_acc(rw + 3, el, ey, er, tap3c_acc(rw, cl, cy, cr, cz<float>()));
         }
         C res = cz<float>();
-        if (colin[r] && zin && lane >= 1 && lane <= 30) res = pb[OZ][r] - hu;
+        if (colin[r] && zin && lane >= 1 && lane <= 30) res = plb[by[r] * kS3BoxW + lane] - hu;
         if (owncol[r] && zown) nrm = fmaf(res.x, res.x, fmaf(res.y, res.y, nrm));
         // Jacobi update, c-point mask (hb), outputs or BPX hold
         C du = S.omd[tx + 4 * ty[r] + 16 * tz] * res;
@@ -408,7 +488,6 @@ __global__ void __launch_bounds__(32 * (32 / RPT), 1) sweep3s_kernel(const Sweep
       }
 #pragma unroll
       for (int r = 0; r < RPT; ++r) {
-        pb[OZ][r] = ldB(z + 3, r);
         um[r] = u0[r];
         u0[r] = up[r];
       }
