@@ -277,10 +277,18 @@ int mg_get_level(mg_ctx* ctx, int level, int which, mg_c128* out, int on_device)
  * Forward problem H(V) u = M f with k^2 = E - V; functional
  * s = sum_q w_q u(x_q) (d-linear samples of the fine solution), J = |s|^2. */
 
-/* Replaces the fine k^2 field (host, fine-vertex layout) of a context that
- * was created with a varying field; coarse levels and cell shifts follow.
- * MG_ERR_INVALID for contexts created with a constant field. */
-int mg_set_k2(mg_ctx* ctx, const double* k2_field);
+/* Replaces the fine k^2 field (fine-vertex layout, (3^depth+1)^d values, x
+ * fastest) of a context that was created with a varying field; coarse levels
+ * and cell shifts follow (a cell takes the mean of its vertex values, coarse
+ * levels sample the field at their own vertices).  on_device = 0: k2_field is
+ * host memory, checked for finite values (MG_ERR_INVALID otherwise),
+ * synchronising.  on_device = 1: k2_field is device memory; it is copied and
+ * the cell shifts are formed on the context's stream, with no host round
+ * trip and no synchronisation (the pointer must stay valid until the stream
+ * reaches the call; values are not checked: a non-finite field shows up as a
+ * diverged or non-finite solve).  MG_ERR_INVALID for contexts created with a
+ * constant field, d = 4 and adaptive contexts. */
+int mg_set_k2(mg_ctx* ctx, const double* k2_field, int on_device);
 
 /* Sets the fine right-hand side vector b_L itself (host or device), instead
  * of M f; boundary entries are ignored. */

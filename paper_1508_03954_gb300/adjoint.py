@@ -43,8 +43,8 @@ class FarField(torch.autograd.Function):
     @staticmethod
     def forward(ctx, V, f, solver, E, xyz, g, opts):
         shape = solver.shape
-        k2 = (E - V.detach()).to("cpu", torch.float64).numpy().reshape(shape)
-        solver.set_k2(k2)
+        k2 = (E - V.detach()).to(torch.float64).contiguous().reshape(-1)
+        solver.set_k2(k2)  # device tensor: no host round trip
         solver.set_rhs(f.detach().to(torch.complex128).contiguous().reshape(-1))
         solver.set_solution(np.zeros(shape, dtype=np.complex128))
         n_fwd, rel_fwd = _solve(solver, opts)

@@ -12,6 +12,32 @@
 
 namespace mg {
 
+// Cell shift of a level from the fine k^2 field: phi_c = mean of k^2 at the
+// cell's 2^D vertices, sampled on the level's own vertices (stride
+// 3^(L - l) on the fine grid, fine row length NL).  The corners are summed in
+// the same order as the host version, so both give the same values.
+template <typename R, int D>
+__global__ void cell_shift_kernel(int n, long long stride, long long NL, const double* __restrict__ k2,
+                                  R* __restrict__ phic) {
+  long long ncell = 1;
+  for (int a = 0; a < D; ++a) ncell *= n;
+  for (long long ci = blockIdx.x * (long long)blockDim.x + threadIdx.x; ci < ncell;
+       ci += (long long)gridDim.x * blockDim.x) {
+    long long q[3] = {0, 0, 0}, r = ci;
+    for (int a = 0; a < D; ++a) { q[a] = r % n; r /= n; }
+    double acc = 0.0;
+    for (int e = 0; e < (1 << D); ++e) {
+      long long gi = 0, st = 1;
+      for (int a = 0; a < D; ++a) {
+        gi += (q[a] + ((e >> a) & 1)) * stride * st;
+        st *= NL;
+      }
+      acc += k2[gi];
+    }
+    phic[ci] = (R)(acc / (double)(1 << D));
+  }
+}
+
 // q_c = lambda_c^T M_c u_c for every cell c of a 2D or 3D level (complex).
 template <int D>
 __global__ void cell_mass_form_kernel(int n, const cplx<double>* __restrict__ lam,

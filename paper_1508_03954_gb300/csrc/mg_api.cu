@@ -238,6 +238,8 @@ struct mg_ctx {
   std::vector<double> k2;              // fine k^2 (host copy)
   cplx<double>* f_dev = nullptr;       // nodal f (fine)
   cplx<double>* scratch = nullptr;     // fine-size FP64 scratch
+  double* k2dev = nullptr;             // fine k^2 field set from device memory (mg_set_k2)
+  bool k2_host_stale = false;          // k2 (host copy) older than k2dev
   cplx<double>* rvec = nullptr;        // fine residual vector (allocated on first use)
   double* host_norm = nullptr;         // pinned
   std::string err;
@@ -451,6 +453,23 @@ std::vector<R> cell_shift(const mg_ctx* c, int l) {
   return phic;
 }
 
+int grid_for(size_t nv);
+
+// Cell shift of level l formed on the device from the device copy of the fine
+// field (the values of cell_shift), enqueued on the context's stream.
+template <typename R>
+cudaError_t cell_shift_dev(mg_ctx* c, int l, R* phic) {
+  const int n = (int)ipow(3, l);
+  const long long stride = ipow(3, c->L - l), NL = ipow(3, c->L) + 1;
+  const size_t ncell = (size_t)ipow(n, c->d);
+  ++c->launches;
+  if (c->d == 2)
+    mg::cell_shift_kernel<R, 2><<<grid_for(ncell), kThreads, 0, c->stream>>>(n, stride, NL, c->k2dev, phic);
+  else
+    mg::cell_shift_kernel<R, 3><<<grid_for(ncell), kThreads, 0, c->stream>>>(n, stride, NL, c->k2dev, phic);
+  return cudaGetLastError();
+}
+
 // Builds the arrays and tables of one precision.
 template <typename R>
 int build_hier(mg_ctx* c, Hier<R>& H) {
@@ -640,9 +659,15 @@ int build_hier(mg_ctx* c, Hier<R>& H) {
     MG_CUDA(c, cudaMemcpy(V.coefM, hM.data(), hM.size() * sizeof(cplx<R>), cudaMemcpyHostToDevice));
     if (H.varphi) {
       const size_t ncell = (size_t)ipow(V.n, d);
-      std::vector<R> phic = cell_shift<R>(c, l);
       if ((rc = dalloc(c, H, (void**)&V.phic, ncell * sizeof(R))) != MG_OK) return rc;
-      MG_CUDA(c, cudaMemcpy(V.phic, phic.data(), ncell * sizeof(R), cudaMemcpyHostToDevice));
+      if (c->k2_host_stale) {
+        // the field was last set from device memory
+        MG_CUDA(c, cell_shift_dev<R>(c, l, V.phic));
+        MG_CUDA(c, cudaStreamSynchronize(c->stream));
+      } else {
+        std::vector<R> phic = cell_shift<R>(c, l);
+        MG_CUDA(c, cudaMemcpy(V.phic, phic.data(), ncell * sizeof(R), cudaMemcpyHostToDevice));
+      }
     }
     {
       // complex cell width per axis index (per-cell shift and adjoint kernels)
@@ -2786,6 +2811,7 @@ void mg_destroy(mg_ctx* c) {
   ada_free(c->ada);
   if (c->f_dev) cudaFree(c->f_dev);
   if (c->scratch) cudaFree(c->scratch);
+  if (c->k2dev) cudaFree(c->k2dev);
   if (c->rvec) cudaFree(c->rvec);
   if (c->host_norm) cudaFreeHost(c->host_norm);
   delete c;
@@ -3353,7 +3379,7 @@ int mg_get_stats(mg_ctx* c, long long* launches, int* fine_sweeps, double* fine_
   return MG_OK;
 }
 
-int mg_set_k2(mg_ctx* c, const double* k2) {
+int mg_set_k2(mg_ctx* c, const double* k2, int on_device) {
   if (check_ctx(c)) return MG_ERR_INVALID;
   if (c->d == 4) return fail(c, MG_ERR_INVALID, std::string("mg_set_k2") + kNot4);
   if (c->ada != nullptr) return fail(c, MG_ERR_INVALID, std::string("mg_set_k2") + kNotA);
@@ -3361,10 +3387,23 @@ int mg_set_k2(mg_ctx* c, const double* k2) {
   if (!c->h64.varphi)
     return fail(c, MG_ERR_INVALID, "the context was created with a constant k^2; create a new context");
   const size_t nv = c->k2.size();
+  if (on_device) {
+    // copied on the context's stream, cell shifts formed there: no host round trip
+    if (c->k2dev == nullptr) MG_CUDA(c, cudaMalloc(&c->k2dev, nv * sizeof(double)));
+    MG_CUDA(c, cudaMemcpyAsync(c->k2dev, k2, nv * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    for (int l = 1; l <= c->L; ++l) {
+      MG_CUDA(c, cell_shift_dev<double>(c, l, c->h64.lev[l].phic));
+      if (c->h32.ready) MG_CUDA(c, cell_shift_dev<float>(c, l, c->h32.lev[l].phic));
+    }
+    c->k2_host_stale = true;
+    c->r0 = -1.0;
+    return MG_OK;
+  }
   for (size_t i = 0; i < nv; ++i)
     if (!std::isfinite(k2[i])) return fail(c, MG_ERR_INVALID, "k2 holds a non-finite value");
   MG_CUDA(c, cudaStreamSynchronize(c->stream));
   c->k2.assign(k2, k2 + nv);
+  c->k2_host_stale = false;
   for (int l = 1; l <= c->L; ++l) {
     auto p64 = cell_shift<double>(c, l);
     MG_CUDA(c, cudaMemcpy(c->h64.lev[l].phic, p64.data(), p64.size() * sizeof(double), cudaMemcpyHostToDevice));

@@ -90,7 +90,7 @@ def load(path: str | None = None):
         "mg_set_trace": (ip, [vp, ip]),
         "mg_set_spin_limit": (ip, [vp, ctypes.c_uint]),
         "mg_debug_unsatisfiable_wait": (ip, [vp, ip]),
-        "mg_set_k2": (ip, [vp, ctypes.POINTER(dp)]),
+        "mg_set_k2": (ip, [vp, ctypes.c_void_p, ctypes.c_int]),
         "mg_set_rhs_vector": (ip, [vp, vp, ip]),
         "mg_sample": (ip, [vp, ip, ctypes.POINTER(dp), pc, pc]),
         "mg_set_rhs_samples": (ip, [vp, ip, ctypes.POINTER(dp), pc]),
@@ -336,11 +336,18 @@ class Solver:
         return n.value, k.value, ms.value
 
     def set_k2(self, k2):
+        """Fine k^2 field: a host array, or a contiguous float64 CUDA tensor
+        (copied and turned into cell shifts on the solver's stream)."""
+        if hasattr(k2, "data_ptr") and hasattr(k2, "is_cuda") and k2.is_cuda:
+            import torch
+            if k2.dtype != torch.float64 or not k2.is_contiguous() or k2.numel() != self.nv:
+                raise ValueError(f"k2 on the device must be a contiguous float64 tensor of {self.nv} values")
+            self._check(self._L.mg_set_k2(self._view, ctypes.c_void_p(k2.data_ptr()), 1), "mg_set_k2")
+            return
         a = np.ascontiguousarray(np.asarray(k2, dtype=np.float64))
         if a.size != self.nv:
             raise ValueError(f"k2 needs {self.nv} values")
-        self._check(self._L.mg_set_k2(self._view, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
-                    "mg_set_k2")
+        self._check(self._L.mg_set_k2(self._view, a.ctypes.data_as(ctypes.c_void_p), 0), "mg_set_k2")
 
     def set_rhs_vector(self, b):
         p, dev, _keep = _ptr(b, self.nv)

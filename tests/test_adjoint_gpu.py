@@ -118,3 +118,89 @@ def test_full_size_gradients_match_directional_differences():
                 errs.append(abs(fd - ad) / max(abs(ad), abs(fd)))
             print(which, ad, errs)
             assert min(errs) <= 1e-6, (which, ad, errs)
+
+
+def test_full_size_gradients_match_pointwise_central_differences():
+    """Depth 6: dJ/dV_v and dJ/df_v at 64 random interior vertices against
+    central differences of J (each J a full forward solve to 1e-12).  J is
+    quadratic in f, so a central difference in f_v is exact up to rounding;
+    in V_v it is Richardson-extrapolated from steps h and h/2 (error O(h^4)),
+    with h sized so that J moves by about 1% of itself (at most 10, which
+    keeps the perturbed k^2 = -V nearly definite).  The errors are measured
+    against the largest gradient entry among the 64."""
+    import torch
+    from paper_1508_03954_gb300.adjoint import far_field
+    c = W.config5(depth=6)
+    E = 0.0
+    V0, th, w = c["V"], c["theta"], c["layer_width"]
+    f0 = np.real(c["f"])
+    xyz, g = W.circle_samples(256)
+    s = mg.Solver(2, 6, E - V0, th, w)
+    s.set_stream(torch.cuda.current_stream().cuda_stream)
+    opts = _opts(6)
+    V = torch.from_numpy(V0).cuda().requires_grad_(True)
+    f = torch.from_numpy(f0).cuda().requires_grad_(True)
+    J = far_field(V, f, s, E, xyz, g, opts)
+    J.backward()
+    J0 = J.item()
+    gV, gf = V.grad.cpu().numpy(), f.grad.cpu().numpy()
+    n = 3 ** 6
+    rng = np.random.default_rng(5)
+    pts = [tuple(p) for p in rng.integers(1, n, size=(64, 2))]
+
+    def J_at(Vp, fp):
+        with torch.no_grad():
+            return far_field(torch.from_numpy(Vp).cuda(), torch.from_numpy(fp).cuda(), s, E, xyz, g, opts).item()
+
+    def central(which, v, h):
+        e = np.zeros_like(V0)
+        e[v] = h
+        if which == "V":
+            return (J_at(V0 + e, f0) - J_at(V0 - e, f0)) / (2 * h)
+        return (J_at(V0, f0 + e) - J_at(V0, f0 - e)) / (2 * h)
+
+    fdV, fdf, adV, adf = [], [], [], []
+    fmax = np.abs(f0).max()
+    for v in pts:
+        # steps capped where the gradient is tiny: a V step keeps k^2 = -V
+        # nearly definite, an f step keeps J(f + h e) within rounding reach
+        hv = min(1e-2 * J0 / max(abs(gV[v]), 1e-300), 10.0)
+        d1, d2 = central("V", v, hv), central("V", v, hv / 2)
+        fdV.append((4 * d2 - d1) / 3)
+        fdf.append(central("f", v, min(1e-1 * J0 / max(abs(gf[v]), 1e-300), 10.0 * fmax)))
+        adV.append(gV[v])
+        adf.append(gf[v])
+    for fd, ad in ((np.array(fdV), np.array(adV)), (np.array(fdf), np.array(adf))):
+        err = np.abs(fd - ad).max() / np.abs(ad).max()
+        print(err, np.abs(ad).max())
+        assert err <= 1e-6, err
+
+
+def test_set_k2_from_device_memory_matches_host_path():
+    """mg_set_k2 with a device field forms the same cell shifts as with a host
+    field: the cycles of both contexts agree bit for bit, in complex128 and in
+    the complex64 refinement form (whose hierarchy is built after the device
+    field was set, from the device copy)."""
+    import torch
+    c = W.config5(depth=4)
+    V1 = c["V"] * 1.3 + 5.0
+    f = c["f"]
+    om = np.full(4, 0.6)
+    outs = []
+    for dev in (False, True):
+        s = mg.Solver(2, 4, -c["V"], c["theta"], c["layer_width"])
+        s.set_stream(torch.cuda.current_stream().cuda_stream)
+        k2 = -V1
+        s.set_k2(torch.from_numpy(np.ascontiguousarray(k2)).cuda().reshape(-1) if dev else k2)
+        s.set_rhs(f)
+        for _ in range(3):
+            s.cycle(mg.MG_BPX, om, mg.MG_HIERARCHICAL)
+        a = s.get_solution()
+        s.set_solution(np.zeros(s.shape, complex))
+        s.set_precision(mg.MG_C64_REFINE, 4)
+        st, nc, rel = s.solve(mg.MG_ADD, np.full(4, 0.6), mg.MG_DLINEAR, 1e-9, 400)
+        assert st == mg.MG_OK
+        outs.append((a, s.get_solution()))
+        s.close()
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert np.array_equal(outs[0][1], outs[1][1])
