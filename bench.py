@@ -531,6 +531,36 @@ def form_refine_3d(mg, torch, peaks):
     return cc
 
 
+def form_aligned_layer(mg, torch):
+    """Time to 1e-8 where both arms converge: the definite companions of the
+    2D depth-6 and 3D depth-5 workloads with the layer edge on coarse grid
+    lines (width 1/3, so rediscretisation equals the Galerkin product on
+    every level and the plain FAS cycle's fixed point is the discrete
+    solution).  Arms: complex64 cycles inside FP64 defect correction (16 per
+    outer step) and plain complex128 cycles, both additive with exponential
+    damping (omega 0.6), from u = 0.  Seconds are host wall time around the
+    synchronising solve; cycles are inner cycles for the refinement arm."""
+    out = {}
+    for name, cfg in (("2d_depth6", W.config2()), ("3d_depth5", W.config3())):
+        c = W.definite(cfg)
+        d, depth = c["d"], c["depth"]
+        om = mg.omega_scheme(mg.MG_OMEGA_EXP, 0.6, depth)
+        s = mg.Solver(d, depth, c["k2"], c["theta"], 1.0 / 3.0)
+        s.set_stream(torch.cuda.current_stream().cuda_stream)
+        s.set_rhs(c["f"])
+        res = {}
+        for arm, prec, cap in (("c64_refine", mg.MG_C64_REFINE, 4000), ("c128_plain", mg.MG_C128, 1000)):
+            s.set_precision(prec, INNER)
+            s.solve(mg.MG_ADD, om, mg.MG_DLINEAR, 1e-8, min(cap, 2 * INNER))  # warm-up (graphs)
+            s.set_solution(np.zeros(s.shape, complex))
+            (st, n, rel), dt = _wall(torch, lambda: s.solve(mg.MG_ADD, om, mg.MG_DLINEAR, 1e-8, cap))
+            res[arm] = {"status": mg.STATUS_NAMES[st], "cycles": n, "rel_res": rel, "seconds": dt}
+        res["speedup_c64_refine"] = res["c128_plain"]["seconds"] / res["c64_refine"]["seconds"]
+        out[name] = res
+        s.close()
+    return out
+
+
 def form_batched(mg, torch):
     """256 problems of depth 4-6 (definite companions) in one persistent
     launch per outer step against the same problems one after another."""
@@ -596,6 +626,7 @@ def form_table(mg, torch, peaks):
             "configured_2d_depth6": lambda: form_configured_2d(mg, torch),
             "time_to_1e-8_2d_depth6_definite": lambda: form_refine_2d(mg, torch),
             "time_to_1e-8_3d_depth5_definite": lambda: form_refine_3d(mg, torch, peaks),
+            "time_to_1e-8_aligned_layer": lambda: form_aligned_layer(mg, torch),
             "batched_256_definite": lambda: form_batched(mg, torch),
             "adjoint_2d_depth6": lambda: form_adjoint(mg, torch),
             "csg_sweep": lambda: csg_sweep(mg, torch),
@@ -962,7 +993,8 @@ def adaptive(mg, torch, d=2, depth=6, cycles=100):
 
 # ---------------------------------------------------------------- main
 FORMS_DEFAULT = ("cycle_2d_depth6", "configured_2d_depth6", "time_to_1e-8_2d_depth6_definite",
-                 "time_to_1e-8_3d_depth5_definite", "batched_256_definite", "adjoint_2d_depth6",
+                 "time_to_1e-8_3d_depth5_definite", "time_to_1e-8_aligned_layer", "batched_256_definite",
+                 "adjoint_2d_depth6",
                  "csg_sweep", "channel_table2", "four_d", "adaptive", "adaptive_3d")
 
 

@@ -1,14 +1,17 @@
-"""Parity of the separable complex128 3D sweep (levels with 27 or more cells
-per axis) with the FP64 oracle, through the C ABI.
+"""Parity of the separable complex128 3D sweep (finest levels with 27 or more
+cells per axis, coarse levels with 81 or more) with the FP64 oracle, through
+the C ABI.
 
 Per-iterate relative L2 against the oracle within 1e-12 (the complex128
 contract) over several cycles, every variant and transfer, at depths 3 and 4
-(the finest level and its coarse levels run the separable kernel; the tiles
-of 9 coarse cells leave a ragged last tile at both depths), with layers that
-make some, none or all axis rows complex, real and complex relaxation
-factors.  At the full 3D size (depth 5, 14.5 M vertices) the oracle's two
-iterates are stored at 1024 seeded sample vertices (written by
-tests/golden/make_config3_samples.py, which calls only the oracle).
+(the finest level runs the separable kernel: one tile of 9 coarse cells at
+depth 3, three per axis at depth 4, the last one owning the boundary coarse
+column), with layers that make some, none or all axis rows complex, real
+and complex relaxation factors.  At the full 3D size (depth 5, 14.5 M
+vertices; level 4 runs the separable kernel as a coarse level) the oracle's
+two iterates of every variant are stored at 512 seeded sample vertices
+(written by tests/golden/make_config3_samples.py, which calls only the
+oracle).
 """
 import json
 import math
@@ -84,12 +87,26 @@ def test_depth4_iterates(var, omega):
     run(4, 0.1, 25.0, var, omega, 2, 200)
 
 
-def test_config3_full_size_iterates_match_stored_oracle_samples():
-    """Full-size 3D workload: two BPX cycles from the stored seeded start;
-    the iterates at the oracle's sample vertices and the residual norms."""
+def _golden_blocks():
+    blocks, cur = {}, None
     with open(GOLDEN) as fh:
-        head = json.loads(fh.readline()[2:])
-        rows = np.loadtxt(fh, comments="#")
+        for line in fh:
+            if line.startswith("# {"):
+                cur = json.loads(line[2:])
+                cur["rows"] = []
+                blocks[cur["variant"]] = cur
+            elif not line.startswith("#") and line.strip():
+                cur["rows"].append([float(x) for x in line.split()])
+    return blocks
+
+
+@pytest.mark.parametrize("var", VARIANTS, ids=IDS)
+def test_config3_full_size_iterates_match_stored_oracle_samples(var):
+    """Full-size 3D workload (the finest level and level 4 run the separable
+    kernel): two cycles from the stored seeded start; the iterates at the
+    oracle's sample vertices and the residual norms."""
+    head = _golden_blocks()[IDS[VARIANTS.index(var)]]
+    rows = np.array(head["rows"])
     flat = rows[:, 0].astype(np.int64)
     u1 = rows[:, 1] + 1j * rows[:, 2]
     u2 = rows[:, 3] + 1j * rows[:, 4]
@@ -102,7 +119,7 @@ def test_config3_full_size_iterates_match_stored_oracle_samples():
     assert abs(a0 - norms[0]) <= 1e-12 * norms[0]
     om = np.full(head["depth"], head["omega"])
     for k, ref in enumerate((u1, u2)):
-        g.cycle(mg.MG_BPX, om, mg.MG_HIERARCHICAL)
+        g.cycle(var[0], om, var[1])
         u = np.ravel(g.get_solution())[flat]
         assert rel_l2(u, ref) <= TOL, (k, rel_l2(u, ref))
         a, _ = g.residual_norm()
