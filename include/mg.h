@@ -417,6 +417,48 @@ int mg_residual_noalloc(mg_ctx* ctx, const mg_c128* u, const mg_c128* b, mg_c128
  * for failures of mg_create. */
 const char* mg_last_error(const mg_ctx* ctx);
 
+/* ---- coupled multichannel form (Section 7.5, Eq. coupledHelmholtz) -------
+ * c channels of the Helmholtz problem fused into one grid: every vertex
+ * carries a C^c tuple, and the operator keeps the couplings inside the
+ * block (the matrix A-hat of Section 7.5):
+ *     (A u)_i = K u_i - sum_j Phi_ij M u_j,
+ * i.e. H_ii = K - phi_i M on the diagonal and A_ij = -kappa_ij M (a constant
+ * coupling potential times the mass matrix) off it, with the complex-scaled
+ * d-linear K and M of the single-channel form (coordinate-wise layer of
+ * width layer_width and angle theta).  One cycle is Algorithm 4 on tuples
+ * with damped block-Jacobi smoothing, du_v = omega_l D_v^{-1} r_v, D_v the
+ * c x c diagonal block of A at v; restriction, prolongation, injection, the
+ * hb mask and the BPX transfer act channel by channel.  It runs the plain
+ * (not single-touch pipelined) form of the cycle.
+ * Layout: tuple arrays hold (3^depth+1)^d vertices x c channels, channel
+ * fastest (index = vertex * c + channel), vertices as in the single-channel
+ * form.  d is 2 or 3; c is 1, 2, 3, 4, 8 or 16. */
+typedef struct mg_mc_ctx mg_mc_ctx;
+
+/* phi: host, c x c complex matrix, row-major (phi_i = Phi_ii, kappa_ij =
+ * Phi_ij); finite values.  The same Phi serves every level.  MG_ERR_INVALID
+ * for d, depth, c, theta or layer_width out of range or a singular diagonal
+ * block; MG_ERR_OOM when the arrays do not fit. */
+int mg_mc_create(int d, int depth, int channels, const mg_c128* phi, double theta, double layer_width,
+                 mg_mc_ctx** out);
+int mg_mc_set_stream(mg_mc_ctx* ctx, void* cuda_stream);
+/* b = M f channel by channel from nodal f (host or device, tuple layout);
+ * resets the reference residual. */
+int mg_mc_set_rhs(mg_mc_ctx* ctx, const mg_c128* f_nodal, int on_device);
+/* u (host or device, tuple layout); the Dirichlet ring is taken as zero. */
+int mg_mc_set_solution(mg_mc_ctx* ctx, const mg_c128* u, int on_device);
+/* the current fine solution (host or device); synchronising for host out. */
+int mg_mc_get_solution(mg_mc_ctx* ctx, mg_c128* out, int on_device);
+/* one cycle; variant MG_ADD / MG_HB, transfer MG_DLINEAR / MG_HIERARCHICAL
+ * (MG_BPX = MG_ADD with MG_HIERARCHICAL), omega_per_level[depth] (index l-1). */
+int mg_mc_cycle(mg_mc_ctx* ctx, int variant, const mg_c128* omega_per_level, int transfer);
+/* FP64 Euclidean norm of b - A u over all interior vertices and channels,
+ * and the same relative to the first norm taken after the last set_rhs /
+ * set_solution; synchronising. */
+int mg_mc_residual_norm(mg_mc_ctx* ctx, double* abs_l2, double* rel_l2);
+const char* mg_mc_last_error(const mg_mc_ctx* ctx);
+void mg_mc_destroy(mg_mc_ctx* ctx);
+
 #ifdef __cplusplus
 }
 #endif

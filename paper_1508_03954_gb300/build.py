@@ -19,7 +19,7 @@ LIB = os.path.join(OUT_DIR, "libmg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include"), "-I", CSRC]
-SOURCES = ["mg_api.cu"]
+SOURCES = ["mg_api.cu", "mg_mc.cu"]
 
 
 def nvcc() -> str:

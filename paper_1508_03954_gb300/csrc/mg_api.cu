@@ -571,10 +571,17 @@ int build_hier(mg_ctx* c, Hier<R>& H) {
     }
     if (d == 3 && !H.varphi && l > 1 && V.n >= 27 && V.g3ok) {
       // cost of each (9 x 9 coarse-cell tile, coarse plane) unit of the
-      // separable sweeps, in floating-point operations per lane: z-pair on the
-      // 32 box rows (10 real, 24 complex), y-pair (16 / 36), x-pass (12 / 26)
-      // and the rest (~30) on the 30 residual rows; blocks take ranges of
-      // equal cost
+      // separable sweeps: complex128 is bound by the FP64 pipe, so its weights
+      // are FP64 operations per lane -- z-pair on the 32 box rows (10 real,
+      // 24 complex), y-pair (16 / 36), x-pass (12 / 26) and the rest (~30) on
+      // the 30 residual rows; complex64 is bound by instruction issue, where
+      // the complex passes add about half as much relative to a row's other
+      // work (measured: the FP64 weights overload the interior blocks by as
+      // much as equal units overload the layer blocks).  Blocks take ranges of
+      // equal cost.
+      const unsigned cz_ = std::is_same<R, double>::value ? 14u : 7u;
+      const unsigned cx_ = std::is_same<R, double>::value ? 14u : 7u;
+      const unsigned cy_ = std::is_same<R, double>::value ? 20u : 10u;
       const int n = V.n, nc = n / 3, tl = (nc + 8) / 9;
       std::vector<unsigned> pref((size_t)tl * tl * nc + 1, 0u);
       size_t u = 0;
@@ -587,7 +594,7 @@ int build_hier(mg_ctx* c, Hier<R>& H) {
         for (int Z = 0; Z < nc; ++Z, ++u) {
           unsigned cost = 0;
           for (int z = 3 * Z; z < 3 * Z + 3; ++z)
-            cost += 32u * (typ[z] != 0 ? 24u : 10u) + 30u * (58u + (xc ? 14u : 0u)) + 20u * (unsigned)yc;
+            cost += 32u * (10u + (typ[z] != 0 ? cz_ : 0u)) + 30u * (58u + (xc ? cx_ : 0u)) + cy_ * (unsigned)yc;
           pref[u + 1] = pref[u] + cost;
         }
       }

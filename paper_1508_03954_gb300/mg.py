@@ -31,7 +31,9 @@ EXPORTS = ["mg_create", "mg_create_ecs", "mg_create_adaptive", "mg_adapt", "mg_g
            "mg_set_trace", "mg_get_trace", "mg_set_spin_limit", "mg_debug_unsatisfiable_wait", "mg_set_k2", "mg_set_rhs_vector", "mg_sample",
            "mg_set_rhs_samples", "mg_adjoint_grad", "mg_residual_noalloc", "mg_batch_create",
            "mg_batch_destroy", "mg_batch_get_ctx", "mg_batch_set_stream", "mg_batch_solve",
-           "mg_batch_autotune", "mg_batch_launches", "mg_batch_last_error", "mg_last_error"]
+           "mg_batch_autotune", "mg_batch_launches", "mg_batch_last_error", "mg_last_error",
+           "mg_mc_create", "mg_mc_set_stream", "mg_mc_set_rhs", "mg_mc_set_solution", "mg_mc_get_solution",
+           "mg_mc_cycle", "mg_mc_residual_norm", "mg_mc_last_error", "mg_mc_destroy"]
 
 
 class MgC128(ctypes.Structure):
@@ -108,6 +110,15 @@ def load(path: str | None = None):
         "mg_batch_launches": (ctypes.c_longlong, [vp]),
         "mg_batch_last_error": (ctypes.c_char_p, [vp]),
         "mg_last_error": (ctypes.c_char_p, [vp]),
+        "mg_mc_create": (ip, [ip, ip, ip, pc, dp, dp, ctypes.POINTER(vp)]),
+        "mg_mc_set_stream": (ip, [vp, vp]),
+        "mg_mc_set_rhs": (ip, [vp, vp, ip]),
+        "mg_mc_set_solution": (ip, [vp, vp, ip]),
+        "mg_mc_get_solution": (ip, [vp, vp, ip]),
+        "mg_mc_cycle": (ip, [vp, ip, pc, ip]),
+        "mg_mc_residual_norm": (ip, [vp, ctypes.POINTER(dp), ctypes.POINTER(dp)]),
+        "mg_mc_last_error": (ctypes.c_char_p, [vp]),
+        "mg_mc_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -559,3 +570,72 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class MultiChannel:
+    """Coupled multichannel context (mg_mc_create .. mg_mc_destroy): c channels
+    per vertex, A = I (x) K - Phi (x) M.  Tuple arrays have shape
+    (N, .., N, c) (channel fastest) or the same values flattened."""
+
+    def __init__(self, d, depth, phi, theta, layer_width):
+        self._L = load()
+        phi = np.asarray(phi, dtype=np.complex128)
+        if phi.ndim != 2 or phi.shape[0] != phi.shape[1]:
+            raise ValueError("phi must be a square matrix")
+        self.d, self.depth, self.c = d, depth, phi.shape[0]
+        self.n = 3 ** depth
+        self.nv = (self.n + 1) ** d
+        self.shape = (self.n + 1,) * d + (self.c,)
+        arr = (MgC128 * phi.size)()
+        for k, z in enumerate(phi.reshape(-1)):
+            arr[k].re, arr[k].im = float(z.real), float(z.imag)
+        h = ctypes.c_void_p()
+        rc = self._L.mg_mc_create(d, depth, self.c, arr, float(theta), float(layer_width), ctypes.byref(h))
+        if rc != MG_OK:
+            raise MgError(rc, "mg_mc_create")
+        self._h = h
+
+    def _check(self, rc, what):
+        if rc != MG_OK:
+            msg = self._L.mg_mc_last_error(self._h)
+            raise MgError(rc, f"{what}: {msg.decode() if msg else ''}")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.mg_mc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        self._check(self._L.mg_mc_set_stream(self._h, ctypes.c_void_p(stream)), "mg_mc_set_stream")
+
+    def set_rhs(self, f):
+        p, dev, _keep = _ptr(f, self.nv * self.c)
+        self._check(self._L.mg_mc_set_rhs(self._h, p, dev), "mg_mc_set_rhs")
+
+    def set_solution(self, u):
+        p, dev, _keep = _ptr(u, self.nv * self.c)
+        self._check(self._L.mg_mc_set_solution(self._h, p, dev), "mg_mc_set_solution")
+
+    def get_solution(self, out=None):
+        if out is None:
+            a = np.empty(self.shape, dtype=np.complex128)
+            self._check(self._L.mg_mc_get_solution(self._h, a.ctypes.data_as(ctypes.c_void_p), 0),
+                        "mg_mc_get_solution")
+            return a
+        p, dev, _keep = _ptr(out, self.nv * self.c)
+        self._check(self._L.mg_mc_get_solution(self._h, p, dev), "mg_mc_get_solution")
+        return out
+
+    def cycle(self, variant, omega, transfer):
+        self._check(self._L.mg_mc_cycle(self._h, variant, _omega_array(omega, self.depth), transfer), "mg_mc_cycle")
+
+    def residual_norm(self):
+        a, r = ctypes.c_double(), ctypes.c_double()
+        self._check(self._L.mg_mc_residual_norm(self._h, ctypes.byref(a), ctypes.byref(r)), "mg_mc_residual_norm")
+        return a.value, r.value

@@ -90,3 +90,15 @@ def build_c_client(root, out_path):
 def test_plain_c_client_compiles_and_links(lib, root_dir, tmp_path):
     exe = build_c_client(root_dir, str(tmp_path / "solve_c"))
     assert os.path.exists(exe)
+
+
+def test_multichannel_argument_validation_before_device_work(lib):
+    h = ctypes.c_void_p()
+    phi = (mg.MgC128 * 4)()
+    for args in [(4, 2, 2, phi, 0.5, 0.1), (2, 0, 2, phi, 0.5, 0.1), (2, 2, 5, phi, 0.5, 0.1),
+                 (2, 2, 2, None, 0.5, 0.1), (2, 2, 2, phi, 2.0, 0.1), (2, 2, 2, phi, 0.5, 0.7),
+                 (3, 7, 2, phi, 0.5, 0.1)]:
+        assert lib.mg_mc_create(*args, ctypes.byref(h)) == mg.MG_ERR_INVALID
+    assert lib.mg_mc_cycle(None, 0, None, 0) == mg.MG_ERR_INVALID
+    assert lib.mg_mc_residual_norm(None, None, None) == mg.MG_ERR_INVALID
+    lib.mg_mc_destroy(None)
