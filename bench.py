@@ -561,6 +561,50 @@ def form_aligned_layer(mg, torch):
     return out
 
 
+def form_multichannel(mg, torch, cycles=20):
+    """Coupled multichannel cycles (Section 7.5; the channel counts of its
+    Table 4): c = 1, 2, 4, 8, 16 channels fused on one grid, 2D depth 6
+    (p = 2) and 3D depth 4 (p = 3), 10% layer with theta = pi/6, a definite
+    synthetic coupling matrix (channel shifts -(5 + 3 i)^2 on the diagonal,
+    couplings 0.05 |phi| e^{-|i-j|} off it: the closer to the diagonal, the
+    stronger, as Section 2 describes), a Gaussian rhs per channel.  Per run:
+    device time per BPX cycle (CUDA events over `cycles` cycles) and
+    unknown-updates/s (vertices x channels)."""
+    rows = []
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    for d, depth in ((2, 6), (3, 4)):
+        n = 3 ** depth
+        for c in (1, 2, 4, 8, 16):
+            ph = -np.array([(5.0 + 3.0 * i) ** 2 for i in range(c)])
+            Phi = np.diag(ph).astype(complex)
+            for i in range(c):
+                for j in range(c):
+                    if i != j:
+                        Phi[i, j] = 0.05 * math.sqrt(abs(ph[i] * ph[j])) * math.exp(-abs(i - j))
+            g = mg.MultiChannel(d, depth, Phi, W.THETA, 0.1)
+            g.set_stream(stream.cuda_stream)
+            f = np.stack([W.gaussian(d, depth, (0.5,) * d, 0.05)] * c, axis=-1).astype(np.complex128)
+            g.set_rhs(f)
+            g.residual_norm()  # reference: the residual of u = 0
+            om = np.full(depth, 0.6)
+            for _ in range(3):
+                g.cycle(mg.MG_BPX, om, mg.MG_HIERARCHICAL)
+            torch.cuda.synchronize()
+            ev[0].record(stream)
+            for _ in range(cycles):
+                g.cycle(mg.MG_BPX, om, mg.MG_HIERARCHICAL)
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            ms = ev[0].elapsed_time(ev[1]) / cycles
+            _, rel = g.residual_norm()
+            rows.append({"p": d, "depth": depth, "channels": c, "ms_per_cycle": ms,
+                         "unknown_updates_per_s": c * (n - 1) ** d / (ms / 1e3),
+                         "rel_res_after_cycles": rel, "cycles_done": cycles + 3})
+            g.close()
+    return {"cycles": cycles, "variant": "BPX, omega 0.6", "runs": rows}
+
+
 def form_batched(mg, torch):
     """256 problems of depth 4-6 (definite companions) in one persistent
     launch per outer step against the same problems one after another."""
@@ -628,6 +672,7 @@ def form_table(mg, torch, peaks):
             "time_to_1e-8_3d_depth5_definite": lambda: form_refine_3d(mg, torch, peaks),
             "time_to_1e-8_aligned_layer": lambda: form_aligned_layer(mg, torch),
             "batched_256_definite": lambda: form_batched(mg, torch),
+            "multichannel": lambda: form_multichannel(mg, torch),
             "adjoint_2d_depth6": lambda: form_adjoint(mg, torch),
             "csg_sweep": lambda: csg_sweep(mg, torch),
             "channel_table2": lambda: channel_table2(mg, torch),
@@ -994,8 +1039,28 @@ def adaptive(mg, torch, d=2, depth=6, cycles=100):
 # ---------------------------------------------------------------- main
 FORMS_DEFAULT = ("cycle_2d_depth6", "configured_2d_depth6", "time_to_1e-8_2d_depth6_definite",
                  "time_to_1e-8_3d_depth5_definite", "time_to_1e-8_aligned_layer", "batched_256_definite",
-                 "adjoint_2d_depth6",
+                 "adjoint_2d_depth6", "multichannel",
                  "csg_sweep", "channel_table2", "four_d", "adaptive", "adaptive_3d")
+
+
+def profile_sequence(mg, torch, which):
+    """A short fixed launch sequence for ncu (no timing, no output but a
+    status line)."""
+    if which == "cycle3d":
+        c = W.config3()
+        s = mg.Solver(3, 5, c["k2"], c["theta"], c["layer_width"])
+        s.set_rhs(c["f"])
+        for _ in range(3):
+            s.cycle(mg.MG_BPX, np.full(5, 0.6), mg.MG_HIERARCHICAL)
+    else:
+        c = W.definite(W.config3())
+        s = mg.Solver(3, 5, c["k2"], c["theta"], c["layer_width"])
+        s.set_rhs(c["f"])
+        s.set_precision(mg.MG_C64_REFINE, INNER)
+        s.solve(mg.MG_ADD, mg.omega_scheme(mg.MG_OMEGA_EXP, 0.6, 5), mg.MG_DLINEAR, 1e-30, INNER)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": which, "ok": True}), flush=True)
+    s.close()
 
 
 def headline_line(value, steps, warmup, total_ms, world, roofline, e2e, launches, clk, cpu=None):
@@ -1026,6 +1091,10 @@ def main():
     ap.add_argument("--form", choices=sorted(form_table(None, None, {}).keys()), default=None,
                     help="run only this form and print its result (profiling)")
     ap.add_argument("--four-d-depth", type=int, default=4, help="depth of the four_d form (profiling)")
+    ap.add_argument("--profile", choices=["cycle3d", "refine3d"], default=None,
+                    help="run a short fixed sequence for a profiler and exit: cycle3d = three complex128 "
+                         "BPX cycles of the headline workload, refine3d = one outer step (16 complex64 "
+                         "cycles) of the 3D depth-5 refinement form")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -1050,6 +1119,9 @@ def main():
     B.build()
     mg.load()
     peaks, peak_src = measured_peaks()
+    if args.profile is not None:
+        profile_sequence(mg, torch, args.profile)
+        return
     if args.form is not None:
         if args.form == "four_d":
             res = four_d(mg, torch, peaks, depth=args.four_d_depth)
