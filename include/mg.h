@@ -404,7 +404,10 @@ int mg_get_trace(mg_ctx* ctx, unsigned long long* out, int fine_slots, int chain
  * file-scope device array of 16384 doubles + 256 bytes that every GPU which
  * loads the library holds until exit.  The first call on a device looks up
  * that array's device address (cudaGetSymbolAddress, with the device
- * current), so make the first call on each device before any stream capture.
+ * current), so make the first call on each device before any stream capture;
+ * later calls outside capture look it up again (a device reset may move it),
+ * calls during capture use the cached address.  The context's device (the
+ * one current at mg_create) must be current: MG_ERR_INVALID otherwise.
  * Every call shares the array and it keeps the last call's contents (the
  * call clears the ticket itself); calls whose kernels overlap on the GPU
  * race on it.  Limit: one block per 256 vertices and one partial per block,

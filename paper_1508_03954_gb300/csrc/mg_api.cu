@@ -239,6 +239,7 @@ struct mg_ctx {
   cplx<double>* f_dev = nullptr;       // nodal f (fine)
   cplx<double>* scratch = nullptr;     // fine-size FP64 scratch
   double* k2dev = nullptr;             // fine k^2 field set from device memory (mg_set_k2)
+  int device = -1;                     // CUDA device current at creation
   bool k2_host_stale = false;          // k2 (host copy) older than k2dev
   cplx<double>* rvec = nullptr;        // fine residual vector (allocated on first use)
   double* host_norm = nullptr;         // pinned
@@ -2720,6 +2721,7 @@ static int create_ctx(int d, int depth, const double* k2_field, double theta_lay
     if (need > (double)fr) return fail(nullptr, MG_ERR_OOM, "grid too large for free device memory");
   }
   mg_ctx* c = new (std::nothrow) mg_ctx();
+  if (c != nullptr && cudaGetDevice(&c->device) != cudaSuccess) c->device = -1;
   if (c == nullptr) return fail(nullptr, MG_ERR_OOM, "host allocation failed");
   c->d = d;
   c->L = depth;
@@ -3586,14 +3588,25 @@ void* g_noalloc_addr[kNoAllocMaxDevices] = {};
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 namespace {
-// Device address of the scratch array on the current device, looked up once
-// per device (with that device current) by the first call that needs it.
+// Device address of the scratch array on the context's device, which must be
+// the current one.  Looked up (with that device current) by the first call on
+// the device and again by every call made outside stream capture, so an
+// address that changed with a device reset is picked up; calls during
+// capture use the cached address.
 int noalloc_scratch(mg_ctx* c, unsigned char** out) {
   int dev = -1;
   MG_CUDA(c, cudaGetDevice(&dev));
   if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(c, MG_ERR_INVALID, "device ordinal out of range");
+  if (c->device >= 0 && dev != c->device)
+    return fail(c, MG_ERR_INVALID, "mg_residual_noalloc: the current device is " + std::to_string(dev) +
+                                       ", the context was created on device " + std::to_string(c->device));
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(c->stream, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    cs = cudaStreamCaptureStatusNone;
+  }
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (g_noalloc_addr[dev] == nullptr) {
+  if (g_noalloc_addr[dev] == nullptr || cs == cudaStreamCaptureStatusNone) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || p == nullptr)

@@ -65,6 +65,30 @@ def test_noalloc_residual_matches_existing_entry_point(d, depth, varying):
     s.close()
 
 
+def test_noalloc_residual_norm_only():
+    """r = NULL: only the norm is formed, still equal to mg_residual_norm's."""
+    import torch
+
+    B.build()
+    mg.load()
+    d, depth = 2, 4
+    s = mg.Solver(d, depth, W.constant_k2(d, depth, 45.0), TH, 0.1)
+    s.set_stream(torch.cuda.current_stream().cuda_stream)
+    s.set_rhs(W.random_complex(d, depth, 31))
+    b = torch.empty(s.nv, dtype=torch.complex128, device="cuda")
+    s.get_level_device(depth, 1, b)
+    norm2 = torch.zeros(1, dtype=torch.float64, device="cuda")
+    for seed in (32, 33):
+        u0 = _zero_ring(W.random_complex(d, depth, seed))
+        s.set_solution(u0)
+        ref_abs, _ = s.residual_norm()
+        s.residual_noalloc(torch.from_numpy(u0.reshape(-1)).cuda(), b, None, norm2)
+        torch.cuda.synchronize()
+        got = math.sqrt(norm2.item())
+        assert abs(got - ref_abs) <= 1e-12 * ref_abs, (got, ref_abs)
+    s.close()
+
+
 def test_noalloc_residual_refuses_grids_above_its_limit():
     import torch
 
