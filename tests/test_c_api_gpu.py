@@ -1,6 +1,10 @@
-"""The library used from plain C through include/mg.h alone: a definite 2D
-solve to 1e-10 (checked again by mg_residual_norm inside the client) and a
-3D cycle from a page-locked host buffer (tests/c_api/solve_c.c)."""
+"""The library used from plain C through include/mg.h alone
+(tests/c_api/solve_c.c): a definite 2D solve to 1e-10 (checked again by
+mg_residual_norm inside the client), the same solve with complex64 cycles in
+FP64 defect correction (solutions within 1e-7), a 3D cycle from a page-locked
+host buffer, dynamic refinement of an adaptive grid, a batch of three
+problems, the adjoint calls with a device k^2 field, and coupled two-channel
+cycles."""
 import os
 import subprocess
 
