@@ -171,7 +171,10 @@ __global__ void __launch_bounds__(32 * (32 / RPT), 1)
   const bool bpx = A.hier && !A.hb;
   // restriction and coarse outputs: 4 warps x 25 lanes take the 10 x 10
   // coarse columns C0 .. C0+9 (column 9 only matters on the last tile)
-  const int ek = (warp < 4 && lane < 25) ? warp * 25 + lane : -1;
+  // (warps 0, 4, 3, 7: the sub-partitions that also hold the box rows 0 and
+  // 31, which need no residual, so the issue work per sub-partition evens out)
+  const int wsel = warp == 0 ? 0 : (warp == 4 ? 1 : (warp == 3 ? 2 : (warp == 7 ? 3 : -1)));
+  const int ek = (wsel >= 0 && lane < 25) ? wsel * 25 + lane : -1;
   const bool emit = ek >= 0 && A.has_coarse;
   const int ejx = emit ? ek % 10 : 0, ejy = emit ? ek / 10 : 0;
   const float m0 = A.row[0][0].x, m1 = A.row[0][1].x, m2 = A.row[0][2].x;

@@ -125,8 +125,13 @@ __global__ void __launch_bounds__(512, 1) sweep3sd_kernel(const Sweep3sdArgs A) 
   const bool use_c = A.fine && A.c != nullptr;
   const bool bpx = A.hier && !A.hb;
   // y/z-restriction and coarse outputs: 4 warps x 25 lanes take the 10 x 10
-  // coarse columns C0 .. C0+9 (column 9 only matters on the last tile)
-  const int ek = (warp < 4 && lane < 25) ? warp * 25 + lane : -1;
+  // coarse columns C0 .. C0+9 (column 9 only matters on the last tile).  The
+  // four are warps 0, 4 (sub-partition 0) and 3, 7 (sub-partition 3): those
+  // sub-partitions also hold warps 0 and 15, whose box rows 0 and 31 need no
+  // residual, so every sub-partition's FP64 unit gets about the same work
+  // between two barriers
+  const int wsel = warp == 0 ? 0 : (warp == 4 ? 1 : (warp == 3 ? 2 : (warp == 7 ? 3 : -1)));
+  const int ek = (wsel >= 0 && lane < 25) ? wsel * 25 + lane : -1;
   const bool emit = ek >= 0 && A.has_coarse;
   const int ejx = emit ? ek % 10 : 0, ejy = emit ? ek / 10 : 0;
   // unscaled rows are symmetric: (outer sum) * c0 + centre * c1
