@@ -125,15 +125,17 @@ def fine_sweep3_counts(depth, w, bpx=True):
       Jacobi 2 (6 with a complex factor), update 2, |r|^2 4;
       restriction R r (separable, x at c-columns, y at c-rows, z by
         accumulation), 7.6;
-      Galerkin rows G u_{l-1}: 27 real MACs per coarse vertex, 4;
-      BPX P I du: bilinear per c-plane + two weights per plane, 12.
+      Galerkin rows G u_{l-1}: 27 real MACs per coarse vertex, 4.
+    With the BPX transfer the fine sweep stores du and I du; P I du is
+    subtracted in the correction stage on the next coarser level (through
+    the pending correction), so it is not part of this kernel's work.
     Bytes: U, b read and U' written (3 x 16 B per fine vertex); pending
     correction read, b and u written on the next coarser level (3 x 16 B per
     coarse vertex)."""
     n = 3 ** depth
     f = axis_complex_fraction(depth, w)
     per = 14 + 24 + 20 + f * ((48 - 14) + (72 - 24) + (50 - 20))
-    per += 12.7 + 2 + 4 * (1 - (1 - f) ** 3) + 2 + 4 + 7.6 + 4 + (12 if bpx else 0)
+    per += 12.7 + 2 + 4 * (1 - (1 - f) ** 3) + 2 + 4 + 7.6 + 4
     flops = per * (n - 1) ** 3
     nbytes = 3 * 16 * (n + 1) ** 3 + 3 * 16 * (n // 3 + 1) ** 3
     return flops, nbytes

@@ -88,6 +88,7 @@ struct Hier {
     bool g3ok = false;        // 3D Galerkin-row tables available
     unsigned greal = 0;       // bit k: 1D Galerkin row class k is real (3D)
     unsigned* s3pref = nullptr; // 3D FP64 separable sweep: prefix sums of the unit costs
+    cplx<R>* idu = nullptr;     // 3D FP64 separable sweep, BPX: du at the c-points (level l-1 layout)
     // 2D FP64 path: Galerkin rows of G_{l-1} = R H_l P per coarse row class
     bool gok = false;
     int* order8 = nullptr;      // fine tiles (8 coarse cells) by decreasing cost
@@ -601,6 +602,9 @@ int build_hier(mg_ctx* c, Hier<R>& H) {
       }
       if ((rc = dalloc(c, H, (void**)&V.s3pref, pref.size() * sizeof(unsigned))) != MG_OK) return rc;
       MG_CUDA(c, cudaMemcpy(V.s3pref, pref.data(), pref.size() * sizeof(unsigned), cudaMemcpyHostToDevice));
+      if (std::is_same<R, double>::value &&
+          (rc = dalloc(c, H, (void**)&V.idu, (size_t)ipow(nc + 1, 3) * sizeof(cplx<R>))) != MG_OK)
+        return rc;
     }
     if (d == 2 && !H.varphi && V.n / 3 + 1 >= 200) {
       // LPT order of the 8-coarse-cell tiles: interior vertices weighted by
@@ -1120,6 +1124,7 @@ cudaError_t launch_sweep3sd(mg_ctx* c, Hier<double>& H, int l, bool fine, int hb
   A.gcoef = V.gcoef;
   A.greal = V.greal;
   A.upref = V.s3pref;
+  A.idu = (hier && !hb) ? V.idu : nullptr;
   axis_rows(c, V.n, A.row);
   for (size_t t = 0; t < V.diag.size() && t < 64; ++t) {
     const cd q = om / V.diag[t];
@@ -1300,16 +1305,33 @@ T* pinned_view(T* p) {
   return reinterpret_cast<T*>(a.devicePointer);
 }
 
+// Level l of a cycle on levels 1..s runs the complex128 separable 3D sweep
+// with the BPX transfer: it then stores t_l = du_l and I du_l, and the
+// correction stage forms du_l - P I du_l (the same test as the dispatch in
+// sweep3/sweep).
 template <typename R>
-cudaError_t prolong(mg_ctx* c, Hier<R>& H, int l) {
+bool sd_bpx_level(const mg_ctx* c, const Hier<R>& H, int l, int s, int hb, int hier) {
+  return std::is_same<R, double>::value && c->d == 3 && !H.varphi && l > 1 && H.lev[l].g3ok &&
+         interior_real(c) && hier && !hb && H.lev[l].idu != nullptr && H.lev[l].n >= (l == s ? 27 : 81);
+}
+
+// corr_l = T_l du_l + P corr_{l-1}.  Levels whose sweep stored t_l = du_l
+// and I du_l (BPX on the separable complex128 sweep) use
+// corr_l = du_l + P (corr_{l-1} - I du_l); when the finest level s did so,
+// corr_{s-1} (the pending correction) also takes - I du_s, so that
+// U + P corr_{s-1} = u + du_s - P I du_s + P corr_{s-1}.
+template <typename R>
+cudaError_t prolong(mg_ctx* c, Hier<R>& H, int l, int s, int hb, int hier) {
   auto& V = H.lev[l];
+  const cplx<R>* sub_c = sd_bpx_level(c, H, l, s, hb, hier) ? V.idu : nullptr;
+  const cplx<R>* sub_f = (l == s - 1 && sd_bpx_level(c, H, s, s, hb, hier)) ? H.lev[s].idu : nullptr;
   ++c->launches;
   if (c->d == 2)
     mg::prolong_add_kernel<R, 2><<<grid_for(V.nv), kThreads, 0, c->stream>>>(
-        V.n, V.t, H.lev[l - 1].corr, V.corr);
+        V.n, V.t, H.lev[l - 1].corr, V.corr, sub_c, sub_f);
   else
     mg::prolong_add_kernel<R, 3><<<grid_for(V.nv), kThreads, 0, c->stream>>>(
-        V.n, V.t, H.lev[l - 1].corr, V.corr);
+        V.n, V.t, H.lev[l - 1].corr, V.corr, sub_c, sub_f);
   return cudaGetLastError();
 }
 
@@ -1349,7 +1371,7 @@ cudaError_t enqueue_cycle_part(mg_ctx* c, Hier<R>& H, int s, int hb, int hier,
     }
   }
   for (int l = s - 1; l >= 1 && e == cudaSuccess; --l, ++*nkern) e = sweep(c, H, l, false, s, hb, hier, omega);
-  for (int l = 2; l <= s - 1 && e == cudaSuccess; ++l, ++*nkern) e = prolong(c, H, l);
+  for (int l = 2; l <= s - 1 && e == cudaSuccess; ++l, ++*nkern) e = prolong(c, H, l, s, hb, hier);
   return e;
 }
 

@@ -694,11 +694,17 @@ __global__ void zero_ring_kernel(int n, cplx<double>* u) {
 }
 
 // ---------------------------------------------------------------------------
-// corr_l = t_l + P corr_{l-1} on all vertices of level l (boundary stays 0).
+// corr_l = t_l + P (corr_{l-1} - sub_c) - sub_f on all vertices of level l
+// (boundary stays 0).  sub_c (on level l-1) and sub_f (on level l) may be
+// null.  With sub_c = I du_l this is the BPX correction
+// du_l - P I du_l + P corr_{l-1} of a level that stored t_l = du_l; sub_f =
+// I du_{l+1} takes the finer level's P I du into the pending correction.
 // ---------------------------------------------------------------------------
 template <typename R, int D>
 __global__ void prolong_add_kernel(int n, const cplx<R>* __restrict__ t,
-                                   const cplx<R>* __restrict__ cc, cplx<R>* __restrict__ out) {
+                                   const cplx<R>* __restrict__ cc, cplx<R>* __restrict__ out,
+                                   const cplx<R>* __restrict__ sub_c = nullptr,
+                                   const cplx<R>* __restrict__ sub_f = nullptr) {
   const int N = n + 1, Nc = n / 3 + 1;
   long long total = 1;
   for (int a = 0; a < D; ++a) total *= N;
@@ -724,8 +730,9 @@ __global__ void prolong_add_kernel(int n, const cplx<R>* __restrict__ t,
           ci += (long long)(g[a] / 3 + bit) * cs;
           cs *= Nc;
         }
-        if (w != R(0)) v = rfma(w, cc[ci], v);
+        if (w != R(0)) v = rfma(w, sub_c != nullptr ? cc[ci] - sub_c[ci] : cc[ci], v);
       }
+      if (sub_f != nullptr) v = v - sub_f[i];
     }
     out[i] = v;
   }

@@ -54,6 +54,9 @@ struct Sweep3sdArgs {
   cplx<double>* out;        // fine: U'; coarse: T du
   cplx<double>* b_coarse;
   cplx<double>* u_coarse;
+  cplx<double>* idu;        // BPX: du at the c-points (I du, level l-1 layout); the
+                            // output then holds du, and the correction stage
+                            // subtracts P I du (corr_l = du + P (corr_{l-1} - I du))
   const uint8_t* typ;       // axis class per fine index (n+1)
   const uint8_t* gtyp;      // Galerkin row class per coarse index (n/3+1)
   const cplx<double>* gcoef;  // [kMaxG3^3][27]
@@ -69,14 +72,11 @@ struct Sweep3sdArgs {
 struct Sweep3sdShared {
   cplx<double> za[2][32][32];  // M_z u of the plane (two planes in flight)
   cplx<double> zb[2][32][32];  // (K_z - phi M_z) u
-  cplx<double> pv[3][32][32];  // BPX: u + du of the fine planes waiting for P I du
   cplx<double> rx[2][32][10];  // r restricted along x at the c-columns C0 .. C0+9
-  cplx<double> dc[10][10];     // du at the c-points of the last c-plane
   cplx<double> q[3][11][11];   // u at the c-points of three c-planes, C0-1 .. C0+9
   cplx<double> cc[12][12];     // one coarse plane of the pending correction, C0-1 .. C0+10
   cplx<double> ccx[12][32];    // that plane interpolated along x to the box's columns
   cplx<double> cxy[2][32][32]; // P c at this column on the two coarse planes bracketing z + 1
-  cplx<double> pidp[32][32];   // BPX: P I du of the previous c-plane at this column
   cplx<double> pu[32][32];     // U(z + 1), copied asynchronously one step ahead
   cplx<double> pb[32][32];     // b(z), copied asynchronously one step ahead
   cplx<double> row[4][9];
@@ -152,12 +152,6 @@ __global__ void __launch_bounds__(512, 1) sweep3sd_kernel(const Sweep3sdArgs A) 
   // d-linear weights of the right / upper coarse vertex at fine offset o
   // (formed where used: they would otherwise hold registers all along)
   auto w1 = [](int o) { return o == 0 ? 0.0 : (o == 1 ? 1.0 / 3.0 : 2.0 / 3.0); };
-  // bilinear interpolation of a coarse 2D block at fine offsets (ox, o_y)
-  auto bil = [&](int o_y, const C& a, const C& b2, const C& c2, const C& d2) -> C {
-    const double wx1 = w1(ox), wx0 = 1.0 - wx1, wy1 = w1(o_y), wy0 = 1.0 - wy1;
-    return C{wy0 * fma(wx1, b2.x, wx0 * a.x) + wy1 * fma(wx1, d2.x, wx0 * c2.x),
-             wy0 * fma(wx1, b2.y, wx0 * a.y) + wy1 * fma(wx1, d2.y, wx0 * c2.y)};
-  };
   // x-restriction gather: lane = 10 * rr + jc (lanes 0..19) takes row rr of
   // the warp's pair at c-column jc, from box columns 3 jc + 1 .. 3 jc + 5
   const int xr_rr = lane / 10, xr_jc = lane % 10;
@@ -242,10 +236,9 @@ __global__ void __launch_bounds__(512, 1) sweep3sd_kernel(const Sweep3sdArgs A) 
 
     __syncthreads();  // the previous range's shared memory is free
     // per-column state kept in shared memory (private to the thread): the
-    // coarse correction on the bracketing planes and the BPX P I du
+    // coarse correction on the two planes bracketing z + 1
     C* cxy0 = &S.cxy[0][by[0]][lane];  // [r * 32]: row r
     C* cxy1 = &S.cxy[1][by[0]][lane];
-    C* pidp = &S.pidp[by[0]][lane];
     C ccpre = cz<double>();
 #pragma unroll
     for (int r = 0; r < RPT; ++r) cxy0[32 * r] = cxy1[32 * r] = cz<double>();
@@ -282,7 +275,6 @@ __global__ void __launch_bounds__(512, 1) sweep3sd_kernel(const Sweep3sdArgs A) 
         }
       }
       if (cpx && cpy[r]) S.q[qslot(Z0 - 1)][by[r] / 3][lane / 3] = um[r];
-      pidp[32 * r] = cz<double>();
     }
     // one plane staged ahead: step z takes U(z + 1) and b(z) from shared
     // memory; groups alternate U, b so that each wait leaves the newest
@@ -352,27 +344,6 @@ __global__ void __launch_bounds__(512, 1) sweep3sd_kernel(const Sweep3sdArgs A) 
           const int ci = Zc * NNc + cy * Nc + cx;
           A.b_coarse[ci] = bs;
           A.u_coarse[ci] = uc;
-        }
-      }
-      if (bpx && OZD == 0) {
-#pragma unroll
-        for (int r = 0; r < RPT; ++r) {
-          if (!owncol[r]) continue;
-          // P I du on this column from the c-points of c-plane zd / 3
-          const int jx = lane / 3 - 1, jy = by[r] / 3 - 1;
-          const C a = S.dc[jy][jx];
-          const C b2 = ox ? S.dc[jy][jx + 1] : cz<double>();
-          const C c2 = oy[r] ? S.dc[jy + 1][jx] : cz<double>();
-          const C d2 = (ox && oy[r]) ? S.dc[jy + 1][jx + 1] : cz<double>();
-          const C pid = bil(oy[r], a, b2, c2, d2);
-          if (zd - 2 >= 3 * Z0) {
-            const C v1 = S.pv[0][by[r]][lane], v2 = S.pv[1][by[r]][lane];
-            const C pp = pidp[32 * r];
-            A.out[(zd - 2) * NN + col[r]] = rfma(-1.0 / 3.0, pid, rfma(-2.0 / 3.0, pp, v1));
-            A.out[(zd - 1) * NN + col[r]] = rfma(-2.0 / 3.0, pid, rfma(-1.0 / 3.0, pp, v2));
-          }
-          if (zd < 3 * Z1 || zd == n) A.out[zd * NN + col[r]] = S.pv[2][by[r]][lane] - pid;
-          pidp[32 * r] = pid;
         }
       }
     };
@@ -463,7 +434,8 @@ __global__ void __launch_bounds__(512, 1) sweep3sd_kernel(const Sweep3sdArgs A) 
         }
         if (colin[r] && zin && lane >= 1 && lane <= 30) res[r] = rv;
         if (owncol[r] && zown) nrm = fma(res[r].x, res[r].x, fma(res[r].y, res[r].y, nrm));
-        // Jacobi update, c-point mask (hb), outputs or BPX hold
+        // Jacobi update, c-point mask (hb), outputs; BPX: I du at the owned
+        // c-points (the correction stage subtracts P I du)
         const C om = S.omd[tx + 4 * ty[r] + 16 * tz];
         C du;
         if (__all_sync(0xffffffffu, om.y == 0.0))
@@ -472,13 +444,10 @@ __global__ void __launch_bounds__(512, 1) sweep3sd_kernel(const Sweep3sdArgs A) 
           du = om * res[r];
         if (A.hb && OZ == 0 && cpx && cpy[r]) du = cz<double>();
         const C v = A.fine ? u0[r] + du : du;
-        if (!bpx) {
-          if (owncol[r] && zown) A.out[z * NN + col[r]] = v;
-        } else if (owncol[r]) {
-          S.pv[OZ == 1 ? 0 : (OZ == 2 ? 1 : 2)][by[r]][lane] = v;
+        if (owncol[r] && zown) {
+          A.out[z * NN + col[r]] = v;
+          if (bpx && OZ == 0 && cpx && cpy[r]) A.idu[((z / 3) * Nc + gy[r] / 3) * Nc + gx / 3] = du;
         }
-        if (bpx && OZ == 0 && cpx && cpy[r] && lane >= 3 && by[r] >= 3)
-          S.dc[by[r] / 3 - 1][lane / 3 - 1] = du;
       }
       // restriction along x to the c-columns, both rows by 20 lanes
       if (A.has_coarse) {
