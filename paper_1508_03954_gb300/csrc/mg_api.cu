@@ -89,6 +89,9 @@ struct Hier {
     unsigned greal = 0;       // bit k: 1D Galerkin row class k is real (3D)
     unsigned* s3pref = nullptr; // 3D FP64 separable sweep: prefix sums of the unit costs
     cplx<R>* idu = nullptr;     // 3D FP64 separable sweep, BPX: du at the c-points (level l-1 layout)
+    unsigned* s3split_f = nullptr;  // 3D separable sweeps: balanced unit ranges, finest-level grid
+    unsigned* s3split_c = nullptr;  //   and coarse-level grid
+    int s3grid_f = 0, s3grid_c = 0;
     // 2D FP64 path: Galerkin rows of G_{l-1} = R H_l P per coarse row class
     bool gok = false;
     int* order8 = nullptr;      // fine tiles (8 coarse cells) by decreasing cost
@@ -472,6 +475,48 @@ cudaError_t cell_shift_dev(mg_ctx* c, int l, R* phic) {
   return cudaGetLastError();
 }
 
+// Contiguous ranges of (tile, coarse plane) units for G blocks of the 3D
+// separable sweeps, minimising the largest range cost (binary search on the
+// bound, greedy fill).  A range pays its units' costs plus a warm-up of two
+// fine planes (2/3 of a unit) where it starts and wherever it enters a new
+// tile (each tile's z-march starts two planes early for the restriction).
+// Returns G + 1 unit indices (block b takes [r[b], r[b+1])).
+std::vector<unsigned> balanced_ranges(const std::vector<unsigned>& pref, int nc, int G) {
+  const size_t U = pref.size() - 1;
+  auto cost = [&](size_t u) { return (double)(pref[u + 1] - pref[u]); };
+  auto fill = [&](double T, std::vector<unsigned>* split) -> bool {
+    int b = 0;
+    double acc = 0.0;
+    long long tile = -1;
+    if (split) split->assign(1, 0u);
+    for (size_t u = 0; u < U; ++u) {
+      const long long t = (long long)(u / (size_t)nc);
+      const double add = cost(u) * (t != tile ? 5.0 / 3.0 : 1.0);
+      if (acc > 0.0 && acc + add > T) {
+        if (++b >= G) return false;
+        if (split) split->push_back((unsigned)u);
+        acc = cost(u) * 5.0 / 3.0;
+      } else {
+        acc += add;
+      }
+      tile = t;
+    }
+    if (split) {
+      while ((int)split->size() < G) split->push_back((unsigned)U);
+      split->push_back((unsigned)U);
+    }
+    return true;
+  };
+  double lo = 0.0, hi = 2.0 * (double)pref[U] + 1.0;
+  for (int it = 0; it < 60; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (fill(mid, nullptr)) hi = mid; else lo = mid;
+  }
+  std::vector<unsigned> split;
+  fill(hi, &split);
+  return split;
+}
+
 // Builds the arrays and tables of one precision.
 template <typename R>
 int build_hier(mg_ctx* c, Hier<R>& H) {
@@ -602,6 +647,17 @@ int build_hier(mg_ctx* c, Hier<R>& H) {
       }
       if ((rc = dalloc(c, H, (void**)&V.s3pref, pref.size() * sizeof(unsigned))) != MG_OK) return rc;
       MG_CUDA(c, cudaMemcpy(V.s3pref, pref.data(), pref.size() * sizeof(unsigned), cudaMemcpyHostToDevice));
+      // ranges for the launch grids of the finest-level and coarse-level sweeps
+      for (int k = 0; k < 2; ++k) {
+        const long long U = (long long)tl * tl * nc;
+        const long long upb = k == 0 ? 4 : (std::is_same<R, double>::value ? 2 : 1);
+        const int G = (int)std::min<long long>(152, std::max<long long>(1, (U + upb - 1) / upb));
+        const std::vector<unsigned> sp = balanced_ranges(pref, nc, G);
+        unsigned*& dst = k == 0 ? V.s3split_f : V.s3split_c;
+        if ((rc = dalloc(c, H, (void**)&dst, sp.size() * sizeof(unsigned))) != MG_OK) return rc;
+        MG_CUDA(c, cudaMemcpy(dst, sp.data(), sp.size() * sizeof(unsigned), cudaMemcpyHostToDevice));
+        (k == 0 ? V.s3grid_f : V.s3grid_c) = G;
+      }
       if (std::is_same<R, double>::value &&
           (rc = dalloc(c, H, (void**)&V.idu, (size_t)ipow(nc + 1, 3) * sizeof(cplx<R>))) != MG_OK)
         return rc;
@@ -1084,6 +1140,7 @@ cudaError_t launch_sweep3s(mg_ctx* c, Hier<float>& H, int l, bool fine, int hb, 
   A.ticket = H.ticket;
   A.norm2 = fine ? H.norm2 : nullptr;
   A.upref = V.s3pref;
+  A.usplit = fine ? V.s3split_f : V.s3split_c;
   A.spin_limit = c->spin_limit;
   A.err = c->dev_err;
   // the u and b planes come in by TMA: 34-column boxes of 32 rows
@@ -1091,9 +1148,9 @@ cudaError_t launch_sweep3s(mg_ctx* c, Hier<float>& H, int l, bool fine, int hb, 
   if (!plane_map<float>(&tmU, A.u, V.n, mg::kS3BoxW) || !plane_map<float>(&tmB, A.b, V.n, mg::kS3BoxW))
     return cudaErrorNotSupported;
   // fine levels: about four coarse planes per block at least (a range's first
-  // coarse step is overhead); coarse levels: every SM that has a unit
-  const long long upb = fine ? 4 : 1;
-  const long long grid = std::min<long long>(152, std::max<long long>(1, (A.nunits + upb - 1) / upb));
+  // coarse step is overhead); coarse levels: every SM that has a unit; the
+  // ranges were balanced for this grid at set-up
+  const int grid = fine ? V.s3grid_f : V.s3grid_c;
   // two box rows per thread (four: 255 registers, 8 warps per SM, 17% slower)
   mg::sweep3s_kernel<2><<<(int)grid, 512, sizeof(mg::Sweep3sShared) + 128, c->stream>>>(A, tmU, tmB);
   return cudaGetLastError();
@@ -1124,6 +1181,7 @@ cudaError_t launch_sweep3sd(mg_ctx* c, Hier<double>& H, int l, bool fine, int hb
   A.gcoef = V.gcoef;
   A.greal = V.greal;
   A.upref = V.s3pref;
+  A.usplit = fine ? V.s3split_f : V.s3split_c;
   A.idu = (hier && !hb) ? V.idu : nullptr;
   axis_rows(c, V.n, A.row);
   for (size_t t = 0; t < V.diag.size() && t < 64; ++t) {
@@ -1134,9 +1192,9 @@ cudaError_t launch_sweep3sd(mg_ctx* c, Hier<double>& H, int l, bool fine, int hb
   A.ticket = H.ticket;
   A.norm2 = fine ? H.norm2 : nullptr;
   // at least two coarse planes per block: a range starts with two fine
-  // planes of overhead (the restriction's lower halo)
-  const long long upb = fine ? 4 : 2;
-  const long long grid = std::min<long long>(152, std::max<long long>(1, (A.nunits + upb - 1) / upb));
+  // planes of overhead (the restriction's lower halo); the ranges were
+  // balanced for this grid at set-up
+  const int grid = fine ? V.s3grid_f : V.s3grid_c;
   mg::sweep3sd_kernel<<<(int)grid, 512, sizeof(mg::Sweep3sdShared), c->stream>>>(A);
   return cudaGetLastError();
 }

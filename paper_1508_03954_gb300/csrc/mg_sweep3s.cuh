@@ -53,6 +53,7 @@ struct Sweep3sArgs {
   int tiles_x;          // x-y tiles per axis (9 coarse cells each)
   long long nunits;     // tiles_x^2 * (n / 3)
   const unsigned* upref;    // prefix sums of the unit costs, nunits + 1 entries
+  const unsigned* usplit;   // block b takes units [usplit[b], usplit[b+1]) (null: by upref)
   unsigned spin_limit;      // polls before a plane wait gives up
   unsigned* err;            // sticky error flag (bit 2: a plane wait gave up)
   const cplx<float>* u;     // fine: pending U; coarse: u_l
@@ -208,8 +209,8 @@ __global__ void __launch_bounds__(32 * (32 / RPT), 1)
     }
     return (int)lo;
   };
-  int unit = first_at(Wt * blockIdx.x / gridDim.x);
-  const int uend = first_at(Wt * (blockIdx.x + 1) / gridDim.x);
+  int unit = A.usplit != nullptr ? (int)A.usplit[blockIdx.x] : first_at(Wt * blockIdx.x / gridDim.x);
+  const int uend = A.usplit != nullptr ? (int)A.usplit[blockIdx.x + 1] : first_at(Wt * (blockIdx.x + 1) / gridDim.x);
   while (unit < uend) {
     const int tile = unit / nc, Z0 = unit % nc;
     const int Z1 = min(nc, Z0 + (uend - unit));

@@ -48,6 +48,7 @@ struct Sweep3sdArgs {
   int tiles_x;              // x-y tiles per axis (9 coarse cells each)
   long long nunits;         // tiles_x^2 * (n / 3)
   const unsigned* upref;    // prefix sums of the unit costs, nunits + 1 entries
+  const unsigned* usplit;   // block b takes units [usplit[b], usplit[b+1]) (null: by upref)
   const cplx<double>* u;    // fine: pending U; coarse: u_l
   const cplx<double>* c;    // pending correction on level l-1 (fine only; may be null)
   const cplx<double>* b;
@@ -169,8 +170,8 @@ __global__ void __launch_bounds__(512, 1) sweep3sd_kernel(const Sweep3sdArgs A) 
     }
     return (int)lo;
   };
-  int unit = first_at(Wt * blockIdx.x / gridDim.x);
-  const int uend = first_at(Wt * (blockIdx.x + 1) / gridDim.x);
+  int unit = A.usplit != nullptr ? (int)A.usplit[blockIdx.x] : first_at(Wt * blockIdx.x / gridDim.x);
+  const int uend = A.usplit != nullptr ? (int)A.usplit[blockIdx.x + 1] : first_at(Wt * (blockIdx.x + 1) / gridDim.x);
   while (unit < uend) {
     const int tile = unit / nc, Z0 = unit % nc;
     const int Z1 = min(nc, Z0 + (uend - unit));
