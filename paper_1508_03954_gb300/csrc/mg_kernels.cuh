@@ -720,18 +720,21 @@ __global__ void prolong_add_kernel(int n, const cplx<R>* __restrict__ t,
     }
     cplx<R> v = cz<R>();
     if (inner) {
-      v = t[i];
+      // P with integer weights: the tripartite weights are k/3 per axis, so a
+      // corner's weight is an integer product over 3^D, applied once at the end
+      cplx<R> acc = cz<R>();
       for (int e = 0; e < (1 << D); ++e) {
-        R w = R(1);
+        int iw = 1;
         long long ci = 0, cs = 1;
         for (int a = 0; a < D; ++a) {
-          int bit = (e >> a) & 1;
-          w *= pw<R>(g[a] % 3, bit);
+          const int bit = (e >> a) & 1, o = g[a] % 3;
+          iw *= bit ? o : 3 - o;
           ci += (long long)(g[a] / 3 + bit) * cs;
           cs *= Nc;
         }
-        if (w != R(0)) v = rfma(w, sub_c != nullptr ? cc[ci] - sub_c[ci] : cc[ci], v);
+        if (iw != 0) acc = rfma((R)iw, sub_c != nullptr ? cc[ci] - sub_c[ci] : cc[ci], acc);
       }
+      v = rfma(R(1) / R(D == 2 ? 9 : 27), acc, t[i]);
       if (sub_f != nullptr) v = v - sub_f[i];
     }
     out[i] = v;
