@@ -155,3 +155,21 @@ def test_largest_3d_grid_keeps_the_symmetries_of_a_symmetric_problem():
               u[:, :, ::-1], u.transpose(1, 2, 0)[::-1, :, ::-1]]:
         assert np.abs(t - u).max() <= 1e-12 * scale
     assert u.shape == (n + 1,) * 3
+
+
+@pytest.mark.parametrize("var", [VARIANTS[0], VARIANTS[2]], ids=["add", "bpx"])
+def test_fmg_start_in_3d_matches_oracle(var):
+    """FMG grid unfolding in 3D (depth 4): the stages up to level 3 run the
+    separable sweep as their finest level (with BPX: du and I du stored, P I du
+    taken through the pending correction), so the interpolated start checks
+    that the pending correction is complete at every stage."""
+    depth = 4
+    k2 = W.constant_k2(3, depth, 30.0)
+    f = W.random_complex(3, depth, 41)
+    g = mg.Solver(3, depth, k2, TH, 0.1)
+    g.set_rhs(f)
+    om = np.array([0.6, 0.55, 0.6, 0.65])
+    g.fmg(var[0], om, var[1], 3)
+    ho = O.fmg_start(3, depth, k2, TH, 0.1, f, om, var[2], var[3], 3)
+    assert rel_l2(g.get_solution(), ho.u) <= TOL
+    g.close()
