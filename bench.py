@@ -621,8 +621,16 @@ def form_batched(mg, torch):
     (st, cyc, rel), dt = _wall(torch, lambda: bt.solve(mg.MG_ADD, oms, mg.MG_DLINEAR, 1e-8, 400, INNER))
     unknowns = sum((3 ** pr["depth"] - 1) ** 2 for pr in probs)
     upd = sum((3 ** pr["depth"] - 1) ** 2 * cyc[p] for p, pr in enumerate(probs))
+    # algorithmic bytes of one outer step per fine vertex: the FP64 residual
+    # (u, b read, complex64 rhs written: 40 B), INNER complex64 cycles (U, b
+    # read, U' written, ~12% more on the coarse levels: 27 B each) and the FP64
+    # update (u, e read, u written: 40 B)
+    outer_bytes = sum((3 ** pr["depth"] + 1) ** 2 for pr in probs) * (40 + 27 * INNER + 40)
+    hbm_gbs = outer_bytes / (ms / 1e3) / 1e9
     bb = {"problems": 256, "fine_unknowns": unknowns,
           "autotuned": {"tile": tc, "blocks_per_sm": bp, "ms_per_outer_step": ms},
+          "outer_step_hbm": {"algorithmic_bytes": outer_bytes, "achieved_gbs": hbm_gbs,
+                             "frac": hbm_gbs / 6703.8},
           "batched": {"seconds": dt, "all_ok": all(x == mg.MG_OK for x in st), "max_rel_res": max(rel),
                       "dof_updates_per_s": upd / dt}}
 
