@@ -822,7 +822,12 @@ cudaError_t configure_kernels() {
   set((const void*)mg::sweep3_kernel<double, 4, 256>, mg::Tile3<double, 4>::smem_bytes);
   set((const void*)mg::sweep3_kernel<float, 7, 512>, mg::Tile3<float, 7>::smem_bytes);
   set((const void*)mg::sweep3_kernel<float, 4, 256>, mg::Tile3<float, 4>::smem_bytes);
-  set((const void*)mg::sweep3s_kernel<2>, sizeof(mg::Sweep3sShared) + 128);
+  set((const void*)mg::sweep3s_kernel<2, true, false, false>, sizeof(mg::Sweep3sShared) + 128);
+  set((const void*)mg::sweep3s_kernel<2, true, true, false>, sizeof(mg::Sweep3sShared) + 128);
+  set((const void*)mg::sweep3s_kernel<2, true, false, true>, sizeof(mg::Sweep3sShared) + 128);
+  set((const void*)mg::sweep3s_kernel<2, false, false, false>, sizeof(mg::Sweep3sShared) + 128);
+  set((const void*)mg::sweep3s_kernel<2, false, true, false>, sizeof(mg::Sweep3sShared) + 128);
+  set((const void*)mg::sweep3s_kernel<2, false, false, true>, sizeof(mg::Sweep3sShared) + 128);
   set((const void*)mg::sweep3sd_kernel, sizeof(mg::Sweep3sdShared));
   set((const void*)mg::defect3_kernel<float>, sizeof(mg::Defect3Shared<float>));
   set((const void*)mg::defect3_kernel<double>, sizeof(mg::Defect3Shared<double>));
@@ -1151,8 +1156,19 @@ cudaError_t launch_sweep3s(mg_ctx* c, Hier<float>& H, int l, bool fine, int hb, 
   // coarse step is overhead); coarse levels: every SM that has a unit; the
   // ranges were balanced for this grid at set-up
   const int grid = fine ? V.s3grid_f : V.s3grid_c;
-  // two box rows per thread (four: 255 registers, 8 warps per SM, 17% slower)
-  mg::sweep3s_kernel<2><<<(int)grid, 512, sizeof(mg::Sweep3sShared) + 128, c->stream>>>(A, tmU, tmB);
+  // two box rows per thread (four: 255 registers, 8 warps per SM, 17% slower);
+  // one instantiation per level role and variant
+  const size_t sm = sizeof(mg::Sweep3sShared) + 128;
+  const bool bpx = hier && !hb;
+  if (fine) {
+    if (hb) mg::sweep3s_kernel<2, true, true, false><<<grid, 512, sm, c->stream>>>(A, tmU, tmB);
+    else if (bpx) mg::sweep3s_kernel<2, true, false, true><<<grid, 512, sm, c->stream>>>(A, tmU, tmB);
+    else mg::sweep3s_kernel<2, true, false, false><<<grid, 512, sm, c->stream>>>(A, tmU, tmB);
+  } else {
+    if (hb) mg::sweep3s_kernel<2, false, true, false><<<grid, 512, sm, c->stream>>>(A, tmU, tmB);
+    else if (bpx) mg::sweep3s_kernel<2, false, false, true><<<grid, 512, sm, c->stream>>>(A, tmU, tmB);
+    else mg::sweep3s_kernel<2, false, false, false><<<grid, 512, sm, c->stream>>>(A, tmU, tmB);
+  }
   return cudaGetLastError();
 }
 

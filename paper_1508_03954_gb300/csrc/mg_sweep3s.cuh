@@ -143,7 +143,10 @@ template <int O> __device__ __forceinline__ constexpr float W1() {
 // two columns, the y-pass of a row pair needs only the two outer neighbour
 // rows from shared memory, and 128 registers hold both columns' state (one
 // row per thread at 1024 threads was 15% slower and spilled at 64 registers).
-template <int RPT>
+// FINE, HB, BPX: the level's role and the variant, fixed at compile time so
+// that each instantiation carries only its own branches (the kernel is
+// issue-bound); A.fine, A.hb and A.hier must agree with them.
+template <int RPT, bool FINE, bool HB, bool BPX>
 __global__ void __launch_bounds__(32 * (32 / RPT), 1)
     sweep3s_kernel(const Sweep3sArgs A, const __grid_constant__ CUtensorMap tmU,
                    const __grid_constant__ CUtensorMap tmB) {
@@ -167,9 +170,8 @@ __global__ void __launch_bounds__(32 * (32 / RPT), 1)
   }
   __syncthreads();
   unsigned ph_u = 0, ph_b = 0;  // parity of the next wait, one bit per slot
-  const bool zero_u = A.fine && A.first;
-  const bool use_c = A.fine && !A.first && A.c != nullptr;
-  const bool bpx = A.hier && !A.hb;
+  constexpr bool use_c = FINE;  // a finest level always has a pending correction level
+  constexpr bool bpx = BPX;
   // restriction and coarse outputs: 4 warps x 25 lanes take the 10 x 10
   // coarse columns C0 .. C0+9 (column 9 only matters on the last tile)
   // (warps 0, 4, 3, 7: the sub-partitions that also hold the box rows 0 and
@@ -276,7 +278,7 @@ __global__ void __launch_bounds__(32 * (32 / RPT), 1)
       return &S.bb[k][0][xsh];
     };
     auto plane_val = [&](const C* pl, int r) -> C {
-      return zero_u ? cz<float>() : pl[by[r] * kS3BoxW + lane];
+      return pl[by[r] * kS3BoxW + lane];
     };
 
     __syncthreads();  // the previous range's shared memory is free
@@ -473,8 +475,8 @@ __global__ void __launch_bounds__(32 * (32 / RPT), 1)
         if (owncol[r] && zown) nrm = fmaf(res.x, res.x, fmaf(res.y, res.y, nrm));
         // Jacobi update, c-point mask (hb), outputs or BPX hold
         C du = S.omd[tx + 4 * ty[r] + 16 * tz] * res;
-        if (A.hb && OZ == 0 && cpx && cpy[r]) du = cz<float>();
-        const C v = A.fine ? u0[r] + du : du;
+        if (HB && OZ == 0 && cpx && cpy[r]) du = cz<float>();
+        const C v = FINE ? u0[r] + du : du;
         if (!bpx) {
           if (owncol[r] && zown) A.out[z * NN + col[r]] = v;
         } else if (owncol[r]) {
@@ -514,7 +516,7 @@ __global__ void __launch_bounds__(32 * (32 / RPT), 1)
       }
     }
   }
-  if (A.fine && A.norm2 != nullptr)
+  if (FINE && A.norm2 != nullptr)
     block_norm_finish_tile<NTHR>((double)nrm, s_red, A.partial, A.ticket, A.norm2, blockIdx.x,
                                          gridDim.x);
 }
