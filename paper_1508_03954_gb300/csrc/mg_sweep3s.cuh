@@ -318,12 +318,13 @@ __global__ void __launch_bounds__(32 * (32 / RPT), 1)
       // u on planes 3 Z0 - 3 (c-plane Z0 - 1) and 3 Z0 - 2
       um[r] = plane_val(plm, r);
       u0[r] = plane_val(pl0, r);
-      if (use_c && colin[r]) {
-        if (3 * Z0 - 3 > 0) um[r] = um[r] + cxy0[r];
-        if (3 * Z0 - 2 > 0) {
-          u0[r] = rfma(W0<1>(), cxy0[r], u0[r]);
-          u0[r] = rfma(W1<1>(), cxy1[r], u0[r]);
-        }
+      // P c is exactly zero on and beyond the Dirichlet ring (the coarse
+      // correction's ring is zero and the coarse plane loads are zero outside
+      // the grid), so it is added without tests
+      if (use_c) {
+        um[r] = um[r] + cxy0[r];
+        u0[r] = rfma(W0<1>(), cxy0[r], u0[r]);
+        u0[r] = rfma(W1<1>(), cxy1[r], u0[r]);
       }
       if (cpx && cpy[r]) S.q[qslot(Z0 - 1)][by[r] / 3][lane / 3] = um[r];
       pidp[r] = cz<float>();
@@ -414,7 +415,7 @@ __global__ void __launch_bounds__(32 * (32 / RPT), 1)
       for (int r = 0; r < RPT; ++r) {
         if (OZP == 0) cxy0[r] = cxy1[r];
         up[r] = plane_val(plp, r);
-        if (use_c && colin[r] && zp > 0 && zp < n) {
+        if (use_c) {  // zero on and beyond the ring (see the first planes)
           up[r] = rfma(W0<OZP>(), cxy0[r], up[r]);
           if (OZP != 0) up[r] = rfma(W1<OZP>(), cxy1[r], up[r]);
         }
@@ -471,8 +472,12 @@ __global__ void __launch_bounds__(32 * (32 / RPT), 1)
           hu = tap3c_acc(rw + 3, el, ey, er, tap3c_acc(rw, cl, cy, cr, cz<float>()));
         }
         C res = cz<float>();
-        if (colin[r] && zin && lane >= 1 && lane <= 30) res = plb[by[r] * kS3BoxW + lane] - hu;
-        if (owncol[r] && zown) nrm = fmaf(res.x, res.x, fmaf(res.y, res.y, nrm));
+        {
+          const C rr = plb[by[r] * kS3BoxW + lane] - hu;
+          res = (colin[r] && zin && lane >= 1 && lane <= 30) ? rr : cz<float>();
+          const C rn = (owncol[r] && zown) ? res : cz<float>();
+          nrm = fmaf(rn.x, rn.x, fmaf(rn.y, rn.y, nrm));
+        }
         // Jacobi update, c-point mask (hb), outputs or BPX hold
         C du = S.omd[tx + 4 * ty[r] + 16 * tz] * res;
         if (HB && OZ == 0 && cpx && cpy[r]) du = cz<float>();
@@ -488,8 +493,8 @@ __global__ void __launch_bounds__(32 * (32 / RPT), 1)
         if (A.has_coarse) {
           const C r1l = shfl_c(res, 1, true), r1r = shfl_c(res, 1, false);
           const C r2l = shfl_c(res, 2, true), r2r = shfl_c(res, 2, false);
-          if (cpx && lane >= 3 && lane <= 30)
-            S.rx[buf][by[r]][lane / 3 - 1] = restrict5f(r2l, r1l, res, r1r, r2r);
+          const C rxv = restrict5f(r2l, r1l, res, r1r, r2r);
+          if (cpx && lane >= 3 && lane <= 30) S.rx[buf][by[r]][lane / 3 - 1] = rxv;
         }
       }
 #pragma unroll
