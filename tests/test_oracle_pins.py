@@ -717,3 +717,57 @@ def test_fmg_start_is_the_prolongated_discrete_solution_of_the_coarser_stage(d, 
     # H s = d kappa mu^(d-1) s and M s = mu^d s for the sine mode s
     exact = d * math.pi ** 2 * mu ** d / (d * kap * mu ** (d - 1)) * _sine_mode(d, m)
     np.testing.assert_allclose(hs.u, O.prolong(exact.astype(complex)), rtol=0, atol=1e-9)
+
+
+@pytest.mark.parametrize("variant,transfer", [(O.ADD, O.DLINEAR), (O.HB, O.DLINEAR),
+                                              (O.ADD, O.HIERARCHICAL), (O.HB, O.HIERARCHICAL)])
+@pytest.mark.parametrize("d,depth,varying", [(2, 3, False), (2, 3, True), (3, 2, True)])
+def test_fas_cycle_equals_dense_fas_restatement_without_galerkin(variant, transfer, d, depth, varying):
+    """Where rediscretisation is not the Galerkin product -- a layer edge inside
+    coarse cells (w = 0.1) and, optionally, a varying shift -- the FAS cycle is
+    not the correction scheme (Lemma 2 needs Galerkin), so it is pinned against
+    Algorithm 4 restated with dense matrices on the interior unknowns: each
+    level's operator from unit vectors, P from Kronecker products of 1D
+    tripartite interpolation, R = P^T, I as the c-point selection, two
+    cycles."""
+    n = 3 ** depth
+    rng = np.random.default_rng(21)
+    k2 = rng.uniform(-30, 90, size=(n + 1,) * d) if varying else np.full((n + 1,) * d, 40.0)
+    w = 0.1
+    H = O.Hierarchy(d, depth, k2, TH, w)
+    f = rng.standard_normal((n + 1,) * d) + 1j * rng.standard_normal((n + 1,) * d)
+    u0 = rng.standard_normal((n + 1,) * d) + 1j * rng.standard_normal((n + 1,) * d)
+    H.set_rhs_nodal(f)
+    H.set_solution(u0)
+    omega = np.array([0.5 - 0.03j, 0.6, 0.65 + 0.02j][:depth])
+    A, idx, dg = {}, {}, {}
+    for lev in range(1, depth + 1):
+        stride = 3 ** (depth - lev)
+        k2l = k2[(slice(None, None, stride),) * d]  # coarse levels sample k^2 at their vertices
+        A[lev], idx[lev], _ = dense_level(d, lev, k2l, TH, w)
+        dg[lev] = np.diag(A[lev])
+    Ps = {lev: kron_all([interp_1d(3 ** (lev - 1))] * d) for lev in range(2, depth + 1)}
+    cps = {lev: np.array([all(i % 3 == 0 for i in t) for t in idx[lev]]) for lev in range(1, depth + 1)}
+    u = np.array([H.u[i] for i in idx[depth]])
+    b = np.array([H.b[i] for i in idx[depth]])
+    for _ in range(2):
+        ul, bl, du = {depth: u}, {depth: b}, {}
+        for lev in range(depth, 0, -1):
+            r = bl[lev] - A[lev] @ ul[lev]
+            du[lev] = omega[lev - 1] * r / dg[lev]
+            if lev > 1:
+                ul[lev - 1] = ul[lev][cps[lev]]
+                uh = ul[lev] - Ps[lev] @ ul[lev - 1]
+                bl[lev - 1] = Ps[lev].T @ (bl[lev] - A[lev] @ uh)
+        corr = None
+        for lev in range(1, depth + 1):
+            t = du[lev]
+            if variant == O.HB:
+                t = np.where(cps[lev], 0, t)
+            if transfer == O.HIERARCHICAL and lev > 1:
+                t = t - Ps[lev] @ t[cps[lev]]
+            corr = t if lev == 1 else t + Ps[lev] @ corr
+        u = u + corr
+        H.cycle(omega, variant, transfer)
+        got = np.array([H.u[i] for i in idx[depth]])
+        np.testing.assert_allclose(got, u, rtol=0, atol=1e-12 * np.abs(u).max())
