@@ -22,6 +22,7 @@
 #include "mg_sweep3s.cuh"
 #include "mg_defect3.cuh"
 #include "mg_sweep3sd.cuh"
+#include "mg_coarse3.cuh"
 #include "mg_sweep2w.cuh"
 #include "mg_persist.cuh"
 #include "mg_adjoint.cuh"
@@ -88,7 +89,8 @@ struct Hier {
     bool g3ok = false;        // 3D Galerkin-row tables available
     unsigned greal = 0;       // bit k: 1D Galerkin row class k is real (3D)
     unsigned* s3pref = nullptr; // 3D FP64 separable sweep: prefix sums of the unit costs
-    cplx<R>* idu = nullptr;     // 3D FP64 separable sweep, BPX: du at the c-points (level l-1 layout)
+    cplx<R>* idu = nullptr;     // 3D BPX with stored du (separable FP64 sweep, point levels): du at the c-points (level l-1 layout)
+    cplx<R>* r = nullptr;       // 3D point levels (mg_coarse3.cuh): r_l for the next coarser level's restriction
     unsigned* s3split_f = nullptr;  // 3D separable sweeps: balanced unit ranges, finest-level grid
     unsigned* s3split_c = nullptr;  //   and coarse-level grid
     int s3grid_f = 0, s3grid_c = 0;
@@ -315,6 +317,10 @@ Widths widths(const mg_ctx* c, int n) {
 // take the rows of cells outside the layer as real; a rotated interior makes
 // them complex and sends every level to the kernels with complex rows.
 bool interior_real(const mg_ctx* c) { return c->theta_in == 0.0; }
+
+// Coarse 3D levels up to 81 cells per axis with a constant shift run the
+// one-thread-per-vertex kernel (mg_coarse3.cuh) within a cycle.
+constexpr int kPoint3MaxN = 81;
 
 // Stencil rows of the d-linear element operator for every vertex type.  A
 // vertex of type t has left/right cell widths hl, hr along each axis; its
@@ -660,6 +666,14 @@ int build_hier(mg_ctx* c, Hier<R>& H) {
       }
       if (std::is_same<R, double>::value &&
           (rc = dalloc(c, H, (void**)&V.idu, (size_t)ipow(nc + 1, 3) * sizeof(cplx<R>))) != MG_OK)
+        return rc;
+    }
+    if (d == 3 && !H.varphi && l > 1 && V.g3ok && V.n <= kPoint3MaxN) {
+      // a coarse level of the point kernel: its residual (read by the next
+      // coarser level's restriction) and, for BPX, du at its c-points
+      if ((rc = dalloc(c, H, (void**)&V.r, bytes)) != MG_OK) return rc;
+      if (V.idu == nullptr &&
+          (rc = dalloc(c, H, (void**)&V.idu, (size_t)ipow(V.n / 3 + 1, 3) * sizeof(cplx<R>))) != MG_OK)
         return rc;
     }
     if (d == 2 && !H.varphi && V.n / 3 + 1 >= 200) {
@@ -1306,6 +1320,56 @@ cudaError_t sweep3(mg_ctx* c, Hier<R>& H, int l, bool fine, int hb, int hier, co
   }
 }
 
+// Level l < s of a cycle on levels 1..s runs the point kernel (mg_coarse3.cuh):
+// 3D, constant shift, at most kPoint3MaxN cells per axis.
+template <typename R>
+bool point3_level(const mg_ctx* c, const Hier<R>& H, int l, int s) {
+  if (c->d != 3 || H.varphi || l < 1 || l >= s) return false;
+  const auto& V = H.lev[l];
+  return V.n <= kPoint3MaxN && (l == 1 || (V.g3ok && V.r != nullptr && V.idu != nullptr));
+}
+
+// A coarse level of the point kernel: its right-hand side is formed here from
+// the finer level's stored residual when that level was a point level too.
+template <typename R>
+cudaError_t launch_coarse3(mg_ctx* c, Hier<R>& H, int l, int s, int hb, int hier, const cd& om) {
+  auto& V = H.lev[l];
+  mg::Coarse3Args<R> A;
+  std::memset(&A, 0, sizeof(A));
+  A.n = V.n;
+  A.fused = point3_level(c, H, l + 1, s) ? 1 : 0;
+  A.has_coarse = l > 1 ? 1 : 0;
+  A.hb = hb;
+  A.realrow = V.realrow3;
+  A.u = V.u[0];
+  A.b = V.b;
+  if (A.fused) {
+    const auto& F = H.lev[l + 1];
+    A.rf = F.r;
+    A.gtyp = F.gtyp;
+    A.gcoef = F.gcoef;
+    A.greal = F.greal;
+  }
+  A.typ = V.typ;
+  A.coef = V.coefH;
+  for (size_t t = 0; t < V.diag.size() && t < 64; ++t) {
+    const cd q = om / V.diag[t];
+    A.omd[t] = cplx<R>{(R)q.real(), (R)q.imag()};
+  }
+  A.r = V.r;
+  A.t = V.t;
+  A.idu = (l > 1 && hier && !hb) ? V.idu : nullptr;
+  A.u_coarse = l > 1 ? H.lev[l - 1].u[0] : nullptr;
+  // lanes per vertex: one where the level fills the GPU, more on the small,
+  // FP64-latency-bound levels (blocks of 128 threads spread them over the SMs)
+  const int lpv = V.nv > 200000 ? 1 : (V.nv > 8000 ? 2 : 32);
+  const long long blocks = std::min<long long>(((long long)V.nv * lpv + 127) / 128, 152 * 16);
+  if (lpv == 1) mg::coarse3_kernel<R, 1><<<(int)blocks, 128, 0, c->stream>>>(A);
+  else if (lpv == 2) mg::coarse3_kernel<R, 2><<<(int)blocks, 128, 0, c->stream>>>(A);
+  else mg::coarse3_kernel<R, 32><<<(int)blocks, 128, 0, c->stream>>>(A);
+  return cudaGetLastError();
+}
+
 template <typename R>
 cudaError_t sweep(mg_ctx* c, Hier<R>& H, int l, bool fine, int s_active, int hb, int hier,
                   const cplx<double>* omega) {
@@ -1313,6 +1377,7 @@ cudaError_t sweep(mg_ctx* c, Hier<R>& H, int l, bool fine, int s_active, int hb,
   ++c->launches;
   if (c->d == 3 && !H.varphi && (l == 1 || V.g3ok)) {
     const cplx<double> w = omega[l - 1 + (H.L - s_active)];
+    if (!fine && point3_level(c, H, l, s_active)) return launch_coarse3(c, H, l, s_active, hb, hier, cd(w.x, w.y));
     return sweep3(c, H, l, fine, hb, hier, cd(w.x, w.y));
   }
   if constexpr (std::is_same<R, float>::value) {
@@ -1397,14 +1462,15 @@ bool sd_bpx_level(const mg_ctx* c, const Hier<R>& H, int l, int s, int hb, int h
 template <typename R>
 cudaError_t prolong(mg_ctx* c, Hier<R>& H, int l, int s, int hb, int hier) {
   auto& V = H.lev[l];
-  const cplx<R>* sub_c = sd_bpx_level(c, H, l, s, hb, hier) ? V.idu : nullptr;
+  const bool stored_du = point3_level(c, H, l, s) ? (l > 1 && hier && !hb) : sd_bpx_level(c, H, l, s, hb, hier);
+  const cplx<R>* sub_c = stored_du ? V.idu : nullptr;
   const cplx<R>* sub_f = (l == s - 1 && sd_bpx_level(c, H, s, s, hb, hier)) ? H.lev[s].idu : nullptr;
   ++c->launches;
   if (c->d == 2)
     mg::prolong_add_kernel<R, 2><<<grid_for(V.nv), kThreads, 0, c->stream>>>(
         V.n, V.t, H.lev[l - 1].corr, V.corr, sub_c, sub_f);
   else
-    mg::prolong_add_kernel<R, 3><<<grid_for(V.nv), kThreads, 0, c->stream>>>(
+    mg::prolong3_kernel<R><<<(int)ipow((V.n + 1 + 8) / 9, 3), 256, 0, c->stream>>>(
         V.n, V.t, H.lev[l - 1].corr, V.corr, sub_c, sub_f);
   return cudaGetLastError();
 }
