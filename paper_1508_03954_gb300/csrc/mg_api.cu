@@ -1863,8 +1863,33 @@ int ensure_r0(mg_ctx* c) {
 // rhs of level s from the stored nodal f: b_s = M_s (f sampled on level s)
 int set_level_rhs(mg_ctx* c, int s) {
   auto& H = c->h64;
-  cudaError_t e = stencil<double, double>(c, H, s, (int)ipow(3, c->L - s), c->f_dev, nullptr,
-                                          H.lev[s].coefM, false, H.lev[s].b, -1);
+  cudaError_t e;
+  if (c->d == 3) {
+    // b = M_x M_y M_z f: z-pass from the (strided) fine f into b, y-pass into
+    // the scratch array, x-pass back into b
+    auto& V = H.lev[s];
+    mg::MassRows3 mr;
+    cplx<double> row[4][9];
+    axis_rows(c, V.n, row);
+    mr.real = 0;
+    for (int t = 0; t < 4; ++t) {
+      bool re = true;
+      for (int j = 0; j < 3; ++j) {
+        mr.m[t][j] = row[t][j];
+        re = re && row[t][j].y == 0.0;
+      }
+      if (re) mr.real |= 1u << t;
+    }
+    const int g = grid_for(V.nv);
+    c->launches += 3;
+    mg::mass_pass3_kernel<2><<<g, kThreads, 0, c->stream>>>(V.n, (int)ipow(3, c->L - s), c->f_dev, V.b, V.typ, mr);
+    mg::mass_pass3_kernel<1><<<g, kThreads, 0, c->stream>>>(V.n, 1, V.b, c->scratch, V.typ, mr);
+    mg::mass_pass3_kernel<0><<<g, kThreads, 0, c->stream>>>(V.n, 1, c->scratch, V.b, V.typ, mr);
+    e = cudaGetLastError();
+  } else {
+    e = stencil<double, double>(c, H, s, (int)ipow(3, c->L - s), c->f_dev, nullptr, H.lev[s].coefM, false,
+                                H.lev[s].b, -1);
+  }
   if (e != cudaSuccess) return fail(c, MG_ERR_CUDA, cudaGetErrorString(e));
   return MG_OK;
 }

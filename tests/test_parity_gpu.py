@@ -119,12 +119,14 @@ def test_config2_full_size_iterates():
 
 
 # ------------------------------------------------------------------ pieces
-def test_rhs_and_restricted_rhs_and_injection():
-    depth = 4
-    k2 = W.constant_k2(2, depth, 50.0)
-    f = W.random_complex(2, depth, 3)
-    u0 = W.random_complex(2, depth, 4)
-    g, o = pair(2, depth, k2, TH, 0.1, f, u0)
+@pytest.mark.parametrize("d,depth", [(2, 4), (3, 3), (3, 4)])
+def test_rhs_and_restricted_rhs_and_injection(d, depth):
+    # 3D: b_L = M f by separable mass passes; b_l of the coarse levels from the
+    # level sweeps and from the point kernels' restriction of the stored residual
+    k2 = W.constant_k2(d, depth, 50.0)
+    f = W.random_complex(d, depth, 3)
+    u0 = W.random_complex(d, depth, 4)
+    g, o = pair(d, depth, k2, TH, 0.1, f, u0)
     assert rel_l2(g.get_level(depth, 1), o.b) <= 1e-13
     tr = {}
     g.cycle(mg.MG_ADD, np.full(depth, 0.6), mg.MG_DLINEAR)
