@@ -1362,10 +1362,10 @@ cudaError_t launch_coarse3(mg_ctx* c, Hier<R>& H, int l, int s, int hb, int hier
   A.u_coarse = l > 1 ? H.lev[l - 1].u[0] : nullptr;
   // lanes per vertex: one where the level fills the GPU, more on the small,
   // FP64-latency-bound levels (blocks of 128 threads spread them over the SMs)
-  const int lpv = V.nv > 200000 ? 1 : (V.nv > 8000 ? 2 : 32);
+  const int lpv = V.nv > 200000 ? 1 : (V.nv > 8000 ? 8 : 32);
   const long long blocks = std::min<long long>(((long long)V.nv * lpv + 127) / 128, 152 * 16);
   if (lpv == 1) mg::coarse3_kernel<R, 1><<<(int)blocks, 128, 0, c->stream>>>(A);
-  else if (lpv == 2) mg::coarse3_kernel<R, 2><<<(int)blocks, 128, 0, c->stream>>>(A);
+  else if (lpv == 8) mg::coarse3_kernel<R, 8><<<(int)blocks, 128, 0, c->stream>>>(A);
   else mg::coarse3_kernel<R, 32><<<(int)blocks, 128, 0, c->stream>>>(A);
   return cudaGetLastError();
 }
