@@ -628,13 +628,13 @@ int build_hier(mg_ctx* c, Hier<R>& H) {
       // are FP64 operations per lane -- z-pair on the 32 box rows (10 real,
       // 24 complex), y-pair (16 / 36), x-pass (12 / 26) and the rest (~30) on
       // the 30 residual rows; complex64 is bound by instruction issue, where
-      // the complex passes add about half as much relative to a row's other
-      // work (measured: the FP64 weights overload the interior blocks by as
-      // much as equal units overload the layer blocks).  Blocks take ranges of
-      // equal cost.
-      const unsigned cz_ = std::is_same<R, double>::value ? 14u : 7u;
-      const unsigned cx_ = std::is_same<R, double>::value ? 14u : 7u;
-      const unsigned cy_ = std::is_same<R, double>::value ? 20u : 10u;
+      // the complex passes add less than a third as much relative to a row's
+      // other work (weights 4 / 4 / 6 measured fastest; 7 / 7 / 10 and
+      // 10 / 10 / 14 left the slowest blocks 1-5% further behind).  Blocks
+      // take ranges of equal cost.
+      const unsigned cz_ = std::is_same<R, double>::value ? 14u : 4u;
+      const unsigned cx_ = std::is_same<R, double>::value ? 14u : 4u;
+      const unsigned cy_ = std::is_same<R, double>::value ? 20u : 6u;
       const int n = V.n, nc = n / 3, tl = (nc + 8) / 9;
       std::vector<unsigned> pref((size_t)tl * tl * nc + 1, 0u);
       size_t u = 0;

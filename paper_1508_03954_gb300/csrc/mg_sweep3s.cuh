@@ -118,6 +118,19 @@ __device__ __forceinline__ cplx<float> shfl_c(cplx<float> v, int delta, bool up)
   }
   return o;
 }
+// Stores taken by some lanes only, as predicated instructions: the other
+// lanes skip them without a divergent branch and its reconvergence (the
+// address is formed by every lane and used by none whose predicate is false).
+__device__ __forceinline__ void st_global_if(cplx<float>* p, cplx<float> v, bool pred) {
+  asm volatile("{\n .reg .pred q;\n setp.ne.u32 q, %3, 0;\n @q st.global.v2.f32 [%0], {%1, %2};\n}\n" ::"l"(p),
+               "f"(v.x), "f"(v.y), "r"((unsigned)pred));
+}
+__device__ __forceinline__ void st_shared_if(cplx<float>* p, cplx<float> v, bool pred) {
+  asm volatile("{\n .reg .pred q;\n setp.ne.u32 q, %3, 0;\n @q st.shared.v2.f32 [%0], {%1, %2};\n}\n" ::"r"(
+                   smem_u32(p)),
+               "f"(v.x), "f"(v.y), "r"((unsigned)pred)
+               : "memory");
+}
 __device__ __forceinline__ cplx<float> ld_nc(const cplx<float>* p) {
   const float2 v = __ldg(reinterpret_cast<const float2*>(p));
   return cplx<float>{v.x, v.y};
@@ -419,7 +432,7 @@ __global__ void __launch_bounds__(32 * (32 / RPT), 1)
           up[r] = rfma(W0<OZP>(), cxy0[r], up[r]);
           if (OZP != 0) up[r] = rfma(W1<OZP>(), cxy1[r], up[r]);
         }
-        if (OZP == 0 && cpx && cpy[r]) S.q[qslot(zp / 3)][by[r] / 3][lane / 3] = up[r];
+        if (OZP == 0) st_shared_if(&S.q[qslot(zp / 3)][by[r] / 3][lane / 3], up[r], cpx && cpy[r]);
         if (tz == 0) {
           za[r] = tap3r(m0, m1, m2, um[r], u0[r], up[r]);
           zb[r] = tap3r(p0, p1, p2, um[r], u0[r], up[r]);
@@ -483,7 +496,7 @@ __global__ void __launch_bounds__(32 * (32 / RPT), 1)
         if (HB && OZ == 0 && cpx && cpy[r]) du = cz<float>();
         const C v = FINE ? u0[r] + du : du;
         if (!bpx) {
-          if (owncol[r] && zown) A.out[z * NN + col[r]] = v;
+          st_global_if(A.out + ((long long)z * NN + col[r]), v, owncol[r] && zown);
         } else if (owncol[r]) {
           S.pv[OZ == 1 ? 0 : (OZ == 2 ? 1 : 2)][by[r]][lane] = v;
         }
@@ -494,7 +507,7 @@ __global__ void __launch_bounds__(32 * (32 / RPT), 1)
           const C r1l = shfl_c(res, 1, true), r1r = shfl_c(res, 1, false);
           const C r2l = shfl_c(res, 2, true), r2r = shfl_c(res, 2, false);
           const C rxv = restrict5f(r2l, r1l, res, r1r, r2r);
-          if (cpx && lane >= 3 && lane <= 30) S.rx[buf][by[r]][lane / 3 - 1] = rxv;
+          st_shared_if(&S.rx[buf][by[r]][lane >= 3 ? lane / 3 - 1 : 0], rxv, cpx && lane >= 3 && lane <= 30);
         }
       }
 #pragma unroll
