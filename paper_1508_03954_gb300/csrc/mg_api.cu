@@ -1321,12 +1321,17 @@ cudaError_t sweep3(mg_ctx* c, Hier<R>& H, int l, bool fine, int hb, int hier, co
 }
 
 // Level l < s of a cycle on levels 1..s runs the point kernel (mg_coarse3.cuh):
-// 3D, constant shift, at most kPoint3MaxN cells per axis.
+// 3D, constant shift, at most kPoint3MaxN cells per axis, and every coarser
+// level a point level too (a point level leaves its coarse right-hand side to
+// the next coarser level's launch, which must therefore be one).
 template <typename R>
 bool point3_level(const mg_ctx* c, const Hier<R>& H, int l, int s) {
-  if (c->d != 3 || H.varphi || l < 1 || l >= s) return false;
-  const auto& V = H.lev[l];
-  return V.n <= kPoint3MaxN && (l == 1 || (V.g3ok && V.r != nullptr && V.idu != nullptr));
+  if (c->d != 3 || H.varphi || l < 1 || l >= s || H.lev[l].n > kPoint3MaxN) return false;
+  for (int k = 2; k <= l; ++k) {
+    const auto& V = H.lev[k];
+    if (!V.g3ok || V.r == nullptr || V.idu == nullptr) return false;
+  }
+  return true;
 }
 
 // A coarse level of the point kernel: its right-hand side is formed here from
