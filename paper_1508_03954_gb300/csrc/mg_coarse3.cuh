@@ -92,7 +92,20 @@ __global__ void __launch_bounds__(128) coarse3_kernel(const Coarse3Args<R> A) {
     const long long iv = valid ? i : 0;
     const int x = (int)(iv % N), y = (int)((iv / N) % N), z = (int)(iv / ((long long)N * N));
     const bool inner = valid && x > 0 && x < n && y > 0 && y < n && z > 0 && z < n;
-    int ty = 0;
+    const int ty = inner ? (int)A.typ[x] + 4 * (int)A.typ[y] + 16 * (int)A.typ[z] : 0;
+    int gt = 0;
+    bool greal = true;
+    if (inner && A.fused) {
+      const int G = kMaxG3;
+      const int gx = A.gtyp[x], gy = A.gtyp[y], gz = A.gtyp[z];
+      gt = gx + G * (gy + G * gz);
+      greal = (((A.greal >> gx) & (A.greal >> gy) & (A.greal >> gz)) & 1u) != 0u;
+    }
+    // one path per warp: a warp at a layer edge holds real and complex rows,
+    // and the complex path gives real rows the same sums (zero imaginary
+    // parts), so taking it for the whole warp avoids running both
+    const bool hreal = __all_sync(0xffffffffu, !inner || ((A.realrow >> ty) & 1ull) != 0ull);
+    const bool greal_w = __all_sync(0xffffffffu, greal);
     C pb = cz<R>(), ph = cz<R>();
     if (inner) {
       if (A.fused) {
@@ -116,18 +129,14 @@ __global__ void __launch_bounds__(128) coarse3_kernel(const Coarse3Args<R> A) {
         }
         pb = rmul(R(1) / R(27), pb);
         // + G_l u_l: the Galerkin row of the vertex's three 1D classes
-        const int G = kMaxG3;
-        const int gx = A.gtyp[x], gy = A.gtyp[y], gz = A.gtyp[z];
-        const C* gc = A.gcoef + (gx + G * (gy + G * gz)) * 27;
-        if ((((A.greal >> gx) & (A.greal >> gy) & (A.greal >> gz)) & 1u) != 0u)
+        const C* gc = A.gcoef + gt * 27;
+        if (greal_w)
           pb = row27_part<R, LPV, true>(gc, A.u, i, N, q, pb);
         else
           pb = row27_part<R, LPV, false>(gc, A.u, i, N, q, pb);
       }
-      ty = (int)A.typ[x] + 4 * (int)A.typ[y] + 16 * (int)A.typ[z];
       const C* cf = A.coef + ty * 27;
-      ph = ((A.realrow >> ty) & 1ull) ? row27_part<R, LPV, true>(cf, A.u, i, N, q, ph)
-                                      : row27_part<R, LPV, false>(cf, A.u, i, N, q, ph);
+      ph = hreal ? row27_part<R, LPV, true>(cf, A.u, i, N, q, ph) : row27_part<R, LPV, false>(cf, A.u, i, N, q, ph);
     }
 #pragma unroll
     for (int o = LPV / 2; o > 0; o >>= 1) {

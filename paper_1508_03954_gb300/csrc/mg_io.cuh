@@ -68,12 +68,16 @@ __global__ void mass_pass3_kernel(int n, int xs, const cplx<double>* __restrict_
        i += (long long)gridDim.x * blockDim.x) {
     const int g0 = (int)(i % N), g1 = (int)((i / N) % N), g2 = (int)(i / ((long long)N * N));
     const int ga = AX == 0 ? g0 : (AX == 1 ? g1 : g2);
+    const bool in = ga > 0 && ga < n;
+    const int t = in ? typ[ga] : 0;
+    // one path per warp (the complex one gives real rows the same result):
+    // along x a warp often holds both classes
+    const bool wreal = __all_sync(__activemask(), ((rows.real >> t) & 1u) != 0u);
     cplx<double> v = cz<double>();
-    if (ga > 0 && ga < n) {
-      const int t = typ[ga];
+    if (in) {
       const long long j = (((long long)g2 * xs) * Nx + (long long)g1 * xs) * Nx + (long long)g0 * xs;
       const cplx<double> a = x[j - st], b = x[j], d = x[j + st];
-      if ((rows.real >> t) & 1u)
+      if (wreal)
         v = rfma(rows.m[t][2].x, d, rfma(rows.m[t][1].x, b, rmul(rows.m[t][0].x, a)));
       else
         v = cfma(rows.m[t][2], d, cfma(rows.m[t][1], b, rows.m[t][0] * a));
