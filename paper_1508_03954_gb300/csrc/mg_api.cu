@@ -1866,7 +1866,9 @@ int ensure_r0(mg_ctx* c) {
 }
 
 // rhs of level s from the stored nodal f: b_s = M_s (f sampled on level s)
-int set_level_rhs(mg_ctx* c, int s) {
+// b_s = M_s f.  fhost (3D, s = L only): a device view of page-locked host
+// memory holding f, copied into f_dev by the z-pass itself.
+int set_level_rhs(mg_ctx* c, int s, const cplx<double>* fhost = nullptr) {
   auto& H = c->h64;
   cudaError_t e;
   if (c->d == 3) {
@@ -1887,7 +1889,11 @@ int set_level_rhs(mg_ctx* c, int s) {
     }
     const int g = grid_for(V.nv);
     c->launches += 3;
-    mg::mass_pass3_kernel<2><<<g, kThreads, 0, c->stream>>>(V.n, (int)ipow(3, c->L - s), c->f_dev, V.b, V.typ, mr);
+    if (fhost != nullptr && s == c->L)
+      mg::mass_z_copy_kernel<<<grid_for((size_t)(V.n + 1) * (V.n + 1)), kThreads, 0, c->stream>>>(
+          V.n, fhost, c->f_dev, V.b, V.typ, mr);
+    else
+      mg::mass_pass3_kernel<2><<<g, kThreads, 0, c->stream>>>(V.n, (int)ipow(3, c->L - s), c->f_dev, V.b, V.typ, mr);
     mg::mass_pass3_kernel<1><<<g, kThreads, 0, c->stream>>>(V.n, 1, V.b, c->scratch, V.typ, mr);
     mg::mass_pass3_kernel<0><<<g, kThreads, 0, c->stream>>>(V.n, 1, c->scratch, V.b, V.typ, mr);
     e = cudaGetLastError();
@@ -3047,6 +3053,13 @@ int mg_set_rhs(mg_ctx* c, const mg_c128* f, int on_device) {
   }
   const size_t nv = c->d == 4 ? c->h4->lev[c->L].nv : c->h64.lev[c->L].nv;
   const cplx<double>* fv = on_device ? nullptr : pinned_view(reinterpret_cast<const cplx<double>*>(f));
+  if (fv != nullptr && c->d == 3) {
+    // the z-pass of b = M f copies f on its way (one pass over the host link)
+    int rc = set_level_rhs(c, c->L, fv);
+    if (rc != MG_OK) return rc;
+    c->r0 = -1.0;
+    return MG_OK;
+  }
   if (fv != nullptr) {
     ++c->launches;
     mg::copy_c128_kernel<<<grid_for(nv), kThreads, 0, c->stream>>>((long long)nv, fv, c->f_dev);

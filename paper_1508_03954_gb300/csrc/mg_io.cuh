@@ -86,4 +86,39 @@ __global__ void mass_pass3_kernel(int n, int xs, const cplx<double>* __restrict_
   }
 }
 
+// The z-pass of b = M f fused with the copy of f from page-locked host memory:
+// one thread per (x, y) column marches along z, reads each value of f over
+// the host link once, stores it into fcopy (the device copy later passes and
+// FMG stages sample) and stores y = M_z f (zero on the z = 0 and z = n
+// planes).  The z-pass arithmetic is that of mass_pass3_kernel<2>, so b is
+// bit for bit the same as from a staged copy; the pass costs no time of its
+// own, since the host link is the slower part.
+__global__ void mass_z_copy_kernel(int n, const cplx<double>* __restrict__ f, cplx<double>* __restrict__ fcopy,
+                                   cplx<double>* __restrict__ y, const uint8_t* __restrict__ typ,
+                                   const MassRows3 rows) {
+  const int N = n + 1;
+  const long long NN = (long long)N * N;
+  for (long long col = blockIdx.x * (long long)blockDim.x + threadIdx.x; col < NN;
+       col += (long long)gridDim.x * blockDim.x) {
+    cplx<double> fm = f[col], f0 = f[NN + col];
+    fcopy[col] = fm;
+    fcopy[NN + col] = f0;
+    y[col] = cz<double>();
+    for (int z = 1; z < n; ++z) {
+      const cplx<double> fp = f[(long long)(z + 1) * NN + col];
+      fcopy[(long long)(z + 1) * NN + col] = fp;
+      const int t = typ[z];  // one class per plane: every lane takes the same path
+      cplx<double> v;
+      if ((rows.real >> t) & 1u)
+        v = rfma(rows.m[t][2].x, fp, rfma(rows.m[t][1].x, f0, rmul(rows.m[t][0].x, fm)));
+      else
+        v = cfma(rows.m[t][2], fp, cfma(rows.m[t][1], f0, rows.m[t][0] * fm));
+      y[(long long)z * NN + col] = v;
+      fm = f0;
+      f0 = fp;
+    }
+    y[(long long)n * NN + col] = cz<double>();
+  }
+}
+
 }  // namespace mg
