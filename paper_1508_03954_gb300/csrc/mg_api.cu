@@ -1272,7 +1272,8 @@ cudaError_t sweep3(mg_ctx* c, Hier<R>& H, int l, bool fine, int hb, int hier, co
     // complex64: the separable sweep from 27 cells per axis; complex128: from
     // 27 on the finest level, from 81 on coarse levels (a 27-cell level has
     // nine units of the separable layout, too few for the FP64 pipes of the
-    // GPU: within a cycle the small-tile sweep is faster there)
+    // GPU).  Within a cycle, coarse levels of up to 81 cells per axis run the
+    // point kernel instead (sweep() dispatches them before this function).
     if constexpr (std::is_same<R, float>::value) {
       if (H.lev[l].n >= 27) return launch_sweep3s(c, H, l, fine, hb, hier, om);
     } else {

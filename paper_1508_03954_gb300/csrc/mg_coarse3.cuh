@@ -1,5 +1,5 @@
-// mg_coarse3.cuh -- coarse 3D levels with a constant shift, one thread per
-// vertex (sm_103a).
+// mg_coarse3.cuh -- coarse 3D levels with a constant shift, one thread (or a
+// small group of lanes) per vertex, and the separable 3D corrections (sm_103a).
 //
 // The step is the one of the level sweeps (Appendix A Algorithm 4 on a coarse
 // level l: r_l = b_l - H_l u_l, du_l = omega_l D_l^{-1} r_l, the c-point mask
@@ -7,9 +7,9 @@
 // next coarser level's kernel from the stored residual instead of inside a
 // z-marching tile:
 //     b_{l-1} = R r_l + G_{l-1} u_{l-1}     (G = R H P, Eq. HTMG by linearity)
-// so a level is one launch of (3^l + 1)^3 threads with no halo, no plane
-// pipeline and no warm-up: the small levels of a 3D hierarchy (at most a few
-// hundred thousand vertices) are latency-bound in a marching sweep, whose
+// so a level is one launch over its (3^l + 1)^3 vertices with no halo, no
+// plane pipeline and no warm-up: the small levels of a 3D hierarchy (at most a
+// few hundred thousand vertices) are latency-bound in a marching sweep, whose
 // blocks each walk several planes in series while most SMs idle.
 //
 // With the BPX transfer (and no hb mask) the kernel stores du_l and its
