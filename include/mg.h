@@ -337,10 +337,14 @@ int mg_batch_set_stream(mg_batch* batch, void* cuda_stream);
 
 /* Solves every problem to relative FP64 residual tol (relative to its
  * residual at the start of the call), at most max_outer outer steps of
- * inner_cycles complex64 cycles each.  omega: n host pointers, problem p's
- * has depth_p entries.  Per problem: status (MG_OK / MG_NOT_CONVERGED /
- * MG_DIVERGED), inner cycles run and final relative residual (any output
- * may be NULL).  Returns MG_OK unless the call itself failed. */
+ * inner_cycles complex64 cycles each.  Each step measures the residual of
+ * the iterate entering it, so a problem leaves the batch after the step
+ * whose entering residual is at most tol; that step is still applied to it
+ * (and counted).  omega: n host pointers, problem p's has depth_p entries.
+ * Per problem: status (MG_OK / MG_NOT_CONVERGED / MG_DIVERGED, the first
+ * two from the FP64 residual of the returned solution), inner cycles run and
+ * final relative residual (any output may be NULL).  Returns MG_OK unless
+ * the call itself failed. */
 int mg_batch_solve(mg_batch* batch, int variant, const mg_c128* const* omega, int transfer,
                    double tol, int max_outer, int inner_cycles, int* status, int* cycles,
                    double* rel_res);
