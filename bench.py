@@ -1062,12 +1062,20 @@ def profile_sequence(mg, torch, which):
         s.set_rhs(c["f"])
         for _ in range(3):
             s.cycle(mg.MG_BPX, np.full(5, 0.6), mg.MG_HIERARCHICAL)
-    else:
+    elif which == "refine3d":
         c = W.definite(W.config3())
         s = mg.Solver(3, 5, c["k2"], c["theta"], c["layer_width"])
         s.set_rhs(c["f"])
         s.set_precision(mg.MG_C64_REFINE, INNER)
         s.solve(mg.MG_ADD, mg.omega_scheme(mg.MG_OMEGA_EXP, 0.6, 5), mg.MG_DLINEAR, 1e-30, INNER)
+    else:
+        # 2D depth 8 (6561^2 cells, 43 M vertices), definite k^2 = -(20 pi)^2,
+        # 10% layer, one Gaussian source
+        depth = 8
+        s = mg.Solver(2, depth, W.constant_k2(2, depth, -(20 * math.pi) ** 2), W.THETA, 0.1)
+        s.set_rhs(W.gaussian(2, depth, (0.45, 0.55), 0.05))
+        s.set_precision(mg.MG_C64_REFINE, INNER)
+        s.solve(mg.MG_ADD, mg.omega_scheme(mg.MG_OMEGA_EXP, 0.6, depth), mg.MG_DLINEAR, 1e-30, INNER)
     torch.cuda.synchronize()
     print(json.dumps({"profile": which, "ok": True}), flush=True)
     s.close()
@@ -1101,10 +1109,11 @@ def main():
     ap.add_argument("--form", choices=sorted(form_table(None, None, {}).keys()), default=None,
                     help="run only this form and print its result (profiling)")
     ap.add_argument("--four-d-depth", type=int, default=4, help="depth of the four_d form (profiling)")
-    ap.add_argument("--profile", choices=["cycle3d", "refine3d"], default=None,
+    ap.add_argument("--profile", choices=["cycle3d", "refine3d", "refine2d8"], default=None,
                     help="run a short fixed sequence for a profiler and exit: cycle3d = three complex128 "
                          "BPX cycles of the headline workload, refine3d = one outer step (16 complex64 "
-                         "cycles) of the 3D depth-5 refinement form")
+                         "cycles) of the 3D depth-5 refinement form, refine2d8 = one outer step of the "
+                         "2D depth-8 refinement form (the fine level's strips take two columns per lane)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
