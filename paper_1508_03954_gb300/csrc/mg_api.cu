@@ -1265,8 +1265,11 @@ cudaError_t launch_sweep2w(mg_ctx* c, Hier<float>& H, int l, bool fine, int hb, 
   A.partial = H.partial;
   A.ticket = H.ticket;
   A.norm2 = fine ? H.norm2 : nullptr;
-  // about six coarse rows per warp, one wave of resident blocks at most
-  const int warps = std::max(1, std::min(A.nunits / 6, 152 * MG_S2W_MINB * 8));
+  // about six coarse rows per warp (three where that gives less than one
+  // wave: more warps to hide a small level's latency), one wave of resident
+  // blocks at most
+  const int upw = A.nunits / 6 < 152 * MG_S2W_MINB * 8 ? 3 : 6;
+  const int warps = std::max(1, std::min(A.nunits / upw, 152 * MG_S2W_MINB * 8));
   const int grid = (warps + 7) / 8;
   mg::sweep2w_kernel<<<grid, mg::kS2wThreads, 0, c->stream>>>(A);
   return cudaGetLastError();
